@@ -1,0 +1,52 @@
+"""Plant plausible mistakes in a copy of the oracle and check that the pins catch them.
+
+Each mutant is a one-line edit of ``oracle/band_oracle.c`` (a dropped term, a wrong
+index, a flipped sign, a transposed operand), compiled into a temporary library and
+loaded by the pin tests through BAND_ORACLE_LIB.  The pins must fail for every one.
+Runs on the CPU only.
+"""
+import os
+import subprocess
+import sys
+
+import pytest
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+SRC = os.path.join(ROOT, "oracle", "band_oracle.c")
+
+MUTANTS = {
+    "npdm_gamma_wrong_index": ("g = op_sub(b[i], op_mul(alpha[i - 2], a[i], ops), ops);",
+                               "g = op_sub(b[i], op_mul(alpha[i - 1], a[i], ops), ops);"),
+    "npdm_mu_dropped_beta": ("if (i >= 2) m = op_sub(m, op_mul(beta[i - 2], a[i], ops), ops);", ""),
+    "npdm_back_sign": ("x[i] = op_sub(xi, op_mul(beta[i], x[i + 2], ops), ops);",
+                       "x[i] = op_add(xi, op_mul(beta[i], x[i + 2], ops), ops);"),
+    "npdm_z_dropped_term": ("if (i >= 2) zi = op_sub(zi, op_mul(z[i - 2], a[i], ops), ops);", ""),
+    "ntdm_transposed_operand": ("if (i <= n - 2) alpha[i] = op_div(d[i], mu, ops);",
+                                "if (i <= n - 2) alpha[i] = op_div(b[i + 1], mu, ops);"),
+    "gepp_rhs_not_swapped": ("double t = x[j]; x[j] = x[p]; x[p] = t;", ""),
+    "laurent_division_sign": ("for (int j = 1; k - j >= v; ++j) s -= y->q[vy + j + LP] * r.q[k - j + LP];",
+                              "for (int j = 1; k - j >= v; ++j) s += y->q[vy + j + LP] * r.q[k - j + LP];"),
+    "ilu0_wrong_operand": ("w[2] = w[2] - w[0] * u2[i - 2];", "w[2] = w[2] - w[0] * u1[i - 2];"),
+    "hb_missing_2I": ("double y = (m == j ? 2.0 : 0.0) - band_get(P, n, wp, lower, m, j);",
+                      "double y = (m == j ? 1.0 : 0.0) - band_get(P, n, wp, lower, m, j);"),
+    "sip_residual_sign": ("r[i] = op_sub(f[i], s, ops);", "r[i] = op_sub(s, f[i], ops);"),
+    "refine_missing_rescale": ("double dl = s * (double)x32[i];", "double dl = (double)x32[i];"),
+    "adjoint_not_transposed": ("if (i >= 1) tb[i] = d[i - 1];", "if (i >= 1) tb[i] = b[i];"),
+}
+
+
+@pytest.mark.parametrize("name", sorted(MUTANTS))
+def test_pins_catch_planted_mistake(name, tmp_path):
+    old, new = MUTANTS[name]
+    src = open(SRC).read()
+    assert src.count(old) == 1, "mutation anchor must be unique: " + name
+    mutated = tmp_path / "mutant.c"
+    mutated.write_text(src.replace(old, new))
+    lib = tmp_path / "libmutant.so"
+    subprocess.run(["gcc", "-O2", "-ffp-contract=off", "-std=c11", "-fPIC", "-shared", "-pthread",
+                    "-o", str(lib), str(mutated), "-lm"], check=True)
+    env = dict(os.environ, BAND_ORACLE_LIB=str(lib))
+    res = subprocess.run([sys.executable, "-m", "pytest", "-x", "-q", "-p", "no:cacheprovider",
+                          os.path.join(ROOT, "tests", "test_oracle_pins.py")],
+                         cwd=ROOT, env=env, capture_output=True, text=True, timeout=600)
+    assert res.returncode != 0, "pins did not catch mutant %s:\n%s" % (name, res.stdout[-2000:])

@@ -1,0 +1,511 @@
+"""Pins for the CPU oracle: checks against things other than the oracle itself.
+
+Each test ties an oracle routine to the paper (operation counts, Table 7), to
+closed forms, to exact rational arithmetic, or to invariants of the mathematics,
+chosen so that a dropped term, wrong sign, wrong index or transposed operand in
+the oracle fails at least one of them (see test_oracle_mutations.py).
+"""
+import json
+import math
+import os
+from fractions import Fraction
+
+import numpy as np
+import pytest
+
+import oracle
+import synth
+from oracle import exact
+
+GOLD = os.path.join(os.path.dirname(__file__), "golden")
+U = np.finfo(np.float64).eps / 2
+
+
+def _rand_pd(rng, n, dominant=True, k=2):
+    z = lambda: rng.uniform(-1, 1, n)
+    a, b, d, e = z(), z(), z(), z()
+    if k == 1:
+        a[:] = 0
+        e[:] = 0
+    a[:2] = 0
+    b[:1] = 0
+    d[n - 1:] = 0
+    e[max(n - 2, 0):] = 0
+    off = np.abs(a) + np.abs(b) + np.abs(d) + np.abs(e)
+    c = (1 + off) if dominant else rng.uniform(-1, 1, n)
+    return a, b, c, d, e
+
+
+def _dense(k, a, b, c, d, e):
+    n = len(c)
+    A = np.diag(c).astype(float)
+    for i in range(n):
+        if i >= 1:
+            A[i, i - 1] = b[i]
+        if i + 1 < n:
+            A[i, i + 1] = d[i]
+        if k == 2 and i >= 2:
+            A[i, i - 2] = a[i]
+        if k == 2 and i + 2 < n:
+            A[i, i + 2] = e[i]
+    return A
+
+
+# ------------------------------------------------------------ Table 7 counts
+def test_npdm_operation_count_is_19N_minus_29():
+    """Table 7: NPDM costs 19N - 29 operations (valid for N >= 2)."""
+    spec = json.load(open(os.path.join(GOLD, "table7_op_counts.json")))["NPDM"]
+    rng = np.random.default_rng(7)
+    for n in (2, 3, 4, 5, 7, 16, 128, 1000):
+        a, b, c, d, e = _rand_pd(rng, n)
+        x, st, ops = oracle.npdm(a, b, c, d, e, rng.uniform(-1, 1, n), count_ops=True)
+        assert st == "OK"
+        assert ops == spec["coef"] * n + spec["const"], n
+
+
+def test_ntdm_operation_count_recorded():
+    """R1 performs the textbook 8N - 7; Table 7 prints 9N + 2 (parity unpinned)."""
+    spec = json.load(open(os.path.join(GOLD, "table7_op_counts.json")))["NTDM"]
+    rng = np.random.default_rng(8)
+    for n in (2, 10, 100):
+        _, b, c, d, _ = _rand_pd(rng, n, k=1)
+        _, st, ops = oracle.ntdm(b, c, d, rng.uniform(-1, 1, n), count_ops=True)
+        assert ops == 8 * n - 7
+        assert spec["coef"] * n + spec["const"] != ops   # recorded difference
+
+
+# ------------------------------------------------------------- closed forms
+def _tinv_exact(n):
+    """(T^{-1})_{ij} = min(i,j) (n+1-max(i,j)) / (n+1), 1-based, T = tridiag(-1, 2, -1)."""
+    return [[Fraction(min(i, j) * (n + 1 - max(i, j)), n + 1) for j in range(1, n + 1)]
+            for i in range(1, n + 1)]
+
+
+@pytest.mark.parametrize("n", [1, 2, 3, 17, 64, 1000])
+def test_toeplitz_td_closed_form(n):
+    """tridiag(-1, 2, -1) x = 1 has x_i = i (n+1-i) / 2 (1-based)."""
+    b = np.full(n, -1.0)
+    c = np.full(n, 2.0)
+    d = np.full(n, -1.0)
+    f = np.ones(n)
+    i = np.arange(1, n + 1)
+    want = i * (n + 1 - i) / 2.0
+    tol = 4 * n * U * np.abs(want).max() + 1e-300
+    for x, st in (oracle.ntdm(b, c, d, f), oracle.gepp_band(1, None, b, c, d, None, f)[:2],
+                  oracle.symbolic(1, None, b, c, d, None, f)[:2]):
+        assert st == "OK"
+        assert np.abs(x - want).max() <= max(tol, 1e-12)
+
+
+@pytest.mark.parametrize("n", [3, 6, 11])
+def test_toeplitz_td_inverse_closed_form(n):
+    """Random f: GEPP and NTDM equal the closed-form inverse applied exactly."""
+    rng = np.random.default_rng(n)
+    f = rng.integers(-5, 6, n).astype(float)
+    Ti = _tinv_exact(n)
+    want = np.array([float(sum(Ti[i][j] * Fraction(f[j]) for j in range(n))) for i in range(n)])
+    b, c, d = np.full(n, -1.0), np.full(n, 2.0), np.full(n, -1.0)
+    x1, _ = oracle.ntdm(b, c, d, f)
+    x2, _, det = oracle.gepp_band(1, None, b, c, d, None, f)
+    assert np.allclose(x1, want, rtol=1e-13, atol=1e-13)
+    assert np.allclose(x2, want, rtol=1e-13, atol=1e-13)
+    assert abs(det - (n + 1)) <= 1e-12 * (n + 1)        # det tridiag(-1,2,-1) = n + 1
+
+
+@pytest.mark.parametrize("n", [3, 5, 12, 40])
+def test_toeplitz_square_pd_closed_form(n):
+    """T^2 = pentadiag(1, -4, 6, -4, 1) with corner diagonal entries 5, solved by
+    applying the closed-form T^{-1} twice in exact rationals."""
+    rng = np.random.default_rng(100 + n)
+    f = rng.integers(-5, 6, n).astype(float)
+    Ti = _tinv_exact(n)
+    y = [sum(Ti[i][j] * Fraction(f[j]) for j in range(n)) for i in range(n)]
+    want = np.array([float(sum(Ti[i][j] * y[j] for j in range(n))) for i in range(n)])
+    a, e = np.ones(n), np.ones(n)
+    b, d = np.full(n, -4.0), np.full(n, -4.0)
+    c = np.full(n, 6.0)
+    c[0] = c[-1] = 5.0
+    kappa = (n + 1) ** 4
+    for x, st in (oracle.npdm(a, b, c, d, e, f)[:2], oracle.gepp_band(2, a, b, c, d, e, f)[:2],
+                  oracle.symbolic(2, a, b, c, d, e, f)[:2]):
+        assert st == "OK"
+        assert np.abs(x - want).max() <= 8 * kappa * U * np.abs(want).max() + 1e-14
+    _, _, det = oracle.gepp_band(2, a, b, c, d, e, f)
+    assert abs(det - (n + 1) ** 2) <= 1e-9 * (n + 1) ** 2   # det T^2 = (n+1)^2
+
+
+# ------------------------------------------------------ exact rational brute force
+def _int_system(rng, k, n, dominant):
+    a = [int(rng.integers(-3, 4)) if (k == 2 and i >= 2) else 0 for i in range(n)]
+    b = [int(rng.integers(-3, 4)) if i >= 1 else 0 for i in range(n)]
+    d = [int(rng.integers(-3, 4)) if i <= n - 2 else 0 for i in range(n)]
+    e = [int(rng.integers(-3, 4)) if (k == 2 and i <= n - 3) else 0 for i in range(n)]
+    if dominant:
+        c = [1 + abs(a[i]) + abs(b[i]) + abs(d[i]) + abs(e[i]) for i in range(n)]
+    else:
+        c = [int(rng.integers(-4, 5)) for i in range(n)]
+    f = [int(rng.integers(-6, 7)) for i in range(n)]
+    return a, b, c, d, e, f
+
+
+@pytest.mark.parametrize("k", [1, 2])
+@pytest.mark.parametrize("dominant", [True, False])
+def test_direct_methods_vs_exact_rational(k, dominant):
+    """R1/R2 (float) and R0 (float) against exact Gaussian elimination, n <= 12;
+    the exact R1/R2 recurrences equal exact GE exactly whenever no pivot is zero."""
+    rng = np.random.default_rng(11 + k + 10 * dominant)
+    checked = 0
+    for trial in range(60):
+        n = int(rng.integers(1, 13))
+        a, b, c, d, e, f = _int_system(rng, k, n, dominant)
+        A = exact.dense(k, a, b, c, d, e)
+        xe, det = exact.ge_solve(A, f)
+        if det == 0:
+            continue
+        xe_f = np.array([float(v) for v in xe])
+        An = _dense(k, *(np.array(v, float) for v in (a, b, c, d, e)))
+        kappa = np.linalg.cond(An, np.inf)
+        scale = np.abs(xe_f).max() or 1.0
+        try:
+            xl = exact.lu_solve(k, a, b, c, d, e, f)
+            assert xl == xe                    # same rational, other algorithm
+            if k == 2:
+                x, st = oracle.npdm(*(np.array(v, float) for v in (a, b, c, d, e, f)))
+            else:
+                x, st = oracle.ntdm(*(np.array(v, float) for v in (b, c, d, f)))
+            if st == "OK":
+                assert np.abs(x - xe_f).max() <= 1e4 * n * kappa * U * scale
+        except ZeroDivisionError:
+            pass
+        xg, st, dg = oracle.gepp_band(k, *(np.array(v, float) for v in (a, b, c, d, e, f)))
+        assert st == "OK"
+        assert np.abs(xg - xe_f).max() <= 50 * n * kappa * U * scale + 1e-300
+        assert abs(dg - float(det)) <= 1e-10 * abs(float(det))
+        checked += 1
+    assert checked > 20
+
+
+@pytest.mark.parametrize("k", [1, 2])
+def test_symbolic_vs_exact_on_random_integer_systems(k):
+    """R3 in exact rational functions equals exact GE; the C oracle's truncated
+    Laurent arithmetic agrees to rounding; zero pivots occur often here."""
+    rng = np.random.default_rng(21 + k)
+    flagged = 0
+    for trial in range(80):
+        n = int(rng.integers(1, 10))
+        a, b, c, d, e, f = _int_system(rng, k, n, dominant=False)
+        A = exact.dense(k, a, b, c, d, e)
+        xe, det = exact.ge_solve(A, f)
+        sym = exact.symbolic_solve(k, a, b, c, d, e, f)
+        x, st, dm, dex, nf = oracle.symbolic(k, *(np.array(v, float) for v in (a, b, c, d, e, f)))
+        if det == 0:
+            assert sym["status"] == "SINGULAR"
+            assert st in ("SINGULAR", "SYMBOLIC_RANGE")
+            continue
+        assert sym["status"] == "OK"
+        assert sym["x"] == xe
+        assert sym["det"] == det
+        assert nf == sym["nflag"]
+        flagged += nf > 0
+        assert st == "OK"
+        xe_f = np.array([float(v) for v in xe])
+        An = _dense(k, *(np.array(v, float) for v in (a, b, c, d, e)))
+        kappa = np.linalg.cond(An, np.inf)
+        assert np.abs(x - xe_f).max() <= 1e3 * kappa * U * (np.abs(xe_f).max() or 1.0)
+        assert abs(dm * 2.0 ** dex - float(det)) <= 1e-9 * abs(float(det))
+    assert flagged >= 3
+
+
+def _golden_cases():
+    return json.load(open(os.path.join(GOLD, "zero_pivot_cases.json")))["cases"]
+
+
+@pytest.mark.parametrize("case", _golden_cases(), ids=lambda c: c["name"])
+def test_zero_pivot_golden_cases(case):
+    """Hand-made exact zero pivots (Sec. 1) and singular systems (Sec. 3.2 Remark 1)."""
+    fl = lambda key: np.array([float(Fraction(v)) for v in case[key]])
+    k = case["k"]
+    diags = [fl(key) for key in "abcdef"]
+    x, st, dm, dex, nf = oracle.symbolic(k, *diags)
+    assert st == case["status"]
+    assert nf == case["nflag"]
+    sym = exact.symbolic_solve(k, *[[Fraction(v) for v in case[key]] for key in "abcdef"])
+    assert sym["status"] == case["status"]
+    if case["status"] == "OK":
+        want = fl("x")
+        assert [str(v) for v in sym["x"]] == case["x"]
+        assert np.abs(x - want).max() <= 1e-12 * max(1.0, np.abs(want).max())
+        assert abs(dm * 2.0 ** dex - float(Fraction(case["det"]))) <= 1e-12 * abs(float(Fraction(case["det"])))
+        # the numeric method stops at the zero pivot
+        if k == 2:
+            assert oracle.npdm(*diags)[1] == "ZERO_PIVOT"
+        else:
+            assert oracle.ntdm(diags[1], diags[2], diags[3], diags[5])[1] == "ZERO_PIVOT"
+
+
+def test_td_swap_is_f_swapped():
+    x, st, dm, dex, nf = oracle.symbolic(1, None, np.array([0.0, 1.0]), np.array([0.0, 0.0]),
+                                         np.array([1.0, 0.0]), None, np.array([3.0, 5.0]))
+    assert st == "OK" and nf == 1
+    assert list(x) == [5.0, 3.0]
+
+
+def test_symbolic_equals_numeric_bitwise_without_zero_pivots():
+    """With no zero pivot every series is a plain number, so R3 performs R2's
+    operations in R2's order."""
+    rng = np.random.default_rng(5)
+    for k in (1, 2):
+        a, b, c, d, e = _rand_pd(rng, 300, dominant=False, k=k)
+        f = rng.uniform(-1, 1, 300)
+        xs, st, *_ = oracle.symbolic(k, a, b, c, d, e, f)
+        xn = oracle.npdm(a, b, c, d, e, f)[0] if k == 2 else oracle.ntdm(b, c, d, f)[0]
+        assert st == "OK"
+        assert np.array_equal(xs, xn)
+
+
+# ----------------------------------------------------- manufactured solutions
+@pytest.mark.parametrize("k", [1, 2])
+def test_manufactured_dominant(k):
+    B = synth.cfg0(nsys=16, n=128, k=k)
+    xt = B["x_true"].reshape(128, 16)
+    for s in range(16):
+        S = synth.system(B, s)
+        if k == 2:
+            x, st = oracle.npdm(*(S[q] for q in "abcdef"))
+        else:
+            x, st = oracle.ntdm(S["b"], S["c"], S["d"], S["f"])
+        assert st == "OK"
+        assert np.abs(x - xt[:, s]).max() <= 128 * 8 * U
+
+
+def test_out_of_matrix_slots_are_ignored():
+    rng = np.random.default_rng(3)
+    n = 9
+    a, b, c, d, e = _rand_pd(rng, n)
+    f = rng.uniform(-1, 1, n)
+    ref = oracle.npdm(a, b, c, d, e, f)[0]
+    a2, b2, d2, e2 = a.copy(), b.copy(), d.copy(), e.copy()
+    a2[:2] = np.nan
+    b2[0] = np.inf
+    d2[-1] = np.nan
+    e2[-2:] = np.nan
+    for x in (oracle.npdm(a2, b2, c, d2, e2, f)[0], oracle.symbolic(2, a2, b2, c, d2, e2, f)[0],
+              oracle.gepp_band(2, a2, b2, c, d2, e2, f)[0]):
+        assert np.allclose(x, ref, rtol=1e-14, atol=1e-14)
+
+
+# --------------------------------------------------------------- invariants
+def test_ilu0_equals_npdm_factorisation():
+    """For a pentadiagonal pattern ILU(0) drops nothing: U's diagonal is NPDM's mu,
+    and K = LU - A is at the rounding level (Algorithm 1's K)."""
+    rng = np.random.default_rng(9)
+    n = 200
+    a, b, c, d, e = _rand_pd(rng, n, dominant=False)
+    (l2, l1, u0, u1, u2), st = oracle.ilu0(a, b, c, d, e)
+    assert st == "OK"
+    _, st2, (gam, mu, alpha, beta) = oracle.npdm(a, b, c, d, e, np.ones(n), factors=True)
+    assert st2 == "OK"
+    assert np.allclose(u0, mu, rtol=1e-10, atol=0)
+    assert np.allclose(u1[:-1], (alpha * mu)[:-1], rtol=1e-10, atol=1e-14)
+    assert np.allclose(l1[1:] * u0[:-1], gam[1:], rtol=1e-10, atol=1e-14)
+    assert np.array_equal(u2[:-2], e[:-2])
+    K = oracle.lu_minus_a((l2, l1, u0, u1, u2), a, b, c, d, e)
+    An = _dense(2, a, b, c, d, e)
+    L = np.eye(n) + np.diag(l1[1:], -1) + np.diag(l2[2:], -2)
+    Um = np.diag(u0) + np.diag(u1[:-1], 1) + np.diag(u2[:-2], 2)
+    assert np.abs(L @ Um - An).max() <= 1e-10 * np.abs(An).max()
+    assert max(np.abs(v).max() for v in K) <= 1e-10 * np.abs(An).max()
+
+
+@pytest.mark.parametrize("n", [5, 16, 37])
+def test_hotelling_bodewig_exact_for_full_width(n):
+    """With w >= n the HB error squares, E_{k+1} = E_k^2, and E_0 = I - L X_0 is
+    strictly lower triangular, so X is L^{-1} after ceil(log2 n) iterations and not
+    before.  L = unit lower with l1 = l2 = 1 has an integer, non-decaying inverse."""
+    ones = np.ones(n)
+    L = np.eye(n) + np.diag(ones[1:], -1) + np.diag(ones[2:], -2)
+    Linv = np.rint(np.linalg.inv(L))
+    its = math.ceil(math.log2(n))
+    X, it, st = oracle.hb(n, True, None, ones, ones, max_it=its, tol=0.0)
+    assert it == its
+
+    def dense_lower(Xb):
+        Xd = np.zeros((n, n))
+        for j in range(n):
+            for i in range(j, n):
+                Xd[i, i - j] = Xb[j, i]
+        return Xd
+
+    assert np.array_equal(dense_lower(X), Linv)
+    X1, _, _ = oracle.hb(n, True, None, ones, ones, max_it=its - 1, tol=0.0)
+    assert not np.array_equal(dense_lower(X1), Linv)
+    # convergence is detected one iteration later (no change)
+    X2, it2, st2 = oracle.hb(n, True, None, ones, ones, max_it=60, tol=1e-14)
+    assert st2 == "OK" and it2 == its + 1
+    # the upper factor of a dominant system, from X_0 = diag(U)^{-1}
+    rng = np.random.default_rng(n)
+    a, b, c, d, e = _rand_pd(rng, n)
+    (l2, l1, u0, u1, u2), _ = oracle.ilu0(a, b, c, d, e)
+    Um = np.diag(u0) + np.diag(u1[:-1], 1) + np.diag(u2[:-2], 2)
+    XU, itu, stu = oracle.hb(n, False, u0, u1, u2, max_it=60, tol=1e-14)
+    Xu = np.zeros((n, n))
+    for j in range(n):
+        for i in range(0, n - j):
+            Xu[i, i + j] = XU[j, i]
+    assert stu == "OK"
+    assert np.abs(Xu - np.linalg.inv(Um)).max() <= 1e-10 * np.abs(np.linalg.inv(Um)).max()
+
+
+def test_hotelling_bodewig_fixed_point_equation():
+    """Eq. (1): X_{k+1} = X_k (2I - M X_k), checked densely for one step from X_0."""
+    rng = np.random.default_rng(2)
+    n = 12
+    a, b, c, d, e = _rand_pd(rng, n)
+    (l2, l1, u0, u1, u2), _ = oracle.ilu0(a, b, c, d, e)
+    Um = np.diag(u0) + np.diag(u1[:-1], 1) + np.diag(u2[:-2], 2)
+    X1, _, _ = oracle.hb(n, False, u0, u1, u2, max_it=1, tol=0.0)
+    X0 = np.diag(1.0 / u0)
+    want = X0 @ (2 * np.eye(n) - Um @ X0)
+    got = np.zeros((n, n))
+    for j in range(n):
+        for i in range(0, n - j):
+            got[i, i + j] = X1[j, i]
+    assert np.allclose(got, np.triu(np.tril(want, n), 0), atol=1e-14)
+
+
+def test_sip_algorithm1_and_full_width_hb_one_iteration():
+    """ILU(0) is exact for a PD band, so Algorithm 1 and SIP with w >= n inverses
+    converge after one update to the direct solution."""
+    rng = np.random.default_rng(4)
+    n = 40
+    a, b, c, d, e = _rand_pd(rng, n)
+    f = rng.uniform(-1, 1, n)
+    xg = oracle.gepp_band(2, a, b, c, d, e, f)[0]
+    for w in (0, n):
+        R = oracle.sip(a, b, c, d, e, f, tol=1e-12, max_it=20, hb_width=w, hb_max_it=60,
+                       hb_tol=1e-15)
+        assert R["status"] == "OK"
+        assert R["iters"] == 1
+        assert np.abs(R["x"] - xg).max() <= 1e-13
+
+
+def test_sip_hb_band_converges_on_dominant_systems():
+    rng = np.random.default_rng(6)
+    for n in (50, 500):
+        a, b, c, d, e = _rand_pd(rng, n)
+        f = rng.uniform(-1, 1, n)
+        xg = oracle.gepp_band(2, a, b, c, d, e, f)[0]
+        R = oracle.sip(a, b, c, d, e, f, tol=1e-10, max_it=200, hb_width=5)
+        assert R["status"] == "OK", R["status"]
+        assert 1 < R["iters"] < 60
+        An = _dense(2, a, b, c, d, e)
+        r = f - An @ R["x"]
+        assert np.abs(r).max() < 1e-10 and abs(np.abs(r).max() - R["resid"]) < 1e-15
+        assert np.abs(R["x"] - xg).max() <= 1e-9
+
+
+def test_residual_bound_direct():
+    rng = np.random.default_rng(12)
+    n = 2000
+    a, b, c, d, e = _rand_pd(rng, n)
+    f = rng.uniform(-1, 1, n)
+    x, _ = oracle.npdm(a, b, c, d, e, f)
+    An = _dense(2, a, b, c, d, e)
+    r = f - An @ x
+    assert np.abs(r).max() / (np.abs(An).sum(1).max() * np.abs(x).max()) <= 10 * U
+
+
+# ----------------------------------------------------------------- refinement
+@pytest.mark.parametrize("ratio", [1.01, 1.1, 2.0])
+def test_refinement_reaches_1e10(ratio):
+    rng = np.random.default_rng(int(ratio * 100))
+    n, nsys = 256, 6
+    D = synth.dominant(rng, nsys, n, k=2, dtype=np.float32, ratio=ratio, flip_frac=0.05)
+    xt, f = synth.manufactured(rng, 2, D, nsys, n)
+    for s in range(nsys):
+        d32 = [D[q][:, s] for q in "abcde"]
+        x, steps, st = oracle.refine(*d32, f[:, s])
+        assert st == "OK"
+        xg = oracle.gepp_band(2, *[v.astype(np.float64) for v in d32], f[:, s])[0]
+        err = np.abs(x - xg).max() / np.abs(xg).max()
+        assert err <= 1e-10
+        assert 1 <= steps <= 10
+        # the FP32 solve alone is far from it
+        x0, steps0, _ = oracle.refine(*d32, f[:, s], max_steps=0)
+        assert np.abs(x0 - xg).max() / np.abs(xg).max() > 1e-9
+
+
+# -------------------------------------------------------------------- adjoint
+def test_adjoint_vs_dense_and_finite_differences():
+    rng = np.random.default_rng(13)
+    n = 30
+    a, b, c, d, e = _rand_pd(rng, n)
+    f = rng.uniform(-1, 1, n)
+    w = rng.uniform(-1, 1, n)
+    x = oracle.gepp_band(2, a, b, c, d, e, f)[0]
+    (ga, gb, gc, gd, ge), gf, st = oracle.adjoint(2, a, b, c, d, e, x, w)
+    assert st == "OK"
+    An = _dense(2, a, b, c, d, e)
+    lam = np.linalg.solve(An.T, w)
+    assert np.allclose(gf, lam, rtol=1e-12, atol=1e-14)
+    G = -np.outer(lam, x)
+    for i in range(n):
+        if i >= 2:
+            assert abs(ga[i] - G[i, i - 2]) <= 1e-12
+        if i >= 1:
+            assert abs(gb[i] - G[i, i - 1]) <= 1e-12
+        assert abs(gc[i] - G[i, i]) <= 1e-12
+        if i + 1 < n:
+            assert abs(gd[i] - G[i, i + 1]) <= 1e-12
+        if i + 2 < n:
+            assert abs(ge[i] - G[i, i + 2]) <= 1e-12
+    assert ga[0] == ga[1] == gb[0] == gd[-1] == ge[-1] == ge[-2] == 0.0
+    # central finite differences along a random direction, h = 1e-6
+    h = 1e-6
+    V = [rng.uniform(-1, 1, n) for _ in range(6)]
+    theta = [a, b, c, d, e, f]
+
+    def loss(sign):
+        p = [t + sign * h * v for t, v in zip(theta, V)]
+        return float(w @ oracle.gepp_band(2, *p)[0])
+
+    fd = (loss(+1) - loss(-1)) / (2 * h)
+    an = sum(float(g @ v) for g, v in zip((ga, gb, gc, gd, ge, gf), V))
+    assert abs(fd - an) <= 1e-6 * abs(an)
+
+
+def test_adjoint_td():
+    rng = np.random.default_rng(14)
+    n = 17
+    _, b, c, d, _ = _rand_pd(rng, n, k=1)
+    f, w = rng.uniform(-1, 1, n), rng.uniform(-1, 1, n)
+    x = oracle.ntdm(b, c, d, f)[0]
+    (ga, gb, gc, gd, ge), gf, st = oracle.adjoint(1, None, b, c, d, None, x, w)
+    An = _dense(1, np.zeros(n), b, c, d, np.zeros(n))
+    lam = np.linalg.solve(An.T, w)
+    assert np.allclose(gf, lam, rtol=1e-12)
+    assert np.allclose(gc, -lam * x, rtol=1e-12)
+    assert not ga.any() and not ge.any()
+
+
+# --------------------------------------------------------------- batch driver
+@pytest.mark.parametrize("layout", ["interleaved", "contiguous"])
+def test_batch_driver_layouts(layout):
+    B = synth.cfg0(nsys=8, n=33, layout=layout)
+    x, st, _, _ = oracle.batch("direct", 2, [B[q] for q in "abcde"], B["f"], B["nsys"], B["n"],
+                               B["sys_stride"], B["elem_stride"], nthreads=3)
+    assert (st == 0).all()
+    for s in range(8):
+        S = synth.system(B, s)
+        xs = oracle.npdm(*(S[q] for q in "abcdef"))[0]
+        idx = s * B["sys_stride"] + np.arange(33) * B["elem_stride"]
+        assert np.array_equal(x[idx], xs)
+
+
+def test_batch_driver_ragged():
+    B = synth.cfg2(nsys=40, nmin=3, nmax=60)
+    for method in ("direct", "symbolic", "gepp"):
+        x, st, _, _ = oracle.batch(method, 0, [B[q] for q in "abcde"], B["f"], B["nsys"], 0, 0, 1,
+                                   offsets=B["offsets"], hbw=B["hbw"], nthreads=2)
+        assert (st == 0).all()
+        assert np.abs(x - B["x_true"]).max() <= 1e-13
