@@ -1,0 +1,168 @@
+/*
+ * band.h -- C ABI of libband: batched tridiagonal / pentadiagonal solvers on one
+ * NVIDIA GB300 (sm_103a).
+ *
+ * Methods (Veneva & Ayriyan, "Performance Analysis of Effective Methods for Solving
+ * Band Matrix SLAEs after Parabolic Nonlinear PDEs", arXiv:1804.09666):
+ *   NTDM / NPDM  LU-based direct solvers without pivoting for tridiagonal (TD) and
+ *                pentadiagonal (PD) systems (Sec. 1; cost 9N+2 and 19N-29, Table 7).
+ *   STDM / SPDM  the symbolic variants: a pivot that is exactly zero is replaced by a
+ *                symbol t and the solution is evaluated at the limit t -> 0, so only
+ *                nonsingularity is required (Sec. 1; O(N) determinant, Sec. 3.2
+ *                Remark 1).
+ *   SIP          the Stone method with ILU(0) (Sec. 2, Algorithm 1), optionally with
+ *                Hotelling-Bodewig inverses in place of the substitutions (Remark of
+ *                Sec. 2; Eq. (1) of the Appendix).
+ * The paper solves N independent systems "independently (or in parallel)" per ADI
+ * time step (Sec. 1); every call here solves a batch of such systems.
+ *
+ * Storage.  A system of n rows is given by five row-aligned diagonals
+ *   a[i] = A[i][i-2], b[i] = A[i][i-1], c[i] = A[i][i], d[i] = A[i][i+1], e[i] = A[i][i+2]
+ * (TD systems use b, c, d; a and e may be NULL).  Slots outside the matrix
+ * (a[0], a[1], b[0], d[n-1], e[n-2], e[n-1]) must be readable but never enter the
+ * arithmetic (they may hold NaN).  Right-hand side f, solution x.
+ * Element i of system s of every array lives at
+ *   s * sys_stride + i * elem_stride          (uniform batches, offsets == NULL), or
+ *   offsets[s] + i                             (ragged batches, offsets != NULL),
+ * counted in elements of the array's type.  Interleaved (sys_stride 1, elem_stride
+ * >= nsys) gives coalesced access and is the fast layout; contiguous systems
+ * (elem_stride 1, sys_stride >= n) and any other stride pair are accepted.
+ *
+ * Ownership and asynchrony.  Every pointer except `desc` and the host-side arrays
+ * named as such is a device pointer owned by the caller.  The library allocates no
+ * device memory: scratch comes from the caller's workspace, whose size
+ * band_workspace_size() gives (256-byte aligned).  All calls enqueue work on
+ * `stream` (a cudaStream_t; NULL = the legacy default stream) and return without
+ * waiting.  Inputs are never modified; x may alias f.
+ *
+ * Errors.  The return value reports argument, workspace and launch errors only.
+ * Numerical outcomes are written per system to the device array sys_status
+ * (band_status values; NULL = not wanted).
+ */
+#ifndef BAND_H
+#define BAND_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum {
+  BAND_OK = 0,
+  BAND_ERR_ARG = 1,             /* invalid argument (return value) */
+  BAND_ERR_CUDA = 2,            /* CUDA launch or runtime error (return value) */
+  BAND_ERR_ZERO_PIVOT = 3,      /* per system: NTDM/NPDM met a pivot that is exactly 0 */
+  BAND_ERR_SINGULAR = 4,        /* per system: the determinant's limit is 0 (STDM/SPDM) */
+  BAND_ERR_NONFINITE = 5,       /* per system: Inf or NaN in the result */
+  BAND_ERR_NOT_CONVERGED = 6,   /* per system: SIP / refinement / HB reached its cap */
+  BAND_ERR_SYMBOLIC_RANGE = 7,  /* per system: the Laurent window of the symbolic path ran out */
+  BAND_ERR_INTERNAL = 8,        /* per system: a kernel-side consistency check failed */
+  BAND_ERR_WORKSPACE = 9        /* workspace missing or smaller than band_workspace_size() */
+} band_status;
+
+typedef enum {
+  BAND_NTDM = 0,   /* numeric TD (requires half_bw 1) */
+  BAND_NPDM = 1,   /* numeric PD (requires half_bw 2) */
+  BAND_STDM = 2,   /* symbolic TD */
+  BAND_SPDM = 3,   /* symbolic PD */
+  BAND_AUTO_NUMERIC = 4,   /* NTDM or NPDM per system by its half bandwidth (ragged mixes) */
+  BAND_AUTO_SYMBOLIC = 5   /* STDM or SPDM per system by its half bandwidth */
+} band_method;
+
+typedef enum { BAND_F64 = 0, BAND_F32 = 1 } band_dtype;
+
+typedef struct {
+  int32_t half_bw;        /* 1 = tridiagonal, 2 = pentadiagonal (default when hbw is NULL) */
+  int32_t dtype;          /* band_dtype of the diagonals, f and x */
+  int64_t nsys;           /* number of independent systems, >= 0 */
+  int64_t n;              /* uniform: rows per system (>= 1); ragged: an upper bound on
+                             every system's rows (>= 1) */
+  int64_t sys_stride;     /* uniform: elements between row i of systems s and s+1 */
+  int64_t elem_stride;    /* uniform: elements between rows i and i+1 of one system */
+  const int64_t* offsets; /* ragged: device array of nsys+1 nondecreasing row offsets
+                             (system s = rows offsets[s] .. offsets[s+1]-1); else NULL */
+  const int8_t* hbw;      /* device array of per-system half bandwidths (1 or 2), or NULL */
+  int64_t total_rows;     /* ragged: offsets[nsys] (the host's copy); uniform: ignored */
+} band_desc;
+
+/* Bytes of workspace that the operation `op` needs for `desc` (0 = none).  op is one
+ * of the BAND_OP_* values; `method` as for the call it serves (ignored where n/a). */
+enum {
+  BAND_OP_SOLVE = 0,      /* band_solve */
+  BAND_OP_FACTOR = 1,     /* band_factor: returns the size of the factor buffer */
+  BAND_OP_SIP = 2,        /* band_sip (uses sip_width) */
+  BAND_OP_REFINE = 3,     /* band_refine_solve */
+  BAND_OP_ADJOINT = 4     /* band_adjoint */
+};
+size_t band_workspace_size(const band_desc* desc, int32_t op, int32_t method, int32_t sip_width);
+
+/* Solve A x = f for every system (NTDM/NPDM fused factor + solve, or STDM/SPDM:
+ * the same sweep with an exact zero-pivot test, after which only the flagged
+ * systems are redone in truncated Laurent arithmetic in t and evaluated at t -> 0;
+ * their determinant limit decides BAND_ERR_SINGULAR).
+ * diag[5] = {a, b, c, d, e} device pointers (a, e unused and may be NULL for TD).
+ * factors: NULL for the fused path, or a buffer filled by band_factor() for the same
+ * desc and diagonals (then only NTDM/NPDM).  ws: device workspace of ws_bytes >=
+ * band_workspace_size(desc, BAND_OP_SOLVE, method, 0). */
+band_status band_solve(const band_desc* desc, int32_t method, const void* factors,
+                       const void* const diag[5], const void* f, void* x,
+                       int32_t* sys_status, void* ws, size_t ws_bytes, void* stream);
+
+/* LU factors of NTDM/NPDM (gamma, 1/mu, alpha, beta per row; opaque layout) into
+ * `factors`, a device buffer of band_workspace_size(desc, BAND_OP_FACTOR, method, 0)
+ * bytes, for repeated band_solve() calls and for band_adjoint(). */
+band_status band_factor(const band_desc* desc, int32_t method, const void* const diag[5],
+                        void* factors, size_t factors_bytes, int32_t* sys_status, void* stream);
+
+/* SIP / Stone method (Algorithm 1) on PD systems (TD: a = e = 0 is used), FP64 only.
+ * width == 0: Algorithm 1 as printed, with the exact substitutions of the ILU(0)
+ * factors; width > 0: Hotelling-Bodewig inverses of L and U kept to `width`
+ * diagonals (at most 8), iterated from X_0 = diag^{-1} until
+ * max|X_{k+1}-X_k| <= hb_tol max|X_k| or hb_max_it, and the update
+ * x += U~^{-1} L~^{-1} (f - A x).  Stops per system when max|f - A x| < tol or after
+ * max_it updates.  iters (int32[nsys]) and resid (double[nsys], max |f - A x|) may be
+ * NULL. */
+band_status band_sip(const band_desc* desc, const void* const diag[5], const void* f, void* x,
+                     double tol, int32_t max_it, int32_t width, int32_t hb_max_it, double hb_tol,
+                     int32_t* iters, double* resid, int32_t* sys_status, void* ws, size_t ws_bytes,
+                     void* stream);
+
+/* Mixed precision: PD/TD systems stored in FP32 (desc->dtype = BAND_F32 describes
+ * diag32), right-hand side and solution in FP64 with the same strides.  FP32 NPDM/NTDM
+ * solve, then refinement steps r = f - A x (FP64, A = the FP64 values of the FP32
+ * diagonals), delta = s * solve32(r / s) with s = max|r|, x += delta (FP64), until
+ * max|delta| <= rel_stop * max|x| or max_steps steps.  steps (int32[nsys]) may be NULL. */
+band_status band_refine_solve(const band_desc* desc32, const void* const diag32[5],
+                              const double* f, double* x, double rel_stop, int32_t max_steps,
+                              int32_t* steps, int32_t* sys_status, void* ws, size_t ws_bytes,
+                              void* stream);
+
+/* Adjoint of x = A^{-1} f for a loss L with dL/dx = w (FP64, NTDM/NPDM factorisation):
+ * lambda = A^{-T} w by the transposed sweeps of the LU factors, then
+ * grad_f = lambda, grad_a[i] = -lambda_i x_{i-2}, grad_b[i] = -lambda_i x_{i-1},
+ * grad_c[i] = -lambda_i x_i, grad_d[i] = -lambda_i x_{i+1}, grad_e[i] = -lambda_i x_{i+2}
+ * (out-of-matrix slots receive 0; TD: grad_a, grad_e may be NULL).  factors: NULL to
+ * refactor from diag, or band_factor()'s buffer. */
+band_status band_adjoint(const band_desc* desc, int32_t method, const void* factors,
+                         const void* const diag[5], const void* x, const void* w,
+                         void* const grad_diag[5], void* grad_f, int32_t* sys_status,
+                         void* ws, size_t ws_bytes, void* stream);
+
+/* Diagnostic (the paper has no counterpart): measures this GPU's FP64 fused
+ * multiply-add rate in FMA/s with a short register-only kernel on `stream` and waits
+ * for it.  scratch: device buffer of at least 8 * 256 * 8 * (SM count) bytes.
+ * Returns a negative value on error.  The FP64 recurrences are bounded by this rate. */
+double band_fp64_fma_rate(void* scratch, size_t scratch_bytes, void* stream);
+
+/* Human-readable name of a status code (static string). */
+const char* band_status_str(int32_t status);
+
+/* Library version string (static). */
+const char* band_version(void);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* BAND_H */

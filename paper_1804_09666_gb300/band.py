@@ -1,0 +1,221 @@
+"""Python API over torch CUDA tensors; marshals arguments to libband's C ABI.
+
+Uniform batches: every per-row array is a tensor of shape (n, nsys) whose element
+[i, s] is row i of system s; all arrays of one call share the same strides, so a
+contiguous (n, nsys) tensor is the interleaved layout and ``t.T`` of a contiguous
+(nsys, n) tensor is the contiguous-systems layout.  Ragged batches use 1-D packed
+tensors plus device offsets (see ``solve_ragged``).
+
+The workspaces are torch tensors allocated here; the C library allocates nothing.
+Calls run on torch's current CUDA stream and return without synchronising.
+"""
+import ctypes as ct
+
+import torch
+
+from . import _lib as L
+
+_METHODS = {"ntdm": L.NTDM, "npdm": L.NPDM, "stdm": L.STDM, "spdm": L.SPDM,
+            "auto": L.AUTO_NUMERIC, "auto_symbolic": L.AUTO_SYMBOLIC}
+
+
+def status_names(status):
+    """Map a status tensor / list of codes to names."""
+    vals = status.tolist() if hasattr(status, "tolist") else list(status)
+    return [L.STATUS_NAMES.get(int(v), str(v)) for v in vals]
+
+
+def _stream():
+    return ct.c_void_p(torch.cuda.current_stream().cuda_stream)
+
+
+def _ptr(t):
+    return ct.c_void_p(t.data_ptr()) if t is not None else ct.c_void_p(0)
+
+
+def _dtype_code(t):
+    if t.dtype == torch.float64:
+        return L.F64
+    if t.dtype == torch.float32:
+        return L.F32
+    raise TypeError("band arrays must be float64 or float32, got %s" % t.dtype)
+
+
+def desc_for(ref, half_bw):
+    """BandDesc for (n, nsys)-shaped tensors with ref's strides."""
+    if ref.dim() != 2:
+        raise ValueError("expected a (n, nsys) tensor")
+    n, nsys = ref.shape
+    return L.BandDesc(half_bw=half_bw, dtype=_dtype_code(ref), nsys=nsys, n=n,
+                      sys_stride=ref.stride(1) if nsys > 1 else max(n, 1),
+                      elem_stride=ref.stride(0) if n > 1 else max(nsys, 1),
+                      offsets=None, hbw=None, total_rows=0)
+
+
+def _check_same(ref, *ts):
+    for t in ts:
+        if t is None:
+            continue
+        if t.shape != ref.shape or t.stride() != ref.stride() or t.dtype != ref.dtype:
+            raise ValueError("all band arrays must share shape, strides and dtype")
+        if not t.is_cuda:
+            raise ValueError("band arrays must be CUDA tensors")
+
+
+def _diag5(a, b, c, d, e):
+    return L.DIAG5(*[(t.data_ptr() if t is not None else None) for t in (a, b, c, d, e)])
+
+
+def _workspace(nbytes, device):
+    return torch.empty(max(int(nbytes), 1), dtype=torch.uint8, device=device)
+
+
+def solve(a, b, c, d, e, f, method="npdm", x=None, status=None, factors=None, ws=None):
+    """Solve A x = f for a uniform batch.  Returns (x, status int32[nsys]).
+
+    method: "npdm", "ntdm", "spdm", "stdm".  a, e are ignored (may be None) for TD.
+    factors: a buffer from ``factor`` to reuse a factorisation (numeric methods).
+    """
+    lib = L.load()
+    m = _METHODS[method]
+    half_bw = 1 if method in ("ntdm", "stdm") else 2
+    _check_same(c, a if half_bw == 2 else None, b, d, e if half_bw == 2 else None, f)
+    desc = desc_for(c, half_bw)
+    if x is None:
+        x = torch.empty_strided(c.shape, c.stride(), dtype=c.dtype, device=c.device)
+    _check_same(c, x)
+    if status is None:
+        status = torch.empty(c.shape[1], dtype=torch.int32, device=c.device)
+    need = lib.band_workspace_size(ct.byref(desc), L.OP_SOLVE, m, 0)
+    if ws is None or ws.numel() < need:
+        ws = _workspace(need, c.device)
+    code = lib.band_solve(ct.byref(desc), m, _ptr(factors), _diag5(a, b, c, d, e), _ptr(f), _ptr(x),
+                          _ptr(status), _ptr(ws), ws.numel(), _stream())
+    L.check(code, "band_solve")
+    return x, status
+
+
+def factor(a, b, c, d, e, method="npdm", status=None):
+    """LU factors (opaque uint8 buffer) for repeated solves and the adjoint."""
+    lib = L.load()
+    m = _METHODS[method]
+    half_bw = 1 if method == "ntdm" else 2
+    desc = desc_for(c, half_bw)
+    need = lib.band_workspace_size(ct.byref(desc), L.OP_FACTOR, m, 0)
+    buf = _workspace(need, c.device)
+    if status is None:
+        status = torch.empty(c.shape[1], dtype=torch.int32, device=c.device)
+    code = lib.band_factor(ct.byref(desc), m, _diag5(a, b, c, d, e), _ptr(buf), buf.numel(),
+                           _ptr(status), _stream())
+    L.check(code, "band_factor")
+    return buf, status
+
+
+def solve_ragged(a, b, c, d, e, f, offsets, hbw, n_max, total_rows, method="auto", x=None,
+                 status=None, ws=None):
+    """Ragged batch: 1-D packed arrays, system s in rows offsets[s]..offsets[s+1]-1.
+
+    offsets: int64 CUDA tensor (nsys+1); hbw: int8 CUDA tensor of 1/2 per system (or None
+    with method "npdm"/"ntdm"); n_max: an upper bound on the system sizes; total_rows:
+    offsets[-1] as a Python int.
+    """
+    lib = L.load()
+    m = _METHODS[method]
+    nsys = offsets.numel() - 1
+    desc = L.BandDesc(half_bw=1 if method in ("ntdm", "stdm") else 2, dtype=_dtype_code(c),
+                      nsys=nsys, n=int(n_max), sys_stride=0, elem_stride=1,
+                      offsets=offsets.data_ptr(), hbw=hbw.data_ptr() if hbw is not None else None,
+                      total_rows=int(total_rows))
+    if x is None:
+        x = torch.empty_like(f)
+    if status is None:
+        status = torch.empty(nsys, dtype=torch.int32, device=c.device)
+    need = lib.band_workspace_size(ct.byref(desc), L.OP_SOLVE, m, 0)
+    if ws is None or ws.numel() < need:
+        ws = _workspace(need, c.device)
+    code = lib.band_solve(ct.byref(desc), m, None, _diag5(a, b, c, d, e), _ptr(f), _ptr(x),
+                          _ptr(status), _ptr(ws), ws.numel(), _stream())
+    L.check(code, "band_solve")
+    return x, status
+
+
+def sip(a, b, c, d, e, f, tol=1e-10, max_it=200, width=5, hb_max_it=30, hb_tol=1e-12, x=None):
+    """SIP / Stone method (FP64).  Returns (x, iters, resid, status)."""
+    lib = L.load()
+    _check_same(c, a, b, d, e, f)
+    desc = desc_for(c, 2)
+    if x is None:
+        x = torch.empty_strided(c.shape, c.stride(), dtype=c.dtype, device=c.device)
+    nsys = c.shape[1]
+    iters = torch.empty(nsys, dtype=torch.int32, device=c.device)
+    resid = torch.empty(nsys, dtype=torch.float64, device=c.device)
+    status = torch.empty(nsys, dtype=torch.int32, device=c.device)
+    need = lib.band_workspace_size(ct.byref(desc), L.OP_SIP, 0, width)
+    ws = _workspace(need, c.device)
+    code = lib.band_sip(ct.byref(desc), _diag5(a, b, c, d, e), _ptr(f), _ptr(x), tol, max_it,
+                        width, hb_max_it, hb_tol, _ptr(iters), _ptr(resid), _ptr(status), _ptr(ws),
+                        ws.numel(), _stream())
+    L.check(code, "band_sip")
+    return x, iters, resid, status
+
+
+def refine_solve(a32, b32, c32, d32, e32, f, rel_stop=1e-11, max_steps=10, x=None):
+    """FP32 solve + FP64 refinement; f, x float64 with the diagonals' strides."""
+    lib = L.load()
+    desc = desc_for(c32, 2 if a32 is not None else 1)
+    if f.shape != c32.shape or f.stride() != c32.stride() or f.dtype != torch.float64:
+        raise ValueError("f must be float64 with the diagonals' shape and strides")
+    if x is None:
+        x = torch.empty_strided(c32.shape, c32.stride(), dtype=torch.float64, device=c32.device)
+    nsys = c32.shape[1]
+    steps = torch.empty(nsys, dtype=torch.int32, device=c32.device)
+    status = torch.empty(nsys, dtype=torch.int32, device=c32.device)
+    need = lib.band_workspace_size(ct.byref(desc), L.OP_REFINE, 0, 0)
+    ws = _workspace(need, c32.device)
+    code = lib.band_refine_solve(ct.byref(desc), _diag5(a32, b32, c32, d32, e32), _ptr(f), _ptr(x),
+                                 rel_stop, max_steps, _ptr(steps), _ptr(status), _ptr(ws),
+                                 ws.numel(), _stream())
+    L.check(code, "band_refine_solve")
+    return x, steps, status
+
+
+def adjoint(a, b, c, d, e, x, w, factors=None, method="npdm"):
+    """Gradients (ga, gb, gc, gd, ge), gf of sum(w * x) with x = A^{-1} f."""
+    lib = L.load()
+    m = _METHODS[method]
+    half_bw = 1 if method == "ntdm" else 2
+    desc = desc_for(c, half_bw)
+    mk = lambda: torch.empty_strided(c.shape, c.stride(), dtype=c.dtype, device=c.device)
+    grads = [mk() if (half_bw == 2 or k in (1, 2, 3)) else None for k in range(5)]
+    gf = mk()
+    status = torch.empty(c.shape[1], dtype=torch.int32, device=c.device)
+    need = lib.band_workspace_size(ct.byref(desc), L.OP_ADJOINT, m, 0)
+    ws = _workspace(need, c.device)
+    code = lib.band_adjoint(ct.byref(desc), m, _ptr(factors), _diag5(a, b, c, d, e), _ptr(x), _ptr(w),
+                            L.DIAG5(*[(g.data_ptr() if g is not None else None) for g in grads]),
+                            _ptr(gf), _ptr(status), _ptr(ws), ws.numel(), _stream())
+    L.check(code, "band_adjoint")
+    return tuple(grads), gf, status
+
+
+class BandSolve(torch.autograd.Function):
+    """x = A^{-1} f for a batch of PD systems (NPDM forward, hand-written adjoint backward).
+
+    Inputs: a, b, c, d, e, f of shape (n, nsys), float64 CUDA, equal strides.
+    """
+
+    @staticmethod
+    def forward(ctx, a, b, c, d, e, f):
+        x, status = solve(a, b, c, d, e, f, method="npdm")
+        ctx.save_for_backward(a, b, c, d, e, x)
+        ctx.mark_non_differentiable(status)
+        return x, status
+
+    @staticmethod
+    def backward(ctx, gx, gstatus=None):
+        a, b, c, d, e, x = ctx.saved_tensors
+        w = gx
+        if w.stride() != c.stride():
+            w = torch.empty_strided(c.shape, c.stride(), dtype=c.dtype, device=c.device).copy_(gx)
+        (ga, gb, gc, gd, ge), gf, _ = adjoint(a, b, c, d, e, x, w)
+        return ga, gb, gc, gd, ge, gf

@@ -1,0 +1,186 @@
+// api.cu -- C entry points for the direct solvers (band_solve, band_factor) and the
+// shared utilities of libband.  See include/band.h for the contract of each call.
+#include <cstring>
+
+#include "api_util.h"
+#include "kernels.h"
+
+using namespace band;
+
+namespace band {
+
+// Workspace of band_solve.  Numeric methods: alpha and beta rows.  Symbolic methods:
+// alpha, beta and z rows, the flagged-system counter and list, and the Laurent-series
+// rows of up to kMaxFixSlots flagged systems redone at a time.
+struct SolveWs {
+  void *al, *be, *zs, *count, *list, *slots;
+  int64_t nslots;
+};
+static SolveWs carve_solve(const band_desc* d, int32_t method, void* base, size_t* bytes) {
+  Carve c(base);
+  SolveWs w{};
+  const size_t rows = (size_t)spill_rows(d) * dtype_size(d->dtype);
+  w.al = c.take(rows);
+  w.be = c.take(rows);
+  if (is_symbolic(method)) {
+    w.zs = c.take(rows);
+    w.count = c.take(sizeof(unsigned long long));
+    w.list = c.take(sizeof(int64_t) * (size_t)(d->nsys > 0 ? d->nsys : 1));
+    w.nslots = d->nsys < kMaxFixSlots ? d->nsys : kMaxFixSlots;
+    w.slots = c.take((size_t)w.nslots * symbolic_slot_bytes(d->n));
+  }
+  *bytes = c.size();
+  return w;
+}
+
+struct FactorBuf {
+  void *gam, *rmu, *al, *be;
+};
+static FactorBuf carve_factors(const band_desc* d, const void* base, size_t* bytes) {
+  Carve c(const_cast<void*>(base));
+  const size_t rows = (size_t)spill_rows(d) * dtype_size(d->dtype);
+  FactorBuf fb;
+  fb.gam = c.take(rows);
+  fb.rmu = c.take(rows);
+  fb.al = c.take(rows);
+  fb.be = c.take(rows);
+  *bytes = c.size();
+  return fb;
+}
+
+size_t factor_bytes(const band_desc* d) {
+  size_t b = 0;
+  carve_factors(d, nullptr, &b);
+  return b;
+}
+FactorPtrs factor_ptrs(const band_desc* d, const void* factors) {
+  size_t b = 0;
+  FactorBuf fb = carve_factors(d, factors, &b);
+  return FactorPtrs{fb.gam, fb.rmu, fb.al, fb.be};
+}
+
+}  // namespace band
+
+extern "C" {
+
+size_t band_workspace_size(const band_desc* desc, int32_t op, int32_t method, int32_t sip_width) {
+  if (!desc_ok(desc)) return 0;
+  size_t bytes = 0;
+  switch (op) {
+    case BAND_OP_SOLVE: carve_solve(desc, method, nullptr, &bytes); return bytes;
+    case BAND_OP_FACTOR: return factor_bytes(desc);
+    case BAND_OP_SIP: return sip_workspace_bytes(desc, sip_width);
+    case BAND_OP_REFINE: return refine_workspace_bytes(desc);
+    case BAND_OP_ADJOINT: return adjoint_workspace_bytes(desc);
+    default: return 0;
+  }
+}
+
+band_status band_solve(const band_desc* desc, int32_t method, const void* factors,
+                       const void* const diag[5], const void* f, void* x, int32_t* sys_status,
+                       void* ws, size_t ws_bytes, void* stream) {
+  if (!desc_ok(desc)) return BAND_ERR_ARG;
+  const int kmode = kmode_for(desc, method);
+  if (kmode < 0) return BAND_ERR_ARG;
+  if (is_symbolic(method) && (desc->dtype != BAND_F64 || factors)) return BAND_ERR_ARG;
+  if (desc->nsys == 0) return BAND_OK;   // nothing to do (empty arrays may be NULL)
+  if (!diag || !f || !x) return BAND_ERR_ARG;
+  if (!diag[1] || !diag[2] || !diag[3]) return BAND_ERR_ARG;
+  if (may_be_pd(desc) && kmode != 1 && (!diag[0] || !diag[4])) return BAND_ERR_ARG;
+  cudaStream_t st = static_cast<cudaStream_t>(stream);
+  const Layout L = layout_of(desc);
+  const Spill W = spill_of(desc);
+  if (factors) {
+    const FactorPtrs fp = factor_ptrs(desc, factors);
+    if (desc->dtype == BAND_F64) {
+      FactoredArgs<double> p{L, W, (const double*)diag[0], (const double*)fp.gam,
+                             (const double*)fp.rmu, (const double*)fp.al, (const double*)fp.be,
+                             (const double*)f, (double*)x, sys_status};
+      return cuda_status(launch_fsolve<double>(p, kmode, st));
+    }
+    FactoredArgs<float> p{L, W, (const float*)diag[0], (const float*)fp.gam,
+                          (const float*)fp.rmu, (const float*)fp.al, (const float*)fp.be,
+                          (const float*)f, (float*)x, sys_status};
+    return cuda_status(launch_fsolve<float>(p, kmode, st));
+  }
+  size_t need = 0;
+  carve_solve(desc, method, nullptr, &need);
+  if (!ws || ws_bytes < need) return BAND_ERR_WORKSPACE;
+  const SolveWs w = carve_solve(desc, method, ws, &need);
+  if (desc->dtype == BAND_F64) {
+    DirectArgs<double> p{L, W,
+                         (const double*)diag[0], (const double*)diag[1], (const double*)diag[2],
+                         (const double*)diag[3], (const double*)diag[4], (const double*)f,
+                         (double*)x, (double*)w.al, (double*)w.be, (double*)w.zs, sys_status,
+                         (unsigned long long*)w.count, (int64_t*)w.list};
+    if (is_symbolic(method)) {
+      cudaError_t e = cudaMemsetAsync(w.count, 0, sizeof(unsigned long long), st);
+      if (e != cudaSuccess) return BAND_ERR_CUDA;
+    } else {
+      p.fix_count = nullptr;
+      p.fix_list = nullptr;
+    }
+    cudaError_t e = launch_direct<double>(p, kmode, st);
+    if (e != cudaSuccess) return BAND_ERR_CUDA;
+    if (is_symbolic(method)) {
+      SymArgs q{L, (const double*)diag[0], (const double*)diag[1], (const double*)diag[2],
+                (const double*)diag[3], (const double*)diag[4], (const double*)f, (double*)x,
+                sys_status, (const unsigned long long*)w.count, (const int64_t*)w.list,
+                w.slots, w.nslots, desc->n, nullptr, nullptr};
+      e = launch_symbolic_fixup(q, st);
+    }
+    return cuda_status(e);
+  }
+  DirectArgs<float> p{L, W,
+                      (const float*)diag[0], (const float*)diag[1], (const float*)diag[2],
+                      (const float*)diag[3], (const float*)diag[4], (const float*)f, (float*)x,
+                      (float*)w.al, (float*)w.be, nullptr, sys_status, nullptr, nullptr};
+  return cuda_status(launch_direct<float>(p, kmode, st));
+}
+
+band_status band_factor(const band_desc* desc, int32_t method, const void* const diag[5],
+                        void* factors, size_t factors_bytes, int32_t* sys_status, void* stream) {
+  if (!desc_ok(desc)) return BAND_ERR_ARG;
+  const int kmode = kmode_for(desc, method);
+  if (kmode < 0 || is_symbolic(method)) return BAND_ERR_ARG;
+  if (desc->nsys == 0) return BAND_OK;
+  if (!diag || !factors) return BAND_ERR_ARG;
+  if (!diag[1] || !diag[2] || !diag[3]) return BAND_ERR_ARG;
+  if (may_be_pd(desc) && kmode != 1 && (!diag[0] || !diag[4])) return BAND_ERR_ARG;
+  if (factors_bytes < factor_bytes(desc)) return BAND_ERR_WORKSPACE;
+  cudaStream_t st = static_cast<cudaStream_t>(stream);
+  const FactorPtrs fp = factor_ptrs(desc, factors);
+  const Layout L = layout_of(desc);
+  const Spill W = spill_of(desc);
+  if (desc->dtype == BAND_F64) {
+    FactorArgs<double> p{L, W, (const double*)diag[0], (const double*)diag[1],
+                         (const double*)diag[2], (const double*)diag[3], (const double*)diag[4],
+                         (double*)fp.gam, (double*)fp.rmu, (double*)fp.al, (double*)fp.be,
+                         sys_status};
+    return cuda_status(launch_factor<double>(p, kmode, st));
+  }
+  FactorArgs<float> p{L, W, (const float*)diag[0], (const float*)diag[1], (const float*)diag[2],
+                      (const float*)diag[3], (const float*)diag[4], (float*)fp.gam,
+                      (float*)fp.rmu, (float*)fp.al, (float*)fp.be, sys_status};
+  return cuda_status(launch_factor<float>(p, kmode, st));
+}
+
+const char* band_status_str(int32_t s) {
+  switch (s) {
+    case BAND_OK: return "BAND_OK";
+    case BAND_ERR_ARG: return "BAND_ERR_ARG";
+    case BAND_ERR_CUDA: return "BAND_ERR_CUDA";
+    case BAND_ERR_ZERO_PIVOT: return "BAND_ERR_ZERO_PIVOT";
+    case BAND_ERR_SINGULAR: return "BAND_ERR_SINGULAR";
+    case BAND_ERR_NONFINITE: return "BAND_ERR_NONFINITE";
+    case BAND_ERR_NOT_CONVERGED: return "BAND_ERR_NOT_CONVERGED";
+    case BAND_ERR_SYMBOLIC_RANGE: return "BAND_ERR_SYMBOLIC_RANGE";
+    case BAND_ERR_INTERNAL: return "BAND_ERR_INTERNAL";
+    case BAND_ERR_WORKSPACE: return "BAND_ERR_WORKSPACE";
+    default: return "BAND_UNKNOWN_STATUS";
+  }
+}
+
+const char* band_version(void) { return "libband 0.1 (sm_103a)"; }
+
+}  // extern "C"

@@ -1,0 +1,82 @@
+// common.cuh -- device helpers shared by the libband kernels (sm_103a).
+#pragma once
+#include <cstdint>
+#include <cuda_runtime.h>
+
+#include "band.h"
+
+namespace band {
+
+constexpr int kWarp = 32;
+
+__host__ __device__ inline int64_t round_up(int64_t v, int64_t m) { return (v + m - 1) / m * m; }
+
+// Where the rows of one system live.  Uniform batches: element i of system s at
+// s*sys_stride + i*elem_stride.  Ragged batches (n == 0): offsets[s] + i.
+struct Layout {
+  int64_t nsys, n, ss, es;
+  const int64_t* offsets;
+  const int8_t* hbw;
+  int32_t half_bw;
+  __device__ __forceinline__ int64_t base(int64_t s) const { return offsets ? offsets[s] : s * ss; }
+  __device__ __forceinline__ int64_t rows(int64_t s) const {
+    return offsets ? offsets[s + 1] - offsets[s] : n;
+  }
+  __device__ __forceinline__ int64_t stride() const { return offsets ? 1 : es; }
+  __device__ __forceinline__ int kband(int64_t s) const { return hbw ? (int)hbw[s] : half_bw; }
+};
+
+// Scratch rows of one system: interleaved by system (row i of system s at
+// i*S + s, S = nsys rounded up to a warp) for uniform batches, packed like the data
+// for ragged ones.
+struct Spill {
+  int64_t S;
+  const int64_t* offsets;
+  __device__ __forceinline__ int64_t base(int64_t s) const { return offsets ? offsets[s] : s; }
+  __device__ __forceinline__ int64_t stride() const { return offsets ? 1 : S; }
+};
+
+// ---------------------------------------------------------------- reciprocals
+// 1/m in FP64 from an FP32 seed refined by Newton's method for the reciprocal.
+// The seed: the double's exponent is rebased into float range with integer ops (the
+// leading 20 mantissa bits are kept), rcp.approx.f32 gives ~22 correct bits, and the
+// result is rebased back.  With e = 1 - m r0 (|e| < 2^-19), one step of the cubic
+// form of the iteration, r = r0 + r0 (e + e^2), leaves a relative error of order
+// e^3 < 2^-57 before the final rounding.  Outside the exponent window where the
+// rebasing is valid (|m| roughly in [2^-120, 2^120]) and for 0, Inf and NaN the
+// division is used instead.
+__device__ __forceinline__ double rcp64(double m) {
+  const unsigned hi = (unsigned)__double2hiint(m);
+  const unsigned ex = (hi >> 20) & 0x7ffu;
+  if (ex - 903u > 240u) return 1.0 / m;
+  const unsigned fb = (hi & 0x80000000u) | (((hi & 0x7fffffffu) - (896u << 20)) << 3);
+  float r0f;
+  asm("rcp.approx.ftz.f32 %0, %1;" : "=f"(r0f) : "f"(__uint_as_float(fb)));
+  const unsigned rb = __float_as_uint(r0f);
+  const unsigned rh = (rb & 0x80000000u) | (((rb & 0x7fffffffu) >> 3) + (896u << 20));
+  const double r0 = __hiloint2double((int)rh, (int)(rb << 29));
+  const double e = fma(-m, r0, 1.0);
+  return fma(r0, fma(e, e, e), r0);
+}
+
+__device__ __forceinline__ float rcp32(float m) { return __frcp_rn(m); }
+
+template <typename T>
+__device__ __forceinline__ T rcp(T m);
+template <>
+__device__ __forceinline__ double rcp<double>(double m) { return rcp64(m); }
+template <>
+__device__ __forceinline__ float rcp<float>(float m) { return rcp32(m); }
+
+template <typename T>
+__device__ __forceinline__ bool finite(T v) { return isfinite(v); }
+
+// read-only global load (the diagonals are never written by any kernel)
+template <typename T>
+__device__ __forceinline__ T ldro(const T* p) { return __ldg(p); }
+
+__device__ __forceinline__ void set_status(int32_t* st, int64_t s, int32_t v) {
+  if (st) st[s] = v;
+}
+
+}  // namespace band

@@ -1,0 +1,75 @@
+// kernels.h -- argument blocks and launchers of the libband kernels (internal).
+#pragma once
+#include <cstddef>
+#include <cstdint>
+#include <cuda_runtime.h>
+
+#include "common.cuh"
+
+namespace band {
+
+constexpr int kSerPole = 4;                  // Laurent window t^-4 .. t^4 (symbolic fix-up)
+constexpr int kSerWidth = 2 * kSerPole + 1;
+constexpr int64_t kMaxFixSlots = 64;         // flagged systems redone concurrently
+
+template <typename T>
+struct DirectArgs {
+  Layout L;
+  Spill W;
+  const T *a, *b, *c, *d, *e, *f;
+  T* x;
+  T *al, *be, *zs;                 // workspace rows (zs: symbolic methods only)
+  int32_t* status;
+  unsigned long long* fix_count;   // symbolic methods: flagged-system counter and list
+  int64_t* fix_list;
+};
+
+template <typename T>
+struct FactorArgs {
+  Layout L;
+  Spill W;
+  const T *a, *b, *c, *d, *e;
+  T *gam, *rmu, *al, *be;
+  int32_t* status;
+};
+
+template <typename T>
+struct FactoredArgs {
+  Layout L;
+  Spill W;
+  const T* a;
+  const T *gam, *rmu, *al, *be;
+  const T* f;
+  T* x;
+  int32_t* status;
+};
+
+struct SymArgs {
+  Layout L;
+  const double *a, *b, *c, *d, *e, *f;
+  double* x;
+  int32_t* status;
+  const unsigned long long* fix_count;
+  const int64_t* fix_list;
+  void* slot_mem;
+  int64_t nslots, nmax;
+  double* det_mant;       // optional per-system determinant (mantissa, base-2 exponent)
+  long long* det_exp;
+};
+
+template <typename T> cudaError_t launch_direct(const DirectArgs<T>&, int kmode, cudaStream_t);
+template <typename T> cudaError_t launch_factor(const FactorArgs<T>&, int kmode, cudaStream_t);
+template <typename T> cudaError_t launch_fsolve(const FactoredArgs<T>&, int kmode, cudaStream_t);
+cudaError_t launch_symbolic_fixup(const SymArgs&, cudaStream_t);
+size_t symbolic_slot_bytes(int64_t nmax);
+
+// host-side helpers shared by the entry points (defined in api.cu and the feature files)
+struct FactorPtrs {
+  void *gam, *rmu, *al, *be;
+};
+size_t factor_bytes(const band_desc* d);
+FactorPtrs factor_ptrs(const band_desc* d, const void* factors);
+size_t sip_workspace_bytes(const band_desc* d, int32_t width);
+size_t refine_workspace_bytes(const band_desc* d);
+size_t adjoint_workspace_bytes(const band_desc* d);
+}  // namespace band

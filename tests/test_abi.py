@@ -1,0 +1,131 @@
+"""CPU checks of the C ABI: the library loads, exports what include/band.h declares,
+and rejects bad arguments before touching the GPU.  No compute calls."""
+import ctypes as ct
+import os
+import re
+
+import pytest
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+HEADER = os.path.join(ROOT, "include", "band.h")
+
+
+@pytest.fixture(scope="module")
+def lib():
+    from paper_1804_09666_gb300 import build
+    from paper_1804_09666_gb300 import _lib as L
+    build.build()
+    return L.load()
+
+
+def declared_functions():
+    src = open(HEADER).read()
+    src = re.sub(r"/\*.*?\*/", "", src, flags=re.S)
+    return sorted(set(re.findall(r"\b(band_[a-z0-9_]+)\s*\(", src)))
+
+
+def test_header_declares_the_boundary():
+    names = declared_functions()
+    for must in ("band_solve", "band_factor", "band_sip", "band_refine_solve", "band_adjoint",
+                 "band_workspace_size", "band_status_str"):
+        assert must in names
+
+
+def test_every_declared_symbol_is_exported(lib):
+    for name in declared_functions():
+        assert hasattr(lib, name), name
+
+
+def test_exports_match_binding_list(lib):
+    from paper_1804_09666_gb300 import _lib as L
+    assert sorted(L.EXPORTS) == sorted(n for n in declared_functions() if n in L.EXPORTS)
+    for name in L.EXPORTS:
+        assert hasattr(lib, name)
+
+
+def test_desc_layout():
+    from paper_1804_09666_gb300 import _lib as L
+    # int32, int32, 4 x int64, 2 pointers, int64
+    assert ct.sizeof(L.BandDesc) == 8 + 4 * 8 + 2 * 8 + 8
+
+
+def test_status_strings(lib):
+    from paper_1804_09666_gb300 import _lib as L
+    for code, name in L.STATUS_NAMES.items():
+        assert lib.band_status_str(code).decode() == "BAND_" + ("OK" if name == "OK" else "ERR_" + name)
+    assert b"sm_103a" in lib.band_version()
+
+
+def _desc(**kw):
+    from paper_1804_09666_gb300 import _lib as L
+    base = dict(half_bw=2, dtype=L.F64, nsys=64, n=128, sys_stride=1, elem_stride=64, offsets=None,
+                hbw=None, total_rows=0)
+    base.update(kw)
+    return L.BandDesc(**base)
+
+
+def test_workspace_sizes(lib):
+    from paper_1804_09666_gb300 import _lib as L
+    d = _desc()
+    rows = 64 * 128 * 8
+    assert lib.band_workspace_size(ct.byref(d), L.OP_SOLVE, L.NPDM, 0) >= 2 * rows
+    assert lib.band_workspace_size(ct.byref(d), L.OP_SOLVE, L.SPDM, 0) > \
+        lib.band_workspace_size(ct.byref(d), L.OP_SOLVE, L.NPDM, 0)
+    assert lib.band_workspace_size(ct.byref(d), L.OP_FACTOR, L.NPDM, 0) >= 4 * rows
+    assert lib.band_workspace_size(ct.byref(d), L.OP_SIP, 0, 5) > \
+        lib.band_workspace_size(ct.byref(d), L.OP_SIP, 0, 0)
+    assert lib.band_workspace_size(ct.byref(d), L.OP_SIP, 0, 9) == 0       # width > 8
+    assert lib.band_workspace_size(ct.byref(_desc(n=0)), L.OP_SOLVE, L.NPDM, 0) == 0
+    for v in (lib.band_workspace_size(ct.byref(d), op, L.NPDM, 5) for op in range(5)):
+        assert v % 256 == 0
+
+
+def test_bad_arguments_are_rejected_without_gpu(lib):
+    from paper_1804_09666_gb300 import _lib as L
+    nul = L.DIAG5(None, 1, 2, 3, None)
+    full = L.DIAG5(8, 16, 24, 32, 40)
+    cases = [
+        (_desc(n=0), L.NPDM, full),               # n < 1
+        (_desc(half_bw=3), L.NPDM, full),         # bad bandwidth
+        (_desc(dtype=7), L.NPDM, full),           # bad dtype
+        (_desc(nsys=-1), L.NPDM, full),
+        (_desc(elem_stride=0), L.NPDM, full),
+        (_desc(sys_stride=1, elem_stride=10), L.NPDM, full),   # overlapping systems
+        (_desc(half_bw=2), L.NTDM, full),         # method / bandwidth mismatch
+        (_desc(half_bw=1), L.NPDM, full),
+        (_desc(half_bw=2), L.NPDM, nul),          # PD without a, e
+        (_desc(), 17, full),                      # unknown method
+        (_desc(dtype=L.F32), L.SPDM, full),       # symbolic path is FP64 only
+    ]
+    for d, m, diag in cases:
+        code = lib.band_solve(ct.byref(d), m, None, diag, 8, 8, None, 8, 1 << 30, None)
+        assert code == L.ERR_ARG, (d.half_bw, d.dtype, d.nsys, d.n, m)
+    # workspace too small
+    d = _desc()
+    assert lib.band_solve(ct.byref(d), L.NPDM, None, full, 8, 8, None, 8, 16, None) == L.ERR_WORKSPACE
+    assert lib.band_solve(ct.byref(d), L.NPDM, None, full, 8, 8, None, None, 0, None) == L.ERR_WORKSPACE
+    # empty batch is a no-op that succeeds
+    d0 = _desc(nsys=0)
+    assert lib.band_solve(ct.byref(d0), L.NPDM, None, full, 8, 8, None, 8, 1 << 20, None) == L.OK
+    # SIP argument checks
+    assert lib.band_sip(ct.byref(d), full, 8, 8, 1e-10, 10, 9, 30, 1e-12, None, None, None, 8,
+                        1 << 30, None) == L.ERR_ARG
+    assert lib.band_sip(ct.byref(_desc(dtype=L.F32)), full, 8, 8, 1e-10, 10, 5, 30, 1e-12, None,
+                        None, None, 8, 1 << 30, None) == L.ERR_ARG
+    assert lib.band_sip(ct.byref(d), full, 8, 8, float("nan"), 10, 5, 30, 1e-12, None, None, None,
+                        8, 1 << 30, None) == L.ERR_ARG
+    # refinement wants an FP32 descriptor
+    assert lib.band_refine_solve(ct.byref(d), full, 8, 8, 1e-11, 10, None, None, 8, 1 << 30,
+                                 None) == L.ERR_ARG
+    # adjoint rejects symbolic methods and missing gradient buffers
+    g = L.DIAG5(8, 16, 24, 32, 40)
+    assert lib.band_adjoint(ct.byref(d), L.SPDM, None, full, 8, 8, g, 8, None, 8, 1 << 30,
+                            None) == L.ERR_ARG
+    assert lib.band_adjoint(ct.byref(d), L.NPDM, None, full, 8, 8, L.DIAG5(None, 1, 2, 3, None), 8,
+                            None, 8, 1 << 30, None) == L.ERR_ARG
+
+
+def test_package_refuses_to_run_without_library(tmp_path):
+    from paper_1804_09666_gb300 import _lib as L
+    with pytest.raises(RuntimeError):
+        L.load(str(tmp_path / "missing.so"))

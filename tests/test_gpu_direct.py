@@ -1,0 +1,215 @@
+"""GPU parity: NTDM / NPDM / STDM / SPDM through the C ABI against the CPU oracle.
+
+Tolerances (relative, per system, max-norm): 1e-12 on diagonally dominant systems,
+1e-10 on the non-dominant ADI systems; symbolic zero-pivot cases against exact
+rational solutions to 1e-12.
+"""
+import json
+import os
+from fractions import Fraction
+
+import numpy as np
+import pytest
+import torch
+
+import oracle
+import synth
+from gpu_helpers import DEV, flat_of, per_system_rel, strided_view, to_dev
+
+pytestmark = pytest.mark.gpu
+
+GOLD = os.path.join(os.path.dirname(__file__), "golden")
+
+
+@pytest.fixture(scope="module")
+def band():
+    import paper_1804_09666_gb300 as band
+    from paper_1804_09666_gb300 import build
+    build.build()
+    band.load()
+    return band
+
+
+def _solve(band, T, method, k):
+    a, e = (T["a"], T["e"]) if k == 2 else (None, None)
+    x, st = band.solve(a, T["b"], T["c"], T["d"], e, T["f"], method=method)
+    torch.cuda.synchronize()
+    return x, st.cpu().numpy()
+
+
+def _oracle(B, k, method="direct"):
+    return oracle.batch(method, k, [B[q] for q in "abcde"], B["f"], B["nsys"], B["n"],
+                        B["sys_stride"], B["elem_stride"])
+
+
+def test_npdm_cfg0_full_size(band):
+    """The small plain-NPDM workload: 1024 dominant PD systems of n = 128."""
+    B = synth.cfg0()
+    T = to_dev(B)
+    x, st = _solve(band, T, "npdm", 2)
+    assert (st == 0).all()
+    xo, so, _, _ = _oracle(B, 2)
+    xg = flat_of(x)
+    args = (B["n"], B["nsys"], B["sys_stride"], B["elem_stride"])
+    assert per_system_rel(xg, xo, *args).max() <= 1e-12
+    assert per_system_rel(xg, B["x_true"], *args).max() <= 1e-12
+
+
+@pytest.mark.parametrize("method,k", [("npdm", 2), ("ntdm", 1), ("spdm", 2), ("stdm", 1)])
+@pytest.mark.parametrize("layout", ["interleaved", "contiguous", "padded", "general"])
+def test_methods_and_layouts(band, method, k, layout):
+    """nsys = 100 (a warp tail) and n = 257 in every accepted stride pattern."""
+    n, nsys = 257, 100
+    base = synth.cfg0(nsys=nsys, n=n, k=k, layout="interleaved", seed_salt=3)
+    canon = {q: base[q].reshape(n, nsys) for q in "abcdef"}
+    if layout == "interleaved":
+        ss, es, size = 1, nsys, n * nsys
+    elif layout == "contiguous":
+        ss, es, size = n, 1, n * nsys
+    elif layout == "padded":
+        ss, es, size = 1, 128, n * 128
+    else:
+        ss, es, size = 3, 3 * nsys + 5, (n - 1) * (3 * nsys + 5) + 3 * (nsys - 1) + 1
+    idx = np.arange(nsys)[None, :] * ss + np.arange(n)[:, None] * es
+    B = dict(n=n, nsys=nsys, sys_stride=ss, elem_stride=es)
+    for q in "abcdef":
+        flat = np.full(size, np.nan)
+        flat[idx] = canon[q]
+        B[q] = flat
+    T = to_dev(B)
+    x, st = _solve(band, T, method, k)
+    assert (st == 0).all()
+    xo, so, _, _ = _oracle(B, k, "symbolic" if method in ("spdm", "stdm") else "direct")
+    assert (so == 0).all()
+    xg = flat_of(x)
+    assert per_system_rel(xg, xo, n, nsys, ss, es).max() <= 1e-12
+
+
+@pytest.mark.parametrize("n", [1, 2, 3, 4, 5])
+@pytest.mark.parametrize("method,k", [("npdm", 2), ("ntdm", 1), ("spdm", 2), ("stdm", 1)])
+def test_tiny_systems(band, n, method, k):
+    B = synth.cfg0(nsys=37, n=n, k=k)
+    T = to_dev(B)
+    x, st = _solve(band, T, method, k)
+    assert (st == 0).all()
+    xo, _, _, _ = _oracle(B, k)
+    assert per_system_rel(flat_of(x), xo, n, 37, 1, 37).max() <= 1e-13
+
+
+def test_empty_batch(band):
+    t = torch.empty((16, 0), dtype=torch.float64, device=DEV)
+    x, st = band.solve(t, t, t, t, t, t, method="npdm")
+    assert st.numel() == 0
+
+
+def test_out_of_matrix_slots_hold_nan(band):
+    B = synth.cfg0(nsys=64, n=40)
+    ref = _oracle(B, 2)[0]
+    C = dict(B)
+    for q, rows in (("a", [0, 1]), ("b", [0]), ("d", [39]), ("e", [38, 39])):
+        arr = B[q].copy().reshape(40, 64)
+        arr[rows, :] = np.nan
+        C[q] = arr.reshape(-1)
+    for method in ("npdm", "spdm"):
+        x, st = _solve(band, to_dev(C), method, 2)
+        assert (st == 0).all()
+        assert per_system_rel(flat_of(x), ref, 40, 64, 1, 64).max() <= 1e-13
+
+
+def _golden():
+    return json.load(open(os.path.join(GOLD, "zero_pivot_cases.json")))["cases"]
+
+
+@pytest.mark.parametrize("case", _golden(), ids=lambda c: c["name"])
+def test_symbolic_zero_pivots(band, case):
+    """Hand-made exact zero pivots: the numeric method reports ZERO_PIVOT, the
+    symbolic one returns the exact solution (or SINGULAR).  Each case is repeated
+    over 40 systems, mixed with ordinary systems that take the fast path."""
+    k, n = case["k"], case["n"]
+    fl = lambda key: np.array([float(Fraction(v)) for v in case[key]])
+    nsys = 40
+    rng = np.random.default_rng(1)
+    canon = {q: np.repeat(fl(q)[:, None], nsys, axis=1) for q in "abcdef"}
+    # every third system is an ordinary dominant one
+    D = synth.dominant(rng, nsys, n, k=k)
+    xt, fo = synth.manufactured(rng, k, D, nsys, n)
+    plain = np.arange(nsys) % 3 == 2
+    for q in "abcde":
+        canon[q][:, plain] = D[q][:, plain]
+    canon["f"][:, plain] = fo[:, plain]
+    B = dict(n=n, nsys=nsys, sys_stride=1, elem_stride=nsys)
+    for q in "abcdef":
+        B[q] = canon[q].reshape(-1)
+    T = to_dev(B)
+    sym, num = ("spdm", "npdm") if k == 2 else ("stdm", "ntdm")
+    x, st = _solve(band, T, sym, k)
+    want_status = 0 if case["status"] == "OK" else 4
+    assert (st[plain] == 0).all()
+    assert (st[~plain] == want_status).all(), st
+    xg = flat_of(x).reshape(n, nsys)
+    assert np.abs(xg[:, plain] - xt[:, plain]).max() <= 1e-12
+    if case["status"] == "OK":
+        want = fl("x")
+        err = np.abs(xg[:, ~plain] - want[:, None]).max() / max(1.0, np.abs(want).max())
+        assert err <= 1e-12
+    _, stn = _solve(band, T, num, k)
+    assert (stn[~plain] == 3).all() and (stn[plain] == 0).all()
+
+
+def test_factor_then_solve(band):
+    B = synth.cfg0(nsys=96, n=200, seed_salt=5)
+    T = to_dev(B)
+    fac, st = band.factor(T["a"], T["b"], T["c"], T["d"], T["e"])
+    x1, st1 = band.solve(T["a"], T["b"], T["c"], T["d"], T["e"], T["f"], method="npdm",
+                         factors=fac)
+    x2, st2 = band.solve(T["a"], T["b"], T["c"], T["d"], T["e"], T["f"], method="npdm")
+    torch.cuda.synchronize()
+    assert (st.cpu() == 0).all() and (st1.cpu() == 0).all()
+    assert torch.equal(x1, x2)                   # same operations in the same order
+    f2 = T["f"] * 2.0
+    x3, _ = band.solve(T["a"], T["b"], T["c"], T["d"], T["e"], f2, method="npdm", factors=fac)
+    torch.cuda.synchronize()
+    assert torch.allclose(x3, 2.0 * x2, rtol=1e-14, atol=0)
+
+
+def test_x_may_alias_f(band):
+    B = synth.cfg0(nsys=64, n=50)
+    ref = _oracle(B, 2)[0]
+    for method in ("npdm", "spdm"):
+        T = to_dev(B)
+        x, st = band.solve(T["a"], T["b"], T["c"], T["d"], T["e"], T["f"], method=method, x=T["f"])
+        torch.cuda.synchronize()
+        assert (st.cpu() == 0).all()
+        assert per_system_rel(flat_of(T["f"]), ref, 50, 64, 1, 64).max() <= 1e-13
+
+
+@pytest.mark.parametrize("r", synth.ADI_R)
+@pytest.mark.parametrize("sweep", ["x", "y"])
+def test_adi_sweeps_subset(band, r, sweep):
+    """The ADI workload on 64 lines of each sweep: PD non-dominant (1e-10), TD (1e-12)."""
+    for k, tol in ((2, 1e-10), (1, 1e-12)):
+        B = synth.cfg1(r=r, k=k, sweep=sweep, grid=2048, nsys=64)
+        T = to_dev(B)
+        args = (B["n"], B["nsys"], B["sys_stride"], B["elem_stride"])
+        xo, so, _, _ = _oracle(B, k)
+        assert (so == 0).all()
+        for method in (("npdm", "spdm") if k == 2 else ("ntdm", "stdm")):
+            x, st = _solve(band, T, method, k)
+            assert (st == 0).all()
+            assert per_system_rel(flat_of(x), xo, *args).max() <= tol, (method, k)
+
+
+@pytest.mark.parametrize("sweep", ["x", "y"])
+def test_adi_full_grid_sampled(band, sweep):
+    """Full 2048 x 2048 sweep (the benchmark's launch), 24 systems checked."""
+    B = synth.cfg1(r=2.0, k=2, sweep=sweep)
+    T = to_dev(B)
+    x, st = _solve(band, T, "npdm", 2)
+    assert (st == 0).all()
+    xg = flat_of(x)
+    rng = np.random.default_rng(0)
+    for s in rng.choice(B["nsys"], 24, replace=False):
+        S = synth.system(B, int(s))
+        xo, so = oracle.npdm(*(S[q] for q in "abcdef"))
+        idx = int(s) * B["sys_stride"] + np.arange(B["n"]) * B["elem_stride"]
+        assert np.abs(xg[idx] - xo).max() / np.abs(xo).max() <= 1e-10

@@ -1,0 +1,175 @@
+"""GPU parity: SIP (ILU(0), Hotelling-Bodewig), FP32 + refinement, the adjoint and
+ragged batches, through the C ABI against the CPU oracle."""
+import numpy as np
+import pytest
+import torch
+
+import oracle
+import synth
+from gpu_helpers import DEV, flat_of, per_system_rel, strided_view, to_dev
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def band():
+    import paper_1804_09666_gb300 as band
+    from paper_1804_09666_gb300 import build
+    build.build()
+    band.load()
+    return band
+
+
+# ------------------------------------------------------------------------ SIP
+@pytest.mark.parametrize("width", [0, 3, 5, 8])
+def test_sip_dominant(band, width):
+    """Dominant PD systems (n = 300, 70 systems): iteration counts within one of the
+    oracle's, residual below tol, solution next to the truth."""
+    B = synth.cfg0(nsys=70, n=300, seed_salt=11)
+    T = to_dev(B)
+    x, it, rs, st = band.sip(T["a"], T["b"], T["c"], T["d"], T["e"], T["f"], tol=1e-10,
+                             max_it=200, width=width)
+    torch.cuda.synchronize()
+    st, it, rs = st.cpu().numpy(), it.cpu().numpy(), rs.cpu().numpy()
+    assert (st == 0).all()
+    assert (rs < 1e-10).all()
+    xg = flat_of(x)
+    for s in range(70):
+        S = synth.system(B, s)
+        R = oracle.sip(*(S[q] for q in "abcdef"), tol=1e-10, max_it=200, hb_width=width)
+        assert R["status"] == "OK"
+        assert abs(int(it[s]) - R["iters"]) <= 1, (s, it[s], R["iters"])
+        idx = s + np.arange(300) * 70
+        assert np.abs(xg[idx] - R["x"]).max() <= 1e-9
+    xt = B["x_true"]
+    assert per_system_rel(xg, xt, 300, 70, 1, 70).max() <= 1e-9
+
+
+@pytest.mark.parametrize("r", synth.ADI_R)
+def test_sip_algorithm1_on_adi(band, r):
+    """Algorithm 1 as printed (exact substitutions) on the non-dominant ADI systems:
+    one iteration, like the oracle."""
+    B = synth.cfg1(r=r, k=2, sweep="y", nsys=48)
+    T = to_dev(B)
+    x, it, rs, st = band.sip(T["a"], T["b"], T["c"], T["d"], T["e"], T["f"], tol=1e-10,
+                             max_it=200, width=0)
+    torch.cuda.synchronize()
+    assert (st.cpu() == 0).all()
+    xo, so, ito, _ = oracle.batch("sip", 2, [B[q] for q in "abcde"], B["f"], 48, 2048, 1, 48,
+                                  hb_width=0, tol=1e-10)
+    assert (so == 0).all()
+    assert np.abs(it.cpu().numpy() - ito).max() <= 1
+    xg = flat_of(x)
+    xgepp, _, _, _ = oracle.batch("gepp", 2, [B[q] for q in "abcde"], B["f"], 48, 2048, 1, 48)
+    assert per_system_rel(xg, xgepp, 2048, 48, 1, 48).max() <= 1e-10
+
+
+def test_sip_hb_divergence_matches_oracle(band):
+    """Band-truncated inverses of the indefinite ADI factors do not decay, so SIP-HB
+    diverges there; the GPU reports the same outcome as the oracle."""
+    B = synth.cfg1(r=2.0, k=2, sweep="y", nsys=8)
+    T = to_dev(B)
+    x, it, rs, st = band.sip(T["a"], T["b"], T["c"], T["d"], T["e"], T["f"], tol=1e-10,
+                             max_it=200, width=5)
+    torch.cuda.synchronize()
+    st = st.cpu().numpy()
+    _, so, _, _ = oracle.batch("sip", 2, [B[q] for q in "abcde"], B["f"], 8, 2048, 1, 8,
+                               hb_width=5, tol=1e-10)
+    assert (st != 0).all() and (so != 0).all()
+
+
+# ----------------------------------------------------------------- refinement
+def test_refine_cfg3_subset(band):
+    """FP32 storage, FP64 refinement: forward error <= 1e-10 against the FP64 truth."""
+    nsys, n = 96, 512
+    B = synth.cfg3(nsys=nsys, n=n)
+    T = to_dev(B, keys="abcde", dtype=torch.float32)
+    f = strided_view(B["f"], n, nsys, 1, nsys)
+    x, steps, st = band.refine_solve(T["a"], T["b"], T["c"], T["d"], T["e"], f)
+    torch.cuda.synchronize()
+    assert (st.cpu() == 0).all()
+    steps = steps.cpu().numpy()
+    assert (steps >= 1).all() and (steps <= 10).all()
+    xg = flat_of(x)
+    A64 = [B[q].astype(np.float64) for q in "abcde"]
+    xt, so, _, _ = oracle.batch("gepp", 2, A64, B["f"], nsys, n, 1, nsys)
+    assert (so == 0).all()
+    err = per_system_rel(xg, xt, n, nsys, 1, nsys)
+    assert err.max() <= 1e-10
+    for s in range(0, nsys, 7):
+        S = {q: B[q].reshape(n, nsys)[:, s] for q in "abcde"}
+        xr, so_steps, sto = oracle.refine(*(S[q] for q in "abcde"), B["f"].reshape(n, nsys)[:, s])
+        assert sto == "OK"
+        assert abs(int(steps[s]) - so_steps) <= 1
+
+
+# -------------------------------------------------------------------- adjoint
+def test_adjoint_vs_oracle(band):
+    nsys, n = 64, 256
+    B = synth.cfg4(nsys=nsys, n=n)
+    T = to_dev(B, keys="abcdefw")
+    x, st = band.solve(T["a"], T["b"], T["c"], T["d"], T["e"], T["f"], method="npdm")
+    (ga, gb, gc, gd, ge), gf, sta = band.adjoint(T["a"], T["b"], T["c"], T["d"], T["e"], x, T["w"])
+    fac, _ = band.factor(T["a"], T["b"], T["c"], T["d"], T["e"])
+    (ga2, gb2, gc2, gd2, ge2), gf2, _ = band.adjoint(T["a"], T["b"], T["c"], T["d"], T["e"], x,
+                                                     T["w"], factors=fac)
+    torch.cuda.synchronize()
+    assert (sta.cpu() == 0).all()
+    assert torch.equal(gf, gf2) and torch.equal(gc, gc2) and torch.equal(ga, ga2)
+    xg = x.cpu().numpy()
+    G = [g.cpu().numpy() for g in (ga, gb, gc, gd, ge, gf)]
+    w = B["w"].reshape(n, nsys)
+    for s in range(nsys):
+        S = synth.system(B, s)
+        go, gfo, sto = oracle.adjoint(2, *(S[q] for q in "abcde"), xg[:, s], w[:, s])
+        assert sto == "OK"
+        for g_gpu, g_orc in zip(G, list(go) + [gfo]):
+            den = max(np.abs(g_orc).max(), 1e-300)
+            assert np.abs(g_gpu[:, s] - g_orc).max() / den <= 1e-11
+
+
+def test_autograd_finite_differences(band):
+    nsys, n = 32, 64
+    B = synth.cfg4(nsys=nsys, n=n, seed_salt=2)
+    T = to_dev(B, keys="abcdefw")
+    params = [T[q].clone().requires_grad_(True) for q in "abcdef"]
+    x, _ = band.BandSolve.apply(*params)
+    loss = (x * T["w"]).sum()
+    loss.backward()
+    grads = [p.grad.clone() for p in params]
+    rng = np.random.default_rng(3)
+    V = [torch.from_numpy(rng.uniform(-1, 1, (n, nsys))).to(DEV) for _ in range(6)]
+    h = 1e-6
+
+    def L(sign):
+        with torch.no_grad():
+            ps = [p.detach() + sign * h * v for p, v in zip(params, V)]
+            xx, _ = band.solve(*ps, method="npdm")
+            return float((xx * T["w"]).sum())
+
+    fd = (L(+1) - L(-1)) / (2 * h)
+    # out-of-matrix slots carry no gradient; the directional derivative ignores them
+    an = 0.0
+    for g, v in zip(grads, V):
+        an += float((g * v).sum())
+    assert abs(fd - an) <= 1e-6 * abs(an)
+
+
+# --------------------------------------------------------------------- ragged
+@pytest.mark.parametrize("method", ["auto", "auto_symbolic"])
+def test_ragged_mixed_bandwidth(band, method):
+    B = synth.cfg2(nsys=300, nmin=16, nmax=700)
+    dev = {q: torch.from_numpy(B[q]).to(DEV) for q in "abcdef"}
+    offs = torch.from_numpy(B["offsets"]).to(DEV)
+    hbw = torch.from_numpy(B["hbw"]).to(DEV)
+    x, st = band.solve_ragged(dev["a"], dev["b"], dev["c"], dev["d"], dev["e"], dev["f"], offs, hbw,
+                              n_max=int(B["sizes"].max()), total_rows=int(B["offsets"][-1]),
+                              method=method)
+    torch.cuda.synchronize()
+    assert (st.cpu() == 0).all()
+    xo, so, _, _ = oracle.batch("direct", 0, [B[q] for q in "abcde"], B["f"], 300, 0, 0, 1,
+                                offsets=B["offsets"], hbw=B["hbw"])
+    xg = x.cpu().numpy()
+    for s in range(300):
+        lo, hi = B["offsets"][s], B["offsets"][s + 1]
+        assert np.abs(xg[lo:hi] - xo[lo:hi]).max() / np.abs(xo[lo:hi]).max() <= 1e-12
