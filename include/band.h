@@ -122,7 +122,9 @@ band_status band_factor(const band_desc* desc, int32_t method, const void* const
  * diagonals (at most 8), iterated from X_0 = diag^{-1} until
  * max|X_{k+1}-X_k| <= hb_tol max|X_k| or hb_max_it, and the update
  * x += U~^{-1} L~^{-1} (f - A x).  Stops per system when max|f - A x| < tol or after
- * max_it updates.  iters (int32[nsys]) and resid (double[nsys], max |f - A x|) may be
+ * max_it updates; with width == 0 also when an update from the second on does not
+ * lower max|f - A x| (exact ILU(0) factors leave K = LU - A at the rounding level, so
+ * the residual has reached its floor; status NOT_CONVERGED).  iters (int32[nsys]) and resid (double[nsys], max |f - A x|) may be
  * NULL. */
 band_status band_sip(const band_desc* desc, const void* const diag[5], const void* f, void* x,
                      double tol, int32_t max_it, int32_t width, int32_t hb_max_it, double hb_tol,

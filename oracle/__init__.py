@@ -65,6 +65,8 @@ def _load():
                                    _ct.POINTER(c_int)]
         lib.orc_adjoint.argtypes = [i64, c_int, _D, _D, _D, _D, _D, _D, _D,
                                     _D, _D, _D, _D, _D, _D]
+        lib.orc_cond1.argtypes = [i64, c_int, _D, _D, _D, _D, _D]
+        lib.orc_cond1.restype = dbl
         lib.orc_batch.argtypes = [c_int, c_int, i64, i64, i64, i64, _I64, _I8,
                                   _D, _D, _D, _D, _D, _D, _D, _I32, dbl, c_int, c_int, c_int,
                                   dbl, _I32, _D, c_int]
@@ -231,6 +233,25 @@ def adjoint(k, a, b, c, d, e, x, w):
     g = [_zeros_like_n(n) for _ in range(6)]
     st = lib.orc_adjoint(n, k, *[p for _, p in A], px, pw, *[v.ctypes.data_as(_D) for v in g])
     return tuple(g[:5]), g[5], STATUS[st]
+
+
+def cond1(k, a, b, c, d, e):
+    """Hager/Higham estimate of kappa_1(A) (a lower bound, usually exact)."""
+    lib = _load()
+    n = len(c)
+    a, b, c, d, e = _diags(k, a, b, c, d, e, n)
+    A = [_d(v) for v in (a, b, c, d, e)]
+    return lib.orc_cond1(n, k, *[p for _, p in A])
+
+
+def cond1_batch(k, diags, nsys, n, sys_stride, elem_stride):
+    """cond1 of every system of a uniform strided batch (numpy array)."""
+    out = _np.empty(nsys)
+    idx = _np.arange(n) * elem_stride
+    for s in range(nsys):
+        sel = s * sys_stride + idx
+        out[s] = cond1(k, *[None if v is None else _np.asarray(v)[sel] for v in diags])
+    return out
 
 
 METHOD = {"direct": 0, "symbolic": 1, "gepp": 2, "sip": 3}

@@ -608,7 +608,11 @@ static double residual_pd(int64_t n, const double* a, const double* b, const dou
 /*   inverses the update is written in correction form                        */
 /*   x <- x + U~^{-1} L~^{-1} (f - A x), identical to Algorithm 1 when the    */
 /*   inverses are exact (reading).                                            */
-/* The loop also stops after max_it updates (NOT_CONVERGED).  *iters gets k,  */
+/* The loop also stops after max_it updates (NOT_CONVERGED), and, for          */
+/* hb_width == 0, once an update (from the second on) fails to lower max|r|:    */
+/* with exact ILU(0) factors K = LU - A holds only rounding errors, so the      */
+/* residual has reached its rounding floor (NOT_CONVERGED; reading).            */
+/* *iters gets k,                                                               */
 /* *resid the final max |r_i|.  hb_iters (may be NULL) gets the HB counts for */
 /* L and U.                                                                   */
 /* ------------------------------------------------------------------------- */
@@ -648,8 +652,13 @@ int orc_sip(int64_t n, const double* a, const double* b, const double* c, const 
   for (int64_t i = 0; i < n; ++i) x[i] = 0.0;
   int k = 0;
   double rn = residual_pd(n, a, b, c, d, e, f, x, r, ops);
+  double prev = INFINITY;
   while (!(rn < tol)) {
     if (k >= max_it || !isfinite(rn)) break;
+    /* Algorithm 1 with exact substitutions: K = LU - A is rounding-level, so an update
+       that does not lower the residual means the rounding floor is reached (reading) */
+    if (w == 0 && k >= 2 && !(rn < prev)) break;
+    prev = rn;
     if (w == 0) {
       /* rhs = K x + f, into y */
       const double *ka = K, *kb = K + N, *kc = K + 2 * N, *kd = K + 3 * N, *ke = K + 4 * N;
@@ -775,6 +784,58 @@ int orc_adjoint(int64_t n, int k, const double* a, const double* b, const double
   }
   free(T);
   return st;
+}
+
+/* ------------------------------------------------------------------------- */
+/* Condition estimate kappa_1(A) = ||A||_1 ||A^{-1}||_1 with Hager's method    */
+/* (as refined by Higham): x = (1/n, ..., 1/n); repeat y = A^{-1} x,           */
+/* xi = sign(y), z = A^{-T} xi; stop when max|z_j| <= z^T x, else x = e_j with */
+/* j = argmax |z_j|; ||A^{-1}||_1 >= ||y||_1 is the estimate.  Solves use R0.  */
+/* Used only to scale the parity tolerance of ill-conditioned systems.        */
+/* ------------------------------------------------------------------------- */
+double orc_cond1(int64_t n, int k, const double* a, const double* b, const double* c,
+                 const double* d, const double* e) {
+  size_t N = (size_t)n;
+  double* T = (double*)calloc(5 * N, sizeof(double));
+  double* x = (double*)malloc(N * sizeof(double));
+  double* y = (double*)malloc(N * sizeof(double));
+  double* z = (double*)malloc(N * sizeof(double));
+  if (!T || !x || !y || !z) { free(T); free(x); free(y); free(z); return -1.0; }
+  double *ta = T, *tb = T + N, *tc = T + 2 * N, *td = T + 3 * N, *te = T + 4 * N;
+  double anorm = 0.0;     /* ||A||_1 = max column sum */
+  for (int64_t j = 0; j < n; ++j) {
+    double s = fabs(c[j]);
+    if (j + 1 < n) s += fabs(b[j + 1]);
+    if (j >= 1) s += fabs(d[j - 1]);
+    if (k == 2 && j + 2 < n) s += fabs(a[j + 2]);
+    if (k == 2 && j >= 2) s += fabs(e[j - 2]);
+    if (s > anorm) anorm = s;
+    tc[j] = c[j];
+    if (j >= 1) tb[j] = d[j - 1];
+    if (j + 1 < n) td[j] = b[j + 1];
+    if (k == 2 && j >= 2) ta[j] = e[j - 2];
+    if (k == 2 && j + 2 < n) te[j] = a[j + 2];
+  }
+  for (int64_t i = 0; i < n; ++i) x[i] = 1.0 / (double)n;
+  double est = 0.0;
+  for (int it = 0; it < 5; ++it) {
+    if (orc_gepp_band(n, k, a, b, c, d, e, x, y, NULL) != ORC_OK) { est = INFINITY; break; }
+    double s1 = 0.0;
+    for (int64_t i = 0; i < n; ++i) { s1 += fabs(y[i]); y[i] = y[i] >= 0.0 ? 1.0 : -1.0; }
+    est = s1;
+    if (orc_gepp_band(n, k, ta, tb, tc, td, te, y, z, NULL) != ORC_OK) { est = INFINITY; break; }
+    int64_t jm = 0;
+    double zx = 0.0;
+    for (int64_t i = 0; i < n; ++i) {
+      zx += z[i] * x[i];
+      if (fabs(z[i]) > fabs(z[jm])) jm = i;
+    }
+    if (fabs(z[jm]) <= zx) break;
+    for (int64_t i = 0; i < n; ++i) x[i] = 0.0;
+    x[jm] = 1.0;
+  }
+  free(T); free(x); free(y); free(z);
+  return anorm * est;
 }
 
 /* ------------------------------------------------------------------------- */

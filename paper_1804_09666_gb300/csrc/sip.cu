@@ -195,7 +195,9 @@ __device__ __forceinline__ Row load_row(const SipArgs& p, int64_t q, int64_t i, 
   return r;
 }
 
-// Algorithm 1 as printed: rhs = K x + f, L y = rhs, U x = y, r = f - A x.
+// Algorithm 1 as printed: rhs = K x + f, L y = rhs, U x = y, r = f - A x, until
+// max|r| < tol or max_it updates, or until an update from the second on fails to
+// lower max|r| (the rounding floor of exact ILU(0) factors; NOT_CONVERGED).
 __device__ void sip_literal(const SipArgs& p, int64_t s) {
   const int64_t n = p.L.rows(s), q0 = p.L.base(s), es = p.L.stride();
   const int64_t w0 = p.W.base(s), ws = p.W.stride();
@@ -206,7 +208,13 @@ __device__ void sip_literal(const SipArgs& p, int64_t s) {
     p.x[q] = 0.0;
   }
   int k = 0;
-  while (!(rn < p.tol) && k < p.max_it && isfinite(rn)) {
+  double prev = INFINITY;
+  for (;;) {
+    if (rn < p.tol || k >= p.max_it || !isfinite(rn)) break;
+    // K = LU - A holds only rounding errors: an update (from the second on) that does
+    // not lower the residual means its rounding floor is reached
+    if (k >= 2 && !(rn < prev)) break;
+    prev = rn;
     // forward: rhs_i = sum_j K[i][j] x_j + f_i, y_i = rhs_i - l1_i y_{i-1} - l2_i y_{i-2}
     double y1 = 0, y2 = 0;
     double u0m1 = 0, u1m1 = 0, u0m2 = 0, u1m2 = 0, em1 = 0, em2 = 0;

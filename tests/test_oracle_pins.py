@@ -509,3 +509,31 @@ def test_batch_driver_ragged():
                                    offsets=B["offsets"], hbw=B["hbw"], nthreads=2)
         assert (st == 0).all()
         assert np.abs(x - B["x_true"]).max() <= 1e-13
+
+
+def test_sip_algorithm1_stops_at_the_rounding_floor():
+    """An unreachable tolerance: Algorithm 1 stops once an update no longer lowers the
+    residual, well before the cap, with the residual at the rounding level."""
+    rng = np.random.default_rng(15)
+    n = 300
+    a, b, c, d, e = _rand_pd(rng, n)
+    f = rng.uniform(-1, 1, n)
+    R = oracle.sip(a, b, c, d, e, f, tol=1e-300, max_it=200, hb_width=0)
+    assert R["status"] == "NOT_CONVERGED"
+    assert 2 <= R["iters"] <= 20
+    An = _dense(2, a, b, c, d, e)
+    assert R["resid"] <= 50 * U * np.abs(An).sum(1).max() * np.abs(R["x"]).max()
+
+
+@pytest.mark.parametrize("dominant", [True, False])
+def test_condition_estimate_vs_dense(dominant):
+    """Hager's estimate is a lower bound of kappa_1 and, on these sizes, within 3x."""
+    rng = np.random.default_rng(31 + dominant)
+    for n in (5, 20, 60):
+        for k in (1, 2):
+            a, b, c, d, e = _rand_pd(rng, n, dominant=dominant, k=k)
+            An = _dense(k, a, b, c, d, e)
+            true = np.linalg.cond(An, 1)
+            est = oracle.cond1(k, a, b, c, d, e)
+            assert est <= true * (1 + 1e-8)
+            assert est >= true / 3
