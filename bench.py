@@ -36,7 +36,9 @@ SIP_TOL = 1e-10
 SIP_MAX_IT = 200
 # Algorithmic bytes and flops per unknown (inputs read once, output written once).
 ALG_BYTES = {"npdm": 56, "spdm": 56, "ntdm": 40, "stdm": 40, "sip": 56}
-ALG_FLOPS = {"npdm": 19, "spdm": 19, "ntdm": 9, "stdm": 9, "sip": 19 + 31}
+# flops per Table 7: NPDM 19N-29, NTDM 9N+2, SIP 31N-36 per iteration (one iteration on
+# this set) plus ILU(0)'s 10 per row; SPDM/STDM do NPDM/NTDM's work when no pivot is 0.
+ALG_FLOPS = {"npdm": 19, "spdm": 19, "ntdm": 9, "stdm": 9, "sip": 10 + 31}
 
 
 def parse():
@@ -47,6 +49,7 @@ def parse():
     ap.add_argument("--impl", default="gb300", choices=["gb300", "reference"])
     ap.add_argument("--grid", type=int, default=GRID)
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-graph", action="store_true")
     return ap.parse_args()
 
 
@@ -153,13 +156,14 @@ def units_per_step(W):
 
 
 class DeviceSet:
-    """Device tensors, outputs and workspaces of the whole step (allocated once)."""
+    """Device inputs, the batched plan of the 30 solves and its CUDA graph."""
 
-    def __init__(self, W, dev):
+    def __init__(self, W, dev, use_graph=True):
         import torch
         import paper_1804_09666_gb300 as band
-        self.band = band
+        self.torch = torch
         self.items = []
+        specs, self.spec_methods = [], []
         for w in W:
             B = w["B"]
             n, ns, ss, es = B["n"], B["nsys"], B["sys_stride"], B["elem_stride"]
@@ -169,33 +173,55 @@ class DeviceSet:
             for q in keys:
                 flat[q].copy_(host[q])
             view = {q: flat[q].as_strided((n, ns), (es, ss)) for q in keys}
-            outs = {}
-            for m in methods_for(w["k"]):
-                xf = torch.empty(B["f"].shape, dtype=torch.float64, device=dev)
-                outs[m] = dict(flat=xf, view=xf.as_strided((n, ns), (es, ss)),
-                               host=torch.empty(B["f"].shape, dtype=torch.float64).pin_memory())
-            self.items.append(dict(w=w, host=host, flat=flat, view=view, outs=outs, n=n, nsys=ns))
+            self.items.append(dict(w=w, host=host, flat=flat, view=view, n=n, nsys=ns))
+        # heaviest problems first: SIP, then the PD sweeps, then the TD sweeps
+        for kind in ("sip", "npdm", "spdm", "ntdm", "stdm"):
+            for it in self.items:
+                if kind not in methods_for(it["w"]["k"]):
+                    continue
+                v = it["view"]
+                if kind == "sip":
+                    sp = dict(op="sip", tol=SIP_TOL, max_it=SIP_MAX_IT, **v)
+                elif it["w"]["k"] == 2:
+                    sp = dict(method=kind, **v)
+                else:
+                    sp = dict(method=kind, a=None, e=None, **v)
+                specs.append(sp)
+                self.spec_methods.append((kind, it["n"] * it["nsys"]))
+        self.plan = band.BatchPlan(specs)
+        # outputs are compact strided views; copy their storage as flat buffers
+        self.out_flat = [r["x"].as_strided((r["x"].numel(),), (1,)) for r in self.plan.results]
+        self.out_host = [torch.empty(t.numel(), dtype=torch.float64).pin_memory()
+                         for t in self.out_flat]
         self.h2d_bytes = sum(t.numel() * 8 for it in self.items for t in it["host"].values())
-        self.d2h_bytes = sum(o["flat"].numel() * 8 for it in self.items for o in it["outs"].values())
+        self.d2h_bytes = sum(r["x"].numel() * 8 for r in self.plan.results)
+        self.graph = None
+        if use_graph:
+            self.plan.run()
+            torch.cuda.synchronize()
+            s = torch.cuda.Stream()
+            s.wait_stream(torch.cuda.current_stream())
+            g = torch.cuda.CUDAGraph()
+            with torch.cuda.stream(s):
+                with torch.cuda.graph(g, stream=s):
+                    self.plan.run()
+            torch.cuda.current_stream().wait_stream(s)
+            torch.cuda.synchronize()
+            self.graph = g
+
+    def alg(self, table):
+        return sum(table[m] * units for m, units in self.spec_methods)
 
     def step(self, events=None):
-        band = self.band
-        for it in self.items:
-            v = it["view"]
-            for m in methods_for(it["w"]["k"]):
-                x = it["outs"][m]["view"]
-                if events is not None:
-                    e0, e1 = events.new(m)
-                    e0.record()
-                if m == "sip":
-                    band.sip(v["a"], v["b"], v["c"], v["d"], v["e"], v["f"], tol=SIP_TOL,
-                             max_it=SIP_MAX_IT, width=0, x=x)
-                elif it["w"]["k"] == 2:
-                    band.solve(v["a"], v["b"], v["c"], v["d"], v["e"], v["f"], method=m, x=x)
-                else:
-                    band.solve(None, v["b"], v["c"], v["d"], None, v["f"], method=m, x=x)
-                if events is not None:
-                    e1.record()
+        if events is not None:
+            e0, e1 = events.new("batch")
+            e0.record()
+        if self.graph is not None:
+            self.graph.replay()
+        else:
+            self.plan.run()
+        if events is not None:
+            e1.record()
 
     def upload(self):
         for it in self.items:
@@ -203,28 +229,14 @@ class DeviceSet:
                 it["flat"][q].copy_(h, non_blocking=True)
 
     def download(self):
-        for it in self.items:
-            for o in it["outs"].values():
-                o["host"].copy_(o["flat"], non_blocking=True)
+        for t, h in zip(self.out_flat, self.out_host):
+            h.copy_(t, non_blocking=True)
 
     def statuses_ok(self):
-        """Re-run the step once with status outputs and check that every system is OK."""
-        import torch
-        band = self.band
-        bad = 0
-        for it in self.items:
-            v = it["view"]
-            for m in methods_for(it["w"]["k"]):
-                if m == "sip":
-                    _, _, _, st = band.sip(v["a"], v["b"], v["c"], v["d"], v["e"], v["f"],
-                                           tol=SIP_TOL, max_it=SIP_MAX_IT, width=0)
-                elif it["w"]["k"] == 2:
-                    _, st = band.solve(v["a"], v["b"], v["c"], v["d"], v["e"], v["f"], method=m)
-                else:
-                    _, st = band.solve(None, v["b"], v["c"], v["d"], None, v["f"], method=m)
-                bad += int((st != 0).sum())
-        torch.cuda.synchronize()
-        return bad
+        """Number of systems whose status is not OK after one step."""
+        self.step()
+        self.torch.cuda.synchronize()
+        return int(sum(int((r["status"] != 0).sum()) for r in self.plan.results))
 
 
 class EventLog:
@@ -336,7 +348,7 @@ def main():
     dev = torch.device("cuda", local)
     lib = band.load()
     W = host_workload(args.grid)
-    D = DeviceSet(W, dev)
+    D = DeviceSet(W, dev, use_graph=not args.no_graph)
     units = units_per_step(W)
 
     # FP64 FMA rate of this GPU (the ALU roofline of the FP64 recurrences)
@@ -344,10 +356,10 @@ def main():
     fma_rate = lib.band_fp64_fma_rate(ct.c_void_p(scratch.data_ptr()), scratch.numel(),
                                       ct.c_void_p(torch.cuda.current_stream().cuda_stream))
 
+    bad = D.statuses_ok()
     for _ in range(max(args.warmup, 3)):
         D.step()
     torch.cuda.synchronize()
-    bad = D.statuses_ok()
 
     # timed region: inputs resident in HBM
     clocks = ClockSampler(torch.cuda.current_device())
@@ -387,45 +399,38 @@ def main():
     e2e = {"value": units * args.steps * world / (ms_e2e * 1e-3), "unit": UNIT,
            "h2d_bytes_per_step": D.h2d_bytes, "d2h_bytes_per_step": D.d2h_bytes}
 
-    # per-method launch times (CUDA events on the launching stream, inside the timed region)
-    per = events.summary()
-    per_call_units = W[0]["B"]["n"] * W[0]["B"]["nsys"]
-    methods = {}
-    for m, times in per.items():
-        avg = float(np.mean(times))
-        methods[m] = {"ms_per_launch": avg, "launches": len(times),
-                      "share": float(np.sum(times)) / sum(float(np.sum(t)) for t in per.values()),
-                      "unknowns_per_s": per_call_units / (avg * 1e-3),
-                      "alg_GBps": ALG_BYTES[m] * per_call_units / (avg * 1e-3) / 1e9,
-                      "alg_TFLOPs": ALG_FLOPS[m] * per_call_units / (avg * 1e-3) / 1e12}
-    dom = max(methods, key=lambda m: methods[m]["share"])
+    # the batched launch's time per step (CUDA events on the launching stream inside the
+    # timed region) against the algorithmic bytes and flops of the 30 solves it does
+    per = events.summary()["batch"]
+    avg_ms = float(np.mean(per))
+    alg_bytes, alg_flops = D.alg(ALG_BYTES), D.alg(ALG_FLOPS)
     peaks = json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json"))) \
         if os.path.exists(os.path.join(ROOT, "MEASURED_PEAKS.json")) else {}
     hbm_peak = float(peaks.get("hbm_gbs", 6800.0))
     fp64_peak_tf = 2.0 * fma_rate / 1e12 if fma_rate > 0 else 1.25
-    mm = methods[dom]
-    frac_hbm = mm["alg_GBps"] / hbm_peak
-    frac_alu = mm["alg_TFLOPs"] / fp64_peak_tf
+    gbps = alg_bytes / (avg_ms * 1e-3) / 1e9
+    tflops = alg_flops / (avg_ms * 1e-3) / 1e12
+    frac_hbm, frac_alu = gbps / hbm_peak, tflops / fp64_peak_tf
+    common = {"kernel": "k_batch (one launch: the 30 solves of a step)",
+              "ms_per_launch": avg_ms, "launches": len(per),
+              "alg_bytes_per_launch": alg_bytes, "alg_flops_per_launch": alg_flops}
     if frac_alu >= frac_hbm:
-        roof = {"bound": "alu", "achieved": mm["alg_TFLOPs"], "peak": fp64_peak_tf,
-                "unit": "TFLOP/s", "frac": frac_alu, "traffic": None,
-                "kernel": dom, "peak_source": "measured FP64 FMA rate (band_fp64_fma_rate) x 2",
-                "hbm_frac_of_measured": frac_hbm}
+        roof = dict({"bound": "alu", "achieved": tflops, "peak": fp64_peak_tf, "unit": "TFLOP/s",
+                     "frac": frac_alu, "traffic": None,
+                     "peak_source": "measured FP64 FMA rate (band_fp64_fma_rate) x 2",
+                     "hbm_GBps": gbps, "hbm_frac_of_measured": frac_hbm}, **common)
     else:
-        roof = {"bound": "hbm", "achieved": mm["alg_GBps"], "peak": hbm_peak, "unit": "GB/s",
-                "frac": frac_hbm, "traffic": None, "kernel": dom,
-                "peak_source": "MEASURED_PEAKS.json hbm_gbs", "alu_frac": frac_alu}
-
-    launches_per_step = sum(
-        {"npdm": 1, "ntdm": 1, "spdm": 2, "stdm": 2, "sip": 2}[m]
-        for it in D.items for m in methods_for(it["w"]["k"]))
+        roof = dict({"bound": "hbm", "achieved": gbps, "peak": hbm_peak, "unit": "GB/s",
+                     "frac": frac_hbm, "traffic": None, "peak_source": "MEASURED_PEAKS.json hbm_gbs",
+                     "fp64_TFLOPs": tflops, "alu_frac_of_measured": frac_alu}, **common)
+    launches_per_step = 2         # k_batch and k_symbolic_batch (plus 12 counter memsets)
 
     line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
             "warmup": max(args.warmup, 3), "ms_per_step": ms / args.steps,
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
             "data": "synthetic", "config": workload_config(args.grid, world),
             "clocks": ck, "e2e": e2e, "gpu_launches": launches_per_step * args.steps,
-            "roofline": roof, "methods": methods, "bad_systems": bad,
+            "roofline": roof, "bad_systems": bad,
             "fp64_fma_per_s": fma_rate}
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         line["cpu_baseline"] = cpu_baseline(W)

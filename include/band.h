@@ -131,6 +131,35 @@ band_status band_sip(const band_desc* desc, const void* const diag[5], const voi
                      int32_t* iters, double* resid, int32_t* sys_status, void* ws, size_t ws_bytes,
                      void* stream);
 
+/* One batched launch over several independent problems (at most BAND_MAX_BATCH).
+ * The ADI step solves N systems per grid line and direction (Sec. 1); its solves are
+ * independent, so they share one kernel launch in which every warp takes 32 systems
+ * of one problem, filling the GPU even when each problem alone has too few systems.
+ * op = BAND_OP_SOLVE: method as for band_solve (fused, no stored factors; STDM/SPDM
+ *   systems with a zero pivot go through one batched symbolic fix-up launch).
+ * op = BAND_OP_SIP: Algorithm 1 with exact substitutions (width 0) on FP64 PD
+ *   systems, with tol and max_it as for band_sip; iters / resid may be NULL.
+ * Each problem brings its own workspace of band_workspace_size(desc, op, method, 0)
+ * bytes.  Argument checks as for the single calls; the first failing problem's code
+ * is returned and nothing is launched. */
+#define BAND_MAX_BATCH 64
+typedef struct {
+  int32_t op;                /* BAND_OP_SOLVE or BAND_OP_SIP */
+  int32_t method;            /* band_method (BAND_OP_SOLVE) */
+  const band_desc* desc;     /* host pointer */
+  const void* diag[5];
+  const void* f;
+  void* x;
+  int32_t* sys_status;
+  void* ws;
+  size_t ws_bytes;
+  double tol;                /* BAND_OP_SIP */
+  int32_t max_it;            /* BAND_OP_SIP */
+  int32_t* iters;            /* BAND_OP_SIP, may be NULL */
+  double* resid;             /* BAND_OP_SIP, may be NULL */
+} band_problem;
+band_status band_solve_batch(const band_problem* problems, int32_t count, void* stream);
+
 /* Mixed precision: PD/TD systems stored in FP32 (desc->dtype = BAND_F32 describes
  * diag32), right-hand side and solution in FP64 with the same strides.  FP32 NPDM/NTDM
  * solve, then refinement steps r = f - A x (FP64, A = the FP64 values of the FP32

@@ -281,6 +281,15 @@ def batch(method, k, diags, f, nsys, n, sys_stride, elem_stride, offsets=None, h
 
     f_arr = _np.ascontiguousarray(_np.asarray(f, dtype=_np.float64).reshape(-1))
     x = _np.zeros_like(f_arr)
+    # the C driver trusts the strides: check that every element it touches exists
+    if offsets is None:
+        last = (nsys - 1) * sys_stride + (n - 1) * elem_stride if nsys > 0 and n > 0 else -1
+    else:
+        last = int(_np.asarray(offsets)[-1]) - 1 if nsys > 0 else -1
+    for v in (a, b, c, d, e, f_arr):
+        if v is not None and last >= _np.asarray(v).size:
+            raise ValueError("batch layout reaches element %d of an array of %d"
+                             % (last, _np.asarray(v).size))
     status = _np.zeros(nsys, dtype=_np.int32)
     iters = _np.zeros(nsys, dtype=_np.int32)
     resid = _np.zeros(nsys, dtype=_np.float64)

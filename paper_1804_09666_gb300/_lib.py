@@ -24,7 +24,9 @@ F64, F32 = 0, 1
 OP_SOLVE, OP_FACTOR, OP_SIP, OP_REFINE, OP_ADJOINT = range(5)
 
 EXPORTS = ("band_workspace_size", "band_solve", "band_factor", "band_sip", "band_refine_solve",
-           "band_adjoint", "band_status_str", "band_version", "band_fp64_fma_rate")
+           "band_adjoint", "band_status_str", "band_version", "band_fp64_fma_rate",
+           "band_solve_batch", "band_solve_static")
+MAX_BATCH = 64
 
 
 class BandDesc(ct.Structure):
@@ -36,6 +38,13 @@ class BandDesc(ct.Structure):
 _lib = None
 P = ct.c_void_p
 DIAG5 = ct.c_void_p * 5
+
+
+class BandProblem(ct.Structure):
+    _fields_ = [("op", ct.c_int32), ("method", ct.c_int32), ("desc", ct.POINTER(BandDesc)),
+                ("diag", DIAG5), ("f", P), ("x", P), ("sys_status", P), ("ws", P),
+                ("ws_bytes", ct.c_size_t), ("tol", ct.c_double), ("max_it", ct.c_int32),
+                ("iters", P), ("resid", P)]
 
 
 def load(path=None):
@@ -61,6 +70,10 @@ def load(path=None):
         getattr(lib, name).restype = ct.c_int
     lib.band_status_str.argtypes = [i32]
     lib.band_status_str.restype = ct.c_char_p
+    lib.band_solve_batch.argtypes = [ct.POINTER(BandProblem), i32, P]
+    lib.band_solve_batch.restype = ct.c_int
+    lib.band_solve_static.argtypes = [D, i32, DIAG5, P, P, P, P]
+    lib.band_solve_static.restype = ct.c_int
     lib.band_fp64_fma_rate.argtypes = [P, sz, P]
     lib.band_fp64_fma_rate.restype = ct.c_double
     lib.band_version.argtypes = []

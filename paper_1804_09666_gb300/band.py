@@ -198,6 +198,75 @@ def adjoint(a, b, c, d, e, x, w, factors=None, method="npdm"):
     return tuple(grads), gf, status
 
 
+class BatchPlan:
+    """Several independent solves in one batched launch (band_solve_batch).
+
+    specs: list of dicts with keys
+      op      "solve" (default) or "sip" (Algorithm 1, exact substitutions)
+      method  for "solve": "npdm", "ntdm", "spdm", "stdm"
+      a, b, c, d, e, f   (n, nsys) tensors with equal strides (a, e None for TD)
+      x       optional output tensor
+      tol, max_it        for "sip"
+    Outputs, statuses and workspaces are allocated once here; ``run()`` only launches,
+    so a run can be captured in a CUDA graph.  results[i] holds x, status (and iters,
+    resid for "sip").
+    """
+
+    def __init__(self, specs):
+        lib = L.load()
+        if len(specs) > L.MAX_BATCH:
+            raise ValueError("at most %d problems per batch" % L.MAX_BATCH)
+        self.lib = lib
+        self.keep = []
+        self.results = []
+        self.arr = (L.BandProblem * max(len(specs), 1))()
+        for i, sp in enumerate(specs):
+            op = sp.get("op", "solve")
+            a, b, c, d, e, f = (sp.get(k) for k in "abcdef")
+            if op == "solve":
+                m = _METHODS[sp.get("method", "npdm")]
+                half_bw = 1 if sp.get("method") in ("ntdm", "stdm") else 2
+                opc = L.OP_SOLVE
+            elif op == "sip":
+                m, half_bw, opc = 0, 2, L.OP_SIP
+            else:
+                raise ValueError(op)
+            _check_same(c, a if half_bw == 2 else None, b, d, e if half_bw == 2 else None, f)
+            desc = desc_for(c, half_bw)
+            x = sp.get("x")
+            if x is None:
+                x = torch.empty_strided(c.shape, c.stride(), dtype=c.dtype, device=c.device)
+            status = torch.empty(c.shape[1], dtype=torch.int32, device=c.device)
+            need = lib.band_workspace_size(ct.byref(desc), opc, m, 0)
+            ws = _workspace(need, c.device)
+            res = dict(x=x, status=status)
+            P = self.arr[i]
+            P.op, P.method = opc, m
+            P.desc = ct.pointer(desc)
+            P.diag = _diag5(a, b, c, d, e)
+            P.f, P.x, P.sys_status = f.data_ptr(), x.data_ptr(), status.data_ptr()
+            P.ws, P.ws_bytes = ws.data_ptr(), ws.numel()
+            if op == "sip":
+                iters = torch.empty(c.shape[1], dtype=torch.int32, device=c.device)
+                resid = torch.empty(c.shape[1], dtype=torch.float64, device=c.device)
+                P.tol, P.max_it = sp.get("tol", 1e-10), sp.get("max_it", 200)
+                P.iters, P.resid = iters.data_ptr(), resid.data_ptr()
+                res.update(iters=iters, resid=resid)
+            self.keep.append((desc, a, b, c, d, e, f, ws))
+            self.results.append(res)
+        self.count = len(specs)
+
+    def run(self):
+        code = self.lib.band_solve_batch(self.arr, self.count, _stream())
+        L.check(code, "band_solve_batch")
+        return self.results
+
+
+def solve_batch(specs):
+    """One-shot batched solve; see BatchPlan.  Returns the list of results."""
+    return BatchPlan(specs).run()
+
+
 class BandSolve(torch.autograd.Function):
     """x = A^{-1} f for a batch of PD systems (NPDM forward, hand-written adjoint backward).
 

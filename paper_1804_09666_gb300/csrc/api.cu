@@ -12,11 +12,7 @@ namespace band {
 // Workspace of band_solve.  Numeric methods: alpha and beta rows.  Symbolic methods:
 // alpha, beta and z rows, the flagged-system counter and list, and the Laurent-series
 // rows of up to kMaxFixSlots flagged systems redone at a time.
-struct SolveWs {
-  void *al, *be, *zs, *count, *list, *slots;
-  int64_t nslots;
-};
-static SolveWs carve_solve(const band_desc* d, int32_t method, void* base, size_t* bytes) {
+SolveWs carve_solve(const band_desc* d, int32_t method, void* base, size_t* bytes) {
   Carve c(base);
   SolveWs w{};
   const size_t rows = (size_t)spill_rows(d) * dtype_size(d->dtype);
@@ -59,6 +55,49 @@ FactorPtrs factor_ptrs(const band_desc* d, const void* factors) {
   return FactorPtrs{fb.gam, fb.rmu, fb.al, fb.be};
 }
 
+band_status make_direct(const band_desc* desc, int32_t method, const void* const diag[5],
+                        const void* f, void* x, int32_t* sys_status, void* ws, size_t ws_bytes,
+                        DirectReq* r) {
+  if (!desc_ok(desc)) return BAND_ERR_ARG;
+  const int kmode = kmode_for(desc, method);
+  if (kmode < 0) return BAND_ERR_ARG;
+  if (is_symbolic(method) && desc->dtype != BAND_F64) return BAND_ERR_ARG;
+  if (!diag || !f || !x || !diag[1] || !diag[2] || !diag[3]) return BAND_ERR_ARG;
+  if (may_be_pd(desc) && kmode != 1 && (!diag[0] || !diag[4])) return BAND_ERR_ARG;
+  size_t need = 0;
+  carve_solve(desc, method, nullptr, &need);
+  if (!ws || ws_bytes < need) return BAND_ERR_WORKSPACE;
+  const SolveWs w = carve_solve(desc, method, ws, &need);
+  const Layout L = layout_of(desc);
+  const Spill W = spill_of(desc);
+  r->kmode = kmode;
+  r->symbolic = is_symbolic(method);
+  r->d64 = DirectArgs<double>{L, W,
+                              (const double*)diag[0], (const double*)diag[1],
+                              (const double*)diag[2], (const double*)diag[3],
+                              (const double*)diag[4], (const double*)f, (double*)x,
+                              (double*)w.al, (double*)w.be, (double*)w.zs, sys_status,
+                              (unsigned long long*)w.count, (int64_t*)w.list};
+  r->d32 = DirectArgs<float>{L, W,
+                             (const float*)diag[0], (const float*)diag[1], (const float*)diag[2],
+                             (const float*)diag[3], (const float*)diag[4], (const float*)f,
+                             (float*)x, (float*)w.al, (float*)w.be, nullptr, sys_status,
+                             nullptr, nullptr};
+  if (!r->symbolic) {
+    r->d64.zs = nullptr;
+    r->d64.fix_count = nullptr;
+    r->d64.fix_list = nullptr;
+  } else {
+    r->sym.fix_count_mut = w.count;
+    r->sym.args = SymArgs{L, (const double*)diag[0], (const double*)diag[1],
+                          (const double*)diag[2], (const double*)diag[3],
+                          (const double*)diag[4], (const double*)f, (double*)x, sys_status,
+                          (const unsigned long long*)w.count, (const int64_t*)w.list, w.slots,
+                          w.nslots, desc->n, nullptr, nullptr};
+  }
+  return BAND_OK;
+}
+
 }  // namespace band
 
 extern "C" {
@@ -84,13 +123,12 @@ band_status band_solve(const band_desc* desc, int32_t method, const void* factor
   if (kmode < 0) return BAND_ERR_ARG;
   if (is_symbolic(method) && (desc->dtype != BAND_F64 || factors)) return BAND_ERR_ARG;
   if (desc->nsys == 0) return BAND_OK;   // nothing to do (empty arrays may be NULL)
-  if (!diag || !f || !x) return BAND_ERR_ARG;
-  if (!diag[1] || !diag[2] || !diag[3]) return BAND_ERR_ARG;
-  if (may_be_pd(desc) && kmode != 1 && (!diag[0] || !diag[4])) return BAND_ERR_ARG;
   cudaStream_t st = static_cast<cudaStream_t>(stream);
-  const Layout L = layout_of(desc);
-  const Spill W = spill_of(desc);
   if (factors) {
+    if (!diag || !f || !x || !diag[1] || !diag[2] || !diag[3]) return BAND_ERR_ARG;
+    if (may_be_pd(desc) && kmode != 1 && (!diag[0] || !diag[4])) return BAND_ERR_ARG;
+    const Layout L = layout_of(desc);
+    const Spill W = spill_of(desc);
     const FactorPtrs fp = factor_ptrs(desc, factors);
     if (desc->dtype == BAND_F64) {
       FactoredArgs<double> p{L, W, (const double*)diag[0], (const double*)fp.gam,
@@ -103,39 +141,17 @@ band_status band_solve(const band_desc* desc, int32_t method, const void* factor
                           (const float*)f, (float*)x, sys_status};
     return cuda_status(launch_fsolve<float>(p, kmode, st));
   }
-  size_t need = 0;
-  carve_solve(desc, method, nullptr, &need);
-  if (!ws || ws_bytes < need) return BAND_ERR_WORKSPACE;
-  const SolveWs w = carve_solve(desc, method, ws, &need);
-  if (desc->dtype == BAND_F64) {
-    DirectArgs<double> p{L, W,
-                         (const double*)diag[0], (const double*)diag[1], (const double*)diag[2],
-                         (const double*)diag[3], (const double*)diag[4], (const double*)f,
-                         (double*)x, (double*)w.al, (double*)w.be, (double*)w.zs, sys_status,
-                         (unsigned long long*)w.count, (int64_t*)w.list};
-    if (is_symbolic(method)) {
-      cudaError_t e = cudaMemsetAsync(w.count, 0, sizeof(unsigned long long), st);
-      if (e != cudaSuccess) return BAND_ERR_CUDA;
-    } else {
-      p.fix_count = nullptr;
-      p.fix_list = nullptr;
-    }
-    cudaError_t e = launch_direct<double>(p, kmode, st);
-    if (e != cudaSuccess) return BAND_ERR_CUDA;
-    if (is_symbolic(method)) {
-      SymArgs q{L, (const double*)diag[0], (const double*)diag[1], (const double*)diag[2],
-                (const double*)diag[3], (const double*)diag[4], (const double*)f, (double*)x,
-                sys_status, (const unsigned long long*)w.count, (const int64_t*)w.list,
-                w.slots, w.nslots, desc->n, nullptr, nullptr};
-      e = launch_symbolic_fixup(q, st);
-    }
-    return cuda_status(e);
-  }
-  DirectArgs<float> p{L, W,
-                      (const float*)diag[0], (const float*)diag[1], (const float*)diag[2],
-                      (const float*)diag[3], (const float*)diag[4], (const float*)f, (float*)x,
-                      (float*)w.al, (float*)w.be, nullptr, sys_status, nullptr, nullptr};
-  return cuda_status(launch_direct<float>(p, kmode, st));
+  DirectReq r;
+  const band_status v = make_direct(desc, method, diag, f, x, sys_status, ws, ws_bytes, &r);
+  if (v != BAND_OK) return v;
+  if (r.symbolic && cudaMemsetAsync(r.sym.fix_count_mut, 0, sizeof(unsigned long long), st) !=
+                        cudaSuccess)
+    return BAND_ERR_CUDA;
+  cudaError_t e = desc->dtype == BAND_F64 ? launch_direct<double>(r.d64, r.kmode, st)
+                                          : launch_direct<float>(r.d32, r.kmode, st);
+  if (e != cudaSuccess) return BAND_ERR_CUDA;
+  if (r.symbolic) e = launch_symbolic_fixup(r.sym.args, st);
+  return cuda_status(e);
 }
 
 band_status band_factor(const band_desc* desc, int32_t method, const void* const diag[5],

@@ -1,0 +1,190 @@
+// batch.cu -- band_solve_batch: several independent problems in one launch.
+//
+// The ADI step of the paper solves N systems per grid line and direction
+// (Veneva & Ayriyan, Sec. 1); the solves of one step are independent.  One 2048 x 2048
+// sweep has only 2048 systems, 64 warps for 152 SMs, while the FP64 units of a
+// GB300 SM need at least four resident warps.  Here the problems of a step share one
+// kernel: every warp takes 32 consecutive systems of one problem (thread per system,
+// the sweeps of sweeps.cuh / sip_impl.cuh), so the launch holds the warps of all of
+// them.  The problem table travels as a __grid_constant__ kernel parameter; nothing
+// is allocated.
+#include <cstring>
+
+#include "api_util.h"
+#include "kernels.h"
+#include "sip_impl.cuh"
+#include "sweeps.cuh"
+
+namespace band {
+namespace {
+
+enum : int32_t { kDirect64 = 0, kDirect32 = 1, kSip = 2 };
+
+struct BatchItem {
+  int32_t kind;
+  int32_t kmode;     // 1 TD, 2 PD, 0 per system
+  int64_t task0;     // first warp of this problem
+  union {
+    DirectArgs<double> d64;
+    DirectArgs<float> d32;
+    SipArgs sip;
+  } u;
+};
+
+struct BatchTable {
+  int32_t count;
+  int32_t pad;
+  int64_t total;     // warps
+  BatchItem it[BAND_MAX_BATCH];
+};
+
+struct TailTable {
+  int32_t count;
+  int32_t pad;
+  SipArgs it[BAND_MAX_BATCH];
+};
+
+struct SymItem {
+  SymArgs a;
+  int64_t slot0;
+};
+
+struct SymTable {
+  int32_t count;
+  int32_t pad;
+  int64_t total;     // threads
+  SymItem it[BAND_MAX_BATCH];
+};
+
+template <typename T>
+__device__ __forceinline__ void run_direct(const DirectArgs<T>& p, int kmode, int64_t s) {
+  if (s >= p.L.nsys) return;
+  const int K = kmode ? kmode : p.L.kband(s);
+  if (K == 1) direct_one<T, 1>(p, s);
+  else direct_one<T, 2>(p, s);
+}
+
+__global__ void __launch_bounds__(128) k_batch(const __grid_constant__ BatchTable t) {
+  const int64_t warp = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+  if (warp >= t.total) return;
+  int j = 0;
+  while (j + 1 < t.count && t.it[j + 1].task0 <= warp) ++j;
+  const BatchItem& b = t.it[j];
+  const int64_t s = (warp - b.task0) * kWarp + (threadIdx.x & (kWarp - 1));
+  if (b.kind == kDirect64) run_direct<double>(b.u.d64, b.kmode, s);
+  else if (b.kind == kDirect32) run_direct<float>(b.u.d32, b.kmode, s);
+  else if (s < b.u.sip.L.nsys) sip_literal(b.u.sip, s);
+}
+
+__global__ void __launch_bounds__(64) k_symbolic_batch(const __grid_constant__ SymTable t) {
+  const int64_t g = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (g >= t.total) return;
+  int j = 0;
+  while (j + 1 < t.count && t.it[j + 1].slot0 <= g) ++j;
+  const SymArgs& p = t.it[j].a;
+  const int64_t slot = g - t.it[j].slot0;
+  const unsigned long long count = *p.fix_count;
+  Ser* mem = reinterpret_cast<Ser*>(p.slot_mem) + slot * 3 * p.nmax;
+  for (unsigned long long item = slot; item < count; item += p.nslots)
+    symbolic_one(p, p.fix_list[item], mem);
+}
+
+__global__ void __launch_bounds__(kTailThreads) k_sip_tail_batch(const __grid_constant__ TailTable t) {
+  __shared__ Aff sh[kTailThreads];
+  __shared__ double red[kTailThreads / 32];
+  for (int j = 0; j < t.count; ++j) {
+    const SipArgs& p = t.it[j];
+    const unsigned long long count = *p.tail_count;
+    for (unsigned long long it = blockIdx.x; it < count; it += gridDim.x) {
+      const int64_t s = p.tail_list[it];
+      sip_tail_block(p, s, p.tail_rn[s], sh, red);
+    }
+  }
+}
+
+}  // namespace
+}  // namespace band
+
+using namespace band;
+
+extern "C" band_status band_solve_batch(const band_problem* probs, int32_t count, void* stream) {
+  if (count < 0 || count > BAND_MAX_BATCH || (count > 0 && !probs)) return BAND_ERR_ARG;
+  static_assert(sizeof(BatchTable) < 32000, "kernel parameter table too large");
+  static_assert(sizeof(TailTable) < 32000, "kernel parameter table too large");
+  BatchTable t;
+  SymTable sym;
+  TailTable tail;
+  std::memset(&t, 0, sizeof t);
+  std::memset(&sym, 0, sizeof sym);
+  std::memset(&tail, 0, sizeof tail);
+  void* counters[BAND_MAX_BATCH];
+  int ncounters = 0;
+  int64_t warps = 0, slots = 0;
+  for (int32_t i = 0; i < count; ++i) {
+    const band_problem& q = probs[i];
+    if (!q.desc || !desc_ok(q.desc)) return BAND_ERR_ARG;
+    if (q.desc->nsys == 0) {
+      if (q.op != BAND_OP_SOLVE && q.op != BAND_OP_SIP) return BAND_ERR_ARG;
+      continue;
+    }
+    BatchItem& b = t.it[t.count];
+    if (q.op == BAND_OP_SOLVE) {
+      DirectReq r;
+      const band_status v = make_direct(q.desc, q.method, q.diag, q.f, q.x, q.sys_status, q.ws,
+                                        q.ws_bytes, &r);
+      if (v != BAND_OK) return v;
+      b.kmode = r.kmode;
+      if (q.desc->dtype == BAND_F64) {
+        b.kind = kDirect64;
+        b.u.d64 = r.d64;
+      } else {
+        b.kind = kDirect32;
+        b.u.d32 = r.d32;
+      }
+      if (r.symbolic) {
+        counters[ncounters++] = r.sym.fix_count_mut;
+        SymItem& si = sym.it[sym.count++];
+        si.a = r.sym.args;
+        si.slot0 = slots;
+        slots += r.sym.args.nslots;
+      }
+    } else if (q.op == BAND_OP_SIP) {
+      SipArgs sa;
+      const band_status v = make_sip(q.desc, q.diag, q.f, q.x, q.tol, q.max_it, 0, q.iters,
+                                     q.resid, q.sys_status, q.ws, q.ws_bytes, &sa, nullptr);
+      if (v != BAND_OK) return v;
+      b.kind = kSip;
+      b.kmode = 2;
+      b.u.sip = sa;
+      counters[ncounters++] = sa.tail_count;
+      tail.it[tail.count++] = sa;
+    } else {
+      return BAND_ERR_ARG;
+    }
+    b.task0 = warps;
+    warps += (q.desc->nsys + kWarp - 1) / kWarp;
+    ++t.count;
+  }
+  t.total = warps;
+  sym.total = slots;
+  if (warps == 0) return BAND_OK;
+  cudaStream_t st = static_cast<cudaStream_t>(stream);
+  for (int i = 0; i < ncounters; ++i)
+    if (cudaMemsetAsync(counters[i], 0, sizeof(unsigned long long), st) != cudaSuccess)
+      return BAND_ERR_CUDA;
+  const int64_t threads = warps * kWarp;
+  k_batch<<<(unsigned)((threads + 127) / 128), 128, 0, st>>>(t);
+  if (cudaGetLastError() != cudaSuccess) return BAND_ERR_CUDA;
+  if (sym.count > 0 && slots > 0) {
+    k_symbolic_batch<<<(unsigned)((slots + 63) / 64), 64, 0, st>>>(sym);
+    if (cudaGetLastError() != cudaSuccess) return BAND_ERR_CUDA;
+  }
+  if (tail.count > 0) {
+    int dev = 0, nsm = 0;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev);
+    k_sip_tail_batch<<<(unsigned)(2 * (nsm > 0 ? nsm : 1)), kTailThreads, 0, st>>>(tail);
+    if (cudaGetLastError() != cudaSuccess) return BAND_ERR_CUDA;
+  }
+  return BAND_OK;
+}

@@ -68,8 +68,23 @@ __device__ __forceinline__ double rcp<double>(double m) { return rcp64(m); }
 template <>
 __device__ __forceinline__ float rcp<float>(float m) { return rcp32(m); }
 
+// Tests on doubles done on their bit patterns with integer instructions: the FP64 pipe
+// of GB300 is the scarce unit of these kernels, so comparisons stay off it.
+__device__ __forceinline__ bool is_zero(double v) { return (__double_as_longlong(v) << 1) == 0; }
+__device__ __forceinline__ bool is_zero(float v) { return v == 0.0f; }
+__device__ __forceinline__ bool not_finite(double v) {
+  return ((unsigned)__double2hiint(v) & 0x7ff00000u) == 0x7ff00000u;
+}
+__device__ __forceinline__ bool not_finite(float v) { return !isfinite(v); }
+// max(acc, |v|) for acc >= 0 by integer comparison of the bit patterns (NaN wins).
+__device__ __forceinline__ double max_abs(double acc, double v) {
+  const long long a = __double_as_longlong(acc);
+  const long long b = __double_as_longlong(v) & 0x7fffffffffffffffLL;
+  return __longlong_as_double(a > b ? a : b);
+}
+
 template <typename T>
-__device__ __forceinline__ bool finite(T v) { return isfinite(v); }
+__device__ __forceinline__ bool finite(T v) { return !not_finite(v); }
 
 // read-only global load (the diagonals are never written by any kernel)
 template <typename T>

@@ -63,6 +63,29 @@ template <typename T> cudaError_t launch_fsolve(const FactoredArgs<T>&, int kmod
 cudaError_t launch_symbolic_fixup(const SymArgs&, cudaStream_t);
 size_t symbolic_slot_bytes(int64_t nmax);
 
+// Workspace of band_solve (see api.cu).
+struct SolveWs {
+  void *al, *be, *zs, *count, *list, *slots;
+  int64_t nslots;
+};
+SolveWs carve_solve(const band_desc* d, int32_t method, void* base, size_t* bytes);
+
+// A validated fused direct solve: kernel arguments for both element types and, for
+// symbolic methods, the fix-up arguments and the counter to clear before the sweep.
+struct DirectReq {
+  int kmode;
+  bool symbolic;
+  DirectArgs<double> d64;
+  DirectArgs<float> d32;
+  struct {
+    void* fix_count_mut;
+    SymArgs args;
+  } sym;
+};
+band_status make_direct(const band_desc* desc, int32_t method, const void* const diag[5],
+                        const void* f, void* x, int32_t* sys_status, void* ws, size_t ws_bytes,
+                        DirectReq* r);
+
 // host-side helpers shared by the entry points (defined in api.cu and the feature files)
 struct FactorPtrs {
   void *gam, *rmu, *al, *be;

