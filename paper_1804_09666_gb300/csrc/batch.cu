@@ -8,6 +8,7 @@
 // the sweeps of sweeps.cuh / sip_impl.cuh), so the launch holds the warps of all of
 // them.  The problem table travels as a __grid_constant__ kernel parameter; nothing
 // is allocated.
+#include <algorithm>
 #include <cstring>
 
 #include "api_util.h"
@@ -33,7 +34,7 @@ struct BatchItem {
 
 struct BatchTable {
   int32_t count;
-  int32_t pad;
+  int32_t stage_bytes;   // staging ring bytes per warp (0: none)
   int64_t total;     // warps
   BatchItem it[BAND_MAX_BATCH];
 };
@@ -57,23 +58,26 @@ struct SymTable {
 };
 
 template <typename T>
-__device__ __forceinline__ void run_direct(const DirectArgs<T>& p, int kmode, int64_t s) {
+__device__ __forceinline__ void run_direct(const DirectArgs<T>& p, int kmode, int64_t s,
+                                           void* stage) {
   if (s >= p.L.nsys) return;
   const int K = kmode ? kmode : p.L.kband(s);
-  if (K == 1) direct_one<T, 1>(p, s);
-  else direct_one<T, 2>(p, s);
+  if (K == 1) direct_one<T, 1>(p, s, stage);
+  else direct_one<T, 2>(p, s, stage);
 }
 
 __global__ void __launch_bounds__(128) k_batch(const __grid_constant__ BatchTable t) {
+  extern __shared__ __align__(16) unsigned char stage_mem[];
+  void* stage = t.stage_bytes ? stage_mem + (threadIdx.x >> 5) * t.stage_bytes : nullptr;
   const int64_t warp = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
   if (warp >= t.total) return;
   int j = 0;
   while (j + 1 < t.count && t.it[j + 1].task0 <= warp) ++j;
   const BatchItem& b = t.it[j];
   const int64_t s = (warp - b.task0) * kWarp + (threadIdx.x & (kWarp - 1));
-  if (b.kind == kDirect64) run_direct<double>(b.u.d64, b.kmode, s);
-  else if (b.kind == kDirect32) run_direct<float>(b.u.d32, b.kmode, s);
-  else if (s < b.u.sip.L.nsys) sip_literal(b.u.sip, s);
+  if (b.kind == kDirect64) run_direct<double>(b.u.d64, b.kmode, s, stage);
+  else if (b.kind == kDirect32) run_direct<float>(b.u.d32, b.kmode, s, stage);
+  else if (s < b.u.sip.L.nsys) sip_literal(b.u.sip, s, nullptr);
 }
 
 __global__ void __launch_bounds__(64) k_symbolic_batch(const __grid_constant__ SymTable t) {
@@ -137,9 +141,11 @@ extern "C" band_status band_solve_batch(const band_problem* probs, int32_t count
       if (q.desc->dtype == BAND_F64) {
         b.kind = kDirect64;
         b.u.d64 = r.d64;
+        t.stage_bytes = std::max(t.stage_bytes, stage_bytes_per_warp<double>());
       } else {
         b.kind = kDirect32;
         b.u.d32 = r.d32;
+        t.stage_bytes = std::max(t.stage_bytes, stage_bytes_per_warp<float>());
       }
       if (r.symbolic) {
         counters[ncounters++] = r.sym.fix_count_mut;
@@ -173,7 +179,8 @@ extern "C" band_status band_solve_batch(const band_problem* probs, int32_t count
     if (cudaMemsetAsync(counters[i], 0, sizeof(unsigned long long), st) != cudaSuccess)
       return BAND_ERR_CUDA;
   const int64_t threads = warps * kWarp;
-  k_batch<<<(unsigned)((threads + 127) / 128), 128, 0, st>>>(t);
+  k_batch<<<(unsigned)((threads + 127) / 128), 128,
+            (size_t)kStageWarpsPerBlock * (size_t)t.stage_bytes, st>>>(t);
   if (cudaGetLastError() != cudaSuccess) return BAND_ERR_CUDA;
   if (sym.count > 0 && slots > 0) {
     k_symbolic_batch<<<(unsigned)((slots + 63) / 64), 64, 0, st>>>(sym);

@@ -94,4 +94,51 @@ __device__ __forceinline__ void set_status(int32_t* st, int64_t s, int32_t v) {
   if (st) st[s] = v;
 }
 
+// ------------------------------------------------------------- async staging
+// Each lane copies its own element of a row into shared memory with cp.async (LDGSTS)
+// and later waits for the copy group of that row: rows are fetched kStage rows ahead
+// without holding registers.  A lane only ever reads what it copied itself, so no
+// barrier is involved.
+__device__ __forceinline__ void cp_async_elem(void* smem, const double* g) {
+  const unsigned s = (unsigned)__cvta_generic_to_shared(smem);
+  asm volatile("cp.async.ca.shared.global [%0], [%1], 8;\n" ::"r"(s), "l"(g) : "memory");
+}
+__device__ __forceinline__ void cp_async_elem(void* smem, const float* g) {
+  const unsigned s = (unsigned)__cvta_generic_to_shared(smem);
+  asm volatile("cp.async.ca.shared.global [%0], [%1], 4;\n" ::"r"(s), "l"(g) : "memory");
+}
+__device__ __forceinline__ void cp_async_commit() {
+  asm volatile("cp.async.commit_group;\n" ::: "memory");
+}
+template <int N>
+__device__ __forceinline__ void cp_async_wait() {
+  asm volatile("cp.async.wait_group %0;\n" ::"n"(N) : "memory");
+}
+
+// Rows staged per warp: an FP64 row carries ~14 FP64 instructions (>1000 cycles with
+// several warps per sub-partition), so 4 rows cover the memory latency; an FP32 row is
+// cheap, so 16.  Ring bytes per warp for six arrays: 6 KiB (FP64) and 12 KiB (FP32).
+template <typename T> struct StageDepth;
+template <> struct StageDepth<double> { static constexpr int value = 4; };
+template <> struct StageDepth<float> { static constexpr int value = 16; };
+constexpr int kStageArrays = 6;
+template <typename T>
+__host__ __device__ constexpr int stage_bytes_per_warp() { return StageDepth<T>::value * kStageArrays * 32 * (int)sizeof(T); }
+constexpr int kStageWarpsPerBlock = 4;
+
+// Ring of D rows x NA arrays x 32 lanes for one warp.
+template <typename T, int NA, int D>
+struct RowRing {
+  T* sm;
+  int lane;
+  __device__ __forceinline__ T* at(int slot, int a) const { return sm + ((slot * NA + a) << 5) + lane; }
+  __device__ __forceinline__ void issue(int slot, const T* const* src, int64_t q) const {
+#pragma unroll
+    for (int a = 0; a < NA; ++a) cp_async_elem(at(slot, a), src[a] + q);
+    cp_async_commit();
+  }
+  __device__ __forceinline__ void skip() const { cp_async_commit(); }
+  __device__ __forceinline__ T get(int slot, int a) const { return *at(slot, a); }
+};
+
 }  // namespace band

@@ -25,24 +25,27 @@ namespace band {
 // ---------------------------------------------------------------------------
 template <typename T, int K>
 __global__ void __launch_bounds__(128) k_direct(const DirectArgs<T> p) {
+  extern __shared__ __align__(16) unsigned char stage_mem[];
   const int64_t s = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   if (s >= p.L.nsys) return;
+  void* stage = stage_mem + (threadIdx.x >> 5) * stage_bytes_per_warp<T>();
   if (K == 0) {
-    if (p.L.kband(s) == 1) direct_one<T, 1>(p, s);
-    else direct_one<T, 2>(p, s);
+    if (p.L.kband(s) == 1) direct_one<T, 1>(p, s, stage);
+    else direct_one<T, 2>(p, s, stage);
   } else {
-    direct_one<T, K>(p, s);
+    direct_one<T, K>(p, s, stage);
   }
 }
 
 template <typename T>
 cudaError_t launch_direct(const DirectArgs<T>& p, int kmode, cudaStream_t st) {
   if (p.L.nsys == 0) return cudaSuccess;
-  const int tb = 128;
+  const int tb = 32 * kStageWarpsPerBlock;
+  const size_t smem = (size_t)kStageWarpsPerBlock * stage_bytes_per_warp<T>();
   const unsigned grid = (unsigned)((p.L.nsys + tb - 1) / tb);
-  if (kmode == 1) k_direct<T, 1><<<grid, tb, 0, st>>>(p);
-  else if (kmode == 2) k_direct<T, 2><<<grid, tb, 0, st>>>(p);
-  else k_direct<T, 0><<<grid, tb, 0, st>>>(p);
+  if (kmode == 1) k_direct<T, 1><<<grid, tb, smem, st>>>(p);
+  else if (kmode == 2) k_direct<T, 2><<<grid, tb, smem, st>>>(p);
+  else k_direct<T, 0><<<grid, tb, smem, st>>>(p);
   return cudaGetLastError();
 }
 template cudaError_t launch_direct<double>(const DirectArgs<double>&, int, cudaStream_t);

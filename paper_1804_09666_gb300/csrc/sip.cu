@@ -121,11 +121,11 @@ __global__ void __launch_bounds__(128) k_ilu0(const SipArgs p) {
   set_status(p.status, s, ilu0_into(p, s) ? BAND_OK : BAND_ERR_ZERO_PIVOT);
 }
 
-__global__ void __launch_bounds__(64) k_sip(const SipArgs p) {
+__global__ void __launch_bounds__(128) k_sip(const SipArgs p) {
   const int64_t s = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   if (s >= p.L.nsys) return;
   if (p.w == 0) {            // ILU(0) is fused into the first update
-    sip_literal(p, s);
+    sip_literal(p, s, nullptr);
     return;
   }
   if (p.status && p.status[s] != BAND_OK) {  // ILU(0) or HB failed for this system
@@ -282,7 +282,7 @@ extern "C" band_status band_sip(const band_desc* desc, const void* const diag[5]
   if (width == 0 && cudaMemsetAsync(sa.tail_count, 0, sizeof(unsigned long long), st) !=
                         cudaSuccess)
     return BAND_ERR_CUDA;
-  k_sip<<<g64, 64, 0, st>>>(sa);
+  k_sip<<<g128, 128, 0, st>>>(sa);
   if (cudaGetLastError() != cudaSuccess) return BAND_ERR_CUDA;
   if (width == 0) return cuda_status(launch_sip_tail(sa, desc->nsys, st));
   return BAND_OK;

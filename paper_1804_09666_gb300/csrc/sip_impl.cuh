@@ -254,7 +254,7 @@ __device__ inline bool ilu0_into(const SipArgs& p, int64_t s) {
 // is x^1 = U^{-1} L^{-1} f: one forward sweep does ILU(0) and L y = f together (only
 // 1/u0, u1 and y are kept), one backward sweep does U x = y and the residual of every
 // row (two rows behind).  Systems that need more updates rebuild the full factors.
-__device__ inline void sip_literal(const SipArgs& p, int64_t s) {
+__device__ inline void sip_literal(const SipArgs& p, int64_t s, void* stage) {
   const int64_t n = p.L.rows(s), q0 = p.L.base(s), es = p.L.stride();
   const int64_t w0 = p.W.base(s), ws = p.W.stride();
   double ru0_1 = 0, u1_1 = 0, e_1 = 0, ru0_2 = 0, u1_2 = 0, e_2 = 0;

@@ -35,12 +35,48 @@ __device__ __forceinline__ void load_in(const DirectArgs<T>& p, int64_t q, RowIn
   }
 }
 
-// One system, one thread: forward sweep (factor + z), then backward sweep (x).  Loads
-// are issued two rows ahead of their use so that the memory latency overlaps the
-// recurrence.  alpha, beta go to the workspace rows; z goes to x (numeric methods) or
-// to the workspace (symbolic methods, keeping f intact when x aliases f).
+// One row of the NPDM / NTDM forward recurrence.  Returns false on a zero pivot.
 template <typename T, int K>
-__device__ __forceinline__ void direct_one(const DirectArgs<T>& p, int64_t s) {
+__device__ __forceinline__ bool forward_row(const DirectArgs<T>& p, int64_t i, int64_t n,
+                                            int64_t q, int64_t w, T ai, T bi, T ci, T di, T ei,
+                                            T fi, T& al1, T& al2, T& be1, T& be2, T& z1, T& z2) {
+  bi = (i >= 1) ? bi : T(0);
+  di = (i + 1 < n) ? di : T(0);
+  if (K == 2) {
+    ai = (i >= 2) ? ai : T(0);
+    ei = (i + 2 < n) ? ei : T(0);
+    const T g = fma(-al2, ai, bi);
+    const T m = fma(-al1, g, fma(-be2, ai, ci));
+    if (is_zero(m)) return false;
+    const T r = rcp<T>(m);
+    const T alv = fma(-be1, g, di) * r;
+    const T bev = ei * r;
+    const T zv = fma(-z1, g, fma(-z2, ai, fi)) * r;
+    p.al[w] = alv;
+    p.be[w] = bev;
+    if (p.zs) p.zs[w] = zv; else p.x[q] = zv;
+    al2 = al1; al1 = alv; be2 = be1; be1 = bev; z2 = z1; z1 = zv;
+  } else {
+    const T m = fma(-al1, bi, ci);
+    if (is_zero(m)) return false;
+    const T r = rcp<T>(m);
+    const T alv = di * r;
+    const T zv = fma(-z1, bi, fi) * r;
+    p.al[w] = alv;
+    if (p.zs) p.zs[w] = zv; else p.x[q] = zv;
+    al1 = alv; z1 = zv;
+  }
+  return true;
+}
+
+// One system, one thread: forward sweep (factor + z), then backward sweep (x).  The
+// rows of the forward sweep are staged through this warp's shared-memory ring
+// (`stage`, stage_bytes_per_warp<T>() bytes) StageDepth<T> rows ahead of their use, so the
+// memory latency overlaps the recurrence.  alpha, beta go to the workspace rows; z goes
+// to x (numeric methods) or to the workspace (symbolic methods, keeping f intact when
+// x aliases f).
+template <typename T, int K>
+__device__ __forceinline__ void direct_one(const DirectArgs<T>& p, int64_t s, void* stage) {
   const int64_t n = p.L.rows(s);
   if (n <= 0) {
     set_status(p.status, s, BAND_OK);
@@ -50,41 +86,55 @@ __device__ __forceinline__ void direct_one(const DirectArgs<T>& p, int64_t s) {
   const int64_t w0 = p.W.base(s), wst = p.W.stride();
   T al1 = 0, al2 = 0, be1 = 0, be2 = 0, z1 = 0, z2 = 0;
   bool zero = false;
-  RowIn<T> r0, r1, r2;
-  load_in<T, K>(p, q0, r0);
-  if (n > 1) load_in<T, K>(p, q0 + es, r1);
-  for (int64_t i = 0; i < n; ++i) {
-    if (i + 2 < n) load_in<T, K>(p, q0 + (i + 2) * es, r2);
-    const int64_t q = q0 + i * es;
-    const int64_t w = w0 + i * wst;
-    const T bi = (i >= 1) ? r0.b : T(0);
-    const T di = (i + 1 < n) ? r0.d : T(0);
+  // Interleaved systems (consecutive lanes read consecutive addresses) are staged through
+  // the warp's shared-memory ring; other layouts prefetch two rows into registers and
+  // lean on L1 for the sectors they share across rows.
+  if (stage && !p.L.offsets && p.L.ss == 1) {
+    constexpr int D = StageDepth<T>::value;
+    constexpr int NA = K == 2 ? 6 : 4;     // arrays staged: (a,) b, c, d, (e,) f
+    const RowRing<T, NA, D> ring{static_cast<T*>(stage), (int)(threadIdx.x & 31)};
+    const T* src[NA];
     if (K == 2) {
-      const T ai = (i >= 2) ? r0.a : T(0);
-      const T ei = (i + 2 < n) ? r0.e : T(0);
-      const T g = fma(-al2, ai, bi);
-      const T m = fma(-al1, g, fma(-be2, ai, r0.c));
-      if (is_zero(m)) { zero = true; break; }
-      const T r = rcp<T>(m);
-      const T alv = fma(-be1, g, di) * r;
-      const T bev = ei * r;
-      const T zv = fma(-z1, g, fma(-z2, ai, r0.f)) * r;
-      p.al[w] = alv;
-      p.be[w] = bev;
-      if (p.zs) p.zs[w] = zv; else p.x[q] = zv;
-      al2 = al1; al1 = alv; be2 = be1; be1 = bev; z2 = z1; z1 = zv;
+      src[0] = p.a; src[1] = p.b; src[2] = p.c; src[3] = p.d; src[4] = p.e; src[5] = p.f;
     } else {
-      const T m = fma(-al1, bi, r0.c);
-      if (is_zero(m)) { zero = true; break; }
-      const T r = rcp<T>(m);
-      const T alv = di * r;
-      const T zv = fma(-z1, bi, r0.f) * r;
-      p.al[w] = alv;
-      if (p.zs) p.zs[w] = zv; else p.x[q] = zv;
-      al1 = alv; z1 = zv;
+      src[0] = p.b; src[1] = p.c; src[2] = p.d; src[3] = p.f;
     }
-    r0 = r1;
-    r1 = r2;
+    constexpr int IB = K == 2 ? 1 : 0, IC = IB + 1, ID = IB + 2, IF = NA - 1;
+#pragma unroll
+    for (int j = 0; j < D - 1; ++j) {
+      if (j < n) ring.issue(j, src, q0 + j * es);
+      else ring.skip();
+    }
+    for (int64_t i = 0; i < n; ++i) {
+      const int64_t ip = i + D - 1;
+      if (ip < n) ring.issue((int)(ip & (D - 1)), src, q0 + ip * es);
+      else ring.skip();
+      cp_async_wait<D - 1>();
+      const int slot = (int)(i & (D - 1));
+      const T ai = K == 2 ? ring.get(slot, 0) : T(0);
+      const T ei = K == 2 ? ring.get(slot, 4) : T(0);
+      if (!forward_row<T, K>(p, i, n, q0 + i * es, w0 + i * wst, ai, ring.get(slot, IB),
+                             ring.get(slot, IC), ring.get(slot, ID), ei, ring.get(slot, IF),
+                             al1, al2, be1, be2, z1, z2)) {
+        zero = true;
+        break;
+      }
+    }
+    cp_async_wait<0>();
+  } else {
+    RowIn<T> r0, r1, r2;
+    load_in<T, K>(p, q0, r0);
+    if (n > 1) load_in<T, K>(p, q0 + es, r1);
+    for (int64_t i = 0; i < n; ++i) {
+      if (i + 2 < n) load_in<T, K>(p, q0 + (i + 2) * es, r2);
+      if (!forward_row<T, K>(p, i, n, q0 + i * es, w0 + i * wst, r0.a, r0.b, r0.c, r0.d, r0.e,
+                             r0.f, al1, al2, be1, be2, z1, z2)) {
+        zero = true;
+        break;
+      }
+      r0 = r1;
+      r1 = r2;
+    }
   }
   if (zero) {
     if (p.fix_list) {  // symbolic method: hand the system to the fix-up pass
