@@ -228,3 +228,29 @@ def test_sip_tail_with_unreachable_tolerance(band, nsys, n):
     assert (so == 6).all()
     assert (rs <= 1e-14).all() and (rso <= 1e-14).all()
     assert per_system_rel(flat_of(x), xo, n, nsys, 1, nsys).max() <= 1e-13
+
+
+@pytest.mark.parametrize("k,layout,n,nsys", [(2, "interleaved", 700, 70), (1, "interleaved", 300, 40),
+                                             (2, "contiguous", 257, 33), (1, "contiguous", 64, 5),
+                                             (2, "interleaved", 1, 8), (2, "interleaved", 2, 8),
+                                             (2, "interleaved", 3, 8), (1, "interleaved", 2, 8)])
+def test_refine_layouts_and_bandwidths(band, k, layout, n, nsys):
+    """FP32 storage, FP64 result: forward error <= 1e-10 against the FP64 truth for TD
+    (a, e omitted) and PD systems, interleaved and contiguous, and tiny n."""
+    rng = np.random.default_rng(100 * k + n)
+    D = synth.dominant(rng, nsys, n, k=k, dtype=np.float32, ratio=1.1, flip_frac=0.05)
+    if n == 1:                        # no off-diagonals: ratio * 0 would be singular
+        D["c"][:] = np.float32(1.5)
+    xt, f = synth.manufactured(rng, k, D, nsys, n)
+    B = synth.batch(D, f, k, nsys, n, layout)
+    ss, es = B["sys_stride"], B["elem_stride"]
+    T = {q: strided_view(B[q], n, nsys, ss, es, torch.float32) for q in "abcde"}
+    fd = strided_view(B["f"], n, nsys, ss, es)
+    a, e = (T["a"], T["e"]) if k == 2 else (None, None)
+    x, steps, st = band.refine_solve(a, T["b"], T["c"], T["d"], e, fd)
+    torch.cuda.synchronize()
+    assert (st.cpu() == 0).all()
+    xtruth, so, _, _ = oracle.batch("gepp", k, [B[q].astype(np.float64) for q in "abcde"], B["f"],
+                                    nsys, n, ss, es)
+    assert (so == 0).all()
+    assert per_system_rel(flat_of(x), xtruth, n, nsys, ss, es).max() <= 1e-10
