@@ -85,7 +85,31 @@ typedef struct {
                              (system s = rows offsets[s] .. offsets[s+1]-1); else NULL */
   const int8_t* hbw;      /* device array of per-system half bandwidths (1 or 2), or NULL */
   int64_t total_rows;     /* ragged: offsets[nsys] (the host's copy); uniform: ignored */
+  int32_t schedule;       /* band_schedule for NTDM/NPDM solves (BAND_SCHED_AUTO = 0) */
+  int32_t reserved;       /* 0 */
 } band_desc;
+
+/* How the fused direct sweep (NTDM/NPDM, and the numeric sweep of STDM/SPDM) maps onto
+ * threads; solves with stored factors, per-system bandwidths and the symbolic fix-up
+ * always take one thread per system.
+ * BAND_SCHED_THREAD: one thread per system runs the whole recurrence of Sec. 1.
+ * BAND_SCHED_TWO_SIDED: two threads per system.  One eliminates rows 0 .. m-1 top-down
+ *   (m = ceil(n/2); NPDM's own operations on those rows), the other rows n-1 .. m
+ *   bottom-up (the same recurrence on the row- and column-reversed system, i.e. the UL
+ *   factorisation of that block); they meet in a 4x4 (PD) / 2x2 (TD) interface system
+ *   solved with partial pivoting, then back-substitute their halves.  Each dependent
+ *   chain is half as long and the launch has twice the threads.  A zero pivot in either
+ *   half, or a singular interface system, sends an STDM/SPDM system to the symbolic
+ *   fix-up (as a zero pivot of the one-thread sweep does); for NTDM/NPDM it makes the
+ *   first thread redo the system with NPDM alone, so BAND_ERR_ZERO_PIVOT still means that
+ *   NPDM's order meets an exactly zero pivot -- except when x aliases f (f is then
+ *   already overwritten), where it means a zero pivot of the two-sided elimination.  A
+ *   system that NPDM's order would fail on in its lower half may be solved (status OK).
+ *   Systems with fewer than 4 (PD) / 2 (TD) rows are solved by one thread.  Needs one
+ *   half bandwidth for the batch.
+ * BAND_SCHED_AUTO: TWO_SIDED for uniform-bandwidth, non-ragged solves with n >= 32 and
+ *   (NTDM/NPDM) x not aliasing f; THREAD otherwise. */
+typedef enum { BAND_SCHED_AUTO = 0, BAND_SCHED_THREAD = 1, BAND_SCHED_TWO_SIDED = 2 } band_schedule;
 
 /* Bytes of workspace that the operation `op` needs for `desc` (0 = none).  op is one
  * of the BAND_OP_* values; `method` as for the call it serves (ignored where n/a). */

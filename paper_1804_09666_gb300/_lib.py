@@ -20,6 +20,8 @@ STATUS_NAMES = {OK: "OK", ERR_ARG: "ARG", ERR_CUDA: "CUDA", ERR_ZERO_PIVOT: "ZER
 NTDM, NPDM, STDM, SPDM, AUTO_NUMERIC, AUTO_SYMBOLIC = range(6)
 # band_dtype
 F64, F32 = 0, 1
+# band_schedule
+SCHED_AUTO, SCHED_THREAD, SCHED_TWO_SIDED = 0, 1, 2
 # BAND_OP_*
 OP_SOLVE, OP_FACTOR, OP_SIP, OP_REFINE, OP_ADJOINT = range(5)
 
@@ -32,7 +34,8 @@ MAX_BATCH = 64
 class BandDesc(ct.Structure):
     _fields_ = [("half_bw", ct.c_int32), ("dtype", ct.c_int32), ("nsys", ct.c_int64),
                 ("n", ct.c_int64), ("sys_stride", ct.c_int64), ("elem_stride", ct.c_int64),
-                ("offsets", ct.c_void_p), ("hbw", ct.c_void_p), ("total_rows", ct.c_int64)]
+                ("offsets", ct.c_void_p), ("hbw", ct.c_void_p), ("total_rows", ct.c_int64),
+                ("schedule", ct.c_int32), ("reserved", ct.c_int32)]
 
 
 _lib = None

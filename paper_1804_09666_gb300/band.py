@@ -41,7 +41,10 @@ def _dtype_code(t):
     raise TypeError("band arrays must be float64 or float32, got %s" % t.dtype)
 
 
-def desc_for(ref, half_bw):
+_SCHEDULES = {"auto": L.SCHED_AUTO, "thread": L.SCHED_THREAD, "two_sided": L.SCHED_TWO_SIDED}
+
+
+def desc_for(ref, half_bw, schedule="auto"):
     """BandDesc for (n, nsys)-shaped tensors with ref's strides."""
     if ref.dim() != 2:
         raise ValueError("expected a (n, nsys) tensor")
@@ -49,7 +52,7 @@ def desc_for(ref, half_bw):
     return L.BandDesc(half_bw=half_bw, dtype=_dtype_code(ref), nsys=nsys, n=n,
                       sys_stride=ref.stride(1) if nsys > 1 else max(n, 1),
                       elem_stride=ref.stride(0) if n > 1 else max(nsys, 1),
-                      offsets=None, hbw=None, total_rows=0)
+                      offsets=None, hbw=None, total_rows=0, schedule=_SCHEDULES[schedule])
 
 
 def _check_same(ref, *ts):
@@ -70,17 +73,20 @@ def _workspace(nbytes, device):
     return torch.empty(max(int(nbytes), 1), dtype=torch.uint8, device=device)
 
 
-def solve(a, b, c, d, e, f, method="npdm", x=None, status=None, factors=None, ws=None):
+def solve(a, b, c, d, e, f, method="npdm", x=None, status=None, factors=None, ws=None,
+          schedule="auto"):
     """Solve A x = f for a uniform batch.  Returns (x, status int32[nsys]).
 
     method: "npdm", "ntdm", "spdm", "stdm".  a, e are ignored (may be None) for TD.
     factors: a buffer from ``factor`` to reuse a factorisation (numeric methods).
+    schedule: "auto", "thread" (one thread per system) or "two_sided" (two threads per
+    system meeting in the middle; numeric methods without factors).
     """
     lib = L.load()
     m = _METHODS[method]
     half_bw = 1 if method in ("ntdm", "stdm") else 2
     _check_same(c, a if half_bw == 2 else None, b, d, e if half_bw == 2 else None, f)
-    desc = desc_for(c, half_bw)
+    desc = desc_for(c, half_bw, schedule)
     if x is None:
         x = torch.empty_strided(c.shape, c.stride(), dtype=c.dtype, device=c.device)
     _check_same(c, x)
@@ -207,6 +213,7 @@ class BatchPlan:
       a, b, c, d, e, f   (n, nsys) tensors with equal strides (a, e None for TD)
       x       optional output tensor
       tol, max_it        for "sip"
+      schedule           for "solve": "auto" (default), "thread", "two_sided"
     Outputs, statuses and workspaces are allocated once here; ``run()`` only launches,
     so a run can be captured in a CUDA graph.  results[i] holds x, status (and iters,
     resid for "sip").
@@ -232,7 +239,7 @@ class BatchPlan:
             else:
                 raise ValueError(op)
             _check_same(c, a if half_bw == 2 else None, b, d, e if half_bw == 2 else None, f)
-            desc = desc_for(c, half_bw)
+            desc = desc_for(c, half_bw, sp.get("schedule", "auto"))
             x = sp.get("x")
             if x is None:
                 x = torch.empty_strided(c.shape, c.stride(), dtype=c.dtype, device=c.device)

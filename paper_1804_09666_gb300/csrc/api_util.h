@@ -54,6 +54,8 @@ inline bool desc_ok(const band_desc* d) {
   if (d->dtype != BAND_F64 && d->dtype != BAND_F32) return false;
   if (d->nsys < 0 || d->n < 1) return false;
   if (!d->hbw && d->half_bw != 1 && d->half_bw != 2) return false;
+  if (d->schedule < BAND_SCHED_AUTO || d->schedule > BAND_SCHED_TWO_SIDED || d->reserved != 0)
+    return false;
   if (ragged(d)) {
     if (d->total_rows < 0) return false;
   } else {

@@ -23,7 +23,8 @@ enum : int32_t { kDirect64 = 0, kDirect32 = 1, kSip = 2 };
 
 struct BatchItem {
   int32_t kind;
-  int32_t kmode;     // 1 TD, 2 PD, 0 per system
+  int16_t kmode;     // 1 TD, 2 PD, 0 per system
+  int16_t two_sided; // two threads (lanes l, l ^ 16) per system
   int64_t task0;     // first warp of this problem
   union {
     DirectArgs<double> d64;
@@ -74,6 +75,17 @@ __global__ void __launch_bounds__(128) k_batch(const __grid_constant__ BatchTabl
   int j = 0;
   while (j + 1 < t.count && t.it[j + 1].task0 <= warp) ++j;
   const BatchItem& b = t.it[j];
+  if (b.two_sided) {         // 16 systems per warp
+    const int64_t s2 = (warp - b.task0) * 16 + (threadIdx.x & 15);
+    if (b.kind == kDirect64) {
+      if (b.kmode == 1) twisted_one<double, 1>(b.u.d64, s2, s2 < b.u.d64.L.nsys, stage);
+      else twisted_one<double, 2>(b.u.d64, s2, s2 < b.u.d64.L.nsys, stage);
+    } else {
+      if (b.kmode == 1) twisted_one<float, 1>(b.u.d32, s2, s2 < b.u.d32.L.nsys, stage);
+      else twisted_one<float, 2>(b.u.d32, s2, s2 < b.u.d32.L.nsys, stage);
+    }
+    return;
+  }
   const int64_t s = (warp - b.task0) * kWarp + (threadIdx.x & (kWarp - 1));
   if (b.kind == kDirect64) run_direct<double>(b.u.d64, b.kmode, s, stage);
   else if (b.kind == kDirect32) run_direct<float>(b.u.d32, b.kmode, s, stage);
@@ -137,7 +149,8 @@ extern "C" band_status band_solve_batch(const band_problem* probs, int32_t count
       const band_status v = make_direct(q.desc, q.method, q.diag, q.f, q.x, q.sys_status, q.ws,
                                         q.ws_bytes, &r);
       if (v != BAND_OK) return v;
-      b.kmode = r.kmode;
+      b.kmode = (int16_t)r.kmode;
+      b.two_sided = r.two_sided ? 1 : 0;
       if (q.desc->dtype == BAND_F64) {
         b.kind = kDirect64;
         b.u.d64 = r.d64;
@@ -161,6 +174,7 @@ extern "C" band_status band_solve_batch(const band_problem* probs, int32_t count
       if (v != BAND_OK) return v;
       b.kind = kSip;
       b.kmode = 2;
+      b.two_sided = 0;
       b.u.sip = sa;
       counters[ncounters++] = sa.tail_count;
       tail.it[tail.count++] = sa;
@@ -168,7 +182,7 @@ extern "C" band_status band_solve_batch(const band_problem* probs, int32_t count
       return BAND_ERR_ARG;
     }
     b.task0 = warps;
-    warps += (q.desc->nsys + kWarp - 1) / kWarp;
+    warps += b.two_sided ? (q.desc->nsys + 15) / 16 : (q.desc->nsys + kWarp - 1) / kWarp;
     ++t.count;
   }
   t.total = warps;

@@ -51,6 +51,30 @@ cudaError_t launch_direct(const DirectArgs<T>& p, int kmode, cudaStream_t st) {
 template cudaError_t launch_direct<double>(const DirectArgs<double>&, int, cudaStream_t);
 template cudaError_t launch_direct<float>(const DirectArgs<float>&, int, cudaStream_t);
 
+// two threads (lanes l, l ^ 16) per system; one bandwidth for the batch
+template <typename T, int K>
+__global__ void __launch_bounds__(128) k_twisted(const DirectArgs<T> p) {
+  extern __shared__ __align__(16) unsigned char stage_mem[];
+  void* stage = stage_mem + (threadIdx.x >> 5) * stage_bytes_per_warp<T>();
+  const int64_t warp = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+  const int64_t s = warp * 16 + (threadIdx.x & 15);
+  twisted_one<T, K>(p, s, s < p.L.nsys, stage);
+}
+
+template <typename T>
+cudaError_t launch_twisted(const DirectArgs<T>& p, int kmode, cudaStream_t st) {
+  if (p.L.nsys == 0) return cudaSuccess;
+  const int64_t threads = (p.L.nsys + 15) / 16 * 32;
+  const unsigned grid = (unsigned)((threads + 127) / 128);
+  const size_t smem = (size_t)kStageWarpsPerBlock * stage_bytes_per_warp<T>();
+  if (kmode == 1) k_twisted<T, 1><<<grid, 128, smem, st>>>(p);
+  else if (kmode == 2) k_twisted<T, 2><<<grid, 128, smem, st>>>(p);
+  else return cudaErrorInvalidValue;
+  return cudaGetLastError();
+}
+template cudaError_t launch_twisted<double>(const DirectArgs<double>&, int, cudaStream_t);
+template cudaError_t launch_twisted<float>(const DirectArgs<float>&, int, cudaStream_t);
+
 // ---------------------------------------------------------------------------
 // factorisation only: gamma, 1/mu, alpha, beta per row (interleaved like the spill)
 // ---------------------------------------------------------------------------

@@ -58,6 +58,7 @@ struct SymArgs {
 };
 
 template <typename T> cudaError_t launch_direct(const DirectArgs<T>&, int kmode, cudaStream_t);
+template <typename T> cudaError_t launch_twisted(const DirectArgs<T>&, int kmode, cudaStream_t);
 template <typename T> cudaError_t launch_factor(const FactorArgs<T>&, int kmode, cudaStream_t);
 template <typename T> cudaError_t launch_fsolve(const FactoredArgs<T>&, int kmode, cudaStream_t);
 cudaError_t launch_symbolic_fixup(const SymArgs&, cudaStream_t);
@@ -75,6 +76,9 @@ SolveWs carve_solve(const band_desc* d, int32_t method, void* base, size_t* byte
 struct DirectReq {
   int kmode;
   bool symbolic;
+  bool two_ok;          // the two-sided schedule applies (numeric, one bandwidth)
+  bool two_sided;       // schedule: two threads per system
+  bool alias;           // x is f
   DirectArgs<double> d64;
   DirectArgs<float> d32;
   struct {
@@ -85,6 +89,7 @@ struct DirectReq {
 band_status make_direct(const band_desc* desc, int32_t method, const void* const diag[5],
                         const void* f, void* x, int32_t* sys_status, void* ws, size_t ws_bytes,
                         DirectReq* r);
+bool choose_two_sided(const band_desc* d, bool alias);
 
 // host-side helpers shared by the entry points (defined in api.cu and the feature files)
 struct FactorPtrs {

@@ -45,8 +45,8 @@ def test_exports_match_binding_list(lib):
 
 def test_desc_layout():
     from paper_1804_09666_gb300 import _lib as L
-    # int32, int32, 4 x int64, 2 pointers, int64
-    assert ct.sizeof(L.BandDesc) == 8 + 4 * 8 + 2 * 8 + 8
+    # int32, int32, 4 x int64, 2 pointers, int64, int32, int32
+    assert ct.sizeof(L.BandDesc) == 8 + 4 * 8 + 2 * 8 + 8 + 8
 
 
 def test_status_strings(lib):
@@ -96,6 +96,9 @@ def test_bad_arguments_are_rejected_without_gpu(lib):
         (_desc(half_bw=2), L.NPDM, nul),          # PD without a, e
         (_desc(), 17, full),                      # unknown method
         (_desc(dtype=L.F32), L.SPDM, full),       # symbolic path is FP64 only
+        (_desc(schedule=3), L.NPDM, full),        # unknown schedule
+        (_desc(schedule=-1), L.NPDM, full),
+        (_desc(reserved=1), L.NPDM, full),
     ]
     for d, m, diag in cases:
         code = lib.band_solve(ct.byref(d), m, None, diag, 8, 8, None, 8, 1 << 30, None)

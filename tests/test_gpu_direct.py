@@ -30,9 +30,9 @@ def band():
     return band
 
 
-def _solve(band, T, method, k):
+def _solve(band, T, method, k, schedule="auto"):
     a, e = (T["a"], T["e"]) if k == 2 else (None, None)
-    x, st = band.solve(a, T["b"], T["c"], T["d"], e, T["f"], method=method)
+    x, st = band.solve(a, T["b"], T["c"], T["d"], e, T["f"], method=method, schedule=schedule)
     torch.cuda.synchronize()
     return x, st.cpu().numpy()
 
@@ -162,7 +162,8 @@ def test_factor_then_solve(band):
     fac, st = band.factor(T["a"], T["b"], T["c"], T["d"], T["e"])
     x1, st1 = band.solve(T["a"], T["b"], T["c"], T["d"], T["e"], T["f"], method="npdm",
                          factors=fac)
-    x2, st2 = band.solve(T["a"], T["b"], T["c"], T["d"], T["e"], T["f"], method="npdm")
+    x2, st2 = band.solve(T["a"], T["b"], T["c"], T["d"], T["e"], T["f"], method="npdm",
+                         schedule="thread")
     torch.cuda.synchronize()
     assert (st.cpu() == 0).all() and (st1.cpu() == 0).all()
     assert torch.equal(x1, x2)                   # same operations in the same order
@@ -186,17 +187,26 @@ def test_x_may_alias_f(band):
 @pytest.mark.parametrize("r", synth.ADI_R)
 @pytest.mark.parametrize("sweep", ["x", "y"])
 def test_adi_sweeps_subset(band, r, sweep):
-    """The ADI workload on 64 lines of each sweep: PD non-dominant (1e-10), TD (1e-12)."""
+    """The ADI workload on 64 lines of each sweep: PD non-dominant (1e-10), TD (1e-12).
+    One thread per system follows the oracle's order of operations; the two-sided
+    schedule is held to the same bound against GEPP, widened to 10x the oracle's own
+    distance from GEPP where the system's conditioning makes that larger."""
     for k, tol in ((2, 1e-10), (1, 1e-12)):
         B = synth.cfg1(r=r, k=k, sweep=sweep, grid=2048, nsys=64)
         T = to_dev(B)
         args = (B["n"], B["nsys"], B["sys_stride"], B["elem_stride"])
         xo, so, _, _ = _oracle(B, k)
+        xt, _, _, _ = _oracle(B, k, "gepp")
+        err_o = per_system_rel(xo, xt, *args)
         assert (so == 0).all()
         for method in (("npdm", "spdm") if k == 2 else ("ntdm", "stdm")):
-            x, st = _solve(band, T, method, k)
+            x, st = _solve(band, T, method, k, schedule="thread")
             assert (st == 0).all()
             assert per_system_rel(flat_of(x), xo, *args).max() <= tol, (method, k)
+        x, st = _solve(band, T, "npdm" if k == 2 else "ntdm", k, schedule="two_sided")
+        assert (st == 0).all()
+        err = per_system_rel(flat_of(x), xt, *args)
+        assert (err <= np.maximum(tol, 10 * err_o)).all(), (k, err.max(), err_o.max())
 
 
 @pytest.mark.parametrize("sweep", ["x", "y"])
@@ -211,5 +221,8 @@ def test_adi_full_grid_sampled(band, sweep):
     for s in rng.choice(B["nsys"], 24, replace=False):
         S = synth.system(B, int(s))
         xo, so = oracle.npdm(*(S[q] for q in "abcdef"))
+        xt, _, _, _ = oracle.batch("gepp", 2, [S[q] for q in "abcde"], S["f"], 1, B["n"], 1, 1)
         idx = int(s) * B["sys_stride"] + np.arange(B["n"]) * B["elem_stride"]
-        assert np.abs(xg[idx] - xo).max() / np.abs(xo).max() <= 1e-10
+        scale = np.abs(xt).max()
+        err_o = np.abs(xo - xt).max() / scale
+        assert np.abs(xg[idx] - xt).max() / scale <= max(1e-10, 10 * err_o)
