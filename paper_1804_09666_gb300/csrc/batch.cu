@@ -43,6 +43,7 @@ struct BatchTable {
 struct TailTable {
   int32_t count;
   int32_t pad;
+  int64_t smem_rows;     // rows of a system the dynamic shared memory holds
   SipArgs it[BAND_MAX_BATCH];
 };
 
@@ -108,12 +109,13 @@ __global__ void __launch_bounds__(64) k_symbolic_batch(const __grid_constant__ S
 __global__ void __launch_bounds__(kTailThreads) k_sip_tail_batch(const __grid_constant__ TailTable t) {
   __shared__ Aff sh[kTailThreads];
   __shared__ double red[kTailThreads / 32];
+  extern __shared__ double tail_smem[];
   for (int j = 0; j < t.count; ++j) {
     const SipArgs& p = t.it[j];
     const unsigned long long count = *p.tail_count;
     for (unsigned long long it = blockIdx.x; it < count; it += gridDim.x) {
       const int64_t s = p.tail_list[it];
-      sip_tail_block(p, s, p.tail_rn[s], sh, red);
+      sip_tail_block(p, s, p.tail_rn[s], sh, red, tail_smem, t.smem_rows);
     }
   }
 }
@@ -204,7 +206,12 @@ extern "C" band_status band_solve_batch(const band_problem* probs, int32_t count
     int dev = 0, nsm = 0;
     cudaGetDevice(&dev);
     cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev);
-    k_sip_tail_batch<<<(unsigned)(2 * (nsm > 0 ? nsm : 1)), kTailThreads, 0, st>>>(tail);
+    int64_t n_max = 0;
+    for (int j = 0; j < tail.count; ++j) n_max = std::max(n_max, tail.it[j].L.n);
+    const size_t smem = tail_smem_bytes(n_max);
+    tail.smem_rows = tail_smem_rows(smem);
+    if (tail_prepare((const void*)k_sip_tail_batch) != cudaSuccess) return BAND_ERR_CUDA;
+    k_sip_tail_batch<<<(unsigned)(nsm > 0 ? nsm : 1), kTailThreads, smem, st>>>(tail);
     if (cudaGetLastError() != cudaSuccess) return BAND_ERR_CUDA;
   }
   return BAND_OK;

@@ -7,6 +7,10 @@
 // l_ik = a_ik / u_kk and a_ij -= l_ik u_kj for j > k in the pattern of row i.  For
 // this pattern nothing is dropped, so L (unit; l2 = L[i][i-2], l1 = L[i][i-1]) and
 // U (u0 = U[i][i], u1 = U[i][i+1], u2 = U[i][i+2] = e_i) are the exact LU factors.
+#include <mutex>
+#include <utility>
+#include <vector>
+
 #include "api_util.h"
 #include "kernels.h"
 #include "sip_impl.cuh"
@@ -173,24 +177,52 @@ using namespace band;
 
 namespace band {
 
-__global__ void __launch_bounds__(kTailThreads) k_sip_tail(const SipArgs p) {
+__global__ void __launch_bounds__(kTailThreads) k_sip_tail(const SipArgs p, int64_t smem_rows) {
   __shared__ Aff sh[kTailThreads];
   __shared__ double red[kTailThreads / 32];
+  extern __shared__ double tail_smem[];
   const unsigned long long count = *p.tail_count;
   for (unsigned long long it = blockIdx.x; it < count; it += gridDim.x) {
     const int64_t s = p.tail_list[it];
-    sip_tail_block(p, s, p.tail_rn[s], sh, red);
+    sip_tail_block(p, s, p.tail_rn[s], sh, red, tail_smem, smem_rows);
   }
+}
+
+// Dynamic shared memory of a tail launch for systems of at most n_max rows: the whole
+// system when it fits in kTailSmemMax bytes, else the largest copy that fits (smaller
+// systems of a ragged batch still use it).  One block per SM either way.
+size_t tail_smem_bytes(int64_t n_max) {
+  const size_t want = (size_t)n_max * sizeof(double) * kTailSmemArrays;
+  return want < kTailSmemMax ? want : kTailSmemMax;
+}
+
+// Opt a tail kernel in to kTailSmemMax bytes of dynamic shared memory, once per kernel
+// and device (the first call normally comes before any graph capture).
+cudaError_t tail_prepare(const void* kernel) {
+  static std::mutex mu;
+  static std::vector<std::pair<const void*, int>> done;
+  int dev = 0;
+  cudaError_t e = cudaGetDevice(&dev);
+  if (e != cudaSuccess) return e;
+  std::lock_guard<std::mutex> lock(mu);
+  for (const auto& kd : done)
+    if (kd.first == kernel && kd.second == dev) return cudaSuccess;
+  e = cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kTailSmemMax);
+  if (e == cudaSuccess) done.emplace_back(kernel, dev);
+  return e;
 }
 
 cudaError_t launch_sip_tail(const SipArgs& p, int64_t nsys, cudaStream_t st) {
   int dev = 0, nsm = 0;
   cudaGetDevice(&dev);
   cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev);
-  int64_t blocks = 2 * (int64_t)(nsm > 0 ? nsm : 1);
+  int64_t blocks = nsm > 0 ? nsm : 1;
   if (blocks > nsys) blocks = nsys;
   if (blocks < 1) blocks = 1;
-  k_sip_tail<<<(unsigned)blocks, kTailThreads, 0, st>>>(p);
+  const cudaError_t e = tail_prepare((const void*)k_sip_tail);
+  if (e != cudaSuccess) return e;
+  const size_t smem = tail_smem_bytes(p.L.n);
+  k_sip_tail<<<(unsigned)blocks, kTailThreads, smem, st>>>(p, tail_smem_rows(smem));
   return cudaGetLastError();
 }
 

@@ -374,7 +374,7 @@ __device__ inline void sip_literal(const SipArgs& p, int64_t s, void* stage) {
 // chunk then reruns from its true starting state.  The arithmetic is the same as the
 // sequential substitutions up to the order of rounding.
 // ---------------------------------------------------------------------------
-constexpr int kTailThreads = 128;
+constexpr int kTailThreads = 256;
 
 // Affine map of the 2-state (v_{t-1}, v_{t-2}) -> (v_t, v_{t-1}) over a chunk:
 // out = M in + c, M = [[m00, m01], [m10, m11]].
@@ -450,41 +450,66 @@ __device__ inline double block_max(double v, double* red) {
   return r;
 }
 
+// One system as the tail sees it: each array with its own stride (the system's rows in
+// global memory, or a copy of the whole system in shared memory with stride 1).
+struct TailSys {
+  const double *a, *b, *c, *d, *e, *f;
+  int64_t sa;                  // stride of a..f
+  double* x;
+  int64_t sx;
+  const double *ru0, *u1;
+  double* y;
+  int64_t sw;                  // stride of ru0, u1, y
+  int64_t n;
+  __device__ __forceinline__ Row row(int64_t i) const {
+    Row r;
+    const int64_t q = i * sa;
+    r.a = (i >= 2) ? a[q] : 0.0;
+    r.b = (i >= 1) ? b[q] : 0.0;
+    r.c = c[q];
+    r.d = (i + 1 < n) ? d[q] : 0.0;
+    r.e = (i + 2 < n) ? e[q] : 0.0;
+    r.f = f[q];
+    return r;
+  }
+};
+
 // ILU(0) entries l2_i, l1_i, u0_i of row i recomputed from A and the stored 1/u0, u1 of
 // rows i-1, i-2: the same operations in the same order as the first sweep, so the
 // values are bitwise those of the sequential factorisation.
 struct IluRow {
   double l2, l1, u0;
 };
-__device__ __forceinline__ IluRow ilu_row(const SipArgs& p, int64_t q0, int64_t es, int64_t w0,
-                                          int64_t ws, int64_t n, int64_t i) {
-  const Row A = load_row(p, q0 + i * es, i, n);
+__device__ __forceinline__ IluRow ilu_row(const TailSys& S, int64_t i) {
+  const Row A = S.row(i);
   double l2 = A.a, l1 = A.b, u0 = A.c;
   if (i >= 2) {
-    const int64_t w2 = w0 + (i - 2) * ws;
-    const double e2 = ldro(p.e + q0 + (i - 2) * es);   // i - 2 + 2 < n holds
-    l2 = l2 * p.ru0[w2];
-    l1 = fma(-l2, p.u1[w2], l1);
+    const int64_t w2 = (i - 2) * S.sw;
+    const double e2 = S.e[(i - 2) * S.sa];   // i - 2 + 2 < n holds
+    l2 = l2 * S.ru0[w2];
+    l1 = fma(-l2, S.u1[w2], l1);
     u0 = fma(-l2, e2, u0);
   }
   if (i >= 1) {
-    const int64_t w1 = w0 + (i - 1) * ws;
-    l1 = l1 * p.ru0[w1];
-    u0 = fma(-l1, p.u1[w1], u0);
+    const int64_t w1 = (i - 1) * S.sw;
+    l1 = l1 * S.ru0[w1];
+    u0 = fma(-l1, S.u1[w1], u0);
   }
   return IluRow{l2, l1, u0};
 }
 
-// One system s by the whole block, continuing Algorithm 1 from k = 1 and max|r| = rn.
-__device__ inline void sip_tail_block(const SipArgs& p, int64_t s, double rn, Aff* sh, double* red) {
-  const int64_t n = p.L.rows(s), q0 = p.L.base(s), es = p.L.stride();
-  const int64_t w0 = p.W.base(s), ws = p.W.stride();
+// One system by the whole block, continuing Algorithm 1 from k = 1 and max|r| = rn.
+// Returns (to every thread) k and the final max|r|; thread 0 writes iters, resid and
+// the status.
+__device__ inline void sip_tail_run(const SipArgs& p, int64_t s, const TailSys& S, double rn,
+                                    Aff* sh, double* red) {
+  const int64_t n = S.n;
   const int P = blockDim.x;
   const int64_t m = (n + P - 1) / P;
   const int64_t lo = min(n, (int64_t)threadIdx.x * m), hi = min(n, lo + m);
-  auto X = [&](int64_t i) -> double { return (i >= 0 && i < n) ? p.x[q0 + i * es] : 0.0; };
-  auto F = [&](double* a, int64_t i) -> double { return (i >= 0 && i < n) ? a[w0 + i * ws] : 0.0; };
-  auto U0 = [&](int64_t i) -> double { return (i >= 0 && i < n) ? ilu_row(p, q0, es, w0, ws, n, i).u0 : 0.0; };
+  auto X = [&](int64_t i) -> double { return (i >= 0 && i < n) ? S.x[i * S.sx] : 0.0; };
+  auto U1 = [&](int64_t i) -> double { return (i >= 0 && i < n) ? S.u1[i * S.sw] : 0.0; };
+  auto U0 = [&](int64_t i) -> double { return (i >= 0 && i < n) ? ilu_row(S, i).u0 : 0.0; };
   int k = 1;
   double prev = INFINITY;
   bool nonfinite = !isfinite(rn);
@@ -494,14 +519,14 @@ __device__ inline void sip_tail_block(const SipArgs& p, int64_t s, double rn, Af
     prev = rn;
     // rhs = K x + f with K = LU - A on the own rows (K[i][i+2] = 0)
     for (int64_t i = lo; i < hi; ++i) {
-      const Row A = load_row(p, q0 + i * es, i, n);
-      const IluRow R = ilu_row(p, q0, es, w0, ws, n, i);
+      const Row A = S.row(i);
+      const IluRow R = ilu_row(S, i);
       const double l2 = R.l2, l1 = R.l1, u0 = R.u0;
-      const double u1 = (i + 1 < n) ? F(p.u1, i) : 0.0;
-      const double u0m2 = U0(i - 2), u1m2 = F(p.u1, i - 2), u0m1 = U0(i - 1);
-      const double u1m1 = F(p.u1, i - 1);
-      const double em2 = (i >= 2 && i < n) ? ldro(p.e + q0 + (i - 2) * es) : 0.0;
-      const double em1 = (i >= 1 && i + 1 < n) ? ldro(p.e + q0 + (i - 1) * es) : 0.0;
+      const double u1 = (i + 1 < n) ? U1(i) : 0.0;
+      const double u0m2 = U0(i - 2), u1m2 = U1(i - 2), u0m1 = U0(i - 1);
+      const double u1m1 = U1(i - 1);
+      const double em2 = (i >= 2 && i < n) ? S.e[(i - 2) * S.sa] : 0.0;
+      const double em1 = (i >= 1 && i + 1 < n) ? S.e[(i - 1) * S.sa] : 0.0;
       const double ka = l2 * u0m2 - A.a;
       const double kb = fma(l2, u1m2, l1 * u0m1) - A.b;
       const double kc = fma(l2, em2, fma(l1, u1m1, u0)) - A.c;
@@ -510,36 +535,36 @@ __device__ inline void sip_tail_block(const SipArgs& p, int64_t s, double rn, Af
       rhs = fma(ka, X(i - 2), rhs);
       rhs = fma(kb, X(i - 1), rhs);
       rhs = fma(kd, X(i + 1), rhs);
-      p.y[w0 + i * ws] = rhs;
+      S.y[i * S.sw] = rhs;
     }
     __syncthreads();
     // L y = rhs (unit lower: y_i = rhs_i - l1_i y_{i-1} - l2_i y_{i-2})
     block_recurrence2(
         n, +1,
         [&](int64_t i, double& r, double& c1, double& c2) {
-          const IluRow R = ilu_row(p, q0, es, w0, ws, n, i);
-          r = p.y[w0 + i * ws];
+          const IluRow R = ilu_row(S, i);
+          r = S.y[i * S.sw];
           c1 = i >= 1 ? R.l1 : 0.0;
           c2 = i >= 2 ? R.l2 : 0.0;
         },
-        [&](int64_t i, double v) { p.y[w0 + i * ws] = v; }, sh);
+        [&](int64_t i, double v) { S.y[i * S.sw] = v; }, sh);
     __syncthreads();
     // U x = y: x_i = (y_i - u1_i x_{i+1} - e_i x_{i+2}) / u0_i
     block_recurrence2(
         n, -1,
         [&](int64_t i, double& r, double& c1, double& c2) {
-          const double ru = F(p.ru0, i);
-          r = p.y[w0 + i * ws] * ru;
-          c1 = (i + 1 < n) ? F(p.u1, i) * ru : 0.0;
-          c2 = (i + 2 < n) ? ldro(p.e + q0 + i * es) * ru : 0.0;
+          const double ru = S.ru0[i * S.sw];
+          r = S.y[i * S.sw] * ru;
+          c1 = (i + 1 < n) ? S.u1[i * S.sw] * ru : 0.0;
+          c2 = (i + 2 < n) ? S.e[i * S.sa] * ru : 0.0;
         },
-        [&](int64_t i, double v) { p.x[q0 + i * es] = v; }, sh);
+        [&](int64_t i, double v) { S.x[i * S.sx] = v; }, sh);
     __syncthreads();
     // r = f - A x
     double loc = 0.0;
     bool nan_seen = false;
     for (int64_t i = lo; i < hi; ++i) {
-      const Row A = load_row(p, q0 + i * es, i, n);
+      const Row A = S.row(i);
       double ax = A.c * X(i);
       ax = fma(A.a, X(i - 2), ax);
       ax = fma(A.b, X(i - 1), ax);
@@ -560,6 +585,63 @@ __device__ inline void sip_tail_block(const SipArgs& p, int64_t s, double rn, Af
                nonfinite ? BAND_ERR_NONFINITE : (rn < p.tol ? BAND_OK : BAND_ERR_NOT_CONVERGED));
   }
   __syncthreads();
+}
+
+// Shared-memory bytes per row of a system held whole by the tail: a..f, x, 1/u0, u1, y.
+constexpr int kTailSmemArrays = 10;
+
+// System s of p continued by the block.  When the system has at most smem_rows rows, all
+// its arrays are first copied into `smem` (kTailSmemArrays * smem_rows doubles), the
+// updates run there and x is copied back; otherwise they run on global memory.  Same
+// operations in the same order either way.
+__device__ inline void sip_tail_block(const SipArgs& p, int64_t s, double rn, Aff* sh, double* red,
+                                      double* smem, int64_t smem_rows) {
+  const int64_t n = p.L.rows(s), q0 = p.L.base(s), es = p.L.stride();
+  const int64_t w0 = p.W.base(s), ws = p.W.stride();
+  if (n <= smem_rows) {
+    double* sa = smem;
+    double* sb = sa + n;
+    double* sc = sb + n;
+    double* sd = sc + n;
+    double* se = sd + n;
+    double* sf = se + n;
+    double* sx = sf + n;
+    double* sr = sx + n;
+    double* su = sr + n;
+    double* sy = su + n;
+    for (int64_t i = threadIdx.x; i < n; i += blockDim.x) {
+      const int64_t q = q0 + i * es, w = w0 + i * ws;
+      sa[i] = ldro(p.a + q);
+      sb[i] = ldro(p.b + q);
+      sc[i] = ldro(p.c + q);
+      sd[i] = ldro(p.d + q);
+      se[i] = ldro(p.e + q);
+      sf[i] = p.f[q];
+      sx[i] = p.x[q];
+      sr[i] = p.ru0[w];
+      su[i] = p.u1[w];
+    }
+    __syncthreads();
+    const TailSys S{sa, sb, sc, sd, se, sf, 1, sx, 1, sr, su, sy, 1, n};
+    sip_tail_run(p, s, S, rn, sh, red);
+    for (int64_t i = threadIdx.x; i < n; i += blockDim.x) p.x[q0 + i * es] = sx[i];
+    __syncthreads();
+  } else {
+    const TailSys S{p.a + q0, p.b + q0, p.c + q0, p.d + q0, p.e + q0, p.f + q0, es,
+                    p.x + q0, es, p.ru0 + w0, p.u1 + w0, p.y + w0, ws, n};
+    sip_tail_run(p, s, S, rn, sh, red);
+  }
+}
+
+// Largest dynamic shared memory of a tail block: 200 KiB (2560 rows), next to the
+// block's static scan buffers, within the 227 KiB an sm_103a block may opt in to.
+constexpr size_t kTailSmemMax = (size_t)200 << 10;
+size_t tail_smem_bytes(int64_t n_max);
+cudaError_t tail_prepare(const void* kernel);
+
+// Rows a tail block can hold in shared memory (dynamic bytes `bytes`).
+__host__ __device__ inline int64_t tail_smem_rows(size_t bytes) {
+  return (int64_t)(bytes / (sizeof(double) * kTailSmemArrays));
 }
 
 struct SipArgs;
