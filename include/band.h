@@ -148,8 +148,15 @@ band_status band_factor(const band_desc* desc, int32_t method, const void* const
  * x += U~^{-1} L~^{-1} (f - A x).  Stops per system when max|f - A x| < tol or after
  * max_it updates; with width == 0 also when an update from the second on does not
  * lower max|f - A x| (exact ILU(0) factors leave K = LU - A at the rounding level, so
- * the residual has reached its floor; status NOT_CONVERGED).  iters (int32[nsys]) and resid (double[nsys], max |f - A x|) may be
- * NULL. */
+ * the residual has reached its floor; status NOT_CONVERGED).  iters (int32[nsys]) and
+ * resid (double[nsys], max |f - A x|) may be NULL.  x must not alias f.
+ * desc->schedule (band_schedule) applies to width == 0: on BAND_SCHED_TWO_SIDED (and
+ * AUTO for n >= 32, non-ragged) the first update x^1 = (LU)^{-1} f runs with two
+ * threads per system, the lower half of the exact ILU(0) = LU factorisation taken
+ * bottom-up (equal in exact arithmetic; the residual and the stop test are
+ * Algorithm 1's); later updates use the top-down factors, rebuilt for the lower half.
+ * As for the direct sweeps, a system whose top-down order meets a zero pivot only in
+ * its lower half may then be solved in one update (status OK). */
 band_status band_sip(const band_desc* desc, const void* const diag[5], const void* f, void* x,
                      double tol, int32_t max_it, int32_t width, int32_t hb_max_it, double hb_tol,
                      int32_t* iters, double* resid, int32_t* sys_status, void* ws, size_t ws_bytes,
@@ -162,7 +169,8 @@ band_status band_sip(const band_desc* desc, const void* const diag[5], const voi
  * op = BAND_OP_SOLVE: method as for band_solve (fused, no stored factors; STDM/SPDM
  *   systems with a zero pivot go through one batched symbolic fix-up launch).
  * op = BAND_OP_SIP: Algorithm 1 with exact substitutions (width 0) on FP64 PD
- *   systems, with tol and max_it as for band_sip; iters / resid may be NULL.
+ *   systems, with tol and max_it as for band_sip; iters / resid may be NULL.  One
+ *   thread per system whatever desc->schedule says.
  * Each problem brings its own workspace of band_workspace_size(desc, op, method, 0)
  * bytes.  Argument checks as for the single calls; the first failing problem's code
  * is returned and nothing is launched. */

@@ -145,11 +145,16 @@ def solve_ragged(a, b, c, d, e, f, offsets, hbw, n_max, total_rows, method="auto
     return x, status
 
 
-def sip(a, b, c, d, e, f, tol=1e-10, max_it=200, width=5, hb_max_it=30, hb_tol=1e-12, x=None):
-    """SIP / Stone method (FP64).  Returns (x, iters, resid, status)."""
+def sip(a, b, c, d, e, f, tol=1e-10, max_it=200, width=5, hb_max_it=30, hb_tol=1e-12, x=None,
+        schedule="auto"):
+    """SIP / Stone method (FP64).  Returns (x, iters, resid, status).
+
+    schedule applies to width 0 (Algorithm 1 with exact substitutions): "two_sided" runs
+    the first update with two threads per system, "thread" with one, "auto" picks.
+    """
     lib = L.load()
     _check_same(c, a, b, d, e, f)
-    desc = desc_for(c, 2)
+    desc = desc_for(c, 2, schedule)
     if x is None:
         x = torch.empty_strided(c.shape, c.stride(), dtype=c.dtype, device=c.device)
     nsys = c.shape[1]
@@ -213,7 +218,8 @@ class BatchPlan:
       a, b, c, d, e, f   (n, nsys) tensors with equal strides (a, e None for TD)
       x       optional output tensor
       tol, max_it        for "sip"
-      schedule           for "solve": "auto" (default), "thread", "two_sided"
+      schedule           "auto" (default), "thread", "two_sided" (for "sip": the first
+                         update of Algorithm 1)
     Outputs, statuses and workspaces are allocated once here; ``run()`` only launches,
     so a run can be captured in a CUDA graph.  results[i] holds x, status (and iters,
     resid for "sip").

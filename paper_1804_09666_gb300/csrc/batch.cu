@@ -36,7 +36,7 @@ struct BatchItem {
 struct BatchTable {
   int32_t count;
   int32_t stage_bytes;   // staging ring bytes per warp (0: none)
-  int64_t total;     // warps
+  int64_t total;     // warp tasks
   BatchItem it[BAND_MAX_BATCH];
 };
 
@@ -68,16 +68,21 @@ __device__ __forceinline__ void run_direct(const DirectArgs<T>& p, int kmode, in
   else direct_one<T, 2>(p, s, stage);
 }
 
+// One warp task: 32 systems of one problem (16 on the two-sided schedule).  Blocks are
+// handed out by the hardware scheduler as earlier ones finish, in task order, and the
+// host orders the problems heaviest first.  (A persistent loop over a task counter was
+// tried: keeping every task variant's state live across the loop doubled the kernel's
+// registers, 126 -> 255, and halved the resident warps.)
 __global__ void __launch_bounds__(128) k_batch(const __grid_constant__ BatchTable t) {
   extern __shared__ __align__(16) unsigned char stage_mem[];
   void* stage = t.stage_bytes ? stage_mem + (threadIdx.x >> 5) * t.stage_bytes : nullptr;
-  const int64_t warp = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
-  if (warp >= t.total) return;
+  const int64_t task = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+  if (task >= t.total) return;
   int j = 0;
-  while (j + 1 < t.count && t.it[j + 1].task0 <= warp) ++j;
+  while (j + 1 < t.count && t.it[j + 1].task0 <= task) ++j;
   const BatchItem& b = t.it[j];
   if (b.two_sided) {         // 16 systems per warp
-    const int64_t s2 = (warp - b.task0) * 16 + (threadIdx.x & 15);
+    const int64_t s2 = (task - b.task0) * 16 + (threadIdx.x & 15);
     if (b.kind == kDirect64) {
       if (b.kmode == 1) twisted_one<double, 1>(b.u.d64, s2, s2 < b.u.d64.L.nsys, stage);
       else twisted_one<double, 2>(b.u.d64, s2, s2 < b.u.d64.L.nsys, stage);
@@ -87,7 +92,7 @@ __global__ void __launch_bounds__(128) k_batch(const __grid_constant__ BatchTabl
     }
     return;
   }
-  const int64_t s = (warp - b.task0) * kWarp + (threadIdx.x & (kWarp - 1));
+  const int64_t s = (task - b.task0) * kWarp + (threadIdx.x & (kWarp - 1));
   if (b.kind == kDirect64) run_direct<double>(b.u.d64, b.kmode, s, stage);
   else if (b.kind == kDirect32) run_direct<float>(b.u.d32, b.kmode, s, stage);
   else if (s < b.u.sip.L.nsys) sip_literal(b.u.sip, s, nullptr);
@@ -125,8 +130,35 @@ __global__ void __launch_bounds__(kTailThreads) k_sip_tail_batch(const __grid_co
 
 using namespace band;
 
-extern "C" band_status band_solve_batch(const band_problem* probs, int32_t count, void* stream) {
-  if (count < 0 || count > BAND_MAX_BATCH || (count > 0 && !probs)) return BAND_ERR_ARG;
+// Relative cost of one warp task of a problem: rows on its longest dependent chain times
+// the work per row (SIP's first update and residual ~2.5x a PD sweep, TD ~0.6x, FP32
+// ~0.5x).  Tasks are handed out heaviest problem first.
+static double task_cost(const band_problem& q) {
+  const band_desc* d = q.desc;
+  double rows = (double)d->n;
+  double w = 1.0;
+  if (q.op == BAND_OP_SIP) {
+    w = 2.5;
+  } else {
+    const bool td = d->hbw == nullptr && d->half_bw == 1;
+    w = td ? 0.6 : 1.0;
+    if (d->dtype == BAND_F32) w *= 0.5;
+  }
+  return rows * w;
+}
+
+extern "C" band_status band_solve_batch(const band_problem* in, int32_t count, void* stream) {
+  if (count < 0 || count > BAND_MAX_BATCH || (count > 0 && !in)) return BAND_ERR_ARG;
+  for (int32_t i = 0; i < count; ++i)
+    if (!in[i].desc || !desc_ok(in[i].desc)) return BAND_ERR_ARG;
+  // heaviest problems first (a stable order; results do not depend on it)
+  int32_t order[BAND_MAX_BATCH];
+  for (int32_t i = 0; i < count; ++i) order[i] = i;
+  std::stable_sort(order, order + count, [&](int32_t x, int32_t y) {
+    return task_cost(in[x]) > task_cost(in[y]);
+  });
+  band_problem probs[BAND_MAX_BATCH];
+  for (int32_t i = 0; i < count; ++i) probs[i] = in[order[i]];
   static_assert(sizeof(BatchTable) < 32000, "kernel parameter table too large");
   static_assert(sizeof(TailTable) < 32000, "kernel parameter table too large");
   BatchTable t;
@@ -140,7 +172,6 @@ extern "C" band_status band_solve_batch(const band_problem* probs, int32_t count
   int64_t warps = 0, slots = 0;
   for (int32_t i = 0; i < count; ++i) {
     const band_problem& q = probs[i];
-    if (!q.desc || !desc_ok(q.desc)) return BAND_ERR_ARG;
     if (q.desc->nsys == 0) {
       if (q.op != BAND_OP_SOLVE && q.op != BAND_OP_SIP) return BAND_ERR_ARG;
       continue;
@@ -174,6 +205,9 @@ extern "C" band_status band_solve_batch(const band_problem* probs, int32_t count
       const band_status v = make_sip(q.desc, q.diag, q.f, q.x, q.tol, q.max_it, 0, q.iters,
                                      q.resid, q.sys_status, q.ws, q.ws_bytes, &sa, nullptr);
       if (v != BAND_OK) return v;
+      // SIP runs one thread per system here: the two-sided first update needs more
+      // registers than the other tasks of this kernel, and would cost them occupancy
+      sa.two_sided = 0;
       b.kind = kSip;
       b.kmode = 2;
       b.two_sided = 0;
@@ -194,9 +228,8 @@ extern "C" band_status band_solve_batch(const band_problem* probs, int32_t count
   for (int i = 0; i < ncounters; ++i)
     if (cudaMemsetAsync(counters[i], 0, sizeof(unsigned long long), st) != cudaSuccess)
       return BAND_ERR_CUDA;
-  const int64_t threads = warps * kWarp;
-  k_batch<<<(unsigned)((threads + 127) / 128), 128,
-            (size_t)kStageWarpsPerBlock * (size_t)t.stage_bytes, st>>>(t);
+  const size_t smem = (size_t)kStageWarpsPerBlock * (size_t)t.stage_bytes;
+  k_batch<<<(unsigned)((warps + 3) / 4), 128, smem, st>>>(t);
   if (cudaGetLastError() != cudaSuccess) return BAND_ERR_CUDA;
   if (sym.count > 0 && slots > 0) {
     k_symbolic_batch<<<(unsigned)((slots + 63) / 64), 64, 0, st>>>(sym);

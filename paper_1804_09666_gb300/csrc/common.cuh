@@ -94,6 +94,46 @@ __device__ __forceinline__ void set_status(int32_t* st, int64_t s, int32_t v) {
   if (st) st[s] = v;
 }
 
+// Gaussian elimination with partial pivoting on an NU x NU system (augmented column
+// NU), fully unrolled: row exchanges are selects, so M stays in registers.
+template <typename T, int NU>
+__device__ __forceinline__ bool solve_small(T (&M)[4][5]) {
+#pragma unroll
+  for (int c = 0; c < NU; ++c) {
+    int piv = c;
+    T big = fabs(M[c][c]);
+#pragma unroll
+    for (int r = c + 1; r < NU; ++r)
+      if (fabs(M[r][c]) > big) { big = fabs(M[r][c]); piv = r; }
+#pragma unroll
+    for (int r = c + 1; r < NU; ++r) {
+      const bool sw = (r == piv);
+#pragma unroll
+      for (int k = c; k <= NU; ++k) {
+        const T u = M[c][k], v = M[r][k];
+        M[c][k] = sw ? v : u;
+        M[r][k] = sw ? u : v;
+      }
+    }
+    if (is_zero(M[c][c])) return false;
+    const T inv = T(1) / M[c][c];
+#pragma unroll
+    for (int r = c + 1; r < NU; ++r) {
+      const T l = M[r][c] * inv;
+#pragma unroll
+      for (int k = c; k <= NU; ++k) M[r][k] = fma(-l, M[c][k], M[r][k]);
+    }
+  }
+#pragma unroll
+  for (int c = NU - 1; c >= 0; --c) {
+    T v = M[c][NU];
+#pragma unroll
+    for (int k = c + 1; k < NU; ++k) v = fma(-M[c][k], M[k][NU], v);
+    M[c][NU] = v / M[c][c];
+  }
+  return true;
+}
+
 // ------------------------------------------------------------- async staging
 // Each lane copies its own element of a row into shared memory with cp.async (LDGSTS)
 // and later waits for the copy group of that row: rows are fetched kStage rows ahead

@@ -119,6 +119,14 @@ __global__ void __launch_bounds__(64) k_hb(const HbArgs p) {
   if (st == BAND_ERR_NONFINITE) set_status(p.status, s, st);
 }
 
+// Algorithm 1 with exact substitutions, first update on the two-sided schedule: 16
+// systems per warp (lanes l, l ^ 16).
+__global__ void __launch_bounds__(128) k_sip_two(const SipArgs p) {
+  const int64_t warp = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+  const int64_t s = warp * 16 + (threadIdx.x & 15);
+  sip_two_sided(p, s, s < p.L.nsys);
+}
+
 __global__ void __launch_bounds__(128) k_ilu0(const SipArgs p) {
   const int64_t s = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   if (s >= p.L.nsys) return;
@@ -259,6 +267,8 @@ band_status make_sip(const band_desc* desc, const void* const diag[5], const voi
     sa->tail_count = w.tail_count;
     sa->tail_list = w.tail_list;
     sa->tail_rn = w.tail_rn;
+    // Algorithm 1's first update may run on the two-sided schedule (band_schedule)
+    sa->two_sided = choose_two_sided(desc, false) ? 1 : 0;
   }
   if (wout) *wout = w;
   return BAND_OK;
@@ -314,7 +324,12 @@ extern "C" band_status band_sip(const band_desc* desc, const void* const diag[5]
   if (width == 0 && cudaMemsetAsync(sa.tail_count, 0, sizeof(unsigned long long), st) !=
                         cudaSuccess)
     return BAND_ERR_CUDA;
-  k_sip<<<g128, 128, 0, st>>>(sa);
+  if (sa.two_sided) {
+    const int64_t threads = (desc->nsys + 15) / 16 * 32;
+    k_sip_two<<<(unsigned)((threads + 127) / 128), 128, 0, st>>>(sa);
+  } else {
+    k_sip<<<g128, 128, 0, st>>>(sa);
+  }
   if (cudaGetLastError() != cudaSuccess) return BAND_ERR_CUDA;
   if (width == 0) return cuda_status(launch_sip_tail(sa, desc->nsys, st));
   return BAND_OK;

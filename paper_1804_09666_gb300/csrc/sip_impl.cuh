@@ -48,6 +48,9 @@ struct SipArgs {
   unsigned long long* tail_count;
   int64_t* tail_list;
   double* tail_rn;     // per system (indexed by s): max|r| after the first update
+  // the first update ran on the two-sided schedule (sip_two_sided): rows (n+1)/2 .. n-1
+  // of ru0, u1 hold the mirrored factors and the tail rebuilds them first
+  int32_t two_sided;
 };
 
 struct Row {
@@ -365,6 +368,202 @@ __device__ inline void sip_literal(const SipArgs& p, int64_t s, void* stage) {
 }
 
 // ---------------------------------------------------------------------------
+// Algorithm 1's first update on the two-sided schedule (lanes l and l ^ 16 of a warp
+// share system s).  x^1 = (LU)^{-1} f with the exact ILU(0) = LU factors: the top lane
+// runs sip_literal's forward sweep (ILU(0) row by row with L y = f) on rows 0 .. m-1,
+// the bottom lane the same sweep on the reversed system (rows n-1 .. m, diagonals
+// (a, b, c, d, e) read as (e, d, c, b, a)), i.e. the UL factorisation of that block.
+// Their last two rows, normalised (x_i + alpha x_{i+-1} + beta x_{i+-2} = z), form the
+// same 4x4 interface system as the two-sided direct sweep; then each lane
+// back-substitutes its half and computes the residual of its own rows (the interface
+// unknowns it needs are in its registers).  x^1 equals sip_literal's in exact
+// arithmetic.  A zero pivot in either half, a singular interface system or n < 4 hands
+// the system to the tail kernel from x^0 = 0 (tail_rn = -1), which factors it top-down
+// and runs Algorithm 1 from its first update.  Needs the tail list.
+// ---------------------------------------------------------------------------
+__device__ inline void sip_two_sided(const SipArgs& p, int64_t s, bool active) {
+  const int lane = (int)(threadIdx.x & 31);
+  const bool bottom = lane >= 16;
+  const unsigned full = 0xffffffffu;
+  const int64_t n = active ? p.L.rows(s) : 0;
+  const bool split = n >= 4;
+  const int64_t m = (n + 1) / 2;
+  const int64_t q0 = active ? p.L.base(s) : 0, es = active ? p.L.stride() : 0;
+  const int64_t w0 = active ? p.W.base(s) : 0, ws = active ? p.W.stride() : 0;
+  const int64_t rows = (!active || !split) ? 0 : (bottom ? n - m : m);
+  const int dir = bottom ? -1 : 1;
+  const int64_t first = bottom ? n - 1 : 0;
+  // ---- forward: ILU(0) of this lane's block with L y = f (register prefetch)
+  double ru0_1 = 0, u1_1 = 0, e_1 = 0, ru0_2 = 0, u1_2 = 0, e_2 = 0;
+  double y1 = 0, y2 = 0, rn0 = 0.0;
+  bool zero = false;
+  {
+    auto load = [&](int64_t j) -> Row {            // j-th row of this lane's sweep
+      const int64_t i = first + dir * j;
+      Row r = load_row(p, q0 + i * es, i, n);
+      if (bottom) {                                // reversed system
+        const double ta = r.a, tb = r.b;
+        r.a = r.e; r.b = r.d; r.d = tb; r.e = ta;
+      }
+      return r;
+    };
+    Row r0{}, r1{}, r2{};
+    if (rows > 0) r0 = load(0);
+    if (rows > 1) r1 = load(1);
+    for (int64_t j = 0; j < rows; ++j) {
+      if (j + 2 < rows) r2 = load(j + 2);
+      const int64_t w = w0 + (first + dir * j) * ws;
+      double l2 = r0.a, l1 = r0.b, u0 = r0.c, u1 = r0.d;
+      if (j >= 2) {
+        l2 = l2 * ru0_2;
+        l1 = fma(-l2, u1_2, l1);
+        u0 = fma(-l2, e_2, u0);
+      }
+      if (j >= 1) {
+        l1 = l1 * ru0_1;
+        u0 = fma(-l1, u1_1, u0);
+        u1 = fma(-l1, e_1, u1);
+      }
+      if (is_zero(u0)) { zero = true; break; }
+      const double r = rcp64(u0);
+      const double yv = fma(-l2, y2, fma(-l1, y1, r0.f));
+      p.ru0[w] = r;
+      p.u1[w] = u1;
+      p.y[w] = yv;
+      rn0 = max_abs(rn0, r0.f);          // r^0 = f - A x^0 = f
+      y2 = y1; y1 = yv;
+      ru0_2 = ru0_1; u1_2 = u1_1; e_2 = e_1;
+      ru0_1 = r; u1_1 = u1; e_1 = r0.e;
+      r0 = r1;
+      r1 = r2;
+    }
+  }
+  // ---- exchange (every lane reaches every shuffle)
+  const double o_rn0 = __shfl_xor_sync(full, rn0, 16);
+  const bool o_zero = __shfl_xor_sync(full, (int)zero, 16) != 0;
+  // normalised last two rows: row "1" is the last one eliminated, row "2" the one before
+  const double al1 = u1_1 * ru0_1, be1 = e_1 * ru0_1, z1 = y1 * ru0_1;
+  const double al2 = u1_2 * ru0_2, be2 = e_2 * ru0_2, z2 = y2 * ru0_2;
+  const double o_al1 = __shfl_xor_sync(full, al1, 16), o_al2 = __shfl_xor_sync(full, al2, 16);
+  const double o_be1 = __shfl_xor_sync(full, be1, 16), o_be2 = __shfl_xor_sync(full, be2, 16);
+  const double o_z1 = __shfl_xor_sync(full, z1, 16), o_z2 = __shfl_xor_sync(full, z2, 16);
+  __syncwarp();
+  rn0 = max_abs(rn0, o_rn0);
+  bool fail = split && (zero || o_zero);
+  const bool stop0 = split && !fail && (rn0 < p.tol || p.max_it < 1 || !isfinite(rn0));
+  double xm2 = 0, xm1 = 0, xm0 = 0, xp1 = 0;      // x_{m-2} .. x_{m+1}
+  if (active && split && !fail && !stop0) {
+    const double tal2 = bottom ? o_al2 : al2, tbe2 = bottom ? o_be2 : be2, tz2 = bottom ? o_z2 : z2;
+    const double tal1 = bottom ? o_al1 : al1, tbe1 = bottom ? o_be1 : be1, tz1 = bottom ? o_z1 : z1;
+    const double bal2 = bottom ? al2 : o_al2, bbe2 = bottom ? be2 : o_be2, bz2 = bottom ? z2 : o_z2;
+    const double bal1 = bottom ? al1 : o_al1, bbe1 = bottom ? be1 : o_be1, bz1 = bottom ? z1 : o_z1;
+    double M[4][5];
+    M[0][0] = 1;    M[0][1] = tal2; M[0][2] = tbe2; M[0][3] = 0;    M[0][4] = tz2;
+    M[1][0] = 0;    M[1][1] = 1;    M[1][2] = tal1; M[1][3] = tbe1; M[1][4] = tz1;
+    M[2][0] = bbe1; M[2][1] = bal1; M[2][2] = 1;    M[2][3] = 0;    M[2][4] = bz1;
+    M[3][0] = 0;    M[3][1] = bbe2; M[3][2] = bal2; M[3][3] = 1;    M[3][4] = bz2;
+    if (solve_small<double, 4>(M)) {
+      xm2 = M[0][4]; xm1 = M[1][4]; xm0 = M[2][4]; xp1 = M[3][4];
+    } else {
+      fail = true;         // both lanes hold the same M, so both see this
+    }
+  }
+  // ---- back-substitution of this lane's half with the residual of its own rows.
+  // Walk top: i = m-3 down to -2, bottom: i = m+2 up to n+1 (x_i = 0 outside the matrix),
+  // with x_{m-2} .. x_{m+1} known; the residual of row jr = i + 2 (top) or i - 2
+  // (bottom) is taken once x_{jr-2} .. x_{jr+2} are known.  n1 .. n4 hold the previous
+  // four x's in walk order.
+  double rn = 0.0;
+  if (active && split && !fail && !stop0) {
+    double n1, n2, n3, n4;
+    if (!bottom) { n1 = xm2; n2 = xm1; n3 = xm0; n4 = xp1; }
+    else { n1 = xp1; n2 = xm0; n3 = xm1; n4 = xm2; }
+    const int64_t start = bottom ? m + 2 : m - 3;
+    const int64_t steps = bottom ? n - m : m;
+    const int bdir = bottom ? 1 : -1;
+    const double* pe = bottom ? p.a : p.e;    // coefficient of x_{i+-2}: e_i, or a_i reversed
+    constexpr int kBack = 4;
+    for (int64_t k0 = 0; k0 < steps; k0 += kBack) {
+      double yv[kBack], uv[kBack], rv[kBack], ev[kBack];
+      Row Av[kBack];
+#pragma unroll
+      for (int j = 0; j < kBack; ++j) {
+        const int64_t i = start + bdir * (k0 + j);
+        const int64_t jr = i - 2 * bdir;
+        yv[j] = uv[j] = rv[j] = ev[j] = 0.0;
+        Av[j] = Row{0, 0, 0, 0, 0, 0};
+        if (k0 + j < steps) {
+          if (i >= 0 && i < n) {
+            const int64_t q = q0 + i * es, w = w0 + i * ws;
+            const bool has_e = bottom ? (i >= 2) : (i + 2 < n);
+            ev[j] = has_e ? ldro(pe + q) : 0.0;
+            yv[j] = p.y[w];
+            uv[j] = p.u1[w];
+            rv[j] = p.ru0[w];
+          }
+          Av[j] = load_row(p, q0 + jr * es, jr, n);
+        }
+      }
+#pragma unroll
+      for (int j = 0; j < kBack; ++j) {
+        if (k0 + j >= steps) break;
+        const int64_t i = start + bdir * (k0 + j);
+        double xi = 0.0;
+        if (i >= 0 && i < n) {
+          xi = fma(-ev[j], n2, fma(-uv[j], n1, yv[j])) * rv[j];
+          p.x[q0 + i * es] = xi;
+        }
+        // row jr's x_{jr-2} .. x_{jr+2} in the original orientation
+        const double xa = bottom ? n4 : xi, xb = bottom ? n3 : n1, xc = n2;
+        const double xd = bottom ? n1 : n3, xe = bottom ? xi : n4;
+        const Row& A = Av[j];
+        double ax = A.c * xc;
+        ax = fma(A.a, xa, ax);
+        ax = fma(A.b, xb, ax);
+        ax = fma(A.d, xd, ax);
+        ax = fma(A.e, xe, ax);
+        rn = max_abs(rn, A.f - ax);
+        n4 = n3; n3 = n2; n2 = n1; n1 = xi;
+      }
+    }
+    if (!bottom) {
+      p.x[q0 + (m - 2) * es] = xm2;
+      p.x[q0 + (m - 1) * es] = xm1;
+    } else {
+      p.x[q0 + m * es] = xm0;
+      p.x[q0 + (m + 1) * es] = xp1;
+    }
+  }
+  rn = max_abs(rn, __shfl_xor_sync(full, rn, 16));
+  if (!active || bottom) return;
+  if (!split || fail) {          // the tail kernel starts this system from x^0 = 0
+    const unsigned long long k = atomicAdd(p.tail_count, 1ull);
+    p.tail_list[k] = s;
+    p.tail_rn[s] = -1.0;
+    return;
+  }
+  if (stop0) {                   // no update: x = x^0 = 0
+    for (int64_t i = 0; i < n; ++i) p.x[q0 + i * es] = 0.0;
+    if (p.iters) p.iters[s] = 0;
+    if (p.resid) p.resid[s] = rn0;
+    set_status(p.status, s,
+               !isfinite(rn0) ? BAND_ERR_NONFINITE : (rn0 < p.tol ? BAND_OK : BAND_ERR_NOT_CONVERGED));
+    return;
+  }
+  if (rn < p.tol || p.max_it <= 1 || !isfinite(rn)) {
+    if (p.iters) p.iters[s] = 1;
+    if (p.resid) p.resid[s] = rn;
+    set_status(p.status, s,
+               !isfinite(rn) ? BAND_ERR_NONFINITE
+                             : (rn < p.tol ? BAND_OK : BAND_ERR_NOT_CONVERGED));
+    return;
+  }
+  const unsigned long long k = atomicAdd(p.tail_count, 1ull);
+  p.tail_list[k] = s;
+  p.tail_rn[s] = rn;
+}
+
+// ---------------------------------------------------------------------------
 // Tail: further Algorithm 1 updates of one system by a whole thread block.  With the
 // ILU(0) factors known every step is either a stencil over rows (K x + f, f - A x) or
 // a second-order linear recurrence (L y = rhs, U x = y), so thread t takes a chunk of
@@ -457,7 +656,7 @@ struct TailSys {
   int64_t sa;                  // stride of a..f
   double* x;
   int64_t sx;
-  const double *ru0, *u1;
+  double *ru0, *u1;
   double* y;
   int64_t sw;                  // stride of ru0, u1, y
   int64_t n;
@@ -498,6 +697,45 @@ __device__ __forceinline__ IluRow ilu_row(const TailSys& S, int64_t i) {
   return IluRow{l2, l1, u0};
 }
 
+// Rows from .. n-1 of the top-down ILU(0) factors (1/u0, u1), continuing from the stored
+// rows from-2, from-1: the operations of sip_literal's forward sweep in its order, so the
+// values are bitwise the sequential ones.  One thread.  Returns false on a zero pivot.
+__device__ inline bool ilu_rebuild(const TailSys& S, int64_t from) {
+  const int64_t n = S.n;
+  double ru0_2 = 0, u1_2 = 0, e_2 = 0, ru0_1 = 0, u1_1 = 0, e_1 = 0;
+  if (from >= 2) {
+    ru0_2 = S.ru0[(from - 2) * S.sw];
+    u1_2 = S.u1[(from - 2) * S.sw];
+    e_2 = S.row(from - 2).e;
+  }
+  if (from >= 1) {
+    ru0_1 = S.ru0[(from - 1) * S.sw];
+    u1_1 = S.u1[(from - 1) * S.sw];
+    e_1 = S.row(from - 1).e;
+  }
+  for (int64_t i = from; i < n; ++i) {
+    const Row A = S.row(i);
+    double l2 = A.a, l1 = A.b, u0 = A.c, u1 = A.d;
+    if (i >= 2) {
+      l2 = l2 * ru0_2;
+      l1 = fma(-l2, u1_2, l1);
+      u0 = fma(-l2, e_2, u0);
+    }
+    if (i >= 1) {
+      l1 = l1 * ru0_1;
+      u0 = fma(-l1, u1_1, u0);
+      u1 = fma(-l1, e_1, u1);
+    }
+    if (is_zero(u0)) return false;
+    const double r = rcp64(u0);
+    S.ru0[i * S.sw] = r;
+    S.u1[i * S.sw] = u1;
+    ru0_2 = ru0_1; u1_2 = u1_1; e_2 = e_1;
+    ru0_1 = r; u1_1 = u1; e_1 = A.e;
+  }
+  return true;
+}
+
 // One system by the whole block, continuing Algorithm 1 from k = 1 and max|r| = rn.
 // Returns (to every thread) k and the final max|r|; thread 0 writes iters, resid and
 // the status.
@@ -511,6 +749,37 @@ __device__ inline void sip_tail_run(const SipArgs& p, int64_t s, const TailSys& 
   auto U1 = [&](int64_t i) -> double { return (i >= 0 && i < n) ? S.u1[i * S.sw] : 0.0; };
   auto U0 = [&](int64_t i) -> double { return (i >= 0 && i < n) ? ilu_row(S, i).u0 : 0.0; };
   int k = 1;
+  const bool scratch = rn < 0.0;      // start from x^0 = 0 (no factors stored yet)
+  if (scratch || (p.two_sided && n >= 4)) {
+    // the top-down factors of every row (from scratch) or of the lower half, which the
+    // two-sided first update left mirrored (one thread, sip_literal's operations)
+    __shared__ int ok;
+    if (threadIdx.x == 0) ok = ilu_rebuild(S, scratch ? 0 : (n + 1) / 2) ? 1 : 0;
+    __syncthreads();
+    const bool good = ok != 0;
+    __syncthreads();
+    if (!good) {      // the top-down order meets a zero pivot: as sip_literal reports it
+      if (threadIdx.x == 0) {
+        if (p.iters) p.iters[s] = 0;
+        if (p.resid) p.resid[s] = NAN;
+        set_status(p.status, s, BAND_ERR_ZERO_PIVOT);
+      }
+      __syncthreads();
+      return;
+    }
+  }
+  if (scratch) {      // x^0 = 0, r^0 = f
+    double loc = 0.0;
+    bool nan_seen = false;
+    for (int64_t i = lo; i < hi; ++i) {
+      S.x[i * S.sx] = 0.0;
+      const double fi = S.f[i * S.sa];
+      nan_seen |= (fi != fi);
+      loc = fmax(loc, fabs(fi));
+    }
+    rn = block_max(nan_seen ? INFINITY : loc, red);
+    k = 0;
+  }
   double prev = INFINITY;
   bool nonfinite = !isfinite(rn);
   for (;;) {

@@ -203,46 +203,6 @@ __device__ __noinline__ void direct_redo(const DirectArgs<T>& p, int64_t s) {
 // system with fewer rows is solved by the top lane alone.  For STDM / SPDM, z goes to
 // the workspace (f stays intact) and a system with a zero pivot goes to the fix-up.
 // ---------------------------------------------------------------------------
-// Gaussian elimination with partial pivoting on an NU x NU system (augmented column
-// NU), fully unrolled: row exchanges are selects, so M stays in registers.
-template <typename T, int NU>
-__device__ __forceinline__ bool solve_small(T (&M)[4][5]) {
-#pragma unroll
-  for (int c = 0; c < NU; ++c) {
-    int piv = c;
-    T big = fabs(M[c][c]);
-#pragma unroll
-    for (int r = c + 1; r < NU; ++r)
-      if (fabs(M[r][c]) > big) { big = fabs(M[r][c]); piv = r; }
-#pragma unroll
-    for (int r = c + 1; r < NU; ++r) {
-      const bool sw = (r == piv);
-#pragma unroll
-      for (int k = c; k <= NU; ++k) {
-        const T u = M[c][k], v = M[r][k];
-        M[c][k] = sw ? v : u;
-        M[r][k] = sw ? u : v;
-      }
-    }
-    if (is_zero(M[c][c])) return false;
-    const T inv = T(1) / M[c][c];
-#pragma unroll
-    for (int r = c + 1; r < NU; ++r) {
-      const T l = M[r][c] * inv;
-#pragma unroll
-      for (int k = c; k <= NU; ++k) M[r][k] = fma(-l, M[c][k], M[r][k]);
-    }
-  }
-#pragma unroll
-  for (int c = NU - 1; c >= 0; --c) {
-    T v = M[c][NU];
-#pragma unroll
-    for (int k = c + 1; k < NU; ++k) v = fma(-M[c][k], M[k][NU], v);
-    M[c][NU] = v / M[c][c];
-  }
-  return true;
-}
-
 template <typename T, int K>
 __device__ __forceinline__ void twisted_one(const DirectArgs<T>& p, int64_t s, bool active,
                                             void* stage) {

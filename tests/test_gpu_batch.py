@@ -61,8 +61,9 @@ def _specs(band):
 
 def _single(band, sp):
     if sp.get("op") == "sip":
+        # the batched kernel runs SIP on one thread per system
         x, it, rs, st = band.sip(*(sp[q] for q in "abcdef"), tol=sp["tol"], max_it=sp["max_it"],
-                                 width=0)
+                                 width=0, schedule="thread")
         return dict(x=x, status=st, iters=it, resid=rs)
     x, st = band.solve(*(sp.get(q) for q in "abcdef"), method=sp["method"])
     return dict(x=x, status=st)
