@@ -339,12 +339,44 @@ def run_reference(args, world, rank):
     print(json.dumps(line), flush=True)
 
 
+# Sources that k_batch is compiled from: an ncu traffic figure applies only while they
+# are unchanged since the capture that measured it.
+K_BATCH_SOURCES = ("include/band.h", "paper_1804_09666_gb300/csrc/batch.cu",
+                   "paper_1804_09666_gb300/csrc/api_util.h", "paper_1804_09666_gb300/csrc/kernels.h",
+                   "paper_1804_09666_gb300/csrc/common.cuh", "paper_1804_09666_gb300/csrc/sweeps.cuh",
+                   "paper_1804_09666_gb300/csrc/sip_impl.cuh")
+TRAFFIC_RECORD = os.path.join(ROOT, "profiles", "k_batch_adi2048_dram.md")
+
+
+def sources_sha256(paths=K_BATCH_SOURCES):
+    import hashlib
+    h = hashlib.sha256()
+    for rel in paths:
+        with open(os.path.join(ROOT, rel), "rb") as fh:
+            h.update(fh.read())
+    return h.hexdigest()
+
+
+def recorded_traffic(grid):
+    """DRAM bytes per k_batch launch from the committed ncu summary, or None when the
+    workload differs or the kernel's sources changed since the capture."""
+    import re
+    if grid != GRID or not os.path.exists(TRAFFIC_RECORD):
+        return None
+    text = open(TRAFFIC_RECORD).read()
+    mb = re.search(r"traffic_bytes_per_launch:\s*(\d+)", text)
+    mh = re.search(r"sources_sha256:\s*([0-9a-f]{64})", text)
+    if not mb or not mh or mh.group(1) != sources_sha256():
+        return None
+    return int(mb.group(1))
+
+
 def workload_config(grid, ngpus):
     return {"workload": "ADI %dx%d grid, x- and y-sweep, r in {0.5, 2, 10}; PD rows solved by "
                         "NPDM, SPDM, SIP (ILU(0), Algorithm 1); TD rows by NTDM, STDM" % (grid, grid),
             "systems_per_sweep": grid, "n": grid, "solves_per_step": 30,
             "layouts": "x-sweep contiguous systems, y-sweep interleaved (row stride)",
-            "l2": "inputs larger than L2 (one PD sweep reads 192 MiB)",
+            "l2": "inputs larger than L2 (one PD sweep reads %d MiB)" % (6 * grid * grid * 8 >> 20),
             "parallelism": "replicas: every rank solves its own full set" if ngpus > 1 else "1 GPU"}
 
 
@@ -447,14 +479,15 @@ def main():
                         "step's graph replay, which adds the symbolic fix-up and SIP tail launches",
               "ms_per_launch": avg_ms, "launches": len(per),
               "alg_bytes_per_launch": alg_bytes, "alg_flops_per_launch": alg_flops}
+    traffic = recorded_traffic(args.grid)
     if frac_alu >= frac_hbm:
         roof = dict({"bound": "alu", "achieved": tflops, "peak": fp64_peak_tf, "unit": "TFLOP/s",
-                     "frac": frac_alu, "traffic": None,
+                     "frac": frac_alu, "traffic": traffic,
                      "peak_source": "measured FP64 FMA rate (band_fp64_fma_rate) x 2",
                      "hbm_GBps": gbps, "hbm_frac_of_measured": frac_hbm}, **common)
     else:
         roof = dict({"bound": "hbm", "achieved": gbps, "peak": hbm_peak, "unit": "GB/s",
-                     "frac": frac_hbm, "traffic": None, "peak_source": "MEASURED_PEAKS.json hbm_gbs",
+                     "frac": frac_hbm, "traffic": traffic, "peak_source": "MEASURED_PEAKS.json hbm_gbs",
                      "fp64_TFLOPs": tflops, "alu_frac_of_measured": frac_alu}, **common)
     launches_per_step = D.kernels_per_step()     # plus one counter memset per SIP/symbolic solve
 
