@@ -87,6 +87,13 @@ typedef struct {
   int64_t total_rows;     /* ragged: offsets[nsys] (the host's copy); uniform: ignored */
   int32_t schedule;       /* band_schedule for NTDM/NPDM solves (BAND_SCHED_AUTO = 0) */
   int32_t reserved;       /* 0 */
+  /* Ragged batches only, else NULL: device array of nsys system ids.  The batch is then
+   * the systems ids[0 .. nsys-1] of the packing that offsets (and hbw) describe, and
+   * every per-system output (sys_status, iters, resid) is indexed by the id.  A solve
+   * over a subset (a size bucket, see band_plan_ragged) writes only its systems' rows of
+   * x.  Accepted by band_solve (without factors), band_solve_batch and band_sip with
+   * width 0 (which then needs sys_status); the other calls return BAND_ERR_ARG. */
+  const int64_t* systems;
 } band_desc;
 
 /* How the fused direct sweep (NTDM/NPDM, and the numeric sweep of STDM/SPDM) maps onto
@@ -107,8 +114,10 @@ typedef struct {
  *   system that NPDM's order would fail on in its lower half may be solved (status OK).
  *   Systems with fewer than 4 (PD) / 2 (TD) rows are solved by one thread.  Needs one
  *   half bandwidth for the batch.
- * BAND_SCHED_AUTO: TWO_SIDED for uniform-bandwidth, non-ragged solves with n >= 32 and
- *   (NTDM/NPDM) x not aliasing f; THREAD otherwise. */
+ * BAND_SCHED_AUTO: TWO_SIDED for uniform-bandwidth solves with n >= 32 that are not a
+ *   whole ragged packing (ragged id lists, i.e. size buckets, qualify) and, for
+ *   NTDM/NPDM, whose x does not alias f; THREAD otherwise.  band_autotune replaces the
+ *   rule by measurement. */
 typedef enum { BAND_SCHED_AUTO = 0, BAND_SCHED_THREAD = 1, BAND_SCHED_TWO_SIDED = 2 } band_schedule;
 
 /* Bytes of workspace that the operation `op` needs for `desc` (0 = none).  op is one
@@ -231,6 +240,43 @@ band_status band_adjoint(const band_desc* desc, int32_t method, const void* fact
 #define BAND_STATIC_SCRATCH_BYTES ((size_t)32 << 20)
 band_status band_solve_static(const band_desc* desc, int32_t method, const void* const diag[5],
                               const void* f, void* x, int32_t* sys_status, void* stream);
+
+/* ---------------------------------------------------------------- batch runtime
+ * A ragged batch of thousands of systems of uneven size and mixed bandwidth runs best
+ * as size buckets: systems of one half bandwidth whose sizes lie within a factor of two,
+ * each bucket one problem of a band_solve_batch launch (id list: band_desc.systems).
+ * Host-side planning, no device work. */
+typedef struct {
+  int64_t first;      /* first position of the bucket in `order` */
+  int64_t count;      /* systems in the bucket */
+  int64_t n_max;      /* largest system size in the bucket */
+  int32_t half_bw;    /* 1 (TD) or 2 (PD) */
+  int32_t pad;
+} band_bucket;
+
+/* Sort the nsys systems of a ragged packing by (half bandwidth, floor(log2 n), n
+ * descending) and cut them into buckets of one half bandwidth and one power-of-two
+ * size range.  offsets (nsys + 1 entries) and hbw (nsys entries, or NULL: half_bw for
+ * every system) are HOST arrays.  Writes order[0 .. nsys-1] (system ids, bucket by
+ * bucket) and the buckets; returns their number, or -1 on bad arguments (a size < 1, a
+ * bandwidth other than 1 or 2) or when more than max_buckets would be needed. */
+int32_t band_plan_ragged(const int64_t* offsets, const int8_t* hbw, int32_t half_bw, int64_t nsys,
+                         int64_t* order, band_bucket* buckets, int32_t max_buckets);
+
+/* Autotuner of the thread-per-system / two-sided choice.  For every problem of the list
+ * that may run on either schedule (a fused direct solve of one half bandwidth whose
+ * desc->schedule is BAND_SCHED_AUTO), time it alone as a band_solve_batch launch on each
+ * schedule (one warm-up, then the best of `reps` runs; CUDA events on `stream`) and
+ * write the faster to schedules[i]; other problems get their desc->schedule.  The trial
+ * runs solve the problems (outputs are overwritten).  Decisions are cached for the
+ * process per (dtype, method, half bandwidth, ceil(log2 n), ceil(log2 nsys), layout), so
+ * later calls reuse them without timing.  Synchronises the stream; do not call while it
+ * is being captured.  Returns BAND_ERR_ARG / BAND_ERR_CUDA / the solve's error. */
+band_status band_autotune(const band_problem* probs, int32_t count, int32_t reps,
+                          int32_t* schedules, void* stream);
+
+/* Forget the autotuner's cached decisions (all devices). */
+void band_autotune_reset(void);
 
 /* Diagnostic (the paper has no counterpart): measures this GPU's FP64 fused
  * multiply-add rate in FMA/s with a short register-only kernel on `stream` and waits

@@ -27,7 +27,8 @@ OP_SOLVE, OP_FACTOR, OP_SIP, OP_REFINE, OP_ADJOINT = range(5)
 
 EXPORTS = ("band_workspace_size", "band_solve", "band_factor", "band_sip", "band_refine_solve",
            "band_adjoint", "band_status_str", "band_version", "band_fp64_fma_rate",
-           "band_solve_batch", "band_solve_static")
+           "band_solve_batch", "band_solve_static", "band_plan_ragged", "band_autotune",
+           "band_autotune_reset")
 MAX_BATCH = 64
 
 
@@ -35,12 +36,17 @@ class BandDesc(ct.Structure):
     _fields_ = [("half_bw", ct.c_int32), ("dtype", ct.c_int32), ("nsys", ct.c_int64),
                 ("n", ct.c_int64), ("sys_stride", ct.c_int64), ("elem_stride", ct.c_int64),
                 ("offsets", ct.c_void_p), ("hbw", ct.c_void_p), ("total_rows", ct.c_int64),
-                ("schedule", ct.c_int32), ("reserved", ct.c_int32)]
+                ("schedule", ct.c_int32), ("reserved", ct.c_int32), ("systems", ct.c_void_p)]
 
 
 _lib = None
 P = ct.c_void_p
 DIAG5 = ct.c_void_p * 5
+
+
+class BandBucket(ct.Structure):
+    _fields_ = [("first", ct.c_int64), ("count", ct.c_int64), ("n_max", ct.c_int64),
+                ("half_bw", ct.c_int32), ("pad", ct.c_int32)]
 
 
 class BandProblem(ct.Structure):
@@ -77,6 +83,12 @@ def load(path=None):
     lib.band_solve_batch.restype = ct.c_int
     lib.band_solve_static.argtypes = [D, i32, DIAG5, P, P, P, P]
     lib.band_solve_static.restype = ct.c_int
+    lib.band_plan_ragged.argtypes = [P, P, i32, i64, P, ct.POINTER(BandBucket), i32]
+    lib.band_plan_ragged.restype = i32
+    lib.band_autotune.argtypes = [ct.POINTER(BandProblem), i32, i32, P, P]
+    lib.band_autotune.restype = ct.c_int
+    lib.band_autotune_reset.argtypes = []
+    lib.band_autotune_reset.restype = None
     lib.band_fp64_fma_rate.argtypes = [P, sz, P]
     lib.band_fp64_fma_rate.restype = ct.c_double
     lib.band_version.argtypes = []

@@ -275,6 +275,77 @@ class BatchPlan:
         return self.results
 
 
+class RaggedPlan:
+    """A ragged packing solved as size buckets in one batched launch (band_plan_ragged).
+
+    a, b, c, d, e, f: 1-D device tensors of the packed rows (system s in rows
+    offsets[s] .. offsets[s+1]-1; the a, e rows of TD systems are not read).
+    offsets: host int64 array (nsys + 1); hbw: host int8 array of 1/2 per system, or None
+    with half_bw for all.  method: "numeric" (NTDM/NPDM per bucket) or "symbolic"
+    (STDM/SPDM).  schedule: "auto", "thread", "two_sided", or "tune" (band_autotune
+    measures both schedules per bucket once and keeps the faster).  The buckets'
+    workspaces are allocated here; run() only launches (graph-capturable).  x is packed
+    like f; status holds one entry per system id.
+    """
+
+    def __init__(self, a, b, c, d, e, f, offsets, hbw=None, half_bw=2, method="numeric",
+                 schedule="auto", x=None, status=None, reps=3):
+        import numpy as np
+        lib = L.load()
+        self.lib = lib
+        offs = np.ascontiguousarray(np.asarray(offsets, dtype=np.int64))
+        nsys = len(offs) - 1
+        hb = None if hbw is None else np.ascontiguousarray(np.asarray(hbw, dtype=np.int8))
+        order = np.empty(max(nsys, 1), dtype=np.int64)
+        buckets = (L.BandBucket * L.MAX_BATCH)()
+        nb = lib.band_plan_ragged(offs.ctypes.data, hb.ctypes.data if hb is not None else None,
+                                  half_bw, nsys, order.ctypes.data, buckets, L.MAX_BATCH)
+        if nb < 0:
+            raise ValueError("band_plan_ragged: bad sizes or bandwidths, or more than %d buckets"
+                             % L.MAX_BATCH)
+        dev = f.device
+        self.order = torch.from_numpy(order[:nsys].copy()).to(dev)
+        self.offsets = torch.from_numpy(offs).to(dev)
+        self.buckets = [(bk.first, bk.count, bk.n_max, bk.half_bw) for bk in buckets[:nb]]
+        self.x = x if x is not None else torch.empty_like(f)
+        self.status = status if status is not None else torch.empty(nsys, dtype=torch.int32,
+                                                                    device=dev)
+        sched = "auto" if schedule == "tune" else schedule
+        self.descs, self.keep = [], [a, b, c, d, e, f]
+        self.arr = (L.BandProblem * max(nb, 1))()
+        for i, (first, count, n_max, k) in enumerate(self.buckets):
+            desc = L.BandDesc(half_bw=k, dtype=_dtype_code(f), nsys=count, n=n_max, sys_stride=0,
+                              elem_stride=1, offsets=self.offsets.data_ptr(), hbw=None,
+                              total_rows=int(offs[-1]), schedule=_SCHEDULES[sched],
+                              systems=self.order.data_ptr() + 8 * first)
+            name = ("npdm" if k == 2 else "ntdm") if method == "numeric" else \
+                   ("spdm" if k == 2 else "stdm")
+            m = _METHODS[name]
+            ws = _workspace(lib.band_workspace_size(ct.byref(desc), L.OP_SOLVE, m, 0), dev)
+            P = self.arr[i]
+            P.op, P.method = L.OP_SOLVE, m
+            P.desc = ct.pointer(desc)
+            P.diag = _diag5(a if k == 2 else None, b, c, d, e if k == 2 else None)
+            P.f, P.x, P.sys_status = f.data_ptr(), self.x.data_ptr(), self.status.data_ptr()
+            P.ws, P.ws_bytes = ws.data_ptr(), ws.numel()
+            self.descs.append(desc)
+            self.keep.append(ws)
+        self.count = nb
+        self.schedules = [d.schedule for d in self.descs]
+        if schedule == "tune" and nb > 0:
+            out = (ct.c_int32 * nb)()
+            code = lib.band_autotune(self.arr, nb, reps, out, _stream())
+            L.check(code, "band_autotune")
+            for desc, v in zip(self.descs, out):
+                desc.schedule = v
+            self.schedules = list(out)
+
+    def run(self):
+        code = self.lib.band_solve_batch(self.arr, self.count, _stream())
+        L.check(code, "band_solve_batch")
+        return self.x, self.status
+
+
 def solve_batch(specs):
     """One-shot batched solve; see BatchPlan.  Returns the list of results."""
     return BatchPlan(specs).run()

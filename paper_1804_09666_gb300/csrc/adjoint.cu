@@ -140,7 +140,7 @@ extern "C" band_status band_adjoint(const band_desc* desc, int32_t method, const
                                     const void* const diag[5], const void* x, const void* w,
                                     void* const grad_diag[5], void* grad_f, int32_t* sys_status,
                                     void* ws, size_t ws_bytes, void* stream) {
-  if (!desc_ok(desc) || desc->dtype != BAND_F64) return BAND_ERR_ARG;
+  if (!desc_ok(desc) || desc->dtype != BAND_F64 || desc->systems) return BAND_ERR_ARG;
   const int kmode = kmode_for(desc, method);
   if (kmode < 0 || is_symbolic(method)) return BAND_ERR_ARG;
   if (desc->nsys == 0) return BAND_OK;

@@ -64,7 +64,7 @@ FactorPtrs factor_ptrs(const band_desc* d, const void* factors) {
 bool choose_two_sided(const band_desc* d, bool alias) {
   if (d->schedule == BAND_SCHED_THREAD) return false;
   if (d->schedule == BAND_SCHED_TWO_SIDED) return true;
-  if (d->offsets || alias) return false;        // ragged: thread per system
+  if ((d->offsets && !d->systems) || alias) return false;   // whole ragged packings: thread
   return d->n >= 32;
 }
 
@@ -138,6 +138,7 @@ band_status band_solve(const band_desc* desc, int32_t method, const void* factor
   const int kmode = kmode_for(desc, method);
   if (kmode < 0) return BAND_ERR_ARG;
   if (is_symbolic(method) && (desc->dtype != BAND_F64 || factors)) return BAND_ERR_ARG;
+  if (factors && desc->systems) return BAND_ERR_ARG;
   if (desc->nsys == 0) return BAND_OK;   // nothing to do (empty arrays may be NULL)
   cudaStream_t st = static_cast<cudaStream_t>(stream);
   if (factors) {
@@ -177,7 +178,7 @@ band_status band_solve(const band_desc* desc, int32_t method, const void* factor
 
 band_status band_factor(const band_desc* desc, int32_t method, const void* const diag[5],
                         void* factors, size_t factors_bytes, int32_t* sys_status, void* stream) {
-  if (!desc_ok(desc)) return BAND_ERR_ARG;
+  if (!desc_ok(desc) || desc->systems) return BAND_ERR_ARG;
   const int kmode = kmode_for(desc, method);
   if (kmode < 0 || is_symbolic(method)) return BAND_ERR_ARG;
   if (desc->nsys == 0) return BAND_OK;

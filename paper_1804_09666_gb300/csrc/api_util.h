@@ -27,13 +27,15 @@ inline bool ragged(const band_desc* d) { return d->offsets != nullptr; }
 
 // Rows of one scratch array: interleaved by system for uniform batches (S x n with S
 // = nsys rounded up to a warp), packed like the data for ragged batches.
+// Ragged batches with an id list (a size bucket) keep their scratch interleaved by
+// position in the list, rows up to n (the bucket's largest size).
 inline int64_t spill_rows(const band_desc* d) {
-  return ragged(d) ? d->total_rows : round_up(d->nsys, kWarp) * d->n;
+  return (ragged(d) && !d->systems) ? d->total_rows : round_up(d->nsys, kWarp) * d->n;
 }
 inline Spill spill_of(const band_desc* d) {
   Spill w;
   w.S = round_up(d->nsys, kWarp);
-  w.offsets = d->offsets;
+  w.offsets = d->systems ? nullptr : d->offsets;
   return w;
 }
 inline Layout layout_of(const band_desc* d) {
@@ -44,6 +46,7 @@ inline Layout layout_of(const band_desc* d) {
   L.es = d->elem_stride;
   L.offsets = d->offsets;
   L.hbw = d->hbw;
+  L.ids = d->systems;
   L.half_bw = d->half_bw;
   return L;
 }
@@ -56,6 +59,7 @@ inline bool desc_ok(const band_desc* d) {
   if (!d->hbw && d->half_bw != 1 && d->half_bw != 2) return false;
   if (d->schedule < BAND_SCHED_AUTO || d->schedule > BAND_SCHED_TWO_SIDED || d->reserved != 0)
     return false;
+  if (d->systems && !d->offsets) return false;     // id lists select from a ragged packing
   if (ragged(d)) {
     if (d->total_rows < 0) return false;
   } else {

@@ -60,12 +60,12 @@ struct SymTable {
 };
 
 template <typename T>
-__device__ __forceinline__ void run_direct(const DirectArgs<T>& p, int kmode, int64_t s,
+__device__ __forceinline__ void run_direct(const DirectArgs<T>& p, int kmode, int64_t t,
                                            void* stage) {
-  if (s >= p.L.nsys) return;
-  const int K = kmode ? kmode : p.L.kband(s);
-  if (K == 1) direct_one<T, 1>(p, s, stage);
-  else direct_one<T, 2>(p, s, stage);
+  if (t >= p.L.nsys) return;
+  const int K = kmode ? kmode : p.L.kband(p.L.sys(t));
+  if (K == 1) direct_one<T, 1>(p, t, stage);
+  else direct_one<T, 2>(p, t, stage);
 }
 
 // One warp task: 32 systems of one problem (16 on the two-sided schedule).  Blocks are
@@ -82,13 +82,13 @@ __global__ void __launch_bounds__(128) k_batch(const __grid_constant__ BatchTabl
   while (j + 1 < t.count && t.it[j + 1].task0 <= task) ++j;
   const BatchItem& b = t.it[j];
   if (b.two_sided) {         // 16 systems per warp
-    const int64_t s2 = (task - b.task0) * 16 + (threadIdx.x & 15);
+    const int64_t t2 = (task - b.task0) * 16 + (threadIdx.x & 15);
     if (b.kind == kDirect64) {
-      if (b.kmode == 1) twisted_one<double, 1>(b.u.d64, s2, s2 < b.u.d64.L.nsys, stage);
-      else twisted_one<double, 2>(b.u.d64, s2, s2 < b.u.d64.L.nsys, stage);
+      if (b.kmode == 1) twisted_one<double, 1>(b.u.d64, t2, t2 < b.u.d64.L.nsys, stage);
+      else twisted_one<double, 2>(b.u.d64, t2, t2 < b.u.d64.L.nsys, stage);
     } else {
-      if (b.kmode == 1) twisted_one<float, 1>(b.u.d32, s2, s2 < b.u.d32.L.nsys, stage);
-      else twisted_one<float, 2>(b.u.d32, s2, s2 < b.u.d32.L.nsys, stage);
+      if (b.kmode == 1) twisted_one<float, 1>(b.u.d32, t2, t2 < b.u.d32.L.nsys, stage);
+      else twisted_one<float, 2>(b.u.d32, t2, t2 < b.u.d32.L.nsys, stage);
     }
     return;
   }
@@ -120,7 +120,7 @@ __global__ void __launch_bounds__(kTailThreads) k_sip_tail_batch(const __grid_co
     const unsigned long long count = *p.tail_count;
     for (unsigned long long it = blockIdx.x; it < count; it += gridDim.x) {
       const int64_t s = p.tail_list[it];
-      sip_tail_block(p, s, p.tail_rn[s], sh, red, tail_smem, t.smem_rows);
+      sip_tail_block(p, s, p.tail_rn[it], sh, red, tail_smem, t.smem_rows);
     }
   }
 }

@@ -17,7 +17,10 @@ struct Layout {
   int64_t nsys, n, ss, es;
   const int64_t* offsets;
   const int8_t* hbw;
+  const int64_t* ids;     // ragged subsets: the batch's s-th system is ids[s]
   int32_t half_bw;
+  // id of the batch's s-th system (the index of every per-system array)
+  __device__ __forceinline__ int64_t sys(int64_t s) const { return ids ? ids[s] : s; }
   __device__ __forceinline__ int64_t base(int64_t s) const { return offsets ? offsets[s] : s * ss; }
   __device__ __forceinline__ int64_t rows(int64_t s) const {
     return offsets ? offsets[s + 1] - offsets[s] : n;
@@ -26,9 +29,9 @@ struct Layout {
   __device__ __forceinline__ int kband(int64_t s) const { return hbw ? (int)hbw[s] : half_bw; }
 };
 
-// Scratch rows of one system: interleaved by system (row i of system s at
-// i*S + s, S = nsys rounded up to a warp) for uniform batches, packed like the data
-// for ragged ones.
+// Scratch rows of one system: interleaved (row i of the batch's t-th system at i*S + t,
+// S = nsys rounded up to a warp) for uniform batches and for ragged batches with an id
+// list, packed like the data (offsets[t]) for other ragged batches.
 struct Spill {
   int64_t S;
   const int64_t* offsets;

@@ -26,14 +26,14 @@ namespace band {
 template <typename T, int K>
 __global__ void __launch_bounds__(128) k_direct(const DirectArgs<T> p) {
   extern __shared__ __align__(16) unsigned char stage_mem[];
-  const int64_t s = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-  if (s >= p.L.nsys) return;
+  const int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (t >= p.L.nsys) return;
   void* stage = stage_mem + (threadIdx.x >> 5) * stage_bytes_per_warp<T>();
   if (K == 0) {
-    if (p.L.kband(s) == 1) direct_one<T, 1>(p, s, stage);
-    else direct_one<T, 2>(p, s, stage);
+    if (p.L.kband(p.L.sys(t)) == 1) direct_one<T, 1>(p, t, stage);
+    else direct_one<T, 2>(p, t, stage);
   } else {
-    direct_one<T, K>(p, s, stage);
+    direct_one<T, K>(p, t, stage);
   }
 }
 
@@ -57,8 +57,8 @@ __global__ void __launch_bounds__(128) k_twisted(const DirectArgs<T> p) {
   extern __shared__ __align__(16) unsigned char stage_mem[];
   void* stage = stage_mem + (threadIdx.x >> 5) * stage_bytes_per_warp<T>();
   const int64_t warp = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
-  const int64_t s = warp * 16 + (threadIdx.x & 15);
-  twisted_one<T, K>(p, s, s < p.L.nsys, stage);
+  const int64_t t = warp * 16 + (threadIdx.x & 15);
+  twisted_one<T, K>(p, t, t < p.L.nsys, stage);
 }
 
 template <typename T>

@@ -401,7 +401,7 @@ extern "C" band_status band_refine_solve(const band_desc* desc32, const void* co
                                          const double* f, double* x, double rel_stop,
                                          int32_t max_steps, int32_t* steps, int32_t* sys_status,
                                          void* ws, size_t ws_bytes, void* stream) {
-  if (!desc_ok(desc32) || desc32->dtype != BAND_F32) return BAND_ERR_ARG;
+  if (!desc_ok(desc32) || desc32->dtype != BAND_F32 || desc32->systems) return BAND_ERR_ARG;
   if (max_steps < 0 || !(rel_stop >= 0.0)) return BAND_ERR_ARG;
   if (desc32->nsys == 0) return BAND_OK;
   if (!diag32 || !f || !x) return BAND_ERR_ARG;

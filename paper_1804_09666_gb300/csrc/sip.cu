@@ -123,8 +123,8 @@ __global__ void __launch_bounds__(64) k_hb(const HbArgs p) {
 // systems per warp (lanes l, l ^ 16).
 __global__ void __launch_bounds__(128) k_sip_two(const SipArgs p) {
   const int64_t warp = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
-  const int64_t s = warp * 16 + (threadIdx.x & 15);
-  sip_two_sided(p, s, s < p.L.nsys);
+  const int64_t t = warp * 16 + (threadIdx.x & 15);
+  sip_two_sided(p, t, t < p.L.nsys);
 }
 
 __global__ void __launch_bounds__(128) k_ilu0(const SipArgs p) {
@@ -192,7 +192,7 @@ __global__ void __launch_bounds__(kTailThreads) k_sip_tail(const SipArgs p, int6
   const unsigned long long count = *p.tail_count;
   for (unsigned long long it = blockIdx.x; it < count; it += gridDim.x) {
     const int64_t s = p.tail_list[it];
-    sip_tail_block(p, s, p.tail_rn[s], sh, red, tail_smem, smem_rows);
+    sip_tail_block(p, s, p.tail_rn[it], sh, red, tail_smem, smem_rows);
   }
 }
 
@@ -239,6 +239,8 @@ band_status make_sip(const band_desc* desc, const void* const diag[5], const voi
                      int32_t* sys_status, void* ws, size_t ws_bytes, SipArgs* sa, SipWs* wout) {
   if (!desc_ok(desc) || desc->dtype != BAND_F64) return BAND_ERR_ARG;
   if (width < 0 || width > kMaxWidth || max_it < 0) return BAND_ERR_ARG;
+  // id lists: Algorithm 1 with exact substitutions only, statuses indexed by id
+  if (desc->systems && (width != 0 || !sys_status)) return BAND_ERR_ARG;
   if (!(tol >= 0.0)) return BAND_ERR_ARG;
   // TD systems are treated as PD with a = e = 0; that needs a and e arrays.
   if (!diag || !f || !x || !diag[0] || !diag[1] || !diag[2] || !diag[3] || !diag[4])

@@ -47,7 +47,7 @@ struct SipArgs {
   // block-cooperative kernel (null: finish them in the same thread)
   unsigned long long* tail_count;
   int64_t* tail_list;
-  double* tail_rn;     // per system (indexed by s): max|r| after the first update
+  double* tail_rn;     // per tail-list entry: max|r| after the first update (-1: none yet)
   // the first update ran on the two-sided schedule (sip_two_sided): rows (n+1)/2 .. n-1
   // of ru0, u1 hold the mirrored factors and the tail rebuilds them first
   int32_t two_sided;
@@ -72,9 +72,11 @@ __device__ __forceinline__ Row load_row(const SipArgs& p, int64_t q, int64_t i, 
 // the workspace: rhs = K x + f, L y = rhs, U x = y, r = f - A x, until max|r| < tol,
 // max_it updates, or an update from the second on fails to lower max|r| (the rounding
 // floor of exact ILU(0) factors; NOT_CONVERGED).
-__device__ inline void sip_literal_more(const SipArgs& p, int64_t s, int k, double rn) {
+__device__ inline void sip_literal_more(const SipArgs& p, int64_t t, int k, double rn) {
+  const int64_t s = p.L.sys(t);     // t: position in the batch, s: the system id
+
   const int64_t n = p.L.rows(s), q0 = p.L.base(s), es = p.L.stride();
-  const int64_t w0 = p.W.base(s), ws = p.W.stride();
+  const int64_t w0 = p.W.base(t), ws = p.W.stride();
   double prev = INFINITY;
   for (;;) {
     if (rn < p.tol || k >= p.max_it || !isfinite(rn)) break;
@@ -257,9 +259,11 @@ __device__ inline bool ilu0_into(const SipArgs& p, int64_t s) {
 // is x^1 = U^{-1} L^{-1} f: one forward sweep does ILU(0) and L y = f together (only
 // 1/u0, u1 and y are kept), one backward sweep does U x = y and the residual of every
 // row (two rows behind).  Systems that need more updates rebuild the full factors.
-__device__ inline void sip_literal(const SipArgs& p, int64_t s, void* stage) {
+__device__ inline void sip_literal(const SipArgs& p, int64_t t, void* stage) {
+  const int64_t s = p.L.sys(t);     // t: position in the batch, s: the system id
+
   const int64_t n = p.L.rows(s), q0 = p.L.base(s), es = p.L.stride();
-  const int64_t w0 = p.W.base(s), ws = p.W.stride();
+  const int64_t w0 = p.W.base(t), ws = p.W.stride();
   double ru0_1 = 0, u1_1 = 0, e_1 = 0, ru0_2 = 0, u1_2 = 0, e_2 = 0;
   double y1 = 0, y2 = 0, rn = 0.0;
   Row r0 = load_row(p, q0, 0, n), r1, r2;
@@ -360,11 +364,11 @@ __device__ inline void sip_literal(const SipArgs& p, int64_t s, void* stage) {
   }
   if (p.tail_list) {   // 1/u0 and u1 are stored: hand over to the tail kernel
     const unsigned long long k = atomicAdd(p.tail_count, 1ull);
-    p.tail_list[k] = s;
-    p.tail_rn[s] = rn;
+    p.tail_list[k] = t;
+    p.tail_rn[k] = rn;
     return;
   }
-  sip_literal_more(p, s, 1, rn);
+  sip_literal_more(p, t, 1, rn);
 }
 
 // ---------------------------------------------------------------------------
@@ -381,7 +385,9 @@ __device__ inline void sip_literal(const SipArgs& p, int64_t s, void* stage) {
 // the system to the tail kernel from x^0 = 0 (tail_rn = -1), which factors it top-down
 // and runs Algorithm 1 from its first update.  Needs the tail list.
 // ---------------------------------------------------------------------------
-__device__ inline void sip_two_sided(const SipArgs& p, int64_t s, bool active) {
+__device__ inline void sip_two_sided(const SipArgs& p, int64_t t, bool active) {
+  const int64_t s = active ? p.L.sys(t) : 0;   // t: position in the batch, s: system id
+
   const int lane = (int)(threadIdx.x & 31);
   const bool bottom = lane >= 16;
   const unsigned full = 0xffffffffu;
@@ -389,7 +395,7 @@ __device__ inline void sip_two_sided(const SipArgs& p, int64_t s, bool active) {
   const bool split = n >= 4;
   const int64_t m = (n + 1) / 2;
   const int64_t q0 = active ? p.L.base(s) : 0, es = active ? p.L.stride() : 0;
-  const int64_t w0 = active ? p.W.base(s) : 0, ws = active ? p.W.stride() : 0;
+  const int64_t w0 = active ? p.W.base(t) : 0, ws = active ? p.W.stride() : 0;
   const int64_t rows = (!active || !split) ? 0 : (bottom ? n - m : m);
   const int dir = bottom ? -1 : 1;
   const int64_t first = bottom ? n - 1 : 0;
@@ -538,8 +544,8 @@ __device__ inline void sip_two_sided(const SipArgs& p, int64_t s, bool active) {
   if (!active || bottom) return;
   if (!split || fail) {          // the tail kernel starts this system from x^0 = 0
     const unsigned long long k = atomicAdd(p.tail_count, 1ull);
-    p.tail_list[k] = s;
-    p.tail_rn[s] = -1.0;
+    p.tail_list[k] = t;
+    p.tail_rn[k] = -1.0;
     return;
   }
   if (stop0) {                   // no update: x = x^0 = 0
@@ -559,8 +565,8 @@ __device__ inline void sip_two_sided(const SipArgs& p, int64_t s, bool active) {
     return;
   }
   const unsigned long long k = atomicAdd(p.tail_count, 1ull);
-  p.tail_list[k] = s;
-  p.tail_rn[s] = rn;
+  p.tail_list[k] = t;
+  p.tail_rn[k] = rn;
 }
 
 // ---------------------------------------------------------------------------
@@ -863,10 +869,12 @@ constexpr int kTailSmemArrays = 10;
 // its arrays are first copied into `smem` (kTailSmemArrays * smem_rows doubles), the
 // updates run there and x is copied back; otherwise they run on global memory.  Same
 // operations in the same order either way.
-__device__ inline void sip_tail_block(const SipArgs& p, int64_t s, double rn, Aff* sh, double* red,
+__device__ inline void sip_tail_block(const SipArgs& p, int64_t t, double rn, Aff* sh, double* red,
                                       double* smem, int64_t smem_rows) {
+  const int64_t s = p.L.sys(t);     // t: position in the batch, s: the system id
+
   const int64_t n = p.L.rows(s), q0 = p.L.base(s), es = p.L.stride();
-  const int64_t w0 = p.W.base(s), ws = p.W.stride();
+  const int64_t w0 = p.W.base(t), ws = p.W.stride();
   if (n <= smem_rows) {
     double* sa = smem;
     double* sb = sa + n;

@@ -52,7 +52,7 @@ using namespace band;
 extern "C" band_status band_solve_static(const band_desc* desc, int32_t method,
                                          const void* const diag[5], const void* f, void* x,
                                          int32_t* sys_status, void* stream) {
-  if (!desc_ok(desc)) return BAND_ERR_ARG;
+  if (!desc_ok(desc) || desc->systems) return BAND_ERR_ARG;
   if (method != BAND_NTDM && method != BAND_NPDM && method != BAND_AUTO_NUMERIC)
     return BAND_ERR_ARG;
   const int kmode = kmode_for(desc, method);

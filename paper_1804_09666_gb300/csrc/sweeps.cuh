@@ -76,14 +76,16 @@ __device__ __forceinline__ bool forward_row(const DirectArgs<T>& p, int64_t i, i
 // to x (numeric methods) or to the workspace (symbolic methods, keeping f intact when
 // x aliases f).
 template <typename T, int K>
-__device__ __forceinline__ void direct_one(const DirectArgs<T>& p, int64_t s, void* stage) {
+__device__ __forceinline__ void direct_one(const DirectArgs<T>& p, int64_t t, void* stage) {
+  const int64_t s = p.L.sys(t);     // t: position in the batch, s: the system id
+
   const int64_t n = p.L.rows(s);
   if (n <= 0) {
     set_status(p.status, s, BAND_OK);
     return;
   }
   const int64_t q0 = p.L.base(s), es = p.L.stride();
-  const int64_t w0 = p.W.base(s), wst = p.W.stride();
+  const int64_t w0 = p.W.base(t), wst = p.W.stride();
   T al1 = 0, al2 = 0, be1 = 0, be2 = 0, z1 = 0, z2 = 0;
   bool zero = false;
   // Interleaved systems (consecutive lanes read consecutive addresses) are staged through
@@ -139,7 +141,7 @@ __device__ __forceinline__ void direct_one(const DirectArgs<T>& p, int64_t s, vo
   if (zero) {
     if (p.fix_list) {  // symbolic method: hand the system to the fix-up pass
       const unsigned long long k = atomicAdd(p.fix_count, 1ull);
-      p.fix_list[k] = s;
+      p.fix_list[k] = t;
     } else {
       set_status(p.status, s, BAND_ERR_ZERO_PIVOT);
     }
@@ -183,8 +185,9 @@ __device__ __forceinline__ void direct_one(const DirectArgs<T>& p, int64_t s, vo
 // The rare path of the two-sided schedule, kept out of line so that it costs its
 // caller no registers.
 template <typename T, int K>
-__device__ __noinline__ void direct_redo(const DirectArgs<T>& p, int64_t s) {
-  direct_one<T, K>(p, s, nullptr);
+__device__ __noinline__ void direct_redo(const DirectArgs<T>& p, int64_t t) {
+
+  direct_one<T, K>(p, t, nullptr);
 }
 
 // ---------------------------------------------------------------------------
@@ -204,15 +207,17 @@ __device__ __noinline__ void direct_redo(const DirectArgs<T>& p, int64_t s) {
 // the workspace (f stays intact) and a system with a zero pivot goes to the fix-up.
 // ---------------------------------------------------------------------------
 template <typename T, int K>
-__device__ __forceinline__ void twisted_one(const DirectArgs<T>& p, int64_t s, bool active,
+__device__ __forceinline__ void twisted_one(const DirectArgs<T>& p, int64_t t, bool active,
                                             void* stage) {
+  const int64_t s = active ? p.L.sys(t) : 0;   // t: position in the batch, s: system id
+
   const int lane = (int)(threadIdx.x & 31);
   const bool bottom = lane >= 16;
   const int64_t n = active ? p.L.rows(s) : 0;
   const bool split = n >= (K == 2 ? 4 : 2);
   const int64_t m = (n + 1) / 2;                       // top rows 0 .. m-1
   const int64_t q0 = active ? p.L.base(s) : 0, es = active ? p.L.stride() : 0;
-  const int64_t w0 = active ? p.W.base(s) : 0, wst = active ? p.W.stride() : 0;
+  const int64_t w0 = active ? p.W.base(t) : 0, wst = active ? p.W.stride() : 0;
   // ---- elimination of this lane's block (the mirrored recurrence for the bottom)
   const int64_t rows = !active ? 0 : (!split ? (bottom ? 0 : n) : (bottom ? n - m : m));
   const int dir = bottom ? -1 : 1;
@@ -375,10 +380,10 @@ __device__ __forceinline__ void twisted_one(const DirectArgs<T>& p, int64_t s, b
   const bool to_fix = active && !bottom && fail && p.fix_list;
   if (to_fix) {
     const unsigned long long k = atomicAdd(p.fix_count, 1ull);
-    p.fix_list[k] = s;
+    p.fix_list[k] = t;
   }
   const bool redo = active && !bottom && split && fail && !p.fix_list && (const T*)p.x != p.f;
-  if (redo) direct_redo<T, K>(p, s);
+  if (redo) direct_redo<T, K>(p, t);
   const bool o_bad = __shfl_xor_sync(full, (int)bad, 16) != 0;
   if (active && !bottom && !redo && !to_fix)
     set_status(p.status, s, fail ? BAND_ERR_ZERO_PIVOT
@@ -473,7 +478,9 @@ __device__ inline Ser ser_div(const Ser& x, const Ser& y, bool& err) {
 
 
 // One flagged system s, series rows in `mem` (3 * nmax series).
-__device__ inline void symbolic_one(const SymArgs& p, int64_t s, Ser* mem) {
+__device__ inline void symbolic_one(const SymArgs& p, int64_t t, Ser* mem) {
+  const int64_t s = p.L.sys(t);     // t: position in the batch, s: the system id
+
   const int64_t n = p.L.rows(s);
   const int K = p.L.kband(s);
   const int64_t q0 = p.L.base(s), es = p.L.stride();

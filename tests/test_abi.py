@@ -45,8 +45,8 @@ def test_exports_match_binding_list(lib):
 
 def test_desc_layout():
     from paper_1804_09666_gb300 import _lib as L
-    # int32, int32, 4 x int64, 2 pointers, int64, int32, int32
-    assert ct.sizeof(L.BandDesc) == 8 + 4 * 8 + 2 * 8 + 8 + 8
+    # int32, int32, 4 x int64, 2 pointers, int64, int32, int32, pointer
+    assert ct.sizeof(L.BandDesc) == 8 + 4 * 8 + 2 * 8 + 8 + 8 + 8
 
 
 def test_status_strings(lib):
