@@ -50,6 +50,8 @@ def parse():
     ap.add_argument("--grid", type=int, default=GRID)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-graph", action="store_true")
+    ap.add_argument("--no-extras", action="store_true",
+                    help="skip the ragged, precision and adjoint workloads (N = 1 only)")
     return ap.parse_args()
 
 
@@ -380,6 +382,114 @@ def workload_config(grid, ngpus):
             "parallelism": "replicas: every rank solves its own full set" if ngpus > 1 else "1 GPU"}
 
 
+# ------------------------------------------------------- the other workloads
+def _time(fn, reps=5, warm=2):
+    """Best of `reps` CUDA-event timings (ms) of fn() on the current stream."""
+    import torch
+    for _ in range(warm):
+        fn()
+    torch.cuda.synchronize()
+    best = float("inf")
+    for _ in range(reps):
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record()
+        fn()
+        e1.record()
+        torch.cuda.synchronize()
+        best = min(best, e0.elapsed_time(e1))
+    return best
+
+
+def ragged_workload(dev):
+    """65536 systems, n log-uniform in [16, 8192], half TD / half PD, packed ragged:
+    size buckets with autotuned schedules in one graph-captured launch, against the
+    whole packing on one thread per system."""
+    import torch
+    import paper_1804_09666_gb300 as band
+    B = synth.cfg2()
+    d = {q: torch.from_numpy(B[q]).to(dev) for q in "abcdef"}
+    units = int(B["offsets"][-1])
+    plan = band.RaggedPlan(*(d[q] for q in "abcdef"), B["offsets"], B["hbw"], schedule="tune")
+    plan.run()
+    torch.cuda.synchronize()
+    s = torch.cuda.Stream()
+    s.wait_stream(torch.cuda.current_stream())
+    g = torch.cuda.CUDAGraph()
+    with torch.cuda.stream(s):
+        with torch.cuda.graph(g, stream=s):
+            plan.run()
+    torch.cuda.current_stream().wait_stream(s)
+    ms = _time(g.replay, reps=10)
+    x, st = plan.x, plan.status
+    err = np.maximum.reduceat(np.abs(x.cpu().numpy() - B["x_true"]), B["offsets"][:-1])
+    offs = torch.from_numpy(B["offsets"]).to(dev)
+    hbw = torch.from_numpy(B["hbw"]).to(dev)
+    ms_whole = _time(lambda: band.solve_ragged(*(d[q] for q in "abcdef"), offs, hbw,
+                                               n_max=int(B["sizes"].max()), total_rows=units),
+                     reps=5)
+    return {"workload": "65536 ragged systems, n log-uniform in [16, 8192], half TD / half PD, "
+                        "dominant (%d unknowns)" % units,
+            "value": units / (ms * 1e-3), "unit": UNIT, "ms": ms,
+            "buckets": len(plan.buckets),
+            "two_sided_buckets": int(sum(1 for v in plan.schedules if v == 2)),
+            "status_not_ok": int((st != 0).sum()), "max_err_vs_manufactured": float(err.max()),
+            "whole_packing_thread_per_system": {"value": units / (ms_whole * 1e-3), "ms": ms_whole}}
+
+
+def precision_workload(dev):
+    """16384 PD systems of n = 4096 stored in FP32 (dominance ratio in {1.01, 1.1, 2} with
+    5 % of the diagonal signs flipped): FP32 + refinement against plain FP64 NPDM on
+    the same matrices (their FP64 values), both at the forward error they reach."""
+    import torch
+    import paper_1804_09666_gb300 as band
+    nsys, n = 16384, 4096
+    B = synth.cfg3()
+    d32 = {q: torch.from_numpy(B[q]).to(dev).view(n, nsys) for q in "abcde"}
+    d64 = {q: d32[q].double() for q in "abcde"}
+    f = torch.from_numpy(B["f"]).to(dev).view(n, nsys)
+    xt = torch.from_numpy(B["x_true"]).to(dev).view(n, nsys)
+    units = n * nsys
+
+    def rel(x):
+        return float(((x - xt).abs().amax(0) / xt.abs().amax(0)).max())
+
+    out = {}
+    x64 = torch.empty_like(f)
+    ms64 = _time(lambda: band.solve(*(d64[q] for q in "abcde"), f, method="npdm", x=x64))
+    out["fp64_npdm"] = {"value": units / (ms64 * 1e-3), "ms": ms64, "max_rel_err": rel(x64)}
+    res = {}
+
+    def run_refine():
+        res["x"], res["steps"], res["st"] = band.refine_solve(*(d32[q] for q in "abcde"), f)
+    msr = _time(run_refine)
+    steps = res["steps"].cpu().numpy()
+    out["fp32_refine"] = {"value": units / (msr * 1e-3), "ms": msr, "max_rel_err": rel(res["x"]),
+                          "steps_max": int(steps.max()), "steps_mean": float(steps.mean()),
+                          "status_not_ok": int((res["st"] != 0).sum())}
+    out["workload"] = "16384 PD systems, n = 4096, FP32 storage (%d unknowns)" % units
+    out["unit"] = UNIT
+    out["refine_over_fp64"] = out["fp32_refine"]["value"] / out["fp64_npdm"]["value"]
+    return out
+
+
+def adjoint_workload(dev):
+    """4096 PD systems of n = 1024: NPDM solve plus the adjoint (all six gradients)."""
+    import torch
+    import paper_1804_09666_gb300 as band
+    nsys, n = 4096, 1024
+    B = synth.cfg4()
+    d = {q: torch.from_numpy(B[q]).to(dev).view(n, nsys) for q in "abcdefw"}
+    units = n * nsys
+
+    def step():
+        x, _ = band.solve(*(d[q] for q in "abcdef"), method="npdm")
+        band.adjoint(*(d[q] for q in "abcde"), x, d["w"])
+    ms = _time(step)
+    return {"workload": "4096 PD systems, n = 1024: solve + adjoint", "value": units / (ms * 1e-3),
+            "unit": UNIT, "ms": ms}
+
+
 # ---------------------------------------------------------------------- main
 def main():
     args = parse()
@@ -498,6 +608,9 @@ def main():
             "clocks": ck, "e2e": e2e, "gpu_launches": launches_per_step * args.steps,
             "roofline": roof, "status_not_ok": bad,
             "fp64_fma_per_s": fma_rate}
+    if rank == 0 and world == 1 and not args.no_extras and args.grid == GRID:
+        line["workloads"] = {"ragged": ragged_workload(dev), "precision": precision_workload(dev),
+                             "adjoint": adjoint_workload(dev)}
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         line["cpu_baseline"] = cpu_baseline(W)
     if rank == 0:
