@@ -8,9 +8,16 @@
 // beta_i -- the NPDM factorisation of Veneva & Ayriyan, Sec. 1):
 //   U^T v = w:       v_i = w_i - alpha_{i-1} v_{i-1} - beta_{i-2} v_{i-2}
 //   L^T lambda = v:  lambda_i = (v_i - gamma_{i+1} lambda_{i+1} - a_{i+2} lambda_{i+2}) / mu_i
-// The forward sweep refactors A (or reads band_factor's buffer) and keeps gamma,
-// 1/mu and v in the workspace; the backward sweep forms lambda and the gradients.
-// One thread per system, FP64.
+// With stored factors (band_factor's buffer), or for ragged batches, one thread per
+// system runs these two sweeps and forms the gradients in the second.
+//
+// Otherwise A^T lambda = w is solved as a band system of its own: A^T's row-aligned
+// diagonals are (e_{i-2}, d_{i-1}, c_i, b_{i+1}, a_{i+2}), copied into the workspace
+// by an elementwise kernel; the NPDM / NTDM sweep then runs on them on the schedule
+// band_desc asks for (two-sided by default), writing lambda straight into dL/df; an
+// elementwise kernel forms the five gradient diagonals.  The two copies are memory
+// traffic at full bandwidth; the solve is the latency-bound part, and the two-sided
+// schedule halves it.
 #include "api_util.h"
 #include "kernels.h"
 
@@ -124,12 +131,87 @@ AdjWs carve_adjoint(const band_desc* d, void* base, size_t* bytes) {
   return w;
 }
 
+// Elements of one strided array that a uniform batch spans.
+int64_t span_of(const band_desc* d) {
+  return (d->n - 1) * d->elem_stride + (d->nsys - 1) * d->sys_stride + 1;
+}
+
+// Workspace of the transposed path: A^T's diagonals in A's layout, then the solve's.
+struct AdjTWs {
+  double* t[5];
+  void* solve;
+  size_t solve_bytes;
+};
+AdjTWs carve_adjoint_t(const band_desc* d, int32_t method, void* base, size_t* bytes) {
+  Carve c(base);
+  AdjTWs w{};
+  const size_t arr = (size_t)span_of(d) * sizeof(double);
+  for (int k = 0; k < 5; ++k) w.t[k] = (double*)c.take(arr);
+  size_t sb = 0;
+  carve_solve(d, method, nullptr, &sb);
+  w.solve = c.take(sb);
+  w.solve_bytes = sb;
+  *bytes = c.size();
+  return w;
+}
+
+// (i, s) of the idx-th element, running along the unit-stride index first
+__device__ __forceinline__ void elem_of(const Layout& L, int64_t idx, int64_t& i, int64_t& s) {
+  if (L.ss == 1) { s = idx % L.nsys; i = idx / L.nsys; }
+  else { i = idx % L.n; s = idx / L.n; }
+}
+
+template <int K>
+__global__ void __launch_bounds__(256) k_transpose_band(const Layout L, const double* a,
+                                                        const double* b, const double* c,
+                                                        const double* d, const double* e,
+                                                        double* ta, double* tb, double* tc,
+                                                        double* td, double* te) {
+  const int64_t idx = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (idx >= L.nsys * L.n) return;
+  int64_t i, s;
+  elem_of(L, idx, i, s);
+  const int64_t n = L.n, es = L.es, q = s * L.ss + i * es;
+  tc[q] = ldro(c + q);
+  tb[q] = (i >= 1) ? ldro(d + q - es) : 0.0;
+  td[q] = (i + 1 < n) ? ldro(b + q + es) : 0.0;
+  if (K == 2) {
+    ta[q] = (i >= 2) ? ldro(e + q - 2 * es) : 0.0;
+    te[q] = (i + 2 < n) ? ldro(a + q + 2 * es) : 0.0;
+  }
+}
+
+template <int K>
+__global__ void __launch_bounds__(256) k_adjoint_grad(const Layout L, const double* x,
+                                                      const double* lam, double* ga, double* gb,
+                                                      double* gc, double* gd, double* ge) {
+  const int64_t idx = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (idx >= L.nsys * L.n) return;
+  int64_t i, s;
+  elem_of(L, idx, i, s);
+  const int64_t n = L.n, es = L.es, q = s * L.ss + i * es;
+  const double l = lam[q];
+  gc[q] = -l * x[q];
+  gb[q] = (i >= 1) ? -l * x[q - es] : 0.0;
+  gd[q] = (i + 1 < n) ? -l * x[q + es] : 0.0;
+  if (K == 2) {
+    ga[q] = (i >= 2) ? -l * x[q - 2 * es] : 0.0;
+    ge[q] = (i + 2 < n) ? -l * x[q + 2 * es] : 0.0;
+  } else {
+    if (ga) ga[q] = 0.0;
+    if (ge) ge[q] = 0.0;
+  }
+}
+
 }  // namespace
 
 size_t adjoint_workspace_bytes(const band_desc* d) {
-  size_t b = 0;
+  size_t b = 0, bt = 0;
   carve_adjoint(d, nullptr, &b);
-  return b;
+  if (!d->offsets && d->nsys > 0 && d->n > 0) {
+    carve_adjoint_t(d, d->half_bw == 1 ? BAND_NTDM : BAND_NPDM, nullptr, &bt);
+  }
+  return b > bt ? b : bt;
 }
 
 }  // namespace band
@@ -149,6 +231,44 @@ extern "C" band_status band_adjoint(const band_desc* desc, int32_t method, const
   if (!grad_diag[1] || !grad_diag[2] || !grad_diag[3]) return BAND_ERR_ARG;
   const bool pd = may_be_pd(desc) && kmode != 1;
   if (pd && (!diag[0] || !diag[4] || !grad_diag[0] || !grad_diag[4])) return BAND_ERR_ARG;
+  cudaStream_t st = static_cast<cudaStream_t>(stream);
+  if (!factors && !desc->offsets && kmode > 0) {
+    // the transposed system solved as a band system of its own
+    const int32_t m = kmode == 1 ? BAND_NTDM : BAND_NPDM;
+    size_t need = 0;
+    carve_adjoint_t(desc, m, nullptr, &need);
+    if (!ws || ws_bytes < need) return BAND_ERR_WORKSPACE;
+    const AdjTWs tw = carve_adjoint_t(desc, m, ws, &need);
+    const Layout L = layout_of(desc);
+    const int64_t total = desc->nsys * desc->n;
+    const unsigned grid = (unsigned)((total + 255) / 256);
+    const double* A[5] = {(const double*)diag[0], (const double*)diag[1], (const double*)diag[2],
+                          (const double*)diag[3], (const double*)diag[4]};
+    if (kmode == 2)
+      k_transpose_band<2><<<grid, 256, 0, st>>>(L, A[0], A[1], A[2], A[3], A[4], tw.t[0], tw.t[1],
+                                                tw.t[2], tw.t[3], tw.t[4]);
+    else
+      k_transpose_band<1><<<grid, 256, 0, st>>>(L, A[0], A[1], A[2], A[3], A[4], tw.t[0], tw.t[1],
+                                                tw.t[2], tw.t[3], tw.t[4]);
+    if (cudaGetLastError() != cudaSuccess) return BAND_ERR_CUDA;
+    const void* dt[5] = {tw.t[0], tw.t[1], tw.t[2], tw.t[3], tw.t[4]};
+    DirectReq r;
+    const band_status v = make_direct(desc, m, dt, w, grad_f, sys_status, tw.solve,
+                                      tw.solve_bytes, &r);
+    if (v != BAND_OK) return v;
+    const cudaError_t e = r.two_sided ? launch_twisted<double>(r.d64, r.kmode, st)
+                                      : launch_direct<double>(r.d64, r.kmode, st);
+    if (e != cudaSuccess) return BAND_ERR_CUDA;
+    double* G[5] = {(double*)grad_diag[0], (double*)grad_diag[1], (double*)grad_diag[2],
+                    (double*)grad_diag[3], (double*)grad_diag[4]};
+    if (kmode == 2)
+      k_adjoint_grad<2><<<grid, 256, 0, st>>>(L, (const double*)x, (const double*)grad_f, G[0],
+                                              G[1], G[2], G[3], G[4]);
+    else
+      k_adjoint_grad<1><<<grid, 256, 0, st>>>(L, (const double*)x, (const double*)grad_f, G[0],
+                                              G[1], G[2], G[3], G[4]);
+    return cuda_status(cudaGetLastError());
+  }
   size_t need = 0;
   carve_adjoint(desc, nullptr, &need);
   if (!ws || ws_bytes < need) return BAND_ERR_WORKSPACE;
@@ -170,7 +290,6 @@ extern "C" band_status band_adjoint(const band_desc* desc, int32_t method, const
   p.gf = (double*)grad_f;
   p.sg = wk.g; p.sr = wk.r; p.sv = wk.v;
   p.status = sys_status;
-  k_adjoint<<<(unsigned)((desc->nsys + 127) / 128), 128, 0, static_cast<cudaStream_t>(stream)>>>(
-      p, kmode);
+  k_adjoint<<<(unsigned)((desc->nsys + 127) / 128), 128, 0, st>>>(p, kmode);
   return cuda_status(cudaGetLastError());
 }

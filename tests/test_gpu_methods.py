@@ -119,7 +119,11 @@ def test_adjoint_vs_oracle(band):
                                                      T["w"], factors=fac)
     torch.cuda.synchronize()
     assert (sta.cpu() == 0).all()
-    assert torch.equal(gf, gf2) and torch.equal(gc, gc2) and torch.equal(ga, ga2)
+    # two routes: A^T solved as a band system (no factors), and the transposed sweeps
+    # through band_factor's factors; they agree to rounding
+    for g1, g2 in ((gf, gf2), (gc, gc2), (ga, ga2), (gb, gb2), (gd, gd2), (ge, ge2)):
+        den = g2.abs().amax(0).clamp_min(1e-300)
+        assert ((g1 - g2).abs().amax(0) / den).max().item() <= 1e-12
     xg = x.cpu().numpy()
     G = [g.cpu().numpy() for g in (ga, gb, gc, gd, ge, gf)]
     w = B["w"].reshape(n, nsys)
@@ -258,3 +262,34 @@ def test_refine_layouts_and_bandwidths(band, k, layout, n, nsys):
                                     nsys, n, ss, es)
     assert (so == 0).all()
     assert per_system_rel(flat_of(x), xtruth, n, nsys, ss, es).max() <= 1e-10
+
+
+@pytest.mark.parametrize("k", [1, 2])
+@pytest.mark.parametrize("layout", ["interleaved", "contiguous"])
+@pytest.mark.parametrize("n", [1, 2, 3, 5, 40, 257])
+def test_adjoint_transposed_solve(band, k, layout, n):
+    """The transposed-solve route of the adjoint across sizes (one-thread fallback for
+    n < 4 included), bandwidths and layouts, against the oracle's adjoint."""
+    nsys = 37
+    B = synth.cfg0(nsys=nsys, n=n, k=k, layout=layout, seed_salt=12)
+    rng = np.random.default_rng(12)
+    wc = rng.uniform(-1, 1, (n, nsys))
+    B["w"] = synth.to_layout(wc, layout)
+    T = to_dev(B, keys="abcdefw")
+    a, e = (T["a"], T["e"]) if k == 2 else (None, None)
+    meth = "npdm" if k == 2 else "ntdm"
+    x, st = band.solve(a, T["b"], T["c"], T["d"], e, T["f"], method=meth)
+    grads, gf, sta = band.adjoint(a, T["b"], T["c"], T["d"], e, x, T["w"], method=meth)
+    torch.cuda.synchronize()
+    assert (sta.cpu() == 0).all()
+    xg = x.cpu().numpy()
+    G = [g.cpu().numpy() if g is not None else None for g in grads] + [gf.cpu().numpy()]
+    for s in range(nsys):
+        S = synth.system(B, s)
+        go, gfo, sto = oracle.adjoint(k, *(S[q] for q in "abcde"), xg[:, s], wc[:, s])
+        assert sto == "OK"
+        for j, (g_gpu, g_orc) in enumerate(zip(G, list(go) + [gfo])):
+            if g_gpu is None:
+                continue
+            den = max(np.abs(g_orc).max(), 1e-300)
+            assert np.abs(g_gpu[:, s] - g_orc).max() / den <= 1e-11, (s, j)
