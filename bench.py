@@ -160,22 +160,24 @@ def units_per_step(W):
 class DeviceSet:
     """Device inputs, the batched plan of the 30 solves and its CUDA graph."""
 
-    def __init__(self, W, dev, use_graph=True):
+    def __init__(self, W, dev, use_graph=True, host=None):
+        """host: another DeviceSet whose pinned host inputs this one shares."""
         import torch
         import paper_1804_09666_gb300 as band
         self.torch = torch
         self.items = []
         specs, self.spec_methods = [], []
-        for w in W:
+        for wi, w in enumerate(W):
             B = w["B"]
             n, ns, ss, es = B["n"], B["nsys"], B["sys_stride"], B["elem_stride"]
             keys = "abcdef" if w["k"] == 2 else "bcdf"
-            host = {q: torch.from_numpy(B[q]).pin_memory() for q in keys}
+            host_in = {q: torch.from_numpy(B[q]).pin_memory() for q in keys} if host is None \
+                else host.items[wi]["host"]
             flat = {q: torch.empty(B[q].shape, dtype=torch.float64, device=dev) for q in keys}
             for q in keys:
-                flat[q].copy_(host[q])
+                flat[q].copy_(host_in[q])
             view = {q: flat[q].as_strided((n, ns), (es, ss)) for q in keys}
-            self.items.append(dict(w=w, host=host, flat=flat, view=view, n=n, nsys=ns))
+            self.items.append(dict(w=w, host=host_in, flat=flat, view=view, n=n, nsys=ns))
         # heaviest problems first: SIP, then the PD sweeps, then the TD sweeps
         for kind in ("sip", "npdm", "spdm", "ntdm", "stdm"):
             for it in self.items:
@@ -254,6 +256,73 @@ class DeviceSet:
         is present."""
         kinds = {k for k, _ in self.spec_methods}
         return 1 + int(bool(kinds & {"spdm", "stdm"})) + int("sip" in kinds)
+
+
+def e2e_serial(D, steps, world):
+    """H2D, solves and D2H of each step one after the other on one stream (ms)."""
+    import torch
+    for _ in range(2):
+        D.upload(); D.step(); D.download()
+    torch.cuda.synchronize()
+    barrier(world)
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    e0.record()
+    for _ in range(steps):
+        D.upload()
+        D.step()
+        D.download()
+    e1.record()
+    torch.cuda.synchronize()
+    barrier(world)
+    return max_over_ranks(e0.elapsed_time(e1), world)
+
+
+def e2e_pipelined(sets, steps, world):
+    """Steps k and k+1 use different device sets; each step's H2D, solves and D2H run on
+    their own streams, ordered by events (ms for `steps` steps, all copies included)."""
+    import torch
+    main = torch.cuda.current_stream()
+    sh, sc, sd = torch.cuda.Stream(), torch.cuda.Stream(), torch.cuda.Stream()
+    ev = {name: [torch.cuda.Event() for _ in sets] for name in ("h2d", "cmp", "d2h")}
+
+    def run(nsteps):
+        for k in range(nsteps):
+            j = k % len(sets)
+            S = sets[j]
+            with torch.cuda.stream(sh):
+                sh.wait_event(ev["cmp"][j])        # the set's previous solves read its inputs
+                S.upload()
+                ev["h2d"][j].record(sh)
+            with torch.cuda.stream(sc):
+                sc.wait_event(ev["h2d"][j])
+                sc.wait_event(ev["d2h"][j])        # its previous results have been read
+                S.step()
+                ev["cmp"][j].record(sc)
+            with torch.cuda.stream(sd):
+                sd.wait_event(ev["cmp"][j])
+                S.download()
+                ev["d2h"][j].record(sd)
+        for s in (sh, sc, sd):
+            main.wait_stream(s)
+
+    for s in (sh, sc, sd):
+        s.wait_stream(main)
+    run(2)
+    torch.cuda.synchronize()
+    barrier(world)
+    for s in (sh, sc, sd):
+        s.wait_stream(main)
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    e0.record(main)
+    for s in (sh, sc, sd):
+        s.wait_stream(main)
+    run(steps)
+    e1.record(main)
+    torch.cuda.synchronize()
+    barrier(world)
+    return max_over_ranks(e0.elapsed_time(e1), world)
 
 
 class EventLog:
@@ -554,24 +623,17 @@ def main():
     ms = max_over_ranks(ms, world)
     value = units * args.steps * world / (ms * 1e-3)
 
-    # end to end: pinned host inputs -> device -> solves -> host, every step
-    for _ in range(2):
-        D.upload(); D.step(); D.download()
-    torch.cuda.synchronize()
-    barrier(world)
-    e0 = torch.cuda.Event(enable_timing=True)
-    e1 = torch.cuda.Event(enable_timing=True)
-    e0.record()
-    for _ in range(args.steps):
-        D.upload()
-        D.step()
-        D.download()
-    e1.record()
-    torch.cuda.synchronize()
-    barrier(world)
-    ms_e2e = max_over_ranks(e0.elapsed_time(e1), world)
+    # end to end: every step copies its inputs from pinned host memory, solves them
+    # through the batched plan and reads its results back into pinned host memory.
+    # Consecutive steps overlap on three streams (H2D of step k+1, the solves of step k,
+    # D2H of step k-1) with two device sets used in turn.
+    D2 = DeviceSet(W, dev, use_graph=not args.no_graph, host=D)
+    ms_e2e = e2e_pipelined([D, D2], args.steps, world)
+    ms_serial = e2e_serial(D, args.steps, world)
     e2e = {"value": units * args.steps * world / (ms_e2e * 1e-3), "unit": UNIT,
-           "h2d_bytes_per_step": D.h2d_bytes, "d2h_bytes_per_step": D.d2h_bytes}
+           "h2d_bytes_per_step": D.h2d_bytes, "d2h_bytes_per_step": D.d2h_bytes,
+           "overlap": "H2D of step k+1, solves of step k and D2H of step k-1 on three streams",
+           "serial_value": units * args.steps * world / (ms_serial * 1e-3)}
 
     # the batched launch's time per step (CUDA events on the launching stream inside the
     # timed region) against the algorithmic bytes and flops of the 30 solves it does

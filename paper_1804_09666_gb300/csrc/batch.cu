@@ -9,6 +9,10 @@
 // them.  The problem table travels as a __grid_constant__ kernel parameter; nothing
 // is allocated.
 #include <algorithm>
+
+#ifndef BATCH_WARPS
+#define BATCH_WARPS 2
+#endif
 #include <cstring>
 
 #include "api_util.h"
@@ -73,7 +77,12 @@ __device__ __forceinline__ void run_direct(const DirectArgs<T>& p, int kmode, in
 // host orders the problems heaviest first.  (A persistent loop over a task counter was
 // tried: keeping every task variant's state live across the loop doubled the kernel's
 // registers, 126 -> 255, and halved the resident warps.)
-__global__ void __launch_bounds__(128) k_batch(const __grid_constant__ BatchTable t) {
+// Warps per block of k_batch.  Small blocks let the hardware spread the heaviest-first
+// tasks over all SMs instead of packing four per SM (measured on the 30-solve ADI step:
+// 1, 2 and 4 warps give 5.00, 4.96 and 5.19 ms); 128 registers allow 16 warps per SM.
+constexpr int kBatchWarps = BATCH_WARPS;
+
+__global__ void __launch_bounds__(32 * kBatchWarps, 16 / kBatchWarps) k_batch(const __grid_constant__ BatchTable t) {
   extern __shared__ __align__(16) unsigned char stage_mem[];
   void* stage = t.stage_bytes ? stage_mem + (threadIdx.x >> 5) * t.stage_bytes : nullptr;
   const int64_t task = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
@@ -228,8 +237,8 @@ extern "C" band_status band_solve_batch(const band_problem* in, int32_t count, v
   for (int i = 0; i < ncounters; ++i)
     if (cudaMemsetAsync(counters[i], 0, sizeof(unsigned long long), st) != cudaSuccess)
       return BAND_ERR_CUDA;
-  const size_t smem = (size_t)kStageWarpsPerBlock * (size_t)t.stage_bytes;
-  k_batch<<<(unsigned)((warps + 3) / 4), 128, smem, st>>>(t);
+  const size_t smem = (size_t)kBatchWarps * (size_t)t.stage_bytes;
+  k_batch<<<(unsigned)((warps + kBatchWarps - 1) / kBatchWarps), 32 * kBatchWarps, smem, st>>>(t);
   if (cudaGetLastError() != cudaSuccess) return BAND_ERR_CUDA;
   if (sym.count > 0 && slots > 0) {
     k_symbolic_batch<<<(unsigned)((slots + 63) / 64), 64, 0, st>>>(sym);
