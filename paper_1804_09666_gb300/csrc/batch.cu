@@ -13,6 +13,9 @@
 #ifndef BATCH_WARPS
 #define BATCH_WARPS 2
 #endif
+#ifndef BATCH_MIN_BLOCKS
+#define BATCH_MIN_BLOCKS (16 / BATCH_WARPS)
+#endif
 #include <cstring>
 
 #include "api_util.h"
@@ -82,7 +85,7 @@ __device__ __forceinline__ void run_direct(const DirectArgs<T>& p, int kmode, in
 // 1, 2 and 4 warps give 5.00, 4.96 and 5.19 ms); 128 registers allow 16 warps per SM.
 constexpr int kBatchWarps = BATCH_WARPS;
 
-__global__ void __launch_bounds__(32 * kBatchWarps, 16 / kBatchWarps) k_batch(const __grid_constant__ BatchTable t) {
+__global__ void __launch_bounds__(32 * kBatchWarps, BATCH_MIN_BLOCKS) k_batch(const __grid_constant__ BatchTable t) {
   extern __shared__ __align__(16) unsigned char stage_mem[];
   void* stage = t.stage_bytes ? stage_mem + (threadIdx.x >> 5) * t.stage_bytes : nullptr;
   const int64_t task = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;

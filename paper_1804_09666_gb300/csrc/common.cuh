@@ -167,7 +167,13 @@ template <> struct StageDepth<float> { static constexpr int value = 16; };
 constexpr int kStageArrays = 6;
 template <typename T>
 __host__ __device__ constexpr int stage_bytes_per_warp() { return StageDepth<T>::value * kStageArrays * 32 * (int)sizeof(T); }
-constexpr int kStageWarpsPerBlock = 4;
+// Warps per block of the single-problem sweeps (k_direct, k_twisted).  Measured on
+// GB300: FP64 gains from one warp per block (the hardware spreads the warps over more
+// SMs: 2048 x 2048 two-sided NPDM 0.84 -> 0.81 ms, 16384 x 4096 2.31 -> 2.10 ms); FP32
+// with its deeper staging ring keeps four (16384 x 4096 two-sided 0.86 ms vs 0.96).
+template <typename T> struct SweepWarps;
+template <> struct SweepWarps<double> { static constexpr int value = 1; };
+template <> struct SweepWarps<float> { static constexpr int value = 4; };
 
 // Ring of D rows x NA arrays x 32 lanes for one warp.
 template <typename T, int NA, int D>

@@ -24,7 +24,7 @@ namespace band {
 // fused factor + solve (device function in sweeps.cuh)
 // ---------------------------------------------------------------------------
 template <typename T, int K>
-__global__ void __launch_bounds__(128) k_direct(const DirectArgs<T> p) {
+__global__ void __launch_bounds__(32 * SweepWarps<T>::value) k_direct(const DirectArgs<T> p) {
   extern __shared__ __align__(16) unsigned char stage_mem[];
   const int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   if (t >= p.L.nsys) return;
@@ -40,8 +40,8 @@ __global__ void __launch_bounds__(128) k_direct(const DirectArgs<T> p) {
 template <typename T>
 cudaError_t launch_direct(const DirectArgs<T>& p, int kmode, cudaStream_t st) {
   if (p.L.nsys == 0) return cudaSuccess;
-  const int tb = 32 * kStageWarpsPerBlock;
-  const size_t smem = (size_t)kStageWarpsPerBlock * stage_bytes_per_warp<T>();
+  const int tb = 32 * SweepWarps<T>::value;
+  const size_t smem = (size_t)SweepWarps<T>::value * stage_bytes_per_warp<T>();
   const unsigned grid = (unsigned)((p.L.nsys + tb - 1) / tb);
   if (kmode == 1) k_direct<T, 1><<<grid, tb, smem, st>>>(p);
   else if (kmode == 2) k_direct<T, 2><<<grid, tb, smem, st>>>(p);
@@ -53,7 +53,7 @@ template cudaError_t launch_direct<float>(const DirectArgs<float>&, int, cudaStr
 
 // two threads (lanes l, l ^ 16) per system; one bandwidth for the batch
 template <typename T, int K>
-__global__ void __launch_bounds__(128) k_twisted(const DirectArgs<T> p) {
+__global__ void __launch_bounds__(32 * SweepWarps<T>::value) k_twisted(const DirectArgs<T> p) {
   extern __shared__ __align__(16) unsigned char stage_mem[];
   void* stage = stage_mem + (threadIdx.x >> 5) * stage_bytes_per_warp<T>();
   const int64_t warp = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
@@ -65,10 +65,11 @@ template <typename T>
 cudaError_t launch_twisted(const DirectArgs<T>& p, int kmode, cudaStream_t st) {
   if (p.L.nsys == 0) return cudaSuccess;
   const int64_t threads = (p.L.nsys + 15) / 16 * 32;
-  const unsigned grid = (unsigned)((threads + 127) / 128);
-  const size_t smem = (size_t)kStageWarpsPerBlock * stage_bytes_per_warp<T>();
-  if (kmode == 1) k_twisted<T, 1><<<grid, 128, smem, st>>>(p);
-  else if (kmode == 2) k_twisted<T, 2><<<grid, 128, smem, st>>>(p);
+  const int tb = 32 * SweepWarps<T>::value;
+  const unsigned grid = (unsigned)((threads + tb - 1) / tb);
+  const size_t smem = (size_t)SweepWarps<T>::value * stage_bytes_per_warp<T>();
+  if (kmode == 1) k_twisted<T, 1><<<grid, tb, smem, st>>>(p);
+  else if (kmode == 2) k_twisted<T, 2><<<grid, tb, smem, st>>>(p);
   else return cudaErrorInvalidValue;
   return cudaGetLastError();
 }
