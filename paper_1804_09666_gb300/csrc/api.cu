@@ -1,5 +1,6 @@
 // api.cu -- C entry points for the direct solvers (band_solve, band_factor) and the
 // shared utilities of libband.  See include/band.h for the contract of each call.
+#include <cstdint>
 #include <cstring>
 
 #include "api_util.h"
@@ -99,6 +100,15 @@ band_status make_direct(const band_desc* desc, int32_t method, const void* const
                              (const float*)diag[3], (const float*)diag[4], (const float*)f,
                              (float*)x, (float*)w.al, (float*)w.be, nullptr, sys_status,
                              nullptr, nullptr};
+  // contiguous rows (each lane its own system) are staged in 16-byte granules when
+  // every array the sweep reads is 16-byte aligned
+  {
+    auto al16 = [](const void* ptr) { return ((uintptr_t)ptr & 15u) == 0; };
+    const bool contig = desc->offsets ? true : (desc->elem_stride == 1 && desc->sys_stride != 1);
+    const bool aligned = al16(diag[1]) && al16(diag[2]) && al16(diag[3]) && al16(f) &&
+                         (kmode == 1 || (diag[0] && diag[4] && al16(diag[0]) && al16(diag[4])));
+    r->d64.gran = r->d32.gran = (contig && aligned) ? 1 : 0;
+  }
   if (!r->symbolic) {
     r->d64.zs = nullptr;
     r->d64.fix_count = nullptr;

@@ -47,6 +47,8 @@ inline Layout layout_of(const band_desc* d) {
   L.offsets = d->offsets;
   L.hbw = d->hbw;
   L.ids = d->systems;
+  L.extent = ragged(d) ? d->total_rows
+                       : (d->n - 1) * d->elem_stride + (d->nsys - 1) * d->sys_stride + 1;
   L.half_bw = d->half_bw;
   return L;
 }

@@ -196,6 +196,10 @@ extern "C" band_status band_solve_batch(const band_problem* in, int32_t count, v
       if (v != BAND_OK) return v;
       b.kmode = (int16_t)r.kmode;
       b.two_sided = r.two_sided ? 1 : 0;
+      // Uniform contiguous problems read through L1 here: next to the batch's other
+      // tasks that measured faster than granule staging (ADI step 4.85 vs 5.16 ms);
+      // ragged buckets keep it (65536 systems: 10.7 -> 8.7 ms).
+      if (!q.desc->offsets) r.d64.gran = r.d32.gran = 0;
       if (q.desc->dtype == BAND_F64) {
         b.kind = kDirect64;
         b.u.d64 = r.d64;

@@ -18,6 +18,7 @@ struct Layout {
   const int64_t* offsets;
   const int8_t* hbw;
   const int64_t* ids;     // ragged subsets: the batch's s-th system is ids[s]
+  int64_t extent;         // elements one array spans (the last valid index + 1)
   int32_t half_bw;
   // id of the batch's s-th system (the index of every per-system array)
   __device__ __forceinline__ int64_t sys(int64_t s) const { return ids ? ids[s] : s; }
@@ -158,15 +159,34 @@ __device__ __forceinline__ void cp_async_wait() {
   asm volatile("cp.async.wait_group %0;\n" ::"n"(N) : "memory");
 }
 
+// 16-byte copy global -> shared that bypasses L1 (cp.async.cg); both addresses 16-byte
+// aligned.
+__device__ __forceinline__ void cp_async16(void* smem, const void* g) {
+  const unsigned s = (unsigned)__cvta_generic_to_shared(smem);
+  asm volatile("cp.async.cg.shared.global [%0], [%1], 16;\n" ::"r"(s), "l"(g) : "memory");
+}
+
 // Rows staged per warp: an FP64 row carries ~14 FP64 instructions (>1000 cycles with
 // several warps per sub-partition), so 4 rows cover the memory latency; an FP32 row is
-// cheap, so 16.  Ring bytes per warp for six arrays: 6 KiB (FP64) and 12 KiB (FP32).
+// cheap, so 16.  Row-ring bytes per warp for six arrays: 6 KiB (FP64) and 12 KiB (FP32);
+// a warp's staging area is the larger of that and the granule ring.
 template <typename T> struct StageDepth;
 template <> struct StageDepth<double> { static constexpr int value = 4; };
 template <> struct StageDepth<float> { static constexpr int value = 16; };
 constexpr int kStageArrays = 6;
+// Granules staged ahead (GranRing, below): 2 x 2 FP64 rows and 4 x 4 FP32 rows, the
+// same shared memory as the row ring (a larger FP64 ring shrinks the L1 that the other
+// tasks of a batched launch read through: measured 4.85 -> 7.2 ms on the ADI step).
+template <typename T> struct GranDepth;
+template <> struct GranDepth<double> { static constexpr int value = 2; };
+template <> struct GranDepth<float> { static constexpr int value = 4; };
 template <typename T>
-__host__ __device__ constexpr int stage_bytes_per_warp() { return StageDepth<T>::value * kStageArrays * 32 * (int)sizeof(T); }
+__host__ __device__ constexpr int stage_bytes_per_warp() {
+  return StageDepth<T>::value * kStageArrays * 32 * (int)sizeof(T) >
+                 GranDepth<T>::value * kStageArrays * 32 * 16
+             ? StageDepth<T>::value * kStageArrays * 32 * (int)sizeof(T)
+             : GranDepth<T>::value * kStageArrays * 32 * 16;
+}
 // Warps per block of the single-problem sweeps (k_direct, k_twisted).  Measured on
 // GB300: FP64 gains from one warp per block (the hardware spreads the warps over more
 // SMs: 2048 x 2048 two-sided NPDM 0.84 -> 0.81 ms, 16384 x 4096 2.31 -> 2.10 ms); FP32
@@ -174,6 +194,38 @@ __host__ __device__ constexpr int stage_bytes_per_warp() { return StageDepth<T>:
 template <typename T> struct SweepWarps;
 template <> struct SweepWarps<double> { static constexpr int value = 1; };
 template <> struct SweepWarps<float> { static constexpr int value = 4; };
+
+// Staging of rows that each lane reads from its own contiguous system (contiguous and
+// ragged layouts): 16-byte granules (2 FP64 / 4 FP32 rows) of every array, D granules
+// ahead of the sweep, copied with cp.async.cg into a per-lane ring.  A warp touches 32
+// lines per row there; through L1 those lines are evicted by the other warps' before
+// their next row, so the rows go around L1.  A granule that would reach past the
+// arrays' last element (`extent`) is copied element by element.
+template <typename T, int NA, int D>
+struct GranRing {
+  static constexpr int E = 16 / (int)sizeof(T);
+  T* sm;     // D x NA x 32 granules
+  int lane;
+  __device__ __forceinline__ T* at(int slot, int a) const {
+    return sm + ((((slot * NA + a) << 5) + lane) * E);
+  }
+  __device__ __forceinline__ void issue(int slot, const T* const* src, int64_t g,
+                                        int64_t extent) const {
+    const int64_t e = g * E;
+#pragma unroll
+    for (int a = 0; a < NA; ++a) {
+      if (e + E <= extent) {
+        cp_async16(at(slot, a), src[a] + e);
+      } else {
+        for (int k = 0; k < E; ++k)
+          if (e + k < extent) cp_async_elem(at(slot, a) + k, src[a] + e + k);
+      }
+    }
+    cp_async_commit();
+  }
+  __device__ __forceinline__ T get(int slot, int a, int off) const { return at(slot, a)[off]; }
+  static constexpr int bytes() { return D * NA * 32 * 16; }
+};
 
 // Ring of D rows x NA arrays x 32 lanes for one warp.
 template <typename T, int NA, int D>

@@ -22,6 +22,7 @@ struct DirectArgs {
   int32_t* status;
   unsigned long long* fix_count;   // symbolic methods: flagged-system counter and list
   int64_t* fix_list;
+  int32_t gran;                    // contiguous rows staged in 16-byte granules (GranRing)
 };
 
 template <typename T>

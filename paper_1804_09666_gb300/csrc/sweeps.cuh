@@ -264,6 +264,56 @@ __device__ __forceinline__ void twisted_one(const DirectArgs<T>& p, int64_t t, b
       }
     }
     cp_async_wait<0>();
+  } else if (stage && p.gran) {
+    // each lane walks its own contiguous system: 16-byte granules staged ahead
+    constexpr int D = GranDepth<T>::value;
+    constexpr int NA = K == 2 ? 6 : 4;
+    constexpr int E = GranRing<T, NA, D>::E;
+    const GranRing<T, NA, D> ring{static_cast<T*>(stage), (int)(threadIdx.x & 31)};
+    const T* src[NA];
+    if (K == 2) {
+      src[0] = p.a; src[1] = p.b; src[2] = p.c; src[3] = p.d; src[4] = p.e; src[5] = p.f;
+    } else {
+      src[0] = p.b; src[1] = p.c; src[2] = p.d; src[3] = p.f;
+    }
+    constexpr int IB = K == 2 ? 1 : 0, IC = IB + 1, ID = IB + 2, IF = NA - 1;
+    // element of row j of this sweep: e0 + dir * j (stride 1); its granule e / E
+    const int64_t e0 = q0 + first;
+    const int64_t g0 = e0 / E;
+    const int64_t ng = rows > 0 ? (dir > 0 ? (e0 + rows - 1) / E - g0 + 1 : g0 - (e0 - rows + 1) / E + 1) : 0;
+#pragma unroll
+    for (int k = 0; k < D - 1; ++k) {
+      if (k < ng) ring.issue(k, src, g0 + dir * k, p.L.extent);
+      else cp_async_commit();
+    }
+    int64_t gk = -1;                       // visit index of the granule of row j
+    for (int64_t j = 0; j < rows; ++j) {
+      const int64_t e = e0 + dir * j;
+      const int off = (int)(e % E);
+      if (j == 0 || off == (dir > 0 ? 0 : E - 1)) {     // entering the next granule
+        ++gk;
+        const int64_t kn = gk + D - 1;
+        if (kn < ng) ring.issue((int)(kn & (D - 1)), src, g0 + dir * kn, p.L.extent);
+        else cp_async_commit();
+        cp_async_wait<D - 1>();
+      }
+      const int slot = (int)(gk & (D - 1));
+      T ai = K == 2 ? ring.get(slot, 0, off) : T(0);
+      T bi = ring.get(slot, IB, off);
+      T di = ring.get(slot, ID, off);
+      T ei = K == 2 ? ring.get(slot, 4, off) : T(0);
+      if (bottom) {                                  // reversed system
+        const T ta = ai, tb = bi;
+        ai = ei; bi = di; di = tb; ei = ta;
+      }
+      const int64_t i = first + dir * j;
+      if (!forward_row<T, K>(p, j, n, q0 + i * es, w0 + i * wst, ai, bi, ring.get(slot, IC, off),
+                             di, ei, ring.get(slot, IF, off), al1, al2, be1, be2, z1, z2)) {
+        zero = true;
+        break;
+      }
+    }
+    cp_async_wait<0>();
   } else {
     RowIn<T> r0, r1, r2;
     auto load = [&](int64_t j, RowIn<T>& r) {       // j-th row of this lane's sweep
