@@ -23,6 +23,7 @@ struct DirectArgs {
   unsigned long long* fix_count;   // symbolic methods: flagged-system counter and list
   int64_t* fix_list;
   int32_t gran;                    // contiguous rows staged in 16-byte granules (GranRing)
+  const int32_t* skip;             // per system id, or null: nonzero = leave the system alone
 };
 
 template <typename T>

@@ -1,30 +1,24 @@
 // refine.cu -- FP32 factor/solve with iterative refinement to FP64 accuracy.
 //
 // The systems are stored in FP32; the right-hand side and the solution are FP64.
-//   x_0 = solve32(f)
-//   per step:  r = f - A x  (A = the exact values of the FP32 diagonals)
-//              delta = 2^e solve32(2^-e r),  x = x + delta
-// until max|delta| <= rel_stop max|x| or max_steps steps.  solve32 is the NPDM / NTDM
-// recurrence (Veneva & Ayriyan, Sec. 1) in single precision; its factors (gamma, 1/mu,
-// alpha, beta) are computed once and reused by every correction.  2^e is a power of two
-// fixed per system from max|f| (exact scaling that keeps the FP32 right-hand side in
-// range).
+//   x_1 = solve32(f)                    (f rounded to FP32)
+//   step k >= 1:  r = f - A x_k         (A = the exact values of the FP32 diagonals)
+//                 x_{k+1} = x_k + 2^e solve32(2^-e r)
+// until max|x_{k+1} - x_k| <= rel_stop max|x_{k+1}|, max|r| = 0, or max_steps steps.
+// solve32 is NPDM / NTDM (Veneva & Ayriyan, Sec. 1) in single precision, run by the
+// library's sweep kernels on the schedule the descriptor asks for (two-sided by
+// default); 2^e is a power of two fixed per system from max|f| (exact scaling that
+// keeps the FP32 right-hand side in range).
 //
-// GB300 runs FP64 at 1/64 of the FP32 rate, and one warp alone on a sub-partition
-// issues one FP64 instruction per 64 cycles, so a residual in FP64 arithmetic would
-// cost as much as the whole FP64 solve.  The residual and the update are therefore
-// computed with pairs of FP32 numbers and error-free transformations (TwoProd with an
-// FMA, TwoSum), giving about 2^-48 relative accuracy: ample for the 1e-10 target
-// (refinement converges to the limit set by the residual's accuracy times kappa).
-// Doubles are split into, and rebuilt from, such pairs with integer bit operations;
-// one FP64 addition per row and step assembles the stored x.
-//
-// Passes over the rows (one thread per system):
-//   F0  forward: factor + z = L^{-1} f                      (writes the factor rows, z)
-//   B   backward: x = U^{-1} z (first time) or x += 2^e U^{-1} z (corrections), and the
-//       residual of row i+2 once x_i .. x_{i+4} are final  (writes x, r)
-//   F   forward: z = L^{-1} (2^-e r) through the stored factors
-// then B, F, B, ... until the stop test.
+// Each step is made of passes that the GPU runs at full width:
+//   update    x += 2^e delta (elementwise), with max|2^e delta| and max|x| per system
+//   residual  r = f - A x (a five-point stencil, elementwise), written as 2^-e r in FP32
+//   decide    per system: stop (converged, exact, non-finite, zero pivot, cap) or go on
+//   solve     delta = solve32(2^-e r) for the systems still going
+// GB300 runs FP64 at 1/64 of the FP32 rate, so x, f, the residual and the update are
+// pairs of FP32 numbers handled with error-free transformations (TwoProd with an FMA,
+// TwoSum): about 2^-48 relative accuracy, ample for the 1e-10 target.  f is split into
+// a pair once (integer bit operations); x is assembled in FP64 once, at the end.
 #include <cuda_runtime.h>
 
 #include "api_util.h"
@@ -89,298 +83,269 @@ __device__ __forceinline__ float pow2f(int k) {
   return __uint_as_float((unsigned)(k + 127) << 23);
 }
 
-// ------------------------------------------------------------------- rows
-struct RefArgs {
+// ------------------------------------------------------------ refinement state
+struct RefState {
   Layout L;
-  Spill W;
   const float *a, *b, *c, *d, *e;
   const double* f;
   double* x;
-  float *fa, *fb, *fg, *fr, *z, *r;   // factor rows, z and scaled residual (workspace)
+  float* r32;                    // 2^-e r (the correction solve's right-hand side)
+  float* d32;                    // delta (the correction solve's solution)
+  float *xh, *xl;                // x as a pair of floats (x = xh + xl to ~2^-48)
+  float *fh, *fl;                // f as a pair of floats
+  int32_t* done;                 // per system: refinement finished
+  int32_t* sst;                  // per system: status of the last FP32 solve
+  int32_t* fexp;                 // per system: e
+  unsigned int* xmax;            // per system: max|x| (bit pattern of a float >= 0)
+  unsigned int* dmax;            // per system: max|2^e delta| (bit pattern of a float >= 0)
+  unsigned int* rmax;            // per system: max|r| (float bits; NaN and Inf on top)
+  unsigned long long* fmax;      // per system: max|f|
+  int32_t *steps, *status;
   double rel_stop;
   int max_steps;
-  int32_t *steps, *status;
 };
 
-// Row sources: either a cp.async ring (interleaved systems) or plain loads.
-template <int NF, int ND, int D>
-struct Ring2 {
-  float* fs;     // D x NF x 32 floats
-  double* ds;    // D x ND x 32 doubles
-  int lane;
-  __device__ __forceinline__ void issue(int slot, const float* const* fsrc, int64_t fq,
-                                        const double* const* dsrc, int64_t dq) const {
-#pragma unroll
-    for (int a = 0; a < NF; ++a) cp_async_elem(fs + ((slot * NF + a) << 5) + lane, fsrc[a] + fq);
-#pragma unroll
-    for (int a = 0; a < ND; ++a) cp_async_elem(ds + ((slot * ND + a) << 5) + lane, dsrc[a] + dq);
-    cp_async_commit();
-  }
-  __device__ __forceinline__ float getf(int slot, int a) const { return fs[((slot * NF + a) << 5) + lane]; }
-  __device__ __forceinline__ double getd(int slot, int a) const { return ds[((slot * ND + a) << 5) + lane]; }
-  static constexpr int bytes() { return D * 32 * (4 * NF + 8 * ND); }
-};
+constexpr int kChunk = 32;       // rows per thread in the elementwise passes
 
-constexpr int kRefWarps = 4;
-constexpr int kDepthF0 = 16, kDepthB = 8, kDepthF = 16;
-// ring bytes per warp of the passes (the largest sets the kernel's shared memory)
-constexpr int kBytesF0 = Ring2<5, 1, kDepthF0>::bytes();     // a..e, f
-constexpr int kBytesB = Ring2<8, 2, kDepthB>::bytes();       // a..e, alpha, beta, z, f, x
-constexpr int kBytesF = Ring2<4, 0, kDepthF>::bytes();       // r, a, gamma, 1/mu
-constexpr int kRefRingBytes =
-    kBytesF0 > kBytesB ? (kBytesF0 > kBytesF ? kBytesF0 : kBytesF) : (kBytesB > kBytesF ? kBytesB : kBytesF);
-
-template <int K, bool RING>
-__device__ void refine_one(const RefArgs& p, int64_t s, unsigned char* stage) {
-  const int64_t n = p.L.rows(s), q0 = p.L.base(s), es = p.L.stride();
-  const int64_t w0 = p.W.base(s), ws = p.W.stride();
-  const int lane = threadIdx.x & 31;
-  // TD systems may come without a and e: their loads read c instead (values unused)
-  const float* pa = K == 2 ? p.a : p.c;
-  const float* pe = K == 2 ? p.e : p.c;
-  const float* A5[5] = {pa, p.b, p.c, p.d, pe};
-
-  // ---- F0: FP32 factorisation and z = L^{-1} f ------------------------------
-  double fmax = 0.0;
-  bool zero = false;
-  {
-    constexpr int D = kDepthF0;
-    const Ring2<5, 1, D> ring{reinterpret_cast<float*>(stage),
-                              reinterpret_cast<double*>(stage + D * 32 * 4 * 5), lane};
-    const double* F1[1] = {p.f};
-    if (RING) {
-#pragma unroll
-      for (int j = 0; j < D - 1; ++j) {
-        if (j < n) ring.issue(j, A5, q0 + j * es, F1, q0 + j * es);
-        else cp_async_commit();
-      }
-    }
-    float al1 = 0, al2 = 0, be1 = 0, be2 = 0, z1 = 0, z2 = 0;
-    for (int64_t i = 0; i < n; ++i) {
-      const int64_t q = q0 + i * es, w = w0 + i * ws;
-      float av, bv, cv, dv, ev;
-      double fv;
-      if (RING) {
-        const int64_t ip = i + D - 1;
-        if (ip < n) ring.issue((int)(ip & (D - 1)), A5, q0 + ip * es, F1, q0 + ip * es);
-        else cp_async_commit();
-        cp_async_wait<D - 1>();
-        const int sl = (int)(i & (D - 1));
-        av = ring.getf(sl, 0); bv = ring.getf(sl, 1); cv = ring.getf(sl, 2);
-        dv = ring.getf(sl, 3); ev = ring.getf(sl, 4); fv = ring.getd(sl, 0);
-      } else {
-        av = K == 2 ? ldro(pa + q) : 0.0f; bv = ldro(p.b + q); cv = ldro(p.c + q);
-        dv = ldro(p.d + q); ev = K == 2 ? ldro(pe + q) : 0.0f; fv = p.f[q];
-      }
-      const float ai = (K == 2 && i >= 2) ? av : 0.0f;
-      const float bi = (i >= 1) ? bv : 0.0f;
-      const float di = (i + 1 < n) ? dv : 0.0f;
-      const float ei = (K == 2 && i + 2 < n) ? ev : 0.0f;
-      const float g = fmaf(-al2, ai, bi);
-      const float m = fmaf(-al1, g, fmaf(-be2, ai, cv));
-      if (m == 0.0f) { zero = true; break; }
-      const float rr = __frcp_rn(m);
-      const float alv = fmaf(-be1, g, di) * rr;
-      const float bev = ei * rr;
-      const float zv = fmaf(-z1, g, fmaf(-z2, ai, __double2float_rn(fv))) * rr;
-      p.fa[w] = alv; p.fb[w] = bev; p.fg[w] = g; p.fr[w] = rr; p.z[w] = zv;
-      fmax = max_abs(fmax, fv);
-      al2 = al1; al1 = alv; be2 = be1; be1 = bev; z2 = z1; z1 = zv;
-    }
-    if (RING) cp_async_wait<0>();
-  }
-  if (zero) {
-    if (p.steps) p.steps[s] = 0;
-    set_status(p.status, s, BAND_ERR_ZERO_PIVOT);
-    return;
-  }
-  // residual scale 2^e with 2^e ~ max|f| 2^-20 (exact power of two)
-  int fexp = ((int)((unsigned)(__double_as_longlong(fmax) >> 52) & 0x7ffu)) - 1023;
-  const int escale = fexp - 20;
-  const float up = pow2f(escale), down = pow2f(-escale);
-
-  int k = 0;
-  int32_t st = BAND_OK;
-  // pass 0 is x_0 = U^{-1} z; pass m >= 1 applies correction m; at most max_steps + 1
-  for (int pass = 0; pass <= p.max_steps; ++pass) {
-    // ---- B: backward substitution (+ update), then the residual of the new x -----
-    const bool first = (pass == 0);
-    float dmaxf = 0.0f;
-    double xmax = 0.0;
-    bool bad = false;
-    {
-      constexpr int D = kDepthB;
-      const Ring2<8, 2, D> ring{reinterpret_cast<float*>(stage),
-                                reinterpret_cast<double*>(stage + D * 32 * 4 * 8), lane};
-      // row t of the sweep is matrix row i = n-1-t; its residual row is i+2
-      const float* FS[8] = {pa, p.b, p.c, p.d, pe, p.fa, p.fb, p.z};
-      const double* DS[2] = {p.f, p.x};
-      auto issue_row = [&](int slot, int64_t i) {
-        // A row and f of residual row i+2 (clamped inside), spill and x of row i
-        const int64_t j = i + 2 < n ? i + 2 : n - 1;
-        const int64_t qj = q0 + j * es, wi = w0 + (i < 0 ? 0 : i) * ws, qi = q0 + (i < 0 ? 0 : i) * es;
-#pragma unroll
-        for (int a = 0; a < 5; ++a) cp_async_elem(ring.fs + ((slot * 8 + a) << 5) + lane, FS[a] + qj);
-#pragma unroll
-        for (int a = 5; a < 8; ++a) cp_async_elem(ring.fs + ((slot * 8 + a) << 5) + lane, FS[a] + wi);
-        cp_async_elem(ring.ds + ((slot * 2 + 0) << 5) + lane, DS[0] + qj);
-        cp_async_elem(ring.ds + ((slot * 2 + 1) << 5) + lane, DS[1] + qi);
-        cp_async_commit();
-      };
-      const int64_t T = n + 2;          // t = 0 .. n+1 covers rows i = n-1 .. -2
-      if (RING) {
-#pragma unroll
-        for (int j = 0; j < D - 1; ++j) {
-          if (j < T) issue_row(j, n - 1 - j);
-          else cp_async_commit();
-        }
-      }
-      float d1 = 0, d2 = 0;               // delta (or x_0) of rows i+1, i+2
-      F2 x1{0, 0}, x2{0, 0}, x3{0, 0}, x4{0, 0};   // new x of rows i+1 .. i+4
-      for (int64_t t = 0; t < T; ++t) {
-        const int64_t i = n - 1 - t;
-        float A[5], av, bv2, zv;
-        double fj, xo;
-        if (RING) {
-          const int64_t tp = t + D - 1;
-          if (tp < T) issue_row((int)(tp & (D - 1)), n - 1 - tp);
-          else cp_async_commit();
-          cp_async_wait<D - 1>();
-          const int sl = (int)(t & (D - 1));
-#pragma unroll
-          for (int a = 0; a < 5; ++a) A[a] = ring.getf(sl, a);
-          av = ring.getf(sl, 5); bv2 = ring.getf(sl, 6); zv = ring.getf(sl, 7);
-          fj = ring.getd(sl, 0); xo = ring.getd(sl, 1);
-        } else {
-          const int64_t j = i + 2 < n ? i + 2 : n - 1;
-          const int64_t qj = q0 + j * es, wi = w0 + (i < 0 ? 0 : i) * ws;
-          const int64_t qi = q0 + (i < 0 ? 0 : i) * es;
-#pragma unroll
-          for (int a = 0; a < 5; ++a) A[a] = (K == 1 && (a == 0 || a == 4)) ? 0.0f : ldro(A5[a] + qj);
-          av = p.fa[wi]; bv2 = p.fb[wi]; zv = p.z[wi];
-          fj = p.f[qj]; xo = p.x[qi];
-        }
-        F2 xn{0, 0};
-        if (i >= 0) {
-          float dv = fmaf(-av, d1, zv);
-          if (K == 2) dv = fmaf(-bv2, d2, dv);
-          d2 = d1;
-          d1 = dv;
-          if (first) {
-            xn = F2{dv, 0.0f};
-          } else {
-            const float dd = dv * up;                 // the correction in x's units
-            dmaxf = fmaxf(dmaxf, fabsf(dd));
-            const F2 xs = split(xo);
-            const F2 t1 = two_sum(xs.h, dd);
-            const F2 t2 = two_sum(t1.h, t1.l + xs.l);
-            xn = t2;
-          }
-          const double xv = f2d(xn.h) + f2d(xn.l);
-          p.x[q0 + i * es] = xv;
-          bad |= not_finite(xv);
-          xmax = max_abs(xmax, xv);
-        }
-        // residual of row j = i + 2: x_{j-2} = xn (row i), x_{j-1} = x1, x_j = x2,
-        // x_{j+1} = x3, x_{j+2} = x4
-        const int64_t j = i + 2;
-        if (j >= 0 && j < n) {
-          F2 sres = split(fj);
-          sub_prod(sres, A[2], x2);
-          if (j >= 1) sub_prod(sres, A[1], x1);
-          if (j + 1 < n) sub_prod(sres, A[3], x3);
-          if (K == 2) {
-            if (j >= 2) sub_prod(sres, A[0], xn);
-            if (j + 2 < n) sub_prod(sres, A[4], x4);
-          }
-          p.r[w0 + j * ws] = (sres.h + sres.l) * down;
-        }
-        x4 = x3; x3 = x2; x2 = x1; x1 = xn;
-      }
-      if (RING) cp_async_wait<0>();
-    }
-    if (bad) { st = BAND_ERR_NONFINITE; break; }
-    if (!first) {
-      k = pass;
-      if ((double)dmaxf <= p.rel_stop * xmax) break;
-    }
-    if (pass >= p.max_steps) break;
-    // ---- F: z = L^{-1} (2^-e r) with the stored factors -----------------------------
-    {
-      constexpr int D = kDepthF;
-      const Ring2<4, 0, D> ring{reinterpret_cast<float*>(stage), nullptr, lane};
-      const float* FS[4] = {p.r, pa, p.fg, p.fr};
-      auto issue_row = [&](int slot, int64_t i) {
-        const int64_t wi = w0 + i * ws, qi = q0 + i * es;
-        cp_async_elem(ring.fs + ((slot * 4 + 0) << 5) + lane, FS[0] + wi);
-        cp_async_elem(ring.fs + ((slot * 4 + 1) << 5) + lane, FS[1] + qi);
-        cp_async_elem(ring.fs + ((slot * 4 + 2) << 5) + lane, FS[2] + wi);
-        cp_async_elem(ring.fs + ((slot * 4 + 3) << 5) + lane, FS[3] + wi);
-        cp_async_commit();
-      };
-      if (RING) {
-#pragma unroll
-        for (int j = 0; j < D - 1; ++j) {
-          if (j < n) issue_row(j, j);
-          else cp_async_commit();
-        }
-      }
-      float z1 = 0, z2 = 0;
-      for (int64_t i = 0; i < n; ++i) {
-        float rv, av, gv, rr;
-        if (RING) {
-          const int64_t ip = i + D - 1;
-          if (ip < n) issue_row((int)(ip & (D - 1)), ip);
-          else cp_async_commit();
-          cp_async_wait<D - 1>();
-          const int sl = (int)(i & (D - 1));
-          rv = ring.getf(sl, 0); av = ring.getf(sl, 1); gv = ring.getf(sl, 2); rr = ring.getf(sl, 3);
-        } else {
-          const int64_t wi = w0 + i * ws;
-          rv = p.r[wi]; av = K == 2 ? ldro(pa + q0 + i * es) : 0.0f; gv = p.fg[wi]; rr = p.fr[wi];
-        }
-        const float ai = (K == 2 && i >= 2) ? av : 0.0f;
-        const float zv = fmaf(-z1, gv, fmaf(-z2, ai, rv)) * rr;
-        p.z[w0 + i * ws] = zv;
-        z2 = z1;
-        z1 = zv;
-      }
-      if (RING) cp_async_wait<0>();
-    }
-  }
-  if (p.steps) p.steps[s] = k;
-  set_status(p.status, s, st);
+// Thread t of an elementwise pass: system (the fastest index, for coalescing on
+// interleaved data) and chunk of kChunk rows.
+__device__ __forceinline__ bool chunk_of(const Layout& L, int64_t t, int64_t& s, int64_t& i0,
+                                         int64_t& i1) {
+  const int64_t nch = (L.n + kChunk - 1) / kChunk;
+  if (t >= L.nsys * nch) return false;
+  s = t % L.nsys;
+  const int64_t c = t / L.nsys;
+  const int64_t n = L.rows(s);
+  i0 = c * kChunk;
+  i1 = i0 + kChunk < n ? i0 + kChunk : n;
+  return i0 < n;
 }
 
-__global__ void __launch_bounds__(32 * kRefWarps) k_refine(const RefArgs p, int kmode) {
-  extern __shared__ __align__(16) unsigned char ref_stage[];
+// The elementwise passes load kBatch rows before using any of them, so that a thread
+// has several loads of each array in flight (one at a time, the passes ran at 40 % of
+// HBM bandwidth, bound by memory latency).  x and f are kept as float pairs in the
+// workspace during the iteration; x is assembled in FP64 once at the end.
+#ifndef REF_BATCH
+#define REF_BATCH 2
+#endif
+#ifndef REF_MINB
+#define REF_MINB 4
+#endif
+constexpr int kBatch = REF_BATCH;
+
+// Pass 0: the first right-hand side f rounded to FP32, f as a pair; max|f| per system.
+__global__ void __launch_bounds__(256) k_ref_start(const RefState p) {
+  int64_t s, i0, i1;
+  if (!chunk_of(p.L, (int64_t)blockIdx.x * blockDim.x + threadIdx.x, s, i0, i1)) return;
+  const int64_t q0 = p.L.base(s), es = p.L.stride();
+  double m = 0.0;
+  for (int64_t ib = i0; ib < i1; ib += kBatch) {
+    double fv[kBatch];
+#pragma unroll
+    for (int u = 0; u < kBatch; ++u) fv[u] = (ib + u < i1) ? p.f[q0 + (ib + u) * es] : 0.0;
+#pragma unroll
+    for (int u = 0; u < kBatch; ++u) {
+      if (ib + u < i1) {
+        const int64_t q = q0 + (ib + u) * es;
+        const F2 fp = split(fv[u]);
+        p.r32[q] = __double2float_rn(fv[u]);
+        p.fh[q] = fp.h;
+        p.fl[q] = fp.l;
+        m = max_abs(m, fv[u]);
+      }
+    }
+  }
+  atomicMax(p.fmax + s, (unsigned long long)__double_as_longlong(m));
+}
+
+// x += 2^e delta (first: x = delta, the unscaled first solve), with the maxima.
+__global__ void __launch_bounds__(256, REF_MINB) k_ref_update(const RefState p, int first) {
+  int64_t s, i0, i1;
+  if (!chunk_of(p.L, (int64_t)blockIdx.x * blockDim.x + threadIdx.x, s, i0, i1)) return;
+  if (p.done[s]) return;
+  const int64_t q0 = p.L.base(s), es = p.L.stride();
+  const float up = pow2f(p.fexp[s]);
+  float dm = 0.0f, xm = 0.0f;
+  bool nan_d = false, nan_x = false;
+  for (int64_t ib = i0; ib < i1; ib += kBatch) {
+    float dv[kBatch], hv[kBatch], lv[kBatch];
+#pragma unroll
+    for (int u = 0; u < kBatch; ++u) {
+      const bool in = ib + u < i1;
+      const int64_t q = q0 + (ib + u) * es;
+      dv[u] = in ? p.d32[q] : 0.0f;
+      hv[u] = (in && !first) ? p.xh[q] : 0.0f;
+      lv[u] = (in && !first) ? p.xl[q] : 0.0f;
+    }
+#pragma unroll
+    for (int u = 0; u < kBatch; ++u) {
+      if (ib + u >= i1) break;
+      const int64_t q = q0 + (ib + u) * es;
+      F2 xn;
+      if (first) {
+        xn = F2{dv[u], 0.0f};
+      } else {
+        const float dd = dv[u] * up;                  // exact: a power of two
+        nan_d |= (dd != dd);
+        dm = fmaxf(dm, fabsf(dd));
+        const F2 t1 = two_sum(hv[u], dd);
+        xn = two_sum(t1.h, t1.l + lv[u]);
+      }
+      p.xh[q] = xn.h;
+      p.xl[q] = xn.l;
+      nan_x |= !isfinite(xn.h);
+      xm = fmaxf(xm, fabsf(xn.h));
+    }
+  }
+  // a NaN wins the max (its bits order above every finite float and Inf)
+  if (!first) atomicMax(p.dmax + s, nan_d ? 0x7fc00000u : __float_as_uint(dm));
+  atomicMax(p.xmax + s, nan_x ? 0x7fc00000u : __float_as_uint(xm));
+}
+
+// r = f - A x in FP32 pairs (A exact in FP32); 2^-e r to r32.
+template <int K>
+__device__ __forceinline__ void residual_rows(const RefState& p, int64_t s, int64_t i0,
+                                              int64_t i1) {
+  const int64_t n = p.L.rows(s), q0 = p.L.base(s), es = p.L.stride();
+  const float down = pow2f(-p.fexp[s]);
+  float rm = 0.0f;
+  bool nan_r = false;
+  auto X = [&](int64_t j) -> F2 {
+    return (j >= 0 && j < n) ? F2{p.xh[q0 + j * es], p.xl[q0 + j * es]} : F2{0.0f, 0.0f};
+  };
+  F2 w0 = X(i0 - 2), w1 = X(i0 - 1), w2 = X(i0), w3 = X(i0 + 1);   // x_{i-2} .. x_{i+1}
+  for (int64_t ib = i0; ib < i1; ib += kBatch) {
+    F2 xv[kBatch], fv[kBatch];
+    float av[kBatch], bv[kBatch], cv[kBatch], dv[kBatch], ev[kBatch];
+#pragma unroll
+    for (int u = 0; u < kBatch; ++u) {
+      const int64_t i = ib + u;
+      const bool in = i < i1;
+      const int64_t q = q0 + (in ? i : i0) * es;
+      xv[u] = in ? X(i + 2) : F2{0.0f, 0.0f};
+      fv[u] = in ? F2{p.fh[q], p.fl[q]} : F2{0.0f, 0.0f};
+      cv[u] = in ? ldro(p.c + q) : 0.0f;
+      bv[u] = (in && i >= 1) ? ldro(p.b + q) : 0.0f;
+      dv[u] = (in && i + 1 < n) ? ldro(p.d + q) : 0.0f;
+      av[u] = (K == 2 && in && i >= 2) ? ldro(p.a + q) : 0.0f;
+      ev[u] = (K == 2 && in && i + 2 < n) ? ldro(p.e + q) : 0.0f;
+    }
+#pragma unroll
+    for (int u = 0; u < kBatch; ++u) {
+      const int64_t i = ib + u;
+      if (i >= i1) break;
+      const F2 w4 = xv[u];                            // x_{i+2}
+      F2 r = fv[u];
+      sub_prod(r, cv[u], w2);
+      sub_prod(r, bv[u], w1);
+      sub_prod(r, dv[u], w3);
+      if (K == 2) {
+        sub_prod(r, av[u], w0);
+        sub_prod(r, ev[u], w4);
+      }
+      const float rv = r.h + r.l;
+      p.r32[q0 + i * es] = rv * down;
+      nan_r |= (rv != rv);
+      rm = fmaxf(rm, fabsf(rv));
+      w0 = w1; w1 = w2; w2 = w3; w3 = w4;
+    }
+  }
+  atomicMax(p.rmax + s, nan_r ? 0x7fc00000u : __float_as_uint(rm));
+}
+
+// x in FP64 from its pair, for every system, at the end.
+__global__ void __launch_bounds__(256) k_ref_finish(const RefState p) {
+  int64_t s, i0, i1;
+  if (!chunk_of(p.L, (int64_t)blockIdx.x * blockDim.x + threadIdx.x, s, i0, i1)) return;
+  const int64_t q0 = p.L.base(s), es = p.L.stride();
+  for (int64_t ib = i0; ib < i1; ib += kBatch) {
+    float hv[kBatch], lv[kBatch];
+#pragma unroll
+    for (int u = 0; u < kBatch; ++u) {
+      const bool in = ib + u < i1;
+      const int64_t q = q0 + (ib + u) * es;
+      hv[u] = in ? p.xh[q] : 0.0f;
+      lv[u] = in ? p.xl[q] : 0.0f;
+    }
+#pragma unroll
+    for (int u = 0; u < kBatch; ++u)
+      if (ib + u < i1) p.x[q0 + (ib + u) * es] = f2d(hv[u]) + f2d(lv[u]);
+  }
+}
+
+__global__ void __launch_bounds__(256, REF_MINB) k_ref_residual(const RefState p, int kmode) {
+  int64_t s, i0, i1;
+  if (!chunk_of(p.L, (int64_t)blockIdx.x * blockDim.x + threadIdx.x, s, i0, i1)) return;
+  if (p.done[s]) return;
+  const int K = kmode ? kmode : p.L.kband(s);
+  if (K == 1) residual_rows<1>(p, s, i0, i1);
+  else residual_rows<2>(p, s, i0, i1);
+}
+
+// After step k's update (k corrections applied, k >= 0) and its residual: stop or go
+// on, and clear the maxima for the next step.  One thread per system.
+__global__ void __launch_bounds__(256) k_ref_decide(const RefState p, int k) {
+  const int64_t s = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (s >= p.L.nsys || p.done[s]) return;
+  int32_t st = -1;                              // -1: go on
+  const float xm = __uint_as_float(p.xmax[s]);
+  const float dm = __uint_as_float(p.dmax[s]);
+  const float rm = __uint_as_float(p.rmax[s]);
+  if (p.sst[s] != BAND_OK) st = p.sst[s];                       // the last solve failed
+  else if (!isfinite(xm) || !(dm == dm) || !(rm == rm) || isinf(rm)) st = BAND_ERR_NONFINITE;
+  else if (k >= 1 && (double)dm <= p.rel_stop * (double)xm) st = BAND_OK;   // converged
+  else if (rm == 0.0f || k >= p.max_steps) st = BAND_OK;         // exact, or the cap
+  if (st >= 0) {
+    p.done[s] = 1;
+    if (p.steps) p.steps[s] = p.sst[s] != BAND_OK ? (k > 0 ? k - 1 : 0) : k;
+    set_status(p.status, s, st);
+  }
+  p.xmax[s] = 0u;
+  p.dmax[s] = 0u;
+  p.rmax[s] = 0u;
+}
+
+__global__ void __launch_bounds__(256) k_ref_init(const RefState p) {
   const int64_t s = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   if (s >= p.L.nsys) return;
-  unsigned char* stage = ref_stage + (threadIdx.x >> 5) * kRefRingBytes;
-  const int K = kmode ? kmode : p.L.kband(s);
-  const bool ring = !p.L.offsets && p.L.ss == 1;
-  if (ring) {
-    if (K == 1) refine_one<1, true>(p, s, stage);
-    else refine_one<2, true>(p, s, stage);
-  } else {
-    if (K == 1) refine_one<1, false>(p, s, stage);
-    else refine_one<2, false>(p, s, stage);
-  }
+  const double fm = __longlong_as_double((long long)p.fmax[s]);
+  // 2^e ~ max|f| 2^-20: the scaled residuals stay far inside FP32's range
+  const int ex = (int)((unsigned)(__double_as_longlong(fm) >> 52) & 0x7ffu) - 1023;
+  p.fexp[s] = ex - 20;
 }
 
+// ----------------------------------------------------------------- workspace
 struct RefWs {
-  float *fa, *fb, *fg, *fr, *z, *r;
+  float *r32, *d32, *xh, *xl, *fh, *fl;
+  int32_t *done, *sst, *fexp;
+  unsigned long long* fmax;
+  unsigned int *xmax, *dmax, *rmax;
+  void* solve;
+  size_t solve_bytes;
 };
 RefWs carve_refine(const band_desc* d, void* base, size_t* bytes) {
   Carve c(base);
-  RefWs w;
-  const size_t rows = (size_t)spill_rows(d) * sizeof(float);
-  w.fa = (float*)c.take(rows);
-  w.fb = (float*)c.take(rows);
-  w.fg = (float*)c.take(rows);
-  w.fr = (float*)c.take(rows);
-  w.z = (float*)c.take(rows);
-  w.r = (float*)c.take(rows);
+  RefWs w{};
+  const size_t span = (size_t)layout_of(d).extent;
+  const size_t ns = (size_t)(d->nsys > 0 ? d->nsys : 1);
+  w.r32 = (float*)c.take(span * sizeof(float));
+  w.d32 = (float*)c.take(span * sizeof(float));
+  w.xh = (float*)c.take(span * sizeof(float));
+  w.xl = (float*)c.take(span * sizeof(float));
+  w.fh = (float*)c.take(span * sizeof(float));
+  w.fl = (float*)c.take(span * sizeof(float));
+  w.done = (int32_t*)c.take(ns * sizeof(int32_t));
+  w.sst = (int32_t*)c.take(ns * sizeof(int32_t));
+  w.fexp = (int32_t*)c.take(ns * sizeof(int32_t));
+  w.fmax = (unsigned long long*)c.take(ns * sizeof(unsigned long long));
+  w.xmax = (unsigned int*)c.take(ns * sizeof(unsigned int));
+  w.dmax = (unsigned int*)c.take(ns * sizeof(unsigned int));
+  w.rmax = (unsigned int*)c.take(ns * sizeof(unsigned int));
+  size_t sb = 0;
+  carve_solve(d, d->hbw ? BAND_AUTO_NUMERIC : (d->half_bw == 1 ? BAND_NTDM : BAND_NPDM), nullptr,
+              &sb);
+  w.solve = c.take(sb);
+  w.solve_bytes = sb;
   *bytes = c.size();
   return w;
 }
@@ -411,17 +376,52 @@ extern "C" band_status band_refine_solve(const band_desc* desc32, const void* co
   carve_refine(desc32, nullptr, &need);
   if (!ws || ws_bytes < need) return BAND_ERR_WORKSPACE;
   const RefWs w = carve_refine(desc32, ws, &need);
-  RefArgs p{layout_of(desc32), spill_of(desc32),
-            (const float*)diag32[0], (const float*)diag32[1], (const float*)diag32[2],
-            (const float*)diag32[3], (const float*)diag32[4], f, x,
-            w.fa, w.fb, w.fg, w.fr, w.z, w.r, rel_stop, max_steps, steps, sys_status};
+  cudaStream_t st = static_cast<cudaStream_t>(stream);
   const int kmode = desc32->hbw ? 0 : desc32->half_bw;
-  const size_t smem = (size_t)kRefWarps * kRefRingBytes;
-  if (cudaFuncSetAttribute(k_refine, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) !=
-      cudaSuccess)
+  const int32_t method = kmode == 0 ? BAND_AUTO_NUMERIC : (kmode == 1 ? BAND_NTDM : BAND_NPDM);
+  RefState p{};
+  p.L = layout_of(desc32);
+  p.a = (const float*)diag32[0]; p.b = (const float*)diag32[1]; p.c = (const float*)diag32[2];
+  p.d = (const float*)diag32[3]; p.e = (const float*)diag32[4];
+  p.f = f;
+  p.x = x;
+  p.r32 = w.r32; p.d32 = w.d32;
+  p.xh = w.xh; p.xl = w.xl; p.fh = w.fh; p.fl = w.fl;
+  p.done = w.done; p.sst = w.sst; p.fexp = w.fexp;
+  p.xmax = w.xmax; p.dmax = w.dmax; p.rmax = w.rmax; p.fmax = w.fmax;
+  p.steps = steps;
+  p.status = sys_status;
+  p.rel_stop = rel_stop;
+  p.max_steps = max_steps;
+  const size_t ns = (size_t)desc32->nsys;
+  // done, sst, fexp, then the maxima are contiguous from w.done on: clear them at once
+  if (cudaMemsetAsync(w.done, 0, (size_t)((char*)w.rmax - (char*)w.done) + ns * sizeof(unsigned),
+                      st) != cudaSuccess)
     return BAND_ERR_CUDA;
-  const int tb = 32 * kRefWarps;
-  k_refine<<<(unsigned)((desc32->nsys + tb - 1) / tb), tb, smem,
-             static_cast<cudaStream_t>(stream)>>>(p, kmode);
+  // the correction solve: A32 d32 = r32, on the schedule the descriptor asks for
+  DirectReq req;
+  const band_status v = make_direct(desc32, method, diag32, w.r32, w.d32, w.sst, w.solve,
+                                    w.solve_bytes, &req);
+  if (v != BAND_OK) return v;
+  req.d32.skip = w.done;
+  auto solve = [&]() -> cudaError_t {
+    return req.two_sided ? launch_twisted<float>(req.d32, req.kmode, st)
+                         : launch_direct<float>(req.d32, req.kmode, st);
+  };
+  const int64_t nch = (desc32->n + kChunk - 1) / kChunk;
+  const unsigned g_elem = (unsigned)((desc32->nsys * nch + 255) / 256);
+  const unsigned g_sys = (unsigned)((desc32->nsys + 255) / 256);
+  k_ref_start<<<g_elem, 256, 0, st>>>(p);
+  k_ref_init<<<g_sys, 256, 0, st>>>(p);
+  if (cudaGetLastError() != cudaSuccess || solve() != cudaSuccess) return BAND_ERR_CUDA;
+  // step k: apply the k-th solution (k = 0: x = delta), residual, decide, solve
+  for (int k = 0; k <= max_steps; ++k) {
+    k_ref_update<<<g_elem, 256, 0, st>>>(p, k == 0 ? 1 : 0);
+    k_ref_residual<<<g_elem, 256, 0, st>>>(p, kmode);
+    k_ref_decide<<<g_sys, 256, 0, st>>>(p, k);
+    if (cudaGetLastError() != cudaSuccess) return BAND_ERR_CUDA;
+    if (k < max_steps && solve() != cudaSuccess) return BAND_ERR_CUDA;
+  }
+  k_ref_finish<<<g_elem, 256, 0, st>>>(p);
   return cuda_status(cudaGetLastError());
 }

@@ -78,6 +78,7 @@ __device__ __forceinline__ bool forward_row(const DirectArgs<T>& p, int64_t i, i
 template <typename T, int K>
 __device__ __forceinline__ void direct_one(const DirectArgs<T>& p, int64_t t, void* stage) {
   const int64_t s = p.L.sys(t);     // t: position in the batch, s: the system id
+  if (p.skip && p.skip[s]) return;
 
   const int64_t n = p.L.rows(s);
   if (n <= 0) {
@@ -210,6 +211,7 @@ template <typename T, int K>
 __device__ __forceinline__ void twisted_one(const DirectArgs<T>& p, int64_t t, bool active,
                                             void* stage) {
   const int64_t s = active ? p.L.sys(t) : 0;   // t: position in the batch, s: system id
+  if (active && p.skip && p.skip[s]) active = false;   // every lane still reaches the shuffles
 
   const int lane = (int)(threadIdx.x & 31);
   const bool bottom = lane >= 16;
