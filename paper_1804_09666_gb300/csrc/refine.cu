@@ -4,7 +4,7 @@
 //   x_1 = solve32(f)                    (f rounded to FP32)
 //   step k >= 1:  r = f - A x_k         (A = the exact values of the FP32 diagonals)
 //                 x_{k+1} = x_k + 2^e solve32(2^-e r)
-// until max|x_{k+1} - x_k| <= rel_stop max|x_{k+1}|, max|r| = 0, or max_steps steps.
+// until max|x_{k+1} - x_k| <= rel_stop max|x_{k+1}| or max_steps steps.
 // solve32 is NPDM / NTDM (Veneva & Ayriyan, Sec. 1) in single precision, run by the
 // library's sweep kernels on the schedule the descriptor asks for (two-sided by
 // default); 2^e is a power of two fixed per system from max|f| (exact scaling that
@@ -12,8 +12,8 @@
 //
 // Each step is made of passes that the GPU runs at full width:
 //   update    x += 2^e delta (elementwise), with max|2^e delta| and max|x| per system
+//   decide    per system: stop (converged, non-finite, zero pivot, cap) or go on
 //   residual  r = f - A x (a five-point stencil, elementwise), written as 2^-e r in FP32
-//   decide    per system: stop (converged, exact, non-finite, zero pivot, cap) or go on
 //   solve     delta = solve32(2^-e r) for the systems still going
 // GB300 runs FP64 at 1/64 of the FP32 rate, so x, f, the residual and the update are
 // pairs of FP32 numbers handled with error-free transformations (TwoProd with an FMA,
@@ -282,8 +282,10 @@ __global__ void __launch_bounds__(256, REF_MINB) k_ref_residual(const RefState p
   else residual_rows<2>(p, s, i0, i1);
 }
 
-// After step k's update (k corrections applied, k >= 0) and its residual: stop or go
-// on, and clear the maxima for the next step.  One thread per system.
+// After step k's update (k corrections applied, k >= 0): stop or go on, and clear the
+// maxima for the next step.  rmax is that of the residual the k-th correction was
+// solved from (k >= 1): zero means the previous x solved the system exactly (the
+// correction is then 0 and the step converged anyway).  One thread per system.
 __global__ void __launch_bounds__(256) k_ref_decide(const RefState p, int k) {
   const int64_t s = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   if (s >= p.L.nsys || p.done[s]) return;
@@ -294,7 +296,7 @@ __global__ void __launch_bounds__(256) k_ref_decide(const RefState p, int k) {
   if (p.sst[s] != BAND_OK) st = p.sst[s];                       // the last solve failed
   else if (!isfinite(xm) || !(dm == dm) || !(rm == rm) || isinf(rm)) st = BAND_ERR_NONFINITE;
   else if (k >= 1 && (double)dm <= p.rel_stop * (double)xm) st = BAND_OK;   // converged
-  else if (rm == 0.0f || k >= p.max_steps) st = BAND_OK;         // exact, or the cap
+  else if (k >= p.max_steps) st = BAND_OK;                       // the cap
   if (st >= 0) {
     p.done[s] = 1;
     if (p.steps) p.steps[s] = p.sst[s] != BAND_OK ? (k > 0 ? k - 1 : 0) : k;
@@ -414,13 +416,15 @@ extern "C" band_status band_refine_solve(const band_desc* desc32, const void* co
   k_ref_start<<<g_elem, 256, 0, st>>>(p);
   k_ref_init<<<g_sys, 256, 0, st>>>(p);
   if (cudaGetLastError() != cudaSuccess || solve() != cudaSuccess) return BAND_ERR_CUDA;
-  // step k: apply the k-th solution (k = 0: x = delta), residual, decide, solve
+  // step k: apply the k-th solution (k = 0: x = delta), decide, and for the systems
+  // that go on the residual and the next solve
   for (int k = 0; k <= max_steps; ++k) {
     k_ref_update<<<g_elem, 256, 0, st>>>(p, k == 0 ? 1 : 0);
-    k_ref_residual<<<g_elem, 256, 0, st>>>(p, kmode);
     k_ref_decide<<<g_sys, 256, 0, st>>>(p, k);
     if (cudaGetLastError() != cudaSuccess) return BAND_ERR_CUDA;
-    if (k < max_steps && solve() != cudaSuccess) return BAND_ERR_CUDA;
+    if (k == max_steps) break;
+    k_ref_residual<<<g_elem, 256, 0, st>>>(p, kmode);
+    if (cudaGetLastError() != cudaSuccess || solve() != cudaSuccess) return BAND_ERR_CUDA;
   }
   k_ref_finish<<<g_elem, 256, 0, st>>>(p);
   return cuda_status(cudaGetLastError());
