@@ -51,7 +51,7 @@ def parse():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-graph", action="store_true")
     ap.add_argument("--no-extras", action="store_true",
-                    help="skip the ragged, precision and adjoint workloads (N = 1 only)")
+                    help="skip the ragged, precision, adjoint and SIP workloads (N = 1 only)")
     return ap.parse_args()
 
 
@@ -542,6 +542,32 @@ def precision_workload(dev):
     return out
 
 
+def sip_workload(dev):
+    """SIP on 4096 dominant PD systems of n = 1024 (cfg0's recipe): Algorithm 1 with the
+    exact ILU(0) substitutions, and with Hotelling-Bodewig inverses kept to 5
+    diagonals (ILU(0), the two HB iterations and the correction-form updates)."""
+    import torch
+    import paper_1804_09666_gb300 as band
+    nsys, n = 4096, 1024
+    B = synth.cfg0(nsys=nsys, n=n, seed_salt=7)
+    d = {q: torch.from_numpy(B[q]).to(dev).view(n, nsys) for q in "abcdef"}
+    xt = torch.from_numpy(B["x_true"]).to(dev).view(n, nsys)
+    units = n * nsys
+    out = {"workload": "4096 dominant PD systems, n = 1024, tol 1e-10", "unit": UNIT}
+    for name, width in (("algorithm1_exact", 0), ("hb_w5", 5)):
+        res = {}
+
+        def run():
+            res["x"], res["it"], res["rs"], res["st"] = band.sip(
+                *(d[q] for q in "abcdef"), tol=1e-10, max_it=200, width=width)
+        ms = _time(run)
+        err = float(((res["x"] - xt).abs().amax(0) / xt.abs().amax(0)).max())
+        out[name] = {"value": units / (ms * 1e-3), "ms": ms,
+                     "iters_mean": float(res["it"].float().mean()),
+                     "status_not_ok": int((res["st"] != 0).sum()), "max_rel_err": err}
+    return out
+
+
 def adjoint_workload(dev):
     """4096 PD systems of n = 1024: NPDM solve plus the adjoint (all six gradients)."""
     import torch
@@ -672,7 +698,7 @@ def main():
             "fp64_fma_per_s": fma_rate}
     if rank == 0 and world == 1 and not args.no_extras and args.grid == GRID:
         line["workloads"] = {"ragged": ragged_workload(dev), "precision": precision_workload(dev),
-                             "adjoint": adjoint_workload(dev)}
+                             "adjoint": adjoint_workload(dev), "sip": sip_workload(dev)}
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         line["cpu_baseline"] = cpu_baseline(W)
     if rank == 0:
