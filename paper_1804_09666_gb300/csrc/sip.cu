@@ -7,6 +7,7 @@
 // l_ik = a_ik / u_kk and a_ij -= l_ik u_kj for j > k in the pattern of row i.  For
 // this pattern nothing is dropped, so L (unit; l2 = L[i][i-2], l1 = L[i][i-1]) and
 // U (u0 = U[i][i], u1 = U[i][i+1], u2 = U[i][i+2] = e_i) are the exact LU factors.
+#include <algorithm>
 #include <mutex>
 #include <utility>
 #include <vector>
@@ -117,6 +118,240 @@ __global__ void __launch_bounds__(64) k_hb(const HbArgs p) {
   if (p.hb_iters) p.hb_iters[s] = it;
   // a capped HB iteration still gives usable approximate inverses; SIP decides
   if (st == BAND_ERR_NONFINITE) set_status(p.status, s, st);
+}
+
+// ---------------------------------------------------------------------------
+// SIP with Hotelling-Bodewig inverses, one block per system, the whole system in shared
+// memory.  Both halves of the method are row-parallel: an HB iteration computes
+// P = M X for every row from the current X, then X <- 2X - X P for every row (each row
+// of X_new needs only its own row of X and w rows of P); an SIP update applies the
+// banded matrices: r = f - A x, y = L~^{-1} r, x <- x + U~^{-1} y.  The threads of the
+// block take rows, the passes are separated by block barriers, and each system stops
+// on its own (the block's own reductions), so no system waits for another.  The
+// arithmetic and its order per row are those of k_hb / sip_hb, which run the same
+// iterations with one thread per system for systems too large for shared memory.
+// ---------------------------------------------------------------------------
+constexpr int kHbThreads = 256;
+
+struct HbBlockSm {
+  double *a, *b, *c, *d, *e, *f;   // n each
+  double *XL, *XU;                 // w x n each (diagonal j of row t at j * n + t)
+  double *P, *m1, *m2, *m0;        // HB scratch: P (w x n) and M's entries along the sweep
+  double *x, *r, *y;               // SIP scratch (over the HB scratch)
+};
+
+// Shared-memory doubles per row for width w: A and f, both inverses, and the larger of
+// the two scratch sets.
+__host__ __device__ inline int64_t hb_block_words_per_row(int w) {
+  const int64_t scratch = (w + 3) > 3 ? (w + 3) : 3;
+  return 6 + 2 * (int64_t)w + scratch;
+}
+
+// One HB inversion in shared memory, sweep coordinates t = 0 .. n-1 (M lower in t):
+// X <- X (2I - M X) truncated to w diagonals from X_0 = diag(M)^{-1}.  Returns the
+// status for the system (OK, NOT_CONVERGED at the cap: usable, NONFINITE).
+template <int W>
+__device__ inline int32_t hb_block(const HbBlockSm& S, double* X, int64_t n, int max_it,
+                                   double tol, double* red, int* iters) {
+  constexpr int w = W;
+  for (int64_t t = threadIdx.x; t < n; t += blockDim.x) {
+    X[t] = 1.0 / S.m0[t];
+    for (int j = 1; j < w; ++j) X[j * n + t] = 0.0;
+  }
+  __syncthreads();
+  int it = 0;
+  int32_t st = BAND_ERR_NOT_CONVERGED;
+  while (it < max_it) {
+    // P = M X on the band: P_j[t] = m0 X_j[t] + m1 X_{j-1}[t-1] + m2 X_{j-2}[t-2]
+    for (int64_t t = threadIdx.x; t < n; t += blockDim.x) {
+      const double mm0 = S.m0[t];
+      const double mm1 = t >= 1 ? S.m1[t] : 0.0;
+      const double mm2 = t >= 2 ? S.m2[t] : 0.0;
+      for (int j = 0; j < w; ++j) {
+        double v = mm0 * X[j * n + t];
+        if (j >= 1 && t >= 1) v = fma(mm1, X[(j - 1) * n + t - 1], v);
+        if (j >= 2 && t >= 2) v = fma(mm2, X[(j - 2) * n + t - 2], v);
+        S.P[j * n + t] = v;
+      }
+    }
+    __syncthreads();
+    // X_new_j[t] = 2 X_j[t] - sum_{k<=j} X_k[t] P_{j-k}[t-k]; a row needs only its own X
+    double dmax = 0.0, xmax = 0.0;
+    bool nan = false;
+    for (int64_t t = threadIdx.x; t < n; t += blockDim.x) {
+      double xo[W], xn[W];
+#pragma unroll
+      for (int j = 0; j < w; ++j) xo[j] = X[j * n + t];
+#pragma unroll
+      for (int j = 0; j < w; ++j) {
+        double acc = 2.0 * xo[j];
+#pragma unroll
+        for (int k = 0; k <= j; ++k) {
+          if (t - k < 0) break;
+          acc = fma(-xo[k], S.P[(j - k) * n + t - k], acc);
+        }
+        xn[j] = acc;
+        nan |= (acc != acc);
+        dmax = fmax(dmax, fabs(acc - xo[j]));
+        xmax = fmax(xmax, fabs(xo[j]));
+      }
+#pragma unroll
+      for (int j = 0; j < w; ++j) X[j * n + t] = xn[j];
+    }
+    const double dm = block_max(nan ? INFINITY : dmax, red);
+    const double xm = block_max(xmax, red);
+    ++it;
+    if (!(dm < INFINITY)) { st = BAND_ERR_NONFINITE; break; }
+    if (dm <= tol * xm) { st = BAND_OK; break; }
+  }
+  __syncthreads();
+  *iters = it;
+  return st;
+}
+
+struct HbBlockArgs {
+  int hb_max_it;
+  double hb_tol;
+  int64_t smem_rows;     // systems with more rows are left to the one-thread path
+};
+
+template <int W>
+__global__ void __launch_bounds__(kHbThreads) k_sip_hb_block(const SipArgs p, const HbBlockArgs h) {
+  extern __shared__ double hb_smem[];
+  __shared__ double red[kHbThreads / 32];
+  constexpr int w = W;
+  for (int64_t s = blockIdx.x; s < p.L.nsys; s += gridDim.x) {
+    const int64_t n = p.L.rows(s);
+    if (n > h.smem_rows) continue;
+    if (p.status && p.status[s] != BAND_OK) {        // ILU(0) met a zero pivot
+      if (threadIdx.x == 0) {
+        if (p.iters) p.iters[s] = 0;
+        if (p.resid) p.resid[s] = NAN;
+      }
+      continue;
+    }
+    const int64_t q0 = p.L.base(s), es = p.L.stride();
+    const int64_t w0 = p.W.base(s), ws = p.W.stride();
+    HbBlockSm S;
+    S.a = hb_smem; S.b = S.a + n; S.c = S.b + n; S.d = S.c + n; S.e = S.d + n; S.f = S.e + n;
+    S.XL = S.f + n; S.XU = S.XL + w * n;
+    S.P = S.XU + w * n; S.m0 = S.P + w * n; S.m1 = S.m0 + n; S.m2 = S.m1 + n;
+    S.x = S.P; S.r = S.x + n; S.y = S.r + n;
+    for (int64_t i = threadIdx.x; i < n; i += blockDim.x) {
+      const Row A = load_row(p, q0 + i * es, i, n);
+      S.a[i] = A.a; S.b[i] = A.b; S.c[i] = A.c; S.d[i] = A.d; S.e[i] = A.e; S.f[i] = A.f;
+      // L along t = i: (1, l1, l2)
+      S.m0[i] = 1.0;
+      S.m1[i] = p.l1[w0 + i * ws];
+      S.m2[i] = p.l2[w0 + i * ws];
+    }
+    __syncthreads();
+    int itl = 0, itu = 0;
+    const int32_t stl = hb_block<W>(S, S.XL, n, h.hb_max_it, h.hb_tol, red, &itl);
+    // U along t = n-1-i: (u0, u1, e)
+    for (int64_t i = threadIdx.x; i < n; i += blockDim.x) {
+      const int64_t t = n - 1 - i;
+      S.m0[t] = p.u0[w0 + i * ws];
+      S.m1[t] = p.u1[w0 + i * ws];
+      S.m2[t] = S.e[i];
+    }
+    __syncthreads();
+    const int32_t stu = hb_block<W>(S, S.XU, n, h.hb_max_it, h.hb_tol, red, &itu);
+    if (stl == BAND_ERR_NONFINITE || stu == BAND_ERR_NONFINITE) {
+      if (threadIdx.x == 0) {
+        if (p.iters) p.iters[s] = 0;
+        if (p.resid) p.resid[s] = NAN;
+        set_status(p.status, s, BAND_ERR_NONFINITE);
+      }
+      __syncthreads();
+      continue;
+    }
+    // SIP in correction form from x^0 = 0
+    for (int64_t i = threadIdx.x; i < n; i += blockDim.x) S.x[i] = 0.0;
+    __syncthreads();
+    int k = 0;
+    double rn = 0.0;
+    int32_t st = BAND_ERR_NOT_CONVERGED;
+    for (;;) {
+      double loc = 0.0;
+      bool nan = false;
+      for (int64_t i = threadIdx.x; i < n; i += blockDim.x) {
+        const double xm2 = i >= 2 ? S.x[i - 2] : 0.0, xm1 = i >= 1 ? S.x[i - 1] : 0.0;
+        const double xp1 = i + 1 < n ? S.x[i + 1] : 0.0, xp2 = i + 2 < n ? S.x[i + 2] : 0.0;
+        double ax = S.c[i] * S.x[i];
+        ax = fma(S.a[i], xm2, ax);
+        ax = fma(S.b[i], xm1, ax);
+        ax = fma(S.d[i], xp1, ax);
+        ax = fma(S.e[i], xp2, ax);
+        const double r = S.f[i] - ax;
+        S.r[i] = r;
+        nan |= (r != r);
+        loc = fmax(loc, fabs(r));
+      }
+      rn = block_max(nan ? INFINITY : loc, red);     // ends with a barrier: r complete
+      if (!(rn < INFINITY)) { rn = NAN; st = BAND_ERR_NONFINITE; break; }
+      if (rn < p.tol) { st = BAND_OK; break; }
+      if (k >= p.max_it) break;
+      // y = L~^{-1} r (lower band along t = i)
+      for (int64_t t = threadIdx.x; t < n; t += blockDim.x) {
+        double yv = 0.0;
+#pragma unroll
+        for (int j = 0; j < w; ++j)
+          if (t - j >= 0) yv = fma(S.XL[j * n + t], S.r[t - j], yv);
+        S.y[t] = yv;
+      }
+      __syncthreads();
+      // x += U~^{-1} y (row i of U~^{-1} is row t = n-1-i of X_U: entries at i .. i+w-1)
+      for (int64_t i = threadIdx.x; i < n; i += blockDim.x) {
+        const int64_t t = n - 1 - i;
+        double acc = 0.0;
+#pragma unroll
+        for (int j = 0; j < w; ++j)
+          if (i + j < n) acc = fma(S.XU[j * n + t], S.y[i + j], acc);
+        S.x[i] = S.x[i] + acc;
+      }
+      __syncthreads();
+      ++k;
+    }
+    for (int64_t i = threadIdx.x; i < n; i += blockDim.x) p.x[q0 + i * es] = S.x[i];
+    if (threadIdx.x == 0) {
+      if (p.iters) p.iters[s] = k;
+      if (p.resid) p.resid[s] = rn;
+      set_status(p.status, s, st);
+    }
+    __syncthreads();
+  }
+}
+
+template <int W>
+cudaError_t launch_hb_w(const SipArgs& sa, const HbBlockArgs& h, size_t smem, int64_t nsys,
+                        cudaStream_t st) {
+  const cudaError_t e = tail_prepare((const void*)k_sip_hb_block<W>);
+  if (e != cudaSuccess) return e;
+  int dev = 0, nsm = 0;
+  cudaGetDevice(&dev);
+  cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev);
+  // as many blocks as fit on the SMs at once (227 KiB of shared memory per SM)
+  const int64_t per_sm = std::max<int64_t>(1, (int64_t)(227 << 10) / (int64_t)(smem + 1024));
+  int64_t grid = (int64_t)(nsm > 0 ? nsm : 1) * per_sm;
+  if (grid > nsys) grid = nsys;
+  k_sip_hb_block<W><<<(unsigned)grid, kHbThreads, smem, st>>>(sa, h);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_sip_hb_block(const SipArgs& sa, int width, int hb_max_it, double hb_tol,
+                                size_t smem, int64_t nsys, cudaStream_t st) {
+  HbBlockArgs h{hb_max_it, hb_tol, (int64_t)(smem / ((size_t)hb_block_words_per_row(width) * sizeof(double)))};
+  switch (width) {
+    case 1: return launch_hb_w<1>(sa, h, smem, nsys, st);
+    case 2: return launch_hb_w<2>(sa, h, smem, nsys, st);
+    case 3: return launch_hb_w<3>(sa, h, smem, nsys, st);
+    case 4: return launch_hb_w<4>(sa, h, smem, nsys, st);
+    case 5: return launch_hb_w<5>(sa, h, smem, nsys, st);
+    case 6: return launch_hb_w<6>(sa, h, smem, nsys, st);
+    case 7: return launch_hb_w<7>(sa, h, smem, nsys, st);
+    default: return launch_hb_w<8>(sa, h, smem, nsys, st);
+  }
 }
 
 // Algorithm 1 with exact substitutions, first update on the two-sided schedule: 16
@@ -297,6 +532,13 @@ extern "C" band_status band_sip(const band_desc* desc, const void* const diag[5]
   if (width > 0) {
     k_ilu0<<<g128, 128, 0, st>>>(sa);
     if (cudaGetLastError() != cudaSuccess) return BAND_ERR_CUDA;
+    // systems that fit in shared memory: one block each, row-parallel
+    const size_t per_row = (size_t)hb_block_words_per_row(width) * sizeof(double);
+    if ((size_t)desc->n * per_row <= kTailSmemMax) {
+      const cudaError_t e = launch_sip_hb_block(sa, width, hb_max_it, hb_tol,
+                                                (size_t)desc->n * per_row, desc->nsys, st);
+      return cuda_status(e);
+    }
     for (int upper = 0; upper < 2; ++upper) {
       HbArgs h{};
       h.L = sa.L;
