@@ -252,10 +252,10 @@ class DeviceSet:
 
     def kernels_per_step(self):
         """Kernels band_solve_batch launches for this plan: the batched sweep, the
-        symbolic fix-up when a symbolic solve is present, the SIP tail when a SIP solve
-        is present."""
+        symbolic fix-up when a symbolic solve is present, and for SIP solves the
+        residual, decision and tail passes."""
         kinds = {k for k, _ in self.spec_methods}
-        return 1 + int(bool(kinds & {"spdm", "stdm"})) + int("sip" in kinds)
+        return 1 + int(bool(kinds & {"spdm", "stdm"})) + 3 * int("sip" in kinds)
 
 
 def e2e_serial(D, steps, world):

@@ -123,6 +123,22 @@ __global__ void __launch_bounds__(64) k_symbolic_batch(const __grid_constant__ S
     symbolic_one(p, p.fix_list[item], mem);
 }
 
+// the deferred residual and decision of the SIP problems (blockIdx.y: the problem)
+__global__ void __launch_bounds__(256) k_sip_resid_batch(const __grid_constant__ TailTable t) {
+  const SipArgs& p = t.it[blockIdx.y];
+  const int64_t idx = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  const int64_t nch = (p.L.n + kResChunk - 1) / kResChunk;
+  if (idx >= p.L.nsys * nch) return;
+  const int64_t s = idx % p.L.nsys;
+  if (p.pend[s]) sip_resid_chunk(p, s, idx / p.L.nsys);
+}
+
+__global__ void __launch_bounds__(256) k_sip_decide_batch(const __grid_constant__ TailTable t) {
+  const SipArgs& p = t.it[blockIdx.y];
+  const int64_t s = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (s < p.L.nsys) sip_decide_one(p, s);
+}
+
 __global__ void __launch_bounds__(kTailThreads) k_sip_tail_batch(const __grid_constant__ TailTable t) {
   __shared__ Aff sh[kTailThreads];
   __shared__ double red[kTailThreads / 32];
@@ -181,6 +197,9 @@ extern "C" band_status band_solve_batch(const band_problem* in, int32_t count, v
   std::memset(&tail, 0, sizeof tail);
   void* counters[BAND_MAX_BATCH];
   int ncounters = 0;
+  void* pend_clear[BAND_MAX_BATCH];     // SIP: per-system max|r| and pending flags
+  size_t pend_bytes[BAND_MAX_BATCH];
+  int npend = 0;
   int64_t warps = 0, slots = 0;
   for (int32_t i = 0; i < count; ++i) {
     const band_problem& q = probs[i];
@@ -229,6 +248,8 @@ extern "C" band_status band_solve_batch(const band_problem* in, int32_t count, v
       b.two_sided = 0;
       b.u.sip = sa;
       counters[ncounters++] = sa.tail_count;
+      pend_clear[npend] = sa.rn_sys;
+      pend_bytes[npend++] = (size_t)((char*)(sa.pend + q.desc->nsys) - (char*)sa.rn_sys);
       tail.it[tail.count++] = sa;
     } else {
       return BAND_ERR_ARG;
@@ -244,6 +265,8 @@ extern "C" band_status band_solve_batch(const band_problem* in, int32_t count, v
   for (int i = 0; i < ncounters; ++i)
     if (cudaMemsetAsync(counters[i], 0, sizeof(unsigned long long), st) != cudaSuccess)
       return BAND_ERR_CUDA;
+  for (int i = 0; i < npend; ++i)
+    if (cudaMemsetAsync(pend_clear[i], 0, pend_bytes[i], st) != cudaSuccess) return BAND_ERR_CUDA;
   const size_t smem = (size_t)kBatchWarps * (size_t)t.stage_bytes;
   k_batch<<<(unsigned)((warps + kBatchWarps - 1) / kBatchWarps), 32 * kBatchWarps, smem, st>>>(t);
   if (cudaGetLastError() != cudaSuccess) return BAND_ERR_CUDA;
@@ -252,6 +275,15 @@ extern "C" band_status band_solve_batch(const band_problem* in, int32_t count, v
     if (cudaGetLastError() != cudaSuccess) return BAND_ERR_CUDA;
   }
   if (tail.count > 0) {
+    int64_t cells = 0, nmax = 0;
+    for (int j = 0; j < tail.count; ++j) {
+      const Layout& L = tail.it[j].L;
+      cells = std::max(cells, L.nsys * ((L.n + kResChunk - 1) / kResChunk));
+      nmax = std::max(nmax, L.nsys);
+    }
+    k_sip_resid_batch<<<dim3((unsigned)((cells + 255) / 256), (unsigned)tail.count), 256, 0, st>>>(tail);
+    k_sip_decide_batch<<<dim3((unsigned)((nmax + 255) / 256), (unsigned)tail.count), 256, 0, st>>>(tail);
+    if (cudaGetLastError() != cudaSuccess) return BAND_ERR_CUDA;
     int dev = 0, nsm = 0;
     cudaGetDevice(&dev);
     cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev);

@@ -362,6 +362,19 @@ __global__ void __launch_bounds__(128) k_sip_two(const SipArgs p) {
   sip_two_sided(p, t, t < p.L.nsys);
 }
 
+__global__ void __launch_bounds__(256) k_sip_resid(const SipArgs p) {
+  const int64_t idx = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  const int64_t nch = (p.L.n + kResChunk - 1) / kResChunk;
+  if (idx >= p.L.nsys * nch) return;
+  const int64_t t = idx % p.L.nsys;
+  if (p.pend[t]) sip_resid_chunk(p, t, idx / p.L.nsys);
+}
+
+__global__ void __launch_bounds__(256) k_sip_decide(const SipArgs p) {
+  const int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (t < p.L.nsys) sip_decide_one(p, t);
+}
+
 __global__ void __launch_bounds__(128) k_ilu0(const SipArgs p) {
   const int64_t s = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   if (s >= p.L.nsys) return;
@@ -403,6 +416,8 @@ SipWs carve_sip(const band_desc* d, int32_t width, void* base, size_t* bytes) {
   w.tail_count = (unsigned long long*)c.take(sizeof(unsigned long long));
   w.tail_list = (int64_t*)c.take(sizeof(int64_t) * ns);
   w.tail_rn = (double*)c.take(sizeof(double) * ns);
+  w.rn_sys = (unsigned long long*)c.take(sizeof(unsigned long long) * ns);
+  w.pend = (int32_t*)c.take(sizeof(int32_t) * ns);
   *bytes = c.size();
   return w;
 }
@@ -504,6 +519,8 @@ band_status make_sip(const band_desc* desc, const void* const diag[5], const voi
     sa->tail_count = w.tail_count;
     sa->tail_list = w.tail_list;
     sa->tail_rn = w.tail_rn;
+    sa->pend = w.pend;
+    sa->rn_sys = w.rn_sys;
     // Algorithm 1's first update may run on the two-sided schedule (band_schedule)
     sa->two_sided = choose_two_sided(desc, false) ? 1 : 0;
   }
@@ -565,8 +582,10 @@ extern "C" band_status band_sip(const band_desc* desc, const void* const diag[5]
       sa.XU[j] = w.X[width + j];
     }
   }
-  if (width == 0 && cudaMemsetAsync(sa.tail_count, 0, sizeof(unsigned long long), st) !=
-                        cudaSuccess)
+  if (width == 0 &&
+      (cudaMemsetAsync(sa.tail_count, 0, sizeof(unsigned long long), st) != cudaSuccess ||
+       cudaMemsetAsync(sa.rn_sys, 0, (size_t)((char*)(sa.pend + desc->nsys) - (char*)sa.rn_sys),
+                       st) != cudaSuccess))
     return BAND_ERR_CUDA;
   if (sa.two_sided) {
     const int64_t threads = (desc->nsys + 15) / 16 * 32;
@@ -575,6 +594,12 @@ extern "C" band_status band_sip(const band_desc* desc, const void* const diag[5]
     k_sip<<<g128, 128, 0, st>>>(sa);
   }
   if (cudaGetLastError() != cudaSuccess) return BAND_ERR_CUDA;
-  if (width == 0) return cuda_status(launch_sip_tail(sa, desc->nsys, st));
+  if (width == 0) {
+    const int64_t nch = (desc->n + kResChunk - 1) / kResChunk;
+    k_sip_resid<<<(unsigned)((desc->nsys * nch + 255) / 256), 256, 0, st>>>(sa);
+    k_sip_decide<<<(unsigned)((desc->nsys + 255) / 256), 256, 0, st>>>(sa);
+    if (cudaGetLastError() != cudaSuccess) return BAND_ERR_CUDA;
+    return cuda_status(launch_sip_tail(sa, desc->nsys, st));
+  }
   return BAND_OK;
 }

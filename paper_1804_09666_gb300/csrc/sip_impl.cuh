@@ -25,6 +25,8 @@ struct SipWs {
   unsigned long long* tail_count;   // systems needing more than one update
   int64_t* tail_list;
   double* tail_rn;
+  int32_t* pend;                    // deferred residual: pending systems and their max|r|
+  unsigned long long* rn_sys;
 };
 SipWs carve_sip(const band_desc* d, int32_t width, void* base, size_t* bytes);
 
@@ -51,6 +53,12 @@ struct SipArgs {
   // the first update ran on the two-sided schedule (sip_two_sided): rows (n+1)/2 .. n-1
   // of ru0, u1 hold the mirrored factors and the tail rebuilds them first
   int32_t two_sided;
+  // Deferred residual (when pend is set): the first update's sweeps leave x^1 and mark
+  // the system pending; an elementwise pass forms max|f - A x^1| (rn_sys, bits of a
+  // double >= 0) and a per-system pass takes Algorithm 1's decision.  Both indexed by
+  // position in the batch.
+  int32_t* pend;
+  unsigned long long* rn_sys;
 };
 
 struct Row {
@@ -309,6 +317,36 @@ __device__ inline void sip_literal(const SipArgs& p, int64_t t, void* stage) {
                              : (rn < p.tol ? BAND_OK : BAND_ERR_NOT_CONVERGED));
     return;
   }
+  if (p.pend) {      // U x = y only; the residual pass and the decision come after
+    constexpr int kB = 8;
+    double x1 = 0, x2 = 0;
+    for (int64_t top = n - 1; top >= 0; top -= kB) {
+      double yv[kB], uv[kB], rv[kB], ev[kB];
+#pragma unroll
+      for (int j = 0; j < kB; ++j) {
+        const int64_t i = top - j;
+        yv[j] = uv[j] = rv[j] = ev[j] = 0.0;
+        if (i >= 0) {
+          const int64_t w = w0 + i * ws;
+          ev[j] = (i + 2 < n) ? ldro(p.e + q0 + i * es) : 0.0;
+          yv[j] = p.y[w];
+          uv[j] = p.u1[w];
+          rv[j] = p.ru0[w];
+        }
+      }
+#pragma unroll
+      for (int j = 0; j < kB; ++j) {
+        const int64_t i = top - j;
+        if (i < 0) break;
+        const double xi = fma(-ev[j], x2, fma(-uv[j], x1, yv[j])) * rv[j];
+        p.x[q0 + i * es] = xi;
+        x2 = x1;
+        x1 = xi;
+      }
+    }
+    p.pend[t] = 1;
+    return;
+  }
   // U x = y, residual of row j = i + 2 once x_i .. x_{i+4} are known; the loads of a
   // block of kBack rows are issued together
   constexpr int kBack = 4;
@@ -480,7 +518,47 @@ __device__ inline void sip_two_sided(const SipArgs& p, int64_t t, bool active) {
   // (bottom) is taken once x_{jr-2} .. x_{jr+2} are known.  n1 .. n4 hold the previous
   // four x's in walk order.
   double rn = 0.0;
-  if (active && split && !fail && !stop0) {
+  if (active && split && !fail && !stop0 && p.pend) {
+    // back-substitution only: the residual pass and the decision come after
+    const int64_t start = bottom ? m + 2 : m - 3;
+    const int64_t cnt = bottom ? n - m - 2 : m - 2;
+    const int bdir = bottom ? 1 : -1;
+    const double* pe = bottom ? p.a : p.e;
+    double x1 = bottom ? xp1 : xm2, x2 = bottom ? xm0 : xm1;
+    constexpr int kB = 8;
+    for (int64_t k0 = 0; k0 < cnt; k0 += kB) {
+      double yv[kB], uv[kB], rv[kB], ev[kB];
+#pragma unroll
+      for (int j = 0; j < kB; ++j) {
+        yv[j] = uv[j] = rv[j] = ev[j] = 0.0;
+        if (k0 + j < cnt) {
+          const int64_t i = start + bdir * (k0 + j);
+          const int64_t w = w0 + i * ws;
+          const bool has_e = bottom ? (i >= 2) : (i + 2 < n);
+          ev[j] = has_e ? ldro(pe + q0 + i * es) : 0.0;
+          yv[j] = p.y[w];
+          uv[j] = p.u1[w];
+          rv[j] = p.ru0[w];
+        }
+      }
+#pragma unroll
+      for (int j = 0; j < kB; ++j) {
+        if (k0 + j >= cnt) break;
+        const int64_t i = start + bdir * (k0 + j);
+        const double xi = fma(-ev[j], x2, fma(-uv[j], x1, yv[j])) * rv[j];
+        p.x[q0 + i * es] = xi;
+        x2 = x1;
+        x1 = xi;
+      }
+    }
+    if (!bottom) {
+      p.x[q0 + (m - 2) * es] = xm2;
+      p.x[q0 + (m - 1) * es] = xm1;
+    } else {
+      p.x[q0 + m * es] = xm0;
+      p.x[q0 + (m + 1) * es] = xp1;
+    }
+  } else if (active && split && !fail && !stop0) {
     double n1, n2, n3, n4;
     if (!bottom) { n1 = xm2; n2 = xm1; n3 = xm0; n4 = xp1; }
     else { n1 = xp1; n2 = xm0; n3 = xm1; n4 = xm2; }
@@ -556,6 +634,10 @@ __device__ inline void sip_two_sided(const SipArgs& p, int64_t t, bool active) {
                !isfinite(rn0) ? BAND_ERR_NONFINITE : (rn0 < p.tol ? BAND_OK : BAND_ERR_NOT_CONVERGED));
     return;
   }
+  if (p.pend) {                  // the residual pass and the decision come after
+    p.pend[t] = 1;
+    return;
+  }
   if (rn < p.tol || p.max_it <= 1 || !isfinite(rn)) {
     if (p.iters) p.iters[s] = 1;
     if (p.resid) p.resid[s] = rn;
@@ -565,6 +647,71 @@ __device__ inline void sip_two_sided(const SipArgs& p, int64_t t, bool active) {
     return;
   }
   const unsigned long long k = atomicAdd(p.tail_count, 1ull);
+  p.tail_list[k] = t;
+  p.tail_rn[k] = rn;
+}
+
+// ---------------------------------------------------------------------------
+// Deferred residual of the first update: r = f - A x^1 over a chunk of rows of the
+// t-th system (the expression and order of sip_literal's inline residual), its max|r|
+// into rn_sys[t]; then Algorithm 1's decision per system.
+// ---------------------------------------------------------------------------
+constexpr int kResChunk = 32;
+
+__device__ inline void sip_resid_chunk(const SipArgs& p, int64_t t, int64_t c) {
+  const int64_t s = p.L.sys(t);
+  const int64_t n = p.L.rows(s), q0 = p.L.base(s), es = p.L.stride();
+  const int64_t i0 = c * kResChunk;
+  if (i0 >= n) return;
+  const int64_t i1 = i0 + kResChunk < n ? i0 + kResChunk : n;
+  auto X = [&](int64_t j) -> double { return (j >= 0 && j < n) ? p.x[q0 + j * es] : 0.0; };
+  double xm2 = X(i0 - 2), xm1 = X(i0 - 1), x0 = X(i0), xp1 = X(i0 + 1);
+  double rn = 0.0;
+  constexpr int kB = 4;
+  for (int64_t ib = i0; ib < i1; ib += kB) {
+    Row A[kB];
+    double xv[kB];
+#pragma unroll
+    for (int u = 0; u < kB; ++u) {
+      const int64_t i = ib + u;
+      A[u] = Row{0, 0, 0, 0, 0, 0};
+      xv[u] = 0.0;
+      if (i < i1) {
+        A[u] = load_row(p, q0 + i * es, i, n);
+        xv[u] = X(i + 2);
+      }
+    }
+#pragma unroll
+    for (int u = 0; u < kB; ++u) {
+      if (ib + u >= i1) break;
+      const double xp2 = xv[u];
+      double ax = A[u].c * x0;
+      ax = fma(A[u].a, xm2, ax);
+      ax = fma(A[u].b, xm1, ax);
+      ax = fma(A[u].d, xp1, ax);
+      ax = fma(A[u].e, xp2, ax);
+      rn = max_abs(rn, A[u].f - ax);      // a NaN wins the max
+      xm2 = xm1; xm1 = x0; x0 = xp1; xp1 = xp2;
+    }
+  }
+  atomicMax(p.rn_sys + t, (unsigned long long)__double_as_longlong(rn));
+}
+
+__device__ inline void sip_decide_one(const SipArgs& p, int64_t t) {
+  if (!p.pend[t]) return;
+  p.pend[t] = 0;
+  const int64_t s = p.L.sys(t);
+  const double rn = __longlong_as_double((long long)p.rn_sys[t]);
+  p.rn_sys[t] = 0ull;
+  if (rn < p.tol || p.max_it <= 1 || !isfinite(rn)) {
+    if (p.iters) p.iters[s] = 1;
+    if (p.resid) p.resid[s] = rn;
+    set_status(p.status, s,
+               !isfinite(rn) ? BAND_ERR_NONFINITE
+                             : (rn < p.tol ? BAND_OK : BAND_ERR_NOT_CONVERGED));
+    return;
+  }
+  const unsigned long long k = atomicAdd(p.tail_count, 1ull);   // more updates: the tail
   p.tail_list[k] = t;
   p.tail_rn[k] = rn;
 }
