@@ -75,86 +75,6 @@ __device__ __forceinline__ Row load_row(const SipArgs& p, int64_t q, int64_t i, 
   return r;
 }
 
-// Further updates of Algorithm 1 after the first one (rare: only systems whose first
-// update leaves max|r| >= tol), from state (k, rn) with the full ILU(0) factors in
-// the workspace: rhs = K x + f, L y = rhs, U x = y, r = f - A x, until max|r| < tol,
-// max_it updates, or an update from the second on fails to lower max|r| (the rounding
-// floor of exact ILU(0) factors; NOT_CONVERGED).
-__device__ inline void sip_literal_more(const SipArgs& p, int64_t t, int k, double rn) {
-  const int64_t s = p.L.sys(t);     // t: position in the batch, s: the system id
-
-  const int64_t n = p.L.rows(s), q0 = p.L.base(s), es = p.L.stride();
-  const int64_t w0 = p.W.base(t), ws = p.W.stride();
-  double prev = INFINITY;
-  for (;;) {
-    if (rn < p.tol || k >= p.max_it || !isfinite(rn)) break;
-    // K = LU - A holds only rounding errors: an update (from the second on) that does
-    // not lower the residual means its rounding floor is reached
-    if (k >= 2 && !(rn < prev)) break;
-    prev = rn;
-    // forward: rhs_i = sum_j K[i][j] x_j + f_i, y_i = rhs_i - l1_i y_{i-1} - l2_i y_{i-2}
-    double y1 = 0, y2 = 0;
-    double u0m1 = 0, u1m1 = 0, u0m2 = 0, u1m2 = 0, em1 = 0, em2 = 0;
-    double xm2 = 0, xm1 = 0, x0 = p.x[q0], xp1 = n > 1 ? p.x[q0 + es] : 0.0;
-    for (int64_t i = 0; i < n; ++i) {
-      const int64_t q = q0 + i * es, wi = w0 + i * ws;
-      const Row A = load_row(p, q, i, n);
-      const double l2 = (i >= 2) ? p.l2[wi] : 0.0, l1 = (i >= 1) ? p.l1[wi] : 0.0;
-      const double u0 = p.u0[wi], u1 = (i + 1 < n) ? p.u1[wi] : 0.0;
-      // K = LU - A on this row (K[i][i+2] = u2 - e = 0)
-      const double ka = l2 * u0m2 - A.a;
-      const double kb = fma(l2, u1m2, l1 * u0m1) - A.b;
-      const double kc = fma(l2, em2, fma(l1, u1m1, u0)) - A.c;
-      const double kd = fma(l1, em1, u1) - A.d;
-      double rhs = fma(kc, x0, A.f);
-      rhs = fma(ka, xm2, rhs);
-      rhs = fma(kb, xm1, rhs);
-      rhs = fma(kd, xp1, rhs);
-      const double yv = fma(-l2, y2, fma(-l1, y1, rhs));
-      p.y[wi] = yv;
-      y2 = y1; y1 = yv;
-      u0m2 = u0m1; u1m2 = u1m1; em2 = em1;
-      u0m1 = u0; u1m1 = u1; em1 = A.e;
-      xm2 = xm1; xm1 = x0; x0 = xp1;
-      xp1 = (i + 2 < n) ? p.x[q + 2 * es] : 0.0;
-    }
-    // backward: x_i = (y_i - u1_i x_{i+1} - e_i x_{i+2}) / u0_i, with the residual of
-    // row i+2 once x_i .. x_{i+4} are new
-    double n1 = 0, n2 = 0, n3 = 0, n4 = 0;  // new x_{i+1} .. x_{i+4}
-    rn = 0.0;
-    bool nan_seen = false;
-    for (int64_t i = n - 1; i >= -2; --i) {
-      double xi = 0.0;
-      if (i >= 0) {
-        const int64_t q = q0 + i * es, wi = w0 + i * ws;
-        const double u1 = (i + 1 < n) ? p.u1[wi] : 0.0;
-        const double ei = (i + 2 < n) ? ldro(p.e + q) : 0.0;
-        xi = fma(-ei, n2, fma(-u1, n1, p.y[wi])) * p.ru0[wi];
-        p.x[q] = xi;
-      }
-      const int64_t j = i + 2;  // residual row
-      if (j >= 0 && j < n) {
-        const Row A = load_row(p, q0 + j * es, j, n);
-        double ax = A.c * n2;
-        ax = fma(A.a, xi, ax);
-        ax = fma(A.b, n1, ax);
-        ax = fma(A.d, n3, ax);
-        ax = fma(A.e, n4, ax);
-        const double r = A.f - ax;
-        nan_seen |= (r != r);
-        rn = fmax(rn, fabs(r));
-      }
-      n4 = n3; n3 = n2; n2 = n1; n1 = xi;
-    }
-    if (nan_seen) rn = NAN;
-    ++k;
-  }
-  if (p.iters) p.iters[s] = k;
-  if (p.resid) p.resid[s] = rn;
-  set_status(p.status, s,
-             !isfinite(rn) ? BAND_ERR_NONFINITE : (rn < p.tol ? BAND_OK : BAND_ERR_NOT_CONVERGED));
-}
-
 // HB variant: x <- x + U~^{-1} (L~^{-1} (f - A x)) in one sweep per iteration.  The
 // sweep computes r = f - A x_old (and its norm), y = L~^{-1} r with a lag of 0 and
 // x_new = x_old + U~^{-1} y with a lag of w-1 rows.  When max|r| < tol the update
@@ -265,8 +185,9 @@ __device__ inline bool ilu0_into(const SipArgs& p, int64_t s) {
 
 // Algorithm 1 with exact substitutions.  x^0 = 0 makes K x^0 = 0, so the first update
 // is x^1 = U^{-1} L^{-1} f: one forward sweep does ILU(0) and L y = f together (only
-// 1/u0, u1 and y are kept), one backward sweep does U x = y and the residual of every
-// row (two rows behind).  Systems that need more updates rebuild the full factors.
+// 1/u0, u1 and y are kept), one backward sweep does U x = y.  The residual of x^1 and
+// the stop / continue decision are separate passes (sip_resid_chunk, sip_decide_one);
+// systems that need more updates go to the block-cooperative tail.
 __device__ inline void sip_literal(const SipArgs& p, int64_t t, void* stage) {
   const int64_t s = p.L.sys(t);     // t: position in the batch, s: the system id
 
@@ -317,96 +238,34 @@ __device__ inline void sip_literal(const SipArgs& p, int64_t t, void* stage) {
                              : (rn < p.tol ? BAND_OK : BAND_ERR_NOT_CONVERGED));
     return;
   }
-  if (p.pend) {      // U x = y only; the residual pass and the decision come after
-    constexpr int kB = 8;
-    double x1 = 0, x2 = 0;
-    for (int64_t top = n - 1; top >= 0; top -= kB) {
-      double yv[kB], uv[kB], rv[kB], ev[kB];
+  // U x = y; the residual pass and Algorithm 1's decision come after (pend)
+  constexpr int kB = 8;
+  double x1 = 0, x2 = 0;
+  for (int64_t top = n - 1; top >= 0; top -= kB) {
+    double yv[kB], uv[kB], rv[kB], ev[kB];
 #pragma unroll
-      for (int j = 0; j < kB; ++j) {
-        const int64_t i = top - j;
-        yv[j] = uv[j] = rv[j] = ev[j] = 0.0;
-        if (i >= 0) {
-          const int64_t w = w0 + i * ws;
-          ev[j] = (i + 2 < n) ? ldro(p.e + q0 + i * es) : 0.0;
-          yv[j] = p.y[w];
-          uv[j] = p.u1[w];
-          rv[j] = p.ru0[w];
-        }
-      }
-#pragma unroll
-      for (int j = 0; j < kB; ++j) {
-        const int64_t i = top - j;
-        if (i < 0) break;
-        const double xi = fma(-ev[j], x2, fma(-uv[j], x1, yv[j])) * rv[j];
-        p.x[q0 + i * es] = xi;
-        x2 = x1;
-        x1 = xi;
-      }
-    }
-    p.pend[t] = 1;
-    return;
-  }
-  // U x = y, residual of row j = i + 2 once x_i .. x_{i+4} are known; the loads of a
-  // block of kBack rows are issued together
-  constexpr int kBack = 4;
-  double n1 = 0, n2 = 0, n3 = 0, n4 = 0;
-  rn = 0.0;
-  for (int64_t top = n - 1; top >= -2; top -= kBack) {
-    double yv[kBack], uv[kBack], rv[kBack], ev[kBack];
-    Row Av[kBack];
-#pragma unroll
-    for (int j = 0; j < kBack; ++j) {
+    for (int j = 0; j < kB; ++j) {
       const int64_t i = top - j;
       yv[j] = uv[j] = rv[j] = ev[j] = 0.0;
       if (i >= 0) {
-        const int64_t q = q0 + i * es, w = w0 + i * ws;
-        ev[j] = (i + 2 < n) ? ldro(p.e + q) : 0.0;
+        const int64_t w = w0 + i * ws;
+        ev[j] = (i + 2 < n) ? ldro(p.e + q0 + i * es) : 0.0;
         yv[j] = p.y[w];
         uv[j] = p.u1[w];
         rv[j] = p.ru0[w];
       }
-      const int64_t jr = i + 2;
-      Av[j] = Row{0, 0, 0, 0, 0, 0};
-      if (jr >= 0 && jr < n && i >= -2) Av[j] = load_row(p, q0 + jr * es, jr, n);
     }
 #pragma unroll
-    for (int j = 0; j < kBack; ++j) {
+    for (int j = 0; j < kB; ++j) {
       const int64_t i = top - j;
-      if (i < -2) break;
-      double xi = 0.0;
-      if (i >= 0) {
-        xi = fma(-ev[j], n2, fma(-uv[j], n1, yv[j])) * rv[j];
-        p.x[q0 + i * es] = xi;
-      }
-      const int64_t jr = i + 2;
-      if (jr >= 0 && jr < n) {
-        const Row& A = Av[j];
-        double ax = A.c * n2;
-        ax = fma(A.a, xi, ax);
-        ax = fma(A.b, n1, ax);
-        ax = fma(A.d, n3, ax);
-        ax = fma(A.e, n4, ax);
-        rn = max_abs(rn, A.f - ax);
-      }
-      n4 = n3; n3 = n2; n2 = n1; n1 = xi;
+      if (i < 0) break;
+      const double xi = fma(-ev[j], x2, fma(-uv[j], x1, yv[j])) * rv[j];
+      p.x[q0 + i * es] = xi;
+      x2 = x1;
+      x1 = xi;
     }
   }
-  if (rn < p.tol || p.max_it <= 1 || !isfinite(rn)) {
-    if (p.iters) p.iters[s] = 1;
-    if (p.resid) p.resid[s] = rn;
-    set_status(p.status, s,
-               !isfinite(rn) ? BAND_ERR_NONFINITE
-                             : (rn < p.tol ? BAND_OK : BAND_ERR_NOT_CONVERGED));
-    return;
-  }
-  if (p.tail_list) {   // 1/u0 and u1 are stored: hand over to the tail kernel
-    const unsigned long long k = atomicAdd(p.tail_count, 1ull);
-    p.tail_list[k] = t;
-    p.tail_rn[k] = rn;
-    return;
-  }
-  sip_literal_more(p, t, 1, rn);
+  p.pend[t] = 1;
 }
 
 // ---------------------------------------------------------------------------
@@ -417,12 +276,11 @@ __device__ inline void sip_literal(const SipArgs& p, int64_t t, void* stage) {
 // (a, b, c, d, e) read as (e, d, c, b, a)), i.e. the UL factorisation of that block.
 // Their last two rows, normalised (x_i + alpha x_{i+-1} + beta x_{i+-2} = z), form the
 // same 4x4 interface system as the two-sided direct sweep; then each lane
-// back-substitutes its half and computes the residual of its own rows (the interface
-// unknowns it needs are in its registers).  x^1 equals sip_literal's in exact
-// arithmetic.  A zero pivot in either half, a singular interface system or n < 4 hands
-// the system to the tail kernel from x^0 = 0 (tail_rn = -1), which factors it top-down
-// and runs Algorithm 1 from its first update.  Needs the tail list.
-// ---------------------------------------------------------------------------
+// back-substitutes its half.  x^1 equals sip_literal's in exact arithmetic; the
+// residual and the decision are the same separate passes.  A zero pivot in either
+// half, a singular interface system or n < 4 hands the system to the tail kernel from
+// x^0 = 0 (tail_rn = -1), which factors it top-down and runs Algorithm 1 from its
+// first update.
 __device__ inline void sip_two_sided(const SipArgs& p, int64_t t, bool active) {
   const int64_t s = active ? p.L.sys(t) : 0;   // t: position in the batch, s: system id
 
@@ -517,8 +375,7 @@ __device__ inline void sip_two_sided(const SipArgs& p, int64_t t, bool active) {
   // with x_{m-2} .. x_{m+1} known; the residual of row jr = i + 2 (top) or i - 2
   // (bottom) is taken once x_{jr-2} .. x_{jr+2} are known.  n1 .. n4 hold the previous
   // four x's in walk order.
-  double rn = 0.0;
-  if (active && split && !fail && !stop0 && p.pend) {
+  if (active && split && !fail && !stop0) {
     // back-substitution only: the residual pass and the decision come after
     const int64_t start = bottom ? m + 2 : m - 3;
     const int64_t cnt = bottom ? n - m - 2 : m - 2;
@@ -558,67 +415,7 @@ __device__ inline void sip_two_sided(const SipArgs& p, int64_t t, bool active) {
       p.x[q0 + m * es] = xm0;
       p.x[q0 + (m + 1) * es] = xp1;
     }
-  } else if (active && split && !fail && !stop0) {
-    double n1, n2, n3, n4;
-    if (!bottom) { n1 = xm2; n2 = xm1; n3 = xm0; n4 = xp1; }
-    else { n1 = xp1; n2 = xm0; n3 = xm1; n4 = xm2; }
-    const int64_t start = bottom ? m + 2 : m - 3;
-    const int64_t steps = bottom ? n - m : m;
-    const int bdir = bottom ? 1 : -1;
-    const double* pe = bottom ? p.a : p.e;    // coefficient of x_{i+-2}: e_i, or a_i reversed
-    constexpr int kBack = 4;
-    for (int64_t k0 = 0; k0 < steps; k0 += kBack) {
-      double yv[kBack], uv[kBack], rv[kBack], ev[kBack];
-      Row Av[kBack];
-#pragma unroll
-      for (int j = 0; j < kBack; ++j) {
-        const int64_t i = start + bdir * (k0 + j);
-        const int64_t jr = i - 2 * bdir;
-        yv[j] = uv[j] = rv[j] = ev[j] = 0.0;
-        Av[j] = Row{0, 0, 0, 0, 0, 0};
-        if (k0 + j < steps) {
-          if (i >= 0 && i < n) {
-            const int64_t q = q0 + i * es, w = w0 + i * ws;
-            const bool has_e = bottom ? (i >= 2) : (i + 2 < n);
-            ev[j] = has_e ? ldro(pe + q) : 0.0;
-            yv[j] = p.y[w];
-            uv[j] = p.u1[w];
-            rv[j] = p.ru0[w];
-          }
-          Av[j] = load_row(p, q0 + jr * es, jr, n);
-        }
-      }
-#pragma unroll
-      for (int j = 0; j < kBack; ++j) {
-        if (k0 + j >= steps) break;
-        const int64_t i = start + bdir * (k0 + j);
-        double xi = 0.0;
-        if (i >= 0 && i < n) {
-          xi = fma(-ev[j], n2, fma(-uv[j], n1, yv[j])) * rv[j];
-          p.x[q0 + i * es] = xi;
-        }
-        // row jr's x_{jr-2} .. x_{jr+2} in the original orientation
-        const double xa = bottom ? n4 : xi, xb = bottom ? n3 : n1, xc = n2;
-        const double xd = bottom ? n1 : n3, xe = bottom ? xi : n4;
-        const Row& A = Av[j];
-        double ax = A.c * xc;
-        ax = fma(A.a, xa, ax);
-        ax = fma(A.b, xb, ax);
-        ax = fma(A.d, xd, ax);
-        ax = fma(A.e, xe, ax);
-        rn = max_abs(rn, A.f - ax);
-        n4 = n3; n3 = n2; n2 = n1; n1 = xi;
-      }
-    }
-    if (!bottom) {
-      p.x[q0 + (m - 2) * es] = xm2;
-      p.x[q0 + (m - 1) * es] = xm1;
-    } else {
-      p.x[q0 + m * es] = xm0;
-      p.x[q0 + (m + 1) * es] = xp1;
-    }
   }
-  rn = max_abs(rn, __shfl_xor_sync(full, rn, 16));
   if (!active || bottom) return;
   if (!split || fail) {          // the tail kernel starts this system from x^0 = 0
     const unsigned long long k = atomicAdd(p.tail_count, 1ull);
@@ -634,21 +431,7 @@ __device__ inline void sip_two_sided(const SipArgs& p, int64_t t, bool active) {
                !isfinite(rn0) ? BAND_ERR_NONFINITE : (rn0 < p.tol ? BAND_OK : BAND_ERR_NOT_CONVERGED));
     return;
   }
-  if (p.pend) {                  // the residual pass and the decision come after
-    p.pend[t] = 1;
-    return;
-  }
-  if (rn < p.tol || p.max_it <= 1 || !isfinite(rn)) {
-    if (p.iters) p.iters[s] = 1;
-    if (p.resid) p.resid[s] = rn;
-    set_status(p.status, s,
-               !isfinite(rn) ? BAND_ERR_NONFINITE
-                             : (rn < p.tol ? BAND_OK : BAND_ERR_NOT_CONVERGED));
-    return;
-  }
-  const unsigned long long k = atomicAdd(p.tail_count, 1ull);
-  p.tail_list[k] = t;
-  p.tail_rn[k] = rn;
+  p.pend[t] = 1;                 // the residual pass and the decision come after
 }
 
 // ---------------------------------------------------------------------------
