@@ -293,3 +293,25 @@ def test_adjoint_transposed_solve(band, k, layout, n):
                 continue
             den = max(np.abs(g_orc).max(), 1e-300)
             assert np.abs(g_gpu[:, s] - g_orc).max() / den <= 1e-11, (s, j)
+
+
+@pytest.mark.parametrize("n,width", [(300, 5), (1200, 8)])
+def test_sip_hb_both_kernels(band, n, width):
+    """SIP-HB on dominant systems through both kernels: one block per system in shared
+    memory (n = 300) and one thread per system (n = 1200 at w = 8 needs more shared
+    memory than a block has).  Iteration counts within one of the oracle's, the
+    solution next to the oracle's and to the truth."""
+    nsys = 40
+    B = synth.cfg0(nsys=nsys, n=n, seed_salt=13)
+    T = to_dev(B)
+    x, it, rs, st = band.sip(*(T[q] for q in "abcdef"), tol=1e-10, max_it=200, width=width)
+    torch.cuda.synchronize()
+    st, it = st.cpu().numpy(), it.cpu().numpy()
+    assert (st == 0).all()
+    xo, so, ito, _ = oracle.batch("sip", 2, [B[q] for q in "abcde"], B["f"], nsys, n, 1, nsys,
+                                  hb_width=width, tol=1e-10)
+    assert (so == 0).all()
+    assert np.abs(it - ito).max() <= 1
+    xg = flat_of(x)
+    assert per_system_rel(xg, xo, n, nsys, 1, nsys).max() <= 1e-9
+    assert per_system_rel(xg, B["x_true"], n, nsys, 1, nsys).max() <= 1e-9
