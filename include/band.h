@@ -86,7 +86,8 @@ typedef struct {
   const int8_t* hbw;      /* device array of per-system half bandwidths (1 or 2), or NULL */
   int64_t total_rows;     /* ragged: offsets[nsys] (the host's copy); uniform: ignored */
   int32_t schedule;       /* band_schedule for NTDM/NPDM solves (BAND_SCHED_AUTO = 0) */
-  int32_t reserved;       /* 0 */
+  int32_t chunks;         /* BAND_SCHED_PARTITIONED: lanes (row chunks) per system, 4, 8,
+                             16 or 32; 0 = chosen from nsys and n.  Otherwise 0. */
   /* Ragged batches only, else NULL: device array of nsys system ids.  The batch is then
    * the systems ids[0 .. nsys-1] of the packing that offsets (and hbw) describe, and
    * every per-system output (sys_status, iters, resid) is indexed by the id.  A solve
@@ -114,11 +115,30 @@ typedef struct {
  *   system that NPDM's order would fail on in its lower half may be solved (status OK).
  *   Systems with fewer than 4 (PD) / 2 (TD) rows are solved by one thread.  Needs one
  *   half bandwidth for the batch.
+ * BAND_SCHED_PARTITIONED: P = desc->chunks lanes of a warp per system (32 / P systems
+ *   a warp).  Lane k eliminates rows [k n / P, (k+1) n / P) (about) with NPDM's
+ *   recurrence, carrying the columns through which the chunk couples to its neighbours'
+ *   boundary rows (the SPIKE partition); the chunks' boundary rows form a
+ *   block-tridiagonal system of P blocks of 4 (PD) / 2 (TD) unknowns that the system's
+ *   first lane solves by block elimination with partial pivoting inside the blocks; then
+ *   every lane back-substitutes its chunk.  About 2.3x (PD) / 1.8x (TD) NPDM's arithmetic
+ *   per row, for a dependent chain of n / P rows: for batches with too few systems to
+ *   fill the GPU, and for the longest systems of a ragged batch.  A zero pivot in a
+ *   chunk or a singular interface block sends an STDM/SPDM system to the symbolic fix-up
+ *   and makes the first lane redo an NTDM/NPDM system with NPDM alone (BAND_ERR_ZERO_PIVOT
+ *   means that NPDM's order meets an exactly zero pivot, also when x aliases f).
+ *   Systems with fewer than 8 P rows are solved by one lane.  Needs one half bandwidth
+ *   for the batch; any layout, ragged packings included.
  * BAND_SCHED_AUTO: TWO_SIDED for uniform-bandwidth solves with n >= 32 that are not a
  *   whole ragged packing (ragged id lists, i.e. size buckets, qualify) and, for
  *   NTDM/NPDM, whose x does not alias f; THREAD otherwise.  band_autotune replaces the
  *   rule by measurement. */
-typedef enum { BAND_SCHED_AUTO = 0, BAND_SCHED_THREAD = 1, BAND_SCHED_TWO_SIDED = 2 } band_schedule;
+typedef enum {
+  BAND_SCHED_AUTO = 0,
+  BAND_SCHED_THREAD = 1,
+  BAND_SCHED_TWO_SIDED = 2,
+  BAND_SCHED_PARTITIONED = 3
+} band_schedule;
 
 /* Bytes of workspace that the operation `op` needs for `desc` (0 = none).  op is one
  * of the BAND_OP_* values; `method` as for the call it serves (ignored where n/a). */
@@ -263,17 +283,31 @@ typedef struct {
 int32_t band_plan_ragged(const int64_t* offsets, const int8_t* hbw, int32_t half_bw, int64_t nsys,
                          int64_t* order, band_bucket* buckets, int32_t max_buckets);
 
-/* Autotuner of the thread-per-system / two-sided choice.  For every problem of the list
- * that may run on either schedule (a fused direct solve of one half bandwidth whose
- * desc->schedule is BAND_SCHED_AUTO), time it alone as a band_solve_batch launch on each
- * schedule (one warm-up, then the best of `reps` runs; CUDA events on `stream`) and
- * write the faster to schedules[i]; other problems get their desc->schedule.  The trial
- * runs solve the problems (outputs are overwritten).  Decisions are cached for the
- * process per (dtype, method, half bandwidth, ceil(log2 n), ceil(log2 nsys), layout), so
- * later calls reuse them without timing.  Synchronises the stream; do not call while it
- * is being captured.  Returns BAND_ERR_ARG / BAND_ERR_CUDA / the solve's error. */
-band_status band_autotune(const band_problem* probs, int32_t count, int32_t reps,
-                          int32_t* schedules, void* stream);
+/* Autotuner of the schedules (band_schedule) of a band_solve_batch list.  Problems it
+ * may decide: fused direct solves of one half bandwidth whose desc->schedule is
+ * BAND_SCHED_AUTO; the others keep their desc->schedule and desc->chunks.
+ * 1. Each such problem is timed alone as a band_solve_batch launch on the thread and
+ *    two-sided schedules (one warm-up, then the best of `reps` runs; CUDA events on
+ *    `stream`) and gets the faster.  These decisions are cached for the process per
+ *    (dtype, method, half bandwidth, ceil(log2 n), ceil(log2 nsys), layout, x aliasing
+ *    f), so later calls reuse them without timing.
+ * 2. With flags & BAND_TUNE_JOINT: the whole list is timed as one launch, and the
+ *    problems (n >= 64, largest n first) are moved in turn to BAND_SCHED_PARTITIONED
+ *    with 4, 8, 16 or 32 chunks (those that leave chunks of 16 rows or more); a move is
+ *    kept when it shortens the launch by 2 % or more, and the search ends after two
+ *    problems in a row gain nothing.  Only problems whose ws_bytes cover the partitioned
+ *    schedule's workspace (band_workspace_size with schedule BAND_SCHED_PARTITIONED)
+ *    and whose every row is diagonally dominant (|c| >= |a| + |b| + |d| + |e|, checked
+ *    on the device) are tried: on other matrices a chunk's block can be far worse
+ *    conditioned than the whole matrix.  Not cached: the result depends on the whole
+ *    list.
+ * Writes schedules[i] and, if chunks is not NULL, chunks[i] (the desc fields to set).
+ * The trial runs solve the problems (outputs are overwritten).  Synchronises the
+ * stream; do not call while it is being captured.  Returns BAND_ERR_ARG (also for
+ * unknown flags) / BAND_ERR_CUDA / the solve's error. */
+#define BAND_TUNE_JOINT 1
+band_status band_autotune(const band_problem* probs, int32_t count, int32_t reps, int32_t flags,
+                          int32_t* schedules, int32_t* chunks, void* stream);
 
 /* Forget the autotuner's cached decisions (all devices). */
 void band_autotune_reset(void);

@@ -21,7 +21,8 @@ NTDM, NPDM, STDM, SPDM, AUTO_NUMERIC, AUTO_SYMBOLIC = range(6)
 # band_dtype
 F64, F32 = 0, 1
 # band_schedule
-SCHED_AUTO, SCHED_THREAD, SCHED_TWO_SIDED = 0, 1, 2
+SCHED_AUTO, SCHED_THREAD, SCHED_TWO_SIDED, SCHED_PARTITIONED = 0, 1, 2, 3
+TUNE_JOINT = 1
 # BAND_OP_*
 OP_SOLVE, OP_FACTOR, OP_SIP, OP_REFINE, OP_ADJOINT = range(5)
 
@@ -36,7 +37,7 @@ class BandDesc(ct.Structure):
     _fields_ = [("half_bw", ct.c_int32), ("dtype", ct.c_int32), ("nsys", ct.c_int64),
                 ("n", ct.c_int64), ("sys_stride", ct.c_int64), ("elem_stride", ct.c_int64),
                 ("offsets", ct.c_void_p), ("hbw", ct.c_void_p), ("total_rows", ct.c_int64),
-                ("schedule", ct.c_int32), ("reserved", ct.c_int32), ("systems", ct.c_void_p)]
+                ("schedule", ct.c_int32), ("chunks", ct.c_int32), ("systems", ct.c_void_p)]
 
 
 _lib = None
@@ -85,7 +86,7 @@ def load(path=None):
     lib.band_solve_static.restype = ct.c_int
     lib.band_plan_ragged.argtypes = [P, P, i32, i64, P, ct.POINTER(BandBucket), i32]
     lib.band_plan_ragged.restype = i32
-    lib.band_autotune.argtypes = [ct.POINTER(BandProblem), i32, i32, P, P]
+    lib.band_autotune.argtypes = [ct.POINTER(BandProblem), i32, i32, i32, P, P, P]
     lib.band_autotune.restype = ct.c_int
     lib.band_autotune_reset.argtypes = []
     lib.band_autotune_reset.restype = None

@@ -41,10 +41,11 @@ def _dtype_code(t):
     raise TypeError("band arrays must be float64 or float32, got %s" % t.dtype)
 
 
-_SCHEDULES = {"auto": L.SCHED_AUTO, "thread": L.SCHED_THREAD, "two_sided": L.SCHED_TWO_SIDED}
+_SCHEDULES = {"auto": L.SCHED_AUTO, "thread": L.SCHED_THREAD, "two_sided": L.SCHED_TWO_SIDED,
+              "partitioned": L.SCHED_PARTITIONED}
 
 
-def desc_for(ref, half_bw, schedule="auto"):
+def desc_for(ref, half_bw, schedule="auto", chunks=0):
     """BandDesc for (n, nsys)-shaped tensors with ref's strides."""
     if ref.dim() != 2:
         raise ValueError("expected a (n, nsys) tensor")
@@ -52,7 +53,8 @@ def desc_for(ref, half_bw, schedule="auto"):
     return L.BandDesc(half_bw=half_bw, dtype=_dtype_code(ref), nsys=nsys, n=n,
                       sys_stride=ref.stride(1) if nsys > 1 else max(n, 1),
                       elem_stride=ref.stride(0) if n > 1 else max(nsys, 1),
-                      offsets=None, hbw=None, total_rows=0, schedule=_SCHEDULES[schedule])
+                      offsets=None, hbw=None, total_rows=0, schedule=_SCHEDULES[schedule],
+                      chunks=chunks)
 
 
 def _check_same(ref, *ts):
@@ -74,19 +76,20 @@ def _workspace(nbytes, device):
 
 
 def solve(a, b, c, d, e, f, method="npdm", x=None, status=None, factors=None, ws=None,
-          schedule="auto"):
+          schedule="auto", chunks=0):
     """Solve A x = f for a uniform batch.  Returns (x, status int32[nsys]).
 
     method: "npdm", "ntdm", "spdm", "stdm".  a, e are ignored (may be None) for TD.
     factors: a buffer from ``factor`` to reuse a factorisation (numeric methods).
-    schedule: "auto", "thread" (one thread per system) or "two_sided" (two threads per
-    system meeting in the middle; numeric methods without factors).
+    schedule: "auto", "thread" (one thread per system), "two_sided" (two threads per
+    system meeting in the middle) or "partitioned" (``chunks`` lanes per system, 4, 8,
+    16 or 32, 0 = chosen by the library); the last two without factors.
     """
     lib = L.load()
     m = _METHODS[method]
     half_bw = 1 if method in ("ntdm", "stdm") else 2
     _check_same(c, a if half_bw == 2 else None, b, d, e if half_bw == 2 else None, f)
-    desc = desc_for(c, half_bw, schedule)
+    desc = desc_for(c, half_bw, schedule, chunks)
     if x is None:
         x = torch.empty_strided(c.shape, c.stride(), dtype=c.dtype, device=c.device)
     _check_same(c, x)
@@ -218,8 +221,9 @@ class BatchPlan:
       a, b, c, d, e, f   (n, nsys) tensors with equal strides (a, e None for TD)
       x       optional output tensor
       tol, max_it        for "sip"
-      schedule           "auto" (default), "thread", "two_sided" (for "sip": the first
-                         update of Algorithm 1)
+      schedule           "auto" (default), "thread", "two_sided", "partitioned" (for
+                         "sip": the first update of Algorithm 1, not partitioned)
+      chunks             lanes per system on the partitioned schedule (0: the library's)
     Outputs, statuses and workspaces are allocated once here; ``run()`` only launches,
     so a run can be captured in a CUDA graph.  results[i] holds x, status (and iters,
     resid for "sip").
@@ -245,7 +249,7 @@ class BatchPlan:
             else:
                 raise ValueError(op)
             _check_same(c, a if half_bw == 2 else None, b, d, e if half_bw == 2 else None, f)
-            desc = desc_for(c, half_bw, sp.get("schedule", "auto"))
+            desc = desc_for(c, half_bw, sp.get("schedule", "auto"), sp.get("chunks", 0))
             x = sp.get("x")
             if x is None:
                 x = torch.empty_strided(c.shape, c.stride(), dtype=c.dtype, device=c.device)
@@ -282,14 +286,16 @@ class RaggedPlan:
     offsets[s] .. offsets[s+1]-1; the a, e rows of TD systems are not read).
     offsets: host int64 array (nsys + 1); hbw: host int8 array of 1/2 per system, or None
     with half_bw for all.  method: "numeric" (NTDM/NPDM per bucket) or "symbolic"
-    (STDM/SPDM).  schedule: "auto", "thread", "two_sided", or "tune" (band_autotune
-    measures both schedules per bucket once and keeps the faster).  The buckets'
-    workspaces are allocated here; run() only launches (graph-capturable).  x is packed
-    like f; status holds one entry per system id.
+    (STDM/SPDM).  schedule: "auto", "thread", "two_sided", "partitioned" (``chunks``
+    lanes per system, 0 = the library's choice), or "tune": band_autotune picks thread
+    or two-sided per bucket, then moves the buckets of the longest systems to the
+    partitioned schedule while that shortens the whole launch (BAND_TUNE_JOINT).  The
+    buckets' workspaces are allocated here; run() only launches (graph-capturable).  x is
+    packed like f; status holds one entry per system id.
     """
 
     def __init__(self, a, b, c, d, e, f, offsets, hbw=None, half_bw=2, method="numeric",
-                 schedule="auto", x=None, status=None, reps=3):
+                 schedule="auto", x=None, status=None, reps=3, chunks=0):
         import numpy as np
         lib = L.load()
         self.lib = lib
@@ -317,11 +323,17 @@ class RaggedPlan:
             desc = L.BandDesc(half_bw=k, dtype=_dtype_code(f), nsys=count, n=n_max, sys_stride=0,
                               elem_stride=1, offsets=self.offsets.data_ptr(), hbw=None,
                               total_rows=int(offs[-1]), schedule=_SCHEDULES[sched],
+                              chunks=chunks if sched == "partitioned" else 0,
                               systems=self.order.data_ptr() + 8 * first)
             name = ("npdm" if k == 2 else "ntdm") if method == "numeric" else \
                    ("spdm" if k == 2 else "stdm")
             m = _METHODS[name]
-            ws = _workspace(lib.band_workspace_size(ct.byref(desc), L.OP_SOLVE, m, 0), dev)
+            need = lib.band_workspace_size(ct.byref(desc), L.OP_SOLVE, m, 0)
+            if schedule == "tune":      # room for the partitioned schedule too
+                dp = L.BandDesc.from_buffer_copy(desc)
+                dp.schedule, dp.chunks = L.SCHED_PARTITIONED, 0
+                need = max(need, lib.band_workspace_size(ct.byref(dp), L.OP_SOLVE, m, 0))
+            ws = _workspace(need, dev)
             P = self.arr[i]
             P.op, P.method = L.OP_SOLVE, m
             P.desc = ct.pointer(desc)
@@ -332,13 +344,16 @@ class RaggedPlan:
             self.keep.append(ws)
         self.count = nb
         self.schedules = [d.schedule for d in self.descs]
+        self.chunks = [d.chunks for d in self.descs]
         if schedule == "tune" and nb > 0:
             out = (ct.c_int32 * nb)()
-            code = lib.band_autotune(self.arr, nb, reps, out, _stream())
+            outc = (ct.c_int32 * nb)()
+            code = lib.band_autotune(self.arr, nb, reps, L.TUNE_JOINT, out, outc, _stream())
             L.check(code, "band_autotune")
-            for desc, v in zip(self.descs, out):
-                desc.schedule = v
+            for desc, v, pc in zip(self.descs, out, outc):
+                desc.schedule, desc.chunks = v, pc
             self.schedules = list(out)
+            self.chunks = list(outc)
 
     def run(self):
         code = self.lib.band_solve_batch(self.arr, self.count, _stream())

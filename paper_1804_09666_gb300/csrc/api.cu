@@ -13,14 +13,24 @@ namespace band {
 // Workspace of band_solve.  Numeric methods: alpha and beta rows.  Symbolic methods:
 // alpha, beta and z rows, the flagged-system counter and list, and the Laurent-series
 // rows of up to kMaxFixSlots flagged systems redone at a time.
+// The partitioned schedule adds the rows of z (always: f stays intact until a failed
+// system has been redone) and of the coupling columns' z, all chunk-major.
 SolveWs carve_solve(const band_desc* d, int32_t method, void* base, size_t* bytes) {
   Carve c(base);
   SolveWs w{};
-  const size_t rows = (size_t)spill_rows(d) * dtype_size(d->dtype);
+  const bool part = d->schedule == BAND_SCHED_PARTITIONED && kmode_for(d, method) > 0;
+  const int64_t r0 = spill_rows(d);
+  const int64_t pr = part ? part_rows_bound(d) : 0;
+  const size_t rows = (size_t)(r0 > pr ? r0 : pr) * dtype_size(d->dtype);
   w.al = c.take(rows);
   w.be = c.take(rows);
-  if (is_symbolic(method)) {
+  if (part) {
     w.zs = c.take(rows);
+    w.zv1 = c.take((size_t)pr * dtype_size(d->dtype));
+    if (may_be_pd(d)) w.zv2 = c.take((size_t)pr * dtype_size(d->dtype));
+  }
+  if (is_symbolic(method)) {
+    if (!w.zs) w.zs = c.take(rows);
     w.count = c.take(sizeof(unsigned long long));
     w.list = c.take(sizeof(int64_t) * (size_t)(d->nsys > 0 ? d->nsys : 1));
     w.nslots = d->nsys < kMaxFixSlots ? d->nsys : kMaxFixSlots;
@@ -63,10 +73,34 @@ FactorPtrs factor_ptrs(const band_desc* d, const void* factors) {
 // inside a batched launch of 30 such problems; below n = 32 the interface solve is a
 // large share of the work.
 bool choose_two_sided(const band_desc* d, bool alias) {
-  if (d->schedule == BAND_SCHED_THREAD) return false;
+  if (d->schedule == BAND_SCHED_THREAD || d->schedule == BAND_SCHED_PARTITIONED) return false;
   if (d->schedule == BAND_SCHED_TWO_SIDED) return true;
   if ((d->offsets && !d->systems) || alias) return false;   // whole ragged packings: thread
   return d->n >= 32;
+}
+
+// Chunk-major rows of one partitioned scratch array, for every chunk count: ceil(n / P)
+// rows of P chunks for nsys rounded up to 32 / P systems.
+int64_t part_rows_bound(const band_desc* d) { return round_up(d->n, 32) * round_up(d->nsys, 8); }
+
+// Lanes per system on the partitioned schedule (0: another schedule).  chunks == 0:
+// the fewest lanes (4 .. 32) that put 8 warps on every SM, while chunks keep 8 rows.
+int choose_parts(const band_desc* d) {
+  if (d->schedule != BAND_SCHED_PARTITIONED) return 0;
+  if (d->chunks) return d->chunks;
+  static int nsm_cache[64];
+  int dev = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess || dev < 0) dev = 0;
+  int nsm = dev < 64 ? nsm_cache[dev] : 0;
+  if (nsm == 0) {
+    if (cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess || nsm < 1)
+      nsm = 1;
+    if (dev < 64) nsm_cache[dev] = nsm;
+  }
+  const int64_t lanes = (int64_t)nsm * 8 * kWarp;
+  int P = 4;
+  while (P < 32 && d->nsys * P < lanes && d->n >= (int64_t)16 * P) P *= 2;
+  return P;
 }
 
 band_status make_direct(const band_desc* desc, int32_t method, const void* const diag[5],
@@ -89,6 +123,7 @@ band_status make_direct(const band_desc* desc, int32_t method, const void* const
   r->two_ok = kmode != 0;
   r->alias = x == f && !r->symbolic;   // symbolic methods keep f until the backward sweep
   r->two_sided = r->two_ok && choose_two_sided(desc, r->alias);
+  r->parts = r->two_ok ? choose_parts(desc) : 0;
   r->d64 = DirectArgs<double>{L, W,
                               (const double*)diag[0], (const double*)diag[1],
                               (const double*)diag[2], (const double*)diag[3],
@@ -109,8 +144,19 @@ band_status make_direct(const band_desc* desc, int32_t method, const void* const
                          (kmode == 1 || (diag[0] && diag[4] && al16(diag[0]) && al16(diag[4])));
     r->d64.gran = r->d32.gran = (contig && aligned) ? 1 : 0;
   }
+  if (r->parts) {
+    const int64_t np = round_up(desc->nsys, 32 / r->parts);
+    r->d64.zs = (double*)w.zs;
+    r->d64.zv1 = (double*)w.zv1;
+    r->d64.zv2 = (double*)w.zv2;
+    r->d64.part_np = np;
+    r->d32.zs = (float*)w.zs;
+    r->d32.zv1 = (float*)w.zv1;
+    r->d32.zv2 = (float*)w.zv2;
+    r->d32.part_np = np;
+  }
   if (!r->symbolic) {
-    r->d64.zs = nullptr;
+    if (!r->parts) r->d64.zs = nullptr;
     r->d64.fix_count = nullptr;
     r->d64.fix_list = nullptr;
   } else {
@@ -175,7 +221,10 @@ band_status band_solve(const band_desc* desc, int32_t method, const void* factor
                         cudaSuccess)
     return BAND_ERR_CUDA;
   cudaError_t e;
-  if (r.two_sided)
+  if (r.parts)
+    e = desc->dtype == BAND_F64 ? launch_partition<double>(r.d64, r.kmode, r.parts, st)
+                                : launch_partition<float>(r.d32, r.kmode, r.parts, st);
+  else if (r.two_sided)
     e = desc->dtype == BAND_F64 ? launch_twisted<double>(r.d64, r.kmode, st)
                                 : launch_twisted<float>(r.d32, r.kmode, st);
   else

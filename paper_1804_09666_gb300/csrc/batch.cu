@@ -20,6 +20,7 @@
 
 #include "api_util.h"
 #include "kernels.h"
+#include "partition.cuh"
 #include "sip_impl.cuh"
 #include "sweeps.cuh"
 
@@ -31,7 +32,8 @@ enum : int32_t { kDirect64 = 0, kDirect32 = 1, kSip = 2 };
 struct BatchItem {
   int32_t kind;
   int16_t kmode;     // 1 TD, 2 PD, 0 per system
-  int16_t two_sided; // two threads (lanes l, l ^ 16) per system
+  int8_t two_sided;  // two threads (lanes l, l ^ 16) per system
+  int8_t parts;      // partitioned: lanes per system (32 / parts systems a warp), or 0
   int64_t task0;     // first warp of this problem
   union {
     DirectArgs<double> d64;
@@ -75,6 +77,27 @@ __device__ __forceinline__ void run_direct(const DirectArgs<T>& p, int kmode, in
   else direct_one<T, 2>(p, t, stage);
 }
 
+template <typename T>
+__device__ __forceinline__ void run_partition(const DirectArgs<T>& p, int kmode, int parts,
+                                              int64_t warp, void* stage) {
+  T* xch = static_cast<T*>(stage);
+  if (kmode == 1) {
+    switch (parts) {
+      case 4: partition_one<T, 1, 4>(p, warp, xch); break;
+      case 8: partition_one<T, 1, 8>(p, warp, xch); break;
+      case 16: partition_one<T, 1, 16>(p, warp, xch); break;
+      default: partition_one<T, 1, 32>(p, warp, xch); break;
+    }
+  } else {
+    switch (parts) {
+      case 4: partition_one<T, 2, 4>(p, warp, xch); break;
+      case 8: partition_one<T, 2, 8>(p, warp, xch); break;
+      case 16: partition_one<T, 2, 16>(p, warp, xch); break;
+      default: partition_one<T, 2, 32>(p, warp, xch); break;
+    }
+  }
+}
+
 // One warp task: 32 systems of one problem (16 on the two-sided schedule).  Blocks are
 // handed out by the hardware scheduler as earlier ones finish, in task order, and the
 // host orders the problems heaviest first.  (A persistent loop over a task counter was
@@ -93,6 +116,12 @@ __global__ void __launch_bounds__(32 * kBatchWarps, BATCH_MIN_BLOCKS) k_batch(co
   int j = 0;
   while (j + 1 < t.count && t.it[j + 1].task0 <= task) ++j;
   const BatchItem& b = t.it[j];
+  if (b.parts) {
+    const int64_t w = task - b.task0;
+    if (b.kind == kDirect64) run_partition<double>(b.u.d64, b.kmode, b.parts, w, stage);
+    else run_partition<float>(b.u.d32, b.kmode, b.parts, w, stage);
+    return;
+  }
   if (b.two_sided) {         // 16 systems per warp
     const int64_t t2 = (task - b.task0) * 16 + (threadIdx.x & 15);
     if (b.kind == kDirect64) {
@@ -160,7 +189,8 @@ using namespace band;
 
 // Relative cost of one warp task of a problem: rows on its longest dependent chain times
 // the work per row (SIP's first update and residual ~2.5x a PD sweep, TD ~0.6x, FP32
-// ~0.5x).  Tasks are handed out heaviest problem first.
+// ~0.5x; a partitioned chunk row ~2.3x, plus the interface solve).  Tasks are handed out
+// heaviest problem first.
 static double task_cost(const band_problem& q) {
   const band_desc* d = q.desc;
   double rows = (double)d->n;
@@ -171,6 +201,12 @@ static double task_cost(const band_problem& q) {
     const bool td = d->hbw == nullptr && d->half_bw == 1;
     w = td ? 0.6 : 1.0;
     if (d->dtype == BAND_F32) w *= 0.5;
+    if (kmode_for(d, q.method) > 0) {
+      const bool alias = q.x == q.f && !is_symbolic(q.method);
+      const int P = choose_parts(d);
+      if (P) rows = rows / P * 2.3 + 8.0 * P;
+      else if (choose_two_sided(d, alias)) rows *= 0.5;
+    }
   }
   return rows * w;
 }
@@ -215,6 +251,7 @@ extern "C" band_status band_solve_batch(const band_problem* in, int32_t count, v
       if (v != BAND_OK) return v;
       b.kmode = (int16_t)r.kmode;
       b.two_sided = r.two_sided ? 1 : 0;
+      b.parts = (int8_t)r.parts;
       // Uniform contiguous problems read through L1 here: next to the batch's other
       // tasks that measured faster than granule staging (ADI step 4.85 vs 5.16 ms);
       // ragged buckets keep it (65536 systems: 10.7 -> 8.7 ms).
@@ -247,6 +284,7 @@ extern "C" band_status band_solve_batch(const band_problem* in, int32_t count, v
       b.kind = kSip;
       b.kmode = 2;
       b.two_sided = 0;
+      b.parts = 0;
       b.u.sip = sa;
       counters[ncounters++] = sa.tail_count;
       pend_clear[npend] = sa.rn_sys;
@@ -256,7 +294,12 @@ extern "C" band_status band_solve_batch(const band_problem* in, int32_t count, v
       return BAND_ERR_ARG;
     }
     b.task0 = warps;
-    warps += b.two_sided ? (q.desc->nsys + 15) / 16 : (q.desc->nsys + kWarp - 1) / kWarp;
+    if (b.parts) {
+      const int per = kWarp / b.parts;
+      warps += (q.desc->nsys + per - 1) / per;
+    } else {
+      warps += b.two_sided ? (q.desc->nsys + 15) / 16 : (q.desc->nsys + kWarp - 1) / kWarp;
+    }
     ++t.count;
   }
   t.total = warps;

@@ -16,6 +16,7 @@
 // sweep writes x.
 #include "common.cuh"
 #include "kernels.h"
+#include "partition.cuh"
 #include "sweeps.cuh"
 
 namespace band {
@@ -75,6 +76,43 @@ cudaError_t launch_twisted(const DirectArgs<T>& p, int kmode, cudaStream_t st) {
 }
 template cudaError_t launch_twisted<double>(const DirectArgs<double>&, int, cudaStream_t);
 template cudaError_t launch_twisted<float>(const DirectArgs<float>&, int, cudaStream_t);
+
+// P lanes per system, 32 / P systems per warp (partition.cuh); one bandwidth
+template <typename T, int K, int P>
+__global__ void __launch_bounds__(32 * SweepWarps<T>::value) k_partition(const DirectArgs<T> p) {
+  extern __shared__ __align__(16) unsigned char stage_mem[];
+  T* xch = reinterpret_cast<T*>(stage_mem + (threadIdx.x >> 5) * part_xch_bytes<T>());
+  const int64_t warp = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+  partition_one<T, K, P>(p, warp, xch);
+}
+
+template <typename T, int K>
+static cudaError_t launch_partition_k(const DirectArgs<T>& p, int parts, unsigned grid, int tb,
+                                      size_t smem, cudaStream_t st) {
+  switch (parts) {
+    case 4: k_partition<T, K, 4><<<grid, tb, smem, st>>>(p); break;
+    case 8: k_partition<T, K, 8><<<grid, tb, smem, st>>>(p); break;
+    case 16: k_partition<T, K, 16><<<grid, tb, smem, st>>>(p); break;
+    case 32: k_partition<T, K, 32><<<grid, tb, smem, st>>>(p); break;
+    default: return cudaErrorInvalidValue;
+  }
+  return cudaGetLastError();
+}
+
+template <typename T>
+cudaError_t launch_partition(const DirectArgs<T>& p, int kmode, int parts, cudaStream_t st) {
+  if (p.L.nsys == 0) return cudaSuccess;
+  if (parts != 4 && parts != 8 && parts != 16 && parts != 32) return cudaErrorInvalidValue;
+  const int64_t warps = (p.L.nsys + 32 / parts - 1) / (32 / parts);
+  const int wpb = SweepWarps<T>::value;
+  const unsigned grid = (unsigned)((warps + wpb - 1) / wpb);
+  const size_t smem = (size_t)wpb * part_xch_bytes<T>();
+  if (kmode == 1) return launch_partition_k<T, 1>(p, parts, grid, 32 * wpb, smem, st);
+  if (kmode == 2) return launch_partition_k<T, 2>(p, parts, grid, 32 * wpb, smem, st);
+  return cudaErrorInvalidValue;
+}
+template cudaError_t launch_partition<double>(const DirectArgs<double>&, int, int, cudaStream_t);
+template cudaError_t launch_partition<float>(const DirectArgs<float>&, int, int, cudaStream_t);
 
 // ---------------------------------------------------------------------------
 // factorisation only: gamma, 1/mu, alpha, beta per row (interleaved like the spill)

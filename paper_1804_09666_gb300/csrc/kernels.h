@@ -24,6 +24,10 @@ struct DirectArgs {
   int64_t* fix_list;
   int32_t gran;                    // contiguous rows staged in 16-byte granules (GranRing)
   const int32_t* skip;             // per system id, or null: nonzero = leave the system alone
+  // partitioned schedule: forward rows of the coupling columns (chunk-major, like al,
+  // be and zs then) and the slots per chunk row (nsys rounded up to 32 / chunks)
+  T *zv1, *zv2;
+  int64_t part_np;
 };
 
 template <typename T>
@@ -61,6 +65,8 @@ struct SymArgs {
 
 template <typename T> cudaError_t launch_direct(const DirectArgs<T>&, int kmode, cudaStream_t);
 template <typename T> cudaError_t launch_twisted(const DirectArgs<T>&, int kmode, cudaStream_t);
+template <typename T>
+cudaError_t launch_partition(const DirectArgs<T>&, int kmode, int parts, cudaStream_t);
 template <typename T> cudaError_t launch_factor(const FactorArgs<T>&, int kmode, cudaStream_t);
 template <typename T> cudaError_t launch_fsolve(const FactoredArgs<T>&, int kmode, cudaStream_t);
 cudaError_t launch_symbolic_fixup(const SymArgs&, cudaStream_t);
@@ -68,7 +74,7 @@ size_t symbolic_slot_bytes(int64_t nmax);
 
 // Workspace of band_solve (see api.cu).
 struct SolveWs {
-  void *al, *be, *zs, *count, *list, *slots;
+  void *al, *be, *zs, *count, *list, *slots, *zv1, *zv2;
   int64_t nslots;
 };
 SolveWs carve_solve(const band_desc* d, int32_t method, void* base, size_t* bytes);
@@ -78,8 +84,9 @@ SolveWs carve_solve(const band_desc* d, int32_t method, void* base, size_t* byte
 struct DirectReq {
   int kmode;
   bool symbolic;
-  bool two_ok;          // the two-sided schedule applies (numeric, one bandwidth)
+  bool two_ok;          // the two-sided and partitioned schedules apply (one bandwidth)
   bool two_sided;       // schedule: two threads per system
+  int parts;            // schedule: partitioned, lanes (chunks) per system; 0 = not
   bool alias;           // x is f
   DirectArgs<double> d64;
   DirectArgs<float> d32;
@@ -92,6 +99,8 @@ band_status make_direct(const band_desc* desc, int32_t method, const void* const
                         const void* f, void* x, int32_t* sys_status, void* ws, size_t ws_bytes,
                         DirectReq* r);
 bool choose_two_sided(const band_desc* d, bool alias);
+int choose_parts(const band_desc* d);
+int64_t part_rows_bound(const band_desc* d);
 
 // host-side helpers shared by the entry points (defined in api.cu and the feature files)
 struct FactorPtrs {

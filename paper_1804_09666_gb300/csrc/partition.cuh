@@ -1,0 +1,415 @@
+// partition.cuh -- the partitioned schedule: P lanes of a warp per system (P = 4, 8,
+// 16 or 32; 32 / P systems per warp), lane k eliminating chunk k of P consecutive row
+// blocks of its system.
+//
+// Chunk k (rows s0 .. s0+L-1, block A_k of the matrix) couples to the K unknowns just
+// above it, u_k = (x_{s0-K} .. x_{s0-1}), through the a, b entries of its first rows
+// (the columns B_k), and to the K just below it, v_k = (x_{s0+L} .. x_{s0+L+K-1}),
+// through the d, e entries of its last rows (C_k).  Hence
+//   x_k = g_k - V_k u_k - W_k v_k,   g = A_k^{-1} f_k,  V = A_k^{-1} B_k,  W = A_k^{-1} C_k.
+// Each lane factors its block with the NPDM / NTDM recurrence of Sec. 1 (U unit upper),
+// carrying f and B's K columns through the forward sweep (C's columns have entries in
+// the last K rows only, so their forward values are formed at the end).  A first
+// backward sweep over the five (three for TD) columns keeps only their top and bottom K
+// rows: with y_k = (top K rows, bottom K rows) of chunk k, these give the
+// block-tridiagonal interface system
+//   y_k + L_k y_{k-1} + U_k y_{k+1} = (g_top, g_bottom)_k,
+//   L_k y_{k-1} = V_k (bottom K rows of y_{k-1}),   U_k y_{k+1} = W_k (top K rows of y_{k+1}),
+// which the system's first lane solves by block elimination (2K x 2K blocks, partial
+// pivoting inside each block).  Then each lane back-substitutes its chunk once more,
+// with z - z_V u_k - z_W v_k in place of z: x_k itself.
+// Arithmetic per row: about 2.3x NPDM (PD) and 1.8x NTDM (TD); the dependent chain of a
+// system is n / P rows long instead of n (one thread) or n / 2 (two-sided).
+//
+// Scratch (alpha, beta, z of f, z of B's columns) is chunk-major: row j of chunk k of
+// the batch's t-th system at ((j * np + t) * P + k), np = nsys rounded up to 32 / P, so
+// the lanes of a warp touch consecutive elements.  z of f goes to x (numeric methods)
+// or to the zs rows (symbolic methods, which keep f intact for the fix-up).
+//
+// A chunk may meet a zero pivot where NPDM's order does not, and the interface
+// elimination may meet a singular block: an STDM / SPDM system then goes to the symbolic
+// fix-up, and an NTDM / NPDM system is redone by its first lane with NPDM alone (so
+// BAND_ERR_ZERO_PIVOT keeps its meaning).  Systems with fewer than 8 P rows are solved by
+// their first lane with NPDM.
+#pragma once
+#include "common.cuh"
+#include "kernels.h"
+#include "sweeps.cuh"
+
+namespace band {
+
+constexpr int kPartMinRowsPerChunk = 8;
+
+// Values of T per lane in the interface exchange: y's right-hand side (2K) and the
+// 2K rows of V's and W's K columns.
+template <int K>
+__host__ __device__ constexpr int part_words() { return 2 * K + 4 * K * K; }
+
+template <typename T>
+__host__ __device__ constexpr int part_xch_bytes() { return 32 * part_words<2>() * (int)sizeof(T); }
+static_assert(part_xch_bytes<double>() <= stage_bytes_per_warp<double>(),
+              "the interface exchange lives in the warp's staging area");
+static_assert(part_xch_bytes<float>() <= stage_bytes_per_warp<float>(),
+              "the interface exchange lives in the warp's staging area");
+
+template <int P>
+__device__ __forceinline__ int64_t part_idx(int64_t j, int64_t t, int64_t np, int k) {
+  return (j * np + t) * P + k;
+}
+
+// Solves M X = R in place (R becomes X) for NB unknowns and NR columns with partial
+// pivoting; false on a zero pivot.  Row exchanges are selects (M stays in registers).
+template <typename T, int NB, int NR>
+__device__ __forceinline__ bool block_solve(T (&M)[NB][NB], T (&R)[NB][NR]) {
+  T inv[NB];
+#pragma unroll
+  for (int c = 0; c < NB; ++c) {
+    int piv = c;
+    T big = fabs(M[c][c]);
+#pragma unroll
+    for (int r = c + 1; r < NB; ++r)
+      if (fabs(M[r][c]) > big) { big = fabs(M[r][c]); piv = r; }
+#pragma unroll
+    for (int r = c + 1; r < NB; ++r) {
+      const bool sw = (r == piv);
+#pragma unroll
+      for (int k = c; k < NB; ++k) {
+        const T u = M[c][k], v = M[r][k];
+        M[c][k] = sw ? v : u;
+        M[r][k] = sw ? u : v;
+      }
+#pragma unroll
+      for (int k = 0; k < NR; ++k) {
+        const T u = R[c][k], v = R[r][k];
+        R[c][k] = sw ? v : u;
+        R[r][k] = sw ? u : v;
+      }
+    }
+    if (is_zero(M[c][c])) return false;
+    inv[c] = rcp<T>(M[c][c]);
+#pragma unroll
+    for (int r = c + 1; r < NB; ++r) {
+      const T l = M[r][c] * inv[c];
+#pragma unroll
+      for (int k = c + 1; k < NB; ++k) M[r][k] = fma(-l, M[c][k], M[r][k]);
+#pragma unroll
+      for (int k = 0; k < NR; ++k) R[r][k] = fma(-l, R[c][k], R[r][k]);
+    }
+  }
+#pragma unroll
+  for (int c = NB - 1; c >= 0; --c) {
+#pragma unroll
+    for (int k = 0; k < NR; ++k) {
+      T v = R[c][k];
+#pragma unroll
+      for (int m = c + 1; m < NB; ++m) v = fma(-M[c][m], R[m][k], v);
+      R[c][k] = v * inv[c];
+    }
+  }
+  return true;
+}
+
+// NPDM / NTDM on one system by one lane, scratch in the chunk-major layout (the redo of
+// a failed partitioned system, and systems too short to cut).  On a zero pivot: the
+// fix-up list (symbolic methods) or BAND_ERR_ZERO_PIVOT.
+template <typename T, int K, int P>
+__device__ __noinline__ void part_serial(const DirectArgs<T>& p, int64_t t) {
+  const int64_t s = p.L.sys(t);
+  const int64_t n = p.L.rows(s);
+  const int64_t q0 = p.L.base(s), es = p.L.stride();
+  const int64_t np = p.part_np;
+  T al1 = 0, al2 = 0, be1 = 0, be2 = 0, z1 = 0, z2 = 0;
+  for (int64_t i = 0; i < n; ++i) {
+    const int64_t q = q0 + i * es;
+    RowIn<T> r;
+    load_in<T, K>(p, q, r);
+    if (!forward_row<T, K>(p, i, n, q, part_idx<P>(i / P, t, np, (int)(i % P)), r.a, r.b, r.c,
+                           r.d, r.e, r.f, al1, al2, be1, be2, z1, z2)) {
+      if (p.fix_list) {
+        const unsigned long long c = atomicAdd(p.fix_count, 1ull);
+        p.fix_list[c] = t;
+      } else {
+        set_status(p.status, s, BAND_ERR_ZERO_PIVOT);
+      }
+      return;
+    }
+  }
+  T x1 = 0, x2 = 0;
+  bool bad = false;
+  for (int64_t i = n - 1; i >= 0; --i) {
+    const int64_t q = q0 + i * es;
+    const int64_t w = part_idx<P>(i / P, t, np, (int)(i % P));
+    T xi = fma(-p.al[w], x1, p.zs ? p.zs[w] : p.x[q]);
+    if (K == 2) xi = fma(-p.be[w], x2, xi);
+    p.x[q] = xi;
+    bad |= not_finite(xi);
+    x2 = x1;
+    x1 = xi;
+  }
+  set_status(p.status, s, bad ? BAND_ERR_NONFINITE : BAND_OK);
+}
+
+// The warp's 32 / P systems, positions t = warp * (32 / P) + (lane / P).  xch: the
+// warp's exchange area (part_xch_bytes<T>() bytes of shared memory).  Every lane of the
+// warp reaches every __syncwarp and shuffle.
+template <typename T, int K, int P>
+__device__ __forceinline__ void partition_one(const DirectArgs<T>& p, int64_t warp, T* xch) {
+  constexpr int NB = 2 * K;
+  constexpr int PW = part_words<K>();
+  constexpr int G = 32 / P;
+  const unsigned full = 0xffffffffu;
+  const int lane = (int)(threadIdx.x & 31);
+  const int grp = lane / P, k = lane % P;
+  const unsigned gmask = P == 32 ? full : (((1u << P) - 1u) << (grp * P));
+  const int64_t t = warp * G + grp;
+  bool active = t < p.L.nsys;
+  const int64_t s = active ? p.L.sys(t) : 0;
+  if (active && p.skip && p.skip[s]) active = false;
+  const int64_t n = active ? p.L.rows(s) : 0;
+  // 0: nothing, 1: the first lane alone (short system), 2: partitioned
+  const int mode = !active ? 0 : (n < (int64_t)kPartMinRowsPerChunk * P ? 1 : 2);
+  const int64_t q0 = active ? p.L.base(s) : 0, es = active ? p.L.stride() : 0;
+  const int64_t L0 = n / P, rem = n % P;
+  const int64_t s0 = k * L0 + (k < rem ? k : rem);
+  const int64_t L = mode == 2 ? L0 + (k < rem ? 1 : 0) : 0;
+  const int64_t np = p.part_np;
+  T* const zsf = p.zs;        // z of f: zs rows (symbolic methods) or x
+
+  // ---- forward: the chunk's LU with f and B's columns
+  T al1 = 0, al2 = 0, be1 = 0, be2 = 0;
+  T zf1 = 0, zf2 = 0, zv11 = 0, zv12 = 0, zv21 = 0, zv22 = 0;
+  T gl = 0, rcl = 0, rcl2 = 0, el2 = 0, dl = 0, el = 0;   // last rows, for C's columns
+  bool zero = false;
+  {
+    RowIn<T> r0, r1;
+    if (L > 0) load_in<T, K>(p, q0 + s0 * es, r0);
+    for (int64_t j = 0; j < L; ++j) {
+      const int64_t i = s0 + j;
+      if (j + 1 < L) load_in<T, K>(p, q0 + (i + 1) * es, r1);
+      // the matrix's masks, then the chunk's own block
+      const T ag = (K == 2 && i >= 2) ? r0.a : T(0);
+      const T bg = (i >= 1) ? r0.b : T(0);
+      const T dg = (i + 1 < n) ? r0.d : T(0);
+      const T eg = (K == 2 && i + 2 < n) ? r0.e : T(0);
+      const T aa = (j >= 2) ? ag : T(0);
+      const T bb = (j >= 1) ? bg : T(0);
+      const T dd = (j + 1 < L) ? dg : T(0);
+      const T ee = (j + 2 < L) ? eg : T(0);
+      // B's columns (unknowns x_{s0-K} ..): row 0 holds a (x_{s0-2}) and b (x_{s0-1}),
+      // row 1 a (x_{s0-1}); TD: row 0 holds b
+      T rv1 = 0, rv2 = 0;
+      if (K == 2) {
+        rv1 = j == 0 ? ag : T(0);
+        rv2 = j == 0 ? bg : (j == 1 ? ag : T(0));
+      } else {
+        rv1 = j == 0 ? bg : T(0);
+      }
+      T g, m;
+      if (K == 2) {
+        g = fma(-al2, aa, bb);
+        m = fma(-al1, g, fma(-be2, aa, r0.c));
+      } else {
+        g = bb;
+        m = fma(-al1, g, r0.c);
+      }
+      if (is_zero(m)) { zero = true; break; }
+      const T rc = rcp<T>(m);
+      const T alv = (K == 2 ? fma(-be1, g, dd) : dd) * rc;
+      const int64_t w = part_idx<P>(j, t, np, k);
+      p.al[w] = alv;
+      T zf, zv1;
+      if (K == 2) {
+        const T bev = ee * rc;
+        p.be[w] = bev;
+        zf = fma(-zf1, g, fma(-zf2, aa, r0.f)) * rc;
+        zv1 = fma(-zv11, g, fma(-zv12, aa, rv1)) * rc;
+        const T zv2 = fma(-zv21, g, fma(-zv22, aa, rv2)) * rc;
+        p.zv2[w] = zv2;
+        zv22 = zv21; zv21 = zv2;
+        be2 = be1; be1 = bev;
+      } else {
+        zf = fma(-zf1, g, r0.f) * rc;
+        zv1 = fma(-zv11, g, rv1) * rc;
+      }
+      if (zsf) zsf[w] = zf; else p.x[q0 + i * es] = zf;
+      p.zv1[w] = zv1;
+      al2 = al1; al1 = alv;
+      zf2 = zf1; zf1 = zf; zv12 = zv11; zv11 = zv1;
+      rcl2 = rcl; rcl = rc; gl = g; el2 = el; el = eg; dl = dg;
+      r0 = r1;
+    }
+  }
+  // forward values of C's columns (nonzero only in the last K rows).  PD: column 1
+  // (x_{s0+L}) has e at row L-2 and d at row L-1, column 2 (x_{s0+L+1}) e at row L-1.
+  T zw1_2 = 0, zw1_1 = 0, zw2_1 = 0;     // zw<column>_<rows from the end>
+  if (!zero && L > 0) {
+    if (K == 2) {
+      zw1_2 = el2 * rcl2;
+      zw1_1 = fma(-zw1_2, gl, dl) * rcl;
+      zw2_1 = el * rcl;
+    } else {
+      zw1_1 = dl * rcl;
+    }
+  }
+  // ---- first backward sweep: top and bottom K rows of g, V, W
+  // y-slot of row j: top rows 0 .. K-1 -> 0 .. K-1, bottom rows L-K .. L-1 -> K .. 2K-1
+  T yf[NB], yv1[NB], yv2[NB], yw1[NB], yw2[NB];
+#pragma unroll
+  for (int c = 0; c < NB; ++c) yf[c] = yv1[c] = yv2[c] = yw1[c] = yw2[c] = T(0);
+  if (!zero && L > 0) {
+    T xf1 = 0, xf2 = 0, xv11 = 0, xv12 = 0, xv21 = 0, xv22 = 0;
+    T xw11 = 0, xw12 = 0, xw21 = 0, xw22 = 0;
+    for (int64_t j = L - 1; j >= 0; --j) {
+      const int64_t w = part_idx<P>(j, t, np, k);
+      const T a = p.al[w];
+      const T zf = zsf ? zsf[w] : p.x[q0 + (s0 + j) * es];
+      const T zv1 = p.zv1[w];
+      // forward values of W's columns at this row
+      const T zw1 = j == L - 1 ? zw1_1 : (K == 2 && j == L - 2 ? zw1_2 : T(0));
+      T xf = fma(-a, xf1, zf);
+      T xv1 = fma(-a, xv11, zv1);
+      T xw1 = fma(-a, xw11, zw1);
+      T xv2 = 0, xw2 = 0;
+      if (K == 2) {
+        const T b = p.be[w];
+        const T zv2 = p.zv2[w];
+        const T zw2 = j == L - 1 ? zw2_1 : T(0);
+        xf = fma(-b, xf2, xf);
+        xv1 = fma(-b, xv12, xv1);
+        xw1 = fma(-b, xw12, xw1);
+        xv2 = fma(-b, xv22, fma(-a, xv21, zv2));
+        xw2 = fma(-b, xw22, fma(-a, xw21, zw2));
+        xv22 = xv21; xv21 = xv2; xw22 = xw21; xw21 = xw2;
+      }
+#pragma unroll
+      for (int c = 0; c < K; ++c) {
+        if (j == c) {
+          yf[c] = xf; yv1[c] = xv1; yv2[c] = xv2; yw1[c] = xw1; yw2[c] = xw2;
+        }
+        if (j == L - K + c) {
+          yf[K + c] = xf; yv1[K + c] = xv1; yv2[K + c] = xv2; yw1[K + c] = xw1; yw2[K + c] = xw2;
+        }
+      }
+      xf2 = xf1; xf1 = xf; xv12 = xv11; xv11 = xv1; xw12 = xw11; xw11 = xw1;
+    }
+  }
+  // ---- the interface system, by the system's first lane
+  {
+    T* my = xch + lane * PW;
+#pragma unroll
+    for (int c = 0; c < NB; ++c) {
+      my[c] = yf[c];
+      my[NB + c] = yv1[c];             // V's column 1
+      my[2 * NB + c] = yw1[c];         // W's column 1
+      if (K == 2) {
+        my[3 * NB + c] = yv2[c];       // V's column 2
+        my[4 * NB + c] = yw2[c];       // W's column 2
+      }
+    }
+  }
+  const bool gzero = (__ballot_sync(full, zero) & gmask) != 0;
+  __syncwarp();
+  bool fail = gzero;
+  if (mode == 2 && k == 0 && !fail) {
+    // Block elimination over the chunks: with D_k = I - L_k Cp_{k-1} (D_0 = I),
+    // hp_k = D_k^{-1} (rhs_k - L_k hp_{k-1}) and Cp_k = D_k^{-1} U_k, then
+    // y_{P-1} = hp_{P-1}, y_k = hp_k - Cp_k y_{k+1}.  Only Cp's first K columns are
+    // nonzero (U_k acts on the top K rows of y_{k+1}); hp overwrites slots [0, NB) of
+    // chunk k and Cp's column c slots [NB (1 + c), NB (2 + c)).
+    T* const base = xch + grp * P * PW;
+    for (int kk = 0; kk < P; ++kk) {
+      T* e = base + kk * PW;
+      T Dm[NB][NB];
+      T R[NB][K + 1];
+#pragma unroll
+      for (int r = 0; r < NB; ++r) {
+#pragma unroll
+        for (int c = 0; c < NB; ++c) Dm[r][c] = (r == c) ? T(1) : T(0);
+        R[r][K] = e[r];
+        R[r][0] = e[2 * NB + r];
+        if (K == 2) R[r][K - 1] = e[4 * NB + r];
+      }
+      if (kk > 0) {
+        const T* ep = e - PW;
+#pragma unroll
+        for (int r = 0; r < NB; ++r) {
+          T vr[K];
+          vr[0] = e[NB + r];
+          if (K == 2) vr[K - 1] = e[3 * NB + r];
+#pragma unroll
+          for (int m = 0; m < K; ++m) {
+#pragma unroll
+            for (int c = 0; c < K; ++c) Dm[r][c] = fma(-vr[m], ep[NB * (1 + c) + K + m], Dm[r][c]);
+            R[r][K] = fma(-vr[m], ep[K + m], R[r][K]);
+          }
+        }
+      }
+      if (!block_solve<T, NB, K + 1>(Dm, R)) { fail = true; break; }
+#pragma unroll
+      for (int r = 0; r < NB; ++r) {
+        e[r] = R[r][K];
+#pragma unroll
+        for (int c = 0; c < K; ++c) e[NB * (1 + c) + r] = R[r][c];
+      }
+    }
+    if (!fail) {
+      for (int kk = P - 2; kk >= 0; --kk) {
+        T* e = base + kk * PW;
+        const T* en = e + PW;
+#pragma unroll
+        for (int r = 0; r < NB; ++r) {
+          T v = e[r];
+#pragma unroll
+          for (int c = 0; c < K; ++c) v = fma(-e[NB * (1 + c) + r], en[c], v);
+          e[r] = v;
+        }
+      }
+    }
+  }
+  fail = __shfl_sync(full, (int)fail, grp * P) != 0;
+  __syncwarp();
+  // ---- redo (short systems, failed eliminations) by the first lane, or the second
+  // backward sweep with z - z_V u - z_W v
+  if (k == 0 && (mode == 1 || (mode == 2 && fail))) {
+    if (mode == 2 && p.fix_list) {
+      const unsigned long long c = atomicAdd(p.fix_count, 1ull);
+      p.fix_list[c] = t;
+    } else {
+      part_serial<T, K, P>(p, t);
+    }
+  }
+  const bool back = mode == 2 && !fail;
+  bool bad = false;
+  if (back) {
+    T u[K], v[K];
+#pragma unroll
+    for (int m = 0; m < K; ++m) {
+      u[m] = k > 0 ? xch[(lane - 1) * PW + K + m] : T(0);
+      v[m] = k + 1 < P ? xch[(lane + 1) * PW + m] : T(0);
+    }
+    T x1 = 0, x2 = 0;
+    for (int64_t j = L - 1; j >= 0; --j) {
+      const int64_t w = part_idx<P>(j, t, np, k);
+      const int64_t q = q0 + (s0 + j) * es;
+      T z = zsf ? zsf[w] : p.x[q];
+      z = fma(-p.zv1[w], u[0], z);
+      if (K == 2) z = fma(-p.zv2[w], u[K - 1], z);
+      if (j == L - 1) {
+        z = fma(-zw1_1, v[0], z);
+        if (K == 2) z = fma(-zw2_1, v[K - 1], z);
+      } else if (K == 2 && j == L - 2) {
+        z = fma(-zw1_2, v[0], z);
+      }
+      T xi = fma(-p.al[w], x1, z);
+      if (K == 2) xi = fma(-p.be[w], x2, xi);
+      p.x[q] = xi;
+      bad |= not_finite(xi);
+      x2 = x1;
+      x1 = xi;
+    }
+  }
+  const bool gbad = (__ballot_sync(full, bad) & gmask) != 0;
+  if (back && k == 0) set_status(p.status, s, gbad ? BAND_ERR_NONFINITE : BAND_OK);
+}
+
+}  // namespace band

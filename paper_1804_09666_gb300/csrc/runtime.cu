@@ -54,18 +54,15 @@ bool tunable(const band_problem& q) {
   return kmode_for(q.desc, q.method) > 0;
 }
 
-band_status time_one(const band_problem& q, int32_t schedule, int32_t reps, cudaStream_t st,
-                     cudaEvent_t e0, cudaEvent_t e1, float* best) {
-  band_desc d = *q.desc;
-  d.schedule = schedule;
-  band_problem p = q;
-  p.desc = &d;
-  band_status v = band_solve_batch(&p, 1, st);            // warm-up
+// Best of `reps` timed band_solve_batch launches of the list, after one warm-up.
+band_status time_batch(const band_problem* p, int32_t count, int32_t reps, cudaStream_t st,
+                       cudaEvent_t e0, cudaEvent_t e1, float* best) {
+  band_status v = band_solve_batch(p, count, st);            // warm-up
   if (v != BAND_OK) return v;
   *best = INFINITY;
   for (int r = 0; r < reps; ++r) {
     if (cudaEventRecord(e0, st) != cudaSuccess) return BAND_ERR_CUDA;
-    v = band_solve_batch(&p, 1, st);
+    v = band_solve_batch(p, count, st);
     if (v != BAND_OK) return v;
     if (cudaEventRecord(e1, st) != cudaSuccess || cudaEventSynchronize(e1) != cudaSuccess)
       return BAND_ERR_CUDA;
@@ -74,6 +71,64 @@ band_status time_one(const band_problem& q, int32_t schedule, int32_t reps, cuda
     *best = std::min(*best, ms);
   }
   return BAND_OK;
+}
+
+band_status time_one(const band_problem& q, int32_t schedule, int32_t reps, cudaStream_t st,
+                     cudaEvent_t e0, cudaEvent_t e1, float* best) {
+  band_desc d = *q.desc;
+  d.schedule = schedule;
+  band_problem p = q;
+  p.desc = &d;
+  return time_batch(&p, 1, reps, st, e0, e1, best);
+}
+
+// A move of the joint phase has to gain this fraction of the launch time to be kept.
+constexpr float kJointGain = 0.02f;
+
+// Row diagonal dominance, |c_i| >= |a_i| + |b_i| + |d_i| + |e_i| (the entries inside the
+// matrix) for every row of every system, one thread per system; a row that fails
+// (NaN included) sets *bad.
+template <typename T, int K>
+__global__ void __launch_bounds__(128) k_dominance(const Layout L, const T* a, const T* b,
+                                                   const T* c, const T* d, const T* e, int* bad) {
+  const int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (t >= L.nsys) return;
+  const int64_t s = L.sys(t);
+  const int64_t n = L.rows(s), q0 = L.base(s), es = L.stride();
+  bool ok = true;
+  for (int64_t i = 0; i < n && ok; ++i) {
+    const int64_t q = q0 + i * es;
+    T off = (i >= 1 ? fabs(b[q]) : T(0)) + (i + 1 < n ? fabs(d[q]) : T(0));
+    if (K == 2) off += (i >= 2 ? fabs(a[q]) : T(0)) + (i + 2 < n ? fabs(e[q]) : T(0));
+    ok = fabs(c[q]) >= off;
+  }
+  if (!ok) atomicOr(bad, 1);
+}
+
+// Is every system of the problem row diagonally dominant?  (-1: CUDA error)
+int dominant(const band_problem& q, int* flag, cudaStream_t st) {
+  const band_desc* d = q.desc;
+  const Layout L = layout_of(d);
+  const int K = kmode_for(d, q.method);
+  if (cudaMemsetAsync(flag, 0, sizeof(int), st) != cudaSuccess) return -1;
+  const unsigned grid = (unsigned)((d->nsys + 127) / 128);
+  if (d->dtype == BAND_F64) {
+    const double* g[5];
+    for (int j = 0; j < 5; ++j) g[j] = static_cast<const double*>(q.diag[j]);
+    if (K == 2) k_dominance<double, 2><<<grid, 128, 0, st>>>(L, g[0], g[1], g[2], g[3], g[4], flag);
+    else k_dominance<double, 1><<<grid, 128, 0, st>>>(L, g[0], g[1], g[2], g[3], g[4], flag);
+  } else {
+    const float* g[5];
+    for (int j = 0; j < 5; ++j) g[j] = static_cast<const float*>(q.diag[j]);
+    if (K == 2) k_dominance<float, 2><<<grid, 128, 0, st>>>(L, g[0], g[1], g[2], g[3], g[4], flag);
+    else k_dominance<float, 1><<<grid, 128, 0, st>>>(L, g[0], g[1], g[2], g[3], g[4], flag);
+  }
+  int h = 1;
+  if (cudaGetLastError() != cudaSuccess ||
+      cudaMemcpyAsync(&h, flag, sizeof(int), cudaMemcpyDeviceToHost, st) != cudaSuccess ||
+      cudaStreamSynchronize(st) != cudaSuccess)
+    return -1;
+  return h == 0 ? 1 : 0;
 }
 
 }  // namespace
@@ -119,9 +174,11 @@ extern "C" int32_t band_plan_ragged(const int64_t* offsets, const int8_t* hbw, i
 }
 
 extern "C" band_status band_autotune(const band_problem* probs, int32_t count, int32_t reps,
-                                     int32_t* schedules, void* stream) {
+                                     int32_t flags, int32_t* schedules, int32_t* chunks,
+                                     void* stream) {
   if (count < 0 || count > BAND_MAX_BATCH || (count > 0 && (!probs || !schedules)) || reps < 1)
     return BAND_ERR_ARG;
+  if (flags & ~BAND_TUNE_JOINT) return BAND_ERR_ARG;
   for (int32_t i = 0; i < count; ++i)
     if (!probs[i].desc || !desc_ok(probs[i].desc)) return BAND_ERR_ARG;
   if (count == 0) return BAND_OK;
@@ -130,9 +187,13 @@ extern "C" band_status band_autotune(const band_problem* probs, int32_t count, i
   if (cudaGetDevice(&dev) != cudaSuccess) return BAND_ERR_CUDA;
   cudaEvent_t e0 = nullptr, e1 = nullptr;
   band_status out = BAND_OK;
+  for (int32_t i = 0; i < count; ++i) {
+    schedules[i] = probs[i].desc->schedule;
+    if (chunks) chunks[i] = probs[i].desc->chunks;
+  }
+  // per problem: thread per system or two-sided, timed alone (cached)
   for (int32_t i = 0; i < count && out == BAND_OK; ++i) {
     const band_problem& q = probs[i];
-    schedules[i] = q.desc->schedule;
     if (!tunable(q)) continue;
     const TuneKey key = tune_key(dev, q);
     {
@@ -156,6 +217,71 @@ extern "C" band_status band_autotune(const band_problem* probs, int32_t count, i
     schedules[i] = pick;
     std::lock_guard<std::mutex> lock(g_tune_mu);
     g_tune[key] = pick;
+  }
+  // joint: the whole list as one launch; problems move to the partitioned schedule,
+  // longest systems first, while that shortens the launch
+  if (out == BAND_OK && (flags & BAND_TUNE_JOINT)) {
+    std::vector<band_desc> descs((size_t)count);
+    std::vector<band_problem> list(probs, probs + count);
+    std::vector<int32_t> cand;
+    int* flag = nullptr;
+    for (int32_t i = 0; i < count && out == BAND_OK; ++i) {
+      descs[(size_t)i] = *probs[i].desc;
+      list[(size_t)i].desc = &descs[(size_t)i];
+      if (!tunable(probs[i])) continue;
+      descs[(size_t)i].schedule = schedules[i];
+      band_desc dp = *probs[i].desc;
+      dp.schedule = BAND_SCHED_PARTITIONED;
+      dp.chunks = 0;
+      size_t need = 0;
+      carve_solve(&dp, probs[i].method, nullptr, &need);
+      if (need > probs[i].ws_bytes || dp.n < 64) continue;
+      if (!flag && cudaMalloc(&flag, sizeof(int)) != cudaSuccess) {
+        out = BAND_ERR_CUDA;
+        break;
+      }
+      const int dom = dominant(probs[i], flag, st);
+      if (dom < 0) out = BAND_ERR_CUDA;
+      else if (dom) cand.push_back(i);
+    }
+    if (flag) cudaFree(flag);
+    std::stable_sort(cand.begin(), cand.end(),
+                     [&](int32_t x, int32_t y) { return probs[x].desc->n > probs[y].desc->n; });
+    if (!cand.empty() && !e0 &&
+        (cudaEventCreate(&e0) != cudaSuccess || cudaEventCreate(&e1) != cudaSuccess))
+      out = BAND_ERR_CUDA;
+    float base = 0.f;
+    if (out == BAND_OK && !cand.empty())
+      out = time_batch(list.data(), count, reps, st, e0, e1, &base);
+    int misses = 0;
+    for (size_t c = 0; c < cand.size() && out == BAND_OK && misses < 2; ++c) {
+      band_desc& d = descs[(size_t)cand[c]];
+      const band_desc keep = d;
+      int best_p = 0;
+      float best_t = base * (1.f - kJointGain);
+      for (int P = 4; P <= 32 && out == BAND_OK; P *= 2) {
+        if (d.n < (int64_t)16 * P) break;
+        d.schedule = BAND_SCHED_PARTITIONED;
+        d.chunks = P;
+        float tm = 0.f;
+        out = time_batch(list.data(), count, reps, st, e0, e1, &tm);
+        if (tm < best_t) { best_t = tm; best_p = P; }
+      }
+      d = keep;
+      if (out != BAND_OK) break;
+      if (best_p) {
+        d.schedule = BAND_SCHED_PARTITIONED;
+        d.chunks = best_p;
+        base = best_t;
+        misses = 0;
+      } else {
+        ++misses;
+      }
+    }
+    for (int32_t i = 0; i < count && out == BAND_OK; ++i) {
+      schedules[i] = descs[(size_t)i].schedule;
+      if (chunks) chunks[i] = descs[(size_t)i].chunks;
+    }
   }
   if (e0) cudaEventDestroy(e0);
   if (e1) cudaEventDestroy(e1);

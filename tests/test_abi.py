@@ -69,6 +69,11 @@ def test_workspace_sizes(lib):
     d = _desc()
     rows = 64 * 128 * 8
     assert lib.band_workspace_size(ct.byref(d), L.OP_SOLVE, L.NPDM, 0) >= 2 * rows
+    # partitioned: alpha, beta, z and the two coupling columns, chunk-major
+    dp = _desc(schedule=L.SCHED_PARTITIONED, chunks=8)
+    assert lib.band_workspace_size(ct.byref(dp), L.OP_SOLVE, L.NPDM, 0) >= 5 * rows
+    dt = _desc(half_bw=1, schedule=L.SCHED_PARTITIONED)
+    assert lib.band_workspace_size(ct.byref(dt), L.OP_SOLVE, L.NTDM, 0) >= 4 * rows
     assert lib.band_workspace_size(ct.byref(d), L.OP_SOLVE, L.SPDM, 0) > \
         lib.band_workspace_size(ct.byref(d), L.OP_SOLVE, L.NPDM, 0)
     assert lib.band_workspace_size(ct.byref(d), L.OP_FACTOR, L.NPDM, 0) >= 4 * rows
@@ -96,9 +101,11 @@ def test_bad_arguments_are_rejected_without_gpu(lib):
         (_desc(half_bw=2), L.NPDM, nul),          # PD without a, e
         (_desc(), 17, full),                      # unknown method
         (_desc(dtype=L.F32), L.SPDM, full),       # symbolic path is FP64 only
-        (_desc(schedule=3), L.NPDM, full),        # unknown schedule
+        (_desc(schedule=4), L.NPDM, full),        # unknown schedule
         (_desc(schedule=-1), L.NPDM, full),
-        (_desc(reserved=1), L.NPDM, full),
+        (_desc(chunks=8), L.NPDM, full),          # chunks without the partitioned schedule
+        (_desc(schedule=L.SCHED_PARTITIONED, chunks=6), L.NPDM, full),   # not 4/8/16/32
+        (_desc(schedule=L.SCHED_PARTITIONED, chunks=64), L.NPDM, full),
     ]
     for d, m, diag in cases:
         code = lib.band_solve(ct.byref(d), m, None, diag, 8, 8, None, 8, 1 << 30, None)

@@ -68,8 +68,11 @@ def test_uniform_bandwidth_and_edge_cases(lib):
 def test_autotune_rejects_bad_arguments(lib):
     from paper_1804_09666_gb300 import _lib as L
     out = (ct.c_int32 * 2)()
-    assert lib.band_autotune(None, 0, 3, out, None) == L.OK
+    outc = (ct.c_int32 * 2)()
+    assert lib.band_autotune(None, 0, 3, 0, out, outc, None) == L.OK
+    assert lib.band_autotune(None, 0, 3, L.TUNE_JOINT, out, None, None) == L.OK
+    assert lib.band_autotune(None, 0, 3, 2, out, outc, None) == L.ERR_ARG   # unknown flag
     arr = (L.BandProblem * 1)()
-    assert lib.band_autotune(arr, 1, 3, out, None) == L.ERR_ARG     # desc NULL
-    assert lib.band_autotune(arr, 65, 3, out, None) == L.ERR_ARG
-    assert lib.band_autotune(arr, 1, 0, out, None) == L.ERR_ARG     # reps < 1
+    assert lib.band_autotune(arr, 1, 3, 0, out, outc, None) == L.ERR_ARG     # desc NULL
+    assert lib.band_autotune(arr, 65, 3, 0, out, outc, None) == L.ERR_ARG
+    assert lib.band_autotune(arr, 1, 0, 0, out, outc, None) == L.ERR_ARG     # reps < 1
