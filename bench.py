@@ -415,7 +415,8 @@ def run_reference(args, world, rank):
 K_BATCH_SOURCES = ("include/band.h", "paper_1804_09666_gb300/csrc/batch.cu",
                    "paper_1804_09666_gb300/csrc/api_util.h", "paper_1804_09666_gb300/csrc/kernels.h",
                    "paper_1804_09666_gb300/csrc/common.cuh", "paper_1804_09666_gb300/csrc/sweeps.cuh",
-                   "paper_1804_09666_gb300/csrc/sip_impl.cuh")
+                   "paper_1804_09666_gb300/csrc/sip_impl.cuh",
+                   "paper_1804_09666_gb300/csrc/partition.cuh")
 TRAFFIC_RECORD = os.path.join(ROOT, "profiles", "k_batch_adi2048_dram.md")
 
 
@@ -497,13 +498,44 @@ def ragged_workload(dev):
     ms_whole = _time(lambda: band.solve_ragged(*(d[q] for q in "abcdef"), offs, hbw,
                                                n_max=int(B["sizes"].max()), total_rows=units),
                      reps=5)
+    two = band.RaggedPlan(*(d[q] for q in "abcdef"), B["offsets"], B["hbw"], schedule="two_sided")
+    ms_two = _time(two.run, reps=5)
+    parted = [{"n_max": int(bk[2]), "half_bw": int(bk[3]), "systems": int(bk[1]), "chunks": int(c)}
+              for bk, v, c in zip(plan.buckets, plan.schedules, plan.chunks) if v == 3]
     return {"workload": "65536 ragged systems, n log-uniform in [16, 8192], half TD / half PD, "
                         "dominant (%d unknowns)" % units,
             "value": units / (ms * 1e-3), "unit": UNIT, "ms": ms,
             "buckets": len(plan.buckets),
             "two_sided_buckets": int(sum(1 for v in plan.schedules if v == 2)),
+            "partitioned_buckets": parted,
             "status_not_ok": int((st != 0).sum()), "max_err_vs_manufactured": float(err.max()),
+            "all_buckets_two_sided": {"value": units / (ms_two * 1e-3), "ms": ms_two},
             "whole_packing_thread_per_system": {"value": units / (ms_whole * 1e-3), "ms": ms_whole}}
+
+
+def small_batch_workload(dev):
+    """A batch too small to fill the GPU: 64 dominant PD systems of n = 65536 (one
+    thread or two per system leave most SMs idle), two-sided against partitioned."""
+    import torch
+    import paper_1804_09666_gb300 as band
+    B = synth.cfg0(nsys=64, n=65536, seed_salt=80)
+    n, nsys = B["n"], B["nsys"]
+    d = {q: torch.from_numpy(B[q]).to(dev).view(n, nsys) for q in "abcdef"}
+    xt = torch.from_numpy(B["x_true"]).to(dev).view(n, nsys)
+    units = n * nsys
+    out = {"workload": "64 PD systems, n = 65536 (dominant, interleaved)"}
+    for sched in ("two_sided", "partitioned"):
+        x = torch.empty_like(d["f"])
+        res = {}
+
+        def run():
+            res["x"], res["st"] = band.solve(*(d[q] for q in "abcdef"), method="npdm", x=x,
+                                             schedule=sched)
+        ms = _time(run)
+        err = float(((res["x"] - xt).abs().amax(0) / xt.abs().amax(0)).max())
+        out[sched] = {"value": units / (ms * 1e-3), "unit": UNIT, "ms": ms,
+                      "status_not_ok": int((res["st"] != 0).sum()), "max_rel_err": err}
+    return out
 
 
 def precision_workload(dev):
@@ -697,7 +729,8 @@ def main():
             "roofline": roof, "status_not_ok": bad,
             "fp64_fma_per_s": fma_rate}
     if rank == 0 and world == 1 and not args.no_extras and args.grid == GRID:
-        line["workloads"] = {"ragged": ragged_workload(dev), "precision": precision_workload(dev),
+        line["workloads"] = {"ragged": ragged_workload(dev), "small_batch": small_batch_workload(dev),
+                             "precision": precision_workload(dev),
                              "adjoint": adjoint_workload(dev), "sip": sip_workload(dev)}
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         line["cpu_baseline"] = cpu_baseline(W)

@@ -120,15 +120,20 @@ typedef struct {
  *   recurrence, carrying the columns through which the chunk couples to its neighbours'
  *   boundary rows (the SPIKE partition); the chunks' boundary rows form a
  *   block-tridiagonal system of P blocks of 4 (PD) / 2 (TD) unknowns that the system's
- *   first lane solves by block elimination with partial pivoting inside the blocks; then
- *   every lane back-substitutes its chunk.  About 2.3x (PD) / 1.8x (TD) NPDM's arithmetic
+ *   first lane solves by block elimination (a 2x2 (PD) / 1x1 (TD) pivot block per
+ *   chunk, partial pivoting); then every lane back-substitutes its chunk.  About 2.3x (PD) / 1.8x (TD) NPDM's arithmetic
  *   per row, for a dependent chain of n / P rows: for batches with too few systems to
  *   fill the GPU, and for the longest systems of a ragged batch.  A zero pivot in a
  *   chunk or a singular interface block sends an STDM/SPDM system to the symbolic fix-up
  *   and makes the first lane redo an NTDM/NPDM system with NPDM alone (BAND_ERR_ZERO_PIVOT
  *   means that NPDM's order meets an exactly zero pivot, also when x aliases f).
  *   Systems with fewer than 8 P rows are solved by one lane.  Needs one half bandwidth
- *   for the batch; any layout, ragged packings included.
+ *   for the batch; any layout, ragged packings included.  Workspace: five (PD) / four
+ *   (TD) scratch arrays of ceil(n / 32) * 32 rows for nsys rounded up to 8 systems.
+ *   Accuracy: on diagonally dominant matrices that of NPDM; on others a chunk's block
+ *   can be much closer to singular than the matrix, and the error then grows with the
+ *   worst chunk's condition number (measured on indefinite PD ADI rows, r = 2:
+ *   relative errors up to 8e-10 where NPDM reaches 1.3e-12).
  * BAND_SCHED_AUTO: TWO_SIDED for uniform-bandwidth solves with n >= 32 that are not a
  *   whole ragged packing (ragged id lists, i.e. size buckets, qualify) and, for
  *   NTDM/NPDM, whose x does not alias f; THREAD otherwise.  band_autotune replaces the

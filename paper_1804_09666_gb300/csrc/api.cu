@@ -83,8 +83,14 @@ bool choose_two_sided(const band_desc* d, bool alias) {
 // rows of P chunks for nsys rounded up to 32 / P systems.
 int64_t part_rows_bound(const band_desc* d) { return round_up(d->n, 32) * round_up(d->nsys, 8); }
 
-// Lanes per system on the partitioned schedule (0: another schedule).  chunks == 0:
-// the fewest lanes (4 .. 32) that put 8 warps on every SM, while chunks keep 8 rows.
+// Lanes per system on the partitioned schedule (0: another schedule).  chunks == 0: the
+// P in {4, 8, 16, 32} (chunks of 8 rows or more) with the least estimated time
+//   warps(P) * (n / P * c_row + P * c_if) / min(1, warps(P) / (8 warps x SMs)),
+// warps(P) = nsys * P / 32: the FP64 instructions of the launch (a chunk row costs
+// c_row = 32 (PD) / 14 (TD), the serial interface c_if = 60 / 25 per chunk), slowed down
+// while too few warps are resident to keep the FP64 pipes busy.  Measured on GB300
+// (FP64 NPDM): 2048 x 2048 takes 0.87 / 0.63 / 0.88 ms at P = 8 / 16 / 32, 7280 x 6000
+// 5.1 / 3.6 / 3.8 / 4.4 ms at P = 4 .. 32, 256 x 8192 its least time at P = 32.
 int choose_parts(const band_desc* d) {
   if (d->schedule != BAND_SCHED_PARTITIONED) return 0;
   if (d->chunks) return d->chunks;
@@ -97,10 +103,19 @@ int choose_parts(const band_desc* d) {
       nsm = 1;
     if (dev < 64) nsm_cache[dev] = nsm;
   }
-  const int64_t lanes = (int64_t)nsm * 8 * kWarp;
-  int P = 4;
-  while (P < 32 && d->nsys * P < lanes && d->n >= (int64_t)16 * P) P *= 2;
-  return P;
+  const bool td = d->hbw == nullptr && d->half_bw == 1;
+  const double c_row = td ? 14.0 : 32.0, c_if = td ? 25.0 : 60.0;
+  const double sat = 8.0 * nsm;
+  int best = 4;
+  double best_t = -1.0;
+  for (int P = 4; P <= 32; P *= 2) {
+    if (P > 4 && d->n < (int64_t)8 * P) break;
+    const double warps = (double)d->nsys * P / 32.0;
+    const double eff = warps < sat ? warps / sat : 1.0;
+    const double t = warps * ((double)d->n / P * c_row + P * c_if) / (eff > 0 ? eff : 1e-9);
+    if (best_t < 0 || t < best_t) { best_t = t; best = P; }
+  }
+  return best;
 }
 
 band_status make_direct(const band_desc* desc, int32_t method, const void* const diag[5],

@@ -15,16 +15,16 @@
 // block-tridiagonal interface system
 //   y_k + L_k y_{k-1} + U_k y_{k+1} = (g_top, g_bottom)_k,
 //   L_k y_{k-1} = V_k (bottom K rows of y_{k-1}),   U_k y_{k+1} = W_k (top K rows of y_{k+1}),
-// which the system's first lane solves by block elimination (2K x 2K blocks, partial
-// pivoting inside each block).  Then each lane back-substitutes its chunk once more,
-// with z - z_V u_k - z_W v_k in place of z: x_k itself.
+// which the system's first lane solves by block elimination; the blocks' structure
+// leaves one K x K solve (partial pivoting) per chunk.  Then each lane back-substitutes
+// its chunk once more, with z - z_V u_k - z_W v_k in place of z: x_k itself.
 // Arithmetic per row: about 2.3x NPDM (PD) and 1.8x NTDM (TD); the dependent chain of a
 // system is n / P rows long instead of n (one thread) or n / 2 (two-sided).
 //
 // Scratch (alpha, beta, z of f, z of B's columns) is chunk-major: row j of chunk k of
 // the batch's t-th system at ((j * np + t) * P + k), np = nsys rounded up to 32 / P, so
-// the lanes of a warp touch consecutive elements.  z of f goes to x (numeric methods)
-// or to the zs rows (symbolic methods, which keep f intact for the fix-up).
+// the lanes of a warp touch consecutive elements.  z of f goes to the zs rows, so f
+// stays intact (also when x aliases f) for a redo or the symbolic fix-up.
 //
 // A chunk may meet a zero pivot where NPDM's order does not, and the interface
 // elimination may meet a singular block: an STDM / SPDM system then goes to the symbolic
@@ -173,7 +173,7 @@ __device__ __forceinline__ void partition_one(const DirectArgs<T>& p, int64_t wa
   const int64_t s0 = k * L0 + (k < rem ? k : rem);
   const int64_t L = mode == 2 ? L0 + (k < rem ? 1 : 0) : 0;
   const int64_t np = p.part_np;
-  T* const zsf = p.zs;        // z of f: zs rows (symbolic methods) or x
+  T* const zsf = p.zs;        // z of f (set for this schedule; x if null)
 
   // ---- forward: the chunk's LU with f and B's columns
   T al1 = 0, al2 = 0, be1 = 0, be2 = 0;
@@ -251,11 +251,10 @@ __device__ __forceinline__ void partition_one(const DirectArgs<T>& p, int64_t wa
       zw1_1 = dl * rcl;
     }
   }
-  // ---- first backward sweep: top and bottom K rows of g, V, W
-  // y-slot of row j: top rows 0 .. K-1 -> 0 .. K-1, bottom rows L-K .. L-1 -> K .. 2K-1
-  T yf[NB], yv1[NB], yv2[NB], yw1[NB], yw2[NB];
-#pragma unroll
-  for (int c = 0; c < NB; ++c) yf[c] = yv1[c] = yv2[c] = yw1[c] = yw2[c] = T(0);
+  // ---- first backward sweep: top and bottom K rows of g, V, W, written to this lane's
+  // exchange slots (y-slot of row j: top rows 0 .. K-1 -> 0 .. K-1, bottom rows
+  // L-K .. L-1 -> K .. 2K-1; columns g, V1, W1, V2, W2 at offsets 0, NB, 2NB, 3NB, 4NB)
+  T* const my = xch + lane * PW;
   if (!zero && L > 0) {
     T xf1 = 0, xf2 = 0, xv11 = 0, xv12 = 0, xv21 = 0, xv22 = 0;
     T xw11 = 0, xw12 = 0, xw21 = 0, xw22 = 0;
@@ -281,31 +280,34 @@ __device__ __forceinline__ void partition_one(const DirectArgs<T>& p, int64_t wa
         xw2 = fma(-b, xw22, fma(-a, xw21, zw2));
         xv22 = xv21; xv21 = xv2; xw22 = xw21; xw21 = xw2;
       }
-#pragma unroll
-      for (int c = 0; c < K; ++c) {
-        if (j == c) {
-          yf[c] = xf; yv1[c] = xv1; yv2[c] = xv2; yw1[c] = xw1; yw2[c] = xw2;
-        }
-        if (j == L - K + c) {
-          yf[K + c] = xf; yv1[K + c] = xv1; yv2[K + c] = xv2; yw1[K + c] = xw1; yw2[K + c] = xw2;
+      if (j >= L - K) {                  // a bottom row
+        const int slot = K + (int)(j - (L - K));
+        my[slot] = xf;
+        my[NB + slot] = xv1;
+        my[2 * NB + slot] = xw1;
+        if (K == 2) {
+          my[3 * NB + slot] = xv2;
+          my[4 * NB + slot] = xw2;
         }
       }
       xf2 = xf1; xf1 = xf; xv12 = xv11; xv11 = xv1; xw12 = xw11; xw11 = xw1;
     }
-  }
-  // ---- the interface system, by the system's first lane
-  {
-    T* my = xch + lane * PW;
-#pragma unroll
-    for (int c = 0; c < NB; ++c) {
-      my[c] = yf[c];
-      my[NB + c] = yv1[c];             // V's column 1
-      my[2 * NB + c] = yw1[c];         // W's column 1
-      if (K == 2) {
-        my[3 * NB + c] = yv2[c];       // V's column 2
-        my[4 * NB + c] = yw2[c];       // W's column 2
-      }
+    // the top rows: the sweep's last values (row 0 in *1, row 1 in *2)
+    my[0] = xf1;
+    my[NB] = xv11;
+    my[2 * NB] = xw11;
+    if (K == 2) {
+      my[1] = xf2;
+      my[NB + 1] = xv12;
+      my[2 * NB + 1] = xw12;
+      my[3 * NB] = xv21;
+      my[3 * NB + 1] = xv22;
+      my[4 * NB] = xw21;
+      my[4 * NB + 1] = xw22;
     }
+  } else {
+#pragma unroll
+    for (int c = 0; c < PW; ++c) my[c] = T(0);
   }
   const bool gzero = (__ballot_sync(full, zero) & gmask) != 0;
   __syncwarp();
@@ -313,21 +315,24 @@ __device__ __forceinline__ void partition_one(const DirectArgs<T>& p, int64_t wa
   if (mode == 2 && k == 0 && !fail) {
     // Block elimination over the chunks: with D_k = I - L_k Cp_{k-1} (D_0 = I),
     // hp_k = D_k^{-1} (rhs_k - L_k hp_{k-1}) and Cp_k = D_k^{-1} U_k, then
-    // y_{P-1} = hp_{P-1}, y_k = hp_k - Cp_k y_{k+1}.  Only Cp's first K columns are
-    // nonzero (U_k acts on the top K rows of y_{k+1}); hp overwrites slots [0, NB) of
-    // chunk k and Cp's column c slots [NB (1 + c), NB (2 + c)).
+    // y_{P-1} = hp_{P-1}, y_k = hp_k - Cp_k y_{k+1}.  U_k acts on the top K rows of
+    // y_{k+1} and L_k on the bottom K rows of y_{k-1}, so only Cp's first K columns are
+    // nonzero and D_k = [[I - X_top, 0], [-X_bottom, I]] with X = V_k (bottom K rows of
+    // Cp_{k-1}): a K x K solve (partial pivoting) for the top rows, then
+    // Y_bottom = R_bottom + X_bottom Y_top.  hp overwrites slots [0, NB) of chunk k and
+    // Cp's column c slots [NB (1 + c), NB (2 + c)).
     T* const base = xch + grp * P * PW;
     for (int kk = 0; kk < P; ++kk) {
       T* e = base + kk * PW;
-      T Dm[NB][NB];
-      T R[NB][K + 1];
+      T R[NB][K + 1];        // columns: W's K columns, then the right-hand side
+      T X[NB][K];
 #pragma unroll
       for (int r = 0; r < NB; ++r) {
-#pragma unroll
-        for (int c = 0; c < NB; ++c) Dm[r][c] = (r == c) ? T(1) : T(0);
         R[r][K] = e[r];
         R[r][0] = e[2 * NB + r];
         if (K == 2) R[r][K - 1] = e[4 * NB + r];
+#pragma unroll
+        for (int c = 0; c < K; ++c) X[r][c] = T(0);
       }
       if (kk > 0) {
         const T* ep = e - PW;
@@ -339,12 +344,31 @@ __device__ __forceinline__ void partition_one(const DirectArgs<T>& p, int64_t wa
 #pragma unroll
           for (int m = 0; m < K; ++m) {
 #pragma unroll
-            for (int c = 0; c < K; ++c) Dm[r][c] = fma(-vr[m], ep[NB * (1 + c) + K + m], Dm[r][c]);
+            for (int c = 0; c < K; ++c) X[r][c] = fma(vr[m], ep[NB * (1 + c) + K + m], X[r][c]);
             R[r][K] = fma(-vr[m], ep[K + m], R[r][K]);
           }
         }
       }
-      if (!block_solve<T, NB, K + 1>(Dm, R)) { fail = true; break; }
+      T A[K][K], Rt[K][K + 1];
+#pragma unroll
+      for (int r = 0; r < K; ++r) {
+#pragma unroll
+        for (int c = 0; c < K; ++c) A[r][c] = (r == c ? T(1) : T(0)) - X[r][c];
+#pragma unroll
+        for (int c = 0; c <= K; ++c) Rt[r][c] = R[r][c];
+      }
+      if (!block_solve<T, K, K + 1>(A, Rt)) { fail = true; break; }
+#pragma unroll
+      for (int c = 0; c <= K; ++c) {
+#pragma unroll
+        for (int r = 0; r < K; ++r) {
+          T v = R[K + r][c];
+#pragma unroll
+          for (int m = 0; m < K; ++m) v = fma(X[K + r][m], Rt[m][c], v);
+          R[K + r][c] = v;
+          R[r][c] = Rt[r][c];
+        }
+      }
 #pragma unroll
       for (int r = 0; r < NB; ++r) {
         e[r] = R[r][K];
