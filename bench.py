@@ -52,6 +52,9 @@ def parse():
     ap.add_argument("--no-graph", action="store_true")
     ap.add_argument("--no-extras", action="store_true",
                     help="skip the ragged, precision, adjoint and SIP workloads (N = 1 only)")
+    ap.add_argument("--workload", choices=sorted(EXTRA_WORKLOADS),
+                    help="run only this one of the other workloads on GPU 0 and print its "
+                         "result as a JSON line (for profiling it alone)")
     return ap.parse_args()
 
 
@@ -617,9 +620,20 @@ def adjoint_workload(dev):
             "unit": UNIT, "ms": ms}
 
 
+EXTRA_WORKLOADS = {"ragged": "ragged_workload", "small_batch": "small_batch_workload",
+                   "precision": "precision_workload", "adjoint": "adjoint_workload",
+                   "sip": "sip_workload"}
+
+
 # ---------------------------------------------------------------------- main
 def main():
     args = parse()
+    if args.workload:
+        import torch
+        dev = torch.device("cuda", 0)
+        out = globals()[EXTRA_WORKLOADS[args.workload]](dev)
+        print(json.dumps({"workload": args.workload, "result": out}))
+        return
     world, rank, local = dist_setup()
     if world > 1:
         import torch.distributed as dist
