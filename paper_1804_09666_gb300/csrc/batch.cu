@@ -80,20 +80,20 @@ __device__ __forceinline__ void run_direct(const DirectArgs<T>& p, int kmode, in
 template <typename T>
 __device__ __forceinline__ void run_partition(const DirectArgs<T>& p, int kmode, int parts,
                                               int64_t warp, void* stage) {
-  T* xch = static_cast<T*>(stage);
+  T* st = static_cast<T*>(stage);    // the warp's staging area (stage_bytes_per_warp<T>)
   if (kmode == 1) {
     switch (parts) {
-      case 4: partition_one<T, 1, 4>(p, warp, xch); break;
-      case 8: partition_one<T, 1, 8>(p, warp, xch); break;
-      case 16: partition_one<T, 1, 16>(p, warp, xch); break;
-      default: partition_one<T, 1, 32>(p, warp, xch); break;
+      case 4: partition_one<T, 1, 4>(p, warp, st); break;
+      case 8: partition_one<T, 1, 8>(p, warp, st); break;
+      case 16: partition_one<T, 1, 16>(p, warp, st); break;
+      default: partition_one<T, 1, 32>(p, warp, st); break;
     }
   } else {
     switch (parts) {
-      case 4: partition_one<T, 2, 4>(p, warp, xch); break;
-      case 8: partition_one<T, 2, 8>(p, warp, xch); break;
-      case 16: partition_one<T, 2, 16>(p, warp, xch); break;
-      default: partition_one<T, 2, 32>(p, warp, xch); break;
+      case 4: partition_one<T, 2, 4>(p, warp, st); break;
+      case 8: partition_one<T, 2, 8>(p, warp, st); break;
+      case 16: partition_one<T, 2, 16>(p, warp, st); break;
+      default: partition_one<T, 2, 32>(p, warp, st); break;
     }
   }
 }

@@ -81,9 +81,9 @@ template cudaError_t launch_twisted<float>(const DirectArgs<float>&, int, cudaSt
 template <typename T, int K, int P>
 __global__ void __launch_bounds__(32 * SweepWarps<T>::value) k_partition(const DirectArgs<T> p) {
   extern __shared__ __align__(16) unsigned char stage_mem[];
-  T* xch = reinterpret_cast<T*>(stage_mem + (threadIdx.x >> 5) * part_xch_bytes<T>());
+  T* stage = reinterpret_cast<T*>(stage_mem + (threadIdx.x >> 5) * stage_bytes_per_warp<T>());
   const int64_t warp = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
-  partition_one<T, K, P>(p, warp, xch);
+  partition_one<T, K, P>(p, warp, stage);
 }
 
 template <typename T, int K>
@@ -106,7 +106,7 @@ cudaError_t launch_partition(const DirectArgs<T>& p, int kmode, int parts, cudaS
   const int64_t warps = (p.L.nsys + 32 / parts - 1) / (32 / parts);
   const int wpb = SweepWarps<T>::value;
   const unsigned grid = (unsigned)((warps + wpb - 1) / wpb);
-  const size_t smem = (size_t)wpb * part_xch_bytes<T>();
+  const size_t smem = (size_t)wpb * stage_bytes_per_warp<T>();
   if (kmode == 1) return launch_partition_k<T, 1>(p, parts, grid, 32 * wpb, smem, st);
   if (kmode == 2) return launch_partition_k<T, 2>(p, parts, grid, 32 * wpb, smem, st);
   return cudaErrorInvalidValue;

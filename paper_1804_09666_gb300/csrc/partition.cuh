@@ -149,11 +149,13 @@ __device__ __noinline__ void part_serial(const DirectArgs<T>& p, int64_t t) {
   set_status(p.status, s, bad ? BAND_ERR_NONFINITE : BAND_OK);
 }
 
-// The warp's 32 / P systems, positions t = warp * (32 / P) + (lane / P).  xch: the
-// warp's exchange area (part_xch_bytes<T>() bytes of shared memory).  Every lane of the
-// warp reaches every __syncwarp and shuffle.
+// The warp's 32 / P systems, positions t = warp * (32 / P) + (lane / P).  stage: the
+// warp's staging area (stage_bytes_per_warp<T>() bytes of shared memory): the forward
+// sweep's row ring, then the interface exchange.  Every lane of the warp reaches every
+// __syncwarp and shuffle.
 template <typename T, int K, int P>
-__device__ __forceinline__ void partition_one(const DirectArgs<T>& p, int64_t warp, T* xch) {
+__device__ __forceinline__ void partition_one(const DirectArgs<T>& p, int64_t warp, T* stage) {
+  T* const xch = stage;
   constexpr int NB = 2 * K;
   constexpr int PW = part_words<K>();
   constexpr int G = 32 / P;
@@ -181,16 +183,36 @@ __device__ __forceinline__ void partition_one(const DirectArgs<T>& p, int64_t wa
   T gl = 0, rcl = 0, rcl2 = 0, el2 = 0, dl = 0, el = 0;   // last rows, for C's columns
   bool zero = false;
   {
-    RowIn<T> r0, r1;
-    if (L > 0) load_in<T, K>(p, q0 + s0 * es, r0);
+    // rows staged through the warp's shared-memory ring, StageDepth rows ahead; each
+    // lane copies (and later reads) only its own slots
+    constexpr int D = StageDepth<T>::value;
+    constexpr int NA = K == 2 ? 6 : 4;     // arrays staged: (a,) b, c, d, (e,) f
+    constexpr int IB = K == 2 ? 1 : 0, IC = IB + 1, ID = IB + 2, IF = NA - 1;
+    const RowRing<T, NA, D> ring{stage, lane};
+    const T* src[NA];
+    if (K == 2) {
+      src[0] = p.a; src[1] = p.b; src[2] = p.c; src[3] = p.d; src[4] = p.e; src[5] = p.f;
+    } else {
+      src[0] = p.b; src[1] = p.c; src[2] = p.d; src[3] = p.f;
+    }
+#pragma unroll
+    for (int j = 0; j < D - 1; ++j) {
+      if (j < L) ring.issue(j, src, q0 + (s0 + j) * es);
+      else ring.skip();
+    }
     for (int64_t j = 0; j < L; ++j) {
       const int64_t i = s0 + j;
-      if (j + 1 < L) load_in<T, K>(p, q0 + (i + 1) * es, r1);
+      const int64_t jp = j + D - 1;
+      if (jp < L) ring.issue((int)(jp & (D - 1)), src, q0 + (s0 + jp) * es);
+      else ring.skip();
+      cp_async_wait<D - 1>();
+      const int slot = (int)(j & (D - 1));
       // the matrix's masks, then the chunk's own block
-      const T ag = (K == 2 && i >= 2) ? r0.a : T(0);
-      const T bg = (i >= 1) ? r0.b : T(0);
-      const T dg = (i + 1 < n) ? r0.d : T(0);
-      const T eg = (K == 2 && i + 2 < n) ? r0.e : T(0);
+      const T ag = (K == 2 && i >= 2) ? ring.get(slot, 0) : T(0);
+      const T bg = (i >= 1) ? ring.get(slot, IB) : T(0);
+      const T dg = (i + 1 < n) ? ring.get(slot, ID) : T(0);
+      const T eg = (K == 2 && i + 2 < n) ? ring.get(slot, 4) : T(0);
+      const T cc = ring.get(slot, IC), ff = ring.get(slot, IF);
       const T aa = (j >= 2) ? ag : T(0);
       const T bb = (j >= 1) ? bg : T(0);
       const T dd = (j + 1 < L) ? dg : T(0);
@@ -207,10 +229,10 @@ __device__ __forceinline__ void partition_one(const DirectArgs<T>& p, int64_t wa
       T g, m;
       if (K == 2) {
         g = fma(-al2, aa, bb);
-        m = fma(-al1, g, fma(-be2, aa, r0.c));
+        m = fma(-al1, g, fma(-be2, aa, cc));
       } else {
         g = bb;
-        m = fma(-al1, g, r0.c);
+        m = fma(-al1, g, cc);
       }
       if (is_zero(m)) { zero = true; break; }
       const T rc = rcp<T>(m);
@@ -221,14 +243,14 @@ __device__ __forceinline__ void partition_one(const DirectArgs<T>& p, int64_t wa
       if (K == 2) {
         const T bev = ee * rc;
         p.be[w] = bev;
-        zf = fma(-zf1, g, fma(-zf2, aa, r0.f)) * rc;
+        zf = fma(-zf1, g, fma(-zf2, aa, ff)) * rc;
         zv1 = fma(-zv11, g, fma(-zv12, aa, rv1)) * rc;
         const T zv2 = fma(-zv21, g, fma(-zv22, aa, rv2)) * rc;
         p.zv2[w] = zv2;
         zv22 = zv21; zv21 = zv2;
         be2 = be1; be1 = bev;
       } else {
-        zf = fma(-zf1, g, r0.f) * rc;
+        zf = fma(-zf1, g, ff) * rc;
         zv1 = fma(-zv11, g, rv1) * rc;
       }
       if (zsf) zsf[w] = zf; else p.x[q0 + i * es] = zf;
@@ -236,9 +258,10 @@ __device__ __forceinline__ void partition_one(const DirectArgs<T>& p, int64_t wa
       al2 = al1; al1 = alv;
       zf2 = zf1; zf1 = zf; zv12 = zv11; zv11 = zv1;
       rcl2 = rcl; rcl = rc; gl = g; el2 = el; el = eg; dl = dg;
-      r0 = r1;
     }
+    cp_async_wait<0>();
   }
+  __syncwarp();     // the ring's slots become the exchange area below
   // forward values of C's columns (nonzero only in the last K rows).  PD: column 1
   // (x_{s0+L}) has e at row L-2 and d at row L-1, column 2 (x_{s0+L+1}) e at row L-1.
   T zw1_2 = 0, zw1_1 = 0, zw2_1 = 0;     // zw<column>_<rows from the end>
@@ -258,39 +281,59 @@ __device__ __forceinline__ void partition_one(const DirectArgs<T>& p, int64_t wa
   if (!zero && L > 0) {
     T xf1 = 0, xf2 = 0, xv11 = 0, xv12 = 0, xv21 = 0, xv22 = 0;
     T xw11 = 0, xw12 = 0, xw21 = 0, xw22 = 0;
-    for (int64_t j = L - 1; j >= 0; --j) {
-      const int64_t w = part_idx<P>(j, t, np, k);
-      const T a = p.al[w];
-      const T zf = zsf ? zsf[w] : p.x[q0 + (s0 + j) * es];
-      const T zv1 = p.zv1[w];
-      // forward values of W's columns at this row
-      const T zw1 = j == L - 1 ? zw1_1 : (K == 2 && j == L - 2 ? zw1_2 : T(0));
-      T xf = fma(-a, xf1, zf);
-      T xv1 = fma(-a, xv11, zv1);
-      T xw1 = fma(-a, xw11, zw1);
-      T xv2 = 0, xw2 = 0;
-      if (K == 2) {
-        const T b = p.be[w];
-        const T zv2 = p.zv2[w];
-        const T zw2 = j == L - 1 ? zw2_1 : T(0);
-        xf = fma(-b, xf2, xf);
-        xv1 = fma(-b, xv12, xv1);
-        xw1 = fma(-b, xw12, xw1);
-        xv2 = fma(-b, xv22, fma(-a, xv21, zv2));
-        xw2 = fma(-b, xw22, fma(-a, xw21, zw2));
-        xv22 = xv21; xv21 = xv2; xw22 = xw21; xw21 = xw2;
-      }
-      if (j >= L - K) {                  // a bottom row
-        const int slot = K + (int)(j - (L - K));
-        my[slot] = xf;
-        my[NB + slot] = xv1;
-        my[2 * NB + slot] = xw1;
-        if (K == 2) {
-          my[3 * NB + slot] = xv2;
-          my[4 * NB + slot] = xw2;
+    // rows in blocks of kB: the block's scratch values are loaded together (one memory
+    // latency a block)
+    constexpr int kB = 4;
+    for (int64_t top = L - 1; top >= 0; top -= kB) {
+      T av[kB], bv[kB], fv[kB], v1[kB], v2[kB];
+#pragma unroll
+      for (int u = 0; u < kB; ++u) {
+        av[u] = bv[u] = fv[u] = v1[u] = v2[u] = T(0);
+        const int64_t j = top - u;
+        if (j >= 0) {
+          const int64_t w = part_idx<P>(j, t, np, k);
+          av[u] = p.al[w];
+          fv[u] = zsf ? zsf[w] : p.x[q0 + (s0 + j) * es];
+          v1[u] = p.zv1[w];
+          if (K == 2) {
+            bv[u] = p.be[w];
+            v2[u] = p.zv2[w];
+          }
         }
       }
-      xf2 = xf1; xf1 = xf; xv12 = xv11; xv11 = xv1; xw12 = xw11; xw11 = xw1;
+#pragma unroll
+      for (int u = 0; u < kB; ++u) {
+        const int64_t j = top - u;
+        if (j < 0) break;
+        const T a = av[u];
+        // forward values of W's columns at this row
+        const T zw1 = j == L - 1 ? zw1_1 : (K == 2 && j == L - 2 ? zw1_2 : T(0));
+        T xf = fma(-a, xf1, fv[u]);
+        T xv1 = fma(-a, xv11, v1[u]);
+        T xw1 = fma(-a, xw11, zw1);
+        T xv2 = 0, xw2 = 0;
+        if (K == 2) {
+          const T b = bv[u];
+          const T zw2 = j == L - 1 ? zw2_1 : T(0);
+          xf = fma(-b, xf2, xf);
+          xv1 = fma(-b, xv12, xv1);
+          xw1 = fma(-b, xw12, xw1);
+          xv2 = fma(-b, xv22, fma(-a, xv21, v2[u]));
+          xw2 = fma(-b, xw22, fma(-a, xw21, zw2));
+          xv22 = xv21; xv21 = xv2; xw22 = xw21; xw21 = xw2;
+        }
+        if (j >= L - K) {                  // a bottom row
+          const int slot = K + (int)(j - (L - K));
+          my[slot] = xf;
+          my[NB + slot] = xv1;
+          my[2 * NB + slot] = xw1;
+          if (K == 2) {
+            my[3 * NB + slot] = xv2;
+            my[4 * NB + slot] = xw2;
+          }
+        }
+        xf2 = xf1; xf1 = xf; xv12 = xv11; xv11 = xv1; xw12 = xw11; xw11 = xw1;
+      }
     }
     // the top rows: the sweep's last values (row 0 in *1, row 1 in *2)
     my[0] = xf1;
@@ -412,24 +455,43 @@ __device__ __forceinline__ void partition_one(const DirectArgs<T>& p, int64_t wa
       v[m] = k + 1 < P ? xch[(lane + 1) * PW + m] : T(0);
     }
     T x1 = 0, x2 = 0;
-    for (int64_t j = L - 1; j >= 0; --j) {
-      const int64_t w = part_idx<P>(j, t, np, k);
-      const int64_t q = q0 + (s0 + j) * es;
-      T z = zsf ? zsf[w] : p.x[q];
-      z = fma(-p.zv1[w], u[0], z);
-      if (K == 2) z = fma(-p.zv2[w], u[K - 1], z);
-      if (j == L - 1) {
-        z = fma(-zw1_1, v[0], z);
-        if (K == 2) z = fma(-zw2_1, v[K - 1], z);
-      } else if (K == 2 && j == L - 2) {
-        z = fma(-zw1_2, v[0], z);
+    constexpr int kB = 4;
+    for (int64_t top = L - 1; top >= 0; top -= kB) {
+      T av[kB], bv[kB], fv[kB], v1[kB], v2[kB];
+#pragma unroll
+      for (int e = 0; e < kB; ++e) {
+        av[e] = bv[e] = fv[e] = v1[e] = v2[e] = T(0);
+        const int64_t j = top - e;
+        if (j >= 0) {
+          const int64_t w = part_idx<P>(j, t, np, k);
+          av[e] = p.al[w];
+          fv[e] = zsf ? zsf[w] : p.x[q0 + (s0 + j) * es];
+          v1[e] = p.zv1[w];
+          if (K == 2) {
+            bv[e] = p.be[w];
+            v2[e] = p.zv2[w];
+          }
+        }
       }
-      T xi = fma(-p.al[w], x1, z);
-      if (K == 2) xi = fma(-p.be[w], x2, xi);
-      p.x[q] = xi;
-      bad |= not_finite(xi);
-      x2 = x1;
-      x1 = xi;
+#pragma unroll
+      for (int e = 0; e < kB; ++e) {
+        const int64_t j = top - e;
+        if (j < 0) break;
+        T z = fma(-v1[e], u[0], fv[e]);
+        if (K == 2) z = fma(-v2[e], u[K - 1], z);
+        if (j == L - 1) {
+          z = fma(-zw1_1, v[0], z);
+          if (K == 2) z = fma(-zw2_1, v[K - 1], z);
+        } else if (K == 2 && j == L - 2) {
+          z = fma(-zw1_2, v[0], z);
+        }
+        T xi = fma(-av[e], x1, z);
+        if (K == 2) xi = fma(-bv[e], x2, xi);
+        p.x[q0 + (s0 + j) * es] = xi;
+        bad |= not_finite(xi);
+        x2 = x1;
+        x1 = xi;
+      }
     }
   }
   const bool gbad = (__ballot_sync(full, bad) & gmask) != 0;
