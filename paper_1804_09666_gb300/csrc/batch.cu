@@ -154,12 +154,7 @@ __global__ void __launch_bounds__(64) k_symbolic_batch(const __grid_constant__ S
 
 // the deferred residual and decision of the SIP problems (blockIdx.y: the problem)
 __global__ void __launch_bounds__(256) k_sip_resid_batch(const __grid_constant__ TailTable t) {
-  const SipArgs& p = t.it[blockIdx.y];
-  const int64_t idx = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-  const int64_t nch = (p.L.n + kResChunk - 1) / kResChunk;
-  if (idx >= p.L.nsys * nch) return;
-  const int64_t s = idx % p.L.nsys;
-  if (p.pend[s]) sip_resid_chunk(p, s, idx / p.L.nsys);
+  sip_resid_cell(t.it[blockIdx.y], (int64_t)blockIdx.x * blockDim.x + threadIdx.x);
 }
 
 __global__ void __launch_bounds__(256) k_sip_decide_batch(const __grid_constant__ TailTable t) {
@@ -322,7 +317,7 @@ extern "C" band_status band_solve_batch(const band_problem* in, int32_t count, v
     int64_t cells = 0, nmax = 0;
     for (int j = 0; j < tail.count; ++j) {
       const Layout& L = tail.it[j].L;
-      cells = std::max(cells, L.nsys * ((L.n + kResChunk - 1) / kResChunk));
+      cells = std::max(cells, resid_cells(L));
       nmax = std::max(nmax, L.nsys);
     }
     k_sip_resid_batch<<<dim3((unsigned)((cells + 255) / 256), (unsigned)tail.count), 256, 0, st>>>(tail);

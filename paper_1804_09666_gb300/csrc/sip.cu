@@ -363,11 +363,7 @@ __global__ void __launch_bounds__(128) k_sip_two(const SipArgs p) {
 }
 
 __global__ void __launch_bounds__(256) k_sip_resid(const SipArgs p) {
-  const int64_t idx = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-  const int64_t nch = (p.L.n + kResChunk - 1) / kResChunk;
-  if (idx >= p.L.nsys * nch) return;
-  const int64_t t = idx % p.L.nsys;
-  if (p.pend[t]) sip_resid_chunk(p, t, idx / p.L.nsys);
+  sip_resid_cell(p, (int64_t)blockIdx.x * blockDim.x + threadIdx.x);
 }
 
 __global__ void __launch_bounds__(256) k_sip_decide(const SipArgs p) {
@@ -595,8 +591,7 @@ extern "C" band_status band_sip(const band_desc* desc, const void* const diag[5]
   }
   if (cudaGetLastError() != cudaSuccess) return BAND_ERR_CUDA;
   if (width == 0) {
-    const int64_t nch = (desc->n + kResChunk - 1) / kResChunk;
-    k_sip_resid<<<(unsigned)((desc->nsys * nch + 255) / 256), 256, 0, st>>>(sa);
+    k_sip_resid<<<(unsigned)((resid_cells(sa.L) + 255) / 256), 256, 0, st>>>(sa);
     k_sip_decide<<<(unsigned)((desc->nsys + 255) / 256), 256, 0, st>>>(sa);
     if (cudaGetLastError() != cudaSuccess) return BAND_ERR_CUDA;
     return cuda_status(launch_sip_tail(sa, desc->nsys, st));

@@ -186,7 +186,7 @@ __device__ inline bool ilu0_into(const SipArgs& p, int64_t s) {
 // Algorithm 1 with exact substitutions.  x^0 = 0 makes K x^0 = 0, so the first update
 // is x^1 = U^{-1} L^{-1} f: one forward sweep does ILU(0) and L y = f together (only
 // 1/u0, u1 and y are kept), one backward sweep does U x = y.  The residual of x^1 and
-// the stop / continue decision are separate passes (sip_resid_chunk, sip_decide_one);
+// the stop / continue decision are separate passes (sip_resid_cell, sip_decide_one);
 // systems that need more updates go to the block-cooperative tail.
 __device__ inline void sip_literal(const SipArgs& p, int64_t t, void* stage) {
   const int64_t s = p.L.sys(t);     // t: position in the batch, s: the system id
@@ -435,18 +435,32 @@ __device__ inline void sip_two_sided(const SipArgs& p, int64_t t, bool active) {
 }
 
 // ---------------------------------------------------------------------------
-// Deferred residual of the first update: r = f - A x^1 over a chunk of rows of the
-// t-th system (the expression and order of sip_literal's inline residual), its max|r|
-// into rn_sys[t]; then Algorithm 1's decision per system.
+// Deferred residual of the first update: r = f - A x^1 over a cell of rows of the t-th
+// system (the expression and order of sip_literal's inline residual), its max|r| into
+// rn_sys[t]; then Algorithm 1's decision per system.
+// Cells: where consecutive systems sit at consecutive addresses (interleaved), a cell
+// is kResChunk rows and consecutive threads take consecutive systems; where each
+// system's rows are consecutive (contiguous, ragged), a cell is kResRows rows and
+// consecutive threads take consecutive cells of one system, so a warp reads
+// 32 x kResRows consecutive rows of every array.
 // ---------------------------------------------------------------------------
 constexpr int kResChunk = 32;
+constexpr int kResRows = 4;
 
-__device__ inline void sip_resid_chunk(const SipArgs& p, int64_t t, int64_t c) {
+__host__ __device__ inline bool resid_rows_fastest(const Layout& L) {
+  return L.offsets != nullptr || (L.es == 1 && L.ss != 1);
+}
+__host__ __device__ inline int64_t resid_cells(const Layout& L) {
+  const int64_t rows = resid_rows_fastest(L) ? kResRows : kResChunk;
+  return L.nsys * ((L.n + rows - 1) / rows);
+}
+
+// max|f - A x| over rows i0 .. i1-1 of the t-th system (bits of a double >= 0)
+__device__ inline double sip_resid_rows(const SipArgs& p, int64_t t, int64_t i0, int64_t i1) {
   const int64_t s = p.L.sys(t);
   const int64_t n = p.L.rows(s), q0 = p.L.base(s), es = p.L.stride();
-  const int64_t i0 = c * kResChunk;
-  if (i0 >= n) return;
-  const int64_t i1 = i0 + kResChunk < n ? i0 + kResChunk : n;
+  if (i1 > n) i1 = n;
+  if (i0 >= i1) return 0.0;
   auto X = [&](int64_t j) -> double { return (j >= 0 && j < n) ? p.x[q0 + j * es] : 0.0; };
   double xm2 = X(i0 - 2), xm1 = X(i0 - 1), x0 = X(i0), xp1 = X(i0 + 1);
   double rn = 0.0;
@@ -477,7 +491,36 @@ __device__ inline void sip_resid_chunk(const SipArgs& p, int64_t t, int64_t c) {
       xm2 = xm1; xm1 = x0; x0 = xp1; xp1 = xp2;
     }
   }
-  atomicMax(p.rn_sys + t, (unsigned long long)__double_as_longlong(rn));
+  return rn;
+}
+
+// Cell idx of the residual pass (idx may lie past the last cell).  Every thread of the
+// warp calls it: in the rows-fastest mapping a warp whose cells all belong to one
+// system combines its maxima by shuffles before the one atomic.
+__device__ inline void sip_resid_cell(const SipArgs& p, int64_t idx) {
+  const bool rows_fastest = resid_rows_fastest(p.L);
+  const int64_t rows = rows_fastest ? kResRows : kResChunk;
+  const int64_t nch = (p.L.n + rows - 1) / rows;
+  const bool valid = idx < p.L.nsys * nch;
+  const int64_t t = !valid ? -1 : (rows_fastest ? idx / nch : idx % p.L.nsys);
+  const int64_t c = !valid ? 0 : (rows_fastest ? idx % nch : idx / p.L.nsys);
+  unsigned long long v = 0ull;
+  if (valid && p.pend[t])
+    v = (unsigned long long)__double_as_longlong(sip_resid_rows(p, t, c * rows, c * rows + rows));
+  if (rows_fastest) {
+    const unsigned full = 0xffffffffu;
+    const int64_t t0 = __shfl_sync(full, t, 0);
+    if (__all_sync(full, t < 0 || t == t0)) {
+#pragma unroll
+      for (int o = 16; o > 0; o >>= 1) {
+        const unsigned long long w = __shfl_xor_sync(full, v, o);
+        v = v > w ? v : w;
+      }
+      if ((threadIdx.x & 31) == 0 && v) atomicMax(p.rn_sys + t0, v);
+      return;
+    }
+  }
+  if (v) atomicMax(p.rn_sys + t, v);
 }
 
 __device__ inline void sip_decide_one(const SipArgs& p, int64_t t) {
