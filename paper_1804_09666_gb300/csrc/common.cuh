@@ -194,6 +194,11 @@ __host__ __device__ constexpr int stage_bytes_per_warp() {
 template <typename T> struct SweepWarps;
 template <> struct SweepWarps<double> { static constexpr int value = 1; };
 template <> struct SweepWarps<float> { static constexpr int value = 4; };
+// Resident warps per SM the sweeps are compiled for (128 registers a thread).  Large
+// batches then fit in fewer waves: k_twisted<double> at its free 152 registers held 13
+// warps per SM, so 32768 PD systems of n = 2048 (2048 warps) needed a second, almost
+// empty wave and took 3.08 ms against 2.07 ms on one thread per system.
+constexpr int kSweepWarpsPerSm = 16;
 
 // Staging of rows that each lane reads from its own contiguous system (contiguous and
 // ragged layouts): 16-byte granules (2 FP64 / 4 FP32 rows) of every array, D granules

@@ -25,7 +25,8 @@ namespace band {
 // fused factor + solve (device function in sweeps.cuh)
 // ---------------------------------------------------------------------------
 template <typename T, int K>
-__global__ void __launch_bounds__(32 * SweepWarps<T>::value) k_direct(const DirectArgs<T> p) {
+__global__ void __launch_bounds__(32 * SweepWarps<T>::value, kSweepWarpsPerSm / SweepWarps<T>::value)
+    k_direct(const DirectArgs<T> p) {
   extern __shared__ __align__(16) unsigned char stage_mem[];
   const int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   if (t >= p.L.nsys) return;
@@ -54,7 +55,8 @@ template cudaError_t launch_direct<float>(const DirectArgs<float>&, int, cudaStr
 
 // two threads (lanes l, l ^ 16) per system; one bandwidth for the batch
 template <typename T, int K>
-__global__ void __launch_bounds__(32 * SweepWarps<T>::value) k_twisted(const DirectArgs<T> p) {
+__global__ void __launch_bounds__(32 * SweepWarps<T>::value, kSweepWarpsPerSm / SweepWarps<T>::value)
+    k_twisted(const DirectArgs<T> p) {
   extern __shared__ __align__(16) unsigned char stage_mem[];
   void* stage = stage_mem + (threadIdx.x >> 5) * stage_bytes_per_warp<T>();
   const int64_t warp = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
