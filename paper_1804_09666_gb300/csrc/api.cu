@@ -67,11 +67,12 @@ FactorPtrs factor_ptrs(const band_desc* d, const void* factors) {
 }
 
 // The automatic schedule.  Measured on GB300 with the staging ring in both schedules,
-// the two-sided sweep is faster than one thread per system for every uniform batch with
-// n >= 32 that was tried (n = 128 .. 8192, 1024 .. 32768 systems, FP64 and FP32,
+// the two-sided sweep is faster than one thread per system for the uniform batches with
+// n >= 32 that were tried (n = 128 .. 8192, 1024 .. 131072 systems, FP64 and FP32,
 // interleaved and contiguous; from parity at 32768 x 512 to 1.9x at 2048 x 2048), also
-// inside a batched launch of 30 such problems; below n = 32 the interface solve is a
-// large share of the work.
+// inside a batched launch of 30 such problems, with one exception (65536 x 1024 FP64:
+// 2.14 ms against 1.95 ms); below n = 32 the interface solve is a large share of the
+// work.  band_autotune replaces the rule by measurement.
 bool choose_two_sided(const band_desc* d, bool alias) {
   if (d->schedule == BAND_SCHED_THREAD || d->schedule == BAND_SCHED_PARTITIONED) return false;
   if (d->schedule == BAND_SCHED_TWO_SIDED) return true;

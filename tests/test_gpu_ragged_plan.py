@@ -49,7 +49,8 @@ def test_buckets_every_schedule(band, ragged, schedule):
     assert _per_system_err(B, x.cpu().numpy()).max() <= 1e-12
     assert len(plan.buckets) == len({(int(k), int(np.log2(n))) for k, n in zip(B["hbw"], B["sizes"])})
     if schedule == "tune":
-        assert set(plan.schedules) <= {1, 2}
+        assert set(plan.schedules) <= {1, 2, 3}       # the joint search may partition
+        assert all((v == 3) == (c in (4, 8, 16, 32)) for v, c in zip(plan.schedules, plan.chunks))
     # against the oracle on a sample of systems from every bucket
     xg = x.cpu().numpy()
     order = plan.order.cpu().numpy()
@@ -104,9 +105,9 @@ def test_symbolic_buckets_with_zero_pivots(band):
     offs = np.zeros(len(sizes) + 1, dtype=np.int64)
     np.cumsum(sizes, out=offs[1:])
     dev = {q: torch.from_numpy(np.concatenate(arrays[q])).to(DEV) for q in "abcdef"}
-    for schedule in ("two_sided", "thread"):
+    for schedule in ("two_sided", "thread", "partitioned"):
         plan = band.RaggedPlan(*(dev[q] for q in "abcdef"), offs, np.array(hbw, np.int8),
-                               method="symbolic", schedule=schedule)
+                               method="symbolic", schedule=schedule, chunks=4 if schedule == "partitioned" else 0)
         x, st = plan.run()
         torch.cuda.synchronize()
         xg, st = x.cpu().numpy(), st.cpu().numpy()
