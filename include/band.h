@@ -87,7 +87,8 @@ typedef struct {
   int64_t total_rows;     /* ragged: offsets[nsys] (the host's copy); uniform: ignored */
   int32_t schedule;       /* band_schedule for NTDM/NPDM solves (BAND_SCHED_AUTO = 0) */
   int32_t chunks;         /* BAND_SCHED_PARTITIONED: lanes (row chunks) per system, 4, 8,
-                             16 or 32; 0 = chosen from nsys and n.  Otherwise 0. */
+                             16, 32 (lanes of a warp) or 64, 128, 256 (a block of 2, 4, 8
+                             warps per system); 0 = chosen from nsys and n.  Otherwise 0. */
   /* Ragged batches only, else NULL: device array of nsys system ids.  The batch is then
    * the systems ids[0 .. nsys-1] of the packing that offsets (and hbw) describe, and
    * every per-system output (sys_status, iters, resid) is indexed by the id.  A solve
@@ -115,8 +116,10 @@ typedef struct {
  *   system that NPDM's order would fail on in its lower half may be solved (status OK).
  *   Systems with fewer than 4 (PD) / 2 (TD) rows are solved by one thread.  Needs one
  *   half bandwidth for the batch.
- * BAND_SCHED_PARTITIONED: P = desc->chunks lanes of a warp per system (32 / P systems
- *   a warp).  Lane k eliminates rows [k n / P, (k+1) n / P) (about) with NPDM's
+ * BAND_SCHED_PARTITIONED: P = desc->chunks lanes per system: 32 / P systems a warp for
+ *   P <= 32, one system per block of P / 32 warps beyond (band_solve only; inside
+ *   band_solve_batch, whose tasks are single warps, P > 32 runs as P = 32).  Lane k
+ *   eliminates rows [k n / P, (k+1) n / P) (about) with NPDM's
  *   recurrence, carrying the columns through which the chunk couples to its neighbours'
  *   boundary rows (the SPIKE partition); the chunks' boundary rows form a
  *   block-tridiagonal system of P blocks of 4 (PD) / 2 (TD) unknowns that the system's
@@ -129,7 +132,8 @@ typedef struct {
  *   means that NPDM's order meets an exactly zero pivot, also when x aliases f).
  *   Systems with fewer than 8 P rows are solved by one lane.  Needs one half bandwidth
  *   for the batch; any layout, ragged packings included.  Workspace: five (PD) / four
- *   (TD) scratch arrays of ceil(n / 32) * 32 rows for nsys rounded up to 8 systems.
+ *   (TD) scratch arrays of ceil(n / P) * P rows for nsys rounded up to 32 / P systems
+ *   (the largest over P when chunks is 0).
  *   Accuracy: on diagonally dominant matrices that of NPDM; on others a chunk's block
  *   can be much closer to singular than the matrix, and the error then grows with the
  *   worst chunk's condition number (measured on indefinite PD ADI rows, r = 2:

@@ -254,10 +254,11 @@ extern "C" band_status band_adjoint(const band_desc* desc, int32_t method, const
     const void* dt[5] = {tw.t[0], tw.t[1], tw.t[2], tw.t[3], tw.t[4]};
     DirectReq r;
     const band_status v = make_direct(desc, m, dt, w, grad_f, sys_status, tw.solve,
-                                      tw.solve_bytes, &r);
+                                      tw.solve_bytes, &r, 256);
     if (v != BAND_OK) return v;
-    const cudaError_t e = r.two_sided ? launch_twisted<double>(r.d64, r.kmode, st)
-                                      : launch_direct<double>(r.d64, r.kmode, st);
+    const cudaError_t e = r.parts ? launch_partition<double>(r.d64, r.kmode, r.parts, st)
+                          : r.two_sided ? launch_twisted<double>(r.d64, r.kmode, st)
+                                        : launch_direct<double>(r.d64, r.kmode, st);
     if (e != cudaSuccess) return BAND_ERR_CUDA;
     double* G[5] = {(double*)grad_diag[0], (double*)grad_diag[1], (double*)grad_diag[2],
                     (double*)grad_diag[3], (double*)grad_diag[4]};

@@ -80,9 +80,21 @@ bool choose_two_sided(const band_desc* d, bool alias) {
   return d->n >= 32;
 }
 
-// Chunk-major rows of one partitioned scratch array, for every chunk count: ceil(n / P)
-// rows of P chunks for nsys rounded up to 32 / P systems.
-int64_t part_rows_bound(const band_desc* d) { return round_up(d->n, 32) * round_up(d->nsys, 8); }
+// Slots per chunk row of the partitioned scratch: nsys rounded up to the systems of a
+// warp (32 / P for P <= 32, one system per block beyond).
+int64_t part_np(int64_t nsys, int parts) { return parts >= 32 ? nsys : round_up(nsys, 32 / parts); }
+
+// Chunk-major rows of one partitioned scratch array: ceil(n / P) rows of P chunks for
+// part_np systems; desc->chunks == 0 takes the largest over the chunk counts.
+int64_t part_rows_bound(const band_desc* d) {
+  int64_t best = 0;
+  for (int P = 4; P <= 256; P *= 2) {
+    if (d->chunks && P != d->chunks) continue;
+    const int64_t r = (d->n + P - 1) / P * P * part_np(d->nsys, P);
+    if (r > best) best = r;
+  }
+  return best;
+}
 
 // Lanes per system on the partitioned schedule (0: another schedule).  chunks == 0: the
 // P in {4, 8, 16, 32} (chunks of 8 rows or more) with the least estimated time
@@ -92,9 +104,9 @@ int64_t part_rows_bound(const band_desc* d) { return round_up(d->n, 32) * round_
 // while too few warps are resident to keep the FP64 pipes busy.  Measured on GB300
 // (FP64 NPDM): 2048 x 2048 takes 0.87 / 0.63 / 0.88 ms at P = 8 / 16 / 32, 7280 x 6000
 // 5.1 / 3.6 / 3.8 / 4.4 ms at P = 4 .. 32, 256 x 8192 its least time at P = 32.
-int choose_parts(const band_desc* d) {
+int choose_parts(const band_desc* d, int max_parts) {
   if (d->schedule != BAND_SCHED_PARTITIONED) return 0;
-  if (d->chunks) return d->chunks;
+  if (d->chunks) return d->chunks < max_parts ? d->chunks : max_parts;
   static int nsm_cache[64];
   int dev = 0;
   if (cudaGetDevice(&dev) != cudaSuccess || dev < 0) dev = 0;
@@ -109,7 +121,7 @@ int choose_parts(const band_desc* d) {
   const double sat = 8.0 * nsm;
   int best = 4;
   double best_t = -1.0;
-  for (int P = 4; P <= 32; P *= 2) {
+  for (int P = 4; P <= max_parts; P *= 2) {
     if (P > 4 && d->n < (int64_t)8 * P) break;
     const double warps = (double)d->nsys * P / 32.0;
     const double eff = warps < sat ? warps / sat : 1.0;
@@ -121,7 +133,7 @@ int choose_parts(const band_desc* d) {
 
 band_status make_direct(const band_desc* desc, int32_t method, const void* const diag[5],
                         const void* f, void* x, int32_t* sys_status, void* ws, size_t ws_bytes,
-                        DirectReq* r) {
+                        DirectReq* r, int max_parts) {
   if (!desc_ok(desc)) return BAND_ERR_ARG;
   const int kmode = kmode_for(desc, method);
   if (kmode < 0) return BAND_ERR_ARG;
@@ -139,7 +151,7 @@ band_status make_direct(const band_desc* desc, int32_t method, const void* const
   r->two_ok = kmode != 0;
   r->alias = x == f && !r->symbolic;   // symbolic methods keep f until the backward sweep
   r->two_sided = r->two_ok && choose_two_sided(desc, r->alias);
-  r->parts = r->two_ok ? choose_parts(desc) : 0;
+  r->parts = r->two_ok ? choose_parts(desc, max_parts) : 0;
   r->d64 = DirectArgs<double>{L, W,
                               (const double*)diag[0], (const double*)diag[1],
                               (const double*)diag[2], (const double*)diag[3],
@@ -161,7 +173,7 @@ band_status make_direct(const band_desc* desc, int32_t method, const void* const
     r->d64.gran = r->d32.gran = (contig && aligned) ? 1 : 0;
   }
   if (r->parts) {
-    const int64_t np = round_up(desc->nsys, 32 / r->parts);
+    const int64_t np = part_np(desc->nsys, r->parts);
     r->d64.zs = (double*)w.zs;
     r->d64.zv1 = (double*)w.zv1;
     r->d64.zv2 = (double*)w.zv2;
@@ -231,7 +243,7 @@ band_status band_solve(const band_desc* desc, int32_t method, const void* factor
     return cuda_status(launch_fsolve<float>(p, kmode, st));
   }
   DirectReq r;
-  const band_status v = make_direct(desc, method, diag, f, x, sys_status, ws, ws_bytes, &r);
+  const band_status v = make_direct(desc, method, diag, f, x, sys_status, ws, ws_bytes, &r, 256);
   if (v != BAND_OK) return v;
   if (r.symbolic && cudaMemsetAsync(r.sym.fix_count_mut, 0, sizeof(unsigned long long), st) !=
                         cudaSuccess)

@@ -198,7 +198,7 @@ static double task_cost(const band_problem& q) {
     if (d->dtype == BAND_F32) w *= 0.5;
     if (kmode_for(d, q.method) > 0) {
       const bool alias = q.x == q.f && !is_symbolic(q.method);
-      const int P = choose_parts(d);
+      const int P = choose_parts(d, 32);
       if (P) rows = rows / P * 2.3 + 8.0 * P;
       else if (choose_two_sided(d, alias)) rows *= 0.5;
     }
@@ -242,7 +242,7 @@ extern "C" band_status band_solve_batch(const band_problem* in, int32_t count, v
     if (q.op == BAND_OP_SOLVE) {
       DirectReq r;
       const band_status v = make_direct(q.desc, q.method, q.diag, q.f, q.x, q.sys_status, q.ws,
-                                        q.ws_bytes, &r);
+                                        q.ws_bytes, &r, 32);
       if (v != BAND_OK) return v;
       b.kmode = (int16_t)r.kmode;
       b.two_sided = r.two_sided ? 1 : 0;

@@ -88,6 +88,14 @@ __global__ void __launch_bounds__(32 * SweepWarps<T>::value) k_partition(const D
   partition_one<T, K, P>(p, warp, stage);
 }
 
+// one system per block of W warps (P = 32 W chunks)
+template <typename T, int K, int W>
+__global__ void __launch_bounds__(32 * W) k_partition_block(const DirectArgs<T> p) {
+  extern __shared__ __align__(16) unsigned char stage_mem[];
+  __shared__ int flag;
+  partition_block<T, K, W>(p, stage_mem, &flag);
+}
+
 template <typename T, int K>
 static cudaError_t launch_partition_k(const DirectArgs<T>& p, int parts, unsigned grid, int tb,
                                       size_t smem, cudaStream_t st) {
@@ -101,9 +109,32 @@ static cudaError_t launch_partition_k(const DirectArgs<T>& p, int parts, unsigne
   return cudaGetLastError();
 }
 
+template <typename T, int K>
+static cudaError_t launch_partition_block_k(const DirectArgs<T>& p, int parts, cudaStream_t st) {
+  const unsigned grid = (unsigned)p.L.nsys;
+  const size_t smem = (size_t)(parts / 32) * stage_bytes_per_warp<T>();
+  switch (parts) {
+    case 64: k_partition_block<T, K, 2><<<grid, 64, smem, st>>>(p); break;
+    case 128: k_partition_block<T, K, 4><<<grid, 128, smem, st>>>(p); break;
+    case 256: {     // 48 KiB of staging areas and the flag: above the default limit
+      const cudaError_t e = tail_prepare((const void*)k_partition_block<T, K, 8>);
+      if (e != cudaSuccess) return e;
+      k_partition_block<T, K, 8><<<grid, 256, smem, st>>>(p);
+      break;
+    }
+    default: return cudaErrorInvalidValue;
+  }
+  return cudaGetLastError();
+}
+
 template <typename T>
 cudaError_t launch_partition(const DirectArgs<T>& p, int kmode, int parts, cudaStream_t st) {
   if (p.L.nsys == 0) return cudaSuccess;
+  if (parts == 64 || parts == 128 || parts == 256) {
+    if (kmode == 1) return launch_partition_block_k<T, 1>(p, parts, st);
+    if (kmode == 2) return launch_partition_block_k<T, 2>(p, parts, st);
+    return cudaErrorInvalidValue;
+  }
   if (parts != 4 && parts != 8 && parts != 16 && parts != 32) return cudaErrorInvalidValue;
   const int64_t warps = (p.L.nsys + 32 / parts - 1) / (32 / parts);
   const int wpb = SweepWarps<T>::value;

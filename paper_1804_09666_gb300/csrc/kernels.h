@@ -95,11 +95,16 @@ struct DirectReq {
     SymArgs args;
   } sym;
 };
+// max_parts: the most lanes per system the caller's kernels run (256 for band_solve's
+// own launch, 32 inside band_solve_batch, whose tasks are single warps).
 band_status make_direct(const band_desc* desc, int32_t method, const void* const diag[5],
                         const void* f, void* x, int32_t* sys_status, void* ws, size_t ws_bytes,
-                        DirectReq* r);
+                        DirectReq* r, int max_parts);
 bool choose_two_sided(const band_desc* d, bool alias);
-int choose_parts(const band_desc* d);
+int choose_parts(const band_desc* d, int max_parts);
+// Lets `kernel` launch with more than 48 KiB of dynamic shared memory (the attribute is
+// set once per kernel and device; defined in sip.cu).
+cudaError_t tail_prepare(const void* kernel);
 int64_t part_rows_bound(const band_desc* d);
 
 // host-side helpers shared by the entry points (defined in api.cu and the feature files)

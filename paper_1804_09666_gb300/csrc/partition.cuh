@@ -1,6 +1,7 @@
-// partition.cuh -- the partitioned schedule: P lanes of a warp per system (P = 4, 8,
-// 16 or 32; 32 / P systems per warp), lane k eliminating chunk k of P consecutive row
-// blocks of its system.
+// partition.cuh -- the partitioned schedule: P lanes per system, lane k eliminating
+// chunk k of P consecutive row blocks of its system.  P = 4, 8, 16 or 32 lanes of a
+// warp (32 / P systems per warp), or P = 64, 128 or 256: a block of P / 32 warps per
+// system.
 //
 // Chunk k (rows s0 .. s0+L-1, block A_k of the matrix) couples to the K unknowns just
 // above it, u_k = (x_{s0-K} .. x_{s0-1}), through the a, b entries of its first rows
@@ -149,21 +150,40 @@ __device__ __noinline__ void part_serial(const DirectArgs<T>& p, int64_t t) {
   set_status(p.status, s, bad ? BAND_ERR_NONFINITE : BAND_OK);
 }
 
-// The warp's 32 / P systems, positions t = warp * (32 / P) + (lane / P).  stage: the
-// warp's staging area (stage_bytes_per_warp<T>() bytes of shared memory): the forward
-// sweep's row ring, then the interface exchange.  Every lane of the warp reaches every
-// __syncwarp and shuffle.
-template <typename T, int K, int P>
-__device__ __forceinline__ void partition_one(const DirectArgs<T>& p, int64_t warp, T* stage) {
-  T* const xch = stage;
+// The lanes that share one system: P of a warp's lanes (P <= 32), or a whole block of
+// P / 32 warps.  any(): some lane of the group holds v; from_leader(): chunk 0's value.
+// Every lane of the warp (block) calls each of them.
+struct WarpGroup {
+  unsigned mask;     // the group's lanes
+  int leader;        // lane of chunk 0
+  __device__ __forceinline__ void sync() const { __syncwarp(); }
+  __device__ __forceinline__ bool any(bool v) const {
+    return (__ballot_sync(0xffffffffu, v) & mask) != 0;
+  }
+  __device__ __forceinline__ bool from_leader(bool v) const {
+    return __shfl_sync(0xffffffffu, (int)v, leader) != 0;
+  }
+};
+struct BlockGroup {
+  int* flag;         // one int of shared memory
+  __device__ __forceinline__ void sync() const { __syncthreads(); }
+  __device__ __forceinline__ bool any(bool v) const { return __syncthreads_or(v) != 0; }
+  __device__ __forceinline__ bool from_leader(bool v) const {
+    if (threadIdx.x == 0) *flag = v ? 1 : 0;
+    __syncthreads();
+    return *flag != 0;
+  }
+};
+
+// The batch's t-th system, chunk k of P, by one lane of its group.  ring: this warp's
+// staging area (stage_bytes_per_warp<T>() bytes of shared memory) for the forward
+// sweep's row ring; xch: the group's exchange area, P * part_words<K>() values of T
+// (it may overlap the group's rings: the group synchronises after the forward sweep).
+template <typename T, int K, int P, class Grp>
+__device__ __forceinline__ void partition_sys(const DirectArgs<T>& p, int64_t t, int k, int lane,
+                                              T* ring_area, T* xch, const Grp& grp) {
   constexpr int NB = 2 * K;
   constexpr int PW = part_words<K>();
-  constexpr int G = 32 / P;
-  const unsigned full = 0xffffffffu;
-  const int lane = (int)(threadIdx.x & 31);
-  const int grp = lane / P, k = lane % P;
-  const unsigned gmask = P == 32 ? full : (((1u << P) - 1u) << (grp * P));
-  const int64_t t = warp * G + grp;
   bool active = t < p.L.nsys;
   const int64_t s = active ? p.L.sys(t) : 0;
   if (active && p.skip && p.skip[s]) active = false;
@@ -188,7 +208,7 @@ __device__ __forceinline__ void partition_one(const DirectArgs<T>& p, int64_t wa
     constexpr int D = StageDepth<T>::value;
     constexpr int NA = K == 2 ? 6 : 4;     // arrays staged: (a,) b, c, d, (e,) f
     constexpr int IB = K == 2 ? 1 : 0, IC = IB + 1, ID = IB + 2, IF = NA - 1;
-    const RowRing<T, NA, D> ring{stage, lane};
+    const RowRing<T, NA, D> ring{ring_area, lane};
     const T* src[NA];
     if (K == 2) {
       src[0] = p.a; src[1] = p.b; src[2] = p.c; src[3] = p.d; src[4] = p.e; src[5] = p.f;
@@ -261,7 +281,7 @@ __device__ __forceinline__ void partition_one(const DirectArgs<T>& p, int64_t wa
     }
     cp_async_wait<0>();
   }
-  __syncwarp();     // the ring's slots become the exchange area below
+  grp.sync();     // the rings' slots become the exchange area below
   // forward values of C's columns (nonzero only in the last K rows).  PD: column 1
   // (x_{s0+L}) has e at row L-2 and d at row L-1, column 2 (x_{s0+L+1}) e at row L-1.
   T zw1_2 = 0, zw1_1 = 0, zw2_1 = 0;     // zw<column>_<rows from the end>
@@ -277,7 +297,7 @@ __device__ __forceinline__ void partition_one(const DirectArgs<T>& p, int64_t wa
   // ---- first backward sweep: top and bottom K rows of g, V, W, written to this lane's
   // exchange slots (y-slot of row j: top rows 0 .. K-1 -> 0 .. K-1, bottom rows
   // L-K .. L-1 -> K .. 2K-1; columns g, V1, W1, V2, W2 at offsets 0, NB, 2NB, 3NB, 4NB)
-  T* const my = xch + lane * PW;
+  T* const my = xch + k * PW;
   if (!zero && L > 0) {
     T xf1 = 0, xf2 = 0, xv11 = 0, xv12 = 0, xv21 = 0, xv22 = 0;
     T xw11 = 0, xw12 = 0, xw21 = 0, xw22 = 0;
@@ -352,8 +372,8 @@ __device__ __forceinline__ void partition_one(const DirectArgs<T>& p, int64_t wa
 #pragma unroll
     for (int c = 0; c < PW; ++c) my[c] = T(0);
   }
-  const bool gzero = (__ballot_sync(full, zero) & gmask) != 0;
-  __syncwarp();
+  const bool gzero = grp.any(zero);
+  grp.sync();
   bool fail = gzero;
   if (mode == 2 && k == 0 && !fail) {
     // Block elimination over the chunks: with D_k = I - L_k Cp_{k-1} (D_0 = I),
@@ -364,7 +384,7 @@ __device__ __forceinline__ void partition_one(const DirectArgs<T>& p, int64_t wa
     // Cp_{k-1}): a K x K solve (partial pivoting) for the top rows, then
     // Y_bottom = R_bottom + X_bottom Y_top.  hp overwrites slots [0, NB) of chunk k and
     // Cp's column c slots [NB (1 + c), NB (2 + c)).
-    T* const base = xch + grp * P * PW;
+    T* const base = xch;
     for (int kk = 0; kk < P; ++kk) {
       T* e = base + kk * PW;
       T R[NB][K + 1];        // columns: W's K columns, then the right-hand side
@@ -433,8 +453,8 @@ __device__ __forceinline__ void partition_one(const DirectArgs<T>& p, int64_t wa
       }
     }
   }
-  fail = __shfl_sync(full, (int)fail, grp * P) != 0;
-  __syncwarp();
+  fail = grp.from_leader(fail);
+  grp.sync();
   // ---- redo (short systems, failed eliminations) by the first lane, or the second
   // backward sweep with z - z_V u - z_W v
   if (k == 0 && (mode == 1 || (mode == 2 && fail))) {
@@ -451,8 +471,8 @@ __device__ __forceinline__ void partition_one(const DirectArgs<T>& p, int64_t wa
     T u[K], v[K];
 #pragma unroll
     for (int m = 0; m < K; ++m) {
-      u[m] = k > 0 ? xch[(lane - 1) * PW + K + m] : T(0);
-      v[m] = k + 1 < P ? xch[(lane + 1) * PW + m] : T(0);
+      u[m] = k > 0 ? xch[(k - 1) * PW + K + m] : T(0);
+      v[m] = k + 1 < P ? xch[(k + 1) * PW + m] : T(0);
     }
     T x1 = 0, x2 = 0;
     constexpr int kB = 4;
@@ -494,8 +514,36 @@ __device__ __forceinline__ void partition_one(const DirectArgs<T>& p, int64_t wa
       }
     }
   }
-  const bool gbad = (__ballot_sync(full, bad) & gmask) != 0;
+  const bool gbad = grp.any(bad);
   if (back && k == 0) set_status(p.status, s, gbad ? BAND_ERR_NONFINITE : BAND_OK);
+}
+
+// The warp's 32 / P systems (P <= 32), positions t = warp * (32 / P) + (lane / P).
+// stage: the warp's staging area (stage_bytes_per_warp<T>() bytes of shared memory):
+// the forward sweep's row ring, then the interface exchange.
+template <typename T, int K, int P>
+__device__ __forceinline__ void partition_one(const DirectArgs<T>& p, int64_t warp, T* stage) {
+  static_assert(P <= 32, "a warp holds at most 32 chunks");
+  const int lane = (int)(threadIdx.x & 31);
+  const int g = lane / P, k = lane % P;
+  const WarpGroup grp{P == 32 ? 0xffffffffu : (((1u << (P & 31)) - 1u) << (g * P)), g * P};
+  partition_sys<T, K, P>(p, warp * (32 / P) + g, k, lane, stage, stage + g * P * part_words<K>(),
+                         grp);
+}
+
+// One system per block of W warps: P = 32 W chunks, the batch's blockIdx.x-th system.
+// smem: W staging areas of stage_bytes_per_warp<T>() bytes (the rings, then the
+// exchange of all P chunks); flag: one int of shared memory.
+template <typename T, int K, int W>
+__device__ __forceinline__ void partition_block(const DirectArgs<T>& p, unsigned char* smem,
+                                                int* flag) {
+  constexpr int P = 32 * W;
+  static_assert(P * part_words<K>() * (int)sizeof(T) <= W * stage_bytes_per_warp<T>(),
+                "the block's exchange fits its staging areas");
+  const int k = (int)threadIdx.x;
+  T* ring = reinterpret_cast<T*>(smem + (k >> 5) * stage_bytes_per_warp<T>());
+  const BlockGroup grp{flag};
+  partition_sys<T, K, P>(p, (int64_t)blockIdx.x, k, k & 31, ring, reinterpret_cast<T*>(smem), grp);
 }
 
 }  // namespace band

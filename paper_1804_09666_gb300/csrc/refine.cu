@@ -403,10 +403,11 @@ extern "C" band_status band_refine_solve(const band_desc* desc32, const void* co
   // the correction solve: A32 d32 = r32, on the schedule the descriptor asks for
   DirectReq req;
   const band_status v = make_direct(desc32, method, diag32, w.r32, w.d32, w.sst, w.solve,
-                                    w.solve_bytes, &req);
+                                    w.solve_bytes, &req, 256);
   if (v != BAND_OK) return v;
   req.d32.skip = w.done;
   auto solve = [&]() -> cudaError_t {
+    if (req.parts) return launch_partition<float>(req.d32, req.kmode, req.parts, st);
     return req.two_sided ? launch_twisted<float>(req.d32, req.kmode, st)
                          : launch_direct<float>(req.d32, req.kmode, st);
   };

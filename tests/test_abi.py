@@ -105,7 +105,9 @@ def test_bad_arguments_are_rejected_without_gpu(lib):
         (_desc(schedule=-1), L.NPDM, full),
         (_desc(chunks=8), L.NPDM, full),          # chunks without the partitioned schedule
         (_desc(schedule=L.SCHED_PARTITIONED, chunks=6), L.NPDM, full),   # not 4/8/16/32
-        (_desc(schedule=L.SCHED_PARTITIONED, chunks=64), L.NPDM, full),
+        (_desc(schedule=L.SCHED_PARTITIONED, chunks=512), L.NPDM, full),
+        (_desc(schedule=L.SCHED_PARTITIONED, chunks=2), L.NPDM, full),
+        (_desc(schedule=L.SCHED_PARTITIONED, chunks=48), L.NPDM, full),
     ]
     for d, m, diag in cases:
         code = lib.band_solve(ct.byref(d), m, None, diag, 8, 8, None, 8, 1 << 30, None)

@@ -23,7 +23,8 @@ from gpu_helpers import flat_of, per_system_rel, to_dev
 pytestmark = pytest.mark.gpu
 
 GOLD = os.path.join(os.path.dirname(__file__), "golden")
-PARTS = [4, 8, 16, 32]
+PARTS = [4, 8, 16, 32]              # lanes of one warp
+BLOCK_PARTS = [64, 128, 256]        # a block of 2, 4, 8 warps per system
 
 
 @pytest.fixture(scope="module")
@@ -57,7 +58,7 @@ def _args(B):
 # remainder pattern, and a long case; 37 systems leave a partial warp for every P.
 @pytest.mark.parametrize("n", [5, 31, 32, 33, 64, 127, 256, 257, 300, 1000, 4099])
 @pytest.mark.parametrize("k", [1, 2])
-@pytest.mark.parametrize("P", PARTS)
+@pytest.mark.parametrize("P", PARTS + BLOCK_PARTS)
 def test_partition_dominant(band, n, k, P):
     B = synth.cfg0(nsys=37, n=n, k=k, seed_salt=61)
     x, st = _solve(band, to_dev(B), k, P)
@@ -67,6 +68,19 @@ def test_partition_dominant(band, n, k, P):
     xg = flat_of(x)
     assert per_system_rel(xg, xo, *_args(B)).max() <= 1e-12
     assert per_system_rel(xg, B["x_true"], *_args(B)).max() <= 1e-12
+
+
+@pytest.mark.parametrize("k", [1, 2])
+@pytest.mark.parametrize("P", BLOCK_PARTS)
+def test_partition_block_long(band, k, P):
+    """A few long systems on a block of warps each (chunks of ~80 .. 320 rows, ragged
+    chunk lengths)."""
+    B = synth.cfg0(nsys=5, n=20481, k=k, seed_salt=74)
+    x, st = _solve(band, to_dev(B), k, P)
+    assert (st == 0).all(), st
+    xo, _, _, _ = _oracle(B, k)
+    assert per_system_rel(flat_of(x), xo, *_args(B)).max() <= 1e-12
+    assert per_system_rel(flat_of(x), B["x_true"], *_args(B)).max() <= 1e-12
 
 
 @pytest.mark.parametrize("layout", ["contiguous", "general"])
@@ -85,7 +99,7 @@ def test_partition_layouts(band, layout, k):
             flat[idx] = base[q].reshape(n, nsys)
             B[q] = flat
     xo, _, _, _ = _oracle(B, k)
-    for P in (8, 32):
+    for P in (8, 32, 64):
         x, st = _solve(band, to_dev(B), k, P)
         assert (st == 0).all()
         assert per_system_rel(flat_of(x), xo, *_args(B)).max() <= 1e-12
@@ -110,7 +124,7 @@ def test_partition_adi_nondominant(band, r):
             err_o = per_system_rel(xo, xt, *_args(B))
             tol = 1e-10 if k == 2 else 1e-12
             bound = 1e-8 if (k == 2 and r == 2.0) else np.maximum(tol, 10 * err_o)
-            for P in (8, 32):
+            for P in (8, 32, 128):
                 x, st = _solve(band, to_dev(B), k, P)
                 assert (st == 0).all(), (sweep, k, P, st)
                 err = per_system_rel(flat_of(x), xt, *_args(B))
@@ -133,7 +147,7 @@ def test_partition_fp32(band, k):
                          method="npdm" if k == 2 else "ntdm", schedule="thread")
     torch.cuda.synchronize()
     e1 = per_system_rel(flat_of(x1).astype(np.float64), xo, *_args(B))
-    for P in PARTS:
+    for P in PARTS + [64]:
         x, st = _solve(band, T, k, P)
         assert (st == 0).all()
         e = per_system_rel(flat_of(x).astype(np.float64), xo, *_args(B))
@@ -144,7 +158,11 @@ def test_partition_x_aliases_f(band):
     B = synth.cfg0(nsys=21, n=500, seed_salt=64)
     T = to_dev(B)
     xo, _, _, _ = _oracle(B, 2)
+    f0 = T["f"].clone()
     _solve(band, T, 2, 16, x=T["f"])
+    assert per_system_rel(flat_of(T["f"]), xo, *_args(B)).max() <= 1e-12
+    T["f"].copy_(f0)
+    _solve(band, T, 2, 64, x=T["f"])
     assert per_system_rel(flat_of(T["f"]), xo, *_args(B)).max() <= 1e-12
 
 
@@ -196,11 +214,33 @@ def test_partition_chunk_zero_pivot(band):
     assert not torch.equal(x[:, 16:], x1[:, 16:])
 
 
+def test_partition_block_chunk_zero_pivot(band):
+    """The same on a block of two warps (P = 64, n = 1280: chunk 1 starts at row 20):
+    the first thread redoes the system with NPDM (bitwise the thread schedule's)."""
+    n, nsys = 1280, 12
+    B = synth.cfg0(nsys=nsys, n=n, seed_salt=75)
+    B["c"].reshape(n, nsys)[20, 0:4] = 0.0
+    T = to_dev(B)
+    xt, _, _, _ = _oracle(B, 2, "gepp")
+    xo, so, _, _ = _oracle(B, 2)
+    assert (so == 0).all()
+    bound = np.maximum(1e-12, 10 * per_system_rel(xo, xt, *_args(B)))
+    for method in ("npdm", "spdm"):
+        x, st = _solve(band, T, 2, 64, method=method)
+        assert (st == 0).all(), (method, st)
+        assert (per_system_rel(flat_of(x), xt, *_args(B)) <= bound).all()
+    x, _ = _solve(band, T, 2, 64)
+    x1, _ = band.solve(T["a"], T["b"], T["c"], T["d"], T["e"], T["f"], method="npdm",
+                       schedule="thread")
+    torch.cuda.synchronize()
+    assert torch.equal(x[:, 0:4], x1[:, 0:4])
+
+
 def test_partition_planted_npdm_zero_pivots(band):
     """a_i = b_i = c_i = 0 (and a_{i+2} = 0) in one row: NPDM's pivot there is exactly 0
     whatever came before.  NPDM on the partitioned schedule still reports ZERO_PIVOT
     (the first lane's redo meets it); SPDM solves the systems through the fix-up."""
-    n, nsys = 400, 16
+    n, nsys = 600, 16
     B = synth.cfg0(nsys=nsys, n=n, seed_salt=67)
     for i, sl in ((20, slice(0, 8)), (333, slice(8, 16))):
         for q, r in (("a", i), ("b", i), ("c", i), ("a", i + 2)):
@@ -210,7 +250,7 @@ def test_partition_planted_npdm_zero_pivots(band):
     xs, ss, _, _ = _oracle(B, 2, "symbolic")
     assert (ss == 0).all()
     bound = np.maximum(1e-12, 10 * per_system_rel(xs, xt, *_args(B)))
-    for P in (4, 32):
+    for P in (4, 32, 64):
         _, st = _solve(band, T, 2, P)
         assert (st == 3).all(), (P, st)
         x, st = _solve(band, T, 2, P, method="spdm")
@@ -255,7 +295,7 @@ def test_partition_auto_chunks(band):
     T = to_dev(B)
     x0, st = _solve(band, T, 2, 0)
     assert (st == 0).all()
-    assert any(torch.equal(x0, _solve(band, T, 2, P)[0]) for P in PARTS)
+    assert any(torch.equal(x0, _solve(band, T, 2, P)[0]) for P in PARTS + BLOCK_PARTS)
 
 
 def test_partition_in_batch_equals_single(band):
@@ -272,6 +312,7 @@ def test_partition_in_batch_equals_single(band):
         dict(method="npdm", schedule="partitioned", chunks=4, **{q: P3[q] for q in "abcdef"}),
         dict(method="npdm", schedule="two_sided", **{q: P1[q] for q in "abcdef"}),
         dict(op="sip", tol=1e-10, max_it=200, **{q: S[q] for q in "abcdef"}),
+        dict(method="npdm", schedule="partitioned", chunks=128, **{q: P1[q] for q in "abcdef"}),
     ]
     res = band.BatchPlan(specs).run()
     torch.cuda.synchronize()
@@ -283,6 +324,8 @@ def test_partition_in_batch_equals_single(band):
         assert (st == 0).all()
     assert torch.allclose(res[0]["x"], res[3]["x"], rtol=0, atol=1e-12)
     assert (res[4]["status"].cpu().numpy() == 0).all()
+    # a batched task is one warp: 128 chunks run as 32
+    assert torch.equal(res[5]["x"], res[0]["x"])
 
 
 def test_partition_ragged_buckets(band):
