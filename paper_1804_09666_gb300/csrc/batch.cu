@@ -167,13 +167,19 @@ __global__ void __launch_bounds__(kTailThreads) k_sip_tail_batch(const __grid_co
   __shared__ Aff sh[kTailThreads];
   __shared__ double red[kTailThreads / 32];
   extern __shared__ double tail_smem[];
-  for (int j = 0; j < t.count; ++j) {
-    const SipArgs& p = t.it[j];
-    const unsigned long long count = *p.tail_count;
-    for (unsigned long long it = blockIdx.x; it < count; it += gridDim.x) {
-      const int64_t s = p.tail_list[it];
-      sip_tail_block(p, s, p.tail_rn[it], sh, red, tail_smem, t.smem_rows);
+  // the tail lists of all problems as one list, dealt out round-robin over the blocks
+  // (a few systems per problem would otherwise queue on the same few blocks)
+  unsigned long long total = 0;
+  for (int j = 0; j < t.count; ++j) total += *t.it[j].tail_count;
+  for (unsigned long long g = blockIdx.x; g < total; g += gridDim.x) {
+    int j = 0;
+    unsigned long long it = g;
+    for (unsigned long long c = *t.it[0].tail_count; it >= c; c = *t.it[j].tail_count) {
+      it -= c;
+      ++j;
     }
+    const SipArgs& p = t.it[j];
+    sip_tail_block(p, p.tail_list[it], p.tail_rn[it], sh, red, tail_smem, t.smem_rows);
   }
 }
 
