@@ -153,7 +153,7 @@ __global__ void __launch_bounds__(64) k_symbolic_batch(const __grid_constant__ S
 }
 
 // the deferred residual and decision of the SIP problems (blockIdx.y: the problem)
-__global__ void __launch_bounds__(256, 3) k_sip_resid_batch(const __grid_constant__ TailTable t) {
+__global__ void __launch_bounds__(256, 4) k_sip_resid_batch(const __grid_constant__ TailTable t) {
   sip_resid_cell(t.it[blockIdx.y], (int64_t)blockIdx.x * blockDim.x + threadIdx.x);
 }
 

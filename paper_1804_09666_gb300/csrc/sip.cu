@@ -362,7 +362,7 @@ __global__ void __launch_bounds__(128) k_sip_two(const SipArgs p) {
   sip_two_sided(p, t, t < p.L.nsys);
 }
 
-__global__ void __launch_bounds__(256, 3) k_sip_resid(const SipArgs p) {
+__global__ void __launch_bounds__(256, 4) k_sip_resid(const SipArgs p) {
   sip_resid_cell(p, (int64_t)blockIdx.x * blockDim.x + threadIdx.x);
 }
 

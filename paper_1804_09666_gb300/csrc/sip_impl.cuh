@@ -464,7 +464,7 @@ __device__ inline double sip_resid_rows(const SipArgs& p, int64_t t, int64_t i0,
   auto X = [&](int64_t j) -> double { return (j >= 0 && j < n) ? p.x[q0 + j * es] : 0.0; };
   double xm2 = X(i0 - 2), xm1 = X(i0 - 1), x0 = X(i0), xp1 = X(i0 + 1);
   double rn = 0.0;
-  constexpr int kB = 2;
+  constexpr int kB = 1;
   for (int64_t ib = i0; ib < i1; ib += kB) {
     Row A[kB];
     double xv[kB];
