@@ -179,7 +179,9 @@ struct BlockGroup {
 // staging area (stage_bytes_per_warp<T>() bytes of shared memory) for the forward
 // sweep's row ring; xch: the group's exchange area, P * part_words<K>() values of T
 // (it may overlap the group's rings: the group synchronises after the forward sweep).
-template <typename T, int K, int P, class Grp>
+// KB: rows whose scratch the backward sweeps load together (registers against memory
+// latency).
+template <typename T, int K, int P, int KB, class Grp>
 __device__ __forceinline__ void partition_sys(const DirectArgs<T>& p, int64_t t, int k, int lane,
                                               T* ring_area, T* xch, const Grp& grp) {
   constexpr int NB = 2 * K;
@@ -303,7 +305,7 @@ __device__ __forceinline__ void partition_sys(const DirectArgs<T>& p, int64_t t,
     T xw11 = 0, xw12 = 0, xw21 = 0, xw22 = 0;
     // rows in blocks of kB: the block's scratch values are loaded together (one memory
     // latency a block)
-    constexpr int kB = 4;
+    constexpr int kB = KB;
     for (int64_t top = L - 1; top >= 0; top -= kB) {
       T av[kB], bv[kB], fv[kB], v1[kB], v2[kB];
 #pragma unroll
@@ -475,7 +477,7 @@ __device__ __forceinline__ void partition_sys(const DirectArgs<T>& p, int64_t t,
       v[m] = k + 1 < P ? xch[(k + 1) * PW + m] : T(0);
     }
     T x1 = 0, x2 = 0;
-    constexpr int kB = 4;
+    constexpr int kB = KB;
     for (int64_t top = L - 1; top >= 0; top -= kB) {
       T av[kB], bv[kB], fv[kB], v1[kB], v2[kB];
 #pragma unroll
@@ -521,14 +523,14 @@ __device__ __forceinline__ void partition_sys(const DirectArgs<T>& p, int64_t t,
 // The warp's 32 / P systems (P <= 32), positions t = warp * (32 / P) + (lane / P).
 // stage: the warp's staging area (stage_bytes_per_warp<T>() bytes of shared memory):
 // the forward sweep's row ring, then the interface exchange.
-template <typename T, int K, int P>
+template <typename T, int K, int P, int KB = 4>
 __device__ __forceinline__ void partition_one(const DirectArgs<T>& p, int64_t warp, T* stage) {
   static_assert(P <= 32, "a warp holds at most 32 chunks");
   const int lane = (int)(threadIdx.x & 31);
   const int g = lane / P, k = lane % P;
   const WarpGroup grp{P == 32 ? 0xffffffffu : (((1u << (P & 31)) - 1u) << (g * P)), g * P};
-  partition_sys<T, K, P>(p, warp * (32 / P) + g, k, lane, stage, stage + g * P * part_words<K>(),
-                         grp);
+  partition_sys<T, K, P, KB>(p, warp * (32 / P) + g, k, lane, stage,
+                             stage + g * P * part_words<K>(), grp);
 }
 
 // One system per block of W warps: P = 32 W chunks, the batch's blockIdx.x-th system.
@@ -543,7 +545,8 @@ __device__ __forceinline__ void partition_block(const DirectArgs<T>& p, unsigned
   const int k = (int)threadIdx.x;
   T* ring = reinterpret_cast<T*>(smem + (k >> 5) * stage_bytes_per_warp<T>());
   const BlockGroup grp{flag};
-  partition_sys<T, K, P>(p, (int64_t)blockIdx.x, k, k & 31, ring, reinterpret_cast<T*>(smem), grp);
+  partition_sys<T, K, P, 4>(p, (int64_t)blockIdx.x, k, k & 31, ring, reinterpret_cast<T*>(smem),
+                            grp);
 }
 
 }  // namespace band
