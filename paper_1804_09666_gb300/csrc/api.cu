@@ -97,13 +97,16 @@ int64_t part_rows_bound(const band_desc* d) {
 }
 
 // Lanes per system on the partitioned schedule (0: another schedule).  chunks == 0: the
-// P in {4, 8, 16, 32} (chunks of 8 rows or more) with the least estimated time
-//   warps(P) * (n / P * c_row + P * c_if) / min(1, warps(P) / (8 warps x SMs)),
+// P in {4, 8, .., max_parts} (chunks of 8 rows or more) with the least estimated time
+//   warps(P) * (n / P * c_row + (P / 2 + 2) * c_if) / min(1, warps(P) / (8 warps x SMs)),
 // warps(P) = nsys * P / 32: the FP64 instructions of the launch (a chunk row costs
-// c_row = 32 (PD) / 14 (TD), the serial interface c_if = 60 / 25 per chunk), slowed down
-// while too few warps are resident to keep the FP64 pipes busy.  Measured on GB300
-// (FP64 NPDM): 2048 x 2048 takes 0.87 / 0.63 / 0.88 ms at P = 8 / 16 / 32, 7280 x 6000
-// 5.1 / 3.6 / 3.8 / 4.4 ms at P = 4 .. 32, 256 x 8192 its least time at P = 32.
+// c_row = 32 (PD) / 14 (TD); the interface, eliminated from both ends, c_if = 60 / 25
+// per chunk on its longer half, plus the meeting), slowed down while too few warps are
+// resident to keep the FP64 pipes busy.  Measured on GB300 (FP64 NPDM, ms):
+// 2048 x 2048 0.53 / 0.45 / 0.75 at P = 8 / 16 / 32 (chosen: 16); 256 x 8192 0.55 /
+// 0.36 / 0.38 at P = 32 / 64 / 128 (chosen: 128); 64 x 65536 1.17 / 1.01 at P = 128 /
+// 256 (chosen: 256); 7280 x 6000 3.77 / 3.07 at P = 8 / 16 (chosen: 8, the model's
+// worst miss; band_autotune measures instead).
 int choose_parts(const band_desc* d, int max_parts) {
   if (d->schedule != BAND_SCHED_PARTITIONED) return 0;
   if (d->chunks) return d->chunks < max_parts ? d->chunks : max_parts;
@@ -125,7 +128,8 @@ int choose_parts(const band_desc* d, int max_parts) {
     if (P > 4 && d->n < (int64_t)8 * P) break;
     const double warps = (double)d->nsys * P / 32.0;
     const double eff = warps < sat ? warps / sat : 1.0;
-    const double t = warps * ((double)d->n / P * c_row + P * c_if) / (eff > 0 ? eff : 1e-9);
+    const double t =
+        warps * ((double)d->n / P * c_row + (P / 2 + 2) * c_if) / (eff > 0 ? eff : 1e-9);
     if (best_t < 0 || t < best_t) { best_t = t; best = P; }
   }
   return best;

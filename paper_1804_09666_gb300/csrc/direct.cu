@@ -92,8 +92,7 @@ __global__ void __launch_bounds__(32 * SweepWarps<T>::value) k_partition(const D
 template <typename T, int K, int W>
 __global__ void __launch_bounds__(32 * W) k_partition_block(const DirectArgs<T> p) {
   extern __shared__ __align__(16) unsigned char stage_mem[];
-  __shared__ int flag;
-  partition_block<T, K, W>(p, stage_mem, &flag);
+  partition_block<T, K, W>(p, stage_mem);
 }
 
 template <typename T, int K>
@@ -116,7 +115,7 @@ static cudaError_t launch_partition_block_k(const DirectArgs<T>& p, int parts, c
   switch (parts) {
     case 64: k_partition_block<T, K, 2><<<grid, 64, smem, st>>>(p); break;
     case 128: k_partition_block<T, K, 4><<<grid, 128, smem, st>>>(p); break;
-    case 256: {     // 48 KiB of staging areas and the flag: above the default limit
+    case 256: {     // 48 KiB of staging areas: the most a launch gets without opting in
       const cudaError_t e = tail_prepare((const void*)k_partition_block<T, K, 8>);
       if (e != cudaSuccess) return e;
       k_partition_block<T, K, 8><<<grid, 256, smem, st>>>(p);

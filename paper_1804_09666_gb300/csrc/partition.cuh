@@ -16,9 +16,9 @@
 // block-tridiagonal interface system
 //   y_k + L_k y_{k-1} + U_k y_{k+1} = (g_top, g_bottom)_k,
 //   L_k y_{k-1} = V_k (bottom K rows of y_{k-1}),   U_k y_{k+1} = W_k (top K rows of y_{k+1}),
-// which the system's first lane solves by block elimination; the blocks' structure
-// leaves one K x K solve (partial pivoting) per chunk.  Then each lane back-substitutes
-// its chunk once more, with z - z_V u_k - z_W v_k in place of z: x_k itself.
+// which two lanes solve by block elimination from both ends, meeting in the middle; the
+// blocks' structure leaves one K x K solve (partial pivoting) per chunk.  Then each lane
+// back-substitutes its chunk once more, with z - z_V u_k - z_W v_k in place of z: x_k.
 // Arithmetic per row: about 2.3x NPDM (PD) and 1.8x NTDM (TD); the dependent chain of a
 // system is n / P rows long instead of n (one thread) or n / 2 (two-sided).
 //
@@ -151,29 +151,169 @@ __device__ __noinline__ void part_serial(const DirectArgs<T>& p, int64_t t) {
 }
 
 // The lanes that share one system: P of a warp's lanes (P <= 32), or a whole block of
-// P / 32 warps.  any(): some lane of the group holds v; from_leader(): chunk 0's value.
-// Every lane of the warp (block) calls each of them.
+// P / 32 warps.  any(): some lane of the group holds v.  Every lane of the warp (block)
+// calls sync() and any().
 struct WarpGroup {
   unsigned mask;     // the group's lanes
-  int leader;        // lane of chunk 0
   __device__ __forceinline__ void sync() const { __syncwarp(); }
   __device__ __forceinline__ bool any(bool v) const {
     return (__ballot_sync(0xffffffffu, v) & mask) != 0;
   }
-  __device__ __forceinline__ bool from_leader(bool v) const {
-    return __shfl_sync(0xffffffffu, (int)v, leader) != 0;
-  }
 };
 struct BlockGroup {
-  int* flag;         // one int of shared memory
   __device__ __forceinline__ void sync() const { __syncthreads(); }
   __device__ __forceinline__ bool any(bool v) const { return __syncthreads_or(v) != 0; }
-  __device__ __forceinline__ bool from_leader(bool v) const {
-    if (threadIdx.x == 0) *flag = v ? 1 : 0;
-    __syncthreads();
-    return *flag != 0;
-  }
 };
+
+// ---------------------------------------------------------------------------
+// The interface system y_k + L_k y_{k-1} + U_k y_{k+1} = g_k over a system's P chunks
+// (exchange slots xch: per chunk g, V's and W's K columns; y_k = (top K, bottom K rows)).
+// Block elimination from both ends: with D_k = I - L_k Cp_{k-1} (D_0 = I),
+// hp_k = D_k^{-1} (g_k - L_k hp_{k-1}) and Cp_k = D_k^{-1} U_k top-down over chunks
+// 0 .. P/2-1.  U_k acts on the top K rows of y_{k+1} and L_k on the bottom K rows of
+// y_{k-1}, so only Cp's first K columns are nonzero and D_k = [[I - X_top, 0],
+// [-X_bottom, I]] with X = V_k (bottom K rows of Cp_{k-1}): a K x K solve (partial
+// pivoting) for the top rows, then Y_bottom = R_bottom + X_bottom Y_top.  Bottom-up over
+// chunks P-1 .. P/2 the same step applies to the mirrored system: y's halves swapped
+// (slot r read as (r + K) mod 2K) and the roles of V and W exchanged.  hp overwrites
+// slots [0, NB) of a chunk and Cp's column c slots [NB (1 + c), NB (2 + c)), in the
+// pass's own row order.  Returns false on a singular K x K pivot block.
+template <typename T, int K, int P>
+__device__ __forceinline__ bool part_eliminate(T* xch, bool up) {
+  constexpr int NB = 2 * K;
+  constexpr int PW = part_words<K>();
+  const int rot = up ? K : 0;                       // slot of row r: (r + rot) mod NB
+  const int offP = up ? 2 * NB : NB;                // coupling to the chunk done before
+  const int offN = up ? NB : 2 * NB;                // coupling to the chunk done after
+  auto row = [&](int r) { return (r + rot) & (NB - 1); };
+  for (int q = 0; q < P / 2; ++q) {
+    const int kk = up ? P - 1 - q : q;
+    T* e = xch + kk * PW;
+    T R[NB][K + 1];        // columns: the coupling to the next chunk, then g
+    T X[NB][K];
+#pragma unroll
+    for (int r = 0; r < NB; ++r) {
+      R[r][K] = e[row(r)];
+      R[r][0] = e[offN + row(r)];
+      if (K == 2) R[r][K - 1] = e[offN + 2 * NB + row(r)];
+#pragma unroll
+      for (int c = 0; c < K; ++c) X[r][c] = T(0);
+    }
+    if (q > 0) {
+      const T* ep = up ? e + PW : e - PW;
+#pragma unroll
+      for (int r = 0; r < NB; ++r) {
+        T vr[K];
+        vr[0] = e[offP + row(r)];
+        if (K == 2) vr[K - 1] = e[offP + 2 * NB + row(r)];
+#pragma unroll
+        for (int m = 0; m < K; ++m) {
+#pragma unroll
+          for (int c = 0; c < K; ++c) X[r][c] = fma(vr[m], ep[NB * (1 + c) + row(K + m)], X[r][c]);
+          R[r][K] = fma(-vr[m], ep[row(K + m)], R[r][K]);
+        }
+      }
+    }
+    T A[K][K], Rt[K][K + 1];
+#pragma unroll
+    for (int r = 0; r < K; ++r) {
+#pragma unroll
+      for (int c = 0; c < K; ++c) A[r][c] = (r == c ? T(1) : T(0)) - X[r][c];
+#pragma unroll
+      for (int c = 0; c <= K; ++c) Rt[r][c] = R[r][c];
+    }
+    if (!block_solve<T, K, K + 1>(A, Rt)) return false;
+#pragma unroll
+    for (int c = 0; c <= K; ++c) {
+#pragma unroll
+      for (int r = 0; r < K; ++r) {
+        T v = R[K + r][c];
+#pragma unroll
+        for (int m = 0; m < K; ++m) v = fma(X[K + r][m], Rt[m][c], v);
+        R[K + r][c] = v;
+        R[r][c] = Rt[r][c];
+      }
+    }
+#pragma unroll
+    for (int r = 0; r < NB; ++r) {
+      e[row(r)] = R[r][K];
+#pragma unroll
+      for (int c = 0; c < K; ++c) e[NB * (1 + c) + row(r)] = R[r][c];
+    }
+  }
+  return true;
+}
+
+// Where the passes meet: chunk m-1 = P/2-1 gives y_{m-1} = hp - Cp (top K rows of y_m),
+// chunk m (bottom-up) y_m = hp' - Cp' (bottom K rows of y_{m-1}).  With u = bottom
+// rows of y_{m-1} and v = top rows of y_m: [[I, Cp_bottom], [Cp'_top, I]] (u, v) =
+// (hp_bottom, hp'_top), solved with partial pivoting; then both chunks' y (natural row
+// order: chunk m's mirrored row r is y's row (r + K) mod NB, in that slot).  False if
+// singular.
+template <typename T, int K, int P>
+__device__ __forceinline__ bool part_meet(T* xch) {
+  constexpr int NB = 2 * K;
+  constexpr int PW = part_words<K>();
+  constexpr int m = P / 2;
+  T* a = xch + (m - 1) * PW;       // top-down, natural row order
+  T* b = xch + m * PW;             // bottom-up: row r in slot (r + K) mod NB
+  T M[4][5];
+#pragma unroll
+  for (int r = 0; r < K; ++r) {
+#pragma unroll
+    for (int c = 0; c < K; ++c) {
+      M[r][c] = r == c ? T(1) : T(0);
+      M[r][K + c] = a[NB * (1 + c) + K + r];            // Cp_{m-1}, bottom row r, column c
+      M[K + r][c] = b[NB * (1 + c) + r];                // Cp'_m, its row K + r = top row r
+      M[K + r][K + c] = r == c ? T(1) : T(0);
+    }
+    M[r][NB] = a[K + r];
+    M[K + r][NB] = b[r];
+  }
+  if (!solve_small<T, NB>(M)) return false;
+  T u[K], v[K];
+#pragma unroll
+  for (int c = 0; c < K; ++c) {
+    u[c] = M[c][NB];
+    v[c] = M[K + c][NB];
+  }
+#pragma unroll
+  for (int r = 0; r < NB; ++r) {
+    T ya = a[r], yb = b[r];
+#pragma unroll
+    for (int c = 0; c < K; ++c) {
+      ya = fma(-a[NB * (1 + c) + r], v[c], ya);
+      yb = fma(-b[NB * (1 + c) + r], u[c], yb);
+    }
+    a[r] = ya;
+    b[r] = yb;
+  }
+  return true;
+}
+
+// Back-substitution of one pass's half, away from the meeting point: top-down chunks
+// P/2-2 .. 0 (y_k = hp_k - Cp_k (top rows of y_{k+1})) or bottom-up chunks P/2+1 .. P-1
+// (the mirrored step).  The mirrored row r sits in slot (r + K) mod NB, which is where
+// y's row (r + K) mod NB belongs: y ends in natural order in both halves.
+template <typename T, int K, int P>
+__device__ __forceinline__ void part_backsub(T* xch, bool up) {
+  constexpr int NB = 2 * K;
+  constexpr int PW = part_words<K>();
+  const int rot = up ? K : 0;
+  for (int q = P / 2 - 2; q >= 0; --q) {
+    const int kk = up ? P - 1 - q : q;
+    T* e = xch + kk * PW;
+    const T* en = up ? e - PW : e + PW;
+#pragma unroll
+    for (int r = 0; r < NB; ++r) {
+      const int sr = (r + rot) & (NB - 1);
+      T v = e[sr];
+#pragma unroll
+      for (int c = 0; c < K; ++c) v = fma(-e[NB * (1 + c) + sr], en[(c + rot) & (NB - 1)], v);
+      e[sr] = v;
+    }
+  }
+}
 
 // The batch's t-th system, chunk k of P, by one lane of its group.  ring: this warp's
 // staging area (stage_bytes_per_warp<T>() bytes of shared memory) for the forward
@@ -377,85 +517,18 @@ __device__ __forceinline__ void partition_sys(const DirectArgs<T>& p, int64_t t,
   const bool gzero = grp.any(zero);
   grp.sync();
   bool fail = gzero;
-  if (mode == 2 && k == 0 && !fail) {
-    // Block elimination over the chunks: with D_k = I - L_k Cp_{k-1} (D_0 = I),
-    // hp_k = D_k^{-1} (rhs_k - L_k hp_{k-1}) and Cp_k = D_k^{-1} U_k, then
-    // y_{P-1} = hp_{P-1}, y_k = hp_k - Cp_k y_{k+1}.  U_k acts on the top K rows of
-    // y_{k+1} and L_k on the bottom K rows of y_{k-1}, so only Cp's first K columns are
-    // nonzero and D_k = [[I - X_top, 0], [-X_bottom, I]] with X = V_k (bottom K rows of
-    // Cp_{k-1}): a K x K solve (partial pivoting) for the top rows, then
-    // Y_bottom = R_bottom + X_bottom Y_top.  hp overwrites slots [0, NB) of chunk k and
-    // Cp's column c slots [NB (1 + c), NB (2 + c)).
-    T* const base = xch;
-    for (int kk = 0; kk < P; ++kk) {
-      T* e = base + kk * PW;
-      T R[NB][K + 1];        // columns: W's K columns, then the right-hand side
-      T X[NB][K];
-#pragma unroll
-      for (int r = 0; r < NB; ++r) {
-        R[r][K] = e[r];
-        R[r][0] = e[2 * NB + r];
-        if (K == 2) R[r][K - 1] = e[4 * NB + r];
-#pragma unroll
-        for (int c = 0; c < K; ++c) X[r][c] = T(0);
-      }
-      if (kk > 0) {
-        const T* ep = e - PW;
-#pragma unroll
-        for (int r = 0; r < NB; ++r) {
-          T vr[K];
-          vr[0] = e[NB + r];
-          if (K == 2) vr[K - 1] = e[3 * NB + r];
-#pragma unroll
-          for (int m = 0; m < K; ++m) {
-#pragma unroll
-            for (int c = 0; c < K; ++c) X[r][c] = fma(vr[m], ep[NB * (1 + c) + K + m], X[r][c]);
-            R[r][K] = fma(-vr[m], ep[K + m], R[r][K]);
-          }
-        }
-      }
-      T A[K][K], Rt[K][K + 1];
-#pragma unroll
-      for (int r = 0; r < K; ++r) {
-#pragma unroll
-        for (int c = 0; c < K; ++c) A[r][c] = (r == c ? T(1) : T(0)) - X[r][c];
-#pragma unroll
-        for (int c = 0; c <= K; ++c) Rt[r][c] = R[r][c];
-      }
-      if (!block_solve<T, K, K + 1>(A, Rt)) { fail = true; break; }
-#pragma unroll
-      for (int c = 0; c <= K; ++c) {
-#pragma unroll
-        for (int r = 0; r < K; ++r) {
-          T v = R[K + r][c];
-#pragma unroll
-          for (int m = 0; m < K; ++m) v = fma(X[K + r][m], Rt[m][c], v);
-          R[K + r][c] = v;
-          R[r][c] = Rt[r][c];
-        }
-      }
-#pragma unroll
-      for (int r = 0; r < NB; ++r) {
-        e[r] = R[r][K];
-#pragma unroll
-        for (int c = 0; c < K; ++c) e[NB * (1 + c) + r] = R[r][c];
-      }
-    }
-    if (!fail) {
-      for (int kk = P - 2; kk >= 0; --kk) {
-        T* e = base + kk * PW;
-        const T* en = e + PW;
-#pragma unroll
-        for (int r = 0; r < NB; ++r) {
-          T v = e[r];
-#pragma unroll
-          for (int c = 0; c < K; ++c) v = fma(-e[NB * (1 + c) + r], en[c], v);
-          e[r] = v;
-        }
-      }
-    }
-  }
-  fail = grp.from_leader(fail);
+  // the interface: chunks 0 .. P/2-1 eliminated top-down by chunk 0's lane, chunks
+  // P-1 .. P/2 bottom-up by chunk P-1's lane, at the same time; they meet in a 2K x 2K
+  // system, then each back-substitutes its half
+  const bool ilane = mode == 2 && (k == 0 || k == P - 1);
+  bool ifail = false;
+  if (ilane && !fail) ifail = !part_eliminate<T, K, P>(xch, k != 0);
+  fail = fail || grp.any(ifail);
+  grp.sync();
+  if (mode == 2 && k == 0 && !fail) ifail = !part_meet<T, K, P>(xch);
+  fail = fail || grp.any(ifail);
+  grp.sync();
+  if (ilane && !fail) part_backsub<T, K, P>(xch, k != 0);
   grp.sync();
   // ---- redo (short systems, failed eliminations) by the first lane, or the second
   // backward sweep with z - z_V u - z_W v
@@ -528,23 +601,22 @@ __device__ __forceinline__ void partition_one(const DirectArgs<T>& p, int64_t wa
   static_assert(P <= 32, "a warp holds at most 32 chunks");
   const int lane = (int)(threadIdx.x & 31);
   const int g = lane / P, k = lane % P;
-  const WarpGroup grp{P == 32 ? 0xffffffffu : (((1u << (P & 31)) - 1u) << (g * P)), g * P};
+  const WarpGroup grp{P == 32 ? 0xffffffffu : (((1u << (P & 31)) - 1u) << (g * P))};
   partition_sys<T, K, P, KB>(p, warp * (32 / P) + g, k, lane, stage,
                              stage + g * P * part_words<K>(), grp);
 }
 
 // One system per block of W warps: P = 32 W chunks, the batch's blockIdx.x-th system.
 // smem: W staging areas of stage_bytes_per_warp<T>() bytes (the rings, then the
-// exchange of all P chunks); flag: one int of shared memory.
+// exchange of all P chunks).
 template <typename T, int K, int W>
-__device__ __forceinline__ void partition_block(const DirectArgs<T>& p, unsigned char* smem,
-                                                int* flag) {
+__device__ __forceinline__ void partition_block(const DirectArgs<T>& p, unsigned char* smem) {
   constexpr int P = 32 * W;
   static_assert(P * part_words<K>() * (int)sizeof(T) <= W * stage_bytes_per_warp<T>(),
                 "the block's exchange fits its staging areas");
   const int k = (int)threadIdx.x;
   T* ring = reinterpret_cast<T*>(smem + (k >> 5) * stage_bytes_per_warp<T>());
-  const BlockGroup grp{flag};
+  const BlockGroup grp{};
   partition_sys<T, K, P, 4>(p, (int64_t)blockIdx.x, k, k & 31, ring, reinterpret_cast<T*>(smem),
                             grp);
 }
