@@ -119,13 +119,13 @@ typedef struct {
  * BAND_SCHED_PARTITIONED: P = desc->chunks lanes per system: 32 / P systems a warp for
  *   P <= 32, one system per block of P / 32 warps beyond (band_solve only; inside
  *   band_solve_batch, whose tasks are single warps, P > 32 runs as P = 32).  Lane k
- *   eliminates rows [k n / P, (k+1) n / P) (about) with NPDM's
- *   recurrence, carrying the columns through which the chunk couples to its neighbours'
- *   boundary rows (the SPIKE partition); the chunks' boundary rows form a
- *   block-tridiagonal system of P blocks of 4 (PD) / 2 (TD) unknowns that the system's
- *   first lane solves by block elimination (a 2x2 (PD) / 1x1 (TD) pivot block per
- *   chunk, partial pivoting); then every lane back-substitutes its chunk.  About 2.3x (PD) / 1.8x (TD) NPDM's arithmetic
- *   per row, for a dependent chain of n / P rows: for batches with too few systems to
+ *   eliminates rows [k n / P, (k+1) n / P) (about) with NPDM's recurrence, carrying the
+ *   columns through which the chunk couples to its neighbours' boundary rows (the SPIKE
+ *   partition); the chunks' boundary rows form a block-tridiagonal system of P blocks
+ *   of 4 (PD) / 2 (TD) unknowns, eliminated from both ends by two lanes (a 2x2 (PD) /
+ *   1x1 (TD) pivot block per chunk, partial pivoting) that meet in a 4x4 / 2x2 system;
+ *   then every lane back-substitutes its chunk.  About 2.3x (PD) / 1.8x (TD) NPDM's
+ *   arithmetic per row, for a dependent chain of n / P rows: for batches with too few systems to
  *   fill the GPU, and for the longest systems of a ragged batch.  A zero pivot in a
  *   chunk or a singular interface block sends an STDM/SPDM system to the symbolic fix-up
  *   and makes the first lane redo an NTDM/NPDM system with NPDM alone (BAND_ERR_ZERO_PIVOT
