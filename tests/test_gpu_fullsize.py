@@ -54,6 +54,46 @@ def test_ragged_65536_systems(band):
         assert np.abs(xg[lo:hi] - xo).max() / np.abs(xo).max() <= 1e-12, s
 
 
+def test_ragged_65536_systems_tuned_buckets(band):
+    """The same batch in bench.py's configuration: size buckets in one batched launch,
+    schedules from the joint autotuner (the longest buckets partitioned), replayed from a
+    CUDA graph.  Every system against its manufactured solution; sampled systems from
+    every bucket, the longest of each included, against the oracle."""
+    B = synth.cfg2()
+    dev = {q: torch.from_numpy(B[q]).to(DEV) for q in "abcdef"}
+    plan = band.RaggedPlan(*(dev[q] for q in "abcdef"), B["offsets"], B["hbw"], schedule="tune")
+    assert 3 in plan.schedules                     # some bucket runs partitioned
+    plan.run()
+    torch.cuda.synchronize()
+    s = torch.cuda.Stream()
+    s.wait_stream(torch.cuda.current_stream())
+    g = torch.cuda.CUDAGraph()
+    with torch.cuda.stream(s):
+        with torch.cuda.graph(g, stream=s):
+            plan.run()
+    torch.cuda.current_stream().wait_stream(s)
+    plan.x.zero_()
+    g.replay()
+    torch.cuda.synchronize()
+    assert (plan.status.cpu() == 0).all()
+    xg = plan.x.cpu().numpy()
+    per = np.maximum.reduceat(np.abs(xg - B["x_true"]), B["offsets"][:-1])
+    assert per.max() <= 1e-12
+    order = plan.order.cpu().numpy()
+    rng = np.random.default_rng(8)
+    for (first, count, n_max, k), sched in zip(plan.buckets, plan.schedules):
+        ids = order[first:first + count]
+        pick = {int(ids[0])} | set(rng.choice(ids, min(3, count), replace=False).tolist())
+        for sid in sorted(pick):
+            S = synth.system(B, sid)
+            if k == 1:
+                xo, _ = oracle.ntdm(S["b"], S["c"], S["d"], S["f"])
+            else:
+                xo, _ = oracle.npdm(*(S[q] for q in "abcdef"))
+            lo, hi = int(B["offsets"][sid]), int(B["offsets"][sid + 1])
+            assert np.abs(xg[lo:hi] - xo).max() / np.abs(xo).max() <= 1e-12, (sid, sched)
+
+
 def test_refine_16384_x_4096(band):
     """The precision workload: 16384 PD systems of n = 4096 in FP32, refined with an
     FP64-accurate residual.  Every system reaches relative forward error <= 1e-10
