@@ -94,6 +94,25 @@ def test_ragged_65536_systems_tuned_buckets(band):
             assert np.abs(xg[lo:hi] - xo).max() / np.abs(xo).max() <= 1e-12, (sid, sched)
 
 
+def test_small_batch_64_x_65536_partitioned(band):
+    """bench.py's small batch: 64 PD systems of n = 65536 on the partitioned schedule with
+    the library's chunk count (a block of warps per system).  Every system against its
+    manufactured solution, and 4 of them against the oracle."""
+    B = synth.cfg0(nsys=64, n=65536, seed_salt=80)
+    T = to_dev(B)
+    x, st = band.solve(*(T[q] for q in "abcdef"), method="npdm", schedule="partitioned")
+    torch.cuda.synchronize()
+    assert (st.cpu().numpy() == 0).all()
+    n, ns = B["n"], B["nsys"]
+    xg = flat_of(x).reshape(n, ns)
+    xt = B["x_true"].reshape(n, ns)
+    assert (np.abs(xg - xt).max(0) / np.abs(xt).max(0)).max() <= 1e-12
+    for s_ in (0, 21, 42, 63):
+        col = {q: B[q].reshape(n, ns)[:, s_] for q in "abcdef"}
+        xo, _ = oracle.npdm(*(col[q] for q in "abcdef"))
+        assert np.abs(xg[:, s_] - xo).max() / np.abs(xo).max() <= 1e-12, s_
+
+
 def test_refine_16384_x_4096(band):
     """The precision workload: 16384 PD systems of n = 4096 in FP32, refined with an
     FP64-accurate residual.  Every system reaches relative forward error <= 1e-10
