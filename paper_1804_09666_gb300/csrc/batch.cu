@@ -4,10 +4,11 @@
 // (Veneva & Ayriyan, Sec. 1); the solves of one step are independent.  One 2048 x 2048
 // sweep has only 2048 systems, 64 warps for 152 SMs, while the FP64 units of a
 // GB300 SM need at least four resident warps.  Here the problems of a step share one
-// kernel: every warp takes 32 consecutive systems of one problem (thread per system,
-// the sweeps of sweeps.cuh / sip_impl.cuh), so the launch holds the warps of all of
-// them.  The problem table travels as a __grid_constant__ kernel parameter; nothing
-// is allocated.
+// kernel: every warp takes consecutive systems of one problem (32 on one thread each,
+// 16 on the two-sided schedule, 32 / P partitioned; the sweeps of sweeps.cuh,
+// partition.cuh and sip_impl.cuh), so the launch holds the warps of all of them.  The
+// problem table travels as a __grid_constant__ kernel parameter; nothing is
+// allocated.
 #include <algorithm>
 
 #ifndef BATCH_WARPS
@@ -104,7 +105,7 @@ __device__ __forceinline__ void run_partition(const DirectArgs<T>& p, int kmode,
   }
 }
 
-// One warp task: 32 systems of one problem (16 on the two-sided schedule).  Blocks are
+// One warp task: 32 systems of one problem (16 two-sided, 32 / P partitioned).  Blocks are
 // handed out by the hardware scheduler as earlier ones finish, in task order, and the
 // host orders the problems heaviest first.  (A persistent loop over a task counter was
 // tried: keeping every task variant's state live across the loop doubled the kernel's

@@ -1,5 +1,6 @@
 // runtime.cu -- host-side batch runtime: size buckets of ragged batches and the
-// measuring autotuner of the thread-per-system / two-sided choice.  See include/band.h.
+// measuring autotuner of the schedules (thread per system, two-sided, partitioned).
+// See include/band.h.
 //
 // The ADI step solves many independent systems (Veneva & Ayriyan, Sec. 1); ragged
 // batches of uneven sizes and mixed bandwidth are cut into buckets so that every
@@ -105,8 +106,11 @@ __global__ void __launch_bounds__(128) k_dominance(const Layout L, const T* a, c
   if (!ok) atomicOr(bad, 1);
 }
 
-// Is every system of the problem row diagonally dominant?  (-1: CUDA error)
-int dominant(const band_problem& q, int* flag, cudaStream_t st) {
+// Is every system of the problem row diagonally dominant?  (-1: CUDA error)  The flag
+// lives in the first bytes of the problem's own workspace, which holds nothing between
+// calls.
+int dominant(const band_problem& q, cudaStream_t st) {
+  int* flag = static_cast<int*>(q.ws);
   const band_desc* d = q.desc;
   const Layout L = layout_of(d);
   const int K = kmode_for(d, q.method);
@@ -224,7 +228,6 @@ extern "C" band_status band_autotune(const band_problem* probs, int32_t count, i
     std::vector<band_desc> descs((size_t)count);
     std::vector<band_problem> list(probs, probs + count);
     std::vector<int32_t> cand;
-    int* flag = nullptr;
     for (int32_t i = 0; i < count && out == BAND_OK; ++i) {
       descs[(size_t)i] = *probs[i].desc;
       list[(size_t)i].desc = &descs[(size_t)i];
@@ -235,16 +238,11 @@ extern "C" band_status band_autotune(const band_problem* probs, int32_t count, i
       dp.chunks = 0;
       size_t need = 0;
       carve_solve(&dp, probs[i].method, nullptr, &need);
-      if (need > probs[i].ws_bytes || dp.n < 64) continue;
-      if (!flag && cudaMalloc(&flag, sizeof(int)) != cudaSuccess) {
-        out = BAND_ERR_CUDA;
-        break;
-      }
-      const int dom = dominant(probs[i], flag, st);
+      if (need > probs[i].ws_bytes || dp.n < 64 || !probs[i].ws) continue;
+      const int dom = dominant(probs[i], st);
       if (dom < 0) out = BAND_ERR_CUDA;
       else if (dom) cand.push_back(i);
     }
-    if (flag) cudaFree(flag);
     std::stable_sort(cand.begin(), cand.end(),
                      [&](int32_t x, int32_t y) { return probs[x].desc->n > probs[y].desc->n; });
     if (!cand.empty() && !e0 &&
