@@ -370,3 +370,34 @@ def test_autotune_joint(band):
     assert (st.cpu().numpy() == 0).all()
     err = np.maximum.reduceat(np.abs(x.cpu().numpy() - B["x_true"]), B["offsets"][:-1])
     assert err.max() <= 1e-11
+
+
+def _packed(B):
+    """A uniform batch repacked as a ragged packing (system after system)."""
+    n, ns, ss, es = B["n"], B["nsys"], B["sys_stride"], B["elem_stride"]
+    idx = np.arange(ns)[:, None] * ss + np.arange(n)[None, :] * es     # [system, row]
+    packed = {q: np.ascontiguousarray(B[q][idx].reshape(-1)) for q in "abcdef"}
+    offsets = np.arange(ns + 1, dtype=np.int64) * n
+    return packed, offsets
+
+
+def test_autotune_joint_dominance_gate(band):
+    """64 systems of n = 2048 fill a twentieth of the GPU: the joint tuner moves a
+    diagonally dominant bucket to the partitioned schedule, and never a non-dominant one
+    (the ADI rows at r = 2), whose chunks may be far worse conditioned than the matrix."""
+    from paper_1804_09666_gb300 import _lib as L
+    cases = [("dominant", synth.cfg0(nsys=64, n=2048, seed_salt=76), True),
+             ("adi r=2", synth.cfg1(r=2.0, k=2, sweep="y", grid=2048, nsys=64), False)]
+    for name, B, may_partition in cases:
+        packed, offs = _packed(B)
+        d = {q: torch.from_numpy(packed[q]).to("cuda") for q in "abcdef"}
+        L.load().band_autotune_reset()
+        plan = band.RaggedPlan(*(d[q] for q in "abcdef"), offs, np.full(64, 2, np.int8),
+                               schedule="tune")
+        if may_partition:
+            assert 3 in plan.schedules, (name, plan.schedules)
+        else:
+            assert 3 not in plan.schedules, (name, plan.schedules)
+        x, st = plan.run()
+        torch.cuda.synchronize()
+        assert (st.cpu().numpy() == 0).all()
