@@ -74,6 +74,19 @@ def test_workspace_sizes(lib):
     assert lib.band_workspace_size(ct.byref(dp), L.OP_SOLVE, L.NPDM, 0) >= 5 * rows
     dt = _desc(half_bw=1, schedule=L.SCHED_PARTITIONED)
     assert lib.band_workspace_size(ct.byref(dt), L.OP_SOLVE, L.NTDM, 0) >= 4 * rows
+    # chunks = 0 leaves the library the choice: its workspace covers every chunk count
+    for nsys, n in ((64, 128), (37, 1031), (3, 5000), (1000, 40)):
+        auto = lib.band_workspace_size(ct.byref(_desc(nsys=nsys, n=n, elem_stride=nsys,
+                                                      schedule=L.SCHED_PARTITIONED)),
+                                       L.OP_SOLVE, L.NPDM, 0)
+        for P in (4, 8, 16, 32, 64, 128, 256):
+            fixed = lib.band_workspace_size(
+                ct.byref(_desc(nsys=nsys, n=n, elem_stride=nsys, schedule=L.SCHED_PARTITIONED,
+                               chunks=P)), L.OP_SOLVE, L.NPDM, 0)
+            assert 0 < fixed <= auto, (nsys, n, P, fixed, auto)
+            # ceil(n / P) * P rows for nsys rounded up to 32 / P systems, five arrays
+            np_ = nsys if P >= 32 else -(-nsys // (32 // P)) * (32 // P)
+            assert fixed >= 5 * (-(-n // P)) * P * np_ * 8
     assert lib.band_workspace_size(ct.byref(d), L.OP_SOLVE, L.SPDM, 0) > \
         lib.band_workspace_size(ct.byref(d), L.OP_SOLVE, L.NPDM, 0)
     assert lib.band_workspace_size(ct.byref(d), L.OP_FACTOR, L.NPDM, 0) >= 4 * rows

@@ -56,7 +56,7 @@ def _args(B):
 
 # n below 8 P (one lane solves the system), exactly 8 P, chunk lengths with every
 # remainder pattern, and a long case; 37 systems leave a partial warp for every P.
-@pytest.mark.parametrize("n", [5, 31, 32, 33, 64, 127, 256, 257, 300, 1000, 4099])
+@pytest.mark.parametrize("n", [5, 31, 32, 33, 64, 127, 256, 257, 300, 1000, 2048, 4099])
 @pytest.mark.parametrize("k", [1, 2])
 @pytest.mark.parametrize("P", PARTS + BLOCK_PARTS)
 def test_partition_dominant(band, n, k, P):
