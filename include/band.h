@@ -260,9 +260,11 @@ band_status band_adjoint(const band_desc* desc, int32_t method, const void* fact
  * BAND_STATIC_SCRATCH_BYTES that the library places in device memory on every GPU
  * that loads it, held until the process exits.  The first call on a device looks up
  * that array's device address (once per device, with that device current); make
- * that first call before any stream capture.  A batch whose scratch (2 arrays of
- * nsys rounded up to 32, times n, times the element size; ragged: total_rows) does
- * not fit returns BAND_ERR_WORKSPACE; other methods return BAND_ERR_ARG.  The array
+ * that first call before any stream capture.  desc->schedule applies as for
+ * band_solve.  A batch whose workspace (band_workspace_size(desc, BAND_OP_SOLVE,
+ * method, 0): 2 arrays of nsys rounded up to 32, times n, times the element size, for
+ * the thread and two-sided schedules) exceeds the array returns BAND_ERR_WORKSPACE;
+ * other methods return BAND_ERR_ARG.  The array
  * is shared by every call and keeps the last call's contents (nothing in it needs to
  * start at zero): calls whose kernels overlap on one GPU race on it and must be
  * serialised by the caller.  No device memory is allocated. */

@@ -4,9 +4,10 @@
 // runs where cudaMalloc would synchronise the whole device (a latency-critical loop
 // between kernel launches), hosts that hand every byte of device memory to their own
 // pool and forbid other allocations, or plain C callers with no allocator at all.
-// For them this entry point takes its scratch rows (alpha and beta of the sweep) from
-// a fixed array in device memory that the library owns: kStaticScratchBytes per GPU,
-// held from the first use of the library on that GPU until the process exits.
+// For them this entry point runs band_solve's own path (every schedule) with its
+// workspace in a fixed array in device memory that the library owns:
+// kStaticScratchBytes per GPU, held from the first use of the library on that GPU
+// until the process exits.
 //
 // Every call shares the array and it keeps whatever the last call wrote: calls whose
 // kernels overlap on a GPU (different streams, or different host threads) race on
@@ -57,31 +58,29 @@ extern "C" band_status band_solve_static(const band_desc* desc, int32_t method,
     return BAND_ERR_ARG;
   const int kmode = kmode_for(desc, method);
   if (kmode < 0) return BAND_ERR_ARG;
-  const size_t esz = dtype_size(desc->dtype);
-  const size_t rows = (size_t)spill_rows(desc);
-  const size_t arr = (rows * esz + 255) & ~size_t(255);
-  if (2 * arr > kStaticScratchBytes) return BAND_ERR_WORKSPACE;   // batch too large
+  size_t need = 0;
+  carve_solve(desc, method, nullptr, &need);     // band_solve's workspace for this desc
+  if (need > kStaticScratchBytes) return BAND_ERR_WORKSPACE;   // batch too large
   if (desc->nsys == 0) return BAND_OK;
   if (!diag || !f || !x || !diag[1] || !diag[2] || !diag[3]) return BAND_ERR_ARG;
   if (may_be_pd(desc) && kmode != 1 && (!diag[0] || !diag[4])) return BAND_ERR_ARG;
   void* base = nullptr;
   if (scratch_on_current_device(&base) != cudaSuccess) return BAND_ERR_CUDA;
-  char* al = static_cast<char*>(base);
-  char* be = al + arr;
+  // from here on band_solve's own path, with the static array as its workspace
+  DirectReq r;
+  const band_status v =
+      make_direct(desc, method, diag, f, x, sys_status, base, kStaticScratchBytes, &r, 256);
+  if (v != BAND_OK) return v;
   cudaStream_t st = static_cast<cudaStream_t>(stream);
-  const Layout L = layout_of(desc);
-  const Spill W = spill_of(desc);
-  if (desc->dtype == BAND_F64) {
-    DirectArgs<double> p{L, W,
-                         (const double*)diag[0], (const double*)diag[1], (const double*)diag[2],
-                         (const double*)diag[3], (const double*)diag[4], (const double*)f,
-                         (double*)x, (double*)al, (double*)be, nullptr, sys_status, nullptr,
-                         nullptr};
-    return cuda_status(launch_direct<double>(p, kmode, st));
-  }
-  DirectArgs<float> p{L, W,
-                      (const float*)diag[0], (const float*)diag[1], (const float*)diag[2],
-                      (const float*)diag[3], (const float*)diag[4], (const float*)f, (float*)x,
-                      (float*)al, (float*)be, nullptr, sys_status, nullptr, nullptr};
-  return cuda_status(launch_direct<float>(p, kmode, st));
+  cudaError_t e;
+  if (r.parts)
+    e = desc->dtype == BAND_F64 ? launch_partition<double>(r.d64, r.kmode, r.parts, st)
+                                : launch_partition<float>(r.d32, r.kmode, r.parts, st);
+  else if (r.two_sided)
+    e = desc->dtype == BAND_F64 ? launch_twisted<double>(r.d64, r.kmode, st)
+                                : launch_twisted<float>(r.d32, r.kmode, st);
+  else
+    e = desc->dtype == BAND_F64 ? launch_direct<double>(r.d64, r.kmode, st)
+                                : launch_direct<float>(r.d32, r.kmode, st);
+  return cuda_status(e);
 }

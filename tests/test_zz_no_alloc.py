@@ -40,11 +40,12 @@ def _batch(k, nsys, n, salt):
     return {q: torch.from_numpy(B[q]).to(dev) for q in "abcdef"}
 
 
-def _call(lib, fn, k, nsys, n, T, dtype):
+def _call(lib, fn, k, nsys, n, T, dtype, schedule=0, chunks=0):
     from paper_1804_09666_gb300 import _lib as L
     T = {q: v.to(dtype) for q, v in T.items()}
     desc = L.BandDesc(half_bw=k, dtype=L.F64 if dtype == torch.float64 else L.F32, nsys=nsys, n=n,
-                      sys_stride=1, elem_stride=nsys, offsets=None, hbw=None, total_rows=0)
+                      sys_stride=1, elem_stride=nsys, offsets=None, hbw=None, total_rows=0,
+                      schedule=schedule, chunks=chunks)
     x = torch.empty_like(T["f"])
     st = torch.full((nsys,), -1, dtype=torch.int32, device=x.device)
     diag = L.DIAG5(*[T[q].data_ptr() if (k == 2 or q in "bcd") else None for q in "abcde"])
@@ -65,15 +66,15 @@ def _call(lib, fn, k, nsys, n, T, dtype):
 
 @pytest.mark.parametrize("k", [2, 1])
 @pytest.mark.parametrize("dtype", [torch.float64, torch.float32])
-def test_static_scratch_matches_band_solve_twice(lib, k, dtype):
-    tol = 1e-12 if dtype == torch.float64 else 1e-5
+@pytest.mark.parametrize("schedule,chunks", [(0, 0), (1, 0), (2, 0), (3, 8), (3, 64)])
+def test_static_scratch_matches_band_solve_twice(lib, k, dtype, schedule, chunks):
+    """The same kernels as band_solve on every schedule: bitwise equal results."""
     for salt, (nsys, n) in enumerate(((1000, 300), (2048, 129))):
         T = _batch(k, nsys, n, salt + 40)
-        xs, sts = _call(lib, "static", k, nsys, n, T, dtype)
-        xw, stw = _call(lib, "ws", k, nsys, n, T, dtype)
+        xs, sts = _call(lib, "static", k, nsys, n, T, dtype, schedule, chunks)
+        xw, stw = _call(lib, "ws", k, nsys, n, T, dtype, schedule, chunks)
         assert (sts == 0).all() and (stw == 0).all()
-        err = ((xs - xw).abs().amax() / xw.abs().amax()).item()
-        assert err <= tol
+        assert torch.equal(xs, xw)
 
 
 def test_static_scratch_rejects_oversized_batches(lib):
