@@ -202,8 +202,10 @@ band_status band_sip(const band_desc* desc, const void* const diag[5], const voi
 
 /* One batched launch over several independent problems (at most BAND_MAX_BATCH).
  * The ADI step solves N systems per grid line and direction (Sec. 1); its solves are
- * independent, so they share one kernel launch in which every warp takes 32 systems
- * of one problem, filling the GPU even when each problem alone has too few systems.
+ * independent, so they share one kernel launch in which every warp takes consecutive
+ * systems of one problem (32 on one thread each, 16 two-sided, 32 / P partitioned with
+ * P <= 32; a larger desc->chunks runs as P = 32), filling the GPU even when each problem
+ * alone has too few systems.
  * op = BAND_OP_SOLVE: method as for band_solve (fused, no stored factors; STDM/SPDM
  *   systems with a zero pivot go through one batched symbolic fix-up launch).
  * op = BAND_OP_SIP: Algorithm 1 with exact substitutions (width 0) on FP64 PD
@@ -234,7 +236,8 @@ band_status band_solve_batch(const band_problem* problems, int32_t count, void* 
  * diag32), right-hand side and solution in FP64 with the same strides.  FP32 NPDM/NTDM
  * solve, then refinement steps r = f - A x (FP64, A = the FP64 values of the FP32
  * diagonals), delta = s * solve32(r / s) with s = max|r|, x += delta (FP64), until
- * max|delta| <= rel_stop * max|x| or max_steps steps.  steps (int32[nsys]) may be NULL. */
+ * max|delta| <= rel_stop * max|x| or max_steps steps.  steps (int32[nsys]) may be NULL.
+ * The FP32 solves run on desc32->schedule (and chunks) as band_solve's would. */
 band_status band_refine_solve(const band_desc* desc32, const void* const diag32[5],
                               const double* f, double* x, double rel_stop, int32_t max_steps,
                               int32_t* steps, int32_t* sys_status, void* ws, size_t ws_bytes,
@@ -245,7 +248,11 @@ band_status band_refine_solve(const band_desc* desc32, const void* const diag32[
  * grad_f = lambda, grad_a[i] = -lambda_i x_{i-2}, grad_b[i] = -lambda_i x_{i-1},
  * grad_c[i] = -lambda_i x_i, grad_d[i] = -lambda_i x_{i+1}, grad_e[i] = -lambda_i x_{i+2}
  * (out-of-matrix slots receive 0; TD: grad_a, grad_e may be NULL).  factors: NULL to
- * refactor from diag, or band_factor()'s buffer. */
+ * refactor from diag, or band_factor()'s buffer.  Without factors on a uniform layout,
+ * A^T (row-aligned diagonals e_{i-2}, d_{i-1}, c_i, b_{i+1}, a_{i+2}) is formed in the
+ * workspace and solved as a band system on desc->schedule (as band_solve; the same
+ * lambda in exact arithmetic, with ZERO_PIVOT referring to A^T's elimination order);
+ * with factors, or on a ragged layout, by the transposed sweeps of the LU factors. */
 band_status band_adjoint(const band_desc* desc, int32_t method, const void* factors,
                          const void* const diag[5], const void* x, const void* w,
                          void* const grad_diag[5], void* grad_f, int32_t* sys_status,

@@ -173,10 +173,12 @@ def sip(a, b, c, d, e, f, tol=1e-10, max_it=200, width=5, hb_max_it=30, hb_tol=1
     return x, iters, resid, status
 
 
-def refine_solve(a32, b32, c32, d32, e32, f, rel_stop=1e-11, max_steps=10, x=None):
-    """FP32 solve + FP64 refinement; f, x float64 with the diagonals' strides."""
+def refine_solve(a32, b32, c32, d32, e32, f, rel_stop=1e-11, max_steps=10, x=None,
+                 schedule="auto", chunks=0):
+    """FP32 solve + FP64 refinement; f, x float64 with the diagonals' strides.  The FP32
+    solves run on `schedule` / `chunks` as in ``solve``."""
     lib = L.load()
-    desc = desc_for(c32, 2 if a32 is not None else 1)
+    desc = desc_for(c32, 2 if a32 is not None else 1, schedule, chunks)
     if f.shape != c32.shape or f.stride() != c32.stride() or f.dtype != torch.float64:
         raise ValueError("f must be float64 with the diagonals' shape and strides")
     if x is None:
@@ -193,12 +195,13 @@ def refine_solve(a32, b32, c32, d32, e32, f, rel_stop=1e-11, max_steps=10, x=Non
     return x, steps, status
 
 
-def adjoint(a, b, c, d, e, x, w, factors=None, method="npdm"):
-    """Gradients (ga, gb, gc, gd, ge), gf of sum(w * x) with x = A^{-1} f."""
+def adjoint(a, b, c, d, e, x, w, factors=None, method="npdm", schedule="auto", chunks=0):
+    """Gradients (ga, gb, gc, gd, ge), gf of sum(w * x) with x = A^{-1} f.  Without
+    factors the transposed system is solved on `schedule` / `chunks` as in ``solve``."""
     lib = L.load()
     m = _METHODS[method]
     half_bw = 1 if method == "ntdm" else 2
-    desc = desc_for(c, half_bw)
+    desc = desc_for(c, half_bw, schedule, chunks)
     mk = lambda: torch.empty_strided(c.shape, c.stride(), dtype=c.dtype, device=c.device)
     grads = [mk() if (half_bw == 2 or k in (1, 2, 3)) else None for k in range(5)]
     gf = mk()
