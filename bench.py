@@ -612,12 +612,17 @@ def adjoint_workload(dev):
     d = {q: torch.from_numpy(B[q]).to(dev).view(n, nsys) for q in "abcdefw"}
     units = n * nsys
 
-    def step():
-        x, _ = band.solve(*(d[q] for q in "abcdef"), method="npdm")
-        band.adjoint(*(d[q] for q in "abcde"), x, d["w"])
-    ms = _time(step)
-    return {"workload": "4096 PD systems, n = 1024: solve + adjoint", "value": units / (ms * 1e-3),
-            "unit": UNIT, "ms": ms}
+    out = {"workload": "4096 PD systems, n = 1024: solve + adjoint", "unit": UNIT}
+    for sched in ("auto", "partitioned"):
+        def step():
+            x, _ = band.solve(*(d[q] for q in "abcdef"), method="npdm", schedule=sched)
+            band.adjoint(*(d[q] for q in "abcde"), x, d["w"], schedule=sched)
+        ms = _time(step)
+        if sched == "auto":
+            out.update(value=units / (ms * 1e-3), ms=ms)
+        else:       # these systems are dominant: the partitioned solves keep NPDM's accuracy
+            out["partitioned"] = {"value": units / (ms * 1e-3), "ms": ms}
+    return out
 
 
 EXTRA_WORKLOADS = {"ragged": "ragged_workload", "small_batch": "small_batch_workload",
