@@ -229,10 +229,13 @@ class BatchPlan:
       chunks             lanes per system on the partitioned schedule (0: the library's)
     Outputs, statuses and workspaces are allocated once here; ``run()`` only launches,
     so a run can be captured in a CUDA graph.  results[i] holds x, status (and iters,
-    resid for "sip").
+    resid for "sip").  tune: band_autotune picks thread or two-sided for every "solve"
+    spec left on "auto", then moves diagonally dominant problems to the partitioned
+    schedule while that shortens the whole launch (BAND_TUNE_JOINT); the trial runs
+    overwrite the outputs.  ``schedules`` / ``chunks`` hold the schedules in use.
     """
 
-    def __init__(self, specs):
+    def __init__(self, specs, tune=False, reps=3):
         lib = L.load()
         if len(specs) > L.MAX_BATCH:
             raise ValueError("at most %d problems per batch" % L.MAX_BATCH)
@@ -258,6 +261,10 @@ class BatchPlan:
                 x = torch.empty_strided(c.shape, c.stride(), dtype=c.dtype, device=c.device)
             status = torch.empty(c.shape[1], dtype=torch.int32, device=c.device)
             need = lib.band_workspace_size(ct.byref(desc), opc, m, 0)
+            if tune and op == "solve" and desc.schedule == L.SCHED_AUTO:
+                dp = L.BandDesc.from_buffer_copy(desc)      # room for the partitioned schedule
+                dp.schedule, dp.chunks = L.SCHED_PARTITIONED, 0
+                need = max(need, lib.band_workspace_size(ct.byref(dp), opc, m, 0))
             ws = _workspace(need, c.device)
             res = dict(x=x, status=status)
             P = self.arr[i]
@@ -275,6 +282,16 @@ class BatchPlan:
             self.keep.append((desc, a, b, c, d, e, f, ws))
             self.results.append(res)
         self.count = len(specs)
+        self.descs = [k[0] for k in self.keep]
+        if tune and self.count > 0:
+            out = (ct.c_int32 * self.count)()
+            outc = (ct.c_int32 * self.count)()
+            code = lib.band_autotune(self.arr, self.count, reps, L.TUNE_JOINT, out, outc, _stream())
+            L.check(code, "band_autotune")
+            for desc, v, pc in zip(self.descs, out, outc):
+                desc.schedule, desc.chunks = v, pc
+        self.schedules = [d.schedule for d in self.descs]
+        self.chunks = [d.chunks for d in self.descs]
 
     def run(self):
         code = self.lib.band_solve_batch(self.arr, self.count, _stream())

@@ -439,3 +439,28 @@ def test_refine_and_adjoint_on_the_partitioned_schedule(band, chunks):
                                   C["w"].reshape(n, nsys)[:, 3])
     assert sto == "OK"
     assert np.abs(gf_par.cpu().numpy()[:, 3] - gfo).max() / np.abs(gfo).max() <= 1e-11
+
+
+def test_batchplan_tune(band):
+    """BatchPlan(tune=True): the joint tuner partitions the dominant problem whose few
+    long systems bound the launch, keeps the non-dominant ADI problem off the
+    partitioned schedule, and the tuned plan solves both (GEPP-bounded for the ADI
+    rows)."""
+    D = synth.cfg0(nsys=64, n=8192, seed_salt=78)
+    A = synth.cfg1(r=2.0, k=2, sweep="x", grid=2048, nsys=256)
+    TD, TA = to_dev(D), to_dev(A)
+    specs = [dict(method="npdm", **{q: TD[q] for q in "abcdef"}),
+             dict(method="npdm", **{q: TA[q] for q in "abcdef"})]
+    plan = band.BatchPlan(specs, tune=True)
+    assert plan.schedules[0] == 3 and plan.chunks[0] in (4, 8, 16, 32), plan.schedules
+    assert plan.schedules[1] in (1, 2), plan.schedules
+    res = plan.run()
+    torch.cuda.synchronize()
+    for r in res:
+        assert (r["status"].cpu().numpy() == 0).all()
+    xo, _, _, _ = _oracle(D, 2)
+    assert per_system_rel(flat_of(res[0]["x"]), xo, *_args(D)).max() <= 1e-12
+    xo, _, _, _ = _oracle(A, 2)
+    xt, _, _, _ = _oracle(A, 2, "gepp")
+    bound = np.maximum(1e-10, 10 * per_system_rel(xo, xt, *_args(A)))
+    assert (per_system_rel(flat_of(res[1]["x"]), xt, *_args(A)) <= bound).all()
