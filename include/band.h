@@ -86,9 +86,9 @@ typedef struct {
   const int8_t* hbw;      /* device array of per-system half bandwidths (1 or 2), or NULL */
   int64_t total_rows;     /* ragged: offsets[nsys] (the host's copy); uniform: ignored */
   int32_t schedule;       /* band_schedule for NTDM/NPDM solves (BAND_SCHED_AUTO = 0) */
-  int32_t chunks;         /* BAND_SCHED_PARTITIONED: lanes (row chunks) per system, 4, 8,
-                             16, 32 (lanes of a warp) or 64, 128, 256 (a block of 2, 4, 8
-                             warps per system); 0 = chosen from nsys and n.  Otherwise 0. */
+  int32_t chunks;         /* BAND_SCHED_PARTITIONED: lanes (row chunks) per system, 8, 16,
+                             32 (lanes of a warp) or 64, 128, 256 (a block of 2, 4, 8 warps
+                             per system); 0 = chosen from nsys and n.  Otherwise 0. */
   /* Ragged batches only, else NULL: device array of nsys system ids.  The batch is then
    * the systems ids[0 .. nsys-1] of the packing that offsets (and hbw) describe, and
    * every per-system output (sys_status, iters, resid) is indexed by the id.  A solve
@@ -134,10 +134,13 @@ typedef struct {
  *   for the batch; any layout, ragged packings included.  Workspace: five (PD) / four
  *   (TD) scratch arrays of ceil(n / P) * P rows for nsys rounded up to 32 / P systems
  *   (the largest over P when chunks is 0).
- *   Accuracy: on diagonally dominant matrices that of NPDM; on others a chunk's block
- *   can be much closer to singular than the matrix, and the error then grows with the
- *   worst chunk's condition number (measured on indefinite PD ADI rows, r = 2:
- *   relative errors up to 8e-10 where NPDM reaches 1.3e-12).
+ *   Accuracy: a chunk restarts NPDM's recurrence at its first row and the interface has
+ *   no pivoting across blocks, so on matrices that are not diagonally dominant either
+ *   can meet pivots far smaller than NPDM's; a pivot 2^-17 (FP64) / 2^-10 (FP32) below
+ *   its row's largest entry, or an interface block as close to singular, is handled
+ *   like a zero pivot (the system is redone as above).  On dominant matrices no system
+ *   is redone.  (With 4 chunks the two-ended interface still met an unguarded
+ *   instability on indefinite rows, so P starts at 8.)
  * BAND_SCHED_AUTO: TWO_SIDED for uniform-bandwidth solves with n >= 32 that are not a
  *   whole ragged packing (ragged id lists, i.e. size buckets, qualify) and, for
  *   NTDM/NPDM, whose x does not alias f; THREAD otherwise.  band_autotune replaces the
@@ -311,7 +314,7 @@ int32_t band_plan_ragged(const int64_t* offsets, const int8_t* hbw, int32_t half
  *    f), so later calls reuse them without timing.
  * 2. With flags & BAND_TUNE_JOINT: the whole list is timed as one launch, and the
  *    problems (n >= 64, largest n first) are moved in turn to BAND_SCHED_PARTITIONED
- *    with 4, 8, 16 or 32 chunks (those that leave chunks of 16 rows or more); a move is
+ *    with 8, 16 or 32 chunks (those that leave chunks of 16 rows or more); a move is
  *    kept when it shortens the launch by 2 % or more, and the search ends after two
  *    problems in a row gain nothing.  Only problems whose ws_bytes cover the partitioned
  *    schedule's workspace (band_workspace_size with schedule BAND_SCHED_PARTITIONED)

@@ -82,8 +82,8 @@ def solve(a, b, c, d, e, f, method="npdm", x=None, status=None, factors=None, ws
     method: "npdm", "ntdm", "spdm", "stdm".  a, e are ignored (may be None) for TD.
     factors: a buffer from ``factor`` to reuse a factorisation (numeric methods).
     schedule: "auto", "thread" (one thread per system), "two_sided" (two threads per
-    system meeting in the middle) or "partitioned" (``chunks`` lanes per system, 4, 8,
-    16 or 32, 0 = chosen by the library); the last two without factors.
+    system meeting in the middle) or "partitioned" (``chunks`` lanes per system, 8, 16,
+    32, 64, 128 or 256, 0 = chosen by the library); the last two without factors.
     """
     lib = L.load()
     m = _METHODS[method]

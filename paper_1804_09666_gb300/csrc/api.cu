@@ -88,7 +88,7 @@ int64_t part_np(int64_t nsys, int parts) { return parts >= 32 ? nsys : round_up(
 // part_np systems; desc->chunks == 0 takes the largest over the chunk counts.
 int64_t part_rows_bound(const band_desc* d) {
   int64_t best = 0;
-  for (int P = 4; P <= 256; P *= 2) {
+  for (int P = 8; P <= 256; P *= 2) {
     if (d->chunks && P != d->chunks) continue;
     const int64_t r = (d->n + P - 1) / P * P * part_np(d->nsys, P);
     if (r > best) best = r;
@@ -97,7 +97,7 @@ int64_t part_rows_bound(const band_desc* d) {
 }
 
 // Lanes per system on the partitioned schedule (0: another schedule).  chunks == 0: the
-// P in {4, 8, .., max_parts} (chunks of 8 rows or more) with the least estimated time
+// P in {8, 16, .., max_parts} (chunks of 8 rows or more) with the least estimated time
 //   warps(P) * (n / P * c_row + (P / 2 + 2) * c_if) / min(1, warps(P) / (8 warps x SMs)),
 // warps(P) = nsys * P / 32: the FP64 instructions of the launch (a chunk row costs
 // c_row = 32 (PD) / 14 (TD); the interface, eliminated from both ends, c_if = 60 / 25
@@ -122,10 +122,10 @@ int choose_parts(const band_desc* d, int max_parts) {
   const bool td = d->hbw == nullptr && d->half_bw == 1;
   const double c_row = td ? 14.0 : 32.0, c_if = td ? 25.0 : 60.0;
   const double sat = 8.0 * nsm;
-  int best = 4;
+  int best = 8;
   double best_t = -1.0;
-  for (int P = 4; P <= max_parts; P *= 2) {
-    if (P > 4 && d->n < (int64_t)8 * P) break;
+  for (int P = 8; P <= max_parts; P *= 2) {
+    if (P > 8 && d->n < (int64_t)8 * P) break;
     const double warps = (double)d->nsys * P / 32.0;
     const double eff = warps < sat ? warps / sat : 1.0;
     const double t =

@@ -90,14 +90,12 @@ __device__ __forceinline__ void run_partition(const DirectArgs<T>& p, int kmode,
   T* st = static_cast<T*>(stage);    // the warp's staging area (stage_bytes_per_warp<T>)
   if (kmode == 1) {
     switch (parts) {
-      case 4: partition_one<T, 1, 4, kBatchPartRows>(p, warp, st); break;
       case 8: partition_one<T, 1, 8, kBatchPartRows>(p, warp, st); break;
       case 16: partition_one<T, 1, 16, kBatchPartRows>(p, warp, st); break;
       default: partition_one<T, 1, 32, kBatchPartRows>(p, warp, st); break;
     }
   } else {
     switch (parts) {
-      case 4: partition_one<T, 2, 4, kBatchPartRows>(p, warp, st); break;
       case 8: partition_one<T, 2, 8, kBatchPartRows>(p, warp, st); break;
       case 16: partition_one<T, 2, 16, kBatchPartRows>(p, warp, st); break;
       default: partition_one<T, 2, 32, kBatchPartRows>(p, warp, st); break;

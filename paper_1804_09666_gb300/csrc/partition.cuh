@@ -1,7 +1,6 @@
 // partition.cuh -- the partitioned schedule: P lanes per system, lane k eliminating
-// chunk k of P consecutive row blocks of its system.  P = 4, 8, 16 or 32 lanes of a
-// warp (32 / P systems per warp), or P = 64, 128 or 256: a block of P / 32 warps per
-// system.
+// chunk k of P consecutive row blocks of its system.  P = 8, 16 or 32 lanes of a warp
+// (32 / P systems per warp), or P = 64, 128 or 256: a block of P / 32 warps per system.
 //
 // Chunk k (rows s0 .. s0+L-1, block A_k of the matrix) couples to the K unknowns just
 // above it, u_k = (x_{s0-K} .. x_{s0-1}), through the a, b entries of its first rows
@@ -27,10 +26,10 @@
 // the lanes of a warp touch consecutive elements.  z of f goes to the zs rows, so f
 // stays intact (also when x aliases f) for a redo or the symbolic fix-up.
 //
-// A chunk may meet a zero pivot where NPDM's order does not, and the interface
-// elimination may meet a singular block: an STDM / SPDM system then goes to the symbolic
-// fix-up, and an NTDM / NPDM system is redone by its first lane with NPDM alone (so
-// BAND_ERR_ZERO_PIVOT keeps its meaning).  Systems with fewer than 8 P rows are solved by
+// A chunk may meet a zero (or, see TinyPivot, a tiny) pivot where NPDM's order does
+// not, and the interface elimination may meet a singular block: an STDM / SPDM system
+// then goes to the symbolic fix-up, and an NTDM / NPDM system is redone by its first
+// lane with NPDM alone (so BAND_ERR_ZERO_PIVOT keeps its meaning).  Systems with fewer than 8 P rows are solved by
 // their first lane with NPDM.
 #pragma once
 #include "common.cuh"
@@ -40,6 +39,41 @@
 namespace band {
 
 constexpr int kPartMinRowsPerChunk = 8;
+
+// Pivot guard.  A chunk restarts the recurrence at its first row, so on matrices that
+// are not diagonally dominant it can meet pivots far smaller than NPDM's on the whole
+// system; the multipliers then grow and the chunk's solution loses accuracy.  (On the
+// indefinite PD ADI rows at r = 2, a plain FP64 emulation shows the error tracking the
+// smallest chunk pivot: 5e-10 at a pivot 1.3e-7 times its row's largest entry, 1e-11 at
+// 5e-6, NPDM's own 1e-12 above 1e-5, with every chunk block's condition number ~2.6e3.)
+// A pivot whose binary exponent lies TinyPivot<T> or more below that of its row's
+// largest entry is handled like a zero pivot: the system is redone by NPDM in one lane
+// (or by the symbolic fix-up).  Exponents are compared with integer operations.
+template <typename T> struct TinyPivot;
+template <> struct TinyPivot<double> { static constexpr int value = 17; };   // < ~7.6e-6
+template <> struct TinyPivot<float> { static constexpr int value = 10; };    // < ~9.8e-4
+__device__ __forceinline__ int expo_of(double v) {
+  return (int)(((unsigned)__double2hiint(v) >> 20) & 0x7ffu);
+}
+__device__ __forceinline__ int expo_of(float v) { return (int)((__float_as_uint(v) >> 23) & 0xffu); }
+
+// The same guard for the interface's K x K pivot blocks: A (= I - X) counts as singular
+// when |det A| lies TinyPivot<T> binary orders per row below max(1, max |A_ij|)^K.  The
+// block elimination has no pivoting across blocks, so on indefinite matrices it can
+// meet such a block where the whole interface system is regular.
+template <typename T, int K>
+__device__ __forceinline__ bool near_singular(const T (&A)[K][K]) {
+  const int one = expo_of(T(1));
+  int s = one;
+#pragma unroll
+  for (int r = 0; r < K; ++r)
+#pragma unroll
+    for (int c = 0; c < K; ++c) s = max(s, expo_of(A[r][c]));
+  const T det = K == 1 ? A[0][0] : fma(A[0][0], A[K - 1][K - 1], -A[0][K - 1] * A[K - 1][0]);
+  if (is_zero(det)) return true;
+  // exponents: det ~ 2^(e - one), scale^K ~ 2^(K (s - one))
+  return (expo_of(det) - one) + K * TinyPivot<T>::value <= K * (s - one);
+}
 
 // Values of T per lane in the interface exchange: y's right-hand side (2K) and the
 // 2K rows of V's and W's K columns.
@@ -222,7 +256,7 @@ __device__ __forceinline__ bool part_eliminate(T* xch, bool up) {
 #pragma unroll
       for (int c = 0; c <= K; ++c) Rt[r][c] = R[r][c];
     }
-    if (!block_solve<T, K, K + 1>(A, Rt)) return false;
+    if (near_singular<T, K>(A) || !block_solve<T, K, K + 1>(A, Rt)) return false;
 #pragma unroll
     for (int c = 0; c <= K; ++c) {
 #pragma unroll
@@ -269,6 +303,19 @@ __device__ __forceinline__ bool part_meet(T* xch) {
     }
     M[r][NB] = a[K + r];
     M[K + r][NB] = b[r];
+  }
+  {   // the meeting system is singular exactly when I - Cp'_top Cp_bottom is
+    T S[K][K];
+#pragma unroll
+    for (int r = 0; r < K; ++r)
+#pragma unroll
+      for (int c = 0; c < K; ++c) {
+        T v = r == c ? T(1) : T(0);
+#pragma unroll
+        for (int q = 0; q < K; ++q) v = fma(-M[K + r][q], M[q][K + c], v);
+        S[r][c] = v;
+      }
+    if (near_singular<T, K>(S)) return false;
   }
   if (!solve_small<T, NB>(M)) return false;
   T u[K], v[K];
@@ -396,7 +443,12 @@ __device__ __forceinline__ void partition_sys(const DirectArgs<T>& p, int64_t t,
         g = bb;
         m = fma(-al1, g, cc);
       }
-      if (is_zero(m)) { zero = true; break; }
+      {
+        int ex = expo_of(cc);
+        ex = max(ex, max(expo_of(bg), expo_of(dg)));
+        if (K == 2) ex = max(ex, max(expo_of(ag), expo_of(eg)));
+        if (is_zero(m) || expo_of(m) + TinyPivot<T>::value <= ex) { zero = true; break; }
+      }
       const T rc = rcp<T>(m);
       const T alv = (K == 2 ? fma(-be1, g, dd) : dd) * rc;
       const int64_t w = part_idx<P>(j, t, np, k);

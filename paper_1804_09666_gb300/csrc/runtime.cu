@@ -257,7 +257,7 @@ extern "C" band_status band_autotune(const band_problem* probs, int32_t count, i
       const band_desc keep = d;
       int best_p = 0;
       float best_t = base * (1.f - kJointGain);
-      for (int P = 4; P <= 32 && out == BAND_OK; P *= 2) {
+      for (int P = 8; P <= 32 && out == BAND_OK; P *= 2) {
         if (d.n < (int64_t)16 * P) break;
         d.schedule = BAND_SCHED_PARTITIONED;
         d.chunks = P;
