@@ -574,11 +574,14 @@ __device__ __forceinline__ void partition_sys(const DirectArgs<T>& p, int64_t t,
   // system, then each back-substitutes its half
   const bool ilane = mode == 2 && (k == 0 || k == P - 1);
   bool ifail = false;
+  // (every lane of the warp or block must reach grp.any: no short-circuit around it)
   if (ilane && !fail) ifail = !part_eliminate<T, K, P>(xch, k != 0);
-  fail = fail || grp.any(ifail);
+  const bool elim_fail = grp.any(ifail);
+  fail = fail || elim_fail;
   grp.sync();
   if (mode == 2 && k == 0 && !fail) ifail = !part_meet<T, K, P>(xch);
-  fail = fail || grp.any(ifail);
+  const bool meet_fail = grp.any(ifail);
+  fail = fail || meet_fail;
   grp.sync();
   if (ilane && !fail) part_backsub<T, K, P>(xch, k != 0);
   grp.sync();
