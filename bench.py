@@ -413,8 +413,8 @@ def run_reference(args, world, rank):
     print(json.dumps(line), flush=True)
 
 
-# Sources that k_batch is compiled from: an ncu traffic figure applies only while they
-# are unchanged since the capture that measured it.
+# Sources that k_batch is compiled from: an ncu traffic figure applies only while their
+# code is unchanged since the capture that measured it (comments and layout are not code).
 K_BATCH_SOURCES = ("include/band.h", "paper_1804_09666_gb300/csrc/batch.cu",
                    "paper_1804_09666_gb300/csrc/api_util.h", "paper_1804_09666_gb300/csrc/kernels.h",
                    "paper_1804_09666_gb300/csrc/common.cuh", "paper_1804_09666_gb300/csrc/sweeps.cuh",
@@ -423,12 +423,61 @@ K_BATCH_SOURCES = ("include/band.h", "paper_1804_09666_gb300/csrc/batch.cu",
 TRAFFIC_RECORD = os.path.join(ROOT, "profiles", "k_batch_adi2048_dram.md")
 
 
-def sources_sha256(paths=K_BATCH_SOURCES):
+def code_text(src):
+    """C / C++ / CUDA source without its comments, blank lines and runs of white space:
+    what the compiler sees up to layout.  Quotes inside comments are ignored; string and
+    character literals are kept whole (with their escapes)."""
+    out, i, n, state, quote = [], 0, len(src), "code", ""
+    while i < n:
+        ch = src[i]
+        if state == "code":
+            if src.startswith("//", i):
+                state, i = "line", i + 2
+            elif src.startswith("/*", i):
+                state, i = "block", i + 2
+                out.append(" ")
+            else:
+                if ch in "\"'":
+                    state, quote = "literal", ch
+                out.append(ch)
+                i += 1
+        elif state == "line":
+            if ch == "\n":
+                state = "code"
+                out.append(ch)
+            i += 1
+        elif state == "block":
+            if src.startswith("*/", i):
+                state, i = "code", i + 2
+            else:
+                if ch == "\n":
+                    out.append(ch)
+                i += 1
+        else:                                   # inside a string or character literal
+            out.append(ch)
+            if ch == "\\" and i + 1 < n:
+                out.append(src[i + 1])
+                i += 2
+                continue
+            if ch == quote or ch == "\n":
+                state = "code"
+            i += 1
+    lines = (" ".join(line.split()) for line in "".join(out).split("\n"))
+    return "\n".join(line for line in lines if line)
+
+
+def sources_sha256(paths=K_BATCH_SOURCES, read=None):
+    """SHA-256 over the code (code_text) of the given files, in order, each followed by
+    a NUL byte.  read(rel) -> source text; the working tree's files by default."""
     import hashlib
+    if read is None:
+        def read(rel):
+            with open(os.path.join(ROOT, rel), encoding="utf-8") as fh:
+                return fh.read()
     h = hashlib.sha256()
     for rel in paths:
-        with open(os.path.join(ROOT, rel), "rb") as fh:
-            h.update(fh.read())
+        h.update(code_text(read(rel)).encode("utf-8"))
+        h.update(b"\0")
     return h.hexdigest()
 
 
@@ -440,7 +489,7 @@ def recorded_traffic(grid):
         return None
     text = open(TRAFFIC_RECORD).read()
     mb = re.search(r"traffic_bytes_per_launch:\s*(\d+)", text)
-    mh = re.search(r"sources_sha256:\s*([0-9a-f]{64})", text)
+    mh = re.search(r"code_sha256:\s*([0-9a-f]{64})", text)
     if not mb or not mh or mh.group(1) != sources_sha256():
         return None
     return int(mb.group(1))

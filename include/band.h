@@ -139,8 +139,7 @@ typedef struct {
  *   can meet pivots far smaller than NPDM's; a pivot 2^-17 (FP64) / 2^-10 (FP32) below
  *   its row's largest entry, or an interface block as close to singular, is handled
  *   like a zero pivot (the system is redone as above).  On dominant matrices no system
- *   is redone.  (With 4 chunks the two-ended interface still met an unguarded
- *   instability on indefinite rows, so P starts at 8.)
+ *   is redone.  Chunk counts are 8 ... 256 (4 is not offered).
  * BAND_SCHED_AUTO: TWO_SIDED for uniform-bandwidth solves with n >= 32 that are not a
  *   whole ragged packing (ragged id lists, i.e. size buckets, qualify) and, for
  *   NTDM/NPDM, whose x does not alias f; THREAD otherwise.  band_autotune replaces the
