@@ -129,6 +129,76 @@ def test_partition_adi_nondominant(band, r):
                 assert (err <= bound).all(), (sweep, k, P, err.max())
 
 
+def _biased_exponent(v):
+    """IEEE binary64 biased exponent of |v| (0 for zero), as the guard compares them."""
+    mant, e = np.frexp(np.abs(v))
+    return np.where(v == 0, 0, e + 1022)
+
+
+def _chunk_guard_trips(B, P, tiny=17):
+    """Systems (PD) whose chunk sweep meets a pivot the partitioned schedule's guard
+    treats as zero: a pivot whose binary exponent lies `tiny` or more below that of the
+    largest entry of its row (chunk k of P restarts NPDM's recurrence at its first row,
+    rows [k L0 + min(k, r), ...) with n = L0 P + r).  A plain numpy model of that one
+    decision, all chunks of all systems at once; it shares nothing with the kernels."""
+    n, ns = B["n"], B["nsys"]
+    idx = np.arange(ns)[None, :] * B["sys_stride"] + np.arange(n)[:, None] * B["elem_stride"]
+    A = {q: B[q][idx] for q in "abcde"}                     # [row, system]
+    L0, rem = divmod(n, P)
+    ks = np.arange(P)
+    Ls = (L0 + (ks < rem))[:, None]                         # [chunk, 1]
+    s0 = (ks * L0 + np.minimum(ks, rem))[:, None]
+    al1, al2, be1, be2 = (np.zeros((P, ns)) for _ in range(4))
+    trip = np.zeros((P, ns), bool)
+    with np.errstate(divide="ignore", invalid="ignore", over="ignore"):
+        for j in range(int(Ls.max())):
+            live = j < Ls
+            i = np.minimum(s0 + j, n - 1)[:, 0]
+            ag = np.where((i >= 2)[:, None], A["a"][i], 0.0)
+            bg = np.where((i >= 1)[:, None], A["b"][i], 0.0)
+            dg = np.where((i + 1 < n)[:, None], A["d"][i], 0.0)
+            eg = np.where((i + 2 < n)[:, None], A["e"][i], 0.0)
+            cc = A["c"][i]
+            aa = ag if j >= 2 else np.zeros_like(ag)
+            bb = bg if j >= 1 else np.zeros_like(bg)
+            dd = np.where(j + 1 < Ls, dg, 0.0)
+            ee = np.where(j + 2 < Ls, eg, 0.0)
+            g = bb - al2 * aa
+            m = cc - be2 * aa - al1 * g
+            ex = np.maximum.reduce([_biased_exponent(v) for v in (cc, bg, dg, ag, eg)])
+            trip |= live & ((m == 0) | (_biased_exponent(m) + tiny <= ex))
+            alv, bev = (dd - be1 * g) / m, ee / m
+            al2, al1 = np.where(live, al1, al2), np.where(live, alv, al1)
+            be2, be1 = np.where(live, be1, be2), np.where(live, bev, be1)
+    return np.flatnonzero(trip.any(0)).tolist()
+
+
+@pytest.mark.parametrize("sweep", ["x", "y"])
+def test_partition_redoes_exactly_the_tripped_systems(band, sweep):
+    """On the indefinite r = 2 PD ADI rows the pivot guard sends some systems back to
+    NPDM in one lane (bitwise the thread schedule's result) and leaves every other
+    system of the warp partitioned: the redone set is exactly the systems whose chunk
+    sweep trips the guard in a plain numpy model of it.  (The interface's guards do not
+    trip on these inputs.)  A group's failure that leaked into the warp's other groups,
+    as a skipped warp vote once did, redoes whole warps and fails this test."""
+    B = synth.cfg1(r=2.0, k=2, sweep=sweep, grid=2048, nsys=40)
+    T = to_dev(B)
+    x1, _ = band.solve(*(T[q] for q in "abcdef"), method="npdm", schedule="thread")
+    xt, _, _, _ = _oracle(B, 2, "gepp")
+    xo, _, _, _ = _oracle(B, 2)
+    bound = np.maximum(1e-10, 10 * per_system_rel(xo, xt, *_args(B)))
+    tripped_any = False
+    for P in PARTS:
+        want = _chunk_guard_trips(B, P)
+        tripped_any |= bool(want)
+        x, st = _solve(band, T, 2, P)
+        assert (st == 0).all(), (sweep, P)
+        redone = [s for s in range(B["nsys"]) if torch.equal(x[:, s], x1[:, s])]
+        assert redone == want, (sweep, P, redone, want)
+        assert (per_system_rel(flat_of(x), xt, *_args(B)) <= bound).all(), (sweep, P)
+    assert tripped_any
+
+
 @pytest.mark.parametrize("k", [1, 2])
 def test_partition_fp32(band, k):
     """FP32 data: within a factor of 4 (or 1e-6) of one thread per system's distance
