@@ -58,13 +58,40 @@ def desc_for(ref, half_bw, schedule="auto", chunks=0):
 
 
 def _check_same(ref, *ts):
+    """ref and every given array share shape, strides, dtype and CUDA device."""
     for t in ts:
         if t is None:
             continue
         if t.shape != ref.shape or t.stride() != ref.stride() or t.dtype != ref.dtype:
             raise ValueError("all band arrays must share shape, strides and dtype")
-        if not t.is_cuda:
-            raise ValueError("band arrays must be CUDA tensors")
+    if not ref.is_cuda:
+        raise ValueError("band arrays must be CUDA tensors")
+    _on_device(ref.device, **{"band array %d" % i: t for i, t in enumerate(ts)})
+
+
+def _on_device(dev, **named):
+    """Every given tensor is a CUDA tensor on device dev: the kernels take raw device
+    pointers, and a host pointer would fault on the GPU instead of failing here."""
+    for name, t in named.items():
+        if t is None:
+            continue
+        if not isinstance(t, torch.Tensor) or not t.is_cuda or t.device != dev:
+            raise ValueError("%s must be a CUDA tensor on %s" % (name, dev))
+
+
+def _status_out(status, nsys, dev):
+    """The per-system status output: given (int32, contiguous, at least nsys entries) or
+    allocated."""
+    if status is None:
+        return torch.empty(nsys, dtype=torch.int32, device=dev)
+    _on_device(dev, status=status)
+    if status.dtype != torch.int32 or not status.is_contiguous() or status.numel() < nsys:
+        raise ValueError("status must be a contiguous int32 tensor of at least nsys entries")
+    return status
+
+
+def _bytes(t):
+    return t.numel() * t.element_size()
 
 
 def _diag5(a, b, c, d, e):
@@ -89,17 +116,20 @@ def solve(a, b, c, d, e, f, method="npdm", x=None, status=None, factors=None, ws
     m = _METHODS[method]
     half_bw = 1 if method in ("ntdm", "stdm") else 2
     _check_same(c, a if half_bw == 2 else None, b, d, e if half_bw == 2 else None, f)
+    _on_device(c.device, factors=factors, ws=ws)
     desc = desc_for(c, half_bw, schedule, chunks)
     if x is None:
         x = torch.empty_strided(c.shape, c.stride(), dtype=c.dtype, device=c.device)
     _check_same(c, x)
-    if status is None:
-        status = torch.empty(c.shape[1], dtype=torch.int32, device=c.device)
+    status = _status_out(status, c.shape[1], c.device)
+    if factors is not None and _bytes(factors) < lib.band_workspace_size(ct.byref(desc),
+                                                                         L.OP_FACTOR, m, 0):
+        raise ValueError("factors is smaller than this batch's factorisation")
     need = lib.band_workspace_size(ct.byref(desc), L.OP_SOLVE, m, 0)
-    if ws is None or ws.numel() < need:
+    if ws is None or _bytes(ws) < need:
         ws = _workspace(need, c.device)
     code = lib.band_solve(ct.byref(desc), m, _ptr(factors), _diag5(a, b, c, d, e), _ptr(f), _ptr(x),
-                          _ptr(status), _ptr(ws), ws.numel(), _stream())
+                          _ptr(status), _ptr(ws), _bytes(ws), _stream())
     L.check(code, "band_solve")
     return x, status
 
@@ -109,11 +139,11 @@ def factor(a, b, c, d, e, method="npdm", status=None):
     lib = L.load()
     m = _METHODS[method]
     half_bw = 1 if method == "ntdm" else 2
+    _check_same(c, a if half_bw == 2 else None, b, d, e if half_bw == 2 else None)
     desc = desc_for(c, half_bw)
     need = lib.band_workspace_size(ct.byref(desc), L.OP_FACTOR, m, 0)
     buf = _workspace(need, c.device)
-    if status is None:
-        status = torch.empty(c.shape[1], dtype=torch.int32, device=c.device)
+    status = _status_out(status, c.shape[1], c.device)
     code = lib.band_factor(ct.byref(desc), m, _diag5(a, b, c, d, e), _ptr(buf), buf.numel(),
                            _ptr(status), _stream())
     L.check(code, "band_factor")
@@ -130,6 +160,17 @@ def solve_ragged(a, b, c, d, e, f, offsets, hbw, n_max, total_rows, method="auto
     """
     lib = L.load()
     m = _METHODS[method]
+    dev = c.device
+    _on_device(dev, a=a, b=b, c=c, d=d, e=e, f=f, offsets=offsets, hbw=hbw, x=x, ws=ws)
+    for name, t in (("a", a), ("b", b), ("d", d), ("e", e), ("f", f), ("x", x)):
+        if t is not None and (t.dtype != c.dtype or t.dim() != 1 or not t.is_contiguous()
+                              or t.numel() < int(total_rows)):
+            raise ValueError("%s must be a contiguous 1-D tensor of c's dtype with at least "
+                             "total_rows entries" % name)
+    if c.dim() != 1 or not c.is_contiguous() or c.numel() < int(total_rows):
+        raise ValueError("c must be a contiguous 1-D tensor with at least total_rows entries")
+    if offsets.dtype != torch.int64 or hbw is not None and hbw.dtype != torch.int8:
+        raise ValueError("offsets must be int64 and hbw int8")
     nsys = offsets.numel() - 1
     desc = L.BandDesc(half_bw=1 if method in ("ntdm", "stdm") else 2, dtype=_dtype_code(c),
                       nsys=nsys, n=int(n_max), sys_stride=0, elem_stride=1,
@@ -137,13 +178,12 @@ def solve_ragged(a, b, c, d, e, f, offsets, hbw, n_max, total_rows, method="auto
                       total_rows=int(total_rows))
     if x is None:
         x = torch.empty_like(f)
-    if status is None:
-        status = torch.empty(nsys, dtype=torch.int32, device=c.device)
+    status = _status_out(status, nsys, dev)
     need = lib.band_workspace_size(ct.byref(desc), L.OP_SOLVE, m, 0)
-    if ws is None or ws.numel() < need:
-        ws = _workspace(need, c.device)
+    if ws is None or _bytes(ws) < need:
+        ws = _workspace(need, dev)
     code = lib.band_solve(ct.byref(desc), m, None, _diag5(a, b, c, d, e), _ptr(f), _ptr(x),
-                          _ptr(status), _ptr(ws), ws.numel(), _stream())
+                          _ptr(status), _ptr(ws), _bytes(ws), _stream())
     L.check(code, "band_solve")
     return x, status
 
@@ -160,6 +200,7 @@ def sip(a, b, c, d, e, f, tol=1e-10, max_it=200, width=5, hb_max_it=30, hb_tol=1
     desc = desc_for(c, 2, schedule)
     if x is None:
         x = torch.empty_strided(c.shape, c.stride(), dtype=c.dtype, device=c.device)
+    _check_same(c, x)
     nsys = c.shape[1]
     iters = torch.empty(nsys, dtype=torch.int32, device=c.device)
     resid = torch.empty(nsys, dtype=torch.float64, device=c.device)
@@ -178,11 +219,16 @@ def refine_solve(a32, b32, c32, d32, e32, f, rel_stop=1e-11, max_steps=10, x=Non
     """FP32 solve + FP64 refinement; f, x float64 with the diagonals' strides.  The FP32
     solves run on `schedule` / `chunks` as in ``solve``."""
     lib = L.load()
+    _check_same(c32, a32, b32, d32, e32)
+    if c32.dtype != torch.float32:
+        raise ValueError("the diagonals must be float32")
     desc = desc_for(c32, 2 if a32 is not None else 1, schedule, chunks)
-    if f.shape != c32.shape or f.stride() != c32.stride() or f.dtype != torch.float64:
-        raise ValueError("f must be float64 with the diagonals' shape and strides")
     if x is None:
         x = torch.empty_strided(c32.shape, c32.stride(), dtype=torch.float64, device=c32.device)
+    for name, t in (("f", f), ("x", x)):
+        _on_device(c32.device, **{name: t})
+        if t.shape != c32.shape or t.stride() != c32.stride() or t.dtype != torch.float64:
+            raise ValueError("%s must be float64 with the diagonals' shape and strides" % name)
     nsys = c32.shape[1]
     steps = torch.empty(nsys, dtype=torch.int32, device=c32.device)
     status = torch.empty(nsys, dtype=torch.int32, device=c32.device)
@@ -201,7 +247,12 @@ def adjoint(a, b, c, d, e, x, w, factors=None, method="npdm", schedule="auto", c
     lib = L.load()
     m = _METHODS[method]
     half_bw = 1 if method == "ntdm" else 2
+    _check_same(c, a if half_bw == 2 else None, b, d, e if half_bw == 2 else None, x, w)
+    _on_device(c.device, factors=factors)
     desc = desc_for(c, half_bw, schedule, chunks)
+    if factors is not None and _bytes(factors) < lib.band_workspace_size(ct.byref(desc),
+                                                                         L.OP_FACTOR, m, 0):
+        raise ValueError("factors is smaller than this batch's factorisation")
     mk = lambda: torch.empty_strided(c.shape, c.stride(), dtype=c.dtype, device=c.device)
     grads = [mk() if (half_bw == 2 or k in (1, 2, 3)) else None for k in range(5)]
     gf = mk()
@@ -259,6 +310,7 @@ class BatchPlan:
             x = sp.get("x")
             if x is None:
                 x = torch.empty_strided(c.shape, c.stride(), dtype=c.dtype, device=c.device)
+            _check_same(c, x)
             status = torch.empty(c.shape[1], dtype=torch.int32, device=c.device)
             need = lib.band_workspace_size(ct.byref(desc), opc, m, 0)
             if tune and op == "solve" and desc.schedule == L.SCHED_AUTO:
@@ -330,12 +382,18 @@ class RaggedPlan:
             raise ValueError("band_plan_ragged: bad sizes or bandwidths, or more than %d buckets"
                              % L.MAX_BATCH)
         dev = f.device
+        _on_device(dev, a=a, b=b, c=c, d=d, e=e, f=f, x=x)
+        rows = int(offs[-1]) if nsys > 0 else 0
+        for name, t in (("a", a), ("b", b), ("c", c), ("d", d), ("e", e), ("f", f), ("x", x)):
+            if t is not None and (t.dtype != f.dtype or t.dim() != 1 or not t.is_contiguous()
+                                  or t.numel() < rows):
+                raise ValueError("%s must be a contiguous 1-D tensor of f's dtype with at "
+                                 "least offsets[-1] entries" % name)
         self.order = torch.from_numpy(order[:nsys].copy()).to(dev)
         self.offsets = torch.from_numpy(offs).to(dev)
         self.buckets = [(bk.first, bk.count, bk.n_max, bk.half_bw) for bk in buckets[:nb]]
         self.x = x if x is not None else torch.empty_like(f)
-        self.status = status if status is not None else torch.empty(nsys, dtype=torch.int32,
-                                                                    device=dev)
+        self.status = _status_out(status, nsys, dev)
         sched = "auto" if schedule == "tune" else schedule
         self.descs, self.keep = [], [a, b, c, d, e, f]
         self.arr = (L.BandProblem * max(nb, 1))()
