@@ -1,5 +1,8 @@
 """FP64 CPU oracle for the batched band solvers -- TEST INFRASTRUCTURE ONLY.
 
+(FP64 throughout, except the Laurent-series pass of STDM/SPDM, whose coefficients are
+double-double so that exact cancellations can be told from rounding residue.)
+
 Only the test suite, the smoke check and the benchmark's CPU-baseline leg may
 import this package.  It is independent of the CUDA library: it shares no code,
 header, table or constant with it, and neither side imports the other.  Its

@@ -1,5 +1,7 @@
 /*
- * band_oracle.c -- plain, slow, FP64 CPU oracle for the batched band solvers.
+ * band_oracle.c -- plain, slow, FP64 CPU oracle for the batched band solvers
+ * (the Laurent-series pass of the symbolic methods carries double-double
+ * coefficients; see R3).
  *
  * TEST INFRASTRUCTURE ONLY.  This file exists to check the CUDA library; it is
  * not part of the product.  Only the test suite, the smoke check and the
@@ -276,12 +278,24 @@ int orc_gepp_band(int64_t n, int k, const double* a, const double* b, const doub
 /* require nonsingularity").  Replacing mu_i by t is the exact LU of          */
 /* A(t) = A + t * sum_{flagged j} e_j e_j^T, so x(t) -> A^{-1} f.             */
 /*                                                                            */
-/* Arithmetic: truncated Laurent series in t.  Coefficient of t^k is stored   */
-/* at q[k + LP] for k in [-LP, LP]; the series is known for exponents        */
-/* k < hi (hi <= LP + 1; a plain number has hi = LP + 1).  Zero tests are     */
-/* exact IEEE compares.  Readings (the paper is silent):                     */
-/*  - one symbol for every zero pivot;                                        */
-/*  - a pivot whose known coefficients are all zero counts as a zero pivot;   */
+/* A system without a zero pivot never meets the symbol: its SPDM / STDM is   */
+/* R2 / R1 itself (R1 is R2 with a = e = 0, operation for operation), and     */
+/* det A is the product of R2's pivots.  A system whose R2 pass meets an      */
+/* exactly zero pivot is solved again in truncated Laurent series in t.       */
+/*                                                                            */
+/* Series arithmetic.  Coefficient of t^k at q[k + LP], k in [-LP, LP]; the   */
+/* series is known for exponents k < hi (hi <= LP + 1; a plain number has hi  */
+/* = LP + 1).  Coefficients are double-double numbers (below), and a          */
+/* coefficient formed as a sum of terms (a sum or difference of two series,   */
+/* a coefficient of a product, the numerator of a quotient's coefficient)    */
+/* whose result lies below 2^-80 of the sum of the terms' magnitudes is set   */
+/* to zero: in exact arithmetic it is zero, and what double-double leaves of  */
+/* it is rounding residue (~2^-104 of the terms per operation), which would   */
+/* otherwise pass for a nonzero leading coefficient.  Readings (the paper is  */
+/* silent):                                                                   */
+/*  - a zero pivot of the R2 pass is an exact IEEE zero; in the series pass   */
+/*    one symbol stands for every pivot whose known coefficients are all      */
+/*    zero;                                                                   */
 /*  - x(t) is analytic at t = 0 when A is nonsingular, so the negative-power */
 /*    coefficients of each x_i are rounding residue and are dropped;          */
 /*  - det A = lim prod mu_i(t): with V = sum of the valuations of the mu_i,   */
@@ -291,20 +305,75 @@ int orc_gepp_band(int64_t n, int k, const double* a, const double* b, const doub
 /*  - a pole deeper than t^-LP, or an x_i whose t^0 coefficient is not known,*/
 /*    is SYMBOLIC_RANGE.                                                      */
 /* ------------------------------------------------------------------------- */
-#define LP 8
+
+/* Double-double numbers hi + lo with |lo| <= ulp(hi) / 2 (Dekker, "A floating- */
+/* point technique for extending the available precision", 1971).  The exact  */
+/* error of a rounded sum comes from Knuth's two-sum, that of a rounded        */
+/* product from one fused multiply-add; sum, product and quotient are then     */
+/* accurate to about 2^-104 relative.                                          */
+typedef struct { double hi, lo; } dd;
+
+static dd dd_of(double v) { dd r = {v, 0.0}; return r; }
+/* s + e = a + b exactly (any a, b) */
+static dd two_sum(double a, double b) {
+  double s = a + b;
+  double bv = s - a;
+  double av = s - bv;
+  dd r = {s, (a - av) + (b - bv)};
+  return r;
+}
+/* s + e = a + b exactly, when |a| >= |b| or a == 0 */
+static dd quick_two_sum(double a, double b) {
+  double s = a + b;
+  dd r = {s, b - (s - a)};
+  return r;
+}
+static dd dd_add(dd x, dd y) {
+  dd s = two_sum(x.hi, y.hi);
+  dd t = two_sum(x.lo, y.lo);
+  s.lo += t.hi;
+  s = quick_two_sum(s.hi, s.lo);
+  s.lo += t.lo;
+  return quick_two_sum(s.hi, s.lo);
+}
+static dd dd_neg(dd x) { dd r = {-x.hi, -x.lo}; return r; }
+static dd dd_mul(dd x, dd y) {
+  double p = x.hi * y.hi;
+  double e = fma(x.hi, y.hi, -p);             /* p + e = x.hi * y.hi exactly */
+  e += x.hi * y.lo + x.lo * y.hi;
+  return quick_two_sum(p, e);
+}
+/* x / y by three quotient digits, each correcting the remainder */
+static dd dd_div(dd x, dd y) {
+  double q1 = x.hi / y.hi;
+  dd r = dd_add(x, dd_neg(dd_mul(y, dd_of(q1))));
+  double q2 = r.hi / y.hi;
+  r = dd_add(r, dd_neg(dd_mul(y, dd_of(q2))));
+  double q3 = r.hi / y.hi;
+  return dd_add(quick_two_sum(q1, q2), dd_of(q3));
+}
+static int dd_is_zero(dd x) { return x.hi == 0.0; }
+#define DD_RESIDUE 0x1p-80
+/* v, or zero when it is rounding residue of terms of total magnitude mag */
+static dd dd_flush(dd v, double mag) {
+  if (fabs(v.hi) <= DD_RESIDUE * mag) return dd_of(0.0);
+  return v;
+}
+
+#define LP 16
 #define LW (2 * LP + 1)
-typedef struct { double q[LW]; int hi; } lser;
+typedef struct { dd q[LW]; int hi; } lser;
 
 static lser ls_const(double v) {
-  lser s; memset(&s, 0, sizeof s); s.q[LP] = v; s.hi = LP + 1; return s;
+  lser s; memset(&s, 0, sizeof s); s.q[LP] = dd_of(v); s.hi = LP + 1; return s;
 }
 static lser ls_symbol(void) {
-  lser s; memset(&s, 0, sizeof s); s.q[LP + 1] = 1.0; s.hi = LP + 1; return s;
+  lser s; memset(&s, 0, sizeof s); s.q[LP + 1] = dd_of(1.0); s.hi = LP + 1; return s;
 }
 /* lowest exponent with a known nonzero coefficient, or LP + 1 if none */
 static int ls_val(const lser* s) {
   for (int k = -LP; k < s->hi && k <= LP; ++k)
-    if (s->q[k + LP] != 0.0) return k;
+    if (!dd_is_zero(s->q[k + LP])) return k;
   return LP + 1;
 }
 static int imin(int x, int y) { return x < y ? x : y; }
@@ -312,7 +381,11 @@ static int imin(int x, int y) { return x < y ? x : y; }
 static lser ls_addsub(const lser* x, const lser* y, double sign) {
   lser r; memset(&r, 0, sizeof r);
   r.hi = imin(x->hi, y->hi);
-  for (int k = -LP; k < r.hi && k <= LP; ++k) r.q[k + LP] = x->q[k + LP] + sign * y->q[k + LP];
+  for (int k = -LP; k < r.hi && k <= LP; ++k) {
+    dd u = x->q[k + LP], v = y->q[k + LP];
+    if (sign < 0) v = dd_neg(v);
+    r.q[k + LP] = dd_flush(dd_add(u, v), fabs(u.hi) + fabs(v.hi));
+  }
   return r;
 }
 /* a series with no known nonzero coefficient is O(t^hi) */
@@ -321,17 +394,20 @@ static int ls_veff(const lser* s) { int v = ls_val(s); return v <= LP ? v : s->h
 /* product; known below min(vx + hi_y, vy + hi_x), so every kept coefficient is complete */
 static lser ls_mul(const lser* x, const lser* y, int* err) {
   lser r; memset(&r, 0, sizeof r);
+  double mag[LW] = {0};
   int vx = ls_veff(x), vy = ls_veff(y);
   r.hi = imin(LP + 1, imin(vx + y->hi, vy + x->hi));
   for (int i = -LP; i < x->hi && i <= LP; ++i)
     for (int j = -LP; j < y->hi && j <= LP; ++j) {
-      double p = x->q[i + LP] * y->q[j + LP];
-      if (p == 0.0) continue;
+      if (dd_is_zero(x->q[i + LP]) || dd_is_zero(y->q[j + LP])) continue;
       int k = i + j;
       if (k >= r.hi) continue;
       if (k < -LP) { *err = 1; continue; }
-      r.q[k + LP] += p;
+      dd p = dd_mul(x->q[i + LP], y->q[j + LP]);
+      r.q[k + LP] = dd_add(r.q[k + LP], p);
+      mag[k + LP] += fabs(p.hi);
     }
+  for (int k = 0; k < LW; ++k) r.q[k] = dd_flush(r.q[k], mag[k]);
   return r;
 }
 /* quotient by long division; relative precision is the smaller of the two */
@@ -347,9 +423,14 @@ static lser ls_div(const lser* x, const lser* y, int* err) {
   if (v < -LP) { *err = 1; return r; }
   /* c_k = (x_{k+vy} - sum_{j>=1} y_{vy+j} c_{k-j}) / y_{vy} */
   for (int k = v; k < r.hi; ++k) {
-    double s = x->q[k + vy + LP];
-    for (int j = 1; k - j >= v; ++j) s -= y->q[vy + j + LP] * r.q[k - j + LP];
-    r.q[k + LP] = s / y->q[vy + LP];
+    dd s = x->q[k + vy + LP];
+    double mag = fabs(s.hi);
+    for (int j = 1; k - j >= v; ++j) {
+      dd p = dd_mul(y->q[vy + j + LP], r.q[k - j + LP]);
+      s = dd_add(s, dd_neg(p));
+      mag += fabs(p.hi);
+    }
+    r.q[k + LP] = dd_div(dd_flush(s, mag), y->q[vy + LP]);
   }
   return r;
 }
@@ -359,28 +440,24 @@ static lser ls_sub_mul(const lser* acc, const lser* p, const lser* q, int* err) 
 }
 
 typedef struct { int V; double mant; long long ex; } detacc;
-static void det_push(detacc* D, const lser* mu) {
-  int v = ls_val(mu);
+static void det_push(detacc* D, int v, double lead) {
   D->V += v;
   int e2;
-  double m = frexp(mu->q[v + LP], &e2);
+  double m = frexp(lead, &e2);
   D->mant *= m; D->ex += e2;
   int e3; D->mant = frexp(D->mant, &e3); D->ex += e3;
 }
 
-/* Symbolic PD (k = 2) or TD (k = 1) solve.  det_out (may be NULL) receives   */
-/* det(A) as mant * 2^ex (ex in *det_ex); *nflag the number of zero pivots.  */
-int orc_symbolic(int64_t n, int k, const double* a, const double* b, const double* c,
-                 const double* d, const double* e, const double* f, double* x,
-                 double* det_mant, long long* det_ex, int* nflag) {
-  if (n < 1 || (k != 1 && k != 2)) return ORC_ARG;
+/* The series pass over a system whose R2 pass met a zero pivot. */
+static int symbolic_series(int64_t n, int k, const double* a, const double* b, const double* c,
+                           const double* d, const double* e, const double* f, double* x,
+                           detacc* D, int* nflag) {
   lser* alpha = (lser*)calloc((size_t)n, sizeof(lser));
   lser* beta = (lser*)calloc((size_t)n, sizeof(lser));
   lser* z = (lser*)calloc((size_t)n, sizeof(lser));
   lser* xs = (lser*)calloc((size_t)n, sizeof(lser));
   if (!alpha || !beta || !z || !xs) { free(alpha); free(beta); free(z); free(xs); return ORC_NOMEM; }
   int err = 0, flags = 0;
-  detacc D = {0, 1.0, 0};
   for (int64_t i = 0; i < n; ++i) {
     lser ai = ls_const((k == 2 && i >= 2) ? a[i] : 0.0);
     lser g = ls_const(0.0);
@@ -390,7 +467,8 @@ int orc_symbolic(int64_t n, int k, const double* a, const double* b, const doubl
     if (k == 2 && i >= 2) m = ls_sub_mul(&m, &beta[i - 2], &ai, &err);
     if (i >= 1) m = ls_sub_mul(&m, &alpha[i - 1], &g, &err);
     if (ls_val(&m) > LP) { m = ls_symbol(); ++flags; }      /* zero pivot -> t */
-    det_push(&D, &m);
+    int v = ls_val(&m);
+    det_push(D, v, m.q[v + LP].hi);
     alpha[i] = ls_const(0.0);
     beta[i] = ls_const(0.0);
     if (i <= n - 2) {
@@ -412,18 +490,42 @@ int orc_symbolic(int64_t n, int k, const double* a, const double* b, const doubl
     lser xi = z[i];
     if (i + 1 < n) xi = ls_sub_mul(&xi, &alpha[i], &xs[i + 1], &err);
     if (k == 2 && i + 2 < n) xi = ls_sub_mul(&xi, &beta[i], &xs[i + 2], &err);
-    for (int kk = -LP; kk < 0; ++kk) xi.q[kk + LP] = 0.0;
+    for (int kk = -LP; kk < 0; ++kk) xi.q[kk + LP] = dd_of(0.0);
     if (xi.hi <= 0) err = 1;
     xs[i] = xi;
-    x[i] = xi.q[LP];
+    x[i] = xi.q[LP].hi;
   }
+  *nflag = flags;
+  free(alpha); free(beta); free(z); free(xs);
+  if (D->V > 0) return ORC_SINGULAR;
+  if (err || D->V < 0) return ORC_SYMBOLIC_RANGE;
+  return all_finite(n, x) ? ORC_OK : ORC_NONFINITE;
+}
+
+/* Symbolic PD (k = 2) or TD (k = 1) solve.  det_out (may be NULL) receives   */
+/* det(A) as mant * 2^ex (ex in *det_ex); *nflag the number of zero pivots.  */
+int orc_symbolic(int64_t n, int k, const double* a, const double* b, const double* c,
+                 const double* d, const double* e, const double* f, double* x,
+                 double* det_mant, long long* det_ex, int* nflag) {
+  if (n < 1 || (k != 1 && k != 2)) return ORC_ARG;
+  double* fac = (double*)malloc(4 * (size_t)n * sizeof(double));
+  double* zero = k == 1 ? (double*)calloc((size_t)n, sizeof(double)) : NULL;
+  if (!fac || (k == 1 && !zero)) { free(fac); free(zero); return ORC_NOMEM; }
+  const double* pa = k == 2 ? a : zero;
+  const double* pe = k == 2 ? e : zero;
+  detacc D = {0, 1.0, 0};
+  int flags = 0;
+  int st = orc_npdm(n, pa, b, c, d, pe, f, x, fac, NULL);
+  if (st == ORC_ZERO_PIVOT) {
+    st = symbolic_series(n, k, pa, b, c, d, pe, f, x, &D, &flags);
+  } else {
+    for (int64_t i = 0; i < n; ++i) det_push(&D, 0, fac[n + i]);    /* R2's mu_i */
+  }
+  free(fac); free(zero);
   if (nflag) *nflag = flags;
   if (det_mant) *det_mant = D.V == 0 ? D.mant : 0.0;
   if (det_ex) *det_ex = D.V == 0 ? D.ex : 0;
-  free(alpha); free(beta); free(z); free(xs);
-  if (D.V > 0) return ORC_SINGULAR;
-  if (err || D.V < 0) return ORC_SYMBOLIC_RANGE;
-  return all_finite(n, x) ? ORC_OK : ORC_NONFINITE;
+  return st;
 }
 
 /* ------------------------------------------------------------------------- */

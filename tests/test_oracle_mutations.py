@@ -4,6 +4,11 @@ Each mutant is a one-line edit of ``oracle/band_oracle.c`` (a dropped term, a wr
 index, a flipped sign, a transposed operand), compiled into a temporary library and
 loaded by the pin tests through BAND_ORACLE_LIB.  The pins must fail for every one.
 Runs on the CPU only.
+
+Edits that no pin can see because they change nothing the oracle returns are not
+listed: computing the product P = M X of the Hotelling-Bodewig step on w + 1 rather
+than w + 2 diagonals (the update X (2I - P) reads only w of them), and keeping the negative powers of x_i(t) in the symbolic
+back-substitution (after the residue flush they are zero).
 """
 import os
 import subprocess
@@ -24,8 +29,14 @@ MUTANTS = {
     "ntdm_transposed_operand": ("if (i <= n - 2) alpha[i] = op_div(d[i], mu, ops);",
                                 "if (i <= n - 2) alpha[i] = op_div(b[i + 1], mu, ops);"),
     "gepp_rhs_not_swapped": ("double t = x[j]; x[j] = x[p]; x[p] = t;", ""),
-    "laurent_division_sign": ("for (int j = 1; k - j >= v; ++j) s -= y->q[vy + j + LP] * r.q[k - j + LP];",
-                              "for (int j = 1; k - j >= v; ++j) s += y->q[vy + j + LP] * r.q[k - j + LP];"),
+    "laurent_division_sign": ("s = dd_add(s, dd_neg(p));", "s = dd_add(s, p);"),
+    "dd_residue_not_flushed": ("if (fabs(v.hi) <= DD_RESIDUE * mag) return dd_of(0.0);", ""),
+    "dd_product_error_dropped": ("double e = fma(x.hi, y.hi, -p);", "double e = 0.0;"),
+    "dd_two_sum_error_dropped": ("dd r = {s, (a - av) + (b - bv)};", "dd r = {s, 0.0};"),
+    "dd_div_one_digit": ("return dd_add(quick_two_sum(q1, q2), dd_of(q3));", "return dd_of(q1);"),
+    "symbolic_det_wrong_factor": ("det_push(&D, 0, fac[n + i]);", "det_push(&D, 0, fac[i]);"),
+    "symbolic_td_reads_a": ("const double* pa = k == 2 ? a : zero;", "const double* pa = a;"),
+    "symbolic_window_short": ("#define LP 16", "#define LP 3"),
     "ilu0_wrong_operand": ("w[2] = w[2] - w[0] * u2[i - 2];", "w[2] = w[2] - w[0] * u1[i - 2];"),
     "hb_missing_2I": ("double y = (m == j ? 2.0 : 0.0) - band_get(P, n, wp, lower, m, j);",
                       "double y = (m == j ? 1.0 : 0.0) - band_get(P, n, wp, lower, m, j);"),

@@ -216,6 +216,45 @@ def test_symbolic_vs_exact_on_random_integer_systems(k):
     assert flagged >= 3
 
 
+@pytest.mark.parametrize("k", [1, 2])
+def test_symbolic_vs_exact_with_many_zero_pivots(k):
+    """R3 where zero pivots crowd: integer systems whose diagonal is mostly 0, so that
+    several pivots vanish and the symbol meets itself in later pivots (poles, exact
+    cancellations of series coefficients).  Against exact rational functions of t on
+    every system that reaches the series pass: a nonsingular matrix gives the exact
+    limit (and determinant), a singular one SINGULAR; the truncated series may give up
+    (SYMBOLIC_RANGE) on at most 1 % of them, never with a wrong result."""
+    rng = np.random.default_rng(40 + k)
+    seen = nonsingular = gave_up = 0
+    for trial in range(700):
+        n = int(rng.integers(3, 17))
+        pick = lambda vals: [int(v) for v in rng.choice(vals, n)]
+        a, b, d, e, f = (pick([-2, -1, 0, 0, 1, 2]) for _ in range(5))
+        c = pick([0, 0, 0, 1, -1])
+        if k == 1:
+            a, e = [0] * n, [0] * n
+        x, st, dm, dex, nf = oracle.symbolic(k, *(np.array(v, float) for v in (a, b, c, d, e, f)))
+        if nf == 0:
+            continue
+        seen += 1
+        sym = exact.symbolic_solve(k, a, b, c, d, e, f)
+        if sym["status"] == "SINGULAR":
+            assert st == "SINGULAR", (trial, st)
+            continue
+        nonsingular += 1
+        if st == "SYMBOLIC_RANGE":
+            gave_up += 1
+            continue
+        assert st == "OK", (trial, st)
+        xe = np.array([float(v) for v in sym["x"]])
+        An = _dense(k, *(np.array(v, float) for v in (a, b, c, d, e)))
+        kappa = np.linalg.cond(An, np.inf)
+        assert np.abs(x - xe).max() <= 1e3 * kappa * U * max(1.0, np.abs(xe).max()), trial
+        assert abs(dm * 2.0 ** dex - float(sym["det"])) <= 1e-9 * abs(float(sym["det"])), trial
+    assert nonsingular >= 50 and seen - nonsingular >= 50
+    assert gave_up <= nonsingular // 100
+
+
 def _golden_cases():
     return json.load(open(os.path.join(GOLD, "zero_pivot_cases.json")))["cases"]
 
@@ -248,6 +287,25 @@ def test_td_swap_is_f_swapped():
                                          np.array([1.0, 0.0]), None, np.array([3.0, 5.0]))
     assert st == "OK" and nf == 1
     assert list(x) == [5.0, 3.0]
+
+
+def test_td_methods_ignore_the_outer_diagonals():
+    """STDM reads b, c, d only: whatever the a and e arrays hold (as in a ragged packing
+    that mixes TD and PD systems), with and without a zero pivot."""
+    rng = np.random.default_rng(17)
+    n = 40
+    _, b, c, d, _ = _rand_pd(rng, n, dominant=True, k=1)
+    f = rng.uniform(-1, 1, n)
+    junk_a, junk_e = rng.uniform(-5, 5, n), rng.uniform(-5, 5, n)
+    for zero_row in (None, 7):
+        b2, cz = b.copy(), c.copy()
+        if zero_row is not None:          # b = c = 0 in that row: its pivot is exactly 0
+            b2[zero_row] = cz[zero_row] = 0.0
+        want = oracle.symbolic(1, None, b2, cz, d, None, f)
+        got = oracle.symbolic(1, junk_a, b2, cz, d, junk_e, f)
+        assert want[1] == got[1] == "OK"
+        assert (want[4] > 0) == (zero_row is not None)
+        assert np.array_equal(want[0], got[0]) and want[2:] == got[2:]
 
 
 def test_symbolic_equals_numeric_bitwise_without_zero_pivots():
