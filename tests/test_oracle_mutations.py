@@ -10,6 +10,7 @@ listed: computing the product P = M X of the Hotelling-Bodewig step on w + 1 rat
 than w + 2 diagonals (the update X (2I - P) reads only w of them), and keeping the negative powers of x_i(t) in the symbolic
 back-substitution (after the residue flush they are zero).
 """
+import concurrent.futures
 import os
 import subprocess
 import sys
@@ -43,21 +44,48 @@ MUTANTS = {
     "sip_residual_sign": ("r[i] = op_sub(f[i], s, ops);", "r[i] = op_sub(s, f[i], ops);"),
     "refine_missing_rescale": ("double dl = s * (double)x32[i];", "double dl = (double)x32[i];"),
     "adjoint_not_transposed": ("if (i >= 1) tb[i] = d[i - 1];", "if (i >= 1) tb[i] = b[i];"),
+    "lu_minus_a_sign": ("ka[i] = i >= 2 ? lu_a - a[i] : 0.0;", "ka[i] = i >= 2 ? a[i] - lu_a : 0.0;"),
+    "refine_absolute_stop": ("if (dmax <= rel_stop * xmax) break;", "if (dmax <= rel_stop) break;"),
+    "ntdm_back_sign": ("x[i] = op_sub(z[i], op_mul(alpha[i], x[i + 1], ops), ops);",
+                       "x[i] = op_add(z[i], op_mul(alpha[i], x[i + 1], ops), ops);"),
+    "hb_start_not_inverse": ("X[i] = 1.0 / dg;", "X[i] = dg;"),
+    "cond1_not_transposed": ("if (orc_gepp_band(n, k, ta, tb, tc, td, te, y, z, NULL) != ORC_OK)",
+                             "if (orc_gepp_band(n, k, a, b, c, d, e, y, z, NULL) != ORC_OK)"),
+    "batch_strides_swapped": ("int64_t p = off + i * J->elem_stride;", "int64_t p = off + i * J->sys_stride;"),
+    "batch_bandwidths_ignored": ("int k = J->hbw ? J->hbw[s] : J->k;", "int k = J->k;"),
 }
 
 
-@pytest.mark.parametrize("name", sorted(MUTANTS))
-def test_pins_catch_planted_mistake(name, tmp_path):
+def _run_mutant(name, workdir):
+    """Compile the oracle with one planted mistake and run the pins against it;
+    returns (pins' exit code, the end of their output)."""
     old, new = MUTANTS[name]
     src = open(SRC).read()
     assert src.count(old) == 1, "mutation anchor must be unique: " + name
-    mutated = tmp_path / "mutant.c"
-    mutated.write_text(src.replace(old, new))
-    lib = tmp_path / "libmutant.so"
+    mutated = os.path.join(workdir, name + ".c")
+    with open(mutated, "w") as fh:
+        fh.write(src.replace(old, new))
+    lib = os.path.join(workdir, "lib" + name + ".so")
     subprocess.run(["gcc", "-O2", "-ffp-contract=off", "-std=c11", "-fPIC", "-shared", "-pthread",
-                    "-o", str(lib), str(mutated), "-lm"], check=True)
-    env = dict(os.environ, BAND_ORACLE_LIB=str(lib))
+                    "-o", lib, mutated, "-lm"], check=True)
+    env = dict(os.environ, BAND_ORACLE_LIB=lib)
     res = subprocess.run([sys.executable, "-m", "pytest", "-x", "-q", "-p", "no:cacheprovider",
                           os.path.join(ROOT, "tests", "test_oracle_pins.py")],
                          cwd=ROOT, env=env, capture_output=True, text=True, timeout=600)
-    assert res.returncode != 0, "pins did not catch mutant %s:\n%s" % (name, res.stdout[-2000:])
+    return res.returncode, res.stdout[-2000:]
+
+
+@pytest.fixture(scope="module")
+def outcomes(tmp_path_factory):
+    """Every mutant's pin run, several at a time (each run is its own process)."""
+    workdir = str(tmp_path_factory.mktemp("mutants"))
+    workers = max(1, min(8, os.cpu_count() or 1))
+    with concurrent.futures.ThreadPoolExecutor(workers) as pool:
+        futures = {name: pool.submit(_run_mutant, name, workdir) for name in MUTANTS}
+        return {name: fut.result() for name, fut in futures.items()}
+
+
+@pytest.mark.parametrize("name", sorted(MUTANTS))
+def test_pins_catch_planted_mistake(name, outcomes):
+    code, tail = outcomes[name]
+    assert code != 0, "pins did not catch mutant %s:\n%s" % (name, tail)

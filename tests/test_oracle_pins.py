@@ -375,6 +375,30 @@ def test_ilu0_equals_npdm_factorisation():
     assert max(np.abs(v).max() for v in K) <= 1e-10 * np.abs(An).max()
 
 
+def test_lu_minus_a_is_the_product_of_any_band_factors():
+    """Algorithm 1's K = LU - A for arbitrary unit lower L (two subdiagonals) and upper
+    U (two superdiagonals), not only ILU(0)'s, for which K is at the rounding level:
+    every diagonal of the dense L U - A, which has no entry outside the five."""
+    rng = np.random.default_rng(31)
+    n = 12
+    l2, l1, u0, u1, u2 = (rng.uniform(-1, 1, n) for _ in range(5))
+    l2[:2] = 0
+    l1[:1] = 0
+    u1[n - 1:] = 0
+    u2[n - 2:] = 0
+    a, b, c, d, e = _rand_pd(rng, n, dominant=False)
+    K = oracle.lu_minus_a((l2, l1, u0, u1, u2), a, b, c, d, e)
+    L = np.eye(n) + np.diag(l1[1:], -1) + np.diag(l2[2:], -2)
+    Um = np.diag(u0) + np.diag(u1[:-1], 1) + np.diag(u2[:-2], 2)
+    Kd = L @ Um - _dense(2, a, b, c, d, e)
+    assert not np.triu(Kd, 3).any() and not np.tril(Kd, -3).any()
+    for off, got in zip((-2, -1, 0, 1, 2), K):
+        want = np.zeros(n)
+        rows = np.arange(max(0, -off), min(n, n - off))
+        want[rows] = Kd[rows, rows + off]
+        assert np.allclose(got, want, rtol=0, atol=1e-15), off
+
+
 @pytest.mark.parametrize("n", [5, 16, 37])
 def test_hotelling_bodewig_exact_for_full_width(n):
     """With w >= n the HB error squares, E_{k+1} = E_k^2, and E_0 = I - L X_0 is
@@ -491,6 +515,24 @@ def test_refinement_reaches_1e10(ratio):
         # the FP32 solve alone is far from it
         x0, steps0, _ = oracle.refine(*d32, f[:, s], max_steps=0)
         assert np.abs(x0 - xg).max() / np.abs(xg).max() > 1e-9
+
+
+def test_refinement_is_invariant_under_power_of_two_scaling():
+    """Scaling f by 2^p scales every quantity of R7 exactly (FP32 and FP64 alike, far
+    from overflow and underflow here), so x scales bitwise and the number of
+    corrections stays: the stopping test compares the correction with x, not with a
+    fixed size."""
+    rng = np.random.default_rng(41)
+    n = 256
+    D = synth.dominant(rng, 1, n, k=2, dtype=np.float32, ratio=1.1, flip_frac=0.05)
+    _, f = synth.manufactured(rng, 2, D, 1, n)
+    d32 = [D[q][:, 0] for q in "abcde"]
+    x0, steps0, st0 = oracle.refine(*d32, f[:, 0])
+    assert st0 == "OK" and 2 <= steps0 < 10
+    for p in (-60, 60):
+        x, steps, st = oracle.refine(*d32, np.ldexp(f[:, 0], p))
+        assert st == "OK" and steps == steps0
+        assert np.array_equal(x, np.ldexp(x0, p))
 
 
 # -------------------------------------------------------------------- adjoint
