@@ -293,9 +293,9 @@ int orc_gepp_band(int64_t n, int k, const double* a, const double* b, const doub
 /* it is rounding residue (~2^-104 of the terms per operation), which would   */
 /* otherwise pass for a nonzero leading coefficient.  Readings (the paper is  */
 /* silent):                                                                   */
-/*  - a zero pivot of the R2 pass is an exact IEEE zero; in the series pass   */
-/*    one symbol stands for every pivot whose known coefficients are all      */
-/*    zero;                                                                   */
+/*  - a zero pivot of the R2 pass is an exact IEEE zero, or a pivot within    */
+/*    rounding residue of zero (residue_pivot below); in the series pass one  */
+/*    symbol stands for every pivot whose known coefficients are all zero;    */
 /*  - x(t) is analytic at t = 0 when A is nonsingular, so the negative-power */
 /*    coefficients of each x_i are rounding residue and are dropped;          */
 /*  - det A = lim prod mu_i(t): with V = sum of the valuations of the mu_i,   */
@@ -502,6 +502,38 @@ static int symbolic_series(int64_t n, int k, const double* a, const double* b, c
   return all_finite(n, x) ? ORC_OK : ORC_NONFINITE;
 }
 
+/* Does R2's pass hold a pivot that double arithmetic cannot tell from zero?   */
+/* mu_i = c_i - beta_{i-2} a_i - alpha_{i-1} gamma_i, with gamma_i = b_i -      */
+/* alpha_{i-2} a_i.  When |mu_i| lies 2^40 or more below the largest quantity  */
+/* that entered it -- the row's entries a_i, b_i, c_i, the products           */
+/* beta_{i-2} a_i and alpha_{i-1} gamma_i, and the terms of alpha_{i-1}       */
+/* gamma_i with gamma_i expanded (alpha_{i-1} b_i, alpha_{i-1} alpha_{i-2}     */
+/* a_i, which catch a cancellation inside gamma_i) -- an exact zero and the    */
+/* rounding residue of one cannot be told apart in double arithmetic, so the   */
+/* system goes to the series pass, whose double-double arithmetic decides      */
+/* (reading; Sec. 1 asks only for a nonsingular matrix).  A pivot that is      */
+/* merely small gets the same, exact-to-double-double, treatment there.        */
+/* fac = R2's (gamma, mu, alpha, beta).                                        */
+#define PIVOT_RESIDUE 0x1p-40
+static double dmax(double x, double y) { return x > y ? x : y; }
+static int residue_pivot(int64_t n, const double* a, const double* b, const double* c,
+                         const double* fac) {
+  const double* gam = fac;
+  const double* mu = fac + n;
+  const double* alpha = fac + 2 * n;
+  const double* beta = fac + 3 * n;
+  for (int64_t i = 0; i < n; ++i) {
+    double ai = i >= 2 ? a[i] : 0.0, bi = i >= 1 ? b[i] : 0.0;
+    double al1 = i >= 1 ? alpha[i - 1] : 0.0, al2 = i >= 2 ? alpha[i - 2] : 0.0;
+    double be2 = i >= 2 ? beta[i - 2] : 0.0;
+    double big = dmax(dmax(fabs(ai), fabs(bi)), fabs(c[i]));
+    big = dmax(big, dmax(fabs(be2 * ai), fabs(al1 * gam[i])));
+    big = dmax(big, dmax(fabs(al1 * bi), fabs(al1 * al2 * ai)));
+    if (fabs(mu[i]) <= PIVOT_RESIDUE * big) return 1;
+  }
+  return 0;
+}
+
 /* Symbolic PD (k = 2) or TD (k = 1) solve.  det_out (may be NULL) receives   */
 /* det(A) as mant * 2^ex (ex in *det_ex); *nflag the number of zero pivots.  */
 int orc_symbolic(int64_t n, int k, const double* a, const double* b, const double* c,
@@ -516,6 +548,7 @@ int orc_symbolic(int64_t n, int k, const double* a, const double* b, const doubl
   detacc D = {0, 1.0, 0};
   int flags = 0;
   int st = orc_npdm(n, pa, b, c, d, pe, f, x, fac, NULL);
+  if (st == ORC_OK && residue_pivot(n, pa, b, c, fac)) st = ORC_ZERO_PIVOT;
   if (st == ORC_ZERO_PIVOT) {
     st = symbolic_series(n, k, pa, b, c, d, pe, f, x, &D, &flags);
   } else {

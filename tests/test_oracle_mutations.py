@@ -7,8 +7,12 @@ Runs on the CPU only.
 
 Edits that no pin can see because they change nothing the oracle returns are not
 listed: computing the product P = M X of the Hotelling-Bodewig step on w + 1 rather
-than w + 2 diagonals (the update X (2I - P) reads only w of them), and keeping the negative powers of x_i(t) in the symbolic
-back-substitution (after the residue flush they are zero).
+than w + 2 diagonals (the update X (2I - P) reads only w of them); reading the stored
+X through one diagonal fewer than it keeps (an off-by-one in band_get's offset test: for
+triangular M the outermost diagonal of X (2I - M X) is rebuilt exactly from the inner
+ones once those are exact, which is no later than the correct iteration gets there, so
+every iterate comes out the same); and keeping the negative powers of x_i(t) in the
+symbolic back-substitution (after the residue flush they are zero).
 """
 import concurrent.futures
 import os
@@ -49,6 +53,12 @@ MUTANTS = {
     "ntdm_back_sign": ("x[i] = op_sub(z[i], op_mul(alpha[i], x[i + 1], ops), ops);",
                        "x[i] = op_add(z[i], op_mul(alpha[i], x[i + 1], ops), ops);"),
     "hb_start_not_inverse": ("X[i] = 1.0 / dg;", "X[i] = dg;"),
+    "hb_band_wrong_side": ("int64_t off = lower ? i - j : j - i;\n  if (off < 0 || off >= w) return 0.0;",
+                           "int64_t off = lower ? j - i : i - j;\n  if (off < 0 || off >= w) return 0.0;"),
+    "hb_update_one_diagonal_short": ("for (int mo = 0; mo < w; ++mo) {",
+                                     "for (int mo = 0; mo < w - 1; ++mo) {"),
+    "symbolic_residue_pivot_ignored": ("if (st == ORC_OK && residue_pivot(n, pa, b, c, fac)) st = ORC_ZERO_PIVOT;",
+                                       ""),
     "cond1_not_transposed": ("if (orc_gepp_band(n, k, ta, tb, tc, td, te, y, z, NULL) != ORC_OK)",
                              "if (orc_gepp_band(n, k, a, b, c, d, e, y, z, NULL) != ORC_OK)"),
     "batch_strides_swapped": ("int64_t p = off + i * J->elem_stride;", "int64_t p = off + i * J->sys_stride;"),

@@ -220,24 +220,28 @@ def test_symbolic_vs_exact_on_random_integer_systems(k):
 def test_symbolic_vs_exact_with_many_zero_pivots(k):
     """R3 where zero pivots crowd: integer systems whose diagonal is mostly 0, so that
     several pivots vanish and the symbol meets itself in later pivots (poles, exact
-    cancellations of series coefficients).  Against exact rational functions of t on
-    every system that reaches the series pass: a nonsingular matrix gives the exact
-    limit (and determinant), a singular one SINGULAR; the truncated series may give up
-    (SYMBOLIC_RANGE) on at most 1 % of them, never with a wrong result."""
-    rng = np.random.default_rng(40 + k)
-    seen = nonsingular = gave_up = 0
-    for trial in range(700):
+    cancellations of series coefficients).  Every system whose exact elimination meets a
+    zero pivot is checked against exact rational functions of t -- also those where
+    double arithmetic leaves a rounding residue in place of the zero, which the numeric
+    pass must hand to the series pass (residue_pivot): a nonsingular matrix gives the
+    exact limit (and determinant), a singular one SINGULAR; the truncated series may give
+    up (SYMBOLIC_RANGE) on at most 1 % of them, never with a wrong result."""
+    rng = np.random.default_rng(47 + k)
+    seen = nonsingular = gave_up = residue = 0
+    for trial in range(1500):
         n = int(rng.integers(3, 17))
         pick = lambda vals: [int(v) for v in rng.choice(vals, n)]
         a, b, d, e, f = (pick([-2, -1, 0, 0, 1, 2]) for _ in range(5))
         c = pick([0, 0, 0, 1, -1])
         if k == 1:
             a, e = [0] * n, [0] * n
-        x, st, dm, dex, nf = oracle.symbolic(k, *(np.array(v, float) for v in (a, b, c, d, e, f)))
-        if nf == 0:
+        sym = exact.symbolic_solve(k, a, b, c, d, e, f)
+        if sym["nflag"] == 0:
             continue
         seen += 1
-        sym = exact.symbolic_solve(k, a, b, c, d, e, f)
+        x, st, dm, dex, nf = oracle.symbolic(k, *(np.array(v, float) for v in (a, b, c, d, e, f)))
+        _, st_num = oracle.npdm(*(np.array(v, float) for v in (a, b, c, d, e, f)))
+        residue += st_num != "ZERO_PIVOT"
         if sym["status"] == "SINGULAR":
             assert st == "SINGULAR", (trial, st)
             continue
@@ -253,6 +257,8 @@ def test_symbolic_vs_exact_with_many_zero_pivots(k):
         assert abs(dm * 2.0 ** dex - float(sym["det"])) <= 1e-9 * abs(float(sym["det"])), trial
     assert nonsingular >= 50 and seen - nonsingular >= 50
     assert gave_up <= nonsingular // 100
+    if k == 2:
+        assert residue >= 1      # the draw holds a residue pivot (the numeric pass is not 0)
 
 
 def _golden_cases():
@@ -453,6 +459,60 @@ def test_hotelling_bodewig_fixed_point_equation():
         for i in range(0, n - j):
             got[i, i + j] = X1[j, i]
     assert np.allclose(got, np.triu(np.tril(want, n), 0), atol=1e-14)
+
+
+def _band_of(M, w, lower):
+    """M with everything outside its w stored diagonals (lower: i - j in [0, w);
+    upper: j - i in [0, w)) set to zero."""
+    n = M.shape[0]
+    i, j = np.indices((n, n))
+    off = (i - j) if lower else (j - i)
+    return np.where((off >= 0) & (off < w), M, 0.0)
+
+
+@pytest.mark.parametrize("lower", [True, False])
+@pytest.mark.parametrize("w", [2, 3, 5])
+def test_hotelling_bodewig_band_truncation_dense(lower, w):
+    """R5 with w < n (the array form of the Appendix): each step of Eq. (1),
+    X_{k+1} = X_k (2I - M X_k), computed densely and then cut to the w diagonals on M's
+    side, must equal the oracle's band-storage iteration after k = 1 .. 4 steps.  The
+    dense side keeps every product entry, so a band that is cut on the wrong side, keeps
+    one diagonal too many or too few, or reads a stored diagonal at the wrong offset
+    changes the result from the first or second step on.  Independently of Eq. (1)'s
+    form: for triangular M the iterate equals the band of M^{-1} from 2^k >= w on."""
+    for n in (12, 16, 20):
+        rng = np.random.default_rng(100 * n + 10 * w + lower)
+        m1 = rng.uniform(-0.4, 0.4, n)
+        m2 = rng.uniform(-0.3, 0.3, n)
+        if lower:
+            m0 = None
+            M = np.eye(n) + np.diag(m1[1:], -1) + np.diag(m2[2:], -2)
+        else:
+            m0 = rng.uniform(1.5, 2.5, n) * rng.choice([-1.0, 1.0], n)
+            M = np.diag(m0) + np.diag(m1[:-1], 1) + np.diag(m2[:-2], 2)
+        X = np.diag(1.0 / np.diag(M))
+        for k in range(1, 5):
+            X = _band_of(X @ (2.0 * np.eye(n) - M @ X), w, lower)
+            Xb, it, _ = oracle.hb(w, lower, m0, m1, m2, max_it=k, tol=0.0)
+            assert it == k or (it < k and np.array_equal(*(
+                oracle.hb(w, lower, m0, m1, m2, max_it=m, tol=0.0)[0] for m in (it, it - 1))))
+            got = np.zeros((n, n))
+            for jo in range(w):
+                for i in range(n):
+                    j = i - jo if lower else i + jo
+                    if 0 <= j < n:
+                        got[i, j] = Xb[jo, i]
+            assert np.abs(got - X).max() <= 1e-13 * np.abs(X).max(), (n, k)
+            # M is triangular, so the band of a product of such matrices depends only on
+            # the bands of the factors, and the error E_k = I - M X_k (strictly
+            # triangular, nonzero from the first off-diagonal on) is squared by every
+            # step: X_k equals the w diagonals of M^{-1} exactly when 2^k >= w.
+            band_inv = _band_of(np.linalg.inv(M), w, lower)
+            gap = np.abs(X - band_inv).max() / np.abs(band_inv).max()
+            if 2 ** k >= w:
+                assert gap <= 1e-13, (n, k, gap)
+            else:
+                assert gap > 1e-6, (n, k, gap)
 
 
 def test_sip_algorithm1_and_full_width_hb_one_iteration():
