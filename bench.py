@@ -674,9 +674,56 @@ def adjoint_workload(dev):
     return out
 
 
+def symbolic_workload(dev):
+    """SPDM on one ADI sweep (2048 PD systems of n = 2048, r = 2, y-sweep: interleaved)
+    with an exact zero pivot planted in 0 %, 1 % and 10 % of the systems (row j of a
+    planted system gets a_j = b_j = c_j = 0, so its pivot mu_j is 0 in any arithmetic;
+    f = A x_true).  Planted systems take the Laurent-series fix-up (one warp each, dense
+    double-double series from row j on); the share of the fix-up in the solve time is
+    the time beyond the unplanted solve."""
+    import torch
+    import paper_1804_09666_gb300 as band
+    grid = GRID
+    B = synth.cfg1(r=2.0, k=2, sweep="y", grid=grid)
+    n, nsys = B["n"], B["nsys"]
+    xt = B["x_true"].reshape(n, nsys)
+    units = n * nsys
+    out = {"workload": "SPDM, ADI y-sweep r = 2, %d PD systems of n = %d, exact zero pivots "
+                       "planted" % (nsys, n), "unit": UNIT}
+    base_ms = None
+    for frac in (0.0, 0.01, 0.1):
+        D = {q: B[q].reshape(n, nsys).copy() for q in "abcde"}
+        rng = np.random.default_rng(90 + int(1000 * frac))
+        planted = rng.choice(nsys, size=int(round(frac * nsys)), replace=False)
+        rows = rng.integers(4, n - 4, size=len(planted))
+        for sy, j in zip(planted, rows):
+            D["a"][j, sy] = D["b"][j, sy] = D["c"][j, sy] = 0.0
+        f = synth.band_matvec(2, D["a"], D["b"], D["c"], D["d"], D["e"], xt)
+        d = {q: torch.from_numpy(D[q]).to(dev) for q in "abcde"}
+        ft = torch.from_numpy(f).to(dev)
+        x = torch.empty_like(ft)
+        res = {}
+
+        def run():
+            res["x"], res["st"] = band.solve(*(d[q] for q in "abcde"), ft, method="spdm", x=x)
+        ms = _time(run, reps=3, warm=1)
+        xg = res["x"].cpu().numpy()
+        err = np.abs(xg - xt).max(0) / np.abs(xt).max(0)
+        key = "planted_%g%%" % (100 * frac)
+        out[key] = {"systems_planted": int(len(planted)), "value": units / (ms * 1e-3), "ms": ms,
+                    "status_not_ok": int((res["st"] != 0).sum()),
+                    "max_rel_err_vs_manufactured": float(err.max()),
+                    "max_rel_err_planted": float(err[planted].max()) if len(planted) else None}
+        if frac == 0.0:
+            base_ms = ms
+        else:
+            out[key]["fixup_share"] = max(0.0, (ms - base_ms) / ms)
+    return out
+
+
 EXTRA_WORKLOADS = {"ragged": "ragged_workload", "small_batch": "small_batch_workload",
                    "precision": "precision_workload", "adjoint": "adjoint_workload",
-                   "sip": "sip_workload"}
+                   "sip": "sip_workload", "symbolic": "symbolic_workload"}
 
 
 # ---------------------------------------------------------------------- main
@@ -799,7 +846,8 @@ def main():
     if rank == 0 and world == 1 and not args.no_extras and args.grid == GRID:
         line["workloads"] = {"ragged": ragged_workload(dev), "small_batch": small_batch_workload(dev),
                              "precision": precision_workload(dev),
-                             "adjoint": adjoint_workload(dev), "sip": sip_workload(dev)}
+                             "adjoint": adjoint_workload(dev), "sip": sip_workload(dev),
+                             "symbolic": symbolic_workload(dev)}
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         line["cpu_baseline"] = cpu_baseline(W)
     if rank == 0:

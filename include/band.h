@@ -13,8 +13,8 @@
  *   SIP          the Stone method with ILU(0) (Sec. 2, Algorithm 1), optionally with
  *                Hotelling-Bodewig inverses in place of the substitutions (Remark of
  *                Sec. 2; Eq. (1) of the Appendix).
- * The paper solves N independent systems "independently (or in parallel)" per ADI
- * time step (Sec. 1); every call here solves a batch of such systems.
+ * In the paper's ADI time step (Sec. 1) the systems of one sweep, one per grid line,
+ * do not depend on one another; every call here solves a batch of such systems.
  *
  * Storage.  A system of n rows is given by five row-aligned diagonals
  *   a[i] = A[i][i-2], b[i] = A[i][i-1], c[i] = A[i][i], d[i] = A[i][i+1], e[i] = A[i][i+2]
@@ -158,7 +158,8 @@ enum {
   BAND_OP_FACTOR = 1,     /* band_factor: returns the size of the factor buffer */
   BAND_OP_SIP = 2,        /* band_sip (uses sip_width) */
   BAND_OP_REFINE = 3,     /* band_refine_solve */
-  BAND_OP_ADJOINT = 4     /* band_adjoint */
+  BAND_OP_ADJOINT = 4,    /* band_adjoint */
+  BAND_OP_DET = 5         /* band_det */
 };
 size_t band_workspace_size(const band_desc* desc, int32_t op, int32_t method, int32_t sip_width);
 
@@ -166,6 +167,14 @@ size_t band_workspace_size(const band_desc* desc, int32_t op, int32_t method, in
  * the same sweep with an exact zero-pivot test, after which only the flagged
  * systems are redone in truncated Laurent arithmetic in t and evaluated at t -> 0;
  * their determinant limit decides BAND_ERR_SINGULAR).
+ * The symbolic fix-up runs one warp per flagged system; its series carry
+ * double-double coefficients of t^-15 .. t^4, and a system that runs out of that
+ * window is redone with t^-15 .. t^16 (BAND_ERR_SYMBOLIC_RANGE beyond).  A coefficient
+ * that comes out below 2^-80 of the magnitude of the terms it was summed from is taken
+ * as exactly zero (rounding residue of an exact cancellation).  The workspace holds
+ * the series rows of min(nsys, 152) flagged systems at a time (one per SM of a GB300;
+ * 1584 * n bytes each); a larger workspace lets more of them run at once, up to
+ * min(nsys, 1216).
  * diag[5] = {a, b, c, d, e} device pointers (a, e unused and may be NULL for TD).
  * factors: NULL for the fused path, or a buffer filled by band_factor() for the same
  * desc and diagonals (then only NTDM/NPDM).  ws: device workspace of ws_bytes >=
@@ -259,6 +268,26 @@ band_status band_adjoint(const band_desc* desc, int32_t method, const void* fact
                          const void* const diag[5], const void* x, const void* w,
                          void* const grad_diag[5], void* grad_f, int32_t* sys_status,
                          void* ws, size_t ws_bytes, void* stream);
+
+/* Determinant of every system in O(n) (Sec. 3.2, Remark 1: the symbolic algorithm
+ * yields det A as the limit of the product of its pivots), FP64 only.
+ * desc->half_bw (or desc->hbw per system) gives the bandwidth; the schedule fields are
+ * ignored; id lists (desc->systems) are not accepted.  diag as for band_solve.
+ * Output per system s: det A = det_mant[s] * 2^det_exp[s], with 0.5 <= |det_mant[s]| < 1
+ * (device arrays of nsys entries), and sys_status[s] (required):
+ *   BAND_OK              the product of the pivots of the NPDM / NTDM factorisation, or,
+ *                        for a system whose factorisation meets a pivot that is exactly
+ *                        zero, the limit t -> 0 of the product of the pivots of the
+ *                        symbolic factorisation (zero pivots replaced by t, as STDM /
+ *                        SPDM do), i.e. the product of the pivots' leading coefficients;
+ *   BAND_ERR_SINGULAR    that limit is 0 (det_mant = 0, det_exp = 0);
+ *   BAND_ERR_SYMBOLIC_RANGE  the Laurent window ran out (det_mant = 0);
+ *   BAND_ERR_NONFINITE   an Inf or NaN entered the product.
+ * Accuracy: the rounding of n pivots, about n ulps relative, more where the pivots
+ * grow (no pivoting).  ws: band_workspace_size(desc, BAND_OP_DET, 0, 0) bytes. */
+band_status band_det(const band_desc* desc, const void* const diag[5], double* det_mant,
+                     int64_t* det_exp, int32_t* sys_status, void* ws, size_t ws_bytes,
+                     void* stream);
 
 /* NTDM / NPDM solve for callers that cannot allocate device memory (the paper has
  * no counterpart).  Some callers cannot allocate where they solve: code that must not

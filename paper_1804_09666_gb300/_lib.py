@@ -24,12 +24,12 @@ F64, F32 = 0, 1
 SCHED_AUTO, SCHED_THREAD, SCHED_TWO_SIDED, SCHED_PARTITIONED = 0, 1, 2, 3
 TUNE_JOINT = 1
 # BAND_OP_*
-OP_SOLVE, OP_FACTOR, OP_SIP, OP_REFINE, OP_ADJOINT = range(5)
+OP_SOLVE, OP_FACTOR, OP_SIP, OP_REFINE, OP_ADJOINT, OP_DET = range(6)
 
 EXPORTS = ("band_workspace_size", "band_solve", "band_factor", "band_sip", "band_refine_solve",
            "band_adjoint", "band_status_str", "band_version", "band_fp64_fma_rate",
            "band_solve_batch", "band_solve_static", "band_plan_ragged", "band_autotune",
-           "band_autotune_reset")
+           "band_autotune_reset", "band_det")
 MAX_BATCH = 64
 
 
@@ -76,7 +76,9 @@ def load(path=None):
     lib.band_sip.argtypes = [D, DIAG5, P, P, dbl, i32, i32, i32, dbl, P, P, P, P, sz, P]
     lib.band_refine_solve.argtypes = [D, DIAG5, P, P, dbl, i32, P, P, P, sz, P]
     lib.band_adjoint.argtypes = [D, i32, P, DIAG5, P, P, DIAG5, P, P, P, sz, P]
-    for name in ("band_solve", "band_factor", "band_sip", "band_refine_solve", "band_adjoint"):
+    lib.band_det.argtypes = [D, DIAG5, P, P, P, P, sz, P]
+    for name in ("band_solve", "band_factor", "band_sip", "band_refine_solve", "band_adjoint",
+                 "band_det"):
         getattr(lib, name).restype = ct.c_int
     lib.band_status_str.argtypes = [i32]
     lib.band_status_str.restype = ct.c_char_p

@@ -134,6 +134,38 @@ def solve(a, b, c, d, e, f, method="npdm", x=None, status=None, factors=None, ws
     return x, status
 
 
+def det(a, b, c, d, e, half_bw=2, status=None):
+    """Determinant of every system of a uniform FP64 batch (Sec. 3.2, Remark 1).
+
+    Returns (mant float64[nsys], exp int64[nsys], status int32[nsys]) with
+    det = mant * 2**exp; systems whose factorisation meets an exact zero pivot take the
+    symbolic limit (status SINGULAR when it is 0).  a, e are ignored for half_bw 1.
+    """
+    lib = L.load()
+    _check_same(c, a if half_bw == 2 else None, b, d, e if half_bw == 2 else None)
+    if c.dtype != torch.float64:
+        raise ValueError("band_det takes float64 diagonals")
+    desc = desc_for(c, half_bw)
+    nsys = c.shape[1]
+    mant = torch.empty(nsys, dtype=torch.float64, device=c.device)
+    ex = torch.empty(nsys, dtype=torch.int64, device=c.device)
+    status = _status_out(status, nsys, c.device)
+    ws = _workspace(lib.band_workspace_size(ct.byref(desc), L.OP_DET, 0, 0), c.device)
+    code = lib.band_det(ct.byref(desc), _diag5(a, b, c, d, e), _ptr(mant), _ptr(ex), _ptr(status),
+                        _ptr(ws), _bytes(ws), _stream())
+    L.check(code, "band_det")
+    return mant, ex, status
+
+
+def slogdet(a, b, c, d, e, half_bw=2):
+    """(sign, log|det|, status) of every system, as torch.linalg.slogdet reports it
+    (sign 0 and log|det| = -inf for a singular system)."""
+    mant, ex, status = det(a, b, c, d, e, half_bw)
+    sign = torch.sign(mant)
+    logabs = torch.log(mant.abs()) + ex.to(torch.float64) * 0.6931471805599453
+    return sign, logabs, status
+
+
 def factor(a, b, c, d, e, method="npdm", status=None):
     """LU factors (opaque uint8 buffer) for repeated solves and the adjoint."""
     lib = L.load()

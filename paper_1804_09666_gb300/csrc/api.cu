@@ -12,7 +12,8 @@ namespace band {
 
 // Workspace of band_solve.  Numeric methods: alpha and beta rows.  Symbolic methods:
 // alpha, beta and z rows, the flagged-system counter and list, and the Laurent-series
-// rows of up to kMaxFixSlots flagged systems redone at a time.
+// rows of min(nsys, kFixSlots) flagged systems redone at a time (the last region, so
+// that a larger workspace holds more of them; see fix_slots).
 // The partitioned schedule adds the rows of z (always: f stays intact until a failed
 // system has been redone) and of the coupling columns' z, all chunk-major.
 SolveWs carve_solve(const band_desc* d, int32_t method, void* base, size_t* bytes) {
@@ -33,11 +34,20 @@ SolveWs carve_solve(const band_desc* d, int32_t method, void* base, size_t* byte
     if (!w.zs) w.zs = c.take(rows);
     w.count = c.take(sizeof(unsigned long long));
     w.list = c.take(sizeof(int64_t) * (size_t)(d->nsys > 0 ? d->nsys : 1));
-    w.nslots = d->nsys < kMaxFixSlots ? d->nsys : kMaxFixSlots;
+    w.nslots = d->nsys < kFixSlots ? d->nsys : kFixSlots;
     w.slots = c.take((size_t)w.nslots * symbolic_slot_bytes(d->n));
   }
   *bytes = c.size();
   return w;
+}
+
+// Fix-up slots a workspace of ws_bytes holds: the stated ones plus as many more as fit
+// behind them, at most min(nsys, kFixSlotsMax).
+int64_t fix_slots(const band_desc* d, const SolveWs& w, size_t need, size_t ws_bytes) {
+  int64_t n = w.nslots;
+  if (ws_bytes > need) n += (int64_t)((ws_bytes - need) / symbolic_slot_bytes(d->n));
+  const int64_t cap = d->nsys < kFixSlotsMax ? d->nsys : kFixSlotsMax;
+  return n < cap ? n : cap;
 }
 
 struct FactorBuf {
@@ -193,11 +203,22 @@ band_status make_direct(const band_desc* desc, int32_t method, const void* const
     r->d64.fix_list = nullptr;
   } else {
     r->sym.fix_count_mut = w.count;
-    r->sym.args = SymArgs{L, (const double*)diag[0], (const double*)diag[1],
-                          (const double*)diag[2], (const double*)diag[3],
-                          (const double*)diag[4], (const double*)f, (double*)x, sys_status,
-                          (const unsigned long long*)w.count, (const int64_t*)w.list, w.slots,
-                          w.nslots, desc->n, nullptr, nullptr};
+    SymArgs& sa = r->sym.args;
+    sa = SymArgs{};
+    sa.L = L;
+    sa.a = (const double*)diag[0];
+    sa.b = (const double*)diag[1];
+    sa.c = (const double*)diag[2];
+    sa.d = (const double*)diag[3];
+    sa.e = (const double*)diag[4];
+    sa.f = (const double*)f;
+    sa.x = (double*)x;
+    sa.status = sys_status;
+    sa.fix_count = (const unsigned long long*)w.count;
+    sa.fix_list = (const int64_t*)w.list;
+    sa.slot_mem = w.slots;
+    sa.nslots = fix_slots(desc, w, need, ws_bytes);
+    sa.nmax = desc->n;
   }
   return BAND_OK;
 }
@@ -215,6 +236,7 @@ size_t band_workspace_size(const band_desc* desc, int32_t op, int32_t method, in
     case BAND_OP_SIP: return sip_workspace_bytes(desc, sip_width);
     case BAND_OP_REFINE: return refine_workspace_bytes(desc);
     case BAND_OP_ADJOINT: return adjoint_workspace_bytes(desc);
+    case BAND_OP_DET: return det_workspace_bytes(desc);
     default: return 0;
   }
 }

@@ -24,6 +24,7 @@
 #include "partition.cuh"
 #include "sip_impl.cuh"
 #include "sweeps.cuh"
+#include "symbolic.cuh"
 
 namespace band {
 namespace {
@@ -65,7 +66,7 @@ struct SymItem {
 struct SymTable {
   int32_t count;
   int32_t pad;
-  int64_t total;     // threads
+  int64_t total;     // warps (slots)
   SymItem it[BAND_MAX_BATCH];
 };
 
@@ -144,17 +145,20 @@ __global__ void __launch_bounds__(32 * kBatchWarps, BATCH_MIN_BLOCKS) k_batch(co
   else if (s < b.u.sip.L.nsys) sip_literal(b.u.sip, s, nullptr);
 }
 
-__global__ void __launch_bounds__(64) k_symbolic_batch(const __grid_constant__ SymTable t) {
-  const int64_t g = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+// the symbolic fix-ups of all problems: warp g serves slot g - slot0 of its problem
+constexpr int kSymWarps = 4;
+__global__ void __launch_bounds__(32 * kSymWarps) k_symbolic_batch(const __grid_constant__ SymTable t) {
+  __shared__ lser::dd stage[kSymWarps][128];
+  const int64_t g = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
   if (g >= t.total) return;
   int j = 0;
   while (j + 1 < t.count && t.it[j + 1].slot0 <= g) ++j;
   const SymArgs& p = t.it[j].a;
   const int64_t slot = g - t.it[j].slot0;
   const unsigned long long count = *p.fix_count;
-  Ser* mem = reinterpret_cast<Ser*>(p.slot_mem) + slot * 3 * p.nmax;
+  const lser::SlotView sv = lser::slot_view(p, slot);
   for (unsigned long long item = slot; item < count; item += p.nslots)
-    symbolic_one(p, p.fix_list[item], mem);
+    lser::symbolic_warp(p, p.fix_list[item], sv, stage[threadIdx.x >> 5]);
 }
 
 // the deferred residual and decision of the SIP problems (blockIdx.y: the problem)
@@ -321,7 +325,7 @@ extern "C" band_status band_solve_batch(const band_problem* in, int32_t count, v
   k_batch<<<(unsigned)((warps + kBatchWarps - 1) / kBatchWarps), 32 * kBatchWarps, smem, st>>>(t);
   if (cudaGetLastError() != cudaSuccess) return BAND_ERR_CUDA;
   if (sym.count > 0 && slots > 0) {
-    k_symbolic_batch<<<(unsigned)((slots + 63) / 64), 64, 0, st>>>(sym);
+    k_symbolic_batch<<<(unsigned)((slots + kSymWarps - 1) / kSymWarps), 32 * kSymWarps, 0, st>>>(sym);
     if (cudaGetLastError() != cudaSuccess) return BAND_ERR_CUDA;
   }
   if (tail.count > 0) {

@@ -98,10 +98,26 @@ __device__ __forceinline__ void set_status(int32_t* st, int64_t s, int32_t v) {
   if (st) st[s] = v;
 }
 
+// Biased binary exponent of a value (0 for zero, all ones for Inf / NaN), by integer
+// operations.
+__device__ __forceinline__ int expo_of(double v) {
+  return (int)(((unsigned)__double2hiint(v) >> 20) & 0x7ffu);
+}
+__device__ __forceinline__ int expo_of(float v) { return (int)((__float_as_uint(v) >> 23) & 0xffu); }
+
 // Gaussian elimination with partial pivoting on an NU x NU system (augmented column
-// NU), fully unrolled: row exchanges are selects, so M stays in registers.
+// NU), fully unrolled: row exchanges are selects, so M stays in registers.  Returns
+// false on a zero pivot, and with guard > 0 also on a pivot whose binary exponent lies
+// guard or more below that of the largest coefficient of M.
 template <typename T, int NU>
-__device__ __forceinline__ bool solve_small(T (&M)[4][5]) {
+__device__ __forceinline__ bool solve_small(T (&M)[4][5], int guard = 0) {
+  int top = 0;
+  if (guard > 0) {
+#pragma unroll
+    for (int r = 0; r < NU; ++r)
+#pragma unroll
+      for (int k = 0; k < NU; ++k) top = max(top, expo_of(M[r][k]));
+  }
 #pragma unroll
   for (int c = 0; c < NU; ++c) {
     int piv = c;
@@ -120,6 +136,7 @@ __device__ __forceinline__ bool solve_small(T (&M)[4][5]) {
       }
     }
     if (is_zero(M[c][c])) return false;
+    if (guard > 0 && expo_of(M[c][c]) + guard <= top) return false;
     const T inv = T(1) / M[c][c];
 #pragma unroll
     for (int r = c + 1; r < NU; ++r) {

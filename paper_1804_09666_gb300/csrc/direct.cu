@@ -18,6 +18,7 @@
 #include "kernels.h"
 #include "partition.cuh"
 #include "sweeps.cuh"
+#include "symbolic.cuh"
 
 namespace band {
 
@@ -277,35 +278,31 @@ template cudaError_t launch_fsolve<double>(const FactoredArgs<double>&, int, cud
 template cudaError_t launch_fsolve<float>(const FactoredArgs<float>&, int, cudaStream_t);
 
 // ---------------------------------------------------------------------------
-// STDM / SPDM fix-up: the systems whose sweep met an exact zero pivot are redone in
-// truncated Laurent arithmetic in one symbol t (every zero pivot becomes t, i.e.
-// c_i -> c_i + t, so the sweep is the exact LU of A(t) = A + t sum e_i e_i^T and
-// x(t) -> A^{-1} f as t -> 0 when A is nonsingular).  A series holds the
-// coefficients of t^-SP .. t^SP and is known for exponents below `hi`.
-//   * a pivot with no known nonzero coefficient is a zero pivot and becomes t;
-//   * det A = lim prod mu_i(t): V = sum of the pivots' valuations; V > 0 -> det 0
-//     (SINGULAR), V = 0 -> product of the leading coefficients, V < 0 impossible in
-//     exact arithmetic (SYMBOLIC_RANGE);
-//   * x(t) is analytic at 0 for nonsingular A, so the negative powers of each x_i are
-//     rounding residue and are cleared; x_i = its t^0 coefficient;
-//   * a pole deeper than t^-SP, or an x_i whose t^0 term is unknown, is SYMBOLIC_RANGE.
+// STDM / SPDM fix-up of the systems whose numeric sweep met an exact zero pivot:
+// Laurent series in one symbol t, one warp per system (symbolic.cuh).  Warp w of the
+// launch takes the flagged systems w, w + nslots, ... of the list; each warp owns one
+// slot of series rows in the workspace.
 // ---------------------------------------------------------------------------
-__global__ void __launch_bounds__(64) k_symbolic_fixup(const SymArgs p) {
-  const int64_t slot = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+constexpr int kFixWarps = 4;
+
+__global__ void __launch_bounds__(32 * kFixWarps) k_symbolic_fixup(const SymArgs p) {
+  __shared__ lser::dd stage[kFixWarps][128];
+  const int64_t slot = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
   if (slot >= p.nslots) return;
   const unsigned long long count = *p.fix_count;
-  Ser* mem = reinterpret_cast<Ser*>(p.slot_mem) + slot * 3 * p.nmax;
+  const lser::SlotView sv = lser::slot_view(p, slot);
   for (unsigned long long item = slot; item < count; item += p.nslots)
-    symbolic_one(p, p.fix_list[item], mem);
+    lser::symbolic_warp(p, p.fix_list[item], sv, stage[threadIdx.x >> 5]);
 }
 
 cudaError_t launch_symbolic_fixup(const SymArgs& p, cudaStream_t st) {
   if (p.nslots <= 0) return cudaSuccess;
-  const int tb = 64;
-  k_symbolic_fixup<<<(unsigned)((p.nslots + tb - 1) / tb), tb, 0, st>>>(p);
+  const int64_t threads = p.nslots * 32;
+  const int tb = 32 * kFixWarps;
+  k_symbolic_fixup<<<(unsigned)((threads + tb - 1) / tb), tb, 0, st>>>(p);
   return cudaGetLastError();
 }
 
-size_t symbolic_slot_bytes(int64_t nmax) { return (size_t)3 * (size_t)nmax * sizeof(Ser); }
+size_t symbolic_slot_bytes(int64_t nmax) { return lser::slot_bytes(nmax); }
 
 }  // namespace band

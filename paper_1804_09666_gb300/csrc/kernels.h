@@ -8,9 +8,11 @@
 
 namespace band {
 
-constexpr int kSerPole = 4;                  // Laurent window t^-4 .. t^4 (symbolic fix-up)
-constexpr int kSerWidth = 2 * kSerPole + 1;
-constexpr int64_t kMaxFixSlots = 64;         // flagged systems redone concurrently
+// Symbolic fix-up: flagged systems redone at a time, one warp each.  The workspace that
+// band_workspace_size() states holds kFixSlots of them (one per SM of a GB300); a larger
+// workspace holds more, up to kFixSlotsMax (two warps per SM sub-partition).
+constexpr int64_t kFixSlots = 152;
+constexpr int64_t kFixSlotsMax = 1216;
 
 template <typename T>
 struct DirectArgs {
@@ -61,6 +63,7 @@ struct SymArgs {
   int64_t nslots, nmax;
   double* det_mant;       // optional per-system determinant (mantissa, base-2 exponent)
   long long* det_exp;
+  int32_t det_only;       // determinant only: no z, no backward sweep, x untouched
 };
 
 template <typename T> cudaError_t launch_direct(const DirectArgs<T>&, int kmode, cudaStream_t);
@@ -116,4 +119,5 @@ FactorPtrs factor_ptrs(const band_desc* d, const void* factors);
 size_t sip_workspace_bytes(const band_desc* d, int32_t width);
 size_t refine_workspace_bytes(const band_desc* d);
 size_t adjoint_workspace_bytes(const band_desc* d);
+size_t det_workspace_bytes(const band_desc* d);
 }  // namespace band

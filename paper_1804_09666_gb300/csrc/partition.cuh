@@ -52,10 +52,6 @@ constexpr int kPartMinRowsPerChunk = 8;
 template <typename T> struct TinyPivot;
 template <> struct TinyPivot<double> { static constexpr int value = 17; };   // < ~7.6e-6
 template <> struct TinyPivot<float> { static constexpr int value = 10; };    // < ~9.8e-4
-__device__ __forceinline__ int expo_of(double v) {
-  return (int)(((unsigned)__double2hiint(v) >> 20) & 0x7ffu);
-}
-__device__ __forceinline__ int expo_of(float v) { return (int)((__float_as_uint(v) >> 23) & 0xffu); }
 
 // The same guard for the interface's K x K pivot blocks: A (= I - X) counts as singular
 // when |det A| lies TinyPivot<T> binary orders per row below max(1, max |A_ij|)^K.  The

@@ -35,7 +35,32 @@ __device__ __forceinline__ void load_in(const DirectArgs<T>& p, int64_t q, RowIn
   }
 }
 
-// One row of the NPDM / NTDM forward recurrence.  Returns false on a zero pivot.
+// Symbolic methods (STDM / SPDM): a pivot that double arithmetic cannot tell from zero
+// goes to the series pass like an exact zero; the series pass, in double-double, decides
+// whether it is one.  mu_i = c_i - beta_{i-2} a_i - alpha_{i-1} gamma_i (gamma_i = b_i -
+// alpha_{i-2} a_i) is such a pivot when its binary exponent lies 40 or more below that of
+// the largest quantity that entered it: a_i, b_i, c_i, beta_{i-2} a_i, alpha_{i-1} gamma_i
+// and, for a cancellation inside gamma_i, alpha_{i-1} b_i and alpha_{i-1} alpha_{i-2} a_i (a
+// product's exponent taken as the sum of its factors').  On integer-valued systems with
+// exact zero pivots, fused multiply-adds leave the rounding error of alpha in place of an
+// exact zero far more often than separately rounded operations do.  Integer operations
+// only (the FP64 pipe is the scarce unit); TD passes a_i = alpha_{i-2} = beta_{i-2} = 0.
+constexpr int kResidueBits = 40;
+template <typename T>
+__device__ __forceinline__ bool residue_pivot(T, T, T, T, T, T, T, T) { return false; }
+template <>
+__device__ __forceinline__ bool residue_pivot<double>(double m, double ai, double bi, double ci,
+                                                      double al1, double al2, double be2,
+                                                      double g) {
+  const int ea1 = expo_of(al1) - 1023, ea = expo_of(ai);
+  int big = max(max(expo_of(bi), expo_of(ci)), ea);
+  big = max(big, ea1 + max(expo_of(g), expo_of(bi)));
+  big = max(big, max(expo_of(be2) - 1023 + ea, ea1 + expo_of(al2) - 1023 + ea));
+  return expo_of(m) + kResidueBits <= big;
+}
+
+// One row of the NPDM / NTDM forward recurrence.  Returns false on a zero pivot (for the
+// symbolic methods also on a pivot within rounding residue of zero, residue_pivot).
 template <typename T, int K>
 __device__ __forceinline__ bool forward_row(const DirectArgs<T>& p, int64_t i, int64_t n,
                                             int64_t q, int64_t w, T ai, T bi, T ci, T di, T ei,
@@ -48,6 +73,7 @@ __device__ __forceinline__ bool forward_row(const DirectArgs<T>& p, int64_t i, i
     const T g = fma(-al2, ai, bi);
     const T m = fma(-al1, g, fma(-be2, ai, ci));
     if (is_zero(m)) return false;
+    if (p.fix_list && residue_pivot<T>(m, ai, bi, ci, al1, al2, be2, g)) return false;
     const T r = rcp<T>(m);
     const T alv = fma(-be1, g, di) * r;
     const T bev = ei * r;
@@ -59,6 +85,7 @@ __device__ __forceinline__ bool forward_row(const DirectArgs<T>& p, int64_t i, i
   } else {
     const T m = fma(-al1, bi, ci);
     if (is_zero(m)) return false;
+    if (p.fix_list && residue_pivot<T>(m, T(0), bi, ci, al1, T(0), T(0), bi)) return false;
     const T r = rcp<T>(m);
     const T alv = di * r;
     const T zv = fma(-z1, bi, fi) * r;
@@ -369,7 +396,9 @@ __device__ __forceinline__ void twisted_one(const DirectArgs<T>& p, int64_t t, b
       M[0][0] = 1;    M[0][1] = tal1; M[0][2] = tz1;
       M[1][0] = bal1; M[1][1] = 1;    M[1][2] = bz1;
     }
-    if (!solve_small<T, K == 2 ? 4 : 2>(M)) {
+    // symbolic methods: an interface pivot within rounding residue of zero counts as
+    // zero (the system goes to the series pass, as for residue_pivot)
+    if (!solve_small<T, K == 2 ? 4 : 2>(M, p.fix_list ? kResidueBits : 0)) {
       fail = true;
     } else if (K == 2) {
       const T xm2 = M[0][4], xm1 = M[1][4], xm0 = M[2][4], xp1 = M[3][4];
@@ -440,165 +469,6 @@ __device__ __forceinline__ void twisted_one(const DirectArgs<T>& p, int64_t t, b
   if (active && !bottom && !redo && !to_fix)
     set_status(p.status, s, fail ? BAND_ERR_ZERO_PIVOT
                                  : ((bad || (split && o_bad)) ? BAND_ERR_NONFINITE : BAND_OK));
-}
-
-// ---------------------------------------------------------------------------
-// STDM / SPDM fix-up: a system whose sweep met an exact zero pivot is redone in
-// truncated Laurent arithmetic in one symbol t (every zero pivot becomes t, i.e.
-// c_i -> c_i + t, so the sweep is the exact LU of A(t) = A + t sum e_i e_i^T and
-// x(t) -> A^{-1} f as t -> 0 when A is nonsingular).  A series holds the
-// coefficients of t^-SP .. t^SP and is known for exponents below `hi`.
-//   * a pivot with no known nonzero coefficient is a zero pivot and becomes t;
-//   * det A = lim prod mu_i(t): V = sum of the pivots' valuations; V > 0 -> det 0
-//     (SINGULAR), V = 0 -> product of the leading coefficients, V < 0 impossible in
-//     exact arithmetic (SYMBOLIC_RANGE);
-//   * x(t) is analytic at 0 for nonsingular A, so the negative powers of each x_i are
-//     rounding residue and are cleared; x_i = its t^0 coefficient;
-//   * a pole deeper than t^-SP, or an x_i whose t^0 term is unknown, is SYMBOLIC_RANGE.
-// ---------------------------------------------------------------------------
-struct Ser {
-  double q[kSerWidth];
-  int hi;
-  int pad;
-};
-constexpr int SP = kSerPole;
-
-__device__ inline Ser ser_const(double v) {
-  Ser r;
-#pragma unroll
-  for (int k = 0; k < kSerWidth; ++k) r.q[k] = 0.0;
-  r.q[SP] = v;
-  r.hi = SP + 1;
-  r.pad = 0;
-  return r;
-}
-__device__ inline Ser ser_symbol() {
-  Ser r = ser_const(0.0);
-  r.q[SP + 1] = 1.0;
-  return r;
-}
-__device__ inline int ser_val(const Ser& s) {
-  for (int k = -SP; k < s.hi && k <= SP; ++k)
-    if (s.q[k + SP] != 0.0) return k;
-  return SP + 1;
-}
-__device__ inline int ser_veff(const Ser& s) {
-  const int v = ser_val(s);
-  return v <= SP ? v : s.hi;
-}
-__device__ inline Ser ser_sub(const Ser& x, const Ser& y) {
-  Ser r = ser_const(0.0);
-  r.hi = min(x.hi, y.hi);
-  for (int k = -SP; k < r.hi && k <= SP; ++k) r.q[k + SP] = x.q[k + SP] - y.q[k + SP];
-  return r;
-}
-__device__ inline Ser ser_mul(const Ser& x, const Ser& y, bool& err) {
-  Ser r = ser_const(0.0);
-  const int vx = ser_veff(x), vy = ser_veff(y);
-  r.hi = min(SP + 1, min(vx + y.hi, vy + x.hi));
-  for (int i = -SP; i < x.hi && i <= SP; ++i) {
-    const double xv = x.q[i + SP];
-    if (xv == 0.0) continue;
-    for (int j = -SP; j < y.hi && j <= SP; ++j) {
-      const double pv = xv * y.q[j + SP];
-      if (pv == 0.0) continue;
-      const int k = i + j;
-      if (k >= r.hi) continue;
-      if (k < -SP) { err = true; continue; }
-      r.q[k + SP] += pv;
-    }
-  }
-  return r;
-}
-__device__ inline Ser ser_div(const Ser& x, const Ser& y, bool& err) {
-  Ser r = ser_const(0.0);
-  const int vy = ser_val(y);
-  if (vy > SP) { err = true; r.hi = -SP; return r; }
-  const int vx = ser_val(x);
-  if (vx > SP) { r.hi = min(SP + 1, x.hi - vy); return r; }
-  const int v = vx - vy;
-  r.hi = min(SP + 1, v + min(x.hi - vx, y.hi - vy));
-  if (v < -SP) { err = true; return r; }
-  const double inv = 1.0 / y.q[vy + SP];
-  for (int k = v; k < r.hi; ++k) {
-    double acc = x.q[k + vy + SP];
-    for (int j = 1; k - j >= v; ++j) acc -= y.q[vy + j + SP] * r.q[k - j + SP];
-    r.q[k + SP] = acc * inv;
-  }
-  return r;
-}
-
-
-// One flagged system s, series rows in `mem` (3 * nmax series).
-__device__ inline void symbolic_one(const SymArgs& p, int64_t t, Ser* mem) {
-  const int64_t s = p.L.sys(t);     // t: position in the batch, s: the system id
-
-  const int64_t n = p.L.rows(s);
-  const int K = p.L.kband(s);
-  const int64_t q0 = p.L.base(s), es = p.L.stride();
-  Ser* AL = mem;
-  Ser* BE = mem + p.nmax;
-  Ser* Z = mem + 2 * p.nmax;
-  bool err = false;
-  int V = 0;
-  double dmant = 1.0;
-  long long dexp = 0;
-  for (int64_t i = 0; i < n; ++i) {
-    const int64_t q = q0 + i * es;
-    const Ser ai = ser_const((K == 2 && i >= 2) ? p.a[q] : 0.0);
-    Ser g = ser_const(i >= 1 ? p.b[q] : 0.0);
-    if (K == 2 && i >= 2) g = ser_sub(g, ser_mul(AL[i - 2], ai, err));
-    Ser m = ser_const(p.c[q]);
-    if (K == 2 && i >= 2) m = ser_sub(m, ser_mul(BE[i - 2], ai, err));
-    if (i >= 1) m = ser_sub(m, ser_mul(AL[i - 1], g, err));
-    if (ser_val(m) > SP) m = ser_symbol();
-    {
-      const int v = ser_val(m);
-      V += v;
-      int e2;
-      dmant *= frexp(m.q[v + SP], &e2);
-      dexp += e2;
-      int e3;
-      dmant = frexp(dmant, &e3);
-      dexp += e3;
-    }
-    Ser al = ser_const(0.0), be = ser_const(0.0);
-    if (i + 1 < n) {
-      Ser num = ser_const(p.d[q]);
-      if (K == 2 && i >= 1) num = ser_sub(num, ser_mul(BE[i - 1], g, err));
-      al = ser_div(num, m, err);
-    }
-    if (K == 2 && i + 2 < n) be = ser_div(ser_const(p.e[q]), m, err);
-    Ser zz = ser_const(p.f[q]);
-    if (K == 2 && i >= 2) zz = ser_sub(zz, ser_mul(Z[i - 2], ai, err));
-    if (i >= 1) zz = ser_sub(zz, ser_mul(Z[i - 1], g, err));
-    AL[i] = al;
-    BE[i] = be;
-    Z[i] = ser_div(zz, m, err);
-  }
-  Ser x1 = ser_const(0.0), x2 = ser_const(0.0);
-  bool bad = false;
-  for (int64_t i = n - 1; i >= 0; --i) {
-    Ser xi = Z[i];
-    if (i + 1 < n) xi = ser_sub(xi, ser_mul(AL[i], x1, err));
-    if (K == 2 && i + 2 < n) xi = ser_sub(xi, ser_mul(BE[i], x2, err));
-    for (int k = 0; k < SP; ++k) xi.q[k] = 0.0;
-    if (xi.hi <= 0) err = true;
-    const double xv = xi.q[SP];
-    p.x[q0 + i * es] = xv;
-    bad |= !isfinite(xv);
-    x2 = x1;
-    x1 = xi;
-  }
-  int32_t st = BAND_OK;
-  if (V > 0) st = BAND_ERR_SINGULAR;
-  else if (err || V < 0) st = BAND_ERR_SYMBOLIC_RANGE;
-  else if (bad) st = BAND_ERR_NONFINITE;
-  set_status(p.status, s, st);
-  if (p.det_mant) {
-    p.det_mant[s] = (V == 0) ? dmant : 0.0;
-    p.det_exp[s] = (V == 0) ? dexp : 0;
-  }
 }
 
 }  // namespace band

@@ -149,6 +149,15 @@ def test_bad_arguments_are_rejected_without_gpu(lib):
                             None) == L.ERR_ARG
     assert lib.band_adjoint(ct.byref(d), L.NPDM, None, full, 8, 8, L.DIAG5(None, 1, 2, 3, None), 8,
                             None, 8, 1 << 30, None) == L.ERR_ARG
+    # determinant: FP64 only, every output required, PD needs a and e, workspace checked
+    assert lib.band_det(ct.byref(_desc(dtype=L.F32)), full, 8, 8, 8, 8, 1 << 30, None) == L.ERR_ARG
+    assert lib.band_det(ct.byref(d), full, 8, 8, None, 8, 1 << 30, None) == L.ERR_ARG
+    assert lib.band_det(ct.byref(d), full, None, 8, 8, 8, 1 << 30, None) == L.ERR_ARG
+    assert lib.band_det(ct.byref(d), nul, 8, 8, 8, 8, 1 << 30, None) == L.ERR_ARG
+    assert lib.band_det(ct.byref(d), full, 8, 8, 8, 8, 16, None) == L.ERR_WORKSPACE
+    assert lib.band_det(ct.byref(_desc(nsys=0)), full, 8, 8, 8, 8, 0, None) == L.OK
+    # its workspace is the flagged-system counter and list
+    assert lib.band_workspace_size(ct.byref(d), L.OP_DET, 0, 0) >= 8 + 64 * 8
 
 
 def test_package_refuses_to_run_without_library(tmp_path):
