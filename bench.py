@@ -721,9 +721,58 @@ def symbolic_workload(dev):
     return out
 
 
+# The paper's single-system timings at N = 10^8 (Table 3, HybriLIT, one Xeon E5-2695v2
+# core, double precision): NPDM 2.7946627 s, NTDM 2.0525187 s.  Context only.
+PAPER_1E8_S = {"npdm": 2.7946627, "ntdm": 2.0525187}
+
+
+def single_system_workload(dev, n=100_000_000):
+    """One dominant system of n = 10^8 rows (the paper's largest N), PD by NPDM and TD by
+    NTDM, on the grid schedule (all SMs on one system), against the manufactured
+    solution.  The paper's one-core times at the same N are quoted for context."""
+    import torch
+    import paper_1804_09666_gb300 as band
+    out = {"workload": "one system of n = %d rows, dominant (cfg0 recipe), grid schedule" % n,
+           "unit": UNIT}
+    for k, method in ((2, "npdm"), (1, "ntdm")):
+        rng = np.random.default_rng(1804_09666 + 100 + k)
+        D = synth.dominant(rng, 1, n, k=k)
+        xt, f = synth.manufactured(rng, k, D, 1, n)
+        d = {q: torch.from_numpy(D[q]).to(dev) for q in "abcde"}
+        ft = torch.from_numpy(f).to(dev)
+        del D, f
+        xtd = torch.from_numpy(xt).to(dev)
+        del xt
+        x = torch.empty_like(ft)
+        desc = band.desc_for(ft, k, "grid")
+        ws = torch.empty(band.load().band_workspace_size(ct.byref(desc), 0, 1 if k == 2 else 0, 0),
+                         dtype=torch.uint8, device=dev)
+        res = {}
+
+        def run():
+            res["x"], res["st"] = band.solve(d["a"] if k == 2 else None, d["b"], d["c"], d["d"],
+                                             d["e"] if k == 2 else None, ft, method=method, x=x,
+                                             schedule="grid", ws=ws)
+        run()
+        torch.cuda.synchronize()
+        ms = _time(run, reps=5, warm=1)
+        err = float(((res["x"] - xtd).abs().max() / xtd.abs().max()).item())
+        flops = (19 if k == 2 else 9) * n
+        out[method] = {"value": n / (ms * 1e-3), "ms": ms, "status": int(res["st"].item()),
+                       "max_rel_err_vs_manufactured": err,
+                       "alg_GBps": (56 if k == 2 else 40) * n / (ms * 1e-3) / 1e9,
+                       "table7_TFLOPs": flops / (ms * 1e-3) / 1e12,
+                       "paper_one_core_s": PAPER_1E8_S[method],
+                       "paper_one_core_unknowns_per_s": n / PAPER_1E8_S[method]}
+        del d, ft, xtd, x, res
+        torch.cuda.empty_cache()
+    return out
+
+
 EXTRA_WORKLOADS = {"ragged": "ragged_workload", "small_batch": "small_batch_workload",
                    "precision": "precision_workload", "adjoint": "adjoint_workload",
-                   "sip": "sip_workload", "symbolic": "symbolic_workload"}
+                   "sip": "sip_workload", "symbolic": "symbolic_workload",
+                   "single": "single_system_workload"}
 
 
 # ---------------------------------------------------------------------- main
@@ -847,7 +896,8 @@ def main():
         line["workloads"] = {"ragged": ragged_workload(dev), "small_batch": small_batch_workload(dev),
                              "precision": precision_workload(dev),
                              "adjoint": adjoint_workload(dev), "sip": sip_workload(dev),
-                             "symbolic": symbolic_workload(dev)}
+                             "symbolic": symbolic_workload(dev),
+                             "single": single_system_workload(dev)}
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         line["cpu_baseline"] = cpu_baseline(W)
     if rank == 0:

@@ -140,6 +140,23 @@ typedef struct {
  *   its row's largest entry, or an interface block as close to singular, is handled
  *   like a zero pivot (the system is redone as above).  On dominant matrices no system
  *   is redone.  Chunk counts are 8 ... 256 (4 is not offered).
+ * BAND_SCHED_GRID: one system, or a few, over the whole GPU (the paper's single
+ *   systems of up to 10^8 rows, Table 3 and Table 5).  band_solve only, NTDM / NPDM,
+ *   uniform layouts, no stored factors, desc->chunks 0; the library cuts every system
+ *   into P chunks of at least 64 rows so that the batch fills one wave of 16 warps per
+ *   SM (P = 77824 / nsys on a GB300, fewer for short systems; one chunk below 128
+ *   rows).  Lane c eliminates chunk c as the partitioned schedule does and writes its
+ *   boundary rows' block row of the reduced system L_c y_{c-1} + y_c + U_c y_{c+1} = g_c
+ *   (y_c: the chunk's top and bottom 2 (PD) / 1 (TD) unknowns); block cyclic reduction
+ *   solves that system in ceil(log2 P) launches each way (2K x 2K blocks, partial
+ *   pivoting inside each block); every lane then back-substitutes its chunk.  About
+ *   2.4x NPDM's arithmetic per row plus the reduction's ~500 operations per chunk; x may
+ *   alias f.  A chunk pivot 2^-17 (FP64) / 2^-10 (FP32) below its row's largest entry,
+ *   or a reduction block as close to singular, ends the system with
+ *   BAND_ERR_ZERO_PIVOT (this schedule's elimination order met a pivot it cannot use;
+ *   another schedule may solve it); on diagonally dominant systems that does not
+ *   happen.  Workspace: five (PD) / four (TD) arrays of ceil(n / P) * P * nsys rows plus
+ *   ~450 B per chunk.  Other calls return BAND_ERR_ARG for this schedule.
  * BAND_SCHED_AUTO: TWO_SIDED for uniform-bandwidth solves with n >= 32 that are not a
  *   whole ragged packing (ragged id lists, i.e. size buckets, qualify) and, for
  *   NTDM/NPDM, whose x does not alias f; THREAD otherwise.  band_autotune replaces the
@@ -148,7 +165,8 @@ typedef enum {
   BAND_SCHED_AUTO = 0,
   BAND_SCHED_THREAD = 1,
   BAND_SCHED_TWO_SIDED = 2,
-  BAND_SCHED_PARTITIONED = 3
+  BAND_SCHED_PARTITIONED = 3,
+  BAND_SCHED_GRID = 4
 } band_schedule;
 
 /* Bytes of workspace that the operation `op` needs for `desc` (0 = none).  op is one

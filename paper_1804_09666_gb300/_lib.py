@@ -21,7 +21,7 @@ NTDM, NPDM, STDM, SPDM, AUTO_NUMERIC, AUTO_SYMBOLIC = range(6)
 # band_dtype
 F64, F32 = 0, 1
 # band_schedule
-SCHED_AUTO, SCHED_THREAD, SCHED_TWO_SIDED, SCHED_PARTITIONED = 0, 1, 2, 3
+SCHED_AUTO, SCHED_THREAD, SCHED_TWO_SIDED, SCHED_PARTITIONED, SCHED_GRID = 0, 1, 2, 3, 4
 TUNE_JOINT = 1
 # BAND_OP_*
 OP_SOLVE, OP_FACTOR, OP_SIP, OP_REFINE, OP_ADJOINT, OP_DET = range(6)

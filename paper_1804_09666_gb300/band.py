@@ -42,7 +42,7 @@ def _dtype_code(t):
 
 
 _SCHEDULES = {"auto": L.SCHED_AUTO, "thread": L.SCHED_THREAD, "two_sided": L.SCHED_TWO_SIDED,
-              "partitioned": L.SCHED_PARTITIONED}
+              "partitioned": L.SCHED_PARTITIONED, "grid": L.SCHED_GRID}
 
 
 def desc_for(ref, half_bw, schedule="auto", chunks=0):
@@ -109,8 +109,9 @@ def solve(a, b, c, d, e, f, method="npdm", x=None, status=None, factors=None, ws
     method: "npdm", "ntdm", "spdm", "stdm".  a, e are ignored (may be None) for TD.
     factors: a buffer from ``factor`` to reuse a factorisation (numeric methods).
     schedule: "auto", "thread" (one thread per system), "two_sided" (two threads per
-    system meeting in the middle) or "partitioned" (``chunks`` lanes per system, 8, 16,
-    32, 64, 128 or 256, 0 = chosen by the library); the last two without factors.
+    system meeting in the middle), "partitioned" (``chunks`` lanes per system, 8, 16,
+    32, 64, 128 or 256, 0 = chosen by the library) or "grid" (one system, or a few,
+    over the whole GPU; numeric methods); the last three without factors.
     """
     lib = L.load()
     m = _METHODS[method]

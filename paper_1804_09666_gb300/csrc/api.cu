@@ -148,7 +148,7 @@ int choose_parts(const band_desc* d, int max_parts) {
 band_status make_direct(const band_desc* desc, int32_t method, const void* const diag[5],
                         const void* f, void* x, int32_t* sys_status, void* ws, size_t ws_bytes,
                         DirectReq* r, int max_parts) {
-  if (!desc_ok(desc)) return BAND_ERR_ARG;
+  if (!desc_ok(desc) || desc->schedule == BAND_SCHED_GRID) return BAND_ERR_ARG;
   const int kmode = kmode_for(desc, method);
   if (kmode < 0) return BAND_ERR_ARG;
   if (is_symbolic(method) && desc->dtype != BAND_F64) return BAND_ERR_ARG;
@@ -231,7 +231,10 @@ size_t band_workspace_size(const band_desc* desc, int32_t op, int32_t method, in
   if (!desc_ok(desc)) return 0;
   size_t bytes = 0;
   switch (op) {
-    case BAND_OP_SOLVE: carve_solve(desc, method, nullptr, &bytes); return bytes;
+    case BAND_OP_SOLVE:
+      if (desc->schedule == BAND_SCHED_GRID) return grid_workspace_bytes(desc);
+      carve_solve(desc, method, nullptr, &bytes);
+      return bytes;
     case BAND_OP_FACTOR: return factor_bytes(desc);
     case BAND_OP_SIP: return sip_workspace_bytes(desc, sip_width);
     case BAND_OP_REFINE: return refine_workspace_bytes(desc);
@@ -268,6 +271,7 @@ band_status band_solve(const band_desc* desc, int32_t method, const void* factor
                           (const float*)f, (float*)x, sys_status};
     return cuda_status(launch_fsolve<float>(p, kmode, st));
   }
+  if (desc->schedule == BAND_SCHED_GRID) return grid_solve(desc, method, diag, f, x, sys_status, ws, ws_bytes, st);
   DirectReq r;
   const band_status v = make_direct(desc, method, diag, f, x, sys_status, ws, ws_bytes, &r, 256);
   if (v != BAND_OK) return v;

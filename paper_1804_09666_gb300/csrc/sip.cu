@@ -483,7 +483,8 @@ cudaError_t launch_sip_tail(const SipArgs& p, int64_t nsys, cudaStream_t st) {
 band_status make_sip(const band_desc* desc, const void* const diag[5], const void* f, void* x,
                      double tol, int32_t max_it, int32_t width, int32_t* iters, double* resid,
                      int32_t* sys_status, void* ws, size_t ws_bytes, SipArgs* sa, SipWs* wout) {
-  if (!desc_ok(desc) || desc->dtype != BAND_F64) return BAND_ERR_ARG;
+  if (!desc_ok(desc) || desc->dtype != BAND_F64 || desc->schedule == BAND_SCHED_GRID)
+    return BAND_ERR_ARG;
   if (width < 0 || width > kMaxWidth || max_it < 0) return BAND_ERR_ARG;
   // id lists: Algorithm 1 with exact substitutions only, statuses indexed by id
   if (desc->systems && (width != 0 || !sys_status)) return BAND_ERR_ARG;
@@ -530,7 +531,8 @@ extern "C" band_status band_sip(const band_desc* desc, const void* const diag[5]
                                 void* x, double tol, int32_t max_it, int32_t width,
                                 int32_t hb_max_it, double hb_tol, int32_t* iters, double* resid,
                                 int32_t* sys_status, void* ws, size_t ws_bytes, void* stream) {
-  if (!desc_ok(desc) || desc->dtype != BAND_F64) return BAND_ERR_ARG;
+  if (!desc_ok(desc) || desc->dtype != BAND_F64 || desc->schedule == BAND_SCHED_GRID)
+    return BAND_ERR_ARG;
   if (width < 0 || width > kMaxWidth || max_it < 0 || hb_max_it < 0) return BAND_ERR_ARG;
   if (!(tol >= 0.0) || !(hb_tol >= 0.0)) return BAND_ERR_ARG;
   if (desc->nsys == 0) return BAND_OK;

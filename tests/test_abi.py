@@ -114,7 +114,10 @@ def test_bad_arguments_are_rejected_without_gpu(lib):
         (_desc(half_bw=2), L.NPDM, nul),          # PD without a, e
         (_desc(), 17, full),                      # unknown method
         (_desc(dtype=L.F32), L.SPDM, full),       # symbolic path is FP64 only
-        (_desc(schedule=4), L.NPDM, full),        # unknown schedule
+        (_desc(schedule=5), L.NPDM, full),        # unknown schedule
+        (_desc(schedule=L.SCHED_GRID), L.SPDM, full),          # grid: numeric methods only
+        (_desc(schedule=L.SCHED_GRID, chunks=8), L.NPDM, full),
+        (_desc(schedule=L.SCHED_GRID, offsets=8, total_rows=100), L.NPDM, full),  # uniform only
         (_desc(schedule=-1), L.NPDM, full),
         (_desc(chunks=8), L.NPDM, full),          # chunks without the partitioned schedule
         (_desc(schedule=L.SCHED_PARTITIONED, chunks=6), L.NPDM, full),   # not 4/8/16/32
@@ -149,6 +152,11 @@ def test_bad_arguments_are_rejected_without_gpu(lib):
                             None) == L.ERR_ARG
     assert lib.band_adjoint(ct.byref(d), L.NPDM, None, full, 8, 8, L.DIAG5(None, 1, 2, 3, None), 8,
                             None, 8, 1 << 30, None) == L.ERR_ARG
+    # the grid schedule is band_solve's alone
+    dg = _desc(schedule=L.SCHED_GRID)
+    assert lib.band_sip(ct.byref(dg), full, 8, 8, 1e-10, 10, 0, 30, 1e-12, None, None, None, 8,
+                        1 << 30, None) == L.ERR_ARG
+    assert lib.band_workspace_size(ct.byref(dg), L.OP_SOLVE, L.NPDM, 0) >= 5 * 64 * 128 * 8
     # determinant: FP64 only, every output required, PD needs a and e, workspace checked
     assert lib.band_det(ct.byref(_desc(dtype=L.F32)), full, 8, 8, 8, 8, 1 << 30, None) == L.ERR_ARG
     assert lib.band_det(ct.byref(d), full, 8, 8, None, 8, 1 << 30, None) == L.ERR_ARG
