@@ -11,7 +11,8 @@ arithmetic lives in ``band_oracle.c`` (plain C, compiled ``-O2
 ``exact.py``.
 
 Method names and readings follow Veneva & Ayriyan, arXiv:1804.09666:
-NTDM/NPDM (R1/R2, Sec. 1, Table 7), STDM/SPDM (R3, Sec. 1 and Sec. 3.2
+NTDM/NPDM (R1/R2, Sec. 1, Table 7), MNPDM (R2m, Sec. 1 and Sec. 3.2 Remark 2),
+STDM/SPDM (R3, Sec. 1 and Sec. 3.2
 Remark 1), ILU(0) (R4, Sec. 2), Hotelling-Bodewig (R5, Eq. (1)), SIP
 (R6, Algorithm 1), FP32 + refinement (R7) and the adjoint (R8).
 
@@ -54,6 +55,7 @@ def _load():
         i64, c_int, dbl = _ct.c_int64, _ct.c_int, _ct.c_double
         lib.orc_ntdm.argtypes = [i64, _D, _D, _D, _D, _D, _LL]
         lib.orc_npdm.argtypes = [i64, _D, _D, _D, _D, _D, _D, _D, _D, _LL]
+        lib.orc_mnpdm.argtypes = [i64, _D, _D, _D, _D, _D, _D, _D, _LL]
         lib.orc_gepp_band.argtypes = [i64, c_int, _D, _D, _D, _D, _D, _D, _D, _D]
         lib.orc_symbolic.argtypes = [i64, c_int, _D, _D, _D, _D, _D, _D, _D, _D, _LL,
                                      _ct.POINTER(c_int)]
@@ -73,7 +75,7 @@ def _load():
         lib.orc_batch.argtypes = [c_int, c_int, i64, i64, i64, i64, _I64, _I8,
                                   _D, _D, _D, _D, _D, _D, _D, _I32, dbl, c_int, c_int, c_int,
                                   dbl, _I32, _D, c_int]
-        for name in ("orc_ntdm", "orc_npdm", "orc_gepp_band", "orc_symbolic", "orc_ilu0",
+        for name in ("orc_ntdm", "orc_npdm", "orc_mnpdm", "orc_gepp_band", "orc_symbolic", "orc_ilu0",
                      "orc_hb", "orc_sip", "orc_refine", "orc_adjoint", "orc_batch"):
             getattr(lib, name).restype = c_int
         _lib = lib
@@ -132,6 +134,19 @@ def _diags(k, a, b, c, d, e, n):
     if e is None:
         e = z
     return a, b, c, d, e
+
+
+def mnpdm(a, b, c, d, e, f, count_ops=False):
+    """R2m MNPDM: the PD -> TD elimination of the nonzero outer entries, then R1.
+    Returns (x, status[, ops])."""
+    lib = _load()
+    n = len(c)
+    (a, pa), (b, pb), (c, pc), (d, pd), (e, pe), (f, pf) = map(_d, (a, b, c, d, e, f))
+    x = _zeros_like_n(n)
+    ops = _ct.c_longlong(0)
+    st = lib.orc_mnpdm(n, pa, pb, pc, pd, pe, pf, x.ctypes.data_as(_D),
+                       _ct.byref(ops) if count_ops else None)
+    return (x, STATUS[st], ops.value) if count_ops else (x, STATUS[st])
 
 
 def gepp_band(k, a, b, c, d, e, f):

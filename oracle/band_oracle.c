@@ -272,6 +272,63 @@ int orc_gepp_band(int64_t n, int k, const double* a, const double* b, const doub
 }
 
 /* ------------------------------------------------------------------------- */
+/* R2m -- MNPDM (Sec. 1: the PD method that takes the sparsity of the outer   */
+/* diagonals into account; Sec. 3.2 Remark 2: a Gaussian elimination turns   */
+/* the PD matrix into a TD one at 16 operations per row that carries nonzero  */
+/* outer entries), then R1 on the TD system.  The paper prints neither the    */
+/* elimination nor its order; reading: first, bottom-up, every nonzero e_i    */
+/* (column i+2) is eliminated with row i+1, which by then has no entry beyond */
+/* column i+2:                                                                */
+/*   m = e_i / D_{i+1};  B_i -= m a_{i+1};  C_i -= m B_{i+1};                  */
+/*   D_i -= m C_{i+1};  F_i -= m F_{i+1}          (1 + 8 operations);          */
+/* then, top-down, every nonzero a_i (column i-2) with row i-1, which by then */
+/* is tridiagonal:                                                            */
+/*   m = a_i / B_{i-1};  B_i -= m C_{i-1};  C_i -= m D_{i-1};                   */
+/*   F_i -= m F_{i-1}                              (1 + 6 operations),         */
+/* where (B, C, D, F) are the row's sub-, main and superdiagonal entries and  */
+/* right-hand side as they stand.  A row with both outer entries nonzero costs */
+/* 16 operations, a row 0 with only e (no column i-1) 7, a row with only a 7.  */
+/* A zero divisor (D_{i+1} or B_{i-1}) is ZERO_PIVOT, as is a zero pivot of   */
+/* R1 on the result.                                                          */
+/* ------------------------------------------------------------------------- */
+int orc_mnpdm(int64_t n, const double* a, const double* b, const double* c, const double* d,
+              const double* e, const double* f, double* x, long long* ops) {
+  if (n < 1) return ORC_ARG;
+  double* B = (double*)malloc(sizeof(double) * (size_t)n);
+  double* C = (double*)malloc(sizeof(double) * (size_t)n);
+  double* D = (double*)malloc(sizeof(double) * (size_t)n);
+  double* F = (double*)malloc(sizeof(double) * (size_t)n);
+  if (!B || !C || !D || !F) { free(B); free(C); free(D); free(F); return ORC_NOMEM; }
+  int st = ORC_OK;
+  for (int64_t i = n - 1; i >= 0; --i) {
+    B[i] = i >= 1 ? b[i] : 0.0;
+    C[i] = c[i];
+    D[i] = i + 1 < n ? d[i] : 0.0;
+    F[i] = f[i];
+    if (i + 2 < n && e[i] != 0.0) {
+      if (D[i + 1] == 0.0) { st = ORC_ZERO_PIVOT; break; }
+      double m = op_div(e[i], D[i + 1], ops);
+      if (i >= 1) B[i] = op_sub(B[i], op_mul(m, i + 1 >= 2 ? a[i + 1] : 0.0, ops), ops);
+      C[i] = op_sub(C[i], op_mul(m, B[i + 1], ops), ops);
+      D[i] = op_sub(D[i], op_mul(m, C[i + 1], ops), ops);
+      F[i] = op_sub(F[i], op_mul(m, F[i + 1], ops), ops);
+    }
+  }
+  for (int64_t i = 2; st == ORC_OK && i < n; ++i) {
+    if (a[i] == 0.0) continue;
+    if (B[i - 1] == 0.0) { st = ORC_ZERO_PIVOT; break; }
+    double m = op_div(a[i], B[i - 1], ops);
+    B[i] = op_sub(B[i], op_mul(m, C[i - 1], ops), ops);
+    C[i] = op_sub(C[i], op_mul(m, D[i - 1], ops), ops);
+    F[i] = op_sub(F[i], op_mul(m, F[i - 1], ops), ops);
+  }
+  if (st == ORC_OK) st = orc_ntdm(n, B, C, D, F, x, ops);
+  else for (int64_t i = 0; i < n; ++i) x[i] = NAN;
+  free(B); free(C); free(D); free(F);
+  return st;
+}
+
+/* ------------------------------------------------------------------------- */
 /* R3 -- SPDM / STDM: the R2 / R1 recurrences in which a pivot that is zero   */
 /* is replaced by a symbol t; every later quantity becomes a function of t    */
 /* and the solution is its limit t -> 0 (Sec. 1: the symbolic methods "only   */

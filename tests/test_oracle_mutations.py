@@ -57,6 +57,11 @@ MUTANTS = {
                            "int64_t off = lower ? j - i : i - j;\n  if (off < 0 || off >= w) return 0.0;"),
     "hb_update_one_diagonal_short": ("for (int mo = 0; mo < w; ++mo) {",
                                      "for (int mo = 0; mo < w - 1; ++mo) {"),
+    "mnpdm_e_elim_drops_b": ("if (i >= 1) B[i] = op_sub(B[i], op_mul(m, i + 1 >= 2 ? a[i + 1] : 0.0, ops), ops);",
+                             ""),
+    "mnpdm_a_elim_wrong_row": ("C[i] = op_sub(C[i], op_mul(m, D[i - 1], ops), ops);",
+                               "C[i] = op_sub(C[i], op_mul(m, C[i - 1], ops), ops);"),
+    "mnpdm_rhs_not_eliminated": ("F[i] = op_sub(F[i], op_mul(m, F[i + 1], ops), ops);", ""),
     "symbolic_residue_pivot_ignored": ("if (st == ORC_OK && residue_pivot(n, pa, b, c, fac)) st = ORC_ZERO_PIVOT;",
                                        ""),
     "cond1_not_transposed": ("if (orc_gepp_band(n, k, ta, tb, tc, td, te, y, z, NULL) != ORC_OK)",
