@@ -721,6 +721,46 @@ def symbolic_workload(dev):
     return out
 
 
+def mnpdm_workload(dev):
+    """PD systems whose outer diagonals are mostly zero (Sec. 3.2 Remark 2: K << N rows
+    carry them): 2048 dominant systems of n = 2048, off-diagonal magnitudes in [0.5, 1],
+    outer entries kept on 1 % of the rows; MNPDM against NPDM (one thread per system and
+    the automatic schedule) on the same matrices, interleaved."""
+    import torch
+    import paper_1804_09666_gb300 as band
+    nsys, n = 2048, 2048
+    rng = np.random.default_rng(1804_09666 + 200)
+    # off-diagonals bounded away from 0 (as a stencil's are): MNPDM divides by them
+    mag = lambda: rng.uniform(0.5, 1.0, (n, nsys)) * rng.choice([-1.0, 1.0], (n, nsys))
+    D = {q: mag() for q in "abde"}
+    keep = rng.random((n, nsys)) < 0.01
+    D["a"] = np.where(keep, D["a"], 0.0)
+    D["e"] = np.where(keep, D["e"], 0.0)
+    D["a"][:2] = D["b"][:1] = 0.0
+    D["d"][n - 1:] = D["e"][n - 2:] = 0.0
+    D["c"] = 1.0 + sum(np.abs(D[q]) for q in "abde")
+    xt, f = synth.manufactured(rng, 2, D, nsys, n)
+    d = {q: torch.from_numpy(D[q]).to(dev) for q in "abcde"}
+    ft = torch.from_numpy(f).to(dev)
+    xtd = torch.from_numpy(xt).to(dev)
+    units = n * nsys
+    out = {"workload": "2048 PD systems, n = 2048, outer entries on 1 %% of the rows (K = %d "
+                       "per system on average)" % int(keep.sum() / nsys), "unit": UNIT}
+    for method, sched in (("mnpdm", "auto"), ("npdm", "thread"), ("npdm", "auto")):
+        x = torch.empty_like(ft)
+        res = {}
+
+        def run():
+            res["x"], res["st"] = band.solve(*(d[q] for q in "abcde"), ft, method=method, x=x,
+                                             schedule=sched)
+        ms = _time(run)
+        err = float(((res["x"] - xtd).abs().amax(0) / xtd.abs().amax(0)).max())
+        out["%s_%s" % (method, sched)] = {"value": units / (ms * 1e-3), "ms": ms,
+                                          "status_not_ok": int((res["st"] != 0).sum()),
+                                          "max_rel_err_vs_manufactured": err}
+    return out
+
+
 # The paper's single-system timings at N = 10^8 (Table 3, HybriLIT, one Xeon E5-2695v2
 # core, double precision): NPDM 2.7946627 s, NTDM 2.0525187 s.  Context only.
 PAPER_1E8_S = {"npdm": 2.7946627, "ntdm": 2.0525187}
@@ -772,7 +812,7 @@ def single_system_workload(dev, n=100_000_000):
 EXTRA_WORKLOADS = {"ragged": "ragged_workload", "small_batch": "small_batch_workload",
                    "precision": "precision_workload", "adjoint": "adjoint_workload",
                    "sip": "sip_workload", "symbolic": "symbolic_workload",
-                   "single": "single_system_workload"}
+                   "single": "single_system_workload", "mnpdm": "mnpdm_workload"}
 
 
 # ---------------------------------------------------------------------- main
@@ -897,7 +937,8 @@ def main():
                              "precision": precision_workload(dev),
                              "adjoint": adjoint_workload(dev), "sip": sip_workload(dev),
                              "symbolic": symbolic_workload(dev),
-                             "single": single_system_workload(dev)}
+                             "single": single_system_workload(dev),
+                             "mnpdm": mnpdm_workload(dev)}
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         line["cpu_baseline"] = cpu_baseline(W)
     if rank == 0:

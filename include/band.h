@@ -68,7 +68,9 @@ typedef enum {
   BAND_STDM = 2,   /* symbolic TD */
   BAND_SPDM = 3,   /* symbolic PD */
   BAND_AUTO_NUMERIC = 4,   /* NTDM or NPDM per system by its half bandwidth (ragged mixes) */
-  BAND_AUTO_SYMBOLIC = 5   /* STDM or SPDM per system by its half bandwidth */
+  BAND_AUTO_SYMBOLIC = 5,  /* STDM or SPDM per system by its half bandwidth */
+  BAND_MNPDM = 6           /* PD systems whose outer diagonals are mostly zero: the outer
+                              entries eliminated, then NTDM (band_solve only; see there) */
 } band_method;
 
 typedef enum { BAND_F64 = 0, BAND_F32 = 1 } band_dtype;
@@ -200,6 +202,19 @@ size_t band_workspace_size(const band_desc* desc, int32_t op, int32_t method, in
 band_status band_solve(const band_desc* desc, int32_t method, const void* factors,
                        const void* const diag[5], const void* f, void* x,
                        int32_t* sys_status, void* ws, size_t ws_bytes, void* stream);
+
+/* band_solve with method BAND_MNPDM (Sec. 1: the PD method that takes the sparsity of the
+ * outer diagonals into account; Sec. 3.2 Remark 2: the Gaussian elimination that turns the
+ * PD matrix into a TD one costs 16 operations per row with both outer entries nonzero):
+ * bottom-up, every nonzero e_i is eliminated with row i+1; top-down, every nonzero a_i
+ * with row i-1; NTDM then solves the TD system.  For PD batches (half_bw 2, no hbw, no id
+ * list), any layout, FP64 or FP32, one thread per system (desc->schedule AUTO or THREAD),
+ * factors NULL; x may alias f.  A zero divisor of the elimination (the superdiagonal of
+ * row i+1, or the subdiagonal of row i-1, as they stand then) or a zero NTDM pivot gives
+ * BAND_ERR_ZERO_PIVOT.  No pivoting: meant for K << n rows with outer entries (on fully
+ * pentadiagonal matrices its multipliers are ratios of off-diagonal entries and it loses
+ * accuracy that NPDM keeps).  Workspace: band_workspace_size(desc, BAND_OP_SOLVE,
+ * BAND_MNPDM, 0), five arrays of nsys rounded up to 32 times n elements. */
 
 /* LU factors of NTDM/NPDM (gamma, 1/mu, alpha, beta per row; opaque layout) into
  * `factors`, a device buffer of band_workspace_size(desc, BAND_OP_FACTOR, method, 0)

@@ -17,7 +17,7 @@ STATUS_NAMES = {OK: "OK", ERR_ARG: "ARG", ERR_CUDA: "CUDA", ERR_ZERO_PIVOT: "ZER
                 ERR_NOT_CONVERGED: "NOT_CONVERGED", ERR_SYMBOLIC_RANGE: "SYMBOLIC_RANGE",
                 ERR_INTERNAL: "INTERNAL", ERR_WORKSPACE: "WORKSPACE"}
 # band_method
-NTDM, NPDM, STDM, SPDM, AUTO_NUMERIC, AUTO_SYMBOLIC = range(6)
+NTDM, NPDM, STDM, SPDM, AUTO_NUMERIC, AUTO_SYMBOLIC, MNPDM = range(7)
 # band_dtype
 F64, F32 = 0, 1
 # band_schedule

@@ -16,7 +16,7 @@ import torch
 from . import _lib as L
 
 _METHODS = {"ntdm": L.NTDM, "npdm": L.NPDM, "stdm": L.STDM, "spdm": L.SPDM,
-            "auto": L.AUTO_NUMERIC, "auto_symbolic": L.AUTO_SYMBOLIC}
+            "auto": L.AUTO_NUMERIC, "auto_symbolic": L.AUTO_SYMBOLIC, "mnpdm": L.MNPDM}
 
 
 def status_names(status):
@@ -106,7 +106,8 @@ def solve(a, b, c, d, e, f, method="npdm", x=None, status=None, factors=None, ws
           schedule="auto", chunks=0):
     """Solve A x = f for a uniform batch.  Returns (x, status int32[nsys]).
 
-    method: "npdm", "ntdm", "spdm", "stdm".  a, e are ignored (may be None) for TD.
+    method: "npdm", "ntdm", "spdm", "stdm", "mnpdm" (PD systems with few nonzero outer
+    entries).  a, e are ignored (may be None) for TD.
     factors: a buffer from ``factor`` to reuse a factorisation (numeric methods).
     schedule: "auto", "thread" (one thread per system), "two_sided" (two threads per
     system meeting in the middle), "partitioned" (``chunks`` lanes per system, 8, 16,

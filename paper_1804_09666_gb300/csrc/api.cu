@@ -232,6 +232,7 @@ size_t band_workspace_size(const band_desc* desc, int32_t op, int32_t method, in
   size_t bytes = 0;
   switch (op) {
     case BAND_OP_SOLVE:
+      if (method == BAND_MNPDM) return mnpdm_workspace_bytes(desc);
       if (desc->schedule == BAND_SCHED_GRID) return grid_workspace_bytes(desc);
       carve_solve(desc, method, nullptr, &bytes);
       return bytes;
@@ -248,6 +249,11 @@ band_status band_solve(const band_desc* desc, int32_t method, const void* factor
                        const void* const diag[5], const void* f, void* x, int32_t* sys_status,
                        void* ws, size_t ws_bytes, void* stream) {
   if (!desc_ok(desc)) return BAND_ERR_ARG;
+  if (method == BAND_MNPDM) {
+    if (factors) return BAND_ERR_ARG;
+    if (desc->nsys == 0) return BAND_OK;
+    return mnpdm_solve(desc, diag, f, x, sys_status, ws, ws_bytes, static_cast<cudaStream_t>(stream));
+  }
   const int kmode = kmode_for(desc, method);
   if (kmode < 0) return BAND_ERR_ARG;
   if (is_symbolic(method) && (desc->dtype != BAND_F64 || factors)) return BAND_ERR_ARG;
