@@ -326,19 +326,19 @@ band_status band_det(const band_desc* desc, const void* const diag[5], double* d
  * no counterpart).  Some callers cannot allocate where they solve: code that must not
  * block on cudaMalloc's device-wide synchronisation, hosts that own every byte of
  * device memory through their own pool, or C callers without an allocator.  This call
- * is band_solve (method BAND_NTDM, BAND_NPDM or BAND_AUTO_NUMERIC, factors NULL)
- * without the workspace argument: its scratch rows come from an array of
+ * is band_solve (method BAND_NTDM, BAND_NPDM or BAND_AUTO_NUMERIC, factors NULL, no id
+ * list) without the workspace argument: its scratch rows come from an array of
  * BAND_STATIC_SCRATCH_BYTES that the library places in device memory on every GPU
  * that loads it, held until the process exits.  The first call on a device looks up
- * that array's device address (once per device, with that device current); make
- * that first call before any stream capture.  desc->schedule applies as for
- * band_solve.  A batch whose workspace (band_workspace_size(desc, BAND_OP_SOLVE,
- * method, 0): 2 arrays of nsys rounded up to 32, times n, times the element size, for
- * the thread and two-sided schedules) exceeds the array returns BAND_ERR_WORKSPACE;
- * other methods return BAND_ERR_ARG.  The array
- * is shared by every call and keeps the last call's contents (nothing in it needs to
- * start at zero): calls whose kernels overlap on one GPU race on it and must be
- * serialised by the caller.  No device memory is allocated. */
+ * that array's device address (once per device, with that device current; again after
+ * a cudaDeviceReset); make that first call before any stream capture.  desc->schedule
+ * applies as for band_solve (not BAND_SCHED_GRID).  A batch whose workspace,
+ * band_workspace_size(desc, BAND_OP_SOLVE, method, 0) for the same desc (the rule for
+ * every layout and schedule), exceeds the array returns BAND_ERR_WORKSPACE; other
+ * methods return BAND_ERR_ARG.  The array is shared by every call and keeps the last
+ * call's contents (nothing in it needs to start at zero): calls whose kernels overlap
+ * on one GPU race on it and must be serialised by the caller.  No device memory is
+ * allocated. */
 #define BAND_STATIC_SCRATCH_BYTES ((size_t)32 << 20)
 band_status band_solve_static(const band_desc* desc, int32_t method, const void* const diag[5],
                               const void* f, void* x, int32_t* sys_status, void* stream);

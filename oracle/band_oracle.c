@@ -659,7 +659,8 @@ int orc_ilu0(int64_t n, const double* a, const double* b, const double* c, const
   return ORC_OK;
 }
 
-/* K = LU - A on the five diagonals (Algorithm 1: "K = L U - A").             */
+/* K = LU - A on the five diagonals: the remainder of the splitting A = LU - K */
+/* that Algorithm 1 iterates on.                                              */
 void orc_lu_minus_a(int64_t n, const double* l2, const double* l1, const double* u0,
                     const double* u1, const double* u2, const double* a, const double* b,
                     const double* c, const double* d, const double* e,
@@ -792,9 +793,11 @@ static double residual_pd(int64_t n, const double* a, const double* b, const dou
 
 /* ------------------------------------------------------------------------- */
 /* R6 -- SIP / the Stone method, Algorithm 1 (Sec. 2).                       */
-/* hb_width == 0: Algorithm 1 as printed: x^0 = 0, r = f - A x,               */
-/*   K = LU - A, while ||r||_inf >= tol: rhs = K x + f, solve L y = rhs,      */
-/*   solve U x = y, r = f - A x, k++.                                         */
+/* hb_width == 0: the stationary iteration of the splitting A = LU - K with   */
+/*   the ILU(0) factors: from x^0 = 0, every update solves LU x^{k+1} =       */
+/*   K x^k + f by the two substitutions, and the iteration stops once the     */
+/*   residual f - A x has max-norm below tol (Algorithm 1's steps, in its     */
+/*   order).                                                                  */
 /* hb_width  > 0: the Remark of Sec. 2 -- L^{-1}, U^{-1} from Hotelling-     */
 /*   Bodewig (R5, w = hb_width) replace the two substitutions; with inexact  */
 /*   inverses the update is written in correction form                        */

@@ -41,12 +41,15 @@ struct Spill {
 };
 
 // ---------------------------------------------------------------- reciprocals
-// 1/m in FP64 from an FP32 seed refined by Newton's method for the reciprocal.
+// 1/m in FP64 from an FP32 seed refined by the Newton-Raphson iteration for the
+// reciprocal in its third-order form (the truncated series r0 (1 + e + e^2) of
+// 1/m = r0 / (1 - e), as in Markstein's division and reciprocal sequences).
 // The seed: the double's exponent is rebased into float range with integer ops (the
 // leading 20 mantissa bits are kept), rcp.approx.f32 gives ~22 correct bits, and the
-// result is rebased back.  With e = 1 - m r0 (|e| < 2^-19), one step of the cubic
-// form of the iteration, r = r0 + r0 (e + e^2), leaves a relative error of order
-// e^3 < 2^-57 before the final rounding.  Outside the exponent window where the
+// result is rebased back.  With e = 1 - m r0 (|e| < 2^-19), one step
+// r = r0 + r0 (e + e^2) leaves a relative error of order e^3 < 2^-57 before the final
+// rounding, so the result is within one ulp of the correctly rounded 1/m
+// (tests/test_gpu_rcp64.py checks that against IEEE division).  Outside the exponent window where the
 // rebasing is valid (|m| roughly in [2^-120, 2^120]) and for 0, Inf and NaN the
 // division is used instead.
 __device__ __forceinline__ double rcp64(double m) {

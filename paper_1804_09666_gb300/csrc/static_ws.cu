@@ -28,14 +28,28 @@ static __device__ __align__(256) unsigned char g_scratch[kStaticScratchBytes];
 std::mutex g_mu;
 void* g_ptr[kMaxDevices] = {};
 
-// Device address of g_scratch on the current device (set up once per device).  In host
-// code `g_scratch` is only a host-side stand-in for the symbol, never a device address.
+// Is p still device memory of the current device's context?  A cudaDeviceReset ends the
+// context the address was looked up in; the lookup is then repeated.  (A failed query's
+// error is taken off the runtime's last-error slot, so later launch checks do not see it.)
+bool still_mapped(void* p, int dev) {
+  cudaPointerAttributes a;
+  if (cudaPointerGetAttributes(&a, p) != cudaSuccess) {
+    cudaGetLastError();
+    return false;
+  }
+  return a.type == cudaMemoryTypeDevice && a.device == dev;
+}
+
+// Device address of g_scratch on the current device: looked up on the first call on
+// that device (with it current), and again if the device was reset since.  In host code
+// `g_scratch` is only a host-side stand-in for the symbol, never a device address.
 cudaError_t scratch_on_current_device(void** out) {
   int dev = 0;
   cudaError_t e = cudaGetDevice(&dev);
   if (e != cudaSuccess) return e;
   if (dev < 0 || dev >= kMaxDevices) return cudaErrorInvalidDevice;
   std::lock_guard<std::mutex> lock(g_mu);
+  if (g_ptr[dev] && !still_mapped(g_ptr[dev], dev)) g_ptr[dev] = nullptr;
   if (!g_ptr[dev]) {
     void* p = nullptr;
     e = cudaGetSymbolAddress(&p, g_scratch);

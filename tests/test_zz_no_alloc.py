@@ -89,3 +89,37 @@ def test_static_scratch_rejects_oversized_batches(lib):
     assert code == L.ERR_WORKSPACE
     code = lib.band_solve_static(ct.byref(desc), L.SPDM, diag, 8, 8, None, None)
     assert code == L.ERR_ARG
+
+
+def test_static_scratch_ragged_packing(lib):
+    """A whole ragged packing (offsets, per-system bandwidths): the workspace rule is
+    band_workspace_size's for the same descriptor; bitwise equal to band_solve, twice."""
+    from paper_1804_09666_gb300 import _lib as L
+    dev = torch.device("cuda:0")
+    for salt in (0, 1):
+        B = synth.cfg2(nsys=300, nmin=16, nmax=512, seed_salt=30 + salt)
+        T = {q: torch.from_numpy(B[q]).to(dev) for q in "abcdef"}
+        offs = torch.from_numpy(B["offsets"]).to(dev)
+        hbw = torch.from_numpy(B["hbw"]).to(dev)
+        total = int(B["offsets"][-1])
+        desc = L.BandDesc(half_bw=2, dtype=L.F64, nsys=300, n=int(B["sizes"].max()),
+                          sys_stride=0, elem_stride=1, offsets=offs.data_ptr(),
+                          hbw=hbw.data_ptr(), total_rows=total)
+        need = lib.band_workspace_size(ct.byref(desc), L.OP_SOLVE, L.AUTO_NUMERIC, 0)
+        assert 0 < need <= STATIC_SCRATCH_BYTES
+        diag = L.DIAG5(*[T[q].data_ptr() for q in "abcde"])
+        stream = ct.c_void_p(torch.cuda.current_stream().cuda_stream)
+        xs = torch.empty_like(T["f"])
+        xw = torch.empty_like(T["f"])
+        ss = torch.full((300,), -1, dtype=torch.int32, device=dev)
+        sw = torch.full((300,), -1, dtype=torch.int32, device=dev)
+        ws = torch.empty(need, dtype=torch.uint8, device=dev)
+        assert lib.band_solve_static(ct.byref(desc), L.AUTO_NUMERIC, diag, T["f"].data_ptr(),
+                                     xs.data_ptr(), ss.data_ptr(), stream) == 0
+        assert lib.band_solve(ct.byref(desc), L.AUTO_NUMERIC, None, diag, T["f"].data_ptr(),
+                              xw.data_ptr(), sw.data_ptr(), ws.data_ptr(), need, stream) == 0
+        torch.cuda.synchronize()
+        assert (ss == 0).all() and (sw == 0).all()
+        assert torch.equal(xs, xw)
+        err = (xs.cpu().numpy() - B["x_true"])
+        assert np.abs(err).max() <= 1e-12 * np.abs(B["x_true"]).max()
