@@ -761,6 +761,39 @@ def mnpdm_workload(dev):
     return out
 
 
+def adi_time_workload(dev, n=GRID, steps=10):
+    """Time-stepping of u_t = Delta u + u (1 - u) + s on the 2048 x 2048 grid by
+    Peaceman-Rachford ADI (band_adi_step): per step the right-hand-side stencil kernel,
+    2048 row systems, the second stencil kernel, 2048 column systems; PD lines
+    (fourth-order stencil, NPDM) and TD lines (3-point, NTDM); `steps` steps captured in
+    one CUDA graph and replayed."""
+    import torch
+    import paper_1804_09666_gb300 as band
+    rng = np.random.default_rng(1804_09666 + 300)
+    src = torch.from_numpy(rng.uniform(-1, 1, (n, n))).to(dev)
+    u0 = torch.from_numpy(rng.uniform(0, 1, (n, n))).to(dev)
+    out = {"workload": "ADI time steps of u_t = Delta u + u (1 - u) + s, %d x %d grid, tau = "
+                       "1e-4, %d steps per graph replay" % (n, n, steps), "unit": UNIT}
+    for k, name in ((2, "pd_npdm"), (1, "td_ntdm")):
+        stepper = band.AdiStepper(n, 1e-4, 1.0, src, half_bw=k)
+        u = u0.clone()
+        stepper.step(u)
+        torch.cuda.synchronize()
+        g = torch.cuda.CUDAGraph()
+        st = torch.cuda.Stream()
+        st.wait_stream(torch.cuda.current_stream())
+        with torch.cuda.stream(st):
+            with torch.cuda.graph(g, stream=st):
+                stepper.step(u, steps=steps)
+        torch.cuda.current_stream().wait_stream(st)
+        ms = _time(g.replay, reps=5) / steps
+        bad = int((stepper.status != 0).sum())
+        out[name] = {"ms_per_step": ms, "value": 2 * n * n / (ms * 1e-3),
+                     "line_status_not_ok": bad,
+                     "finite": bool(torch.isfinite(u).all().item())}
+    return out
+
+
 # The paper's single-system timings at N = 10^8 (Table 3, HybriLIT, one Xeon E5-2695v2
 # core, double precision): NPDM 2.7946627 s, NTDM 2.0525187 s.  Context only.
 PAPER_1E8_S = {"npdm": 2.7946627, "ntdm": 2.0525187}
@@ -812,7 +845,8 @@ def single_system_workload(dev, n=100_000_000):
 EXTRA_WORKLOADS = {"ragged": "ragged_workload", "small_batch": "small_batch_workload",
                    "precision": "precision_workload", "adjoint": "adjoint_workload",
                    "sip": "sip_workload", "symbolic": "symbolic_workload",
-                   "single": "single_system_workload", "mnpdm": "mnpdm_workload"}
+                   "single": "single_system_workload", "mnpdm": "mnpdm_workload",
+                   "adi_time": "adi_time_workload"}
 
 
 # ---------------------------------------------------------------------- main
@@ -938,7 +972,8 @@ def main():
                              "adjoint": adjoint_workload(dev), "sip": sip_workload(dev),
                              "symbolic": symbolic_workload(dev),
                              "single": single_system_workload(dev),
-                             "mnpdm": mnpdm_workload(dev)}
+                             "mnpdm": mnpdm_workload(dev),
+                             "adi_time": adi_time_workload(dev)}
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         line["cpu_baseline"] = cpu_baseline(W)
     if rank == 0:

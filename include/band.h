@@ -179,7 +179,8 @@ enum {
   BAND_OP_SIP = 2,        /* band_sip (uses sip_width) */
   BAND_OP_REFINE = 3,     /* band_refine_solve */
   BAND_OP_ADJOINT = 4,    /* band_adjoint */
-  BAND_OP_DET = 5         /* band_det */
+  BAND_OP_DET = 5,        /* band_det */
+  BAND_OP_ADI = 6         /* band_adi_step (desc describes the grid, see there) */
 };
 size_t band_workspace_size(const band_desc* desc, int32_t op, int32_t method, int32_t sip_width);
 
@@ -202,6 +203,31 @@ size_t band_workspace_size(const band_desc* desc, int32_t op, int32_t method, in
 band_status band_solve(const band_desc* desc, int32_t method, const void* factors,
                        const void* const diag[5], const void* f, void* x,
                        int32_t* sys_status, void* ws, size_t ws_bytes, void* stream);
+
+/* One time step of a nonlinear parabolic PDE by the alternating direction implicit
+ * method, the setting of the paper's band solves (Sec. 1: an ADI step solves N
+ * independent TD or PD systems per direction):
+ *   u_t = u_xx + u_yy + lambda u (1 - u) + s(x, y)  on the unit square, u = 0 on the
+ *   boundary, n x n interior points, h = 1 / (n + 1), u[y * n + x] (row-major, device).
+ * Second differences: the 3-point stencil (1, -2, 1) / h^2 (grid->half_bw 1: TD systems,
+ * NTDM) or the fourth-order 5-point stencil (-1, 16, -30, 16, -1) / (12 h^2) (half_bw 2:
+ * PD systems, NPDM) whose point beyond the boundary is the odd reflection of the first
+ * interior point; the nonlinear term and s stay on the right-hand side, evaluated at
+ * the latest values.  One Peaceman-Rachford step, theta = tau / 2:
+ *   (I - theta D_x) u* = u + theta (D_y u + g(u) + s),   then
+ *   (I - theta D_y) u  = u* + theta (D_x u* + g(u*) + s),   g(u) = lambda u (1 - u):
+ * n row systems (contiguous), then n column systems (interleaved), each solved by
+ * band_solve on the automatic schedule.  grid: half_bw 1 or 2, dtype BAND_F64,
+ * nsys = n = the grid size (n >= 3), hbw / offsets NULL, schedule 0, chunks 0 (strides
+ * ignored).
+ * source: n * n values or NULL (s = 0).  u is updated in place.  sys_status (may be
+ * NULL): 2n entries, the row systems' statuses then the column systems'.  ws:
+ * band_workspace_size(grid, BAND_OP_ADI, 0, 0) bytes.  Asynchronous on `stream` (the
+ * right-hand sides, the constant diagonals and the solves are kernels only), so that a
+ * caller can capture a number of steps in one CUDA graph. */
+band_status band_adi_step(const band_desc* grid, double tau, double lambda, const double* source,
+                          double* u, int32_t* sys_status, void* ws, size_t ws_bytes,
+                          void* stream);
 
 /* band_solve with method BAND_MNPDM (Sec. 1: the PD method that takes the sparsity of the
  * outer diagonals into account; Sec. 3.2 Remark 2: the Gaussian elimination that turns the

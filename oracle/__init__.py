@@ -326,3 +326,72 @@ def batch(method, k, diags, f, nsys, n, sys_stride, elem_stride, offsets=None, h
                   status.ctypes.data_as(_I32), tol, max_it, hb_width, hb_max_it, hb_tol,
                   iters.ctypes.data_as(_I32), resid.ctypes.data_as(_D), nthreads)
     return x.reshape(_np.shape(f)), status, iters, resid
+
+
+def _second_difference(v, axis, k, h):
+    """D v along `axis` of a square grid with u = 0 on the boundary: the 3-point stencil
+    (1, -2, 1) / h^2 (k = 1) or the fourth-order 5-point (-1, 16, -30, 16, -1) / (12 h^2)
+    (k = 2), whose point beyond the boundary is the odd reflection of the first interior
+    point (u(-h) = -u(h), u(1 + h) = -u(1 - h))."""
+    pad = [(0, 0), (0, 0)]
+    pad[axis] = (2, 2)
+    vp = _np.pad(v, pad)
+    n = v.shape[axis]
+
+    def sh(o):
+        sl = [slice(None), slice(None)]
+        sl[axis] = slice(2 + o, 2 + o + n)
+        return vp[tuple(sl)]
+    if k == 1:
+        return (sh(-1) - 2.0 * sh(0) + sh(1)) / (h * h)
+    # the reflected points beyond the boundary
+    lo = [slice(None), slice(None)]
+    lo[axis] = 0
+    hi = [slice(None), slice(None)]
+    hi[axis] = n + 3
+    first = [slice(None), slice(None)]
+    first[axis] = 2
+    last = [slice(None), slice(None)]
+    last[axis] = n + 1
+    vp[tuple(lo)] = -vp[tuple(first)]
+    vp[tuple(hi)] = -vp[tuple(last)]
+    return (-sh(-2) + 16.0 * sh(-1) - 30.0 * sh(0) + 16.0 * sh(1) - sh(2)) / (12.0 * h * h)
+
+
+def adi_step(u, tau, lam, source=None, k=2, nthreads=None):
+    """One Peaceman-Rachford ADI step of u_t = u_xx + u_yy + lam u (1 - u) + s on the
+    n x n interior grid of the unit square (u = 0 on the boundary, h = 1 / (n + 1),
+    u[y, x]; second differences as in _second_difference), the nonlinear term and s on
+    the right-hand side (theta = tau / 2):
+      (I - theta D_x) u* = u + theta (D_y u + g(u) + s),
+      (I - theta D_y) u' = u* + theta (D_x u* + g(u*) + s),
+    every line system solved by R1 (k = 1) / R2 (k = 2).  Returns (u', statuses)."""
+    u = _np.asarray(u, dtype=_np.float64)
+    n = u.shape[0]
+    h = 1.0 / (n + 1)
+    theta = 0.5 * tau
+    r = theta / (h * h)
+    s = _np.zeros_like(u) if source is None else _np.asarray(source, dtype=_np.float64)
+    g = lambda v: lam * v * (1.0 - v)
+    if k == 1:
+        vals = (0.0, -r, 1.0 + 2.0 * r, -r, 0.0)
+    else:
+        vals = (r / 12.0, -4.0 * r / 3.0, 1.0 + 2.5 * r, -4.0 * r / 3.0, r / 12.0)
+    diags = [_np.full(n * n, v) for v in vals]
+    # the 5-point stencil's reflected point makes the first and last rows' diagonal
+    # 1 + 29 r / 12: per sweep, by the position along the system
+    cx = _np.full((n, n), vals[2])
+    cy = _np.full((n, n), vals[2])
+    if k == 2:
+        cx[:, 0] = cx[:, -1] = 1.0 + 29.0 * r / 12.0      # rows: position = x
+        cy[0, :] = cy[-1, :] = 1.0 + 29.0 * r / 12.0      # columns: position = y
+    F = u + theta * (_second_difference(u, 0, k, h) + g(u) + s)
+    # rows (systems y, elements x): system stride n, element stride 1
+    dx = diags[:2] + [cx.reshape(-1)] + diags[3:]
+    ustar, st1, _, _ = batch("direct", k, dx, F.reshape(-1), n, n, n, 1, nthreads=nthreads)
+    ustar = ustar.reshape(n, n)
+    F2 = ustar + theta * (_second_difference(ustar, 1, k, h) + g(ustar) + s)
+    # columns (systems x, elements y): system stride 1, element stride n
+    dy = diags[:2] + [cy.reshape(-1)] + diags[3:]
+    unew, st2, _, _ = batch("direct", k, dy, F2.reshape(-1), n, n, 1, n, nthreads=nthreads)
+    return unew.reshape(n, n), _np.concatenate([st1, st2])

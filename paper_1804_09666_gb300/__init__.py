@@ -7,9 +7,9 @@ refinement and an adjoint, as hand-written sm_103a CUDA kernels behind the C ABI
 of include/band.h.  This package is the thin Python binding over torch CUDA tensors.
 """
 from ._lib import BandError, load  # noqa: F401
-from .band import (BandSolve, BatchPlan, RaggedPlan, adjoint, desc_for, det, factor,  # noqa: F401
+from .band import (AdiStepper, BandSolve, BatchPlan, RaggedPlan, adjoint, desc_for, det, factor,  # noqa: F401
                    refine_solve, sip, slogdet, solve, solve_batch, solve_ragged, status_names)
 
-__all__ = ["solve", "solve_ragged", "solve_batch", "BatchPlan", "RaggedPlan", "factor", "sip",
+__all__ = ["AdiStepper", "solve", "solve_ragged", "solve_batch", "BatchPlan", "RaggedPlan", "factor", "sip",
            "refine_solve", "adjoint", "det", "slogdet", "BandSolve", "desc_for", "status_names", "load",
            "BandError"]

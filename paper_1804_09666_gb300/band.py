@@ -168,6 +168,46 @@ def slogdet(a, b, c, d, e, half_bw=2):
     return sign, logabs, status
 
 
+class AdiStepper:
+    """Time steps of u_t = u_xx + u_yy + lam u (1 - u) + s on an n x n grid (Peaceman-
+    Rachford ADI; band_adi_step): u is an (n, n) float64 CUDA tensor, u[y, x], updated
+    in place.  half_bw 1: 3-point stencil (NTDM lines), 2: fourth-order 5-point stencil
+    (NPDM lines).  The workspace is allocated once here, so ``step`` only launches and a
+    number of steps can be captured in a CUDA graph.  ``status`` holds the 2n line
+    statuses of the last step (rows, then columns)."""
+
+    def __init__(self, n, tau, lam=1.0, source=None, half_bw=2, device=None):
+        lib = L.load()
+        self.lib = lib
+        self.desc = L.BandDesc(half_bw=half_bw, dtype=L.F64, nsys=n, n=n, sys_stride=1,
+                               elem_stride=1, offsets=None, hbw=None, total_rows=0,
+                               schedule=0, chunks=0)
+        dev = device if device is not None else torch.device("cuda", torch.cuda.current_device())
+        if source is not None:
+            _on_device(dev, source=source)
+            if source.dtype != torch.float64 or not source.is_contiguous() or \
+                    source.numel() != n * n:
+                raise ValueError("source must be a contiguous float64 (n, n) tensor")
+        self.n, self.tau, self.lam, self.source = n, float(tau), float(lam), source
+        need = lib.band_workspace_size(ct.byref(self.desc), L.OP_ADI, 0, 0)
+        if need == 0:
+            raise ValueError("bad grid for band_adi_step")
+        self.ws = _workspace(need, dev)
+        self.status = torch.empty(2 * n, dtype=torch.int32, device=dev)
+        self.device = dev
+
+    def step(self, u, steps=1):
+        if not (u.is_cuda and u.device == self.device and u.dtype == torch.float64 and
+                u.is_contiguous() and u.numel() == self.n * self.n):
+            raise ValueError("u must be a contiguous float64 (n, n) tensor on the stepper's device")
+        for _ in range(steps):
+            code = self.lib.band_adi_step(ct.byref(self.desc), self.tau, self.lam,
+                                          _ptr(self.source), _ptr(u), _ptr(self.status),
+                                          _ptr(self.ws), _bytes(self.ws), _stream())
+            L.check(code, "band_adi_step")
+        return u
+
+
 def factor(a, b, c, d, e, method="npdm", status=None):
     """LU factors (opaque uint8 buffer) for repeated solves and the adjoint."""
     lib = L.load()

@@ -228,6 +228,7 @@ band_status make_direct(const band_desc* desc, int32_t method, const void* const
 extern "C" {
 
 size_t band_workspace_size(const band_desc* desc, int32_t op, int32_t method, int32_t sip_width) {
+  if (op == BAND_OP_ADI) return adi_workspace_bytes(desc);   // a grid, checked there
   if (!desc_ok(desc)) return 0;
   size_t bytes = 0;
   switch (op) {

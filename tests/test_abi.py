@@ -164,6 +164,14 @@ def test_bad_arguments_are_rejected_without_gpu(lib):
     assert lib.band_det(ct.byref(d), nul, 8, 8, 8, 8, 1 << 30, None) == L.ERR_ARG
     assert lib.band_det(ct.byref(d), full, 8, 8, 8, 8, 16, None) == L.ERR_WORKSPACE
     assert lib.band_det(ct.byref(_desc(nsys=0)), full, 8, 8, 8, 8, 0, None) == L.OK
+    # the ADI step: a grid descriptor (strides ignored), n >= 3, tau > 0
+    grid = _desc(nsys=64, n=64, sys_stride=1, elem_stride=1)
+    assert lib.band_workspace_size(ct.byref(grid), L.OP_ADI, 0, 0) >= 8 * 64 * 64 * 8
+    assert lib.band_workspace_size(ct.byref(_desc(nsys=2, n=2)), L.OP_ADI, 0, 0) == 0
+    assert lib.band_workspace_size(ct.byref(_desc(nsys=64, n=63)), L.OP_ADI, 0, 0) == 0
+    assert lib.band_adi_step(ct.byref(grid), 0.0, 1.0, None, 8, None, 8, 1 << 40, None) == L.ERR_ARG
+    assert lib.band_adi_step(ct.byref(grid), 0.1, 1.0, None, None, None, 8, 1 << 40, None) == L.ERR_ARG
+    assert lib.band_adi_step(ct.byref(grid), 0.1, 1.0, None, 8, None, 8, 64, None) == L.ERR_WORKSPACE
     # its workspace is the flagged-system counter and list
     assert lib.band_workspace_size(ct.byref(d), L.OP_DET, 0, 0) >= 8 + 64 * 8
 

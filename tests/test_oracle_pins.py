@@ -780,3 +780,52 @@ def test_condition_estimate_vs_dense(dominant):
             est = oracle.cond1(k, a, b, c, d, e)
             assert est <= true * (1 + 1e-8)
             assert est >= true / 3
+
+
+# ------------------------------------------------------------- ADI time step
+def test_adi_heat_mode_amplification():
+    """Heat equation (lam = 0, s = 0), 3-point stencil: sin(p pi x) sin(q pi y) is an
+    eigenvector of D_x and D_y with eigenvalues mu = -4 sin^2(m pi h / 2) / h^2, so one
+    Peaceman-Rachford step multiplies it by exactly
+    (1 + theta mu_q)(1 + theta mu_p) / ((1 - theta mu_p)(1 - theta mu_q))."""
+    n = 31
+    h = 1.0 / (n + 1)
+    xs = h * np.arange(1, n + 1)
+    for p, q, tau in ((1, 1, 0.01), (3, 2, 0.002), (7, 11, 0.05)):
+        u0 = np.outer(np.sin(q * np.pi * xs), np.sin(p * np.pi * xs))     # u[y, x]
+        mu = lambda m: -4.0 * np.sin(m * np.pi * h / 2) ** 2 / h ** 2
+        th = tau / 2
+        G = (1 + th * mu(q)) * (1 + th * mu(p)) / ((1 - th * mu(p)) * (1 - th * mu(q)))
+        u1, st = oracle.adi_step(u0, tau, 0.0, None, k=1)
+        assert (st == 0).all()
+        assert np.abs(u1 - G * u0).max() <= 1e-13
+
+
+@pytest.mark.parametrize("k", [1, 2])
+def test_adi_steady_state_converges_to_manufactured_solution(k):
+    """u_e = sin(pi x) sin(pi y) (1 + x y / 2) solves Delta u + g(u) + s = 0 for
+    s = -Delta u_e - g(u_e); stepping to steady state, the ADI scheme's discrete solution
+    approaches u_e at second order in h (the 5-point stencil's reflected point beyond the
+    boundary is second-order accurate there): a wrong stencil coefficient, sign, axis or
+    boundary row does not converge at that rate."""
+    lam = 1.0
+    errs = []
+    for n in (15, 31, 63):
+        h = 1.0 / (n + 1)
+        xs = h * np.arange(1, n + 1)
+        X, Y = np.meshgrid(xs, xs)          # X[y, x] = x
+        sp = np.sin(np.pi * X) * np.sin(np.pi * Y)
+        ue = sp * (1 + X * Y / 2)
+        # Delta u_e by hand: u = S P with S = sin(pi x) sin(pi y), P = 1 + x y / 2
+        S_xx = -np.pi ** 2 * sp
+        S_x = np.pi * np.cos(np.pi * X) * np.sin(np.pi * Y)
+        S_y = np.pi * np.sin(np.pi * X) * np.cos(np.pi * Y)
+        lap = 2 * S_xx * (1 + X * Y / 2) + 2 * (S_x * Y / 2 + S_y * X / 2)
+        s = -lap - lam * ue * (1 - ue)
+        u = np.zeros((n, n))
+        for _ in range(400):
+            u, st = oracle.adi_step(u, 0.02, lam, s, k=k)
+        assert (st == 0).all()
+        errs.append(np.abs(u - ue).max())
+    rates = [np.log2(errs[i] / errs[i + 1]) for i in range(2)]
+    assert min(rates) >= 1.8, (errs, rates)
