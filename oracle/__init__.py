@@ -56,6 +56,9 @@ def _load():
         lib.orc_ntdm.argtypes = [i64, _D, _D, _D, _D, _D, _LL]
         lib.orc_npdm.argtypes = [i64, _D, _D, _D, _D, _D, _D, _D, _D, _LL]
         lib.orc_mnpdm.argtypes = [i64, _D, _D, _D, _D, _D, _D, _D, _LL]
+        lib.orc_sip2d.argtypes = [i64, i64, _D, _D, _D, _D, _D, _D, _D, dbl, c_int,
+                                  _ct.POINTER(c_int), _D]
+        lib.orc_ilu0_2d.argtypes = [i64, i64, _D, _D, _D, _D, _D, _D, _D, _D]
         lib.orc_gepp_band.argtypes = [i64, c_int, _D, _D, _D, _D, _D, _D, _D, _D]
         lib.orc_symbolic.argtypes = [i64, c_int, _D, _D, _D, _D, _D, _D, _D, _D, _LL,
                                      _ct.POINTER(c_int)]
@@ -75,7 +78,7 @@ def _load():
         lib.orc_batch.argtypes = [c_int, c_int, i64, i64, i64, i64, _I64, _I8,
                                   _D, _D, _D, _D, _D, _D, _D, _I32, dbl, c_int, c_int, c_int,
                                   dbl, _I32, _D, c_int]
-        for name in ("orc_ntdm", "orc_npdm", "orc_mnpdm", "orc_gepp_band", "orc_symbolic", "orc_ilu0",
+        for name in ("orc_ntdm", "orc_npdm", "orc_mnpdm", "orc_sip2d", "orc_ilu0_2d", "orc_gepp_band", "orc_symbolic", "orc_ilu0",
                      "orc_hb", "orc_sip", "orc_refine", "orc_adjoint", "orc_batch"):
             getattr(lib, name).restype = c_int
         _lib = lib
@@ -147,6 +150,29 @@ def mnpdm(a, b, c, d, e, f, count_ops=False):
     st = lib.orc_mnpdm(n, pa, pb, pc, pd, pe, pf, x.ctypes.data_as(_D),
                        _ct.byref(ops) if count_ops else None)
     return (x, STATUS[st], ops.value) if count_ops else (x, STATUS[st])
+
+
+def sip2d(nx, ny, s, w, c, e, t, f, tol=1e-10, max_it=500):
+    """R6b Stone's method on a 2-D five-point matrix (unknown y nx + x; s, w, c, e, t at
+    columns k - nx, k - 1, k, k + 1, k + nx).  Returns dict(x, iters, resid, status)."""
+    lib = _load()
+    (s, ps), (w, pw), (c, pc), (e, pe), (t, pt), (f, pf) = map(_d, (s, w, c, e, t, f))
+    x = _zeros_like_n(nx * ny)
+    it, rs = _ct.c_int(0), _ct.c_double(0)
+    st = lib.orc_sip2d(nx, ny, ps, pw, pc, pe, pt, pf, x.ctypes.data_as(_D), tol, max_it,
+                       _ct.byref(it), _ct.byref(rs))
+    return dict(x=x, iters=it.value, resid=rs.value, status=STATUS[st])
+
+
+def ilu0_2d(nx, ny, s, w, c, e, t):
+    """R6b's ILU(0) factors (ls, lw, uc) of a 2-D five-point matrix, and the status."""
+    lib = _load()
+    (s, ps), (w, pw), (c, pc), (e, pe), (t, pt) = map(_d, (s, w, c, e, t))
+    N = nx * ny
+    ls, lw, uc = _zeros_like_n(N), _zeros_like_n(N), _zeros_like_n(N)
+    st = lib.orc_ilu0_2d(nx, ny, ps, pw, pc, pe, pt, ls.ctypes.data_as(_D), lw.ctypes.data_as(_D),
+                         uc.ctypes.data_as(_D))
+    return (ls, lw, uc), STATUS[st]
 
 
 def gepp_band(k, a, b, c, d, e, f):

@@ -895,6 +895,121 @@ done:
 }
 
 /* ------------------------------------------------------------------------- */
+/* R6b -- SIP on a two-dimensional five-point matrix (Sec. 2: Stone's method,    */
+/* whose ILU(0) drops the fill-in that a two-dimensional pattern creates).       */
+/* Unknown k = y nx + x of an nx x ny grid; row k holds s_k at column k - nx,    */
+/* w_k at k - 1, c_k at k, e_k at k + 1, t_k at k + nx (entries leaving the grid */
+/* are not part of the matrix).  ILU(0) keeps L's and U's entries on A's         */
+/* pattern: L unit lower with ls (column k - nx) and lw (k - 1), U with uc (k),   */
+/* ue (k + 1), ut (k + nx), fixed row by row so that (LU)_{kj} = A_{kj} on the   */
+/* pattern:                                                                     */
+/*   ls_k = s_k / uc_{k-nx},  lw_k = w_k / uc_{k-1},                             */
+/*   uc_k = c_k - ls_k ut_{k-nx} - lw_k ue_{k-1},  ue_k = e_k,  ut_k = t_k;       */
+/* the products ls_k ue_{k-nx} (column k - nx + 1) and lw_k ut_{k-1} (column      */
+/* k + nx - 1) fall outside the pattern and are dropped: they are K = LU - A.    */
+/* Algorithm 1 then iterates LU x^{j+1} = K x^j + f from x^0 = 0 until          */
+/* max|f - A x| < tol, or max_it updates (NOT_CONVERGED).                        */
+/* ------------------------------------------------------------------------- */
+static int in_grid(int64_t nx, int64_t ny, int64_t k, int dx, int dy) {
+  int64_t x = k % nx + dx, y = k / nx + dy;
+  return x >= 0 && x < nx && y >= 0 && y < ny;
+}
+
+int orc_sip2d(int64_t nx, int64_t ny, const double* s, const double* w, const double* c,
+              const double* e, const double* t, const double* f, double* x, double tol,
+              int max_it, int* iters, double* resid) {
+  if (nx < 1 || ny < 1 || max_it < 0) return ORC_ARG;
+  int64_t N = nx * ny;
+  double* ls = (double*)calloc((size_t)N, sizeof(double));
+  double* lw = (double*)calloc((size_t)N, sizeof(double));
+  double* uc = (double*)calloc((size_t)N, sizeof(double));
+  double* y = (double*)calloc((size_t)N, sizeof(double));
+  if (!ls || !lw || !uc || !y) { free(ls); free(lw); free(uc); free(y); return ORC_NOMEM; }
+  int st = ORC_OK;
+  /* entries of A on the grid (zero where the neighbour leaves it) */
+#define AS(k) (in_grid(nx, ny, k, 0, -1) ? s[k] : 0.0)
+#define AW(k) (in_grid(nx, ny, k, -1, 0) ? w[k] : 0.0)
+#define AE(k) (in_grid(nx, ny, k, 1, 0) ? e[k] : 0.0)
+#define AT(k) (in_grid(nx, ny, k, 0, 1) ? t[k] : 0.0)
+  for (int64_t k = 0; k < N; ++k) {
+    double v = c[k];
+    if (in_grid(nx, ny, k, 0, -1)) { ls[k] = AS(k) / uc[k - nx]; v -= ls[k] * AT(k - nx); }
+    if (in_grid(nx, ny, k, -1, 0)) { lw[k] = AW(k) / uc[k - 1]; v -= lw[k] * AE(k - 1); }
+    uc[k] = v;
+    if (v == 0.0) { st = ORC_ZERO_PIVOT; break; }
+  }
+  int it = 0;
+  double rn = INFINITY;
+  if (st == ORC_OK) {
+    for (int64_t k = 0; k < N; ++k) x[k] = 0.0;
+    for (;;) {
+      /* r = f - A x, max |r| */
+      rn = 0.0;
+      for (int64_t k = 0; k < N; ++k) {
+        double ax = c[k] * x[k];
+        if (in_grid(nx, ny, k, 0, -1)) ax += AS(k) * x[k - nx];
+        if (in_grid(nx, ny, k, -1, 0)) ax += AW(k) * x[k - 1];
+        if (in_grid(nx, ny, k, 1, 0)) ax += AE(k) * x[k + 1];
+        if (in_grid(nx, ny, k, 0, 1)) ax += AT(k) * x[k + nx];
+        double r = f[k] - ax;
+        if (!(fabs(r) <= rn)) rn = fabs(r);
+      }
+      if (rn < tol || it >= max_it || !isfinite(rn)) break;
+      /* K x + f, then L y = K x + f, then U x = y */
+      for (int64_t k = 0; k < N; ++k) {
+        double v = f[k];
+        if (in_grid(nx, ny, k, 1, -1)) v += ls[k] * AE(k - nx) * x[k - nx + 1];
+        if (in_grid(nx, ny, k, -1, 1)) v += lw[k] * AT(k - 1) * x[k + nx - 1];
+        y[k] = v;
+      }
+      for (int64_t k = 0; k < N; ++k) {
+        if (in_grid(nx, ny, k, 0, -1)) y[k] -= ls[k] * y[k - nx];
+        if (in_grid(nx, ny, k, -1, 0)) y[k] -= lw[k] * y[k - 1];
+      }
+      for (int64_t k = N - 1; k >= 0; --k) {
+        double v = y[k];
+        if (in_grid(nx, ny, k, 1, 0)) v -= AE(k) * x[k + 1];
+        if (in_grid(nx, ny, k, 0, 1)) v -= AT(k) * x[k + nx];
+        x[k] = v / uc[k];
+      }
+      ++it;
+    }
+#undef AS
+#undef AW
+#undef AE
+#undef AT
+    if (!isfinite(rn)) st = ORC_NONFINITE;
+    else if (!(rn < tol)) st = ORC_NOT_CONVERGED;
+  }
+  if (iters) *iters = it;
+  if (resid) *resid = rn;
+  free(ls); free(lw); free(uc); free(y);
+  return st;
+}
+
+/* The ILU(0) factors of R6b alone (for the pins): ls, lw, uc (ue = e, ut = t). */
+int orc_ilu0_2d(int64_t nx, int64_t ny, const double* s, const double* w, const double* c,
+                const double* e, const double* t, double* ls, double* lw, double* uc) {
+  if (nx < 1 || ny < 1) return ORC_ARG;
+  int64_t N = nx * ny;
+  for (int64_t k = 0; k < N; ++k) {
+    double v = c[k];
+    ls[k] = lw[k] = 0.0;
+    if (in_grid(nx, ny, k, 0, -1)) {
+      ls[k] = s[k] / uc[k - nx];
+      v -= ls[k] * t[k - nx];
+    }
+    if (in_grid(nx, ny, k, -1, 0)) {
+      lw[k] = w[k] / uc[k - 1];
+      v -= lw[k] * e[k - 1];
+    }
+    uc[k] = v;
+    if (v == 0.0) return ORC_ZERO_PIVOT;
+  }
+  return ORC_OK;
+}
+
+/* ------------------------------------------------------------------------- */
 /* R7 -- mixed precision: FP32 R2 solve, then iterative refinement            */
 /*   r = f - A x (FP64, A = the FP64 values of the FP32 diagonals),           */
 /*   s = max|r|, delta = s * solve32(r / s), x += delta (FP64),               */

@@ -62,6 +62,11 @@ MUTANTS = {
     "mnpdm_a_elim_wrong_row": ("C[i] = op_sub(C[i], op_mul(m, D[i - 1], ops), ops);",
                                "C[i] = op_sub(C[i], op_mul(m, C[i - 1], ops), ops);"),
     "mnpdm_rhs_not_eliminated": ("F[i] = op_sub(F[i], op_mul(m, F[i + 1], ops), ops);", ""),
+    "sip2d_fill_dropped_from_k": ("if (in_grid(nx, ny, k, 1, -1)) v += ls[k] * AE(k - nx) * x[k - nx + 1];",
+                                  ""),
+    "sip2d_fill_wrong_column": ("if (in_grid(nx, ny, k, -1, 1)) v += lw[k] * AT(k - 1) * x[k + nx - 1];",
+                                "if (in_grid(nx, ny, k, -1, 1)) v += lw[k] * AT(k - 1) * x[k + nx];"),
+    "ilu0_2d_wrong_u_entry": ("      v -= ls[k] * t[k - nx];", "      v -= ls[k] * e[k - nx];"),
     "symbolic_residue_pivot_ignored": ("if (st == ORC_OK && residue_pivot(n, pa, b, c, fac)) st = ORC_ZERO_PIVOT;",
                                        ""),
     "cond1_not_transposed": ("if (orc_gepp_band(n, k, ta, tb, tc, td, te, y, z, NULL) != ORC_OK)",

@@ -829,3 +829,92 @@ def test_adi_steady_state_converges_to_manufactured_solution(k):
         errs.append(np.abs(u - ue).max())
     rates = [np.log2(errs[i] / errs[i + 1]) for i in range(2)]
     assert min(rates) >= 1.8, (errs, rates)
+
+
+# ------------------------------------------------------- SIP on a 2-D five-point matrix
+def _grid5(rng, nx, ny, r=2.0, spread=0.5):
+    """A backward-Euler-like 2-D five-point matrix: neighbours -r (scaled by factors in
+    [1 - spread, 1 + spread]), diagonal 1 + 4r plus a little; with its dense form."""
+    N = nx * ny
+    s, w, e, t = (-r * rng.uniform(1 - spread, 1 + spread, N) for _ in range(4))
+    c = 1 + 4 * r + rng.uniform(0, 0.1, N)
+    A = np.zeros((N, N))
+    for k in range(N):
+        x, y = k % nx, k // nx
+        A[k, k] = c[k]
+        if y > 0:
+            A[k, k - nx] = s[k]
+        if x > 0:
+            A[k, k - 1] = w[k]
+        if x < nx - 1:
+            A[k, k + 1] = e[k]
+        if y < ny - 1:
+            A[k, k + nx] = t[k]
+    return (s, w, c, e, t), A
+
+
+def _ilu_dense(nx, ny, diags):
+    s, w, c, e, t = diags
+    (ls, lw, uc), st = oracle.ilu0_2d(nx, ny, *diags)
+    assert st == "OK"
+    N = nx * ny
+    L, U = np.eye(N), np.zeros((N, N))
+    for k in range(N):
+        x, y = k % nx, k // nx
+        if y > 0:
+            L[k, k - nx] = ls[k]
+        if x > 0:
+            L[k, k - 1] = lw[k]
+        U[k, k] = uc[k]
+        if x < nx - 1:
+            U[k, k + 1] = e[k]
+        if y < ny - 1:
+            U[k, k + nx] = t[k]
+    return L, U
+
+
+@pytest.mark.parametrize("nx,ny", [(12, 12), (7, 19), (30, 4)])
+def test_ilu0_2d_matches_a_on_its_pattern(nx, ny):
+    """ILU(0)'s defining property (Sec. 2: the zeros of L and U where A has them):
+    (LU)_kj = A_kj wherever A_kj != 0, and LU - A is nonzero only on the two dropped
+    fill diagonals, offsets -(nx - 1) and nx - 1."""
+    rng = np.random.default_rng(nx * ny)
+    diags, A = _grid5(rng, nx, ny)
+    L, U = _ilu_dense(nx, ny, diags)
+    K = L @ U - A
+    assert np.abs(K[A != 0]).max() <= 1e-14 * np.abs(A).max()
+    off = {j - i for i, j in zip(*np.nonzero(np.abs(K) > 1e-14))}
+    assert off == {-(nx - 1), nx - 1}
+
+
+def test_sip2d_one_row_is_ntdm():
+    """ny = 1: the matrix is tridiagonal, ILU(0) is its exact LU, and Algorithm 1 stops
+    after one update at R1's solution."""
+    rng = np.random.default_rng(5)
+    nx = 50
+    diags, A = _grid5(rng, nx, 1)
+    s, w, c, e, t = diags
+    f = rng.uniform(-1, 1, nx)
+    R = oracle.sip2d(nx, 1, *diags, f, tol=1e-12, max_it=10)
+    xt, st = oracle.ntdm(np.r_[0.0, w[1:]], c, np.r_[e[:-1], 0.0], f)
+    assert R["status"] == "OK" and R["iters"] == 1
+    assert np.abs(R["x"] - xt).max() <= 1e-14 * np.abs(xt).max()
+
+
+def test_sip2d_converges_at_the_iteration_matrix_rate():
+    """The residual of Algorithm 1 contracts by the spectral radius of
+    I - (LU)^{-1} A (computed densely); the converged x solves A x = f."""
+    rng = np.random.default_rng(6)
+    nx = ny = 12
+    diags, A = _grid5(rng, nx, ny)
+    f = rng.uniform(-1, 1, nx * ny)
+    L, U = _ilu_dense(nx, ny, diags)
+    rho = max(abs(np.linalg.eigvals(np.eye(nx * ny) - np.linalg.solve(L @ U, A))))
+    res = [oracle.sip2d(nx, ny, *diags, f, tol=0.0, max_it=j)["resid"] for j in range(25, 31)]
+    ratios = [res[i + 1] / res[i] for i in range(len(res) - 1)]
+    assert 0.2 < rho < 0.9
+    assert max(abs(q / rho - 1) for q in ratios) <= 0.02, (rho, ratios)
+    R = oracle.sip2d(nx, ny, *diags, f, tol=1e-12, max_it=500)
+    assert R["status"] == "OK" and R["iters"] > 10
+    xd = np.linalg.solve(A, f)
+    assert np.abs(R["x"] - xd).max() <= 1e-10 * np.abs(xd).max()
