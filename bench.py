@@ -794,6 +794,34 @@ def adi_time_workload(dev, n=GRID, steps=10):
     return out
 
 
+def sip2d_workload(dev, nsys=16384, nx=32, ny=32):
+    """Stone's method where ILU(0) is incomplete: 16384 two-dimensional five-point systems
+    of 32 x 32 unknowns (backward-Euler-like rows: neighbours -r times [0.5, 1], diagonal
+    1 + 4r + [0, 0.1), r in [0.5, 4] per system: diagonally dominant M-matrices, for which
+    ILU(0) is a regular splitting and Algorithm 1 converges), tol 1e-10, interleaved."""
+    import torch
+    import paper_1804_09666_gb300 as band
+    rng = np.random.default_rng(1804_09666 + 400)
+    N = nx * ny
+    r = rng.uniform(0.5, 4.0, nsys)[None, :]
+    d = {q: torch.from_numpy(-r * rng.uniform(0.5, 1.0, (N, nsys))).to(dev) for q in "swet"}
+    d["c"] = torch.from_numpy(1 + 4 * r + rng.uniform(0, 0.1, (N, nsys))).to(dev)
+    f = torch.from_numpy(rng.uniform(-1, 1, (N, nsys))).to(dev)
+    res = {}
+
+    def run():
+        res["x"], res["it"], res["rs"], res["st"] = band.sip2d(
+            d["s"], d["w"], d["c"], d["e"], d["t"], f, nx, tol=1e-10, max_it=500)
+    ms = _time(run)
+    units = N * nsys
+    it = res["it"].float()
+    return {"workload": "Stone's method on %d 2-D five-point systems of %d x %d, tol 1e-10"
+                        % (nsys, nx, ny), "unit": UNIT, "value": units / (ms * 1e-3), "ms": ms,
+            "iters_mean": float(it.mean()), "iters_max": int(it.max()),
+            "status_not_ok": int((res["st"] != 0).sum()),
+            "max_resid": float(res["rs"].max())}
+
+
 # The paper's single-system timings at N = 10^8 (Table 3, HybriLIT, one Xeon E5-2695v2
 # core, double precision): NPDM 2.7946627 s, NTDM 2.0525187 s.  Context only.
 PAPER_1E8_S = {"npdm": 2.7946627, "ntdm": 2.0525187}
@@ -846,7 +874,7 @@ EXTRA_WORKLOADS = {"ragged": "ragged_workload", "small_batch": "small_batch_work
                    "precision": "precision_workload", "adjoint": "adjoint_workload",
                    "sip": "sip_workload", "symbolic": "symbolic_workload",
                    "single": "single_system_workload", "mnpdm": "mnpdm_workload",
-                   "adi_time": "adi_time_workload"}
+                   "adi_time": "adi_time_workload", "sip2d": "sip2d_workload"}
 
 
 # ---------------------------------------------------------------------- main
@@ -973,7 +1001,8 @@ def main():
                              "symbolic": symbolic_workload(dev),
                              "single": single_system_workload(dev),
                              "mnpdm": mnpdm_workload(dev),
-                             "adi_time": adi_time_workload(dev)}
+                             "adi_time": adi_time_workload(dev),
+                             "sip2d": sip2d_workload(dev)}
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         line["cpu_baseline"] = cpu_baseline(W)
     if rank == 0:

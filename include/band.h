@@ -180,7 +180,8 @@ enum {
   BAND_OP_REFINE = 3,     /* band_refine_solve */
   BAND_OP_ADJOINT = 4,    /* band_adjoint */
   BAND_OP_DET = 5,        /* band_det */
-  BAND_OP_ADI = 6         /* band_adi_step (desc describes the grid, see there) */
+  BAND_OP_ADI = 6,        /* band_adi_step (desc describes the grid, see there) */
+  BAND_OP_SIP2D = 7       /* band_sip2d */
 };
 size_t band_workspace_size(const band_desc* desc, int32_t op, int32_t method, int32_t sip_width);
 
@@ -228,6 +229,22 @@ band_status band_solve(const band_desc* desc, int32_t method, const void* factor
 band_status band_adi_step(const band_desc* grid, double tau, double lambda, const double* source,
                           double* u, int32_t* sys_status, void* ws, size_t ws_bytes,
                           void* stream);
+
+/* Stone's method (Sec. 2, Algorithm 1) on a batch of two-dimensional five-point
+ * systems, where ILU(0) drops the fill that the pattern creates (on the PD band it is
+ * the exact LU and Algorithm 1 stops after one update).  System s is an nx x ny grid,
+ * unknown k = y nx + x (desc->n = nx * ny, uniform layout, FP64); row k of the matrix
+ * holds diag[0][k] at column k - nx, diag[1][k] at k - 1, diag[2][k] at k, diag[3][k]
+ * at k + 1, diag[4][k] at k + nx (entries that would leave the grid are read but never
+ * used).  ILU(0) with L's and U's entries on A's pattern, then from x^0 = 0 updates
+ * LU x^{j+1} = (LU - A) x^j + f until max|f - A x| < tol (status OK) or max_it updates
+ * (BAND_ERR_NOT_CONVERGED); a zero ILU(0) pivot is BAND_ERR_ZERO_PIVOT.  One thread per
+ * system (desc->schedule AUTO, chunks 0); x must not alias f; iters, resid (per
+ * system) may be NULL.  ws: band_workspace_size(desc, BAND_OP_SIP2D, 0, 0). */
+band_status band_sip2d(const band_desc* desc, int64_t nx, const void* const diag[5],
+                       const double* f, double* x, double tol, int32_t max_it, int32_t* iters,
+                       double* resid, int32_t* sys_status, void* ws, size_t ws_bytes,
+                       void* stream);
 
 /* band_solve with method BAND_MNPDM (Sec. 1: the PD method that takes the sparsity of the
  * outer diagonals into account; Sec. 3.2 Remark 2: the Gaussian elimination that turns the

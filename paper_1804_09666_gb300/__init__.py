@@ -8,8 +8,8 @@ of include/band.h.  This package is the thin Python binding over torch CUDA tens
 """
 from ._lib import BandError, load  # noqa: F401
 from .band import (AdiStepper, BandSolve, BatchPlan, RaggedPlan, adjoint, desc_for, det, factor,  # noqa: F401
-                   refine_solve, sip, slogdet, solve, solve_batch, solve_ragged, status_names)
+                   refine_solve, sip, sip2d, slogdet, solve, solve_batch, solve_ragged, status_names)
 
 __all__ = ["AdiStepper", "solve", "solve_ragged", "solve_batch", "BatchPlan", "RaggedPlan", "factor", "sip",
-           "refine_solve", "adjoint", "det", "slogdet", "BandSolve", "desc_for", "status_names", "load",
+           "refine_solve", "sip2d", "adjoint", "det", "slogdet", "BandSolve", "desc_for", "status_names", "load",
            "BandError"]

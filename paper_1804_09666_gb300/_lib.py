@@ -24,12 +24,12 @@ F64, F32 = 0, 1
 SCHED_AUTO, SCHED_THREAD, SCHED_TWO_SIDED, SCHED_PARTITIONED, SCHED_GRID = 0, 1, 2, 3, 4
 TUNE_JOINT = 1
 # BAND_OP_*
-OP_SOLVE, OP_FACTOR, OP_SIP, OP_REFINE, OP_ADJOINT, OP_DET, OP_ADI = range(7)
+OP_SOLVE, OP_FACTOR, OP_SIP, OP_REFINE, OP_ADJOINT, OP_DET, OP_ADI, OP_SIP2D = range(8)
 
 EXPORTS = ("band_workspace_size", "band_solve", "band_factor", "band_sip", "band_refine_solve",
            "band_adjoint", "band_status_str", "band_version", "band_fp64_fma_rate",
            "band_solve_batch", "band_solve_static", "band_plan_ragged", "band_autotune",
-           "band_autotune_reset", "band_det", "band_adi_step")
+           "band_autotune_reset", "band_det", "band_adi_step", "band_sip2d")
 MAX_BATCH = 64
 
 
@@ -79,6 +79,8 @@ def load(path=None):
     lib.band_det.argtypes = [D, DIAG5, P, P, P, P, sz, P]
     lib.band_adi_step.argtypes = [D, dbl, dbl, P, P, P, P, sz, P]
     lib.band_adi_step.restype = ct.c_int
+    lib.band_sip2d.argtypes = [D, i64, DIAG5, P, P, dbl, i32, P, P, P, P, sz, P]
+    lib.band_sip2d.restype = ct.c_int
     for name in ("band_solve", "band_factor", "band_sip", "band_refine_solve", "band_adjoint",
                  "band_det"):
         getattr(lib, name).restype = ct.c_int

@@ -168,6 +168,30 @@ def slogdet(a, b, c, d, e, half_bw=2):
     return sign, logabs, status
 
 
+def sip2d(s, w, c, e, t, f, nx, tol=1e-10, max_it=500, x=None):
+    """Stone's method on a batch of 2-D five-point systems (band_sip2d): (n, nsys)
+    float64 tensors with n = nx * ny, unknown k = y nx + x; s, w, c, e, t the entries at
+    columns k - nx, k - 1, k, k + 1, k + nx.  Returns (x, iters, resid, status)."""
+    lib = L.load()
+    _check_same(c, s, w, e, t, f)
+    if c.dtype != torch.float64:
+        raise ValueError("band_sip2d takes float64 arrays")
+    desc = desc_for(c, 2)
+    if x is None:
+        x = torch.empty_strided(c.shape, c.stride(), dtype=c.dtype, device=c.device)
+    _check_same(c, x)
+    nsys = c.shape[1]
+    iters = torch.empty(nsys, dtype=torch.int32, device=c.device)
+    resid = torch.empty(nsys, dtype=torch.float64, device=c.device)
+    status = torch.empty(nsys, dtype=torch.int32, device=c.device)
+    ws = _workspace(lib.band_workspace_size(ct.byref(desc), L.OP_SIP2D, 0, 0), c.device)
+    code = lib.band_sip2d(ct.byref(desc), int(nx), _diag5(s, w, c, e, t), _ptr(f), _ptr(x),
+                          float(tol), int(max_it), _ptr(iters), _ptr(resid), _ptr(status),
+                          _ptr(ws), _bytes(ws), _stream())
+    L.check(code, "band_sip2d")
+    return x, iters, resid, status
+
+
 class AdiStepper:
     """Time steps of u_t = u_xx + u_yy + lam u (1 - u) + s on an n x n grid (Peaceman-
     Rachford ADI; band_adi_step): u is an (n, n) float64 CUDA tensor, u[y, x], updated

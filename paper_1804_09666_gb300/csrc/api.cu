@@ -242,6 +242,7 @@ size_t band_workspace_size(const band_desc* desc, int32_t op, int32_t method, in
     case BAND_OP_REFINE: return refine_workspace_bytes(desc);
     case BAND_OP_ADJOINT: return adjoint_workspace_bytes(desc);
     case BAND_OP_DET: return det_workspace_bytes(desc);
+    case BAND_OP_SIP2D: return sip2d_workspace_bytes(desc);
     default: return 0;
   }
 }

@@ -121,6 +121,7 @@ size_t refine_workspace_bytes(const band_desc* d);
 size_t adjoint_workspace_bytes(const band_desc* d);
 size_t det_workspace_bytes(const band_desc* d);
 size_t adi_workspace_bytes(const band_desc* grid);
+size_t sip2d_workspace_bytes(const band_desc* d);
 // MNPDM (mnpdm.cu): band_solve's path and workspace for BAND_MNPDM
 size_t mnpdm_workspace_bytes(const band_desc* d);
 band_status mnpdm_solve(const band_desc* desc, const void* const diag[5], const void* f, void* x,

@@ -1,0 +1,198 @@
+// sip2d.cu -- band_sip2d: Stone's method (Sec. 2, Algorithm 1) on a batch of
+// two-dimensional five-point systems, the setting where ILU(0) is incomplete.
+//
+// Unknown k = y nx + x of an nx x ny grid; row k holds s_k (column k - nx), w_k (k - 1),
+// c_k (k), e_k (k + 1), t_k (k + nx), stored in the a, b, c, d, e slots of the band
+// arrays; entries that would leave the grid are read but never used.  ILU(0) keeps L's
+// and U's entries on A's pattern (L unit lower with ls, lw; U with uc and A's own e, t):
+//   ls_k = s_k / uc_{k-nx},  lw_k = w_k / uc_{k-1},  uc_k = c_k - ls_k t_{k-nx} - lw_k e_{k-1};
+// the fill products ls_k e_{k-nx} (column k - nx + 1) and lw_k t_{k-1} (column k + nx - 1)
+// are dropped, so K = LU - A lives on those two diagonals.  Algorithm 1 from x^0 = 0:
+// while max|f - A x| >= tol, solve L y = K x + f (forward), U x = y (backward).
+// One thread per system runs the factorisation and every update: three sequential
+// passes per update over the system's rows (residual, forward, backward) on interleaved
+// data (coalesced across the warp's systems); the neighbours k - 1 and k + 1 are kept in
+// registers, those at k -+ nx re-read (the thread wrote them nx rows before: L1 / L2).
+// Statuses: OK, NOT_CONVERGED (max_it updates), ZERO_PIVOT (uc_k = 0), NONFINITE.
+#include <cstdint>
+
+#include "api_util.h"
+#include "kernels.h"
+
+namespace band {
+
+namespace {
+
+struct Sip2dArgs {
+  Layout L;
+  Spill W;
+  int64_t nx, ny;
+  const double *s, *w, *c, *e, *t, *f;
+  double* x;
+  double *ls, *lw, *ruc, *y;
+  double tol;
+  int32_t max_it;
+  int32_t* iters;
+  double* resid;
+  int32_t* status;
+};
+
+__global__ void __launch_bounds__(128) k_sip2d(const Sip2dArgs p) {
+  const int64_t th = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (th >= p.L.nsys) return;
+  const int64_t sys = p.L.sys(th);
+  const int64_t nx = p.nx, ny = p.ny, N = nx * ny;
+  const int64_t q0 = p.L.base(sys), es = p.L.stride();
+  const int64_t w0 = p.W.base(th), ws = p.W.stride();
+  auto Q = [&](int64_t k) { return q0 + k * es; };     // input / output element k
+  auto Wk = [&](int64_t k) { return w0 + k * ws; };    // scratch element k
+  int32_t st = BAND_OK;
+  // ---- ILU(0)
+  {
+    int64_t xk = 0, yk = 0;
+    double uc1 = 0.0, e1 = 0.0;      // uc_{k-1}, e_{k-1}
+    for (int64_t k = 0; k < N; ++k) {
+      double v = ldro(p.c + Q(k));
+      double lsk = 0.0, lwk = 0.0;
+      if (yk > 0) {
+        lsk = ldro(p.s + Q(k)) * p.ruc[Wk(k - nx)];
+        v = fma(-lsk, ldro(p.t + Q(k - nx)), v);
+      }
+      if (xk > 0) {
+        lwk = ldro(p.w + Q(k)) * uc1;
+        v = fma(-lwk, e1, v);
+      }
+      if (is_zero(v)) {
+        st = BAND_ERR_ZERO_PIVOT;
+        break;
+      }
+      const double r = rcp64(v);
+      p.ls[Wk(k)] = lsk;
+      p.lw[Wk(k)] = lwk;
+      p.ruc[Wk(k)] = r;
+      uc1 = r;
+      e1 = ldro(p.e + Q(k));
+      if (++xk == nx) { xk = 0; ++yk; uc1 = 0.0; e1 = 0.0; }
+    }
+  }
+  int32_t it = 0;
+  double rn = 0.0;
+  if (st == BAND_OK) {
+    for (int64_t k = 0; k < N; ++k) p.x[Q(k)] = 0.0;
+    for (;;) {
+      // ---- r = f - A x, max |r|
+      rn = 0.0;
+      {
+        int64_t xk = 0, yk = 0;
+        double xm = 0.0, x0 = p.x[Q(0)];
+        for (int64_t k = 0; k < N; ++k) {
+          const double xp = (xk + 1 < nx) ? p.x[Q(k + 1)] : 0.0;
+          double ax = ldro(p.c + Q(k)) * x0;
+          if (yk > 0) ax = fma(ldro(p.s + Q(k)), p.x[Q(k - nx)], ax);
+          if (xk > 0) ax = fma(ldro(p.w + Q(k)), xm, ax);
+          if (xk + 1 < nx) ax = fma(ldro(p.e + Q(k)), xp, ax);
+          if (yk + 1 < ny) ax = fma(ldro(p.t + Q(k)), p.x[Q(k + nx)], ax);
+          const double r = fabs(p.f[Q(k)] - ax);
+          if (!(r <= rn)) rn = r;
+          xm = x0;
+          x0 = xp;
+          if (++xk == nx) {
+            xk = 0;
+            ++yk;
+            xm = 0.0;
+            x0 = (k + 1 < N) ? p.x[Q(k + 1)] : 0.0;
+          }
+        }
+      }
+      if (rn < p.tol || it >= p.max_it || not_finite(rn)) break;
+      // ---- forward: L y = K x + f
+      {
+        int64_t xk = 0, yk = 0;
+        double y1 = 0.0;
+        for (int64_t k = 0; k < N; ++k) {
+          double v = p.f[Q(k)];
+          const double lsk = p.ls[Wk(k)], lwk = p.lw[Wk(k)];
+          if (yk > 0 && xk + 1 < nx) v = fma(lsk * ldro(p.e + Q(k - nx)), p.x[Q(k - nx + 1)], v);
+          if (xk > 0 && yk + 1 < ny) v = fma(lwk * ldro(p.t + Q(k - 1)), p.x[Q(k + nx - 1)], v);
+          if (yk > 0) v = fma(-lsk, p.y[Wk(k - nx)], v);
+          if (xk > 0) v = fma(-lwk, y1, v);
+          p.y[Wk(k)] = v;
+          y1 = v;
+          if (++xk == nx) { xk = 0; ++yk; y1 = 0.0; }
+        }
+      }
+      // ---- backward: U x = y
+      {
+        int64_t xk = nx - 1, yk = ny - 1;
+        double x1 = 0.0;
+        for (int64_t k = N - 1; k >= 0; --k) {
+          double v = p.y[Wk(k)];
+          if (xk + 1 < nx) v = fma(-ldro(p.e + Q(k)), x1, v);
+          if (yk + 1 < ny) v = fma(-ldro(p.t + Q(k)), p.x[Q(k + nx)], v);
+          v *= p.ruc[Wk(k)];
+          p.x[Q(k)] = v;
+          x1 = v;
+          if (xk-- == 0) { xk = nx - 1; --yk; x1 = 0.0; }
+        }
+      }
+      ++it;
+    }
+    if (not_finite(rn)) st = BAND_ERR_NONFINITE;
+    else if (!(rn < p.tol)) st = BAND_ERR_NOT_CONVERGED;
+  }
+  set_status(p.status, sys, st);
+  if (p.iters) p.iters[sys] = it;
+  if (p.resid) p.resid[sys] = rn;
+}
+
+struct Sip2dWs {
+  void *ls, *lw, *ruc, *y;
+};
+Sip2dWs carve_sip2d(const band_desc* d, void* base, size_t* bytes) {
+  Carve c(base);
+  const size_t rows = (size_t)spill_rows(d) * sizeof(double);
+  Sip2dWs w;
+  w.ls = c.take(rows);
+  w.lw = c.take(rows);
+  w.ruc = c.take(rows);
+  w.y = c.take(rows);
+  *bytes = c.size();
+  return w;
+}
+
+}  // namespace
+
+size_t sip2d_workspace_bytes(const band_desc* d) {
+  if (d->dtype != BAND_F64 || d->offsets) return 0;
+  size_t b = 0;
+  carve_sip2d(d, nullptr, &b);
+  return b;
+}
+
+}  // namespace band
+
+using namespace band;
+
+extern "C" band_status band_sip2d(const band_desc* desc, int64_t nx, const void* const diag[5],
+                                  const double* f, double* x, double tol, int32_t max_it,
+                                  int32_t* iters, double* resid, int32_t* sys_status, void* ws,
+                                  size_t ws_bytes, void* stream) {
+  if (!desc_ok(desc) || desc->dtype != BAND_F64 || desc->offsets || desc->hbw) return BAND_ERR_ARG;
+  if (desc->schedule != BAND_SCHED_AUTO || desc->chunks) return BAND_ERR_ARG;
+  if (nx < 1 || desc->n % nx != 0 || !(tol == tol) || max_it < 0) return BAND_ERR_ARG;
+  if (desc->nsys == 0) return BAND_OK;
+  if (!diag || !diag[0] || !diag[1] || !diag[2] || !diag[3] || !diag[4] || !f || !x)
+    return BAND_ERR_ARG;
+  if ((const void*)x == (const void*)f) return BAND_ERR_ARG;
+  size_t need = 0;
+  carve_sip2d(desc, nullptr, &need);
+  if (!ws || ws_bytes < need) return BAND_ERR_WORKSPACE;
+  const Sip2dWs w = carve_sip2d(desc, ws, &need);
+  Sip2dArgs p{layout_of(desc), spill_of(desc), nx, desc->n / nx,
+              (const double*)diag[0], (const double*)diag[1], (const double*)diag[2],
+              (const double*)diag[3], (const double*)diag[4], f, x, (double*)w.ls,
+              (double*)w.lw, (double*)w.ruc, (double*)w.y, tol, max_it, iters, resid,
+              sys_status};
+  k_sip2d<<<(unsigned)((desc->nsys + 127) / 128), 128, 0, static_cast<cudaStream_t>(stream)>>>(p);
+  return cuda_status(cudaGetLastError());
+}

@@ -172,6 +172,17 @@ def test_bad_arguments_are_rejected_without_gpu(lib):
     assert lib.band_adi_step(ct.byref(grid), 0.0, 1.0, None, 8, None, 8, 1 << 40, None) == L.ERR_ARG
     assert lib.band_adi_step(ct.byref(grid), 0.1, 1.0, None, None, None, 8, 1 << 40, None) == L.ERR_ARG
     assert lib.band_adi_step(ct.byref(grid), 0.1, 1.0, None, 8, None, 8, 64, None) == L.ERR_WORKSPACE
+    # 2-D SIP: nx must divide n, x must not alias f, FP64 uniform only
+    d2 = _desc(nsys=64, n=120)
+    assert lib.band_sip2d(ct.byref(d2), 7, full, 8, 16, 1e-10, 10, None, None, None, 8, 1 << 30,
+                          None) == L.ERR_ARG
+    assert lib.band_sip2d(ct.byref(d2), 12, full, 8, 8, 1e-10, 10, None, None, None, 8, 1 << 30,
+                          None) == L.ERR_ARG
+    assert lib.band_sip2d(ct.byref(_desc(nsys=64, n=120, dtype=L.F32)), 12, full, 8, 16, 1e-10, 10,
+                          None, None, None, 8, 1 << 30, None) == L.ERR_ARG
+    assert lib.band_sip2d(ct.byref(d2), 12, full, 8, 16, 1e-10, 10, None, None, None, 8, 64,
+                          None) == L.ERR_WORKSPACE
+    assert lib.band_workspace_size(ct.byref(d2), L.OP_SIP2D, 0, 0) >= 4 * 64 * 120 * 8
     # its workspace is the flagged-system counter and list
     assert lib.band_workspace_size(ct.byref(d), L.OP_DET, 0, 0) >= 8 + 64 * 8
 
