@@ -182,6 +182,7 @@ class DeviceSet:
             view = {q: flat[q].as_strided((n, ns), (es, ss)) for q in keys}
             self.items.append(dict(w=w, host=host_in, flat=flat, view=view, n=n, nsys=ns))
         # heaviest problems first: SIP, then the PD sweeps, then the TD sweeps
+        self.spec_items = []
         for kind in ("sip", "npdm", "spdm", "ntdm", "stdm"):
             for it in self.items:
                 if kind not in methods_for(it["w"]["k"]):
@@ -195,6 +196,7 @@ class DeviceSet:
                     sp = dict(method=kind, a=None, e=None, **v)
                 specs.append(sp)
                 self.spec_methods.append((kind, it["n"] * it["nsys"]))
+                self.spec_items.append(it)
         self.plan = band.BatchPlan(specs)
         # outputs are compact strided views; copy their storage as flat buffers
         self.out_flat = [r["x"].as_strided((r["x"].numel(),), (1,)) for r in self.plan.results]
@@ -259,6 +261,54 @@ class DeviceSet:
         residual, decision and tail passes."""
         kinds = {k for k, _ in self.spec_methods}
         return 1 + int(bool(kinds & {"spdm", "stdm"})) + 3 * int("sip" in kinds)
+
+
+def accuracy_report(D, sample_every=128):
+    """Forward errors of one step's results: every system against its manufactured
+    solution, and every `sample_every`-th system of every solve against the CPU oracle's
+    result for the same method (relative max-norm per system, maxed).  SIP systems that
+    stop NOT_CONVERGED at their rounding floor are reported on their own."""
+    import oracle
+    D.step()
+    D.torch.cuda.synchronize()
+    kind_of = {"npdm": "direct", "ntdm": "direct", "spdm": "symbolic", "stdm": "symbolic",
+               "sip": "sip"}
+    worst_oracle, worst_true, checked = 0.0, 0.0, 0
+    per_method = {}
+    sip_floor = {"systems": 0, "max_err_vs_manufactured": 0.0}
+    for (kind, _), it, r in zip(D.spec_methods, D.spec_items, D.plan.results):
+        B = it["w"]["B"]
+        n, ns, ss, es = B["n"], B["nsys"], B["sys_stride"], B["elem_stride"]
+        x = r["x"].cpu().numpy()                       # (n, nsys) view of the output
+        st = r["status"].cpu().numpy()
+        xt = B["x_true"]
+        idx = np.arange(ns)[None, :] * ss + np.arange(n)[:, None] * es
+        xtrue = xt[idx]
+        err_true = np.abs(x - xtrue).max(0) / np.abs(xtrue).max(0)
+        ok = st == 0
+        worst_true = max(worst_true, float(err_true[ok].max()) if ok.any() else 0.0)
+        if kind == "sip" and (~ok).any():
+            sip_floor["systems"] += int((~ok).sum())
+            sip_floor["max_err_vs_manufactured"] = max(sip_floor["max_err_vs_manufactured"],
+                                                       float(err_true[~ok].max()))
+        nsamp = (ns + sample_every - 1) // sample_every
+        diags = [B[q] if it["w"]["k"] == 2 or q in "bcd" else None for q in "abcde"]
+        xo, so, _, _ = oracle.batch(kind_of[kind], it["w"]["k"], diags, B["f"], nsamp, n,
+                                    ss * sample_every, es, tol=SIP_TOL, max_it=SIP_MAX_IT,
+                                    hb_width=0)
+        cols = np.arange(0, ns, sample_every)
+        io = np.arange(nsamp)[None, :] * (ss * sample_every) + np.arange(n)[:, None] * es
+        xo = xo[io]
+        good = (so == 0) & ok[cols]
+        if good.any():
+            e = np.abs(x[:, cols] - xo).max(0) / np.abs(xo).max(0)
+            worst_oracle = max(worst_oracle, float(e[good].max()))
+            per_method[kind] = max(per_method.get(kind, 0.0), float(e[good].max()))
+        checked += int(good.sum())
+    return {"max_rel_err_vs_oracle": worst_oracle, "oracle_systems_checked": checked,
+            "max_rel_err_vs_oracle_by_method": per_method,
+            "max_rel_err_vs_manufactured": worst_true,
+            "sip_not_converged_at_rounding_floor": sip_floor}
 
 
 def e2e_serial(D, steps, world):
@@ -382,9 +432,12 @@ def cpu_baseline(W, budget_s=15.0):
         for _ in range(reps):
             ui, di = oracle_sample(W, per, nthreads)
             u, dt = u + ui, dt + di
+    u1, dt1 = oracle_sample(W, 64, 1)
     return {"value": u / dt, "unit": UNIT, "cores": nthreads, "kind": "oracle",
             "sample": "first %d systems of each of the 30 batched solves (every r, sweep and "
-                      "method) of the same workload, %d pass(es); %.1f s" % (per, reps, dt)}
+                      "method) of the same workload, %d pass(es); %.1f s" % (per, reps, dt),
+            "one_core": {"value": u1 / dt1, "unit": UNIT, "cores": 1,
+                         "sample": "first 64 systems of each of the 30 solves; %.1f s" % dt1}}
 
 
 def run_reference(args, world, rank):
@@ -392,7 +445,7 @@ def run_reference(args, world, rank):
         return
     W = host_workload(args.grid)
     nthreads = os.cpu_count() or 1
-    per = 8
+    per = max(8, nthreads)          # at least one system per host core in every solve
     for _ in range(args.warmup):
         oracle_sample(W, per, nthreads)
     units, total = 0, 0.0
@@ -407,8 +460,8 @@ def run_reference(args, world, rank):
             "vs_baseline": None, "dtype": "f64", "data": "synthetic",
             "config": workload_config(args.grid, args.gpus),
             "cpu_baseline": {"value": value, "unit": UNIT, "cores": nthreads, "kind": "oracle",
-                             "sample": "first %d systems of each of the 30 batched solves per step"
-                                       % per},
+                             "sample": "first %d systems of each of the 30 batched solves per step "
+                                       "(at least one per host core)" % per},
             "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
     print(json.dumps(line), flush=True)
 
@@ -674,6 +727,29 @@ def adjoint_workload(dev):
     return out
 
 
+def cfg0_workload(dev):
+    """The small plain-NPDM configuration (1024 dominant PD systems of n = 128, 7 MiB:
+    fits in L2): latency of one band_solve, against the oracle on every system."""
+    import torch
+    import oracle
+    import paper_1804_09666_gb300 as band
+    B = synth.cfg0()
+    n, ns = B["n"], B["nsys"]
+    d = {q: torch.from_numpy(B[q].reshape(n, ns)).to(dev) for q in "abcdef"}
+    x = torch.empty_like(d["f"])
+    res = {}
+
+    def run():
+        res["x"], res["st"] = band.solve(*(d[q] for q in "abcdef"), method="npdm", x=x)
+    ms = _time(run, reps=20, warm=3)
+    xo, so, _, _ = oracle.batch("direct", 2, [B[q] for q in "abcde"], B["f"], ns, n, 1, ns)
+    xg = res["x"].cpu().numpy().reshape(-1)
+    err = (np.abs(xg - xo).reshape(n, ns).max(0) / np.abs(xo).reshape(n, ns).max(0)).max()
+    return {"workload": "1024 PD systems, n = 128, NPDM (fits in L2: latency, not roofline)",
+            "latency_ms": ms, "value": n * ns / (ms * 1e-3), "unit": UNIT,
+            "status_not_ok": int((res["st"] != 0).sum()), "max_rel_err_vs_oracle": float(err)}
+
+
 def symbolic_workload(dev):
     """SPDM on one ADI sweep (2048 PD systems of n = 2048, r = 2, y-sweep: interleaved)
     with an exact zero pivot planted in 0 %, 1 % and 10 % of the systems (row j of a
@@ -874,7 +950,8 @@ EXTRA_WORKLOADS = {"ragged": "ragged_workload", "small_batch": "small_batch_work
                    "precision": "precision_workload", "adjoint": "adjoint_workload",
                    "sip": "sip_workload", "symbolic": "symbolic_workload",
                    "single": "single_system_workload", "mnpdm": "mnpdm_workload",
-                   "adi_time": "adi_time_workload", "sip2d": "sip2d_workload"}
+                   "adi_time": "adi_time_workload", "sip2d": "sip2d_workload",
+                   "cfg0": "cfg0_workload"}
 
 
 # ---------------------------------------------------------------------- main
@@ -994,8 +1071,11 @@ def main():
             "clocks": ck, "e2e": e2e, "gpu_launches": launches_per_step * args.steps,
             "roofline": roof, "status_not_ok": bad,
             "fp64_fma_per_s": fma_rate}
+    if rank == 0:
+        line["accuracy"] = accuracy_report(D)
     if rank == 0 and world == 1 and not args.no_extras and args.grid == GRID:
-        line["workloads"] = {"ragged": ragged_workload(dev), "small_batch": small_batch_workload(dev),
+        line["workloads"] = {"cfg0": cfg0_workload(dev), "ragged": ragged_workload(dev),
+                             "small_batch": small_batch_workload(dev),
                              "precision": precision_workload(dev),
                              "adjoint": adjoint_workload(dev), "sip": sip_workload(dev),
                              "symbolic": symbolic_workload(dev),
