@@ -664,18 +664,52 @@ def precision_workload(dev):
     x64 = torch.empty_like(f)
     ms64 = _time(lambda: band.solve(*(d64[q] for q in "abcde"), f, method="npdm", x=x64))
     out["fp64_npdm"] = {"value": units / (ms64 * 1e-3), "ms": ms64, "max_rel_err": rel(x64)}
-    res = {}
+    import oracle
+    sample = np.random.default_rng(5).choice(nsys, 8, replace=False)
+    truth = {}
+    for s_ in sample:
+        S = {q: B[q].reshape(n, nsys)[:, s_].astype(np.float64) for q in "abcde"}
+        truth[int(s_)] = oracle.gepp_band(2, *(S[q] for q in "abcde"),
+                                          B["f"].reshape(n, nsys)[:, s_])[0]
 
-    def run_refine():
-        res["x"], res["steps"], res["st"] = band.refine_solve(*(d32[q] for q in "abcde"), f)
-    msr = _time(run_refine)
-    steps = res["steps"].cpu().numpy()
-    out["fp32_refine"] = {"value": units / (msr * 1e-3), "ms": msr, "max_rel_err": rel(res["x"]),
-                          "steps_max": int(steps.max()), "steps_mean": float(steps.mean()),
-                          "status_not_ok": int((res["st"] != 0).sum())}
+    def vs_oracle(x):
+        xg = x.cpu().numpy()
+        return max(float(np.abs(xg[:, s_] - xo).max() / np.abs(xo).max())
+                   for s_, xo in truth.items())
+
+    # the FP32 solve alone on each schedule (the refinement's dominant part)
+    f32 = f.float()
+    x32 = torch.empty_like(f32)
+    sched_ms = {}
+    for sched, ch in (("two_sided", 0), ("partitioned", 8), ("partitioned", 16),
+                      ("partitioned", 32)):
+        sched_ms["%s%s" % (sched, "_%d" % ch if ch else "")] = _time(
+            lambda: band.solve(*(d32[q] for q in "abcde"), f32, method="npdm", x=x32,
+                               schedule=sched, chunks=ch))
+    out["fp32_npdm_solve_ms"] = sched_ms
+    best = min(sched_ms, key=sched_ms.get)
+    bsched, bch = ("partitioned", int(best.split("_")[-1])) if best.startswith("partitioned") \
+        else (best, 0)
+    out["fp32_schedule_used"] = best
+    for name, pairs in (("fp32_refine", False), ("fp32_refine_pairs", True)):
+        res = {}
+
+        def run_refine():
+            res["x"], res["steps"], res["st"] = band.refine_solve(*(d32[q] for q in "abcde"), f,
+                                                                  pairs=pairs, schedule=bsched,
+                                                                  chunks=bch)
+        msr = _time(run_refine)
+        steps = res["steps"].cpu().numpy()
+        out[name] = {"value": units / (msr * 1e-3), "ms": msr, "max_rel_err": rel(res["x"]),
+                     "max_rel_err_vs_oracle_gepp": vs_oracle(res["x"]),
+                     "steps_max": int(steps.max()), "steps_mean": float(steps.mean()),
+                     "status_not_ok": int((res["st"] != 0).sum()),
+                     "residual_and_update": "FP32 pairs" if pairs else "FP64"}
+    out["fp64_npdm"]["max_rel_err_vs_oracle_gepp"] = vs_oracle(x64)
     out["workload"] = "16384 PD systems, n = 4096, FP32 storage (%d unknowns)" % units
     out["unit"] = UNIT
     out["refine_over_fp64"] = out["fp32_refine"]["value"] / out["fp64_npdm"]["value"]
+    out["refine_pairs_over_fp64"] = out["fp32_refine_pairs"]["value"] / out["fp64_npdm"]["value"]
     return out
 
 

@@ -321,14 +321,26 @@ band_status band_solve_batch(const band_problem* problems, int32_t count, void* 
 
 /* Mixed precision: PD/TD systems stored in FP32 (desc->dtype = BAND_F32 describes
  * diag32), right-hand side and solution in FP64 with the same strides.  FP32 NPDM/NTDM
- * solve, then refinement steps r = f - A x (FP64, A = the FP64 values of the FP32
- * diagonals), delta = s * solve32(r / s) with s = max|r|, x += delta (FP64), until
- * max|delta| <= rel_stop * max|x| or max_steps steps.  steps (int32[nsys]) may be NULL.
- * The FP32 solves run on desc32->schedule (and chunks) as band_solve's would. */
+ * solve, then refinement steps r = f - A x (A = the FP64 values of the FP32 diagonals),
+ * delta = s * solve32(r / s) with s a power of two near max|f| 2^-20, x += delta,
+ * until max|delta| <= rel_stop * max|x| or max_steps steps.  steps (int32[nsys]) may be
+ * NULL.  The FP32 solves run on desc32->schedule (and chunks) as band_solve's would
+ * (not BAND_SCHED_GRID).
+ * band_refine_solve forms the residual and the update in FP64 (fused multiply-adds on
+ * the caller's FP64 x; x must not alias f).  band_refine_solve_ex with
+ * flags = BAND_REFINE_PAIRS keeps x, f, the residual and the update as pairs of FP32
+ * numbers with error-free transformations instead (about 2^-48 relative; no FP64
+ * arithmetic until x is assembled at the end; x may alias f); flags = 0 is
+ * band_refine_solve. */
+#define BAND_REFINE_PAIRS 1
 band_status band_refine_solve(const band_desc* desc32, const void* const diag32[5],
                               const double* f, double* x, double rel_stop, int32_t max_steps,
                               int32_t* steps, int32_t* sys_status, void* ws, size_t ws_bytes,
                               void* stream);
+band_status band_refine_solve_ex(const band_desc* desc32, const void* const diag32[5],
+                                 const double* f, double* x, double rel_stop, int32_t max_steps,
+                                 int32_t flags, int32_t* steps, int32_t* sys_status, void* ws,
+                                 size_t ws_bytes, void* stream);
 
 /* Adjoint of x = A^{-1} f for a loss L with dL/dx = w (FP64, NTDM/NPDM factorisation):
  * lambda = A^{-T} w by the transposed sweeps of the LU factors, then

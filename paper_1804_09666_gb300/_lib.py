@@ -23,13 +23,15 @@ F64, F32 = 0, 1
 # band_schedule
 SCHED_AUTO, SCHED_THREAD, SCHED_TWO_SIDED, SCHED_PARTITIONED, SCHED_GRID = 0, 1, 2, 3, 4
 TUNE_JOINT = 1
+REFINE_PAIRS = 1
 # BAND_OP_*
 OP_SOLVE, OP_FACTOR, OP_SIP, OP_REFINE, OP_ADJOINT, OP_DET, OP_ADI, OP_SIP2D = range(8)
 
 EXPORTS = ("band_workspace_size", "band_solve", "band_factor", "band_sip", "band_refine_solve",
            "band_adjoint", "band_status_str", "band_version", "band_fp64_fma_rate",
            "band_solve_batch", "band_solve_static", "band_plan_ragged", "band_autotune",
-           "band_autotune_reset", "band_det", "band_adi_step", "band_sip2d")
+           "band_autotune_reset", "band_det", "band_adi_step", "band_sip2d",
+           "band_refine_solve_ex")
 MAX_BATCH = 64
 
 
@@ -75,6 +77,8 @@ def load(path=None):
     lib.band_factor.argtypes = [D, i32, DIAG5, P, sz, P, P]
     lib.band_sip.argtypes = [D, DIAG5, P, P, dbl, i32, i32, i32, dbl, P, P, P, P, sz, P]
     lib.band_refine_solve.argtypes = [D, DIAG5, P, P, dbl, i32, P, P, P, sz, P]
+    lib.band_refine_solve_ex.argtypes = [D, DIAG5, P, P, dbl, i32, i32, P, P, P, sz, P]
+    lib.band_refine_solve_ex.restype = ct.c_int
     lib.band_adjoint.argtypes = [D, i32, P, DIAG5, P, P, DIAG5, P, P, P, sz, P]
     lib.band_det.argtypes = [D, DIAG5, P, P, P, P, sz, P]
     lib.band_adi_step.argtypes = [D, dbl, dbl, P, P, P, P, sz, P]

@@ -313,9 +313,11 @@ def sip(a, b, c, d, e, f, tol=1e-10, max_it=200, width=5, hb_max_it=30, hb_tol=1
 
 
 def refine_solve(a32, b32, c32, d32, e32, f, rel_stop=1e-11, max_steps=10, x=None,
-                 schedule="auto", chunks=0):
-    """FP32 solve + FP64 refinement; f, x float64 with the diagonals' strides.  The FP32
-    solves run on `schedule` / `chunks` as in ``solve``."""
+                 schedule="auto", chunks=0, pairs=False):
+    """FP32 solve + refinement to FP64 accuracy; f, x float64 with the diagonals'
+    strides.  The residual and the update are FP64 (pairs=False; x must not be f) or
+    FP32 pairs (pairs=True).  The FP32 solves run on `schedule` / `chunks` as in
+    ``solve``."""
     lib = L.load()
     _check_same(c32, a32, b32, d32, e32)
     if c32.dtype != torch.float32:
@@ -332,9 +334,9 @@ def refine_solve(a32, b32, c32, d32, e32, f, rel_stop=1e-11, max_steps=10, x=Non
     status = torch.empty(nsys, dtype=torch.int32, device=c32.device)
     need = lib.band_workspace_size(ct.byref(desc), L.OP_REFINE, 0, 0)
     ws = _workspace(need, c32.device)
-    code = lib.band_refine_solve(ct.byref(desc), _diag5(a32, b32, c32, d32, e32), _ptr(f), _ptr(x),
-                                 rel_stop, max_steps, _ptr(steps), _ptr(status), _ptr(ws),
-                                 ws.numel(), _stream())
+    code = lib.band_refine_solve_ex(ct.byref(desc), _diag5(a32, b32, c32, d32, e32), _ptr(f),
+                                    _ptr(x), rel_stop, max_steps, L.REFINE_PAIRS if pairs else 0,
+                                    _ptr(steps), _ptr(status), _ptr(ws), ws.numel(), _stream())
     L.check(code, "band_refine_solve")
     return x, steps, status
 

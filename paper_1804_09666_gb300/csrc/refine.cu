@@ -15,10 +15,15 @@
 //   decide    per system: stop (converged, non-finite, zero pivot, cap) or go on
 //   residual  r = f - A x (a five-point stencil, elementwise), written as 2^-e r in FP32
 //   solve     delta = solve32(2^-e r) for the systems still going
-// GB300 runs FP64 at 1/64 of the FP32 rate, so x, f, the residual and the update are
-// pairs of FP32 numbers handled with error-free transformations (TwoProd with an FMA,
-// TwoSum): about 2^-48 relative accuracy, ample for the 1e-10 target.  f is split into
-// a pair once (integer bit operations); x is assembled in FP64 once, at the end.
+// x, f, the residual and the update are kept in one of two forms:
+//  * FP64 (the default): x in the caller's FP64 array, r = f - A x with FP64 fused
+//    multiply-adds (A widened exactly from FP32 by integer operations), x += 2^e delta
+//    with one FP64 fused multiply-add;
+//  * FP32 pairs (BAND_REFINE_PAIRS): GB300 runs FP64 at 1/64 of the FP32 rate, so x, f,
+//    the residual and the update are pairs of FP32 numbers handled with error-free
+//    transformations (TwoProd with an FMA, TwoSum): about 2^-48 relative accuracy,
+//    ample for the 1e-10 target; f is split into a pair once (integer bit operations),
+//    x is assembled in FP64 once, at the end.
 #include <cuda_runtime.h>
 
 #include "api_util.h"
@@ -103,6 +108,7 @@ struct RefState {
   int32_t *steps, *status;
   double rel_stop;
   int max_steps;
+  int fp64;                      // 1: x, r and the update in FP64; 0: FP32 pairs
 };
 
 constexpr int kChunk = 32;       // rows per thread in the elementwise passes
@@ -147,10 +153,12 @@ __global__ void __launch_bounds__(256) k_ref_start(const RefState p) {
     for (int u = 0; u < kBatch; ++u) {
       if (ib + u < i1) {
         const int64_t q = q0 + (ib + u) * es;
-        const F2 fp = split(fv[u]);
         p.r32[q] = __double2float_rn(fv[u]);
-        p.fh[q] = fp.h;
-        p.fl[q] = fp.l;
+        if (!p.fp64) {
+          const F2 fp = split(fv[u]);
+          p.fh[q] = fp.h;
+          p.fl[q] = fp.l;
+        }
         m = max_abs(m, fv[u]);
       }
     }
@@ -167,39 +175,121 @@ __global__ void __launch_bounds__(256, REF_MINB) k_ref_update(const RefState p, 
   const float up = pow2f(p.fexp[s]);
   float dm = 0.0f, xm = 0.0f;
   bool nan_d = false, nan_x = false;
-  for (int64_t ib = i0; ib < i1; ib += kBatch) {
-    float dv[kBatch], hv[kBatch], lv[kBatch];
+  if (p.fp64) {
+    const double up64 = (double)up;
+    for (int64_t ib = i0; ib < i1; ib += kBatch) {
+      float dv[kBatch];
+      double xv[kBatch];
 #pragma unroll
-    for (int u = 0; u < kBatch; ++u) {
-      const bool in = ib + u < i1;
-      const int64_t q = q0 + (ib + u) * es;
-      dv[u] = in ? p.d32[q] : 0.0f;
-      hv[u] = (in && !first) ? p.xh[q] : 0.0f;
-      lv[u] = (in && !first) ? p.xl[q] : 0.0f;
-    }
-#pragma unroll
-    for (int u = 0; u < kBatch; ++u) {
-      if (ib + u >= i1) break;
-      const int64_t q = q0 + (ib + u) * es;
-      F2 xn;
-      if (first) {
-        xn = F2{dv[u], 0.0f};
-      } else {
-        const float dd = dv[u] * up;                  // exact: a power of two
-        nan_d |= (dd != dd);
-        dm = fmaxf(dm, fabsf(dd));
-        const F2 t1 = two_sum(hv[u], dd);
-        xn = two_sum(t1.h, t1.l + lv[u]);
+      for (int u = 0; u < kBatch; ++u) {
+        const bool in = ib + u < i1;
+        const int64_t q = q0 + (ib + u) * es;
+        dv[u] = in ? p.d32[q] : 0.0f;
+        xv[u] = (in && !first) ? p.x[q] : 0.0;
       }
-      p.xh[q] = xn.h;
-      p.xl[q] = xn.l;
-      nan_x |= !isfinite(xn.h);
-      xm = fmaxf(xm, fabsf(xn.h));
+#pragma unroll
+      for (int u = 0; u < kBatch; ++u) {
+        if (ib + u >= i1) break;
+        const int64_t q = q0 + (ib + u) * es;
+        double xn;
+        if (first) {
+          xn = f2d(dv[u]);
+        } else {
+          const float dd = dv[u] * up;                // exact: a power of two
+          nan_d |= (dd != dd);
+          dm = fmaxf(dm, fabsf(dd));
+          xn = fma(f2d(dv[u]), up64, xv[u]);
+        }
+        p.x[q] = xn;
+        const float xf = (float)xn;
+        nan_x |= !isfinite(xf);
+        xm = fmaxf(xm, fabsf(xf));
+      }
+    }
+  } else {
+    for (int64_t ib = i0; ib < i1; ib += kBatch) {
+      float dv[kBatch], hv[kBatch], lv[kBatch];
+#pragma unroll
+      for (int u = 0; u < kBatch; ++u) {
+        const bool in = ib + u < i1;
+        const int64_t q = q0 + (ib + u) * es;
+        dv[u] = in ? p.d32[q] : 0.0f;
+        hv[u] = (in && !first) ? p.xh[q] : 0.0f;
+        lv[u] = (in && !first) ? p.xl[q] : 0.0f;
+      }
+#pragma unroll
+      for (int u = 0; u < kBatch; ++u) {
+        if (ib + u >= i1) break;
+        const int64_t q = q0 + (ib + u) * es;
+        F2 xn;
+        if (first) {
+          xn = F2{dv[u], 0.0f};
+        } else {
+          const float dd = dv[u] * up;                  // exact: a power of two
+          nan_d |= (dd != dd);
+          dm = fmaxf(dm, fabsf(dd));
+          const F2 t1 = two_sum(hv[u], dd);
+          xn = two_sum(t1.h, t1.l + lv[u]);
+        }
+        p.xh[q] = xn.h;
+        p.xl[q] = xn.l;
+        nan_x |= !isfinite(xn.h);
+        xm = fmaxf(xm, fabsf(xn.h));
+      }
     }
   }
   // a NaN wins the max (its bits order above every finite float and Inf)
   if (!first) atomicMax(p.dmax + s, nan_d ? 0x7fc00000u : __float_as_uint(dm));
   atomicMax(p.xmax + s, nan_x ? 0x7fc00000u : __float_as_uint(xm));
+}
+
+// r = f - A x in FP64 (A widened exactly from FP32); 2^-e r to r32.
+template <int K>
+__device__ __forceinline__ void residual_rows64(const RefState& p, int64_t s, int64_t i0,
+                                                int64_t i1) {
+  const int64_t n = p.L.rows(s), q0 = p.L.base(s), es = p.L.stride();
+  const double down = (double)pow2f(-p.fexp[s]);
+  float rm = 0.0f;
+  bool nan_r = false;
+  auto X = [&](int64_t j) -> double { return (j >= 0 && j < n) ? p.x[q0 + j * es] : 0.0; };
+  double w0 = X(i0 - 2), w1 = X(i0 - 1), w2 = X(i0), w3 = X(i0 + 1);   // x_{i-2} .. x_{i+1}
+  for (int64_t ib = i0; ib < i1; ib += kBatch) {
+    double xv[kBatch], fv[kBatch];
+    float av[kBatch], bv[kBatch], cv[kBatch], dv[kBatch], ev[kBatch];
+#pragma unroll
+    for (int u = 0; u < kBatch; ++u) {
+      const int64_t i = ib + u;
+      const bool in = i < i1;
+      const int64_t q = q0 + (in ? i : i0) * es;
+      xv[u] = in ? X(i + 2) : 0.0;
+      fv[u] = in ? p.f[q] : 0.0;
+      cv[u] = in ? ldro(p.c + q) : 0.0f;
+      bv[u] = (in && i >= 1) ? ldro(p.b + q) : 0.0f;
+      dv[u] = (in && i + 1 < n) ? ldro(p.d + q) : 0.0f;
+      av[u] = (K == 2 && in && i >= 2) ? ldro(p.a + q) : 0.0f;
+      ev[u] = (K == 2 && in && i + 2 < n) ? ldro(p.e + q) : 0.0f;
+    }
+#pragma unroll
+    for (int u = 0; u < kBatch; ++u) {
+      const int64_t i = ib + u;
+      if (i >= i1) break;
+      const double w4 = xv[u];                        // x_{i+2}
+      double r = fma(-f2d(cv[u]), w2, fv[u]);
+      r = fma(-f2d(bv[u]), w1, r);
+      r = fma(-f2d(dv[u]), w3, r);
+      if (K == 2) {
+        r = fma(-f2d(av[u]), w0, r);
+        r = fma(-f2d(ev[u]), w4, r);
+      }
+      const float rv = (float)(r * down);
+      p.r32[q0 + i * es] = rv;
+      const float ra = (float)fabs(r);
+      nan_r |= (ra != ra);
+      rm = fmaxf(rm, ra);
+      w0 = w1; w1 = w2; w2 = w3; w3 = w4;
+    }
+  }
+  atomicMax(p.rmax + s, nan_r ? 0x7fc00000u : __float_as_uint(rm));
 }
 
 // r = f - A x in FP32 pairs (A exact in FP32); 2^-e r to r32.
@@ -256,6 +346,7 @@ __device__ __forceinline__ void residual_rows(const RefState& p, int64_t s, int6
 // x in FP64 from its pair, for every system, at the end.
 __global__ void __launch_bounds__(256) k_ref_finish(const RefState p) {
   int64_t s, i0, i1;
+  if (p.fp64) return;                 // x is FP64 throughout
   if (!chunk_of(p.L, (int64_t)blockIdx.x * blockDim.x + threadIdx.x, s, i0, i1)) return;
   const int64_t q0 = p.L.base(s), es = p.L.stride();
   for (int64_t ib = i0; ib < i1; ib += kBatch) {
@@ -278,8 +369,13 @@ __global__ void __launch_bounds__(256, REF_MINB) k_ref_residual(const RefState p
   if (!chunk_of(p.L, (int64_t)blockIdx.x * blockDim.x + threadIdx.x, s, i0, i1)) return;
   if (p.done[s]) return;
   const int K = kmode ? kmode : p.L.kband(s);
-  if (K == 1) residual_rows<1>(p, s, i0, i1);
-  else residual_rows<2>(p, s, i0, i1);
+  if (p.fp64) {
+    if (K == 1) residual_rows64<1>(p, s, i0, i1);
+    else residual_rows64<2>(p, s, i0, i1);
+  } else {
+    if (K == 1) residual_rows<1>(p, s, i0, i1);
+    else residual_rows<2>(p, s, i0, i1);
+  }
 }
 
 // After step k's update (k corrections applied, k >= 0): stop or go on, and clear the
@@ -364,11 +460,16 @@ size_t refine_workspace_bytes(const band_desc* d) {
 
 using namespace band;
 
-extern "C" band_status band_refine_solve(const band_desc* desc32, const void* const diag32[5],
-                                         const double* f, double* x, double rel_stop,
-                                         int32_t max_steps, int32_t* steps, int32_t* sys_status,
-                                         void* ws, size_t ws_bytes, void* stream) {
+extern "C" band_status band_refine_solve_ex(const band_desc* desc32, const void* const diag32[5],
+                                            const double* f, double* x, double rel_stop,
+                                            int32_t max_steps, int32_t flags, int32_t* steps,
+                                            int32_t* sys_status, void* ws, size_t ws_bytes,
+                                            void* stream) {
   if (!desc_ok(desc32) || desc32->dtype != BAND_F32 || desc32->systems) return BAND_ERR_ARG;
+  if (desc32->schedule == BAND_SCHED_GRID) return BAND_ERR_ARG;
+  if (flags & ~BAND_REFINE_PAIRS) return BAND_ERR_ARG;
+  // the FP64 form updates x in place while later residuals still read f
+  if (!(flags & BAND_REFINE_PAIRS) && (const void*)x == (const void*)f) return BAND_ERR_ARG;
   if (max_steps < 0 || !(rel_stop >= 0.0)) return BAND_ERR_ARG;
   if (desc32->nsys == 0) return BAND_OK;
   if (!diag32 || !f || !x) return BAND_ERR_ARG;
@@ -395,6 +496,7 @@ extern "C" band_status band_refine_solve(const band_desc* desc32, const void* co
   p.status = sys_status;
   p.rel_stop = rel_stop;
   p.max_steps = max_steps;
+  p.fp64 = (flags & BAND_REFINE_PAIRS) ? 0 : 1;
   const size_t ns = (size_t)desc32->nsys;
   // done, sst, fexp, then the maxima are contiguous from w.done on: clear them at once
   if (cudaMemsetAsync(w.done, 0, (size_t)((char*)w.rmax - (char*)w.done) + ns * sizeof(unsigned),
@@ -429,4 +531,12 @@ extern "C" band_status band_refine_solve(const band_desc* desc32, const void* co
   }
   k_ref_finish<<<g_elem, 256, 0, st>>>(p);
   return cuda_status(cudaGetLastError());
+}
+
+extern "C" band_status band_refine_solve(const band_desc* desc32, const void* const diag32[5],
+                                         const double* f, double* x, double rel_stop,
+                                         int32_t max_steps, int32_t* steps, int32_t* sys_status,
+                                         void* ws, size_t ws_bytes, void* stream) {
+  return band_refine_solve_ex(desc32, diag32, f, x, rel_stop, max_steps, 0, steps, sys_status,
+                              ws, ws_bytes, stream);
 }

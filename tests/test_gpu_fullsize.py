@@ -113,16 +113,17 @@ def test_small_batch_64_x_65536_partitioned(band):
         assert np.abs(xg[:, s_] - xo).max() / np.abs(xo).max() <= 1e-12, s_
 
 
-def test_refine_16384_x_4096(band):
-    """The precision workload: 16384 PD systems of n = 4096 in FP32, refined with an
-    FP64-accurate residual.  Every system reaches relative forward error <= 1e-10
-    against its manufactured solution; 12 sampled systems also against the oracle's
-    GEPP and refinement (step counts within one)."""
+@pytest.mark.parametrize("pairs", [False, True])
+def test_refine_16384_x_4096(band, pairs):
+    """The precision workload: 16384 PD systems of n = 4096 in FP32, refined with the
+    residual and update in FP64 (or FP32 pairs).  Every system reaches relative forward
+    error <= 1e-10 against its manufactured solution; 12 sampled systems also against
+    the oracle's GEPP and refinement (step counts within one)."""
     nsys, n = 16384, 4096
     B = synth.cfg3()
     T = to_dev(B, keys="abcde", dtype=torch.float32)
     f = strided_view(B["f"], n, nsys, 1, nsys)
-    x, steps, st = band.refine_solve(T["a"], T["b"], T["c"], T["d"], T["e"], f)
+    x, steps, st = band.refine_solve(T["a"], T["b"], T["c"], T["d"], T["e"], f, pairs=pairs)
     torch.cuda.synchronize()
     assert (st.cpu() == 0).all()
     steps = steps.cpu().numpy()

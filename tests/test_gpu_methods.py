@@ -83,13 +83,15 @@ def test_sip_hb_divergence_matches_oracle(band):
 
 
 # ----------------------------------------------------------------- refinement
-def test_refine_cfg3_subset(band):
-    """FP32 storage, FP64 refinement: forward error <= 1e-10 against the FP64 truth."""
+@pytest.mark.parametrize("pairs", [False, True])
+def test_refine_cfg3_subset(band, pairs):
+    """FP32 storage, refinement with the residual and update in FP64 (or FP32 pairs):
+    forward error <= 1e-10 against the FP64 truth."""
     nsys, n = 96, 512
     B = synth.cfg3(nsys=nsys, n=n)
     T = to_dev(B, keys="abcde", dtype=torch.float32)
     f = strided_view(B["f"], n, nsys, 1, nsys)
-    x, steps, st = band.refine_solve(T["a"], T["b"], T["c"], T["d"], T["e"], f)
+    x, steps, st = band.refine_solve(T["a"], T["b"], T["c"], T["d"], T["e"], f, pairs=pairs)
     torch.cuda.synchronize()
     assert (st.cpu() == 0).all()
     steps = steps.cpu().numpy()
