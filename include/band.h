@@ -437,7 +437,19 @@ int32_t band_plan_ragged(const int64_t* offsets, const int8_t* hbw, int32_t half
  *    and whose every row is diagonally dominant (|c| >= |a| + |b| + |d| + |e|, checked
  *    on the device) are tried: on other matrices a chunk's block can be far worse
  *    conditioned than the whole matrix.  Not cached: the result depends on the whole
- *    list.
+ *    list.  Then the list, on the schedules chosen, is timed with 1, 2 and 4 warps per
+ *    block of band_solve_batch's kernel, and the fastest becomes this device's block
+ *    size for every later band_solve_batch call of the process (2 before any tuning).
+ * Persistence: the decisions of step 1 and the block size are appended as JSON lines
+ *   {"gpu": "<device name>", "cc": "<major>.<minor>", "cuda": <runtime version>,
+ *    "kind": "schedule", "key": [dtype, method, half_bw, ceil log2 n, ceil log2 nsys,
+ *    layout, x aliases f], "value": <band_schedule>}
+ *   {"gpu": ..., "cuda": ..., "kind": "batch_warps", "value": <1, 2 or 4>}
+ * to the file named by the environment variable BAND_TUNE_CACHE (unset:
+ * $HOME/.cache/libband/tune.jsonl; empty: no file), and the lines of this GPU and CUDA
+ * version are read back by the first band_autotune call of a process on each device
+ * (later lines win), so a new process skips the timings already made.  A file that
+ * cannot be read or written is ignored.
  * Writes schedules[i] and, if chunks is not NULL, chunks[i] (the desc fields to set).
  * The trial runs solve the problems (outputs are overwritten).  Synchronises the
  * stream; do not call while it is being captured.  Returns BAND_ERR_ARG (also for
@@ -446,7 +458,13 @@ int32_t band_plan_ragged(const int64_t* offsets, const int8_t* hbw, int32_t half
 band_status band_autotune(const band_problem* probs, int32_t count, int32_t reps, int32_t flags,
                           int32_t* schedules, int32_t* chunks, void* stream);
 
-/* Forget the autotuner's cached decisions (all devices). */
+/* The warps per block (1, 2 or 4) that band_solve_batch launches with on CUDA device
+ * `device`, or -1 for a device number outside 0..63.  No CUDA call. */
+int32_t band_batch_warps(int32_t device);
+
+/* Forget the autotuner's in-process decisions (all devices) and restore the default
+ * block size; the persisted file is left as it is and is read again by the next
+ * band_autotune call. */
 void band_autotune_reset(void);
 
 /* Diagnostic (the paper has no counterpart): measures this GPU's FP64 fused

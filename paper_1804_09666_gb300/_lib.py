@@ -30,7 +30,7 @@ OP_SOLVE, OP_FACTOR, OP_SIP, OP_REFINE, OP_ADJOINT, OP_DET, OP_ADI, OP_SIP2D = r
 EXPORTS = ("band_workspace_size", "band_solve", "band_factor", "band_sip", "band_refine_solve",
            "band_adjoint", "band_status_str", "band_version", "band_fp64_fma_rate",
            "band_solve_batch", "band_solve_static", "band_plan_ragged", "band_autotune",
-           "band_autotune_reset", "band_det", "band_adi_step", "band_sip2d",
+           "band_autotune_reset", "band_batch_warps", "band_det", "band_adi_step", "band_sip2d",
            "band_refine_solve_ex")
 MAX_BATCH = 64
 
@@ -100,6 +100,8 @@ def load(path=None):
     lib.band_autotune.restype = ct.c_int
     lib.band_autotune_reset.argtypes = []
     lib.band_autotune_reset.restype = None
+    lib.band_batch_warps.argtypes = [i32]
+    lib.band_batch_warps.restype = ct.c_int32
     lib.band_fp64_fma_rate.argtypes = [P, sz, P]
     lib.band_fp64_fma_rate.restype = ct.c_double
     lib.band_version.argtypes = []

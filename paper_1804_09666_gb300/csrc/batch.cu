@@ -10,16 +10,11 @@
 // problem table travels as a __grid_constant__ kernel parameter; nothing is
 // allocated.
 #include <algorithm>
-
-#ifndef BATCH_WARPS
-#define BATCH_WARPS 2
-#endif
-#ifndef BATCH_MIN_BLOCKS
-#define BATCH_MIN_BLOCKS (16 / BATCH_WARPS)
-#endif
+#include <atomic>
 #include <cstring>
 
 #include "api_util.h"
+#include "batch_kernel.cuh"
 #include "kernels.h"
 #include "partition.cuh"
 #include "sip_impl.cuh"
@@ -27,29 +22,30 @@
 #include "symbolic.cuh"
 
 namespace band {
+
+// k_batch with two warps per block here; one and four in batch_w1.cu, batch_w4.cu
+template cudaError_t launch_batch_w<2>(const BatchTable&, int64_t, cudaStream_t);
+cudaError_t launch_batch_w1(const BatchTable& t, int64_t warps, cudaStream_t st);
+cudaError_t launch_batch_w4(const BatchTable& t, int64_t warps, cudaStream_t st);
+cudaError_t launch_batch(const BatchTable& t, int64_t warps, int w, cudaStream_t st) {
+  if (w == 1) return launch_batch_w1(t, warps, st);
+  if (w == 4) return launch_batch_w4(t, warps, st);
+  return launch_batch_w<2>(t, warps, st);
+}
+
+// Warps per block of k_batch on each device: two unless the autotuner (runtime.cu) has
+// measured another to be faster.
+static std::atomic<int> g_batch_warps[64];
+int batch_warps(int dev) {
+  const int w = (dev >= 0 && dev < 64) ? g_batch_warps[dev].load(std::memory_order_relaxed) : 0;
+  return w ? w : 2;
+}
+void set_batch_warps(int dev, int w) {
+  if (dev >= 0 && dev < 64 && (w == 1 || w == 2 || w == 4))
+    g_batch_warps[dev].store(w, std::memory_order_relaxed);
+}
+
 namespace {
-
-enum : int32_t { kDirect64 = 0, kDirect32 = 1, kSip = 2 };
-
-struct BatchItem {
-  int32_t kind;
-  int16_t kmode;     // 1 TD, 2 PD, 0 per system
-  int8_t two_sided;  // two threads (lanes l, l ^ 16) per system
-  int8_t parts;      // partitioned: lanes per system (32 / parts systems a warp), or 0
-  int64_t task0;     // first warp of this problem
-  union {
-    DirectArgs<double> d64;
-    DirectArgs<float> d32;
-    SipArgs sip;
-  } u;
-};
-
-struct BatchTable {
-  int32_t count;
-  int32_t stage_bytes;   // staging ring bytes per warp (0: none)
-  int64_t total;     // warp tasks
-  BatchItem it[BAND_MAX_BATCH];
-};
 
 struct TailTable {
   int32_t count;
@@ -69,81 +65,6 @@ struct SymTable {
   int64_t total;     // warps (slots)
   SymItem it[BAND_MAX_BATCH];
 };
-
-template <typename T>
-__device__ __forceinline__ void run_direct(const DirectArgs<T>& p, int kmode, int64_t t,
-                                           void* stage) {
-  if (t >= p.L.nsys) return;
-  const int K = kmode ? kmode : p.L.kband(p.L.sys(t));
-  if (K == 1) direct_one<T, 1>(p, t, stage);
-  else direct_one<T, 2>(p, t, stage);
-}
-
-// Scratch rows a partitioned task's backward sweeps load together inside this kernel.
-// Four, as in the single-problem kernel: under this kernel's 128 registers they spill a
-// little more than two (184 B against 124 B), yet the 65536-system ragged batch took
-// 4.56 ms against 4.68 ms with two.
-constexpr int kBatchPartRows = 4;
-
-template <typename T>
-__device__ __forceinline__ void run_partition(const DirectArgs<T>& p, int kmode, int parts,
-                                              int64_t warp, void* stage) {
-  T* st = static_cast<T*>(stage);    // the warp's staging area (stage_bytes_per_warp<T>)
-  if (kmode == 1) {
-    switch (parts) {
-      case 8: partition_one<T, 1, 8, kBatchPartRows>(p, warp, st); break;
-      case 16: partition_one<T, 1, 16, kBatchPartRows>(p, warp, st); break;
-      default: partition_one<T, 1, 32, kBatchPartRows>(p, warp, st); break;
-    }
-  } else {
-    switch (parts) {
-      case 8: partition_one<T, 2, 8, kBatchPartRows>(p, warp, st); break;
-      case 16: partition_one<T, 2, 16, kBatchPartRows>(p, warp, st); break;
-      default: partition_one<T, 2, 32, kBatchPartRows>(p, warp, st); break;
-    }
-  }
-}
-
-// One warp task: 32 systems of one problem (16 two-sided, 32 / P partitioned).  Blocks are
-// handed out by the hardware scheduler as earlier ones finish, in task order, and the
-// host orders the problems heaviest first.  (A persistent loop over a task counter was
-// tried: keeping every task variant's state live across the loop doubled the kernel's
-// registers, 126 -> 255, and halved the resident warps.)
-// Warps per block of k_batch.  Small blocks let the hardware spread the heaviest-first
-// tasks over all SMs instead of packing four per SM (measured on the 30-solve ADI step:
-// 1, 2 and 4 warps give 5.00, 4.96 and 5.19 ms); 128 registers allow 16 warps per SM.
-constexpr int kBatchWarps = BATCH_WARPS;
-
-__global__ void __launch_bounds__(32 * kBatchWarps, BATCH_MIN_BLOCKS) k_batch(const __grid_constant__ BatchTable t) {
-  extern __shared__ __align__(16) unsigned char stage_mem[];
-  void* stage = t.stage_bytes ? stage_mem + (threadIdx.x >> 5) * t.stage_bytes : nullptr;
-  const int64_t task = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
-  if (task >= t.total) return;
-  int j = 0;
-  while (j + 1 < t.count && t.it[j + 1].task0 <= task) ++j;
-  const BatchItem& b = t.it[j];
-  if (b.parts) {
-    const int64_t w = task - b.task0;
-    if (b.kind == kDirect64) run_partition<double>(b.u.d64, b.kmode, b.parts, w, stage);
-    else run_partition<float>(b.u.d32, b.kmode, b.parts, w, stage);
-    return;
-  }
-  if (b.two_sided) {         // 16 systems per warp
-    const int64_t t2 = (task - b.task0) * 16 + (threadIdx.x & 15);
-    if (b.kind == kDirect64) {
-      if (b.kmode == 1) twisted_one<double, 1>(b.u.d64, t2, t2 < b.u.d64.L.nsys, stage);
-      else twisted_one<double, 2>(b.u.d64, t2, t2 < b.u.d64.L.nsys, stage);
-    } else {
-      if (b.kmode == 1) twisted_one<float, 1>(b.u.d32, t2, t2 < b.u.d32.L.nsys, stage);
-      else twisted_one<float, 2>(b.u.d32, t2, t2 < b.u.d32.L.nsys, stage);
-    }
-    return;
-  }
-  const int64_t s = (task - b.task0) * kWarp + (threadIdx.x & (kWarp - 1));
-  if (b.kind == kDirect64) run_direct<double>(b.u.d64, b.kmode, s, stage);
-  else if (b.kind == kDirect32) run_direct<float>(b.u.d32, b.kmode, s, stage);
-  else if (s < b.u.sip.L.nsys) sip_literal(b.u.sip, s, nullptr);
-}
 
 // the symbolic fix-ups of all problems: warp g serves slot g - slot0 of its problem
 constexpr int kSymWarps = 4;
@@ -321,9 +242,9 @@ extern "C" band_status band_solve_batch(const band_problem* in, int32_t count, v
       return BAND_ERR_CUDA;
   for (int i = 0; i < npend; ++i)
     if (cudaMemsetAsync(pend_clear[i], 0, pend_bytes[i], st) != cudaSuccess) return BAND_ERR_CUDA;
-  const size_t smem = (size_t)kBatchWarps * (size_t)t.stage_bytes;
-  k_batch<<<(unsigned)((warps + kBatchWarps - 1) / kBatchWarps), 32 * kBatchWarps, smem, st>>>(t);
-  if (cudaGetLastError() != cudaSuccess) return BAND_ERR_CUDA;
+  int dev = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess) return BAND_ERR_CUDA;
+  if (launch_batch(t, warps, batch_warps(dev), st) != cudaSuccess) return BAND_ERR_CUDA;
   if (sym.count > 0 && slots > 0) {
     k_symbolic_batch<<<(unsigned)((slots + kSymWarps - 1) / kSymWarps), 32 * kSymWarps, 0, st>>>(sym);
     if (cudaGetLastError() != cudaSuccess) return BAND_ERR_CUDA;

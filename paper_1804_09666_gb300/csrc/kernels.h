@@ -105,6 +105,10 @@ band_status make_direct(const band_desc* desc, int32_t method, const void* const
                         DirectReq* r, int max_parts);
 bool choose_two_sided(const band_desc* d, bool alias);
 int choose_parts(const band_desc* d, int max_parts);
+// Warps per block of band_solve_batch's kernel on device `dev` (1, 2 or 4; 2 unless the
+// autotuner chose otherwise; defined in batch.cu).
+int batch_warps(int dev);
+void set_batch_warps(int dev, int w);
 // Lets `kernel` launch with more than 48 KiB of dynamic shared memory (the attribute is
 // set once per kernel and device; defined in sip.cu).
 cudaError_t tail_prepare(const void* kernel);

@@ -8,8 +8,13 @@
 // two (the warps of a bucket then do similar work, and the two-sided schedule applies).
 #include <algorithm>
 #include <cmath>
+#include <cstdio>
+#include <cstdlib>
+#include <cstring>
 #include <map>
 #include <mutex>
+#include <string>
+#include <sys/stat.h>
 #include <tuple>
 #include <vector>
 
@@ -34,6 +39,99 @@ int log2_ceil(int64_t v) { return v <= 1 ? 0 : log2_floor(v - 1) + 1; }
 using TuneKey = std::tuple<int, int, int, int, int, int, int, int>;
 std::mutex g_tune_mu;
 std::map<TuneKey, int32_t> g_tune;
+bool g_loaded[64];
+
+// The decisions persist in a file of JSON lines, one decision a line, each keyed by the
+// GPU (name and compute capability) and the CUDA runtime version:
+//   {"gpu": "<name>", "cc": "<major>.<minor>", "cuda": <version>, "kind": "schedule",
+//    "key": [dtype, method, half_bw, ceil log2 n, ceil log2 nsys, layout, x is f],
+//    "value": <band_schedule>}
+//   {"gpu": ..., "kind": "batch_warps", "value": <warps per block of the batched kernel>}
+// Later lines override earlier ones.  The file is $BAND_TUNE_CACHE, or
+// $HOME/.cache/libband/tune.jsonl when that is unset; an empty BAND_TUNE_CACHE turns
+// persistence off.
+std::string cache_path() {
+  const char* env = std::getenv("BAND_TUNE_CACHE");
+  if (env) return std::string(env);
+  const char* home = std::getenv("HOME");
+  if (!home || !*home) return std::string();
+  return std::string(home) + "/.cache/libband/tune.jsonl";
+}
+
+struct GpuId {
+  std::string name, cc;
+  int cuda = 0;
+};
+bool gpu_id(int dev, GpuId* id) {
+  cudaDeviceProp pr;
+  if (cudaGetDeviceProperties(&pr, dev) != cudaSuccess) return false;
+  id->name = pr.name;
+  for (char& ch : id->name)
+    if (ch == '"' || ch == '\\') ch = '_';
+  id->cc = std::to_string(pr.major) + "." + std::to_string(pr.minor);
+  return cudaRuntimeGetVersion(&id->cuda) == cudaSuccess;
+}
+
+std::string line_prefix(const GpuId& id) {
+  return "{\"gpu\": \"" + id.name + "\", \"cc\": \"" + id.cc + "\", \"cuda\": " +
+         std::to_string(id.cuda) + ", ";
+}
+
+// Reads this GPU's decisions into the in-process cache (once per device and process).
+// Caller holds g_tune_mu.
+void load_cache(int dev) {
+  if (dev < 0 || dev >= 64 || g_loaded[dev]) return;
+  g_loaded[dev] = true;
+  const std::string path = cache_path();
+  GpuId id;
+  if (path.empty() || !gpu_id(dev, &id)) return;
+  FILE* fp = std::fopen(path.c_str(), "r");
+  if (!fp) return;
+  const std::string prefix = line_prefix(id);
+  char buf[1024];
+  while (std::fgets(buf, sizeof buf, fp)) {
+    if (std::strncmp(buf, prefix.c_str(), prefix.size()) != 0) continue;
+    const char* rest = buf + prefix.size();
+    int k[7], v = 0;
+    if (std::sscanf(rest, "\"kind\": \"schedule\", \"key\": [%d, %d, %d, %d, %d, %d, %d], "
+                          "\"value\": %d}", &k[0], &k[1], &k[2], &k[3], &k[4], &k[5], &k[6],
+                    &v) == 8) {
+      if (v >= BAND_SCHED_THREAD && v <= BAND_SCHED_PARTITIONED)
+        g_tune[TuneKey{dev, k[0], k[1], k[2], k[3], k[4], k[5], k[6]}] = v;
+    } else if (std::sscanf(rest, "\"kind\": \"batch_warps\", \"value\": %d}", &v) == 1) {
+      set_batch_warps(dev, v);
+    }
+  }
+  std::fclose(fp);
+}
+
+void mkdirs_for(const std::string& path) {
+  for (size_t i = 1; i < path.size(); ++i)
+    if (path[i] == '/') mkdir(path.substr(0, i).c_str(), 0755);
+}
+
+// Appends lines of decisions for this GPU (best effort: a file that cannot be written
+// leaves the in-process cache as the only one).
+void save_lines(int dev, const std::vector<std::string>& bodies) {
+  const std::string path = cache_path();
+  GpuId id;
+  if (bodies.empty() || path.empty() || !gpu_id(dev, &id)) return;
+  mkdirs_for(path);
+  FILE* fp = std::fopen(path.c_str(), "a");
+  if (!fp) return;
+  const std::string prefix = line_prefix(id);
+  for (const std::string& b : bodies) std::fprintf(fp, "%s%s}\n", prefix.c_str(), b.c_str());
+  std::fclose(fp);
+}
+
+std::string schedule_line(const TuneKey& k, int32_t v) {
+  char buf[256];
+  std::snprintf(buf, sizeof buf, "\"kind\": \"schedule\", \"key\": [%d, %d, %d, %d, %d, %d, %d], "
+                                 "\"value\": %d",
+                std::get<1>(k), std::get<2>(k), std::get<3>(k), std::get<4>(k), std::get<5>(k),
+                std::get<6>(k), std::get<7>(k), (int)v);
+  return buf;
+}
 
 int layout_class(const band_desc* d) {
   if (d->offsets) return 0;                    // ragged (packed rows, one system a lane)
@@ -195,6 +293,11 @@ extern "C" band_status band_autotune(const band_problem* probs, int32_t count, i
     schedules[i] = probs[i].desc->schedule;
     if (chunks) chunks[i] = probs[i].desc->chunks;
   }
+  {
+    std::lock_guard<std::mutex> lock(g_tune_mu);
+    load_cache(dev);
+  }
+  std::vector<std::string> fresh;      // decisions to persist
   // per problem: thread per system or two-sided, timed alone (cached)
   for (int32_t i = 0; i < count && out == BAND_OK; ++i) {
     const band_problem& q = probs[i];
@@ -221,6 +324,7 @@ extern "C" band_status band_autotune(const band_problem* probs, int32_t count, i
     schedules[i] = pick;
     std::lock_guard<std::mutex> lock(g_tune_mu);
     g_tune[key] = pick;
+    fresh.push_back(schedule_line(key, pick));
   }
   // joint: the whole list as one launch; problems move to the partitioned schedule,
   // longest systems first, while that shortens the launch
@@ -280,13 +384,40 @@ extern "C" band_status band_autotune(const band_problem* probs, int32_t count, i
       schedules[i] = descs[(size_t)i].schedule;
       if (chunks) chunks[i] = descs[(size_t)i].chunks;
     }
+    // the block size of the batched kernel: the whole list at 1, 2 and 4 warps per
+    // block, with the schedules just chosen (kept per device)
+    if (out == BAND_OK) {
+      if (!e0 && (cudaEventCreate(&e0) != cudaSuccess || cudaEventCreate(&e1) != cudaSuccess))
+        out = BAND_ERR_CUDA;
+      const int keep_w = batch_warps(dev);
+      int best_w = keep_w;
+      float best_t = INFINITY;
+      for (int w = 1; w <= 4 && out == BAND_OK; w *= 2) {
+        set_batch_warps(dev, w);
+        float tm = 0.f;
+        out = time_batch(list.data(), count, reps, st, e0, e1, &tm);
+        if (tm < best_t) { best_t = tm; best_w = w; }
+      }
+      set_batch_warps(dev, out == BAND_OK ? best_w : keep_w);
+      if (out == BAND_OK) fresh.push_back("\"kind\": \"batch_warps\", \"value\": " +
+                                         std::to_string(best_w));
+    }
   }
+  if (out == BAND_OK) save_lines(dev, fresh);
   if (e0) cudaEventDestroy(e0);
   if (e1) cudaEventDestroy(e1);
   return out;
 }
 
+extern "C" int32_t band_batch_warps(int32_t device) {
+  return (device >= 0 && device < 64) ? batch_warps(device) : -1;
+}
+
 extern "C" void band_autotune_reset(void) {
   std::lock_guard<std::mutex> lock(g_tune_mu);
   g_tune.clear();
+  for (int d = 0; d < 64; ++d) {
+    g_loaded[d] = false;
+    set_batch_warps(d, 2);
+  }
 }

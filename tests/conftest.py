@@ -11,3 +11,8 @@ if ROOT not in sys.path:
 def pytest_configure(config):
     config.addinivalue_line("markers", "gpu: needs a CUDA GPU (GB300) and the built libband")
     config.addinivalue_line("markers", "slow: takes more than a few seconds")
+
+
+# The autotuner's decisions persist in a file unless BAND_TUNE_CACHE is empty: the
+# tests keep theirs in the process (the persistence test names its own file).
+os.environ["BAND_TUNE_CACHE"] = ""

@@ -76,3 +76,11 @@ def test_autotune_rejects_bad_arguments(lib):
     assert lib.band_autotune(arr, 1, 3, 0, out, outc, None) == L.ERR_ARG     # desc NULL
     assert lib.band_autotune(arr, 65, 3, 0, out, outc, None) == L.ERR_ARG
     assert lib.band_autotune(arr, 1, 0, 0, out, outc, None) == L.ERR_ARG     # reps < 1
+
+
+def test_batch_warps_default(lib):
+    lib.band_autotune_reset()
+    assert lib.band_batch_warps(0) == 2
+    assert lib.band_batch_warps(63) == 2
+    assert lib.band_batch_warps(64) == -1
+    assert lib.band_batch_warps(-1) == -1
