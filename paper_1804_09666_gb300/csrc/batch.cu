@@ -212,6 +212,7 @@ extern "C" band_status band_solve_batch(const band_problem* in, int32_t count, v
       // registers than the other tasks of this kernel (180 against 128) and measured
       // slower in it (ADI step 4.42 -> 6.9 ms)
       sa.two_sided = 0;
+      t.stage_bytes = std::max(t.stage_bytes, stage_bytes_per_warp<double>());
       b.kind = kSip;
       b.kmode = 2;
       b.two_sided = 0;

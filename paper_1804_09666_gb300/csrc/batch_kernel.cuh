@@ -107,7 +107,7 @@ __global__ void __launch_bounds__(32 * W, 16 / W) k_batch(const __grid_constant_
   const int64_t s = (task - b.task0) * kWarp + (threadIdx.x & (kWarp - 1));
   if (b.kind == kDirect64) run_direct<double>(b.u.d64, b.kmode, s, stage);
   else if (b.kind == kDirect32) run_direct<float>(b.u.d32, b.kmode, s, stage);
-  else if (s < b.u.sip.L.nsys) sip_literal(b.u.sip, s, nullptr);
+  else if (s < b.u.sip.L.nsys) sip_literal(b.u.sip, s, stage);
 }
 
 

@@ -195,12 +195,10 @@ __device__ inline void sip_literal(const SipArgs& p, int64_t t, void* stage) {
   const int64_t w0 = p.W.base(t), ws = p.W.stride();
   double ru0_1 = 0, u1_1 = 0, e_1 = 0, ru0_2 = 0, u1_2 = 0, e_2 = 0;
   double y1 = 0, y2 = 0, rn = 0.0;
-  Row r0 = load_row(p, q0, 0, n), r1, r2;
-  if (n > 1) r1 = load_row(p, q0 + es, 1, n);
-  for (int64_t i = 0; i < n; ++i) {
-    if (i + 2 < n) r2 = load_row(p, q0 + (i + 2) * es, i + 2, n);
+  // row i of the forward sweep (ILU(0) with L y = f); false on a zero pivot
+  auto row = [&](int64_t i, const Row& r) -> bool {
     const int64_t w = w0 + i * ws;
-    double l2 = r0.a, l1 = r0.b, u0 = r0.c, u1 = r0.d;
+    double l2 = r.a, l1 = r.b, u0 = r.c, u1 = r.d;
     if (i >= 2) {
       l2 = l2 * ru0_2;
       l1 = fma(-l2, u1_2, l1);
@@ -211,23 +209,67 @@ __device__ inline void sip_literal(const SipArgs& p, int64_t t, void* stage) {
       u0 = fma(-l1, u1_1, u0);
       u1 = fma(-l1, e_1, u1);
     }
-    if (is_zero(u0)) {
-      if (p.iters) p.iters[s] = 0;
-      if (p.resid) p.resid[s] = NAN;
-      set_status(p.status, s, BAND_ERR_ZERO_PIVOT);
-      return;
-    }
-    const double r = rcp64(u0);
-    const double yv = fma(-l2, y2, fma(-l1, y1, r0.f));
-    p.ru0[w] = r;
+    if (is_zero(u0)) return false;
+    const double rr = rcp64(u0);
+    const double yv = fma(-l2, y2, fma(-l1, y1, r.f));
+    p.ru0[w] = rr;
     p.u1[w] = u1;
     p.y[w] = yv;
-    rn = max_abs(rn, r0.f);              // r^0 = f - A x^0 = f (a NaN f wins the max)
+    rn = max_abs(rn, r.f);               // r^0 = f - A x^0 = f (a NaN f wins the max)
     y2 = y1; y1 = yv;
     ru0_2 = ru0_1; u1_2 = u1_1; e_2 = e_1;
-    ru0_1 = r; u1_1 = u1; e_1 = r0.e;
-    r0 = r1;
-    r1 = r2;
+    ru0_1 = rr; u1_1 = u1; e_1 = r.e;
+    return true;
+  };
+  bool zero = false;
+  if (stage && !p.L.offsets && p.L.ss == 1) {
+    // interleaved systems: rows staged through the warp's shared-memory ring ahead of
+    // the recurrence (as the direct sweeps do), so its chain does not wait on memory
+    constexpr int D = StageDepth<double>::value;
+    const RowRing<double, 6, D> ring{static_cast<double*>(stage), (int)(threadIdx.x & 31)};
+    const double* src[6] = {p.a, p.b, p.c, p.d, p.e, p.f};
+#pragma unroll
+    for (int j = 0; j < D - 1; ++j) {
+      if (j < n) ring.issue(j, src, q0 + j * es);
+      else ring.skip();
+    }
+    for (int64_t i = 0; i < n; ++i) {
+      const int64_t ip = i + D - 1;
+      if (ip < n) ring.issue((int)(ip & (D - 1)), src, q0 + ip * es);
+      else ring.skip();
+      cp_async_wait<D - 1>();
+      const int slot = (int)(i & (D - 1));
+      Row r;
+      r.a = (i >= 2) ? ring.get(slot, 0) : 0.0;
+      r.b = (i >= 1) ? ring.get(slot, 1) : 0.0;
+      r.c = ring.get(slot, 2);
+      r.d = (i + 1 < n) ? ring.get(slot, 3) : 0.0;
+      r.e = (i + 2 < n) ? ring.get(slot, 4) : 0.0;
+      r.f = ring.get(slot, 5);
+      if (!row(i, r)) {
+        zero = true;
+        break;
+      }
+    }
+    cp_async_wait<0>();
+  } else {
+    Row r0 = load_row(p, q0, 0, n), r1, r2;
+    if (n > 1) r1 = load_row(p, q0 + es, 1, n);
+    for (int64_t i = 0; i < n; ++i) {
+      if (i + 2 < n) r2 = load_row(p, q0 + (i + 2) * es, i + 2, n);
+      if (!row(i, r0)) {
+        zero = true;
+        break;
+      }
+      r0 = r1;
+      r1 = r2;
+    }
+  }
+  if (zero) {
+    if (p.iters) p.iters[s] = 0;
+    if (p.resid) p.resid[s] = NAN;
+    set_status(p.status, s, BAND_ERR_ZERO_PIVOT);
+    return;
   }
   if (rn < p.tol || p.max_it < 1 || !isfinite(rn)) {   // no update: x = x^0 = 0
     for (int64_t i = 0; i < n; ++i) p.x[q0 + i * es] = 0.0;
