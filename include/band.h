@@ -431,8 +431,10 @@ int32_t band_plan_ragged(const int64_t* offsets, const int8_t* hbw, int32_t half
  * 2. With flags & BAND_TUNE_JOINT: the whole list is timed as one launch, and the
  *    problems (n >= 64, largest n first) are moved in turn to BAND_SCHED_PARTITIONED
  *    with 8, 16 or 32 chunks (those that leave chunks of 16 rows or more); a move is
- *    kept when it shortens the launch by 2 % or more, and the search ends after two
- *    problems in a row gain nothing.  Only problems whose ws_bytes cover the partitioned
+ *    kept when it shortens the launch by 2 % or more.  A pass over the problems not yet
+ *    moved ends after two problems in a row gain nothing; passes repeat (at most four)
+ *    until one moves nothing, since a move can pay only once a longer chain elsewhere
+ *    has been cut.  Only problems whose ws_bytes cover the partitioned
  *    schedule's workspace (band_workspace_size with schedule BAND_SCHED_PARTITIONED)
  *    and whose every row is diagonally dominant (|c| >= |a| + |b| + |d| + |e|, checked
  *    on the device) are tried: on other matrices a chunk's block can be far worse

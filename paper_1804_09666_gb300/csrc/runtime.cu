@@ -183,6 +183,8 @@ band_status time_one(const band_problem& q, int32_t schedule, int32_t reps, cuda
 
 // A move of the joint phase has to gain this fraction of the launch time to be kept.
 constexpr float kJointGain = 0.02f;
+// Passes of the joint search over the partitioned moves.
+constexpr int kJointPasses = 4;
 
 // Row diagonal dominance, |c_i| >= |a_i| + |b_i| + |d_i| + |e_i| (the entries inside the
 // matrix) for every row of every system, one thread per system; a row that fails
@@ -355,30 +357,40 @@ extern "C" band_status band_autotune(const band_problem* probs, int32_t count, i
     float base = 0.f;
     if (out == BAND_OK && !cand.empty())
       out = time_batch(list.data(), count, reps, st, e0, e1, &base);
-    int misses = 0;
-    for (size_t c = 0; c < cand.size() && out == BAND_OK && misses < 2; ++c) {
-      band_desc& d = descs[(size_t)cand[c]];
-      const band_desc keep = d;
-      int best_p = 0;
-      float best_t = base * (1.f - kJointGain);
-      for (int P = 8; P <= 32 && out == BAND_OK; P *= 2) {
-        if (d.n < (int64_t)16 * P) break;
-        d.schedule = BAND_SCHED_PARTITIONED;
-        d.chunks = P;
-        float tm = 0.f;
-        out = time_batch(list.data(), count, reps, st, e0, e1, &tm);
-        if (tm < best_t) { best_t = tm; best_p = P; }
+    // passes over the candidates not yet moved, until a pass moves none: a move that
+    // gains nothing while a longer chain elsewhere bounds the launch can gain once that
+    // chain is cut (a ragged bucket of one 8192-row system after the 8190-row bucket)
+    std::vector<char> moved(cand.size(), 0);
+    for (int pass = 0; pass < kJointPasses && out == BAND_OK; ++pass) {
+      int misses = 0, moves = 0;
+      for (size_t c = 0; c < cand.size() && out == BAND_OK && misses < 2; ++c) {
+        if (moved[c]) continue;
+        band_desc& d = descs[(size_t)cand[c]];
+        const band_desc keep = d;
+        int best_p = 0;
+        float best_t = base * (1.f - kJointGain);
+        for (int P = 8; P <= 32 && out == BAND_OK; P *= 2) {
+          if (d.n < (int64_t)16 * P) break;
+          d.schedule = BAND_SCHED_PARTITIONED;
+          d.chunks = P;
+          float tm = 0.f;
+          out = time_batch(list.data(), count, reps, st, e0, e1, &tm);
+          if (tm < best_t) { best_t = tm; best_p = P; }
+        }
+        d = keep;
+        if (out != BAND_OK) break;
+        if (best_p) {
+          d.schedule = BAND_SCHED_PARTITIONED;
+          d.chunks = best_p;
+          base = best_t;
+          moved[c] = 1;
+          misses = 0;
+          ++moves;
+        } else {
+          ++misses;
+        }
       }
-      d = keep;
-      if (out != BAND_OK) break;
-      if (best_p) {
-        d.schedule = BAND_SCHED_PARTITIONED;
-        d.chunks = best_p;
-        base = best_t;
-        misses = 0;
-      } else {
-        ++misses;
-      }
+      if (moves == 0) break;
     }
     for (int32_t i = 0; i < count && out == BAND_OK; ++i) {
       schedules[i] = descs[(size_t)i].schedule;
