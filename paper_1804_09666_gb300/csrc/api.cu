@@ -90,6 +90,34 @@ bool choose_two_sided(const band_desc* d, bool alias) {
   return d->n >= 32;
 }
 
+// A single problem on AUTO goes to the partitioned schedule when the two-sided one
+// would leave fewer than two warps per SM (nsys < 32 x SMs) and its systems are long
+// (n >= 256): the chains then set the time, not the FP64 pipes, and P lanes per system
+// shorten them P / 2-fold for about twice the arithmetic per row.  Measured on GB300
+// (FP64 NPDM, ms, two-sided against the partitioned schedule's own chunk choice):
+// 2048 x 2048 0.83 / 0.45, 256 x 8192 3.11 / 0.36, 64 x 65536 24.9 / 1.01; above the
+// line two-sided stays ahead (7280 x 6000: 2.84 / 3.78, 16384 x 4096: 2.12 / 5.07).
+// Uniform batches only (ragged packings keep their own rule), one bandwidth.
+band_desc resolve_single(const band_desc* d, int32_t method) {
+  band_desc r = *d;
+  if (d->schedule != BAND_SCHED_AUTO || d->offsets || d->n < 256 || kmode_for(d, method) <= 0)
+    return r;
+  static int nsm_cache[64];
+  int dev = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess || dev < 0) dev = 0;
+  int nsm = dev < 64 ? nsm_cache[dev] : 0;
+  if (nsm == 0) {
+    if (cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess || nsm < 1)
+      return r;
+    if (dev < 64) nsm_cache[dev] = nsm;
+  }
+  if (d->nsys < (int64_t)32 * nsm) {
+    r.schedule = BAND_SCHED_PARTITIONED;
+    r.chunks = 0;
+  }
+  return r;
+}
+
 // Slots per chunk row of the partitioned scratch: nsys rounded up to the systems of a
 // warp (32 / P for P <= 32, one system per block beyond).
 int64_t part_np(int64_t nsys, int parts) { return parts >= 32 ? nsys : round_up(nsys, 32 / parts); }
@@ -235,7 +263,10 @@ size_t band_workspace_size(const band_desc* desc, int32_t op, int32_t method, in
     case BAND_OP_SOLVE:
       if (method == BAND_MNPDM) return mnpdm_workspace_bytes(desc);
       if (desc->schedule == BAND_SCHED_GRID) return grid_workspace_bytes(desc);
-      carve_solve(desc, method, nullptr, &bytes);
+      {
+        const band_desc rd = resolve_single(desc, method);
+        carve_solve(&rd, method, nullptr, &bytes);
+      }
       return bytes;
     case BAND_OP_FACTOR: return factor_bytes(desc);
     case BAND_OP_SIP: return sip_workspace_bytes(desc, sip_width);
@@ -280,8 +311,9 @@ band_status band_solve(const band_desc* desc, int32_t method, const void* factor
     return cuda_status(launch_fsolve<float>(p, kmode, st));
   }
   if (desc->schedule == BAND_SCHED_GRID) return grid_solve(desc, method, diag, f, x, sys_status, ws, ws_bytes, st);
+  const band_desc rd = resolve_single(desc, method);
   DirectReq r;
-  const band_status v = make_direct(desc, method, diag, f, x, sys_status, ws, ws_bytes, &r, 256);
+  const band_status v = make_direct(&rd, method, diag, f, x, sys_status, ws, ws_bytes, &r, 256);
   if (v != BAND_OK) return v;
   if (r.symbolic && cudaMemsetAsync(r.sym.fix_count_mut, 0, sizeof(unsigned long long), st) !=
                         cudaSuccess)

@@ -104,6 +104,12 @@ band_status make_direct(const band_desc* desc, int32_t method, const void* const
                         const void* f, void* x, int32_t* sys_status, void* ws, size_t ws_bytes,
                         DirectReq* r, int max_parts);
 bool choose_two_sided(const band_desc* d, bool alias);
+// The schedule a single-problem call runs (band_solve, band_solve_static, the transposed
+// solve of band_adjoint): desc itself, or a copy on BAND_SCHED_PARTITIONED (chunks 0)
+// when desc asks for BAND_SCHED_AUTO and the two-sided schedule could not fill the GPU
+// (defined in api.cu).  Batched launches keep their own rule: there the other problems
+// fill the GPU.
+band_desc resolve_single(const band_desc* d, int32_t method);
 int choose_parts(const band_desc* d, int max_parts);
 // Warps per block of band_solve_batch's kernel on device `dev` (1, 2 or 4; 2 unless the
 // autotuner chose otherwise; defined in batch.cu).

@@ -72,8 +72,9 @@ extern "C" band_status band_solve_static(const band_desc* desc, int32_t method,
     return BAND_ERR_ARG;
   const int kmode = kmode_for(desc, method);
   if (kmode < 0) return BAND_ERR_ARG;
+  const band_desc rd = resolve_single(desc, method);   // band_solve's schedule
   size_t need = 0;
-  carve_solve(desc, method, nullptr, &need);     // band_solve's workspace for this desc
+  carve_solve(&rd, method, nullptr, &need);      // band_solve's workspace for this desc
   if (need > kStaticScratchBytes) return BAND_ERR_WORKSPACE;   // batch too large
   if (desc->nsys == 0) return BAND_OK;
   if (!diag || !f || !x || !diag[1] || !diag[2] || !diag[3]) return BAND_ERR_ARG;
@@ -83,7 +84,7 @@ extern "C" band_status band_solve_static(const band_desc* desc, int32_t method,
   // from here on band_solve's own path, with the static array as its workspace
   DirectReq r;
   const band_status v =
-      make_direct(desc, method, diag, f, x, sys_status, base, kStaticScratchBytes, &r, 256);
+      make_direct(&rd, method, diag, f, x, sys_status, base, kStaticScratchBytes, &r, 256);
   if (v != BAND_OK) return v;
   cudaStream_t st = static_cast<cudaStream_t>(stream);
   cudaError_t e;

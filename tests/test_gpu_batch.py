@@ -65,7 +65,10 @@ def _single(band, sp):
         x, it, rs, st = band.sip(*(sp[q] for q in "abcdef"), tol=sp["tol"], max_it=sp["max_it"],
                                  width=0, schedule="thread")
         return dict(x=x, status=st, iters=it, resid=rs)
-    x, st = band.solve(*(sp.get(q) for q in "abcdef"), method=sp["method"])
+    # inside a batch AUTO stays two-sided for n >= 32 (the other problems fill the GPU);
+    # a single call on AUTO would take the partitioned schedule for these small batches
+    sched = "two_sided" if sp["c"].shape[0] >= 32 else "auto"
+    x, st = band.solve(*(sp.get(q) for q in "abcdef"), method=sp["method"], schedule=sched)
     return dict(x=x, status=st)
 
 
