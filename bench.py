@@ -52,6 +52,8 @@ def parse():
     ap.add_argument("--no-graph", action="store_true")
     ap.add_argument("--no-extras", action="store_true",
                     help="skip the ragged, precision, adjoint and SIP workloads (N = 1 only)")
+    ap.add_argument("--ragged-nsys", type=int, default=65536,
+                    help="systems of the ragged workload (a smaller case for profiling)")
     ap.add_argument("--workload", choices=sorted(EXTRA_WORKLOADS),
                     help="run only this one of the other workloads on GPU 0 and print its "
                          "result as a JSON line (for profiling it alone)")
@@ -577,13 +579,14 @@ def _time(fn, reps=5, warm=2):
     return best
 
 
-def ragged_workload(dev):
+def ragged_workload(dev, nsys=65536):
     """65536 systems, n log-uniform in [16, 8192], half TD / half PD, packed ragged:
     size buckets with autotuned schedules in one graph-captured launch, against the
-    whole packing on one thread per system."""
+    whole packing on one thread per system.  The timed replays sit in the NVTX range
+    "ragged_replay" (for a profiler's range filter)."""
     import torch
     import paper_1804_09666_gb300 as band
-    B = synth.cfg2()
+    B = synth.cfg2(nsys=nsys)
     d = {q: torch.from_numpy(B[q]).to(dev) for q in "abcdef"}
     units = int(B["offsets"][-1])
     plan = band.RaggedPlan(*(d[q] for q in "abcdef"), B["offsets"], B["hbw"], schedule="tune")
@@ -596,7 +599,9 @@ def ragged_workload(dev):
         with torch.cuda.graph(g, stream=s):
             plan.run()
     torch.cuda.current_stream().wait_stream(s)
+    torch.cuda.nvtx.range_push("ragged_replay")
     ms = _time(g.replay, reps=10)
+    torch.cuda.nvtx.range_pop()
     x, st = plan.x, plan.status
     err = np.maximum.reduceat(np.abs(x.cpu().numpy() - B["x_true"]), B["offsets"][:-1])
     offs = torch.from_numpy(B["offsets"]).to(dev)
@@ -608,8 +613,8 @@ def ragged_workload(dev):
     ms_two = _time(two.run, reps=5)
     parted = [{"n_max": int(bk[2]), "half_bw": int(bk[3]), "systems": int(bk[1]), "chunks": int(c)}
               for bk, v, c in zip(plan.buckets, plan.schedules, plan.chunks) if v == 3]
-    return {"workload": "65536 ragged systems, n log-uniform in [16, 8192], half TD / half PD, "
-                        "dominant (%d unknowns)" % units,
+    return {"workload": "%d ragged systems, n log-uniform in [16, 8192], half TD / half PD, "
+                        "dominant (%d unknowns)" % (nsys, units),
             "value": units / (ms * 1e-3), "unit": UNIT, "ms": ms,
             "buckets": len(plan.buckets),
             "two_sided_buckets": int(sum(1 for v in plan.schedules if v == 2)),
@@ -995,7 +1000,8 @@ def main():
     if args.workload:
         import torch
         dev = torch.device("cuda", 0)
-        out = globals()[EXTRA_WORKLOADS[args.workload]](dev)
+        fn = globals()[EXTRA_WORKLOADS[args.workload]]
+        out = fn(dev, nsys=args.ragged_nsys) if args.workload == "ragged" else fn(dev)
         print(json.dumps({"workload": args.workload, "result": out}))
         return
     world, rank, local = dist_setup()
