@@ -159,12 +159,15 @@ typedef struct {
  *   another schedule may solve it); on diagonally dominant systems that does not
  *   happen.  Workspace: five (PD) / four (TD) arrays of ceil(n / P) * P * nsys rows plus
  *   ~450 B per chunk.  Other calls return BAND_ERR_ARG for this schedule.
- * BAND_SCHED_AUTO: in band_solve, band_solve_static and band_adjoint, a uniform batch of
- *   one bandwidth with n >= 256 and fewer than 32 systems per SM of the GPU (the
- *   two-sided schedule would leave fewer than two warps per SM) runs PARTITIONED with
- *   the chunk count chosen as for chunks == 0, and band_workspace_size sizes its
- *   workspace accordingly.  Otherwise, and always inside band_solve_batch (where the
- *   other problems fill the GPU): TWO_SIDED for uniform-bandwidth solves with n >= 32
+ * BAND_SCHED_AUTO: in band_solve, band_solve_static and band_adjoint, an NTDM / NPDM
+ *   solve of a uniform batch of one bandwidth with n >= 256 and fewer than 32 systems
+ *   per SM of the GPU (the two-sided schedule would leave fewer than two warps per SM)
+ *   runs PARTITIONED, with the chunk count chosen as for chunks == 0; a system whose
+ *   partitioned elimination fails (a chunk pivot the guard rejects, possible on rows
+ *   that are not diagonally dominant) is solved again, from f, by a second launch on
+ *   the schedule described next, and band_workspace_size covers both.  Otherwise, and
+ *   always inside band_solve_batch (where the other problems fill the GPU): TWO_SIDED
+ *   for uniform-bandwidth solves with n >= 32
  *   that are not a whole ragged packing (ragged id lists, i.e. size buckets, qualify)
  *   and, for NTDM/NPDM, whose x does not alias f; THREAD otherwise.  band_autotune
  *   replaces the rule by measurement. */

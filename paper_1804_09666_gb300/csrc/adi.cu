@@ -105,10 +105,7 @@ AdiWs carve_adi(const band_desc* g, void* base, size_t* bytes) {
   band_desc dx, dy;
   sweep_descs(g, &dx, &dy);
   const int32_t m = g->half_bw == 1 ? BAND_NTDM : BAND_NPDM;
-  size_t bx = 0, by = 0;
-  const band_desc rx = resolve_single(&dx, m), ry = resolve_single(&dy, m);   // band_solve's
-  carve_solve(&rx, m, nullptr, &bx);
-  carve_solve(&ry, m, nullptr, &by);
+  const size_t bx = single_solve_bytes(&dx, m), by = single_solve_bytes(&dy, m);  // band_solve's
   w.solve_bytes = bx > by ? bx : by;
   w.solve = c.take(w.solve_bytes);
   *bytes = c.size();

@@ -147,8 +147,7 @@ AdjTWs carve_adjoint_t(const band_desc* d, int32_t method, void* base, size_t* b
   AdjTWs w{};
   const size_t arr = (size_t)span_of(d) * sizeof(double);
   for (int k = 0; k < 5; ++k) w.t[k] = (double*)c.take(arr);
-  size_t sb = 0;
-  carve_solve(d, method, nullptr, &sb);
+  const size_t sb = single_solve_bytes(d, method);    // band_solve's workspace for A^T
   w.solve = c.take(sb);
   w.solve_bytes = sb;
   *bytes = c.size();
@@ -209,9 +208,7 @@ size_t adjoint_workspace_bytes(const band_desc* d) {
   size_t b = 0, bt = 0;
   carve_adjoint(d, nullptr, &b);
   if (!d->offsets && d->nsys > 0 && d->n > 0) {
-    const int32_t m = d->half_bw == 1 ? BAND_NTDM : BAND_NPDM;
-    const band_desc rd = resolve_single(d, m);
-    carve_adjoint_t(&rd, m, nullptr, &bt);
+    carve_adjoint_t(d, d->half_bw == 1 ? BAND_NTDM : BAND_NPDM, nullptr, &bt);
   }
   return b > bt ? b : bt;
 }
@@ -237,11 +234,10 @@ extern "C" band_status band_adjoint(const band_desc* desc, int32_t method, const
   if (!factors && !desc->offsets && kmode > 0) {
     // the transposed system solved as a band system of its own
     const int32_t m = kmode == 1 ? BAND_NTDM : BAND_NPDM;
-    const band_desc rd = resolve_single(desc, m);    // band_solve's schedule for A^T
     size_t need = 0;
-    carve_adjoint_t(&rd, m, nullptr, &need);
+    carve_adjoint_t(desc, m, nullptr, &need);
     if (!ws || ws_bytes < need) return BAND_ERR_WORKSPACE;
-    const AdjTWs tw = carve_adjoint_t(&rd, m, ws, &need);
+    const AdjTWs tw = carve_adjoint_t(desc, m, ws, &need);
     const Layout L = layout_of(desc);
     const int64_t total = desc->nsys * desc->n;
     const unsigned grid = (unsigned)((total + 255) / 256);
@@ -255,14 +251,10 @@ extern "C" band_status band_adjoint(const band_desc* desc, int32_t method, const
                                                 tw.t[2], tw.t[3], tw.t[4]);
     if (cudaGetLastError() != cudaSuccess) return BAND_ERR_CUDA;
     const void* dt[5] = {tw.t[0], tw.t[1], tw.t[2], tw.t[3], tw.t[4]};
-    DirectReq r;
-    const band_status v = make_direct(&rd, m, dt, w, grad_f, sys_status, tw.solve,
-                                      tw.solve_bytes, &r, 256);
+    // A^T solved as band_solve would (its automatic schedule included)
+    const band_status v = run_single(desc, m, dt, w, grad_f, sys_status, tw.solve,
+                                     tw.solve_bytes, st);
     if (v != BAND_OK) return v;
-    const cudaError_t e = r.parts ? launch_partition<double>(r.d64, r.kmode, r.parts, st)
-                          : r.two_sided ? launch_twisted<double>(r.d64, r.kmode, st)
-                                        : launch_direct<double>(r.d64, r.kmode, st);
-    if (e != cudaSuccess) return BAND_ERR_CUDA;
     double* G[5] = {(double*)grad_diag[0], (double*)grad_diag[1], (double*)grad_diag[2],
                     (double*)grad_diag[3], (double*)grad_diag[4]};
     if (kmode == 2)

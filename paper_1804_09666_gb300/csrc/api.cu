@@ -90,32 +90,110 @@ bool choose_two_sided(const band_desc* d, bool alias) {
   return d->n >= 32;
 }
 
-// A single problem on AUTO goes to the partitioned schedule when the two-sided one
-// would leave fewer than two warps per SM (nsys < 32 x SMs) and its systems are long
-// (n >= 256): the chains then set the time, not the FP64 pipes, and P lanes per system
-// shorten them P / 2-fold for about twice the arithmetic per row.  Measured on GB300
-// (FP64 NPDM, ms, two-sided against the partitioned schedule's own chunk choice):
-// 2048 x 2048 0.83 / 0.45, 256 x 8192 3.11 / 0.36, 64 x 65536 24.9 / 1.01; above the
-// line two-sided stays ahead (7280 x 6000: 2.84 / 3.78, 16384 x 4096: 2.12 / 5.07).
-// Uniform batches only (ragged packings keep their own rule), one bandwidth.
-band_desc resolve_single(const band_desc* d, int32_t method) {
-  band_desc r = *d;
-  if (d->schedule != BAND_SCHED_AUTO || d->offsets || d->n < 256 || kmode_for(d, method) <= 0)
-    return r;
+// The automatic schedule of a single problem.  A small batch of long systems (fewer than
+// 32 per SM, n >= 256: the two-sided schedule would leave under two warps per SM) is
+// bound by its chains, not by the FP64 pipes, and P lanes per system shorten them
+// P / 2-fold for about twice the arithmetic per row.  Measured on GB300 (FP64 NPDM,
+// ms, two-sided against partitioned with the library's chunk count): 2048 x 2048
+// 0.83 / 0.45, 256 x 8192 3.11 / 0.36, 64 x 65536 24.9 / 1.01; above the line
+// two-sided stays ahead (7280 x 6000: 2.84 / 3.78, 16384 x 4096: 2.12 / 5.07).
+// A chunk restarts the elimination at its first row, and on rows that are not
+// diagonally dominant it can meet a pivot far below NPDM's (the pivot guard of
+// partition.cuh); such a system is listed, and a second launch of the AUTO sweep
+// (two-sided, or one thread when x aliases f) solves the listed systems again from f,
+// which the partitioned sweep leaves intact.  With the redo inside the partitioned
+// kernel, on one lane, the indefinite r = 2 ADI rows took 2.3-3.5 ms against 0.85-0.96
+// two-sided.  Numeric methods only (a symbolic system that meets a small chunk pivot
+// goes to the series pass, ~30 us a row); uniform batches of one bandwidth.
+namespace {
+
+bool auto_part(const band_desc* d, int32_t method) {
+  if (d->schedule != BAND_SCHED_AUTO || d->offsets || d->n < 256 || is_symbolic(method) ||
+      kmode_for(d, method) <= 0)
+    return false;
   static int nsm_cache[64];
   int dev = 0;
   if (cudaGetDevice(&dev) != cudaSuccess || dev < 0) dev = 0;
   int nsm = dev < 64 ? nsm_cache[dev] : 0;
   if (nsm == 0) {
     if (cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess || nsm < 1)
-      return r;
+      return false;
     if (dev < 64) nsm_cache[dev] = nsm;
   }
-  if (d->nsys < (int64_t)32 * nsm) {
-    r.schedule = BAND_SCHED_PARTITIONED;
-    r.chunks = 0;
-  }
+  return d->nsys < (int64_t)32 * nsm;
+}
+
+band_desc partitioned_of(const band_desc* d) {
+  band_desc r = *d;
+  r.schedule = BAND_SCHED_PARTITIONED;
+  r.chunks = 0;
   return r;
+}
+
+// Byte offset of the redo counter behind the partitioned workspace; the list follows
+// 256 bytes later.
+size_t redo_offset(const band_desc* dp, int32_t method) {
+  size_t need = 0;
+  carve_solve(dp, method, nullptr, &need);
+  return (size_t)round_up((int64_t)need, 256);
+}
+
+cudaError_t launch_req(const DirectReq& r, int32_t dtype, cudaStream_t st) {
+  if (r.parts)
+    return dtype == BAND_F64 ? launch_partition<double>(r.d64, r.kmode, r.parts, st)
+                             : launch_partition<float>(r.d32, r.kmode, r.parts, st);
+  if (r.two_sided)
+    return dtype == BAND_F64 ? launch_twisted<double>(r.d64, r.kmode, st)
+                             : launch_twisted<float>(r.d32, r.kmode, st);
+  return dtype == BAND_F64 ? launch_direct<double>(r.d64, r.kmode, st)
+                           : launch_direct<float>(r.d32, r.kmode, st);
+}
+
+}  // namespace
+
+size_t single_solve_bytes(const band_desc* d, int32_t method) {
+  size_t plain = 0;
+  carve_solve(d, method, nullptr, &plain);
+  if (!auto_part(d, method)) return plain;
+  const band_desc dp = partitioned_of(d);
+  const size_t part = redo_offset(&dp, method) + 256 + (size_t)d->nsys * sizeof(int64_t);
+  return part > plain ? part : plain;
+}
+
+band_status run_single(const band_desc* desc, int32_t method, const void* const diag[5],
+                       const void* f, void* x, int32_t* sys_status, void* ws, size_t ws_bytes,
+                       cudaStream_t st) {
+  if (auto_part(desc, method)) {
+    if (!ws || ws_bytes < single_solve_bytes(desc, method)) return BAND_ERR_WORKSPACE;
+    const band_desc dp = partitioned_of(desc);
+    // both sweeps carve alpha and beta from the workspace's start (the partitioned
+    // carve extends the plain one); the second launch runs after the first is done
+    DirectReq rp, ra;
+    band_status v = make_direct(&dp, method, diag, f, x, sys_status, ws, ws_bytes, &rp, 256);
+    if (v != BAND_OK) return v;
+    v = make_direct(desc, method, diag, f, x, sys_status, ws, ws_bytes, &ra, 256);
+    if (v != BAND_OK) return v;
+    char* base = static_cast<char*>(ws) + redo_offset(&dp, method);
+    auto* count = reinterpret_cast<unsigned long long*>(base);
+    auto* list = reinterpret_cast<int64_t*>(base + 256);
+    if (cudaMemsetAsync(count, 0, sizeof(unsigned long long), st) != cudaSuccess)
+      return BAND_ERR_CUDA;
+    rp.d64.redo_list = rp.d32.redo_list = list;
+    rp.d64.redo_count = rp.d32.redo_count = count;
+    if (launch_req(rp, desc->dtype, st) != cudaSuccess) return BAND_ERR_CUDA;
+    ra.d64.L.ids = ra.d32.L.ids = list;          // position t: the t-th listed system
+    ra.d64.nsys_dev = ra.d32.nsys_dev = count;
+    return cuda_status(launch_req(ra, desc->dtype, st));
+  }
+  DirectReq r;
+  const band_status v = make_direct(desc, method, diag, f, x, sys_status, ws, ws_bytes, &r, 256);
+  if (v != BAND_OK) return v;
+  if (r.symbolic && cudaMemsetAsync(r.sym.fix_count_mut, 0, sizeof(unsigned long long), st) !=
+                        cudaSuccess)
+    return BAND_ERR_CUDA;
+  if (launch_req(r, desc->dtype, st) != cudaSuccess) return BAND_ERR_CUDA;
+  if (r.symbolic) return cuda_status(launch_symbolic_fixup(r.sym.args, st));
+  return BAND_OK;
 }
 
 // Slots per chunk row of the partitioned scratch: nsys rounded up to the systems of a
@@ -263,11 +341,7 @@ size_t band_workspace_size(const band_desc* desc, int32_t op, int32_t method, in
     case BAND_OP_SOLVE:
       if (method == BAND_MNPDM) return mnpdm_workspace_bytes(desc);
       if (desc->schedule == BAND_SCHED_GRID) return grid_workspace_bytes(desc);
-      {
-        const band_desc rd = resolve_single(desc, method);
-        carve_solve(&rd, method, nullptr, &bytes);
-      }
-      return bytes;
+      return single_solve_bytes(desc, method);
     case BAND_OP_FACTOR: return factor_bytes(desc);
     case BAND_OP_SIP: return sip_workspace_bytes(desc, sip_width);
     case BAND_OP_REFINE: return refine_workspace_bytes(desc);
@@ -311,26 +385,7 @@ band_status band_solve(const band_desc* desc, int32_t method, const void* factor
     return cuda_status(launch_fsolve<float>(p, kmode, st));
   }
   if (desc->schedule == BAND_SCHED_GRID) return grid_solve(desc, method, diag, f, x, sys_status, ws, ws_bytes, st);
-  const band_desc rd = resolve_single(desc, method);
-  DirectReq r;
-  const band_status v = make_direct(&rd, method, diag, f, x, sys_status, ws, ws_bytes, &r, 256);
-  if (v != BAND_OK) return v;
-  if (r.symbolic && cudaMemsetAsync(r.sym.fix_count_mut, 0, sizeof(unsigned long long), st) !=
-                        cudaSuccess)
-    return BAND_ERR_CUDA;
-  cudaError_t e;
-  if (r.parts)
-    e = desc->dtype == BAND_F64 ? launch_partition<double>(r.d64, r.kmode, r.parts, st)
-                                : launch_partition<float>(r.d32, r.kmode, r.parts, st);
-  else if (r.two_sided)
-    e = desc->dtype == BAND_F64 ? launch_twisted<double>(r.d64, r.kmode, st)
-                                : launch_twisted<float>(r.d32, r.kmode, st);
-  else
-    e = desc->dtype == BAND_F64 ? launch_direct<double>(r.d64, r.kmode, st)
-                                : launch_direct<float>(r.d32, r.kmode, st);
-  if (e != cudaSuccess) return BAND_ERR_CUDA;
-  if (r.symbolic) e = launch_symbolic_fixup(r.sym.args, st);
-  return cuda_status(e);
+  return run_single(desc, method, diag, f, x, sys_status, ws, ws_bytes, st);
 }
 
 band_status band_factor(const band_desc* desc, int32_t method, const void* const diag[5],

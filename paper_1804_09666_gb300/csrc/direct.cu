@@ -22,6 +22,12 @@
 
 namespace band {
 
+// positions a thread / two-sided launch covers (DirectArgs::nsys_dev)
+template <typename T>
+__device__ __forceinline__ bool in_batch(const DirectArgs<T>& p, int64_t t) {
+  return t < p.L.nsys && (!p.nsys_dev || (unsigned long long)t < *p.nsys_dev);
+}
+
 // ---------------------------------------------------------------------------
 // fused factor + solve (device function in sweeps.cuh)
 // ---------------------------------------------------------------------------
@@ -30,7 +36,7 @@ __global__ void __launch_bounds__(32 * SweepWarps<T>::value, kSweepWarpsPerSm / 
     k_direct(const DirectArgs<T> p) {
   extern __shared__ __align__(16) unsigned char stage_mem[];
   const int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-  if (t >= p.L.nsys) return;
+  if (!in_batch(p, t)) return;
   void* stage = stage_mem + (threadIdx.x >> 5) * stage_bytes_per_warp<T>();
   if (K == 0) {
     if (p.L.kband(p.L.sys(t)) == 1) direct_one<T, 1>(p, t, stage);
@@ -62,7 +68,7 @@ __global__ void __launch_bounds__(32 * SweepWarps<T>::value, kSweepWarpsPerSm / 
   void* stage = stage_mem + (threadIdx.x >> 5) * stage_bytes_per_warp<T>();
   const int64_t warp = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
   const int64_t t = warp * 16 + (threadIdx.x & 15);
-  twisted_one<T, K>(p, t, t < p.L.nsys, stage);
+  twisted_one<T, K>(p, t, in_batch(p, t), stage);
 }
 
 template <typename T>

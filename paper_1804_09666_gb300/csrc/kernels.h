@@ -30,6 +30,14 @@ struct DirectArgs {
   // be and zs then) and the slots per chunk row (nsys rounded up to 32 / chunks)
   T *zv1, *zv2;
   int64_t part_np;
+  // partitioned schedule: a system whose elimination fails is appended to redo_list
+  // (position in the batch; redo_count counts them) for a follow-up launch, instead of
+  // being redone in the kernel by one lane (null: in the kernel)
+  int64_t* redo_list;
+  unsigned long long* redo_count;
+  // thread / two-sided sweeps: positions at or beyond *nsys_dev are left alone (the
+  // follow-up launch over a redo list; null: L.nsys alone bounds them)
+  const unsigned long long* nsys_dev;
 };
 
 template <typename T>
@@ -104,12 +112,16 @@ band_status make_direct(const band_desc* desc, int32_t method, const void* const
                         const void* f, void* x, int32_t* sys_status, void* ws, size_t ws_bytes,
                         DirectReq* r, int max_parts);
 bool choose_two_sided(const band_desc* d, bool alias);
-// The schedule a single-problem call runs (band_solve, band_solve_static, the transposed
-// solve of band_adjoint): desc itself, or a copy on BAND_SCHED_PARTITIONED (chunks 0)
-// when desc asks for BAND_SCHED_AUTO and the two-sided schedule could not fill the GPU
-// (defined in api.cu).  Batched launches keep their own rule: there the other problems
-// fill the GPU.
-band_desc resolve_single(const band_desc* d, int32_t method);
+// A single-problem direct solve (band_solve, band_solve_static, the transposed solve of
+// band_adjoint) with everything band_solve does after its argument checks, on the
+// workspace single_solve_bytes sizes (defined in api.cu).  On BAND_SCHED_AUTO a small
+// batch of long NTDM / NPDM systems runs partitioned, and the systems whose partitioned
+// elimination fails are solved again by the AUTO sweep in a second launch.  Batched
+// launches keep their own rule: there the other problems fill the GPU.
+size_t single_solve_bytes(const band_desc* d, int32_t method);
+band_status run_single(const band_desc* desc, int32_t method, const void* const diag[5],
+                       const void* f, void* x, int32_t* sys_status, void* ws, size_t ws_bytes,
+                       cudaStream_t st);
 int choose_parts(const band_desc* d, int max_parts);
 // Warps per block of band_solve_batch's kernel on device `dev` (1, 2 or 4; 2 unless the
 // autotuner chose otherwise; defined in batch.cu).

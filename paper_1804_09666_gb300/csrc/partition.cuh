@@ -587,6 +587,9 @@ __device__ __forceinline__ void partition_sys(const DirectArgs<T>& p, int64_t t,
     if (mode == 2 && p.fix_list) {
       const unsigned long long c = atomicAdd(p.fix_count, 1ull);
       p.fix_list[c] = t;
+    } else if (mode == 2 && p.redo_list) {      // solved again by a follow-up launch
+      const unsigned long long c = atomicAdd(p.redo_count, 1ull);
+      p.redo_list[c] = t;
     } else {
       part_serial<T, K, P>(p, t);
     }

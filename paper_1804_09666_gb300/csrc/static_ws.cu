@@ -72,9 +72,7 @@ extern "C" band_status band_solve_static(const band_desc* desc, int32_t method,
     return BAND_ERR_ARG;
   const int kmode = kmode_for(desc, method);
   if (kmode < 0) return BAND_ERR_ARG;
-  const band_desc rd = resolve_single(desc, method);   // band_solve's schedule
-  size_t need = 0;
-  carve_solve(&rd, method, nullptr, &need);      // band_solve's workspace for this desc
+  const size_t need = single_solve_bytes(desc, method);   // band_solve's workspace
   if (need > kStaticScratchBytes) return BAND_ERR_WORKSPACE;   // batch too large
   if (desc->nsys == 0) return BAND_OK;
   if (!diag || !f || !x || !diag[1] || !diag[2] || !diag[3]) return BAND_ERR_ARG;
@@ -82,20 +80,6 @@ extern "C" band_status band_solve_static(const band_desc* desc, int32_t method,
   void* base = nullptr;
   if (scratch_on_current_device(&base) != cudaSuccess) return BAND_ERR_CUDA;
   // from here on band_solve's own path, with the static array as its workspace
-  DirectReq r;
-  const band_status v =
-      make_direct(&rd, method, diag, f, x, sys_status, base, kStaticScratchBytes, &r, 256);
-  if (v != BAND_OK) return v;
-  cudaStream_t st = static_cast<cudaStream_t>(stream);
-  cudaError_t e;
-  if (r.parts)
-    e = desc->dtype == BAND_F64 ? launch_partition<double>(r.d64, r.kmode, r.parts, st)
-                                : launch_partition<float>(r.d32, r.kmode, r.parts, st);
-  else if (r.two_sided)
-    e = desc->dtype == BAND_F64 ? launch_twisted<double>(r.d64, r.kmode, st)
-                                : launch_twisted<float>(r.d32, r.kmode, st);
-  else
-    e = desc->dtype == BAND_F64 ? launch_direct<double>(r.d64, r.kmode, st)
-                                : launch_direct<float>(r.d32, r.kmode, st);
-  return cuda_status(e);
+  return run_single(desc, method, diag, f, x, sys_status, base, kStaticScratchBytes,
+                    static_cast<cudaStream_t>(stream));
 }
