@@ -246,9 +246,11 @@ band_status band_adi_step(const band_desc* grid, double tau, double lambda, cons
  * at k + 1, diag[4][k] at k + nx (entries that would leave the grid are read but never
  * used).  ILU(0) with L's and U's entries on A's pattern, then from x^0 = 0 updates
  * LU x^{j+1} = (LU - A) x^j + f until max|f - A x| < tol (status OK) or max_it updates
- * (BAND_ERR_NOT_CONVERGED); a zero ILU(0) pivot is BAND_ERR_ZERO_PIVOT.  One thread per
- * system (desc->schedule AUTO, chunks 0); x must not alias f; iters, resid (per
- * system) may be NULL.  ws: band_workspace_size(desc, BAND_OP_SIP2D, 0, 0). */
+ * (BAND_ERR_NOT_CONVERGED); a zero ILU(0) pivot is BAND_ERR_ZERO_PIVOT.  One warp per
+ * system when nx <= 32 (lane x takes column x; the substitutions run on anti-diagonal
+ * wavefronts), one thread per system otherwise; the same operations per unknown either
+ * way (desc->schedule AUTO, chunks 0); x must not alias f; iters, resid (per system)
+ * may be NULL.  ws: band_workspace_size(desc, BAND_OP_SIP2D, 0, 0). */
 band_status band_sip2d(const band_desc* desc, int64_t nx, const void* const diag[5],
                        const double* f, double* x, double tol, int32_t max_it, int32_t* iters,
                        double* resid, int32_t* sys_status, void* ws, size_t ws_bytes,

@@ -145,6 +145,145 @@ __global__ void __launch_bounds__(128) k_sip2d(const Sip2dArgs p) {
   if (p.resid) p.resid[sys] = rn;
 }
 
+// One warp per system for grids of at most 32 columns: lane x holds column x.  The
+// residual pass walks the grid rows (the x +- 1 neighbours by shuffles, the y +- 1 ones
+// kept in registers); ILU(0), L y = K x + f and U x = y are recurrences along both grid
+// directions ((x, y) needs (x - 1, y) and (x, y - 1), or (x + 1, y) and (x, y + 1)), so
+// they run on anti-diagonals x + y = d: at step d lane x takes row y = d - x, its
+// neighbour in its own column is its own previous step and its neighbour in its row is
+// lane x -+ 1's previous step (one shuffle).  The same arithmetic as k_sip2d, in the
+// same order per unknown; a warp's chains are nx + ny - 1 steps instead of nx ny rows,
+// and the launch has a warp per system instead of a thread.
+__global__ void __launch_bounds__(128) k_sip2d_warp(const Sip2dArgs p) {
+  const int64_t t = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+  if (t >= p.L.nsys) return;                     // the whole warp
+  const unsigned full = 0xffffffffu;
+  const int lane = (int)(threadIdx.x & 31);
+  const int64_t sys = p.L.sys(t);
+  const int nx = (int)p.nx;
+  const int64_t ny = p.ny;
+  const int64_t q0 = p.L.base(sys), es = p.L.stride();
+  const int64_t w0 = p.W.base(t), ws = p.W.stride();
+  auto Q = [&](int64_t k) { return q0 + k * es; };
+  auto Wk = [&](int64_t k) { return w0 + k * ws; };
+  const bool col = lane < nx;
+  const int64_t steps = (int64_t)nx + ny - 1;
+  int32_t st = BAND_OK;
+  // ---- ILU(0)
+  {
+    double ruc = 0.0, tt = 0.0, ee = 0.0;      // this lane's last point: 1/uc, t, e
+    bool zero = false;
+    for (int64_t d = 0; d < steps; ++d) {
+      const double ruc_w = __shfl_up_sync(full, ruc, 1), e_w = __shfl_up_sync(full, ee, 1);
+      const int64_t y = d - lane;
+      if (col && y >= 0 && y < ny && !zero) {
+        const int64_t k = y * nx + lane;
+        double v = ldro(p.c + Q(k));
+        double lsk = 0.0, lwk = 0.0;
+        if (y > 0) {
+          lsk = ldro(p.s + Q(k)) * ruc;
+          v = fma(-lsk, tt, v);
+        }
+        if (lane > 0) {
+          lwk = ldro(p.w + Q(k)) * ruc_w;
+          v = fma(-lwk, e_w, v);
+        }
+        if (is_zero(v)) {
+          zero = true;
+        } else {
+          ruc = rcp64(v);
+          p.ls[Wk(k)] = lsk;
+          p.lw[Wk(k)] = lwk;
+          p.ruc[Wk(k)] = ruc;
+          tt = ldro(p.t + Q(k));
+          ee = ldro(p.e + Q(k));
+        }
+      }
+    }
+    if (__any_sync(full, zero)) st = BAND_ERR_ZERO_PIVOT;
+  }
+  int32_t it = 0;
+  double rn = 0.0;
+  if (st == BAND_OK) {
+    for (int64_t y = 0; y < ny; ++y)
+      if (col) p.x[Q(y * nx + lane)] = 0.0;
+    __syncwarp();
+    for (;;) {
+      // ---- r = f - A x, max |r|
+      rn = 0.0;
+      {
+        double xm = 0.0, x0 = col ? p.x[Q(lane)] : 0.0;
+        for (int64_t y = 0; y < ny; ++y) {
+          const int64_t k = y * nx + lane;
+          const double xp = (col && y + 1 < ny) ? p.x[Q(k + nx)] : 0.0;
+          const double xw = __shfl_up_sync(full, x0, 1), xe = __shfl_down_sync(full, x0, 1);
+          if (col) {
+            double ax = ldro(p.c + Q(k)) * x0;
+            if (y > 0) ax = fma(ldro(p.s + Q(k)), xm, ax);
+            if (lane > 0) ax = fma(ldro(p.w + Q(k)), xw, ax);
+            if (lane + 1 < nx) ax = fma(ldro(p.e + Q(k)), xe, ax);
+            if (y + 1 < ny) ax = fma(ldro(p.t + Q(k)), xp, ax);
+            rn = max_abs(rn, p.f[Q(k)] - ax);
+          }
+          xm = x0;
+          x0 = xp;
+        }
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) rn = max_abs(rn, __shfl_xor_sync(full, rn, o));
+      }
+      if (rn < p.tol || it >= p.max_it || not_finite(rn)) break;
+      // ---- forward: L y = K x + f (x: the previous iterate, read only here)
+      {
+        double yy = 0.0, tt = 0.0;               // this lane's last point: y, t
+        for (int64_t d = 0; d < steps; ++d) {
+          const double y_w = __shfl_up_sync(full, yy, 1), t_w = __shfl_up_sync(full, tt, 1);
+          const int64_t y = d - lane;
+          if (col && y >= 0 && y < ny) {
+            const int64_t k = y * nx + lane;
+            double v = p.f[Q(k)];
+            const double lsk = p.ls[Wk(k)], lwk = p.lw[Wk(k)];
+            if (y > 0 && lane + 1 < nx)
+              v = fma(lsk * ldro(p.e + Q(k - nx)), p.x[Q(k - nx + 1)], v);
+            if (lane > 0 && y + 1 < ny) v = fma(lwk * t_w, p.x[Q(k + nx - 1)], v);
+            if (y > 0) v = fma(-lsk, yy, v);
+            if (lane > 0) v = fma(-lwk, y_w, v);
+            p.y[Wk(k)] = v;
+            yy = v;
+            tt = ldro(p.t + Q(k));
+          }
+        }
+      }
+      __syncwarp();          // every lane's reads of the previous iterate are done
+      // ---- backward: U x = y
+      {
+        double xx = 0.0;                          // this lane's last point: x
+        for (int64_t d = steps - 1; d >= 0; --d) {
+          const double x_e = __shfl_down_sync(full, xx, 1);
+          const int64_t y = d - lane;
+          if (col && y >= 0 && y < ny) {
+            const int64_t k = y * nx + lane;
+            double v = p.y[Wk(k)];
+            if (lane + 1 < nx) v = fma(-ldro(p.e + Q(k)), x_e, v);
+            if (y + 1 < ny) v = fma(-ldro(p.t + Q(k)), xx, v);
+            v *= p.ruc[Wk(k)];
+            p.x[Q(k)] = v;
+            xx = v;
+          }
+        }
+      }
+      __syncwarp();
+      ++it;
+    }
+    if (not_finite(rn)) st = BAND_ERR_NONFINITE;
+    else if (!(rn < p.tol)) st = BAND_ERR_NOT_CONVERGED;
+  }
+  if (lane == 0) {
+    set_status(p.status, sys, st);
+    if (p.iters) p.iters[sys] = it;
+    if (p.resid) p.resid[sys] = rn;
+  }
+}
+
 struct Sip2dWs {
   void *ls, *lw, *ruc, *y;
 };
@@ -193,6 +332,8 @@ extern "C" band_status band_sip2d(const band_desc* desc, int64_t nx, const void*
               (const double*)diag[3], (const double*)diag[4], f, x, (double*)w.ls,
               (double*)w.lw, (double*)w.ruc, (double*)w.y, tol, max_it, iters, resid,
               sys_status};
-  k_sip2d<<<(unsigned)((desc->nsys + 127) / 128), 128, 0, static_cast<cudaStream_t>(stream)>>>(p);
+  cudaStream_t st = static_cast<cudaStream_t>(stream);
+  if (nx <= 32) k_sip2d_warp<<<(unsigned)((desc->nsys + 3) / 4), 128, 0, st>>>(p);
+  else k_sip2d<<<(unsigned)((desc->nsys + 127) / 128), 128, 0, st>>>(p);
   return cuda_status(cudaGetLastError());
 }
