@@ -88,9 +88,10 @@ typedef struct {
   const int8_t* hbw;      /* device array of per-system half bandwidths (1 or 2), or NULL */
   int64_t total_rows;     /* ragged: offsets[nsys] (the host's copy); uniform: ignored */
   int32_t schedule;       /* band_schedule for NTDM/NPDM solves (BAND_SCHED_AUTO = 0) */
-  int32_t chunks;         /* BAND_SCHED_PARTITIONED: lanes (row chunks) per system, 8, 16,
-                             32 (lanes of a warp) or 64, 128, 256 (a block of 2, 4, 8 warps
-                             per system); 0 = chosen from nsys and n.  Otherwise 0. */
+  int32_t chunks;         /* BAND_SCHED_PARTITIONED: lanes (row chunks) per system, 4, 8,
+                             16, 32 (lanes of a warp) or 64, 128, 256 (a block of 2, 4, 8
+                             warps per system); 0 = chosen from nsys and n (8 or more).
+                             band_solve_batch rejects 4.  Otherwise 0. */
   /* Ragged batches only, else NULL: device array of nsys system ids.  The batch is then
    * the systems ids[0 .. nsys-1] of the packing that offsets (and hbw) describe, and
    * every per-system output (sys_status, iters, resid) is indexed by the id.  A solve

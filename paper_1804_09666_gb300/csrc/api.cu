@@ -204,7 +204,7 @@ int64_t part_np(int64_t nsys, int parts) { return parts >= 32 ? nsys : round_up(
 // part_np systems; desc->chunks == 0 takes the largest over the chunk counts.
 int64_t part_rows_bound(const band_desc* d) {
   int64_t best = 0;
-  for (int P = 8; P <= 256; P *= 2) {
+  for (int P = 4; P <= 256; P *= 2) {
     if (d->chunks && P != d->chunks) continue;
     const int64_t r = (d->n + P - 1) / P * P * part_np(d->nsys, P);
     if (r > best) best = r;

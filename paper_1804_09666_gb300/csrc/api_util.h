@@ -60,7 +60,7 @@ inline bool desc_ok(const band_desc* d) {
   if (d->nsys < 0 || d->n < 1) return false;
   if (!d->hbw && d->half_bw != 1 && d->half_bw != 2) return false;
   if (d->schedule < BAND_SCHED_AUTO || d->schedule > BAND_SCHED_GRID) return false;
-  if (d->chunks != 0 && (d->schedule != BAND_SCHED_PARTITIONED || d->chunks < 8 ||
+  if (d->chunks != 0 && (d->schedule != BAND_SCHED_PARTITIONED || d->chunks < 4 ||
                          d->chunks > 256 || (d->chunks & (d->chunks - 1)) != 0))
     return false;
   if (d->systems && !d->offsets) return false;     // id lists select from a ragged packing

@@ -182,6 +182,10 @@ extern "C" band_status band_solve_batch(const band_problem* in, int32_t count, v
       if (v != BAND_OK) return v;
       b.kmode = (int16_t)r.kmode;
       b.two_sided = r.two_sided ? 1 : 0;
+      // four chunks run in band_solve alone: in this kernel their task's code costs
+      // every other task spill space (128-register cap: 72 / 608 B against 60 / 464 B of
+      // spill stores / loads, the ADI step 4.1 -> 4.3 ms)
+      if (r.parts == 4) return BAND_ERR_ARG;
       b.parts = (int8_t)r.parts;
       // Uniform contiguous problems read through L1 here: next to the batch's other
       // tasks that measured faster than granule staging (ADI step 4.85 vs 5.16 ms);

@@ -106,6 +106,7 @@ template <typename T, int K>
 static cudaError_t launch_partition_k(const DirectArgs<T>& p, int parts, unsigned grid, int tb,
                                       size_t smem, cudaStream_t st) {
   switch (parts) {
+    case 4: k_partition<T, K, 4><<<grid, tb, smem, st>>>(p); break;
     case 8: k_partition<T, K, 8><<<grid, tb, smem, st>>>(p); break;
     case 16: k_partition<T, K, 16><<<grid, tb, smem, st>>>(p); break;
     case 32: k_partition<T, K, 32><<<grid, tb, smem, st>>>(p); break;
@@ -140,7 +141,7 @@ cudaError_t launch_partition(const DirectArgs<T>& p, int kmode, int parts, cudaS
     if (kmode == 2) return launch_partition_block_k<T, 2>(p, parts, st);
     return cudaErrorInvalidValue;
   }
-  if (parts != 8 && parts != 16 && parts != 32) return cudaErrorInvalidValue;
+  if (parts != 4 && parts != 8 && parts != 16 && parts != 32) return cudaErrorInvalidValue;
   const int64_t warps = (p.L.nsys + 32 / parts - 1) / (32 / parts);
   const int wpb = SweepWarps<T>::value;
   const unsigned grid = (unsigned)((warps + wpb - 1) / wpb);

@@ -79,7 +79,7 @@ def test_workspace_sizes(lib):
         auto = lib.band_workspace_size(ct.byref(_desc(nsys=nsys, n=n, elem_stride=nsys,
                                                       schedule=L.SCHED_PARTITIONED)),
                                        L.OP_SOLVE, L.NPDM, 0)
-        for P in (8, 16, 32, 64, 128, 256):
+        for P in (4, 8, 16, 32, 64, 128, 256):
             fixed = lib.band_workspace_size(
                 ct.byref(_desc(nsys=nsys, n=n, elem_stride=nsys, schedule=L.SCHED_PARTITIONED,
                                chunks=P)), L.OP_SOLVE, L.NPDM, 0)
@@ -124,7 +124,6 @@ def test_bad_arguments_are_rejected_without_gpu(lib):
         (_desc(schedule=L.SCHED_PARTITIONED, chunks=512), L.NPDM, full),
         (_desc(schedule=L.SCHED_PARTITIONED, chunks=2), L.NPDM, full),
         (_desc(schedule=L.SCHED_PARTITIONED, chunks=48), L.NPDM, full),
-        (_desc(schedule=L.SCHED_PARTITIONED, chunks=4), L.NPDM, full),   # P starts at 8
     ]
     for d, m, diag in cases:
         code = lib.band_solve(ct.byref(d), m, None, diag, 8, 8, None, 8, 1 << 30, None)

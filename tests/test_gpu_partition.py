@@ -23,7 +23,7 @@ from gpu_helpers import flat_of, per_system_rel, to_dev
 pytestmark = pytest.mark.gpu
 
 GOLD = os.path.join(os.path.dirname(__file__), "golden")
-PARTS = [8, 16, 32]                 # lanes of one warp
+PARTS = [4, 8, 16, 32]              # lanes of one warp
 BLOCK_PARTS = [64, 128, 256]        # a block of 2, 4, 8 warps per system
 
 
@@ -532,3 +532,13 @@ def test_batchplan_tune(band):
     xt, _, _, _ = _oracle(A, 2, "gepp")
     bound = np.maximum(1e-10, 10 * per_system_rel(xo, xt, *_args(A)))
     assert (per_system_rel(flat_of(res[1]["x"]), xt, *_args(A)) <= bound).all()
+
+
+def test_four_chunks_single_calls_only(band):
+    """P = 4 runs in band_solve (parity above); band_solve_batch rejects it (its code in
+    the batched kernel would cost every other task registers)."""
+    from paper_1804_09666_gb300 import _lib as L
+    T = to_dev(synth.cfg0(nsys=64, n=512, seed_salt=91))
+    spec = dict(method="npdm", schedule="partitioned", chunks=4, **{q: T[q] for q in "abcdef"})
+    with pytest.raises(L.BandError):
+        band.BatchPlan([spec]).run()
