@@ -262,13 +262,17 @@ band_status band_sip2d(const band_desc* desc, int64_t nx, const void* const diag
  * PD matrix into a TD one costs 16 operations per row with both outer entries nonzero):
  * bottom-up, every nonzero e_i is eliminated with row i+1; top-down, every nonzero a_i
  * with row i-1; NTDM then solves the TD system.  For PD batches (half_bw 2, no hbw, no id
- * list), any layout, FP64 or FP32, one thread per system (desc->schedule AUTO or THREAD),
- * factors NULL; x may alias f.  A zero divisor of the elimination (the superdiagonal of
+ * list), any layout, FP64 or FP32, factors NULL; x may alias f.  desc->schedule AUTO on a
+ * uniform batch: the eliminations run one thread per row (a chain of consecutive rows
+ * with outer entries by the thread of its first row), the TD system goes to the
+ * workspace laid out like the input and is solved as band_solve's NTDM on its automatic
+ * schedule; THREAD, or a ragged packing: one thread per system for all three sweeps.  A zero divisor of the elimination (the superdiagonal of
  * row i+1, or the subdiagonal of row i-1, as they stand then) or a zero NTDM pivot gives
  * BAND_ERR_ZERO_PIVOT.  No pivoting: meant for K << n rows with outer entries (on fully
  * pentadiagonal matrices its multipliers are ratios of off-diagonal entries and it loses
  * accuracy that NPDM keeps).  Workspace: band_workspace_size(desc, BAND_OP_SOLVE,
- * BAND_MNPDM, 0), five arrays of nsys rounded up to 32 times n elements. */
+ * BAND_MNPDM, 0): on AUTO four arrays of the input's span, nsys flags and NTDM's
+ * workspace; on THREAD five arrays of nsys rounded up to 32 times n elements. */
 
 /* LU factors of NTDM/NPDM (gamma, 1/mu, alpha, beta per row; opaque layout) into
  * `factors`, a device buffer of band_workspace_size(desc, BAND_OP_FACTOR, method, 0)

@@ -162,7 +162,7 @@ size_t single_solve_bytes(const band_desc* d, int32_t method) {
 
 band_status run_single(const band_desc* desc, int32_t method, const void* const diag[5],
                        const void* f, void* x, int32_t* sys_status, void* ws, size_t ws_bytes,
-                       cudaStream_t st) {
+                       cudaStream_t st, const int32_t* skip) {
   if (auto_part(desc, method)) {
     if (!ws || ws_bytes < single_solve_bytes(desc, method)) return BAND_ERR_WORKSPACE;
     const band_desc dp = partitioned_of(desc);
@@ -173,6 +173,7 @@ band_status run_single(const band_desc* desc, int32_t method, const void* const 
     if (v != BAND_OK) return v;
     v = make_direct(desc, method, diag, f, x, sys_status, ws, ws_bytes, &ra, 256);
     if (v != BAND_OK) return v;
+    rp.d64.skip = rp.d32.skip = ra.d64.skip = ra.d32.skip = skip;
     char* base = static_cast<char*>(ws) + redo_offset(&dp, method);
     auto* count = reinterpret_cast<unsigned long long*>(base);
     auto* list = reinterpret_cast<int64_t*>(base + 256);
@@ -188,6 +189,7 @@ band_status run_single(const band_desc* desc, int32_t method, const void* const 
   DirectReq r;
   const band_status v = make_direct(desc, method, diag, f, x, sys_status, ws, ws_bytes, &r, 256);
   if (v != BAND_OK) return v;
+  r.d64.skip = r.d32.skip = skip;
   if (r.symbolic && cudaMemsetAsync(r.sym.fix_count_mut, 0, sizeof(unsigned long long), st) !=
                         cudaSuccess)
     return BAND_ERR_CUDA;

@@ -119,9 +119,10 @@ bool choose_two_sided(const band_desc* d, bool alias);
 // elimination fails are solved again by the AUTO sweep in a second launch.  Batched
 // launches keep their own rule: there the other problems fill the GPU.
 size_t single_solve_bytes(const band_desc* d, int32_t method);
+// skip (may be null): per system id, nonzero = leave the system alone (DirectArgs::skip).
 band_status run_single(const band_desc* desc, int32_t method, const void* const diag[5],
                        const void* f, void* x, int32_t* sys_status, void* ws, size_t ws_bytes,
-                       cudaStream_t st);
+                       cudaStream_t st, const int32_t* skip = nullptr);
 int choose_parts(const band_desc* d, int max_parts);
 // Warps per block of band_solve_batch's kernel on device `dev` (1, 2 or 4; 2 unless the
 // autotuner chose otherwise; defined in batch.cu).

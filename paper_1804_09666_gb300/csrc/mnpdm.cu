@@ -9,7 +9,20 @@
 // then top-down every nonzero a_i (column i-2) with row i-1, by then tridiagonal,
 //   m = a_i / B_{i-1};  B_i -= m C_{i-1};  C_i -= m D_{i-1};  F_i -= m F_{i-1},
 // with (B, C, D, F) a row's sub-, main and superdiagonal entries and right-hand side as
-// they stand.  One thread per system, three sweeps:
+// they stand.
+//
+// Uniform batches on the automatic schedule: the eliminations touch only the rows with
+// nonzero outer entries and the rows of a chain of such rows (consecutive rows with
+// e != 0, or with a != 0) depend only on each other, so both run one thread per row:
+//  1. every row with e_i = 0 copies (b, c, d, f) into the workspace's (B, C, D, F);
+//     the bottom row of each chain of e != 0 rows (its row i+1 has e = 0 and is the
+//     pivot row as it stands) eliminates the chain upwards and writes its rows;
+//  2. the top row of each chain of a != 0 rows eliminates it downwards in place;
+//  3. the tridiagonal system (B, C, D, F), laid out like the input, goes to band_solve's
+//     NTDM on its automatic schedule (two-sided, or partitioned for a small batch),
+//     skipping the systems whose elimination met a zero divisor.
+// NTDM then carries the per-row work: 8 FP64 instructions a row against NPDM's 14.
+// Ragged packings and the thread schedule: one thread per system, three sweeps:
 //  1. bottom-up: the e eliminations.  Only rows with e_i != 0 are changed, and only
 //     their (B, C, D, F) are written to the workspace; the sweep reads e and, at those
 //     rows, the rows involved, so with K << n it reads little more than e.
@@ -215,6 +228,158 @@ __global__ void __launch_bounds__(32 * SweepWarps<T>::value) k_mnpdm(const Mnpdm
   set_status(p.status, s, bad ? BAND_ERR_NONFINITE : BAND_OK);
 }
 
+// ---- the row-parallel path (uniform batches)
+template <typename T>
+struct MnRows {
+  Layout L;
+  const T *a, *b, *c, *d, *e, *f;
+  T *B, *C, *D, *F;     // the tridiagonal system, at the input's indices
+  int32_t* skip;        // per system: an elimination met a zero divisor
+  int32_t* status;
+};
+
+// (i, s) of the idx-th element of a uniform batch, the unit-stride index running first
+__device__ __forceinline__ void mn_elem(const Layout& L, int64_t idx, int64_t& i, int64_t& s) {
+  if (L.ss == 1) { s = idx % L.nsys; i = idx / L.nsys; }
+  else { i = idx % L.n; s = idx / L.n; }
+}
+
+template <typename T>
+__device__ __forceinline__ void mn_fail(const MnRows<T>& p, int64_t s) {
+  p.skip[s] = 1;
+  set_status(p.status, s, BAND_ERR_ZERO_PIVOT);
+}
+
+// step 1: copies, and the e chains bottom-up
+template <typename T>
+__global__ void __launch_bounds__(256) k_mnpdm_e(const MnRows<T> p) {
+  const int64_t idx = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (idx >= p.L.nsys * p.L.n) return;
+  int64_t i, s;
+  mn_elem(p.L, idx, i, s);
+  const int64_t n = p.L.n, es = p.L.es, q0 = s * p.L.ss, q = q0 + i * es;
+  const T ei = i + 2 < n ? ldro(p.e + q) : T(0);
+  if (is_zero(ei)) {
+    p.B[q] = i >= 1 ? ldro(p.b + q) : T(0);
+    p.C[q] = ldro(p.c + q);
+    p.D[q] = i + 1 < n ? ldro(p.d + q) : T(0);
+    p.F[q] = p.f[q];
+    return;
+  }
+  if (i + 3 < n && !is_zero(ldro(p.e + q + es))) return;   // not the chain's bottom
+  // row i+1 (e = 0): the pivot row as it stands
+  const int64_t q1 = q + es;
+  T B1 = ldro(p.b + q1), C1 = ldro(p.c + q1), D1 = ldro(p.d + q1), F1 = p.f[q1];
+  for (int64_t r = i;; --r) {
+    const int64_t qr = q0 + r * es;
+    if (is_zero(D1)) {
+      mn_fail(p, s);
+      return;
+    }
+    const T m = ldro(p.e + qr) / D1;
+    const T a1 = r + 1 >= 2 ? ldro(p.a + qr + es) : T(0);
+    const T Bi = r >= 1 ? fma(-m, a1, ldro(p.b + qr)) : T(0);
+    const T Ci = fma(-m, B1, ldro(p.c + qr));
+    const T Di = fma(-m, C1, ldro(p.d + qr));
+    const T Fi = fma(-m, F1, p.f[qr]);
+    p.B[qr] = Bi;
+    p.C[qr] = Ci;
+    p.D[qr] = Di;
+    p.F[qr] = Fi;
+    B1 = Bi; C1 = Ci; D1 = Di; F1 = Fi;
+    if (r == 0 || is_zero(ldro(p.e + qr - es))) break;   // row r-1: its own thread's copy
+  }
+}
+
+// step 2: the a chains top-down, in place
+template <typename T>
+__global__ void __launch_bounds__(256) k_mnpdm_a(const MnRows<T> p) {
+  const int64_t idx = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (idx >= p.L.nsys * p.L.n) return;
+  int64_t i, s;
+  mn_elem(p.L, idx, i, s);
+  const int64_t n = p.L.n, es = p.L.es, q0 = s * p.L.ss, q = q0 + i * es;
+  if (i < 2 || is_zero(ldro(p.a + q)) || p.skip[s]) return;
+  if (i - 1 >= 2 && !is_zero(ldro(p.a + q - es))) return;  // not the chain's top
+  // row i-1 (a = 0): the pivot row as step 1 left it
+  const int64_t qp = q - es;
+  T Bp = p.B[qp], Cp = p.C[qp], Dp = p.D[qp], Fp = p.F[qp];
+  for (int64_t r = i;; ++r) {
+    const int64_t qr = q0 + r * es;
+    if (is_zero(Bp)) {
+      mn_fail(p, s);
+      return;
+    }
+    const T m = ldro(p.a + qr) / Bp;
+    const T B = fma(-m, Cp, p.B[qr]);
+    const T C = fma(-m, Dp, p.C[qr]);
+    const T F = fma(-m, Fp, p.F[qr]);
+    const T D = p.D[qr];
+    p.B[qr] = B;
+    p.C[qr] = C;
+    p.F[qr] = F;
+    Bp = B; Cp = C; Dp = D; Fp = F;
+    if (r + 1 >= n || is_zero(ldro(p.a + qr + es))) break;
+  }
+}
+
+// Elements one strided array of a uniform batch spans.
+int64_t mn_span(const band_desc* d) {
+  return (d->n - 1) * d->elem_stride + (d->nsys - 1) * d->sys_stride + 1;
+}
+
+band_desc mn_td(const band_desc* d) {
+  band_desc t = *d;
+  t.half_bw = 1;
+  t.schedule = BAND_SCHED_AUTO;
+  t.chunks = 0;
+  return t;
+}
+
+struct MnRowWs {
+  void *B, *C, *D, *F;
+  int32_t* skip;
+  void* solve;
+  size_t solve_bytes;
+};
+MnRowWs carve_mn_rows(const band_desc* d, void* base, size_t* bytes) {
+  Carve c(base);
+  MnRowWs w;
+  const size_t arr = (size_t)mn_span(d) * dtype_size(d->dtype);
+  w.B = c.take(arr);
+  w.C = c.take(arr);
+  w.D = c.take(arr);
+  w.F = c.take(arr);
+  w.skip = (int32_t*)c.take((size_t)d->nsys * sizeof(int32_t));
+  const band_desc td = mn_td(d);
+  w.solve_bytes = single_solve_bytes(&td, BAND_NTDM);
+  w.solve = c.take(w.solve_bytes);
+  *bytes = c.size();
+  return w;
+}
+
+bool mn_rows_path(const band_desc* d) {
+  return d->schedule == BAND_SCHED_AUTO && !d->offsets && d->nsys > 0 && d->n > 0;
+}
+
+template <typename T>
+band_status mn_rows_solve(const band_desc* desc, const void* const diag[5], const void* f,
+                          void* x, int32_t* sys_status, const MnRowWs& w, cudaStream_t st) {
+  MnRows<T> p{layout_of(desc), (const T*)diag[0], (const T*)diag[1], (const T*)diag[2],
+              (const T*)diag[3], (const T*)diag[4], (const T*)f, (T*)w.B, (T*)w.C, (T*)w.D,
+              (T*)w.F, w.skip, sys_status};
+  if (cudaMemsetAsync(w.skip, 0, (size_t)desc->nsys * sizeof(int32_t), st) != cudaSuccess)
+    return BAND_ERR_CUDA;
+  const int64_t total = desc->nsys * desc->n;
+  const unsigned grid = (unsigned)((total + 255) / 256);
+  k_mnpdm_e<T><<<grid, 256, 0, st>>>(p);
+  k_mnpdm_a<T><<<grid, 256, 0, st>>>(p);
+  if (cudaGetLastError() != cudaSuccess) return BAND_ERR_CUDA;
+  const band_desc td = mn_td(desc);
+  const void* dtd[5] = {nullptr, w.B, w.C, w.D, nullptr};
+  return run_single(&td, BAND_NTDM, dtd, w.F, x, sys_status, w.solve, w.solve_bytes, st, w.skip);
+}
+
 struct MnpdmWs {
   void *B, *C, *D, *F, *al;
 };
@@ -235,12 +400,14 @@ MnpdmWs carve_mnpdm(const band_desc* d, void* base, size_t* bytes) {
 
 size_t mnpdm_workspace_bytes(const band_desc* d) {
   size_t b = 0;
-  carve_mnpdm(d, nullptr, &b);
+  if (mn_rows_path(d)) carve_mn_rows(d, nullptr, &b);
+  else carve_mnpdm(d, nullptr, &b);
   return b;
 }
 
-// band_solve with method BAND_MNPDM: PD batches (half_bw 2, no per-system bandwidths),
-// any layout, one thread per system whatever desc->schedule (thread or auto) says.
+// band_solve with method BAND_MNPDM: PD batches (half_bw 2, no per-system bandwidths);
+// uniform batches on the automatic schedule row-parallel, the rest one thread per
+// system.
 band_status mnpdm_solve(const band_desc* desc, const void* const diag[5], const void* f, void* x,
                         int32_t* sys_status, void* ws, size_t ws_bytes, cudaStream_t st) {
   if (desc->hbw || desc->half_bw != 2 || desc->systems) return BAND_ERR_ARG;
@@ -248,6 +415,14 @@ band_status mnpdm_solve(const band_desc* desc, const void* const diag[5], const 
   if (!diag || !f || !x || !diag[0] || !diag[1] || !diag[2] || !diag[3] || !diag[4])
     return BAND_ERR_ARG;
   size_t need = 0;
+  if (mn_rows_path(desc)) {
+    carve_mn_rows(desc, nullptr, &need);
+    if (!ws || ws_bytes < need) return BAND_ERR_WORKSPACE;
+    const MnRowWs rw = carve_mn_rows(desc, ws, &need);
+    return desc->dtype == BAND_F64
+               ? mn_rows_solve<double>(desc, diag, f, x, sys_status, rw, st)
+               : mn_rows_solve<float>(desc, diag, f, x, sys_status, rw, st);
+  }
   carve_mnpdm(desc, nullptr, &need);
   if (!ws || ws_bytes < need) return BAND_ERR_WORKSPACE;
   const MnpdmWs w = carve_mnpdm(desc, ws, &need);

@@ -51,14 +51,17 @@ def _dev(D, f, layout, dtype=torch.float64):
     return {q: put(D[q]) for q in "abcde"}, put(f)
 
 
+@pytest.mark.parametrize("schedule", ["auto", "thread"])
 @pytest.mark.parametrize("layout", ["interleaved", "contiguous"])
 @pytest.mark.parametrize("frac,adjacent", [(0.01, False), (0.05, True), (1.0, False)])
-def test_mnpdm_against_oracle(band, layout, frac, adjacent):
+def test_mnpdm_against_oracle(band, layout, frac, adjacent, schedule):
+    """Both paths: the row-parallel eliminations with NTDM on the automatic schedule, and
+    one thread per system."""
     nsys, n = 200, 1031
     rng = np.random.default_rng(int(1000 * frac) + adjacent)
     D, f, xt = sparse_pd(rng, nsys, n, frac, adjacent)
     T, F = _dev(D, f, layout)
-    x, st = band.solve(*(T[q] for q in "abcde"), F, method="mnpdm")
+    x, st = band.solve(*(T[q] for q in "abcde"), F, method="mnpdm", schedule=schedule)
     torch.cuda.synchronize()
     assert (st.cpu().numpy() == OK).all()
     xg = x.cpu().numpy()
@@ -73,7 +76,10 @@ def test_mnpdm_against_oracle(band, layout, frac, adjacent):
 
 
 
-def test_mnpdm_without_outer_entries_is_ntdm(band):
+@pytest.mark.parametrize("schedule", ["auto", "thread"])
+def test_mnpdm_without_outer_entries_is_ntdm(band, schedule):
+    """No outer entries: MNPDM is NTDM on the same schedule, bit for bit (the automatic
+    one of a single call: partitioned for this small batch)."""
     rng = np.random.default_rng(4)
     D, f, xt = sparse_pd(rng, 64, 500, 0.0)
     for q in "ae":
@@ -81,8 +87,8 @@ def test_mnpdm_without_outer_entries_is_ntdm(band):
     D["c"] = 1.0 + np.abs(D["b"]) + np.abs(D["d"])
     f = synth.band_matvec(1, D["a"], D["b"], D["c"], D["d"], D["e"], xt)
     T, F = _dev(D, f, "interleaved")
-    x, st = band.solve(*(T[q] for q in "abcde"), F, method="mnpdm")
-    xt_, stt = band.solve(None, T["b"], T["c"], T["d"], None, F, method="ntdm", schedule="thread")
+    x, st = band.solve(*(T[q] for q in "abcde"), F, method="mnpdm", schedule=schedule)
+    xt_, stt = band.solve(None, T["b"], T["c"], T["d"], None, F, method="ntdm", schedule=schedule)
     torch.cuda.synchronize()
     assert (st.cpu() == OK).all() and (stt.cpu() == OK).all()
     assert torch.equal(x, xt_)
@@ -103,7 +109,8 @@ def test_mnpdm_aliasing_and_fp32(band):
     assert (np.abs(x32.cpu().numpy() - xt).max(0) / np.abs(xt).max(0)).max() <= 1e-4
 
 
-def test_mnpdm_zero_divisor(band):
+@pytest.mark.parametrize("schedule", ["auto", "thread"])
+def test_mnpdm_zero_divisor(band, schedule):
     """Row 2's e is eliminated with row 3, whose superdiagonal is 0: ZERO_PIVOT for that
     system only."""
     n, nsys = 8, 3
@@ -115,7 +122,7 @@ def test_mnpdm_zero_divisor(band):
     D["d"][3, 1] = 0.0
     f = np.ones((n, nsys))
     T, F = _dev(D, f, "interleaved")
-    x, st = band.solve(*(T[q] for q in "abcde"), F, method="mnpdm")
+    x, st = band.solve(*(T[q] for q in "abcde"), F, method="mnpdm", schedule=schedule)
     torch.cuda.synchronize()
     assert st.cpu().tolist() == [OK, ZERO_PIVOT, OK]
     assert oracle.mnpdm(*[D[q][:, 1] for q in "abcde"], f[:, 1])[1] == "ZERO_PIVOT"
