@@ -146,11 +146,19 @@ extern "C" band_status band_solve_batch(const band_problem* in, int32_t count, v
   if (count < 0 || count > BAND_MAX_BATCH || (count > 0 && !in)) return BAND_ERR_ARG;
   for (int32_t i = 0; i < count; ++i)
     if (!in[i].desc || !desc_ok(in[i].desc)) return BAND_ERR_ARG;
-  // heaviest problems first (a stable order; results do not depend on it)
+  // heaviest problems first; among equal costs the numeric methods before the symbolic
+  // ones (a stable order otherwise; results do not depend on it).  Measured on the
+  // 30-solve ADI step: the TD problems with STDM before NTDM 4.54 ms, with NTDM first
+  // 4.14 ms (the same instructions and DRAM bytes; the tail differs).
   int32_t order[BAND_MAX_BATCH];
   for (int32_t i = 0; i < count; ++i) order[i] = i;
+  auto symbolic_of = [&](int32_t x) {
+    return in[x].op == BAND_OP_SOLVE && is_symbolic(in[x].method) ? 1 : 0;
+  };
   std::stable_sort(order, order + count, [&](int32_t x, int32_t y) {
-    return task_cost(in[x]) > task_cost(in[y]);
+    const double cx = task_cost(in[x]), cy = task_cost(in[y]);
+    if (cx != cy) return cx > cy;
+    return symbolic_of(x) < symbolic_of(y);
   });
   band_problem probs[BAND_MAX_BATCH];
   for (int32_t i = 0; i < count; ++i) probs[i] = in[order[i]];
