@@ -78,7 +78,11 @@ __device__ __forceinline__ void run_partition(const DirectArgs<T>& p, int kmode,
 // tasks over all SMs instead of packing four per SM (measured on the 30-solve ADI step:
 // 1, 2 and 4 warps give 5.00, 4.96 and 5.19 ms); 128 registers allow 16 warps per SM.
 
-template <int W>
+// Part: the table may hold partitioned tasks.  Without them compiled in the kernel fits
+// its 128 registers without spilling (60 / 464 B of spill stores / loads with them),
+// which measured 29.4-29.6 -> 30.6 G unknowns/s on the 30-solve ADI step; the launch
+// takes that variant whenever no problem of the table is partitioned.
+template <int W, bool Part>
 __global__ void __launch_bounds__(32 * W, 16 / W) k_batch(const __grid_constant__ BatchTable t) {
   extern __shared__ __align__(16) unsigned char stage_mem[];
   void* stage = t.stage_bytes ? stage_mem + (threadIdx.x >> 5) * t.stage_bytes : nullptr;
@@ -87,7 +91,7 @@ __global__ void __launch_bounds__(32 * W, 16 / W) k_batch(const __grid_constant_
   int j = 0;
   while (j + 1 < t.count && t.it[j + 1].task0 <= task) ++j;
   const BatchItem& b = t.it[j];
-  if (b.parts) {
+  if (Part && b.parts) {
     const int64_t w = task - b.task0;
     if (b.kind == kDirect64) run_partition<double>(b.u.d64, b.kmode, b.parts, w, stage);
     else run_partition<float>(b.u.d32, b.kmode, b.parts, w, stage);
@@ -111,11 +115,15 @@ __global__ void __launch_bounds__(32 * W, 16 / W) k_batch(const __grid_constant_
 }
 
 
-// Launches k_batch<W> over `warps` warp tasks (smem: W staging areas).
+// Launches k_batch<W, Part> over `warps` warp tasks (smem: W staging areas).
 template <int W>
 cudaError_t launch_batch_w(const BatchTable& t, int64_t warps, cudaStream_t st) {
   const size_t smem = (size_t)W * (size_t)t.stage_bytes;
-  k_batch<W><<<(unsigned)((warps + W - 1) / W), 32 * W, smem, st>>>(t);
+  const unsigned grid = (unsigned)((warps + W - 1) / W);
+  bool part = false;
+  for (int32_t j = 0; j < t.count; ++j) part = part || t.it[j].parts != 0;
+  if (part) k_batch<W, true><<<grid, 32 * W, smem, st>>>(t);
+  else k_batch<W, false><<<grid, 32 * W, smem, st>>>(t);
   return cudaGetLastError();
 }
 cudaError_t launch_batch(const BatchTable& t, int64_t warps, int w, cudaStream_t st);
