@@ -16,9 +16,10 @@
 // The implicit operator I - theta D has constant diagonals (r = theta / h^2):
 //   TD: (-r, 1 + 2r, -r);  PD: (r/12, -4r/3, 1 + 5r/2, -4r/3, r/12), the reflection
 // making the PD main diagonal 1 + 29r/12 on each system's first and last row,
-// written into the workspace (the main diagonal once per sweep); the line systems are solved by band_solve (NTDM /
-// NPDM, the automatic schedule: two-sided), x-sweep systems contiguous, y-sweep systems
-// interleaved.  The right-hand sides come from one elementwise stencil kernel each.
+// written into the workspace (the main diagonal once per sweep); the line systems are
+// solved by band_solve (NTDM / NPDM on its automatic schedule: partitioned while the
+// grid has fewer than 32 lines per SM, two-sided beyond), x-sweep systems contiguous,
+// y-sweep systems interleaved.  The right-hand sides come from one elementwise stencil kernel each.
 #include <cstdint>
 
 #include "api_util.h"

@@ -13,11 +13,11 @@
 //
 // Otherwise A^T lambda = w is solved as a band system of its own: A^T's row-aligned
 // diagonals are (e_{i-2}, d_{i-1}, c_i, b_{i+1}, a_{i+2}), copied into the workspace
-// by an elementwise kernel; the NPDM / NTDM sweep then runs on them on the schedule
-// band_desc asks for (two-sided by default), writing lambda straight into dL/df; an
-// elementwise kernel forms the five gradient diagonals.  The two copies are memory
-// traffic at full bandwidth; the solve is the latency-bound part, and the two-sided
-// schedule halves it.
+// by an elementwise kernel; the NPDM / NTDM sweep then runs on them as band_solve would
+// on the schedule band_desc asks for (on AUTO: partitioned for a batch too small to fill
+// the GPU, two-sided otherwise), writing lambda straight into dL/df; an elementwise
+// kernel forms the five gradient diagonals.  The two copies are memory traffic at full
+// bandwidth; the solve is the part bound by its chains.
 #include "api_util.h"
 #include "kernels.h"
 
