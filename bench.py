@@ -397,8 +397,9 @@ class EventLog:
 
 
 # ----------------------------------------------------------- CPU baselines
-def oracle_sample(W, per_batch, nthreads):
-    """Time the CPU oracle on the first `per_batch` systems of every batch and method."""
+def oracle_sample(W, per_batch, nthreads, by_method=None):
+    """Time the CPU oracle on the first `per_batch` systems of every batch and method;
+    by_method (a dict, optional) collects [units, seconds] per method."""
     import oracle
     units = 0
     t0 = time.perf_counter()
@@ -409,10 +410,15 @@ def oracle_sample(W, per_batch, nthreads):
         for m in methods_for(w["k"]):
             kind = {"npdm": "direct", "ntdm": "direct", "spdm": "symbolic", "stdm": "symbolic",
                     "sip": "sip"}[m]
+            tm = time.perf_counter()
             x, st, _, _ = oracle.batch(kind, w["k"], diags, B["f"], ns, B["n"], B["sys_stride"],
                                        B["elem_stride"], nthreads=nthreads, tol=SIP_TOL,
                                        max_it=SIP_MAX_IT, hb_width=0)
             units += ns * B["n"]
+            if by_method is not None:
+                acc = by_method.setdefault(m, [0, 0.0])
+                acc[0] += ns * B["n"]
+                acc[1] += time.perf_counter() - tm
     dt = time.perf_counter() - t0
     return units, dt
 
@@ -434,12 +440,15 @@ def cpu_baseline(W, budget_s=15.0):
         for _ in range(reps):
             ui, di = oracle_sample(W, per, nthreads)
             u, dt = u + ui, dt + di
-    u1, dt1 = oracle_sample(W, 64, 1)
+    bym = {}
+    u1, dt1 = oracle_sample(W, 64, 1, bym)
     return {"value": u / dt, "unit": UNIT, "cores": nthreads, "kind": "oracle",
             "sample": "first %d systems of each of the 30 batched solves (every r, sweep and "
                       "method) of the same workload, %d pass(es); %.1f s" % (per, reps, dt),
             "one_core": {"value": u1 / dt1, "unit": UNIT, "cores": 1,
-                         "sample": "first 64 systems of each of the 30 solves; %.1f s" % dt1}}
+                         "sample": "first 64 systems of each of the 30 solves; %.1f s" % dt1,
+                         "per_method": {m: {"value": v[0] / v[1], "unit": UNIT}
+                                        for m, v in bym.items() if v[1] > 0}}}
 
 
 def run_reference(args, world, rank):
@@ -577,6 +586,32 @@ def _time(fn, reps=5, warm=2):
         torch.cuda.synchronize()
         best = min(best, e0.elapsed_time(e1))
     return best
+
+
+def per_method_workload(D):
+    """Each method's six solves of the step (3 r x 2 sweeps) alone, as one batched launch
+    on the step's own device data: unknowns/s per method (SIP: Algorithm 1 with its
+    residual pass, decision and tail)."""
+    import paper_1804_09666_gb300 as band
+    out = {"workload": "each method's 6 solves of the ADI step (2048 systems of n = 2048 "
+                       "each) in one batched launch", "unit": UNIT}
+    for kind in ("npdm", "spdm", "sip", "ntdm", "stdm"):
+        specs = []
+        for it in D.items:
+            if kind not in methods_for(it["w"]["k"]):
+                continue
+            v = it["view"]
+            if kind == "sip":
+                specs.append(dict(op="sip", tol=SIP_TOL, max_it=SIP_MAX_IT, **v))
+            elif it["w"]["k"] == 2:
+                specs.append(dict(method=kind, **v))
+            else:
+                specs.append(dict(method=kind, a=None, e=None, **v))
+        plan = band.BatchPlan(specs)
+        ms = _time(plan.run, reps=5)
+        units = sum(it["n"] * it["nsys"] for it in D.items if kind in methods_for(it["w"]["k"]))
+        out[kind] = {"value": units / (ms * 1e-3), "ms": ms}
+    return out
 
 
 def ragged_workload(dev, nsys=65536):
@@ -1115,7 +1150,8 @@ def main():
     if rank == 0:
         line["accuracy"] = accuracy_report(D)
     if rank == 0 and world == 1 and not args.no_extras and args.grid == GRID:
-        line["workloads"] = {"cfg0": cfg0_workload(dev), "ragged": ragged_workload(dev),
+        line["workloads"] = {"per_method": per_method_workload(D),
+                             "cfg0": cfg0_workload(dev), "ragged": ragged_workload(dev),
                              "small_batch": small_batch_workload(dev),
                              "precision": precision_workload(dev),
                              "adjoint": adjoint_workload(dev), "sip": sip_workload(dev),
