@@ -63,7 +63,7 @@ static int all_finite(int64_t n, const double* x) {
 
 /* ------------------------------------------------------------------------- */
 /* R1 -- NTDM: LU of a tridiagonal matrix without pivoting, U unit (Sec. 1;   */
-/* "the Thomas method", Sec. 4).                                              */
+/* the Thomas method of Sec. 4).                                              */
 /*   mu_0 = c_0, alpha_0 = d_0/mu_0, z_0 = f_0/mu_0                           */
 /*   mu_i = c_i - b_i alpha_{i-1};  alpha_i = d_i/mu_i;  z_i = (f_i - b_i z_{i-1})/mu_i */
 /*   x_{n-1} = z_{n-1};  x_i = z_i - alpha_i x_{i+1}                           */
@@ -1149,8 +1149,8 @@ double orc_cond1(int64_t n, int k, const double* a, const double* b, const doubl
 }
 
 /* ------------------------------------------------------------------------- */
-/* Batch driver: loops over independent systems (the paper's "solve          */
-/* independently (or in parallel) N SLAEs", Sec. 1), gathering each system    */
+/* Batch driver: loops over independent systems (Sec. 1: the N systems of a */
+/* sweep share no data, so any order is valid), gathering each system        */
 /* into contiguous scratch.  Element i of system s of array p lives at        */
 /* p[off_s + i * elem_stride] with off_s = offsets ? offsets[s] : s*sys_stride*/
 /* and length n_s = offsets ? offsets[s+1]-offsets[s] : n.  Per-system half   */
