@@ -31,9 +31,15 @@
  * Ownership and asynchrony.  Every pointer except `desc` and the host-side arrays
  * named as such is a device pointer owned by the caller.  The library allocates no
  * device memory: scratch comes from the caller's workspace, whose size
- * band_workspace_size() gives (256-byte aligned).  All calls enqueue work on
+ * band_workspace_size() gives (a multiple of 256 bytes).  All calls enqueue work on
  * `stream` (a cudaStream_t; NULL = the legacy default stream) and return without
  * waiting.  Inputs are never modified; x may alias f.
+ *
+ * Alignment.  Every element array starts on a boundary of its element size (8 bytes
+ * for FP64 and int64 arrays, 4 for FP32 and int32); workspaces and factor buffers
+ * start on a 256-byte boundary (as cudaMalloc's allocations do).  A call given a
+ * pointer off its boundary returns BAND_ERR_ARG (BAND_ERR_WORKSPACE for a workspace
+ * or factor buffer) and launches nothing.
  *
  * Errors.  The return value reports argument, workspace and launch errors only.
  * Numerical outcomes are written per system to the device array sys_status
@@ -59,7 +65,7 @@ typedef enum {
   BAND_ERR_NOT_CONVERGED = 6,   /* per system: SIP / refinement / HB reached its cap */
   BAND_ERR_SYMBOLIC_RANGE = 7,  /* per system: the Laurent window of the symbolic path ran out */
   BAND_ERR_INTERNAL = 8,        /* per system: a kernel-side consistency check failed */
-  BAND_ERR_WORKSPACE = 9        /* workspace missing or smaller than band_workspace_size() */
+  BAND_ERR_WORKSPACE = 9        /* workspace missing, misaligned or smaller than band_workspace_size() */
 } band_status;
 
 typedef enum {

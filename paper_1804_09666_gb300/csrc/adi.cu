@@ -136,9 +136,10 @@ extern "C" band_status band_adi_step(const band_desc* grid, double tau, double l
                                      const double* source, double* u, int32_t* sys_status,
                                      void* ws, size_t ws_bytes, void* stream) {
   if (!grid_ok(grid) || !u || !(tau > 0.0) || !(lambda == lambda)) return BAND_ERR_ARG;
+  if (!aligned_all(8, {u, source}) || !aligned_to(sys_status, 4)) return BAND_ERR_ARG;
   size_t need = 0;
   carve_adi(grid, nullptr, &need);
-  if (!ws || ws_bytes < need) return BAND_ERR_WORKSPACE;
+  if (!ws_fits(ws, ws_bytes, need)) return BAND_ERR_WORKSPACE;
   const AdiWs w = carve_adi(grid, ws, &need);
   cudaStream_t st = static_cast<cudaStream_t>(stream);
   const int64_t n = grid->n, cells = n * n;

@@ -230,13 +230,17 @@ extern "C" band_status band_adjoint(const band_desc* desc, int32_t method, const
   if (!grad_diag[1] || !grad_diag[2] || !grad_diag[3]) return BAND_ERR_ARG;
   const bool pd = may_be_pd(desc) && kmode != 1;
   if (pd && (!diag[0] || !diag[4] || !grad_diag[0] || !grad_diag[4])) return BAND_ERR_ARG;
+  if (!arrays_aligned(BAND_F64, diag, x, w, sys_status) ||
+      !arrays_aligned(BAND_F64, grad_diag, grad_f, nullptr, nullptr))
+    return BAND_ERR_ARG;
+  if (!aligned_to(factors, kWsAlign)) return BAND_ERR_WORKSPACE;
   cudaStream_t st = static_cast<cudaStream_t>(stream);
   if (!factors && !desc->offsets && kmode > 0) {
     // the transposed system solved as a band system of its own
     const int32_t m = kmode == 1 ? BAND_NTDM : BAND_NPDM;
     size_t need = 0;
     carve_adjoint_t(desc, m, nullptr, &need);
-    if (!ws || ws_bytes < need) return BAND_ERR_WORKSPACE;
+    if (!ws_fits(ws, ws_bytes, need)) return BAND_ERR_WORKSPACE;
     const AdjTWs tw = carve_adjoint_t(desc, m, ws, &need);
     const Layout L = layout_of(desc);
     const int64_t total = desc->nsys * desc->n;
@@ -267,7 +271,7 @@ extern "C" band_status band_adjoint(const band_desc* desc, int32_t method, const
   }
   size_t need = 0;
   carve_adjoint(desc, nullptr, &need);
-  if (!ws || ws_bytes < need) return BAND_ERR_WORKSPACE;
+  if (!ws_fits(ws, ws_bytes, need)) return BAND_ERR_WORKSPACE;
   const AdjWs wk = carve_adjoint(desc, ws, &need);
   AdjArgs p{};
   p.L = layout_of(desc);

@@ -164,7 +164,7 @@ band_status run_single(const band_desc* desc, int32_t method, const void* const 
                        const void* f, void* x, int32_t* sys_status, void* ws, size_t ws_bytes,
                        cudaStream_t st, const int32_t* skip) {
   if (auto_part(desc, method)) {
-    if (!ws || ws_bytes < single_solve_bytes(desc, method)) return BAND_ERR_WORKSPACE;
+    if (!ws_fits(ws, ws_bytes, single_solve_bytes(desc, method))) return BAND_ERR_WORKSPACE;
     const band_desc dp = partitioned_of(desc);
     // both sweeps carve alpha and beta from the workspace's start (the partitioned
     // carve extends the plain one); the second launch runs after the first is done
@@ -262,9 +262,10 @@ band_status make_direct(const band_desc* desc, int32_t method, const void* const
   if (is_symbolic(method) && desc->dtype != BAND_F64) return BAND_ERR_ARG;
   if (!diag || !f || !x || !diag[1] || !diag[2] || !diag[3]) return BAND_ERR_ARG;
   if (may_be_pd(desc) && kmode != 1 && (!diag[0] || !diag[4])) return BAND_ERR_ARG;
+  if (!arrays_aligned(desc->dtype, diag, f, x, sys_status)) return BAND_ERR_ARG;
   size_t need = 0;
   carve_solve(desc, method, nullptr, &need);
-  if (!ws || ws_bytes < need) return BAND_ERR_WORKSPACE;
+  if (!ws_fits(ws, ws_bytes, need)) return BAND_ERR_WORKSPACE;
   const SolveWs w = carve_solve(desc, method, ws, &need);
   const Layout L = layout_of(desc);
   const Spill W = spill_of(desc);
@@ -358,6 +359,10 @@ band_status band_solve(const band_desc* desc, int32_t method, const void* factor
                        const void* const diag[5], const void* f, void* x, int32_t* sys_status,
                        void* ws, size_t ws_bytes, void* stream) {
   if (!desc_ok(desc)) return BAND_ERR_ARG;
+  if (desc->nsys > 0) {
+    if (!arrays_aligned(desc->dtype, diag, f, x, sys_status)) return BAND_ERR_ARG;
+    if (!aligned_to(factors, kWsAlign)) return BAND_ERR_WORKSPACE;
+  }
   if (method == BAND_MNPDM) {
     if (factors) return BAND_ERR_ARG;
     if (desc->nsys == 0) return BAND_OK;
@@ -399,7 +404,8 @@ band_status band_factor(const band_desc* desc, int32_t method, const void* const
   if (!diag || !factors) return BAND_ERR_ARG;
   if (!diag[1] || !diag[2] || !diag[3]) return BAND_ERR_ARG;
   if (may_be_pd(desc) && kmode != 1 && (!diag[0] || !diag[4])) return BAND_ERR_ARG;
-  if (factors_bytes < factor_bytes(desc)) return BAND_ERR_WORKSPACE;
+  if (!arrays_aligned(desc->dtype, diag, nullptr, nullptr, sys_status)) return BAND_ERR_ARG;
+  if (!aligned_to(factors, kWsAlign) || factors_bytes < factor_bytes(desc)) return BAND_ERR_WORKSPACE;
   cudaStream_t st = static_cast<cudaStream_t>(stream);
   const FactorPtrs fp = factor_ptrs(desc, factors);
   const Layout L = layout_of(desc);

@@ -2,6 +2,7 @@
 #pragma once
 #include <cstddef>
 #include <cstdint>
+#include <initializer_list>
 #include <cuda_runtime.h>
 
 #include "band.h"
@@ -23,6 +24,34 @@ struct Carve {
 };
 
 inline size_t dtype_size(int32_t dt) { return dt == BAND_F32 ? 4 : 8; }
+
+// Alignment the kernels rely on.  Element arrays are read and written as whole elements
+// (8 bytes FP64, 4 FP32; 4-byte statuses, 8-byte offsets and system ids).  Workspaces
+// and factor buffers are carved at 256-byte offsets from their base, and parts of them
+// are read as 16-byte vectors, so the base must sit on a 256-byte boundary (as
+// cudaMalloc's allocations do).  A pointer that breaks this would fault on the GPU; the
+// entry points reject it instead.
+constexpr size_t kWsAlign = 256;
+inline bool aligned_to(const void* p, size_t a) { return ((uintptr_t)p & (a - 1)) == 0; }
+// the caller's workspace: present, on a kWsAlign boundary, at least `need` bytes
+inline bool ws_fits(const void* ws, size_t ws_bytes, size_t need) {
+  return ws && aligned_to(ws, kWsAlign) && ws_bytes >= need;
+}
+// every given pointer (NULL counts as aligned) on an `a`-byte boundary
+inline bool aligned_all(size_t a, std::initializer_list<const void*> ps) {
+  for (const void* p : ps)
+    if (!aligned_to(p, a)) return false;
+  return true;
+}
+// the five diagonals (any may be NULL), f and x in `dtype`, and the int32 statuses
+inline bool arrays_aligned(int32_t dtype, const void* const diag[5], const void* f,
+                           const void* x, const int32_t* status) {
+  const size_t s = dtype_size(dtype);
+  if (diag)
+    for (int q = 0; q < 5; ++q)
+      if (!aligned_to(diag[q], s)) return false;
+  return aligned_all(s, {f, x}) && aligned_to(status, 4);
+}
 inline bool ragged(const band_desc* d) { return d->offsets != nullptr; }
 
 // Rows of one scratch array: interleaved by system for uniform batches (S x n with S
@@ -64,6 +93,7 @@ inline bool desc_ok(const band_desc* d) {
                          d->chunks > 256 || (d->chunks & (d->chunks - 1)) != 0))
     return false;
   if (d->systems && !d->offsets) return false;     // id lists select from a ragged packing
+  if (!aligned_all(8, {d->offsets, d->systems})) return false;   // device int64 arrays
   if (ragged(d)) {
     if (d->total_rows < 0) return false;
   } else {

@@ -120,9 +120,10 @@ extern "C" band_status band_det(const band_desc* desc, const void* const diag[5]
   const int kmode = desc->hbw ? 0 : desc->half_bw;
   if (kmode != 0 && kmode != 1 && kmode != 2) return BAND_ERR_ARG;
   if (kmode != 1 && (!diag[0] || !diag[4])) return BAND_ERR_ARG;
+  if (!arrays_aligned(BAND_F64, diag, det_mant, det_exp, sys_status)) return BAND_ERR_ARG;
   void *count, *list;
   const size_t need = carve_det(desc, nullptr, &count, &list);
-  if (!ws || ws_bytes < need) return BAND_ERR_WORKSPACE;
+  if (!ws_fits(ws, ws_bytes, need)) return BAND_ERR_WORKSPACE;
   carve_det(desc, ws, &count, &list);
   cudaStream_t st = static_cast<cudaStream_t>(stream);
   if (cudaMemsetAsync(count, 0, sizeof(unsigned long long), st) != cudaSuccess) return BAND_ERR_CUDA;

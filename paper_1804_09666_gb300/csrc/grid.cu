@@ -665,7 +665,7 @@ band_status grid_solve(const band_desc* desc, int32_t method, const void* const 
   if (kmode == 2 && (!diag[0] || !diag[4])) return BAND_ERR_ARG;
   size_t need = 0;
   carve_grid(desc, nullptr, &need);
-  if (!ws || ws_bytes < need) return BAND_ERR_WORKSPACE;
+  if (!ws_fits(ws, ws_bytes, need)) return BAND_ERR_WORKSPACE;
   const GridWs w = carve_grid(desc, ws, &need);
   if (cudaMemsetAsync(w.flags, 0, sizeof(int32_t) * (size_t)desc->nsys, st) != cudaSuccess)
     return BAND_ERR_CUDA;

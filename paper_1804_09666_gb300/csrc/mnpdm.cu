@@ -417,14 +417,14 @@ band_status mnpdm_solve(const band_desc* desc, const void* const diag[5], const 
   size_t need = 0;
   if (mn_rows_path(desc)) {
     carve_mn_rows(desc, nullptr, &need);
-    if (!ws || ws_bytes < need) return BAND_ERR_WORKSPACE;
+    if (!ws_fits(ws, ws_bytes, need)) return BAND_ERR_WORKSPACE;
     const MnRowWs rw = carve_mn_rows(desc, ws, &need);
     return desc->dtype == BAND_F64
                ? mn_rows_solve<double>(desc, diag, f, x, sys_status, rw, st)
                : mn_rows_solve<float>(desc, diag, f, x, sys_status, rw, st);
   }
   carve_mnpdm(desc, nullptr, &need);
-  if (!ws || ws_bytes < need) return BAND_ERR_WORKSPACE;
+  if (!ws_fits(ws, ws_bytes, need)) return BAND_ERR_WORKSPACE;
   const MnpdmWs w = carve_mnpdm(desc, ws, &need);
   const Layout L = layout_of(desc);
   const Spill W = spill_of(desc);

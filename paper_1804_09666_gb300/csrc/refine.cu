@@ -475,9 +475,12 @@ extern "C" band_status band_refine_solve_ex(const band_desc* desc32, const void*
   if (!diag32 || !f || !x) return BAND_ERR_ARG;
   if (!diag32[1] || !diag32[2] || !diag32[3]) return BAND_ERR_ARG;
   if (may_be_pd(desc32) && (!diag32[0] || !diag32[4])) return BAND_ERR_ARG;
+  if (!arrays_aligned(BAND_F32, diag32, nullptr, nullptr, sys_status) ||
+      !aligned_all(8, {f, x}) || !aligned_all(4, {steps}))
+    return BAND_ERR_ARG;
   size_t need = 0;
   carve_refine(desc32, nullptr, &need);
-  if (!ws || ws_bytes < need) return BAND_ERR_WORKSPACE;
+  if (!ws_fits(ws, ws_bytes, need)) return BAND_ERR_WORKSPACE;
   const RefWs w = carve_refine(desc32, ws, &need);
   cudaStream_t st = static_cast<cudaStream_t>(stream);
   const int kmode = desc32->hbw ? 0 : desc32->half_bw;

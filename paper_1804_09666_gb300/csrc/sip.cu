@@ -492,9 +492,12 @@ band_status make_sip(const band_desc* desc, const void* const diag[5], const voi
   // TD systems are treated as PD with a = e = 0; that needs a and e arrays.
   if (!diag || !f || !x || !diag[0] || !diag[1] || !diag[2] || !diag[3] || !diag[4])
     return BAND_ERR_ARG;
+  if (!arrays_aligned(BAND_F64, diag, f, x, sys_status) || !aligned_all(8, {resid}) ||
+      !aligned_all(4, {iters}))
+    return BAND_ERR_ARG;
   size_t need = 0;
   carve_sip(desc, width, nullptr, &need);
-  if (!ws || ws_bytes < need) return BAND_ERR_WORKSPACE;
+  if (!ws_fits(ws, ws_bytes, need)) return BAND_ERR_WORKSPACE;
   const SipWs w = carve_sip(desc, width, ws, &need);
   *sa = SipArgs{};
   sa->L = layout_of(desc);

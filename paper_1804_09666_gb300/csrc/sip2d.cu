@@ -330,9 +330,12 @@ extern "C" band_status band_sip2d(const band_desc* desc, int64_t nx, const void*
   if (!diag || !diag[0] || !diag[1] || !diag[2] || !diag[3] || !diag[4] || !f || !x)
     return BAND_ERR_ARG;
   if ((const void*)x == (const void*)f) return BAND_ERR_ARG;
+  if (!arrays_aligned(BAND_F64, diag, f, x, sys_status) || !aligned_all(8, {resid}) ||
+      !aligned_all(4, {iters}))
+    return BAND_ERR_ARG;
   size_t need = 0;
   carve_sip2d(desc, nullptr, &need);
-  if (!ws || ws_bytes < need) return BAND_ERR_WORKSPACE;
+  if (!ws_fits(ws, ws_bytes, need)) return BAND_ERR_WORKSPACE;
   const Sip2dWs w = carve_sip2d(desc, ws, &need);
   Sip2dArgs p{layout_of(desc), spill_of(desc), nx, desc->n / nx,
               (const double*)diag[0], (const double*)diag[1], (const double*)diag[2],

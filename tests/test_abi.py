@@ -186,6 +186,64 @@ def test_bad_arguments_are_rejected_without_gpu(lib):
     assert lib.band_workspace_size(ct.byref(d), L.OP_DET, 0, 0) >= 8 + 64 * 8
 
 
+def test_misaligned_pointers_are_rejected_without_gpu(lib):
+    """A pointer off its boundary (element size for arrays, 256 bytes for workspaces and
+    factor buffers) is refused before anything is launched, so these calls with fake
+    addresses never reach the GPU."""
+    from paper_1804_09666_gb300 import _lib as L
+    ws = 1 << 20                   # a 256-byte aligned stand-in address
+    full = L.DIAG5(8, 16, 24, 32, 40)
+    odd = L.DIAG5(8, 16, 28, 32, 40)                       # c off the 8-byte boundary
+    d, d32 = _desc(), _desc(dtype=L.F32)
+    assert lib.band_solve(ct.byref(d), L.NPDM, None, odd, 8, 8, None, ws, 1 << 30, None) == L.ERR_ARG
+    assert lib.band_solve(ct.byref(d), L.NPDM, None, full, 12, 8, None, ws, 1 << 30, None) == L.ERR_ARG
+    assert lib.band_solve(ct.byref(d), L.NPDM, None, full, 8, 4, None, ws, 1 << 30, None) == L.ERR_ARG
+    assert lib.band_solve(ct.byref(d), L.NPDM, None, full, 8, 8, 6, ws, 1 << 30, None) == L.ERR_ARG
+    assert lib.band_solve(ct.byref(d), L.NPDM, 4096 + 8, full, 8, 8, None, ws, 1 << 30,
+                          None) == L.ERR_WORKSPACE
+    for w in (ws + 8, ws + 128):   # workspace off the 256-byte boundary
+        assert lib.band_solve(ct.byref(d), L.NPDM, None, full, 8, 8, None, w, 1 << 30,
+                              None) == L.ERR_WORKSPACE
+        for s in ("auto", "thread", "two_sided", "partitioned", "grid"):
+            ds = _desc(schedule={"auto": L.SCHED_AUTO, "thread": L.SCHED_THREAD,
+                                 "two_sided": L.SCHED_TWO_SIDED,
+                                 "partitioned": L.SCHED_PARTITIONED, "grid": L.SCHED_GRID}[s])
+            assert lib.band_solve(ct.byref(ds), L.NPDM, None, full, 8, 8, None, w, 1 << 30,
+                                  None) == L.ERR_WORKSPACE, s
+        assert lib.band_sip(ct.byref(d), full, 8, 8, 1e-10, 10, 5, 30, 1e-12, None, None, None, w,
+                            1 << 30, None) == L.ERR_WORKSPACE
+        assert lib.band_det(ct.byref(d), full, 8, 8, 8, w, 1 << 30, None) == L.ERR_WORKSPACE
+    # FP32 arrays need 4 bytes: 4 is on the boundary, 2 is not
+    assert lib.band_solve(ct.byref(d32), L.NPDM, None, L.DIAG5(4, 12, 20, 28, 36), 4, 4, None,
+                          ws + 8, 1 << 30, None) == L.ERR_WORKSPACE   # arrays fine, ws not
+    assert lib.band_solve(ct.byref(d32), L.NPDM, None, L.DIAG5(4, 12, 22, 28, 36), 4, 4, None,
+                          ws, 1 << 30, None) == L.ERR_ARG
+    # the other entry points
+    assert lib.band_factor(ct.byref(d), L.NPDM, odd, ws, 1 << 30, None, None) == L.ERR_ARG
+    assert lib.band_factor(ct.byref(d), L.NPDM, full, ws + 64, 1 << 30, None, None) == L.ERR_WORKSPACE
+    assert lib.band_sip(ct.byref(d), odd, 8, 8, 1e-10, 10, 5, 30, 1e-12, None, None, None, ws,
+                        1 << 30, None) == L.ERR_ARG
+    assert lib.band_sip(ct.byref(d), full, 8, 8, 1e-10, 10, 5, 30, 1e-12, 2, None, None, ws,
+                        1 << 30, None) == L.ERR_ARG               # int32 iters off 4 bytes
+    assert lib.band_refine_solve(ct.byref(d32), L.DIAG5(4, 12, 20, 28, 36), 12, 8, 1e-11, 10,
+                                 None, None, ws, 1 << 30, None) == L.ERR_ARG
+    assert lib.band_adjoint(ct.byref(d), L.NPDM, None, full, 8, 8, odd, 8, None, ws, 1 << 30,
+                            None) == L.ERR_ARG
+    assert lib.band_adjoint(ct.byref(d), L.NPDM, 4096 + 16, full, 8, 8, full, 8, None, ws,
+                            1 << 30, None) == L.ERR_WORKSPACE
+    assert lib.band_det(ct.byref(d), full, 12, 8, 8, ws, 1 << 30, None) == L.ERR_ARG
+    grid = _desc(nsys=64, n=64, sys_stride=1, elem_stride=1)
+    assert lib.band_adi_step(ct.byref(grid), 0.1, 1.0, None, 12, None, ws, 1 << 40, None) == L.ERR_ARG
+    assert lib.band_adi_step(ct.byref(grid), 0.1, 1.0, None, 8, None, ws + 8, 1 << 40,
+                             None) == L.ERR_WORKSPACE
+    d2 = _desc(nsys=64, n=120)
+    assert lib.band_sip2d(ct.byref(d2), 12, full, 8, 20, 1e-10, 10, None, None, None, ws, 1 << 30,
+                          None) == L.ERR_ARG
+    # ragged offsets and id lists are device int64 arrays
+    assert lib.band_workspace_size(ct.byref(_desc(offsets=12, total_rows=100)), L.OP_SOLVE,
+                                   L.NPDM, 0) == 0
+
+
 def test_package_refuses_to_run_without_library(tmp_path):
     from paper_1804_09666_gb300 import _lib as L
     with pytest.raises(RuntimeError):
