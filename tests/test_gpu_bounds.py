@@ -1,13 +1,13 @@
-"""Writes stay inside their arrays, on every schedule.
+"""Writes stay inside their arrays, on every schedule and entry point.
 
-Each output (x and the statuses) and the workspace sits inside a larger buffer whose
-other entries hold a sentinel: a head before the first element, the gaps between
-systems that the strides leave, and a tail after the last one.  The inputs sit the
-same way, their heads, gaps and tails NaN.  Heads of one element put the FP64 arrays
-off the 16-byte boundary (plain loads), heads of two on it (the 16-byte granule ring
-for contiguous systems).  After each solve every sentinel is unchanged and x matches
-the oracle.  This is the bounds evidence of the device code that a memory checker
-would otherwise give.
+Each output (x, the statuses, iteration counts, residuals, gradients, determinants,
+stored factors) and the workspace sits inside a larger buffer whose other entries hold
+a sentinel: a head before the first element, the gaps between systems that the strides
+leave, and a tail after the last one.  The inputs sit the same way, their heads, gaps
+and tails NaN.  Heads of one element put the FP64 arrays off the 16-byte boundary
+(plain loads), heads of two on it (the 16-byte granule ring for contiguous systems).
+After each call every sentinel is unchanged and the results match the oracle.  This is
+the bounds evidence of the device code that a memory checker would otherwise give.
 """
 import ctypes as ct
 
@@ -23,11 +23,14 @@ from paper_1804_09666_gb300 import _lib as L
 pytestmark = pytest.mark.gpu
 
 METHODS = {"ntdm": L.NTDM, "npdm": L.NPDM, "stdm": L.STDM, "spdm": L.SPDM}
-X_SENT = -3.0e299               # a finite double no solve produces here
-ST_SENT = 0x5A5A5A5A            # int32
+X_SENT = -3.0e299               # a finite double none of these calls produces
+I_SENT = 0x5A5A5A5A             # int32 / int64 sentinel
 WS_SENT = 0xA5                  # byte
-TAIL = 40                       # elements after the last one
-WS_PAD = 1024                   # bytes before and after the workspace (256-aligned)
+TAIL = 40                       # entries after the last element
+FLAT_HEAD = 32                  # entries before a per-system output
+WS_PAD = 1024                   # bytes before and after a workspace (256-aligned)
+LAYOUTS = ["interleaved", "contiguous"]
+HEADS = [1, 2]
 
 
 @pytest.fixture(scope="module")
@@ -45,7 +48,7 @@ def _strides(layout, nsys, n):
 
 def _padded(canon, head, ss, es, fill):
     """Flat host buffer: `head` fill entries, then canon (n, nsys) at the given
-    strides with fill in the gaps, then TAIL fill entries."""
+    strides with fill in the gaps, then TAIL fill entries; and the elements' indexes."""
     n, nsys = canon.shape
     span = (n - 1) * es + (nsys - 1) * ss + 1
     buf = np.full(head + span + TAIL, fill, dtype=np.float64)
@@ -74,49 +77,105 @@ def _system(k, nsys, n, seed, plant=None):
     return D, f
 
 
-def _run(band, method, schedule, layout, head, nsys, n, plant=None, seed=0):
-    k = 1 if method in ("ntdm", "stdm") else 2
-    D, f = _system(k, nsys, n, seed, plant)
-    ss, es = _strides(layout, nsys, n)
-    host = {}
-    for q in "abcde":
-        host[q], idx = _padded(D[q], head, ss, es, np.nan)
-    host["f"], idx = _padded(f, head, ss, es, np.nan)
-    view = lambda buf: buf.as_strided((n, nsys), (es, ss), head)
-    dev = {q: torch.from_numpy(v).to(DEV) for q, v in host.items()}
-    args = [view(dev[q]) if (k == 2 or q not in "ae") else None for q in "abcdef"]
-    xbuf = torch.full_like(dev["f"], X_SENT)
-    x = view(xbuf)
-    sbuf = torch.full((nsys + 64,), ST_SENT, dtype=torch.int32, device=DEV)
-    status = sbuf[32:32 + nsys]
-    desc = band.desc_for(x, k, schedule)
-    need = L.load().band_workspace_size(ct.byref(desc), L.OP_SOLVE, METHODS[method], 0)
-    wbuf = torch.full((need + 2 * WS_PAD,), WS_SENT, dtype=torch.uint8, device=DEV)
-    ws = wbuf[WS_PAD:WS_PAD + need]
-    assert ws.data_ptr() % 256 == 0
-    band.solve(*args, method=method, x=x, status=status, ws=ws, schedule=schedule)
-    torch.cuda.synchronize()
-    # every sentinel outside the arrays' elements is unchanged
-    xh = xbuf.cpu().numpy()
-    inside = np.zeros(xh.size, dtype=bool)
-    inside[idx.reshape(-1)] = True
-    assert (xh[~inside] == X_SENT).all(), "x written outside its elements"
-    sh = sbuf.cpu().numpy()
-    assert (sh[:32] == ST_SENT).all() and (sh[32 + nsys:] == ST_SENT).all(), "status overrun"
-    wh = wbuf.cpu().numpy()
-    assert (wh[:WS_PAD] == WS_SENT).all(), "workspace underrun"
-    assert (wh[WS_PAD + need:] == WS_SENT).all(), "workspace overrun"
-    # every system solved, and solved right
-    assert (sh[32:32 + nsys] == 0).all(), sh[32:32 + nsys]
-    diags = tuple(host[q][head:] for q in "abcde")
-    ref, rst, _, _ = oracle.batch("gepp", k, diags, host["f"][head:], nsys, n, ss, es)
-    assert (np.asarray(rst) == 0).all()
-    rel = per_system_rel(xh[head:], ref, n, nsys, ss, es)
-    return rel
+class Case:
+    """One batch's inputs in guarded strided storage on the device; guarded strided,
+    per-system and workspace outputs made on request and checked together."""
+
+    def __init__(self, k, nsys, n, layout, head, seed, plant=None):
+        self.k, self.nsys, self.n, self.head = k, nsys, n, head
+        self.ss, self.es = _strides(layout, nsys, n)
+        D, f = _system(k, nsys, n, seed, plant)
+        self.host = {}
+        for q in "abcde":
+            self.host[q], self.idx = _padded(D[q], head, self.ss, self.es, np.nan)
+        self.host["f"], _ = _padded(f, head, self.ss, self.es, np.nan)
+        self.dev = {q: torch.from_numpy(v).to(DEV) for q, v in self.host.items()}
+        self.inside = np.zeros(self.host["f"].size, dtype=bool)
+        self.inside[self.idx.reshape(-1)] = True
+        self.guards = []          # (name, buffer, check) of every output
+
+    def view(self, buf):
+        return buf.as_strided((self.n, self.nsys), (self.es, self.ss), self.head)
+
+    def put(self, canon):
+        """A strided device input holding canon (n, nsys), NaN outside its elements."""
+        return self.view(torch.from_numpy(_padded(canon, self.head, self.ss, self.es,
+                                                  np.nan)[0]).to(DEV))
+
+    def diag5(self):
+        keep = "abcde" if self.k == 2 else "bcd"
+        return L.DIAG5(*[(self.view(self.dev[q]).data_ptr() if q in keep else None)
+                         for q in "abcde"])
+
+    def system(self, q, s):
+        return self.host[q][self.idx[:, s]]
+
+    def strided_out(self, name):
+        """A strided output in the inputs' layout, the sentinel outside its elements."""
+        buf = torch.full_like(self.dev["f"], X_SENT)
+        self.guards.append((name, buf, lambda h: (h[~self.inside] == X_SENT).all()))
+        return self.view(buf)
+
+    def flat_out(self, name, count, dtype):
+        sent = X_SENT if dtype == torch.float64 else I_SENT
+        buf = torch.full((FLAT_HEAD + count + TAIL,), sent, dtype=dtype, device=DEV)
+        self.guards.append((name, buf, lambda h: (h[:FLAT_HEAD] == sent).all() and
+                            (h[FLAT_HEAD + count:] == sent).all()))
+        return buf[FLAT_HEAD:FLAT_HEAD + count]
+
+    def workspace(self, name, nbytes):
+        buf = torch.full((nbytes + 2 * WS_PAD,), WS_SENT, dtype=torch.uint8, device=DEV)
+        self.guards.append((name, buf, lambda h: (h[:WS_PAD] == WS_SENT).all() and
+                            (h[WS_PAD + nbytes:] == WS_SENT).all()))
+        ws = buf[WS_PAD:WS_PAD + nbytes]
+        assert ws.data_ptr() % 256 == 0
+        return ws
+
+    def check_guards(self):
+        torch.cuda.synchronize()
+        for name, buf, ok in self.guards:
+            assert ok(buf.cpu().numpy()), "%s written outside its elements" % name
+
+    def desc(self, schedule="auto", chunks=0):
+        sched = {"auto": L.SCHED_AUTO, "thread": L.SCHED_THREAD, "two_sided": L.SCHED_TWO_SIDED,
+                 "partitioned": L.SCHED_PARTITIONED, "grid": L.SCHED_GRID}[schedule]
+        return L.BandDesc(half_bw=self.k, dtype=L.F64, nsys=self.nsys, n=self.n,
+                          sys_stride=self.ss, elem_stride=self.es, offsets=None, hbw=None,
+                          total_rows=0, schedule=sched, chunks=chunks)
+
+    def gepp(self):
+        """The oracle's banded GEPP solution, canonical (n, nsys)."""
+        diags = tuple(self.host[q][self.head:] for q in "abcde")
+        ref, st, _, _ = oracle.batch("gepp", self.k, diags, self.host["f"][self.head:],
+                                     self.nsys, self.n, self.ss, self.es)
+        assert (np.asarray(st) == 0).all()
+        return np.asarray(ref)[self.idx - self.head]
+
+    def rel(self, x_view, canon):
+        """Per-system relative error of a strided device output against canon."""
+        got = x_view.cpu().numpy()
+        return per_system_rel(got.reshape(-1), canon.reshape(-1), self.n, self.nsys,
+                              1, self.nsys)
 
 
-LAYOUTS = ["interleaved", "contiguous"]
-HEADS = [1, 2]
+def _stream():
+    return ct.c_void_p(torch.cuda.current_stream().cuda_stream)
+
+
+def _solve(C, method, schedule):
+    lib = L.load()
+    desc = C.desc(schedule)
+    x = C.strided_out("x")
+    status = C.flat_out("status", C.nsys, torch.int32)
+    ws = C.workspace("workspace", lib.band_workspace_size(ct.byref(desc), L.OP_SOLVE,
+                                                          METHODS[method], 0))
+    code = lib.band_solve(ct.byref(desc), METHODS[method], None, C.diag5(),
+                          C.view(C.dev["f"]).data_ptr(), x.data_ptr(), status.data_ptr(),
+                          ws.data_ptr(), ws.numel(), _stream())
+    assert code == L.OK
+    C.check_guards()
+    assert (status.cpu() == 0).all()
+    return C.rel(x, C.gepp())
 
 
 @pytest.mark.parametrize("layout", LAYOUTS)
@@ -124,16 +183,16 @@ HEADS = [1, 2]
 @pytest.mark.parametrize("schedule", ["auto", "thread", "two_sided", "partitioned"])
 @pytest.mark.parametrize("method", ["npdm", "ntdm"])
 def test_numeric_writes_stay_inside(band, method, schedule, layout, head):
-    rel = _run(band, method, schedule, layout, head, nsys=70, n=600, seed=head)
-    assert rel.max() <= 1e-12, rel.max()
+    C = Case(2 if method == "npdm" else 1, 70, 600, layout, head, seed=head)
+    assert _solve(C, method, schedule).max() <= 1e-12
 
 
 @pytest.mark.parametrize("layout", LAYOUTS)
 @pytest.mark.parametrize("head", HEADS)
 @pytest.mark.parametrize("method", ["npdm", "ntdm"])
 def test_grid_schedule_writes_stay_inside(band, method, layout, head):
-    rel = _run(band, method, "grid", layout, head, nsys=3, n=6000, seed=10 + head)
-    assert rel.max() <= 1e-12, rel.max()
+    C = Case(2 if method == "npdm" else 1, 3, 6000, layout, head, seed=10 + head)
+    assert _solve(C, method, "grid").max() <= 1e-12
 
 
 @pytest.mark.parametrize("layout", LAYOUTS)
@@ -141,9 +200,8 @@ def test_grid_schedule_writes_stay_inside(band, method, layout, head):
 def test_redo_list_writes_stay_inside(band, layout, head):
     """The automatic schedule with systems whose partitioned elimination fails: the
     redo counter and list in the workspace, then the second launch."""
-    rel = _run(band, "npdm", "auto", layout, head, nsys=70, n=600,
-               plant=("chunk_starts", (3, 41, 69)), seed=20 + head)
-    assert rel.max() <= 1e-10, rel.max()
+    C = Case(2, 70, 600, layout, head, seed=20 + head, plant=("chunk_starts", (3, 41, 69)))
+    assert _solve(C, "npdm", "auto").max() <= 1e-10
 
 
 @pytest.mark.parametrize("layout", LAYOUTS)
@@ -153,6 +211,144 @@ def test_redo_list_writes_stay_inside(band, layout, head):
 def test_symbolic_writes_stay_inside(band, method, schedule, layout, head):
     """Zero pivots in three systems: the flagged list, the fix-up's slots and its
     series scratch in the workspace."""
-    rel = _run(band, method, schedule, layout, head, nsys=70, n=600,
-               plant=("zero_row", (0, 33, 69)), seed=30 + head)
-    assert rel.max() <= 1e-10, rel.max()
+    C = Case(2 if method == "spdm" else 1, 70, 600, layout, head, seed=30 + head,
+             plant=("zero_row", (0, 33, 69)))
+    assert _solve(C, method, schedule).max() <= 1e-10
+
+
+@pytest.mark.parametrize("layout", LAYOUTS)
+@pytest.mark.parametrize("head", HEADS)
+@pytest.mark.parametrize("width", [0, 5])
+def test_sip_writes_stay_inside(band, width, layout, head):
+    """band_sip: x, iteration counts, residuals, statuses and the workspace (the ILU(0)
+    factors, or the Hotelling-Bodewig band inverses for width 5)."""
+    lib = L.load()
+    C = Case(2, 70, 600, layout, head, seed=40 + head)
+    desc = C.desc()
+    x = C.strided_out("x")
+    iters = C.flat_out("iters", C.nsys, torch.int32)
+    resid = C.flat_out("resid", C.nsys, torch.float64)
+    status = C.flat_out("status", C.nsys, torch.int32)
+    ws = C.workspace("workspace", lib.band_workspace_size(ct.byref(desc), L.OP_SIP, 0, width))
+    code = lib.band_sip(ct.byref(desc), C.diag5(), C.view(C.dev["f"]).data_ptr(), x.data_ptr(),
+                        1e-12, 50, width, 30, 1e-12, iters.data_ptr(), resid.data_ptr(),
+                        status.data_ptr(), ws.data_ptr(), ws.numel(), _stream())
+    assert code == L.OK
+    C.check_guards()
+    assert (status.cpu() == 0).all()
+    assert C.rel(x, C.gepp()).max() <= 1e-9
+
+
+# slots of each diagonal outside the matrix (never part of a gradient)
+_OUTSIDE = {"a": slice(0, 2), "b": slice(0, 1), "c": slice(0, 0), "d": slice(-1, None),
+            "e": slice(-2, None)}
+
+
+@pytest.mark.parametrize("layout", LAYOUTS)
+@pytest.mark.parametrize("head", HEADS)
+@pytest.mark.parametrize("stored", [False, True])
+@pytest.mark.parametrize("k", [1, 2])
+def test_adjoint_writes_stay_inside(band, k, stored, layout, head):
+    """band_adjoint, without factors (the transposed system solved as a band system)
+    and with factors that band_factor wrote into a guarded buffer: the diagonals'
+    gradients, the right-hand side's, the statuses and the workspace."""
+    lib = L.load()
+    m = L.NPDM if k == 2 else L.NTDM
+    C = Case(k, 70, 600, layout, head, seed=50 + 2 * head + k)
+    desc = C.desc()
+    xc = C.gepp()
+    wc = np.random.default_rng(60 + head).uniform(-1.0, 1.0, (C.n, C.nsys))
+    x_d, w_d = C.put(xc), C.put(wc)
+    factors = None
+    if stored:
+        factors = C.workspace("factors", lib.band_workspace_size(ct.byref(desc), L.OP_FACTOR,
+                                                                 m, 0))
+        fst = C.flat_out("factor status", C.nsys, torch.int32)
+        assert lib.band_factor(ct.byref(desc), m, C.diag5(), factors.data_ptr(), factors.numel(),
+                               fst.data_ptr(), _stream()) == L.OK
+    keep = "abcde" if k == 2 else "bcd"
+    grads = {q: C.strided_out("grad " + q) for q in keep}
+    gf = C.strided_out("grad f")
+    status = C.flat_out("status", C.nsys, torch.int32)
+    ws = C.workspace("workspace", lib.band_workspace_size(ct.byref(desc), L.OP_ADJOINT, m, 0))
+    G = L.DIAG5(*[(grads[q].data_ptr() if q in grads else None) for q in "abcde"])
+    code = lib.band_adjoint(ct.byref(desc), m, factors.data_ptr() if stored else None,
+                            C.diag5(), x_d.data_ptr(), w_d.data_ptr(), G, gf.data_ptr(),
+                            status.data_ptr(), ws.data_ptr(), ws.numel(), _stream())
+    assert code == L.OK
+    C.check_guards()
+    assert (status.cpu() == 0).all()
+    got = {q: grads[q].cpu().numpy() for q in grads}
+    gfh = gf.cpu().numpy()
+    for s in range(0, C.nsys, 7):
+        go, gfo, so = oracle.adjoint(k, *[C.system(q, s) for q in "abcde"], xc[:, s], wc[:, s])
+        assert so == "OK"
+        assert np.abs(gfh[:, s] - gfo).max() <= 1e-10 * np.abs(gfo).max(), s
+        for j, q in enumerate("abcde"):
+            if q in got:
+                mask = np.ones(C.n, dtype=bool)
+                mask[_OUTSIDE[q]] = False
+                ref = go[j][mask]
+                assert np.abs(got[q][mask, s] - ref).max() <= 1e-10 * np.abs(ref).max(), (q, s)
+
+
+@pytest.mark.parametrize("layout", LAYOUTS)
+@pytest.mark.parametrize("head", HEADS)
+@pytest.mark.parametrize("k", [1, 2])
+def test_det_writes_stay_inside(band, k, layout, head):
+    """band_det with zero pivots in three systems (the flagged list and the series pass
+    in the workspace): mantissas, exponents, statuses."""
+    lib = L.load()
+    C = Case(k, 70, 600, layout, head, seed=70 + head, plant=("zero_row", (2, 40, 69)))
+    desc = C.desc()
+    mant = C.flat_out("det_mant", C.nsys, torch.float64)
+    ex = C.flat_out("det_exp", C.nsys, torch.int64)
+    status = C.flat_out("status", C.nsys, torch.int32)
+    ws = C.workspace("workspace", lib.band_workspace_size(ct.byref(desc), L.OP_DET, 0, 0))
+    code = lib.band_det(ct.byref(desc), C.diag5(), mant.data_ptr(), ex.data_ptr(),
+                        status.data_ptr(), ws.data_ptr(), ws.numel(), _stream())
+    assert code == L.OK
+    C.check_guards()
+    assert (status.cpu() == 0).all()
+    mant, ex = mant.cpu().numpy(), ex.cpu().numpy()
+    for s in range(C.nsys):
+        _, so, dm, dex, _ = oracle.symbolic(k, *[C.system(q, s) for q in "abcdef"])
+        assert so == "OK"
+        assert np.sign(mant[s]) == np.sign(dm)
+        assert abs(np.log2(abs(mant[s])) + ex[s] - (np.log2(abs(dm)) + dex)) <= 1e-12 * C.n, s
+
+
+@pytest.mark.parametrize("head", HEADS)
+def test_batch_writes_stay_inside(band, head):
+    """band_solve_batch over four problems of different layouts, methods and schedules
+    (NPDM contiguous, NTDM partitioned, SPDM two-sided with zero pivots, SIP), every
+    output and workspace guarded."""
+    lib = L.load()
+    specs = [(Case(2, 70, 600, "contiguous", head, seed=80), L.OP_SOLVE, L.NPDM, "auto"),
+             (Case(1, 45, 900, "interleaved", head, seed=81), L.OP_SOLVE, L.NTDM, "partitioned"),
+             (Case(2, 100, 300, "interleaved", head, seed=82, plant=("zero_row", (1, 99))),
+              L.OP_SOLVE, L.SPDM, "two_sided"),
+             (Case(2, 33, 500, "contiguous", head, seed=83), L.OP_SIP, 0, "auto")]
+    arr = (L.BandProblem * len(specs))()
+    outs = []
+    for P, (C, op, m, sched) in zip(arr, specs):
+        desc = C.desc(sched)
+        x = C.strided_out("x")
+        status = C.flat_out("status", C.nsys, torch.int32)
+        ws = C.workspace("workspace", lib.band_workspace_size(ct.byref(desc), op, m, 0))
+        P.op, P.method, P.desc = op, m, ct.pointer(desc)
+        P.diag = C.diag5()
+        P.f, P.x, P.sys_status = C.view(C.dev["f"]).data_ptr(), x.data_ptr(), status.data_ptr()
+        P.ws, P.ws_bytes = ws.data_ptr(), ws.numel()
+        if op == L.OP_SIP:
+            iters = C.flat_out("iters", C.nsys, torch.int32)
+            resid = C.flat_out("resid", C.nsys, torch.float64)
+            P.tol, P.max_it = 1e-12, 50
+            P.iters, P.resid = iters.data_ptr(), resid.data_ptr()
+        outs.append((desc, x, status))
+    assert lib.band_solve_batch(arr, len(specs), _stream()) == L.OK
+    for (C, op, m, sched), (desc, x, status) in zip(specs, outs):
+        C.check_guards()
+        assert (status.cpu() == 0).all(), (m, sched)
+        tol = 1e-9 if op == L.OP_SIP else (1e-10 if m == L.SPDM else 1e-12)
+        assert C.rel(x, C.gepp()).max() <= tol, (op, m, sched)
