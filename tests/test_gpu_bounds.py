@@ -77,14 +77,46 @@ def _system(k, nsys, n, seed, plant=None):
     return D, f
 
 
-class Case:
+class Guards:
+    """Outputs made inside sentinel-filled buffers, checked together after a call."""
+
+    def __init__(self):
+        self.guards = []          # (name, buffer, check) of every output
+
+    def padded_out(self, name, count, dtype, head=FLAT_HEAD):
+        """count entries after `head` sentinels, TAIL sentinels after them."""
+        sent = X_SENT if dtype == torch.float64 else I_SENT
+        buf = torch.full((head + count + TAIL,), sent, dtype=dtype, device=DEV)
+        self.guards.append((name, buf, lambda h: (h[:head] == sent).all() and
+                            (h[head + count:] == sent).all()))
+        return buf[head:head + count]
+
+    def flat_out(self, name, count, dtype):
+        return self.padded_out(name, count, dtype)
+
+    def workspace(self, name, nbytes):
+        buf = torch.full((nbytes + 2 * WS_PAD,), WS_SENT, dtype=torch.uint8, device=DEV)
+        self.guards.append((name, buf, lambda h: (h[:WS_PAD] == WS_SENT).all() and
+                            (h[WS_PAD + nbytes:] == WS_SENT).all()))
+        ws = buf[WS_PAD:WS_PAD + nbytes]
+        assert ws.data_ptr() % 256 == 0
+        return ws
+
+    def check_guards(self):
+        torch.cuda.synchronize()
+        for name, buf, ok in self.guards:
+            assert ok(buf.cpu().numpy()), "%s written outside its elements" % name
+
+
+class Case(Guards):
     """One batch's inputs in guarded strided storage on the device; guarded strided,
     per-system and workspace outputs made on request and checked together."""
 
-    def __init__(self, k, nsys, n, layout, head, seed, plant=None):
+    def __init__(self, k, nsys, n, layout, head, seed=0, plant=None, data=None):
+        super().__init__()
         self.k, self.nsys, self.n, self.head = k, nsys, n, head
         self.ss, self.es = _strides(layout, nsys, n)
-        D, f = _system(k, nsys, n, seed, plant)
+        D, f = data if data is not None else _system(k, nsys, n, seed, plant)
         self.host = {}
         for q in "abcde":
             self.host[q], self.idx = _padded(D[q], head, self.ss, self.es, np.nan)
@@ -92,7 +124,6 @@ class Case:
         self.dev = {q: torch.from_numpy(v).to(DEV) for q, v in self.host.items()}
         self.inside = np.zeros(self.host["f"].size, dtype=bool)
         self.inside[self.idx.reshape(-1)] = True
-        self.guards = []          # (name, buffer, check) of every output
 
     def view(self, buf):
         return buf.as_strided((self.n, self.nsys), (self.es, self.ss), self.head)
@@ -115,26 +146,6 @@ class Case:
         buf = torch.full_like(self.dev["f"], X_SENT)
         self.guards.append((name, buf, lambda h: (h[~self.inside] == X_SENT).all()))
         return self.view(buf)
-
-    def flat_out(self, name, count, dtype):
-        sent = X_SENT if dtype == torch.float64 else I_SENT
-        buf = torch.full((FLAT_HEAD + count + TAIL,), sent, dtype=dtype, device=DEV)
-        self.guards.append((name, buf, lambda h: (h[:FLAT_HEAD] == sent).all() and
-                            (h[FLAT_HEAD + count:] == sent).all()))
-        return buf[FLAT_HEAD:FLAT_HEAD + count]
-
-    def workspace(self, name, nbytes):
-        buf = torch.full((nbytes + 2 * WS_PAD,), WS_SENT, dtype=torch.uint8, device=DEV)
-        self.guards.append((name, buf, lambda h: (h[:WS_PAD] == WS_SENT).all() and
-                            (h[WS_PAD + nbytes:] == WS_SENT).all()))
-        ws = buf[WS_PAD:WS_PAD + nbytes]
-        assert ws.data_ptr() % 256 == 0
-        return ws
-
-    def check_guards(self):
-        torch.cuda.synchronize()
-        for name, buf, ok in self.guards:
-            assert ok(buf.cpu().numpy()), "%s written outside its elements" % name
 
     def desc(self, schedule="auto", chunks=0):
         sched = {"auto": L.SCHED_AUTO, "thread": L.SCHED_THREAD, "two_sided": L.SCHED_TWO_SIDED,
@@ -352,3 +363,170 @@ def test_batch_writes_stay_inside(band, head):
         assert (status.cpu() == 0).all(), (m, sched)
         tol = 1e-9 if op == L.OP_SIP else (1e-10 if m == L.SPDM else 1e-12)
         assert C.rel(x, C.gepp()).max() <= tol, (op, m, sched)
+
+
+@pytest.mark.parametrize("head", HEADS)
+@pytest.mark.parametrize("method", ["numeric", "symbolic"])
+def test_ragged_single_call_writes_stay_inside(band, method, head):
+    """band_solve on a ragged packing (n in [16, 3000], TD and PD mixed, one thread per
+    system): x, statuses and the workspace guarded; zero pivots planted in three
+    systems for the symbolic methods."""
+    lib = L.load()
+    B = synth.cfg2(nsys=300, nmin=16, nmax=3000, seed_salt=90 + head)
+    offs, hbw, total, nsys = B["offsets"], B["hbw"], int(B["offsets"][-1]), B["nsys"]
+    if method == "symbolic":
+        for s in (0, 150, 299):
+            j = int(offs[s]) + 5
+            B["a"][j] = B["b"][j] = B["c"][j] = 0.0
+        B["f"] = None
+        x_true = B["x_true"]
+        f = B["c"] * x_true
+        for q, sh in (("b", 1), ("d", -1), ("a", 2), ("e", -2)):
+            f += B[q] * np.roll(x_true, sh)     # zero slots stop the spill-over
+        B["f"] = f
+    guard = lambda v: np.concatenate((np.full(head, np.nan), v, np.full(TAIL, np.nan)))
+    dev = {q: torch.from_numpy(guard(B[q])).to(DEV) for q in "abcdef"}
+    C = Guards()
+    x = C.padded_out("x", total, torch.float64, head)
+    status = C.flat_out("status", nsys, torch.int32)
+    offs_d = torch.from_numpy(offs).to(DEV)
+    hbw_d = torch.from_numpy(hbw).to(DEV)
+    desc = L.BandDesc(half_bw=2, dtype=L.F64, nsys=nsys, n=int(B["sizes"].max()), sys_stride=0,
+                      elem_stride=1, offsets=offs_d.data_ptr(), hbw=hbw_d.data_ptr(),
+                      total_rows=total, schedule=L.SCHED_AUTO, chunks=0)
+    m = L.AUTO_NUMERIC if method == "numeric" else L.AUTO_SYMBOLIC
+    ws = C.workspace("workspace", lib.band_workspace_size(ct.byref(desc), L.OP_SOLVE, m, 0))
+    D = L.DIAG5(*[dev[q][head:].data_ptr() for q in "abcde"])
+    code = lib.band_solve(ct.byref(desc), m, None, D, dev["f"][head:].data_ptr(),
+                          x.data_ptr(), status.data_ptr(), ws.data_ptr(), ws.numel(), _stream())
+    assert code == L.OK
+    C.check_guards()
+    assert (status.cpu() == 0).all()
+    ref, st, _, _ = oracle.batch("gepp", 2, tuple(B[q] for q in "abcde"), B["f"], nsys, 0, 0, 1,
+                                 offsets=offs, hbw=hbw)
+    assert (np.asarray(st) == 0).all()
+    xg = x.cpu().numpy()
+    for s in range(nsys):
+        lo, hi = int(offs[s]), int(offs[s + 1])
+        rel = np.abs(xg[lo:hi] - ref[lo:hi]).max() / np.abs(ref[lo:hi]).max()
+        assert rel <= (1e-12 if method == "numeric" else 1e-10), (s, rel)
+
+
+@pytest.mark.parametrize("head", HEADS)
+@pytest.mark.parametrize("schedule", ["thread", "two_sided", "partitioned"])
+def test_ragged_plan_writes_stay_inside(band, schedule, head):
+    """A ragged packing as size buckets in one band_solve_batch (id lists per bucket):
+    the packed x and the per-id statuses guarded."""
+    B = synth.cfg2(nsys=300, nmin=16, nmax=3000, seed_salt=95 + head)
+    offs, total, nsys = B["offsets"], int(B["offsets"][-1]), B["nsys"]
+    guard = lambda v: np.concatenate((np.full(head, np.nan), v, np.full(TAIL, np.nan)))
+    dev = {q: torch.from_numpy(guard(B[q])).to(DEV) for q in "abcdef"}
+    C = Guards()
+    x = C.padded_out("x", total, torch.float64, head)
+    status = C.flat_out("status", nsys, torch.int32)
+    plan = band.RaggedPlan(*(dev[q][head:head + total] for q in "abcdef"), offs, B["hbw"],
+                           schedule=schedule, x=x, status=status)
+    plan.run()
+    C.check_guards()
+    assert (status.cpu() == 0).all()
+    xg = x.cpu().numpy()
+    err = np.maximum.reduceat(np.abs(xg - B["x_true"]), offs[:-1])
+    assert err.max() <= 1e-12
+
+
+@pytest.mark.parametrize("layout", LAYOUTS)
+@pytest.mark.parametrize("head", [1, 4])
+@pytest.mark.parametrize("flags", [0, L.REFINE_PAIRS])
+def test_refine_writes_stay_inside(band, flags, layout, head):
+    """band_refine_solve_ex (FP32 factorisation, FP64 or pair residuals): x, the step
+    counts, statuses and the workspace guarded; FP32 diagonals with heads of one and
+    four elements (off and on the 16-byte boundary)."""
+    lib = L.load()
+    nsys, n = 70, 600
+    rng = np.random.default_rng(100 + head + flags)
+    D = synth.dominant(rng, nsys, n, k=2)
+    D = {q: np.asarray(D[q], dtype=np.float32).astype(np.float64) for q in "abcde"}
+    xt = rng.uniform(-1.0, 1.0, size=(n, nsys))
+    f = synth.band_matvec(2, D["a"], D["b"], D["c"], D["d"], D["e"], xt)
+    C = Case(2, nsys, n, layout, head, data=(D, f))
+    d32 = {q: torch.from_numpy(C.host[q].astype(np.float32)).to(DEV) for q in "abcde"}
+    diag32 = L.DIAG5(*[C.view(d32[q]).data_ptr() for q in "abcde"])
+    desc = C.desc()
+    desc.dtype = L.F32
+    x = C.strided_out("x")
+    steps = C.flat_out("steps", nsys, torch.int32)
+    status = C.flat_out("status", nsys, torch.int32)
+    ws = C.workspace("workspace", lib.band_workspace_size(ct.byref(desc), L.OP_REFINE, 0, 0))
+    code = lib.band_refine_solve_ex(ct.byref(desc), diag32, C.view(C.dev["f"]).data_ptr(),
+                                    x.data_ptr(), 1e-11, 10, flags, steps.data_ptr(),
+                                    status.data_ptr(), ws.data_ptr(), ws.numel(), _stream())
+    assert code == L.OK
+    C.check_guards()
+    assert (status.cpu() == 0).all()
+    assert C.rel(x, C.gepp()).max() <= 1e-10
+
+
+@pytest.mark.parametrize("layout", LAYOUTS)
+@pytest.mark.parametrize("head", HEADS)
+@pytest.mark.parametrize("nx,ny", [(16, 12), (40, 6)])
+def test_sip2d_writes_stay_inside(band, nx, ny, layout, head):
+    """band_sip2d (a warp per system for nx <= 32, a thread per system beyond): x,
+    iteration counts, residuals, statuses and the workspace guarded."""
+    lib = L.load()
+    nsys, N = 40, nx * ny
+    rng = np.random.default_rng(110 + nx + head)
+    r = rng.uniform(0.5, 4.0, nsys)[None, :]
+    G = {q: -r * rng.uniform(0.5, 1.5, (N, nsys)) for q in "swet"}
+    G["c"] = 1 + 4 * r + rng.uniform(0, 0.1, (N, nsys))
+    f = rng.uniform(-1, 1, (N, nsys))
+    # the five diagonals in the order band_sip2d takes them: s, w, c, e, t
+    C = Case(2, nsys, N, layout, head, data=(dict(zip("abcde", (G[q] for q in "swcet"))), f))
+    desc = C.desc()
+    x = C.strided_out("x")
+    iters = C.flat_out("iters", nsys, torch.int32)
+    resid = C.flat_out("resid", nsys, torch.float64)
+    status = C.flat_out("status", nsys, torch.int32)
+    ws = C.workspace("workspace", lib.band_workspace_size(ct.byref(desc), L.OP_SIP2D, 0, 0))
+    code = lib.band_sip2d(ct.byref(desc), nx, C.diag5(), C.view(C.dev["f"]).data_ptr(),
+                          x.data_ptr(), 1e-10, 500, iters.data_ptr(), resid.data_ptr(),
+                          status.data_ptr(), ws.data_ptr(), ws.numel(), _stream())
+    assert code == L.OK
+    C.check_guards()
+    assert (status.cpu() == 0).all()
+    xg = x.cpu().numpy()
+    for s in range(0, nsys, 5):
+        R = oracle.sip2d(nx, ny, *[G[q][:, s] for q in "swcet"], f[:, s], tol=1e-10, max_it=500)
+        assert R["status"] == "OK"
+        assert np.abs(xg[:, s] - R["x"]).max() <= 1e-9 * np.abs(R["x"]).max(), s
+
+
+@pytest.mark.parametrize("head", HEADS)
+@pytest.mark.parametrize("n", [40, 129])
+@pytest.mark.parametrize("k", [1, 2])
+def test_adi_step_writes_stay_inside(band, k, n, head):
+    """band_adi_step (its right-hand side and diagonal kernels and both sweeps' solves on
+    the automatic schedule): u, the 2n line statuses and the workspace guarded."""
+    lib = L.load()
+    rng = np.random.default_rng(120 + n + k + head)
+    u0 = rng.uniform(0, 1, (n, n))
+    src = rng.uniform(-1, 1, (n, n))
+    guard = lambda v, fill: np.concatenate((np.full(head, fill), v.reshape(-1),
+                                            np.full(TAIL, fill)))
+    C = Guards()
+    u = C.padded_out("u", n * n, torch.float64, head)
+    u.copy_(torch.from_numpy(u0.reshape(-1)))
+    sbuf = torch.from_numpy(guard(src, np.nan)).to(DEV)
+    status = C.flat_out("status", 2 * n, torch.int32)
+    grid = L.BandDesc(half_bw=k, dtype=L.F64, nsys=n, n=n, sys_stride=1, elem_stride=1,
+                      offsets=None, hbw=None, total_rows=0, schedule=0, chunks=0)
+    ws = C.workspace("workspace", lib.band_workspace_size(ct.byref(grid), L.OP_ADI, 0, 0))
+    tau, lam = 0.01, 2.0
+    code = lib.band_adi_step(ct.byref(grid), tau, lam, sbuf[head:].data_ptr(), u.data_ptr(),
+                             status.data_ptr(), ws.data_ptr(), ws.numel(), _stream())
+    assert code == L.OK
+    C.check_guards()
+    assert (status.cpu() == 0).all()
+    uo, st = oracle.adi_step(u0, tau, lam, src, k=k)
+    assert (np.asarray(st) == 0).all()
+    ug = u.cpu().numpy().reshape(n, n)
+    assert np.abs(ug - uo).max() <= 1e-12 * np.abs(uo).max()
