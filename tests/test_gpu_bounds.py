@@ -530,3 +530,37 @@ def test_adi_step_writes_stay_inside(band, k, n, head):
     assert (np.asarray(st) == 0).all()
     ug = u.cpu().numpy().reshape(n, n)
     assert np.abs(ug - uo).max() <= 1e-12 * np.abs(uo).max()
+
+
+@pytest.mark.parametrize("layout", LAYOUTS)
+@pytest.mark.parametrize("head", HEADS)
+@pytest.mark.parametrize("schedule", ["auto", "thread"])
+def test_mnpdm_writes_stay_inside(band, schedule, layout, head):
+    """MNPDM on PD systems whose outer diagonals are nonzero on 5 % of the rows: the
+    row-parallel path (its copies of the diagonals, the skip list and NTDM's workspace)
+    and one thread per system."""
+    lib = L.load()
+    nsys, n = 70, 600
+    rng = np.random.default_rng(130 + head)
+    D = synth.dominant(rng, nsys, n, k=2)
+    keep = rng.random((n, nsys)) < 0.05
+    keep[2, :] = keep[n - 3, :] = True
+    D["a"] = np.where(keep, D["a"], 0.0)
+    D["e"] = np.where(keep, D["e"], 0.0)
+    D["a"][:2] = 0.0
+    D["e"][n - 2:] = 0.0
+    D["c"] = 1.0 + sum(np.abs(D[q]) for q in "abde")
+    xt = rng.uniform(-1.0, 1.0, size=(n, nsys))
+    f = synth.band_matvec(2, D["a"], D["b"], D["c"], D["d"], D["e"], xt)
+    C = Case(2, nsys, n, layout, head, data=(D, f))
+    desc = C.desc(schedule)
+    x = C.strided_out("x")
+    status = C.flat_out("status", nsys, torch.int32)
+    ws = C.workspace("workspace", lib.band_workspace_size(ct.byref(desc), L.OP_SOLVE, L.MNPDM, 0))
+    code = lib.band_solve(ct.byref(desc), L.MNPDM, None, C.diag5(),
+                          C.view(C.dev["f"]).data_ptr(), x.data_ptr(), status.data_ptr(),
+                          ws.data_ptr(), ws.numel(), _stream())
+    assert code == L.OK
+    C.check_guards()
+    assert (status.cpu() == 0).all()
+    assert C.rel(x, C.gepp()).max() <= 1e-11
