@@ -205,7 +205,7 @@ size_t band_workspace_size(const band_desc* desc, int32_t op, int32_t method, in
  * systems are redone in truncated Laurent arithmetic in t and evaluated at t -> 0;
  * their determinant limit decides BAND_ERR_SINGULAR).
  * The symbolic fix-up runs one warp per flagged system; its series carry
- * double-double coefficients of t^-15 .. t^4, and a system that runs out of that
+ * double-double coefficients of t^-15 .. t^3, and a system that runs out of that
  * window is redone with t^-15 .. t^16 (BAND_ERR_SYMBOLIC_RANGE beyond).  A coefficient
  * that comes out below 2^-80 of the magnitude of the terms it was summed from is taken
  * as exactly zero (rounding residue of an exact cancellation).  The workspace holds

@@ -29,8 +29,9 @@
 //  * a pole deeper than t^-15, or an x_i whose t^0 coefficient is not known, is
 //    SYMBOLIC_RANGE.
 // The positive extent E of the window is chosen per attempt: a first pass keeps
-// t^-15 .. t^4 (most systems, e.g. a single zero pivot, need t^1 at most), and a system
-// that runs out of window there is solved again with t^16.  Truncation changes only
+// t^-15 .. t^3 (enough for a single zero pivot: its x needs t^1, and on PD rows the
+// known range loses two orders through the pole rows' products), and a system that
+// runs out of window there is solved again with t^16.  Truncation changes only
 // which coefficients are known, never their values, so the first pass can end in
 // SYMBOLIC_RANGE where the second does not, but not in a different result.
 #pragma once
@@ -210,7 +211,10 @@ __device__ __forceinline__ Ser mul(const Ser& x, const Ser& y, int E, bool& err,
 //   (n_{k+vm} - sum_{j>=1} m_{vm+j} c_{k-j}) / m_vm,
 // known below v + min(n.hi - n.v, m.hi - vm) (v = n.v - vm).  The three divisions share
 // the divisor and run interleaved; every finished coefficient is broadcast and pushed
-// into the sums of the higher ones.  sm, s1, s2, s3: staging rows.
+// into the sums of the higher ones.  A divisor with one nonzero coefficient (m.top =
+// vm, e.g. a constant) pushes nothing, so c_k = n_{k+vm} / m_vm is zero beyond n.top:
+// those steps are skipped (their coefficients stay the exact zeros they would get).
+// sm, s1, s2, s3: staging rows.
 __device__ __forceinline__ void div3(const Ser* num, const bool* use, const Ser& m, Ser* out,
                                      int E, bool& err, dd* sm, dd* s1, dd* s2, dd* s3) {
   const int lane = (int)(threadIdx.x & 31), e = lane - kZ;
@@ -235,7 +239,7 @@ __device__ __forceinline__ void div3(const Ser* num, const bool* use, const Ser&
   for (int k = 0; k < 3; ++k) sn[k][lane] = num[k].q;
   __syncwarp();
   const dd inv = dd_recip(sm[vm + kZ]);
-  int v[3], hi[3];
+  int v[3], hi[3], lim[3];
   bool act[3];
   Acc acc[3];
   int steps = 0;
@@ -243,6 +247,7 @@ __device__ __forceinline__ void div3(const Ser* num, const bool* use, const Ser&
   for (int k = 0; k < 3; ++k) {
     act[k] = false;
     v[k] = 0;
+    lim[k] = 0;
     hi[k] = E + 1;
     acc[k] = Acc{0.0, 0.0, 0.0};
     if (!use[k]) continue;
@@ -258,12 +263,14 @@ __device__ __forceinline__ void div3(const Ser* num, const bool* use, const Ser&
     }
     act[k] = true;
     if (e >= v[k] && e < hi[k]) acc[k] = acc_of(sn[k][e + vm + kZ]);
-    steps = max(steps, hi[k] - v[k]);
+    lim[k] = hi[k] - v[k];
+    if (m.top == vm) lim[k] = min(lim[k], num[k].top - num[k].v + 1);
+    steps = max(steps, lim[k]);
   }
   for (int st = 0; st < steps; ++st) {
 #pragma unroll
     for (int k = 0; k < 3; ++k) {
-      if (!act[k] || st >= hi[k] - v[k]) continue;
+      if (!act[k] || st >= lim[k]) continue;
       const int ek = v[k] + st;                  // the exponent finished in this step
       const dd mine = dd_mul(acc_value(acc[k]), inv);
       dd c;
@@ -411,11 +418,12 @@ __device__ inline Outcome solve_attempt(const SymArgs& p, int64_t s, int E, cons
   return o;
 }
 
-// The fix-up of the batch's t-th system by one warp: a pass with t^4, and one with
+// The fix-up of the batch's t-th system by one warp: a pass with t^3, and one with
 // t^16 if that ran out of window.
+constexpr int kFirstE = 3;
 __device__ inline void symbolic_warp(const SymArgs& p, int64_t t, const SlotView& sv, dd* stage) {
   const int64_t s = p.L.sys(t);
-  Outcome o = solve_attempt(p, s, 4, sv, stage);
+  Outcome o = solve_attempt(p, s, kFirstE, sv, stage);
   if (o.status == BAND_ERR_SYMBOLIC_RANGE) o = solve_attempt(p, s, kMaxE, sv, stage);
   if ((threadIdx.x & 31) == 0) {
     set_status(p.status, s, o.status);

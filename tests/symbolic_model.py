@@ -3,7 +3,7 @@
 It mirrors the kernel operation for operation: one series is a list of 32 lane values
 (lane l holds the coefficient of t^(l - 15)) in double-double, with the kernel's
 known-range bookkeeping (hi, v, top), residue flush, compensated sums of products,
-long division by three numerators at once, the positive extents 4 then 16, and the
+long division by three numerators at once, the positive extents 3 then 16, and the
 status rules.  Fused multiply-adds are evaluated exactly and rounded once (through
 fractions), as the GPU's FMA does.  It is test infrastructure: it lets the series
 pass be checked on the CPU against exact rational functions, and a disagreement
@@ -15,6 +15,7 @@ from fractions import Fraction
 
 KZ = 15
 KMAXE = 31 - KZ
+FIRST_E = 3
 NONE = 1 << 20
 RESIDUE = 2.0 ** -80
 OK, SINGULAR, NONFINITE, RANGE = 0, 4, 5, 7
@@ -169,7 +170,7 @@ def div3(num, use, m, E, err):
         return [Ser([ZERO] * 32, -KZ) for _ in range(3)]
     vm = m.v
     inv = dd_recip(m.q[vm + KZ])
-    v, hi, act = [0] * 3, [E + 1] * 3, [False] * 3
+    v, hi, act, lim = [0] * 3, [E + 1] * 3, [False] * 3, [0] * 3
     acc = [[Acc() for _ in range(32)] for _ in range(3)]
     res = [[ZERO] * 32 for _ in range(3)]
     steps = 0
@@ -189,10 +190,13 @@ def div3(num, use, m, E, err):
             e = lane - KZ
             if v[k] <= e < hi[k]:
                 acc[k][lane] = Acc(num[k].q[e + vm + KZ])
-        steps = max(steps, hi[k] - v[k])
+        lim[k] = hi[k] - v[k]
+        if m.top == vm:          # a monomial divisor: the quotient ends at n's top
+            lim[k] = min(lim[k], num[k].top - num[k].v + 1)
+        steps = max(steps, lim[k])
     for st in range(steps):
         for k in range(3):
-            if not act[k] or st >= hi[k] - v[k]:
+            if not act[k] or st >= lim[k]:
                 continue
             ek = v[k] + st
             c = dd_mul(acc[k][ek + KZ].value(), inv)
@@ -293,10 +297,10 @@ def attempt(k, a, b, c, d, e, f, E, want_x=True):
 
 
 def solve(k, a, b, c, d, e, f, want_x=True):
-    """The fix-up of one system: extent 4, then 16 if that ran out of window.
+    """The fix-up of one system: extent 3, then 16 if that ran out of window.
     Returns (status, x, det_mant, det_exp)."""
     a, b, c, d, e, f = ([float(v) for v in arr] for arr in (a, b, c, d, e, f))
-    st, x, V, mant, ex = attempt(k, a, b, c, d, e, f, 4, want_x)
+    st, x, V, mant, ex = attempt(k, a, b, c, d, e, f, FIRST_E, want_x)
     if st == RANGE:
         st, x, V, mant, ex = attempt(k, a, b, c, d, e, f, KMAXE, want_x)
     ok = st in (OK, NONFINITE) and V == 0

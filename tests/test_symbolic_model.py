@@ -49,15 +49,38 @@ def test_model_against_exact_crowded(k):
 
 def test_model_window_bookkeeping():
     """A single zero pivot (TD [[0, 1], [1, 0]] within a larger system) needs t^1 at most:
-    the extent-4 pass settles it; the determinant is the exact one."""
+    the first pass settles it; the determinant is the exact one."""
     a = [0, 0, 0, 0]
     b = [0, 1, 1, 1]
     c = [0, 0, 2, 2]
     d = [1, 1, 1, 0]
     e = [0, 0, 0, 0]
     f = [1, 2, 3, 4]
-    st, x, V, mant, ex = M.attempt(1, *[[float(v) for v in arr] for arr in (a, b, c, d, e, f)], 4)
+    st, x, V, mant, ex = M.attempt(1, *[[float(v) for v in arr] for arr in (a, b, c, d, e, f)],
+                                   M.FIRST_E)
     sym = exact.symbolic_solve(1, a, b, c, d, e, f)
     assert st == M.OK and V == 0
     assert np.allclose(x, [float(v) for v in sym["x"]], rtol=0, atol=1e-15)
     assert mant * 2.0 ** ex == float(sym["det"])
+
+
+def test_model_first_pass_settles_one_pd_zero_pivot():
+    """PD rows with one exact zero pivot (a = b = c = 0 on row 7 of integer rows): the
+    pole rows' products cost the known range two orders, so t^3 is the least first pass
+    that still knows x to t^0 (t^2 runs out of window); the result is the exact limit."""
+    n, j = 16, 7
+    a = [0, 0] + [1] * (n - 2)
+    b = [0] + [-3] * (n - 1)
+    c = [9] * n
+    d = [-3] * (n - 1) + [0]
+    e = [1] * (n - 2) + [0, 0]
+    a[j] = b[j] = c[j] = 0
+    f = [(3 * i) % 7 - 3 for i in range(n)]
+    rows = [[float(v) for v in arr] for arr in (a, b, c, d, e, f)]
+    assert M.FIRST_E == 3
+    assert M.attempt(2, *rows, 2)[0] == M.RANGE
+    st, x, V, mant, ex = M.attempt(2, *rows, M.FIRST_E)
+    sym = exact.symbolic_solve(2, a, b, c, d, e, f)
+    assert st == M.OK and V == 0 and sym["status"] == "OK"
+    xs = np.array([float(v) for v in sym["x"]])
+    assert np.abs(np.array(x) - xs).max() <= 1e-13 * np.abs(xs).max()
