@@ -104,7 +104,7 @@ bool choose_two_sided(const band_desc* d, bool alias) {
 // which the partitioned sweep leaves intact.  With the redo inside the partitioned
 // kernel, on one lane, the indefinite r = 2 ADI rows took 2.3-3.5 ms against 0.85-0.96
 // two-sided.  Numeric methods only (a symbolic system that meets a small chunk pivot
-// goes to the series pass, ~30 us a row); uniform batches of one bandwidth.
+// goes to the series pass, ~24 us a row); uniform batches of one bandwidth.
 namespace {
 
 bool auto_part(const band_desc* d, int32_t method) {
