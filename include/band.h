@@ -256,8 +256,12 @@ band_status band_adi_step(const band_desc* grid, double tau, double lambda, cons
  * (BAND_ERR_NOT_CONVERGED); a zero ILU(0) pivot is BAND_ERR_ZERO_PIVOT.  One warp per
  * system when nx <= 32 (lane x takes column x; the substitutions run on anti-diagonal
  * wavefronts), one thread per system otherwise; the same operations per unknown either
- * way (desc->schedule AUTO, chunks 0); x must not alias f; iters, resid (per system)
- * may be NULL.  ws: band_workspace_size(desc, BAND_OP_SIP2D, 0, 0). */
+ * way (desc->schedule AUTO, chunks 0).  The warp kernel reads each system's elements
+ * consecutively: a batch with elem_stride != 1 is copied system-major into the
+ * workspace (the diagonals, f and x; 7 nsys n doubles more workspace), solved there and
+ * x copied back, with the same bits as a contiguous batch.  A system whose ILU(0)
+ * fails keeps the caller's x.  x must not alias f; iters, resid (per system) may be
+ * NULL.  ws: band_workspace_size(desc, BAND_OP_SIP2D, 0, 0). */
 band_status band_sip2d(const band_desc* desc, int64_t nx, const void* const diag[5],
                        const double* f, double* x, double tol, int32_t max_it, int32_t* iters,
                        double* resid, int32_t* sys_status, void* ws, size_t ws_bytes,

@@ -291,17 +291,67 @@ __global__ void __launch_bounds__(128) k_sip2d_warp(const Sip2dArgs p) {
   }
 }
 
+// Copies between the batch's layout and the system-major one (element k of system s at
+// s n + k) of up to seven arrays (blockIdx.z): tiles of 32 systems x 32 elements pass
+// through shared memory, so the side where consecutive systems are adjacent (the
+// interleaved batch) and the side where consecutive elements are (the system-major
+// copy) are both read or written along consecutive addresses.
+struct Restage {
+  const double* src[7];
+  double* dst[7];
+};
+template <bool ToSysMajor>
+__global__ void __launch_bounds__(256) k_restage(const __grid_constant__ Restage r, const Layout L) {
+  __shared__ double tile[32][33];
+  const int64_t n = L.n, nsys = L.nsys, es = L.stride();
+  const int64_t s0 = (int64_t)blockIdx.x * 32, k0 = (int64_t)blockIdx.y * 32;
+  const double* src = r.src[blockIdx.z];
+  double* dst = r.dst[blockIdx.z];
+  const int tx = (int)(threadIdx.x & 31), ty = (int)(threadIdx.x >> 5);
+  // tile[j][i]: element k0 + j of system s0 + i
+  for (int j = ty; j < 32; j += 8) {
+    if (ToSysMajor) {
+      const int64_t sy = s0 + tx, k = k0 + j;
+      if (sy < nsys && k < n) tile[j][tx] = src[L.base(sy) + k * es];
+    } else {
+      const int64_t sy = s0 + j, k = k0 + tx;
+      if (sy < nsys && k < n) tile[tx][j] = src[sy * n + k];
+    }
+  }
+  __syncthreads();
+  for (int j = ty; j < 32; j += 8) {
+    if (ToSysMajor) {
+      const int64_t sy = s0 + j, k = k0 + tx;
+      if (sy < nsys && k < n) dst[sy * n + k] = tile[tx][j];
+    } else {
+      const int64_t sy = s0 + tx, k = k0 + j;
+      if (sy < nsys && k < n) dst[L.base(sy) + k * es] = tile[j][tx];
+    }
+  }
+}
+
+// Batches whose systems are not stored row-contiguously (elem_stride > 1, e.g.
+// interleaved) are staged: the warp kernel's lanes walk a grid row, i.e. consecutive
+// elements of one system, and on interleaved data those are nsys elements apart (one
+// sector per lane).  The five diagonals, f and x are copied system-major once, the
+// kernel runs on the copies (read ~12 times each over the updates), and x is copied
+// back.  x goes in too, so that a system whose ILU(0) fails keeps the caller's x.
+bool staged(const band_desc* d) { return d->elem_stride != 1 && (d->n + 31) / 32 <= 65535; }
+
 struct Sip2dWs {
   void *ls, *lw, *ruc, *y;
+  void* copy[7];      // staged s, w, c, e, t, f, x (system-major), or null
 };
 Sip2dWs carve_sip2d(const band_desc* d, void* base, size_t* bytes) {
   Carve c(base);
   const size_t rows = (size_t)spill_rows(d) * sizeof(double);
-  Sip2dWs w;
+  Sip2dWs w{};
   w.ls = c.take(rows);
   w.lw = c.take(rows);
   w.ruc = c.take(rows);
   w.y = c.take(rows);
+  if (staged(d))
+    for (int a = 0; a < 7; ++a) w.copy[a] = c.take((size_t)d->nsys * (size_t)d->n * sizeof(double));
   *bytes = c.size();
   return w;
 }
@@ -343,7 +393,36 @@ extern "C" band_status band_sip2d(const band_desc* desc, int64_t nx, const void*
               (double*)w.lw, (double*)w.ruc, (double*)w.y, tol, max_it, iters, resid,
               sys_status};
   cudaStream_t st = static_cast<cudaStream_t>(stream);
-  if (nx <= 32) k_sip2d_warp<<<(unsigned)((desc->nsys + 3) / 4), 128, 0, st>>>(p);
-  else k_sip2d<<<(unsigned)((desc->nsys + 127) / 128), 128, 0, st>>>(p);
+  if (nx > 32) {
+    k_sip2d<<<(unsigned)((desc->nsys + 127) / 128), 128, 0, st>>>(p);
+    return cuda_status(cudaGetLastError());
+  }
+  if (!staged(desc)) {
+    k_sip2d_warp<<<(unsigned)((desc->nsys + 3) / 4), 128, 0, st>>>(p);
+    return cuda_status(cudaGetLastError());
+  }
+  // the system-major copies: s, w, c, e, t, f, x in, the warp kernel, x out
+  const Layout L = layout_of(desc);
+  const dim3 tiles((unsigned)((desc->nsys + 31) / 32), (unsigned)((desc->n + 31) / 32), 7);
+  Restage in{};
+  for (int a = 0; a < 5; ++a) in.src[a] = (const double*)diag[a];
+  in.src[5] = f;
+  in.src[6] = x;
+  for (int a = 0; a < 7; ++a) in.dst[a] = (double*)w.copy[a];
+  k_restage<true><<<tiles, 256, 0, st>>>(in, L);
+  if (cudaGetLastError() != cudaSuccess) return BAND_ERR_CUDA;
+  band_desc dm = *desc;
+  dm.sys_stride = desc->n;
+  dm.elem_stride = 1;
+  p.L = layout_of(&dm);
+  p.s = in.dst[0]; p.w = in.dst[1]; p.c = in.dst[2]; p.e = in.dst[3]; p.t = in.dst[4];
+  p.f = in.dst[5];
+  p.x = in.dst[6];
+  k_sip2d_warp<<<(unsigned)((desc->nsys + 3) / 4), 128, 0, st>>>(p);
+  if (cudaGetLastError() != cudaSuccess) return BAND_ERR_CUDA;
+  Restage out{};
+  out.src[0] = in.dst[6];
+  out.dst[0] = x;
+  k_restage<false><<<dim3(tiles.x, tiles.y, 1), 256, 0, st>>>(out, L);
   return cuda_status(cudaGetLastError());
 }

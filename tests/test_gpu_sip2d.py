@@ -82,3 +82,43 @@ def test_sip2d_cap_and_zero_pivot(band):
     R = oracle.sip2d(nx, ny, *[D[q][:, 0] for q in "swcet"], f[:, 0], tol=1e-10, max_it=3)
     assert R["status"] == "NOT_CONVERGED" and R["iters"] == 3
     assert abs(rs.cpu().numpy()[0] - R["resid"]) <= 1e-9 * R["resid"]
+
+
+@pytest.mark.parametrize("nx,ny", [(16, 16), (32, 5), (7, 9)])
+def test_sip2d_layouts_agree_bitwise(band, nx, ny):
+    """Interleaved batches are copied system-major for the warp kernel and x is copied
+    back: the same grids in either layout give the same x, update counts and residuals
+    bit for bit."""
+    nsys = 45
+    rng = np.random.default_rng(200 + nx + ny)
+    D, f = grid_batch(rng, nx, ny, nsys)
+    out = {}
+    for layout in ("interleaved", "contiguous"):
+        T = {q: _dev(D[q], layout) for q in "swcet"}
+        out[layout] = band.sip2d(T["s"], T["w"], T["c"], T["e"], T["t"], _dev(f, layout), nx,
+                                 tol=1e-10, max_it=500)
+    torch.cuda.synchronize()
+    (xi, ii, ri, si), (xc, ic, rc, sc) = out["interleaved"], out["contiguous"]
+    assert xi.stride() != xc.stride()
+    assert (si.cpu() == OK).all() and torch.equal(si, sc)
+    assert torch.equal(xi.contiguous(), xc.contiguous())
+    assert torch.equal(ii, ic) and torch.equal(ri, rc)
+
+
+def test_sip2d_zero_pivot_keeps_x(band):
+    """A system whose ILU(0) meets a zero pivot is not updated: its x keeps the caller's
+    values, on the interleaved (staged) layout and on the contiguous one."""
+    rng = np.random.default_rng(12)
+    nx, ny, nsys = 16, 8, 40
+    D, f = grid_batch(rng, nx, ny, nsys)
+    D["c"][0, 5] = 0.0
+    for layout in ("interleaved", "contiguous"):
+        T = {q: _dev(D[q], layout) for q in "swcet"}
+        x0 = _dev(np.full((nx * ny, nsys), 7.25), layout)
+        x, it, rs, st = band.sip2d(T["s"], T["w"], T["c"], T["e"], T["t"], _dev(f, layout), nx,
+                                   x=x0)
+        torch.cuda.synchronize()
+        st = st.cpu().numpy()
+        assert st[5] == ZERO_PIVOT and (np.delete(st, 5) == OK).all()
+        assert (x[:, 5].cpu().numpy() == 7.25).all(), layout
+        assert not (x[:, 4].cpu().numpy() == 7.25).any()
