@@ -20,7 +20,7 @@
 // Readings (the paper is silent on the arithmetic of its symbolic methods):
 //  * one symbol stands for every pivot whose known coefficients are all zero, and
 //    that pivot becomes exactly t; a pivot whose t^0 coefficient is not known
-//    (hi < 1) cannot be judged and ends the attempt (SYMBOLIC_RANGE);
+//    (hi < 1) cannot be decided and ends the attempt (SYMBOLIC_RANGE);
 //  * x(t) is analytic at t = 0 for nonsingular A, so the negative powers of every x_i
 //    are rounding residue and are cleared; x_i is its t^0 coefficient;
 //  * det A = lim prod mu_i(t): V = sum of the pivots' valuations; V > 0 -> det A = 0

@@ -85,7 +85,7 @@ def _groups(systems):
     return out
 
 
-def _judge(x, st, group, k):
+def _classify(x, st, group, k):
     """Compare one group's results with the exact limits; returns counts."""
     res = dict(ok=0, range=0, nonsingular=0, singular=0, singular_range=0)
     for j, sy in enumerate(group):
@@ -124,7 +124,7 @@ def test_crowded_zero_pivots_every_schedule(band, crowded, k, schedule, chunks):
         x, st = band.solve(a, T["b"], T["c"], T["d"], e, T["f"], method=method,
                            schedule=schedule, chunks=chunks)
         torch.cuda.synchronize()
-        _tally(total, _judge(x.cpu().numpy(), st.cpu().numpy(), group, k))
+        _tally(total, _classify(x.cpu().numpy(), st.cpu().numpy(), group, k))
     assert total["nonsingular"] >= 100 and total["singular"] >= 100
     assert total["range"] <= total["nonsingular"] // 100, total
     assert total["singular_range"] <= total["singular"] // 100, total
@@ -146,7 +146,7 @@ def test_crowded_zero_pivots_batched(band, crowded):
     torch.cuda.synchronize()
     total = {}
     for (k, T, group), res in zip(specs, outs):
-        _tally(total, _judge(res["x"].cpu().numpy(), res["status"].cpu().numpy(), group, k))
+        _tally(total, _classify(res["x"].cpu().numpy(), res["status"].cpu().numpy(), group, k))
     assert total["range"] <= total["nonsingular"] // 100, total
     assert total["singular_range"] <= total["singular"] // 100, total
 

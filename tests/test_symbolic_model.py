@@ -3,7 +3,7 @@ a lane-by-lane restatement of csrc/symbolic.cuh) against exact rational function
 (oracle.exact) on integer systems with crowded zero pivots: the same acceptance bar as
 the GPU test -- the exact limit with status OK, SINGULAR for a singular matrix, and
 SYMBOLIC_RANGE (the window or the precision ran out) on at most 1 % -- so that a change
-of the kernel's series arithmetic can be judged here before it reaches a GPU."""
+of the kernel's series arithmetic can be checked here before it reaches a GPU."""
 import numpy as np
 import pytest
 
